@@ -1,0 +1,296 @@
+"""Benchmark: FCFS flight-plan scheduling throughput (scheduled plans/s) on GB300.
+
+Workload (default): the 30 km x 30 km x 1 km airspace with a 512^2 fractal heightmap,
+3000 seeded multi-leg known plans and 1000 FCFS requests with 25 actions and horizons up
+to 1800 steps. One step = one whole FCFS pass: the plan table is restored to the 3000
+known plans (device copy) and the 1000 requests are planned, checked and admitted in
+order on the GPU. value = requests planned per second (admitted + rejected).
+
+  value  : requests already resident in device memory, trajectories left on the device
+  e2e    : through the C ABI with host buffers: known plans uploaded from host memory,
+           requests uploaded, trajectories and verdicts copied back, every step
+  roofline: the rollout kernel (dominant), CUDA-event durations over the timed region
+  cpu_baseline: the FP64 oracle on this host's cores on a bounded sample
+
+--impl reference runs the FP64 CPU oracle as the reference arm (rank 0 only).
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "scheduled plans/s vs known-plan count (plain/batched/learned); p99 latency"
+UNIT = "plans/s"
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.index = index
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.index)], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def traffic_from_profile(kernel_src):
+    """Per-launch DRAM traffic recorded from an ncu capture, valid only while the kernel's
+    source is unchanged (the profile records the source digest)."""
+    digest = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+    path = os.path.join(ROOT, "profiles", "rollout_kernel_c2.md")
+    try:
+        for line in open(path):
+            if line.startswith("traffic_bytes_per_slot_step:"):
+                parts = dict(kv.split("=") for kv in line.split(":", 1)[1].split())
+                if parts.get("src") == digest:
+                    return float(parts["value"])
+    except OSError:
+        pass
+    return None
+
+
+def cpu_baseline(sc, seconds=12.0):
+    """The FP64 oracle, as it stands, on the first requests of the same workload."""
+    from oracle import Oracle
+
+    o = Oracle.from_scenario(sc)
+    n = 0
+    t0 = time.perf_counter()
+    while n < len(sc.requests) and (time.perf_counter() - t0) < seconds:
+        o.schedule(sc.requests[n])
+        n += 1
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {n} FCFS requests of the workload against its {len(sc.plans)} known plans, "
+                      f"FP64 C oracle, one thread, {dt:.1f} s"}
+
+
+def run_reference(args, sc):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    from oracle import Oracle
+
+    per_step = max(1, args.ref_requests)
+    times = []
+    for i in range(args.warmup + args.steps):
+        o = Oracle.from_scenario(sc)
+        t0 = time.perf_counter()
+        for r in sc.requests[:per_step]:
+            o.schedule(r)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    tot = sum(times)
+    value = per_step * len(times) / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(sc, per_step),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"first {per_step} FCFS requests per step against {len(sc.plans)} known plans"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(sc, n_req):
+    return {"workload": sc.name, "known_plans": len(sc.plans), "requests_per_step": n_req,
+            "actions": len(sc.actions), "max_horizon": int(sc.requests["horizon"].max()),
+            "airspace_km": [round((sc.box[3] - sc.box[0]) / 1000), round((sc.box[4] - sc.box[1]) / 1000),
+                            round((sc.box[5] - sc.box[2]) / 1000, 1)],
+            "mode": "plain FCFS (one persistent rollout per request, sequential admission)",
+            "l2": "plan table (3 x 4096 x S fp32 planes) larger than L2 and rewritten by the restore every step",
+            "parallelism": "replicas"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="fmdp", choices=["fmdp", "reference"])
+    ap.add_argument("--requests", type=int, default=1000)
+    ap.add_argument("--ref-requests", type=int, default=6)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    rank, local_rank, world = dist_env()
+    if world > 1:
+        os.environ["CUDA_VISIBLE_DEVICES"] = str(local_rank)
+
+    from paper_2008_03518_gb300 import scenarios as S
+
+    sc = S.c2_plain_scale(n_requests=args.requests)
+    if args.impl == "reference":
+        run_reference(args, sc)
+        return
+
+    import torch
+
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", 0))
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    from paper_2008_03518_gb300.fmdp import Scheduler
+
+    s = Scheduler.from_scenario(sc)
+    stream = torch.cuda.current_stream()
+    s.set_stream(stream.cuda_stream)
+    s.snapshot()
+    s.stage(sc.requests)
+
+    def step():
+        s.restore()
+        return s.schedule_staged()
+
+    for _ in range(args.warmup):
+        step()
+    clocks = ClockSampler(local_rank if world == 1 else 0)
+    clocks.start()
+    s.set_profiling(True)
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    admitted = 0
+    for _ in range(args.steps):
+        admitted = step()
+    ev1.record(stream)
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    st = s.stats()
+    s.set_profiling(False)
+    clk = clocks.stop()
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    n_req = len(sc.requests)
+    value = world * n_req * args.steps / (ms / 1e3)
+
+    # ---- roofline of the rollout kernel over the timed region
+    peaks, peak_kind = measured_peaks()
+    launches = max(st["rollout_launches"], 1)
+    avg_ms = st["rollout_ms"] / launches
+    bytes_per_launch = 12.0 * st["slots_scanned"] / launches
+    achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
+    tr = traffic_from_profile(os.path.join(ROOT, "paper_2008_03518_gb300", "csrc", "rollout.cu"))
+    roofline = {"kernel": "rollout_kernel", "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                "traffic": (tr * st["slots_scanned"] / launches) if tr is not None else None,
+                "peak_source": peak_kind,
+                "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_ms,
+                "cluster_size": st["cluster_size"], "threads_per_cta": st["threads_per_cta"],
+                "slots_per_cta": st["slots_per_cta"], "steps_per_launch": st["rollout_steps"] / launches,
+                "us_per_rollout_step": 1e3 * st["rollout_ms"] / max(st["rollout_steps"], 1),
+                "share_of_step": st["rollout_ms"] / ms}
+    gpu_launches = st["rollout_launches"] + st["sepcheck_launches"] + st["admit_launches"] + args.steps
+
+    # ---- end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        plans = [(p.t0, p.xyz) for p in sc.plans]
+        h2d = sum(p.xyz.nbytes + 12 for p in sc.plans) + n_req * 80
+        d2h = 0
+
+        def e2e_step():
+            s.clear()
+            s.add_plans(plans)
+            res = s.schedule_many(sc.requests)
+            return sum(r["xyz"].nbytes + r["actions"].nbytes + 48 for r in res)
+
+        for _ in range(1):
+            e2e_step()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        k = max(1, min(args.steps, 3))
+        for _ in range(k):
+            d2h = e2e_step()
+        e1.record(stream)
+        barrier()
+        ems = e0.elapsed_time(e1)
+        e2e = {"value": world * n_req * k / (ems / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "steps": k}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(sc, n_req),
+            "admitted_per_step": admitted, "e2e": e2e, "gpu_launches": gpu_launches, "roofline": roofline,
+            "clocks": clk}
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(sc, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    s.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

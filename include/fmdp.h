@@ -1,0 +1,213 @@
+/*
+ * fmdp — GB300-native FastMDP first-come-first-served flight-plan scheduler.
+ *
+ * C ABI of libfmdp.so. Plain C types only; every pointer argument is a HOST pointer
+ * owned by the caller and is copied in or out before the call returns (except where
+ * a function says otherwise). Device memory is owned by the library.
+ *
+ * The method is the paper's (Bertram, Zambreno, Wei, "Scalable FastMDP for
+ * Pre-departure Airspace Reservation and Strategic De-conflict", arXiv 2008.03518):
+ *   - a request (origin, destination, departure) is planned by the FastMDP greedy
+ *     rollout: at every step each action's successor state is scored with the
+ *     closed-form value of Alg. 1 (goal peak minus the aggregate of risk wells of
+ *     every known plan, Table 3, minus the hard-deck penalty) and the argmax action
+ *     is taken (Alg. 1, Alg. 3-9);
+ *   - the finished trajectory is checked for loss of separation against every known
+ *     plan and for terrain collision, and is stored as a known plan only if it is
+ *     conflict free (Sec. I and Sec. V, first-come-first-served).
+ *
+ * Conventions:
+ *   - every function returns an fmdp_status; no C++ exception crosses the ABI;
+ *   - a rejected plan is NOT an error: it returns FMDP_OK with verdict != ADMITTED;
+ *   - on error, fmdp_last_error(ctx) returns a message (valid until the next call);
+ *   - a context is used by one host thread at a time;
+ *   - time is in integer steps of airspace.dt seconds; positions are metres.
+ */
+#ifndef FMDP_H
+#define FMDP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fmdp_ctx fmdp_ctx; /* opaque, library-owned */
+
+typedef int32_t fmdp_status;
+#define FMDP_OK 0
+#define FMDP_ERR_ARG (-1)     /* invalid argument (null pointer, bad size, non-finite value) */
+#define FMDP_ERR_OOM (-2)     /* device or host allocation failed */
+#define FMDP_ERR_CUDA (-3)    /* a CUDA call failed; the context should be destroyed */
+#define FMDP_ERR_TIMEOUT (-4) /* a bounded device wait ran out; results of the call are void */
+#define FMDP_ERR_FULL (-5)    /* no free plan slot */
+#define FMDP_ERR_RANGE (-6)   /* time steps outside the table's sliding window */
+#define FMDP_ERR_NOTFOUND (-7)
+
+/* Verdicts of a planning request (Sec. V: only a collision-free trajectory is accepted). */
+#define FMDP_ADMITTED 0
+#define FMDP_REJ_CONFLICT 1  /* loss of separation with a known plan at some step */
+#define FMDP_REJ_TERRAIN 2   /* a trajectory sample below the terrain surface */
+#define FMDP_REJ_HORIZON 3   /* goal not captured within the request's horizon */
+#define FMDP_REJ_NO_ACTION 4 /* every successor left the airspace box */
+
+/* Airspace: box, step, plan-table geometry, terrain (Table 3 terrain peaks as static
+ * wells and/or a heightmap with a hard-deck clearance penalty, Alg. 1). */
+typedef struct {
+    double x0, y0, z0, x1, y1, z1; /* box (m); successors outside it are invalid */
+    double dt;                     /* step length (s) */
+    int32_t n_slices_window;       /* time steps held in the device plan table (ring) */
+    int32_t max_slots;             /* concurrent known plans the table can hold */
+    const float* heightmap;        /* [hm_ny][hm_nx] node heights over the box, or NULL */
+    int32_t hm_nx, hm_ny;
+    double clearance_m;            /* clearance below which the hard-deck penalty applies */
+    double deck_value;             /* penalty = deck_value - clearance (paper: 1000) */
+    const double* static_wells;    /* [n][6] x, y, z, R, |r|, gamma (restricted volumes) */
+    int32_t n_static_wells;        /* <= 64 */
+} fmdp_airspace;
+
+/* One action: heading change (a multiple of 15 degrees, |.| <= 180) and climb rate. */
+typedef struct {
+    double dpsi_deg, climb_mps;
+} fmdp_action;
+
+/* Separation minima: conflict iff horizontal distance < horiz_m AND |dz| < vert_m. */
+typedef struct {
+    double horiz_m, vert_m;
+} fmdp_sep;
+
+/* A risk well attached to every known plan, centred at p + tau * v (Table 3). */
+typedef struct {
+    double tau_s, radius_m, magnitude, gamma;
+} fmdp_well;
+
+typedef struct {
+    int32_t combine;          /* 0: max over negative peaks (paper, Alg. 5-8); 1: sum */
+    const fmdp_well* wells;   /* NULL: the paper's five wells (Table 3) */
+    int32_t n_wells;          /* <= 8 */
+    double goal_reward;       /* |r| of the goal peak (Table 3: 200) */
+    int32_t lookahead_W;      /* lookahead window; only 1 is implemented */
+    int32_t cluster_size;     /* CTAs cooperating on one rollout (0 = automatic) */
+    int32_t threads_per_cta;  /* 0 = automatic */
+    int32_t reserved;
+} fmdp_options;
+
+/* Fills *o with the defaults (max combine, Table 3 wells, goal 200, W = 1, automatic). */
+void fmdp_options_default(fmdp_options* o);
+
+/* Creates a scheduler on the current CUDA device. gamma: MDP discount, used as the decay
+ * of the goal peak (Sec. III: positive peaks share the MDP's discount). actions: up to 32,
+ * index order = tie-break order (lowest index wins). Copies every input. */
+fmdp_status fmdp_create(const fmdp_airspace* airspace, double gamma, const fmdp_action* actions,
+                        int32_t n_actions, const fmdp_sep* sep, const fmdp_options* options,
+                        fmdp_ctx** out);
+void fmdp_destroy(fmdp_ctx* ctx);
+const char* fmdp_last_error(fmdp_ctx* ctx);
+
+/* Uses the caller's CUDA stream (a cudaStream_t passed as void*) for all device work; NULL
+ * selects the library's own stream. Calls remain synchronous with respect to the host. */
+fmdp_status fmdp_set_stream(fmdp_ctx* ctx, void* stream);
+
+/* Stores a known plan without any conflict check (Sec. V: plans may come from an external
+ * source): n fp32 (x,y,z) points, point k at step t0_step + k. The points must lie within
+ * the table window. */
+fmdp_status fmdp_add_plan(fmdp_ctx* ctx, int64_t t0_step, const float* xyz, int32_t n,
+                          uint64_t* plan_id_out);
+/* Bulk form: n_plans plans, counts[i] points each, concatenated in xyz. ids_out may be NULL. */
+fmdp_status fmdp_add_plans(fmdp_ctx* ctx, int32_t n_plans, const int64_t* t0_steps,
+                           const int32_t* counts, const float* xyz, uint64_t* ids_out);
+
+typedef struct {
+    uint64_t req_id;
+    double ox, oy, oz;   /* origin (m) */
+    double gx, gy, gz;   /* destination (m) */
+    double speed_mps;    /* horizontal speed (> 0) */
+    int64_t depart_step; /* time step at the origin */
+    int32_t horizon;     /* maximum number of steps */
+    int32_t reserved;
+} fmdp_request;
+
+typedef struct {
+    int32_t verdict;             /* FMDP_ADMITTED or FMDP_REJ_* */
+    int32_t n_points;            /* trajectory samples including the origin */
+    uint64_t plan_id;            /* id of the stored plan if admitted, else 0 */
+    int32_t first_conflict_step; /* index of the first sample in conflict, -1 if none */
+    int32_t first_terrain_step;  /* index of the first sample below terrain, -1 if none */
+    double min_sep_h;            /* min horizontal distance to a plan within vert_m (inf if none) */
+    double min_sep_v;            /* min |dz| to a plan within horiz_m (inf if none) */
+    int32_t near_ties;           /* steps whose top-2 action values differed by < 1e-4 rel. */
+    int32_t replanned;           /* batch mode: 1 if the speculative plan was redone */
+    float* xyz;                  /* caller-owned [horizon+1][3] or NULL: trajectory samples */
+    uint8_t* actions;            /* caller-owned [horizon] or NULL: chosen action indices */
+} fmdp_result;
+
+/* Plans one request against every stored plan and admits it if conflict free. */
+fmdp_status fmdp_schedule(fmdp_ctx* ctx, const fmdp_request* req, fmdp_result* res);
+/* n requests in first-come-first-served (array) order; results identical to n calls of
+ * fmdp_schedule. The whole sequence is enqueued on the device without host round trips. */
+fmdp_status fmdp_schedule_many(fmdp_ctx* ctx, const fmdp_request* reqs, int32_t n,
+                               fmdp_result* res);
+/* Batched speculative FCFS: all n requests are planned concurrently against the table as
+ * it stands, then re-checked in array order; a request whose plan could have been changed
+ * by an earlier admitted request of the batch is re-planned. Results are identical to
+ * fmdp_schedule_many. */
+fmdp_status fmdp_schedule_batch(fmdp_ctx* ctx, const fmdp_request* reqs, int32_t n,
+                                fmdp_result* res);
+
+/* Device-resident variant used for kernel-side timing: fmdp_stage_requests copies the
+ * requests into library-owned device memory; fmdp_schedule_staged plans them in FCFS
+ * order like fmdp_schedule_many but leaves trajectories on the device (only verdicts and
+ * counts come back); fmdp_fetch_staged copies results of the last staged run. */
+fmdp_status fmdp_stage_requests(fmdp_ctx* ctx, const fmdp_request* reqs, int32_t n);
+fmdp_status fmdp_schedule_staged(fmdp_ctx* ctx, int32_t* n_admitted_out);
+fmdp_status fmdp_fetch_staged(fmdp_ctx* ctx, fmdp_result* res, int32_t n);
+
+/* Ids of stored plans with at least one sample in [t_begin, t_end). */
+fmdp_status fmdp_query_plans(fmdp_ctx* ctx, int64_t t_begin, int64_t t_end, uint64_t* ids,
+                             int32_t cap, int32_t* n_out);
+/* Samples of a stored plan (cap points of room in xyz). */
+fmdp_status fmdp_get_plan(fmdp_ctx* ctx, uint64_t id, int64_t* t0_out, float* xyz, int32_t cap,
+                          int32_t* n_out);
+/* Slides the window to start at t_now_step: plans whose last sample is before it are
+ * removed and their slots freed; table rows of earlier steps are cleared for reuse. */
+fmdp_status fmdp_expire(fmdp_ctx* ctx, int64_t t_now_step);
+/* Saves / restores the whole plan table and its bookkeeping (device copy, no host trip). */
+fmdp_status fmdp_snapshot(fmdp_ctx* ctx);
+fmdp_status fmdp_restore(fmdp_ctx* ctx);
+/* Removes every stored plan. */
+fmdp_status fmdp_clear(fmdp_ctx* ctx);
+
+/* ---- inspection entry points (tests, tracing) ---- */
+
+/* Rollout without separation check or admission. Optional per-step traces (NULL to skip):
+ * q [horizon][n_actions] fp64 action values (-inf invalid), states [horizon+1][3] fp64,
+ * headings [horizon+1] (index of 15-degree heading relative to the initial bearing),
+ * tie_flags [horizon]. res->verdict is FMDP_ADMITTED when the goal was captured. */
+fmdp_status fmdp_rollout_trace(fmdp_ctx* ctx, const fmdp_request* req, fmdp_result* res,
+                               double* q, double* states, int32_t* headings, uint8_t* tie_flags);
+
+typedef struct {
+    int32_t first_conflict_step, first_terrain_step;
+    int64_t conflicts;       /* number of (sample, plan) pairs in conflict */
+    double min_sep_h, min_sep_v;
+} fmdp_sep_report;
+/* Separation and terrain check of n fp32 samples from step t0 against the stored plans. */
+fmdp_status fmdp_sep_check(fmdp_ctx* ctx, int64_t t0_step, const float* xyz, int32_t n,
+                           fmdp_sep_report* out);
+
+typedef struct {
+    int64_t rollout_launches, sepcheck_launches, admit_launches;
+    double rollout_ms, sepcheck_ms, admit_ms; /* summed CUDA-event durations */
+    int64_t rollout_steps;                    /* rollout steps executed */
+    int64_t slots_scanned;                    /* (step, slot) pairs scanned by rollouts */
+    int64_t sep_pairs;                        /* (sample, slot) pairs scanned by sep_check */
+    int32_t cluster_size, threads_per_cta, slots_per_cta;
+} fmdp_stats;
+/* Per-kernel CUDA-event timing on the context's stream (off by default). */
+fmdp_status fmdp_set_profiling(fmdp_ctx* ctx, int32_t on);
+fmdp_status fmdp_get_stats(fmdp_ctx* ctx, fmdp_stats* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FMDP_H */

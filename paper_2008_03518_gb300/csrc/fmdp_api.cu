@@ -1,0 +1,1116 @@
+// Host runtime and C ABI of libfmdp: scheduler context, device plan table, slot
+// allocator, sliding time window and first-come-first-served sequencing.
+//
+// FCFS (Sec. I, Sec. V): requests are planned one after another against every stored
+// plan; each admitted trajectory is stored before the next request is planned. The
+// per-request chain (rollout -> separation check -> admission) is decided entirely on the
+// device, so a whole sequence of requests is enqueued on one stream with no host round
+// trip; the host only reads verdicts back at the end to update its bookkeeping.
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <set>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "fmdp_internal.cuh"
+
+using namespace fmdp;
+
+namespace {
+
+struct ApiError : std::runtime_error {
+    fmdp_status code;
+    ApiError(fmdp_status c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+void cuda_check(cudaError_t e, const char* what) {
+    if (e != cudaSuccess) {
+        const fmdp_status code = (e == cudaErrorMemoryAllocation) ? FMDP_ERR_OOM : FMDP_ERR_CUDA;
+        throw ApiError(code, std::string(what) + ": " + cudaGetErrorString(e));
+    }
+}
+#define CK(x) cuda_check((x), #x)
+
+void require(bool ok, fmdp_status code, const std::string& msg) {
+    if (!ok) throw ApiError(code, msg);
+}
+
+template <class T>
+struct DevArray {
+    T* p = nullptr;
+    size_t n = 0;
+    void ensure(size_t want) {
+        if (want <= n) return;
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+        size_t m = std::max<size_t>(want, 16);
+        CK(cudaMalloc(&p, m * sizeof(T)));
+        n = m;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+};
+
+template <class T>
+struct PinnedArray {
+    T* p = nullptr;
+    size_t n = 0;
+    void ensure(size_t want) {
+        if (want <= n) return;
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        n = 0;
+        size_t m = std::max<size_t>(want, n * 2);
+        CK(cudaMallocHost(&p, m * sizeof(T)));
+        n = m;
+    }
+    void release() {
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        n = 0;
+    }
+};
+
+struct PlanMeta {
+    int32_t slot;
+    int64_t t0;
+    int32_t n;
+};
+
+struct Book {  // host bookkeeping of the table (copied by snapshot / restore)
+    std::set<int32_t> free_slots;
+    std::map<uint64_t, PlanMeta> plans;
+    uint64_t next_id = 1;
+    int64_t t_base = 0;
+    int32_t S_hw = 0;
+};
+
+int32_t round_up(int32_t x, int32_t m) { return (x + m - 1) / m * m; }
+
+// Device buffers of one FCFS sequence run.
+struct SeqBuffers {
+    DevArray<fmdp_request> reqs;
+    DevArray<float> traj;
+    DevArray<uint8_t> acts;
+    DevArray<RolloutOut> rout;
+    DevArray<SepOut> sepo;
+    DevArray<int32_t> slots;
+    void release() {
+        reqs.release(); traj.release(); acts.release(); rout.release(); sepo.release(); slots.release();
+    }
+};
+
+thread_local std::string g_create_error;
+
+}  // namespace
+
+struct fmdp_ctx {
+    Model model{};
+    fmdp_airspace air{};
+    double gamma = 0.0;
+    fmdp_sep sep{};
+    fmdp_options opt{};
+    int32_t A = 0;
+
+    cudaStream_t own = nullptr;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int max_smem = 0;
+
+    // device plan table
+    float* X = nullptr;
+    float* Y = nullptr;
+    float* Z = nullptr;
+    int32_t T_win = 0, S_pad = 0, S_max = 0;
+    Book book;
+
+    float* hm = nullptr;
+    double* statics = nullptr;
+    int32_t* err = nullptr;
+
+    // work buffers
+    SeqBuffers seq;     // fmdp_schedule / fmdp_schedule_many
+    SeqBuffers stg;     // staged (device-resident) runs
+    DevArray<fmdp_request> reqs;
+    DevArray<float> traj;
+    DevArray<uint8_t> acts;
+    DevArray<RolloutOut> rout;
+    DevArray<SepOut> sepo;
+    DevArray<int32_t> slots;
+    DevArray<int64_t> t0s, offs;
+    DevArray<int32_t> counts;
+    DevArray<double> q_trace, st_trace;
+    DevArray<int32_t> hd_trace;
+    DevArray<uint8_t> tie_trace;
+    PinnedArray<float> h_traj;
+    PinnedArray<uint8_t> h_acts;
+    PinnedArray<RolloutOut> h_rout;
+    PinnedArray<SepOut> h_sep;
+
+    // staged (device-resident) requests
+    std::vector<fmdp_request> staged;
+    int32_t staged_cap = 0;
+    bool staged_done = false;
+
+    // snapshot
+    float* sX = nullptr;
+    float* sY = nullptr;
+    float* sZ = nullptr;
+    Book snap;
+    bool has_snap = false;
+
+    // profiling
+    bool profiling = false;
+    fmdp_stats stats{};
+    std::vector<cudaEvent_t> ev_pool;
+    struct Pending { int kind; cudaEvent_t a, b; };
+    std::vector<Pending> pending;
+    size_t ev_next = 0;
+
+    int last_cs = 1, last_threads = 256, last_chunk = 0;
+    std::string err_msg;
+};
+
+namespace {
+
+// ------------------------------------------------------------------ model constants
+
+void fill_model(fmdp_ctx* c, const std::vector<fmdp_well>& wells, const std::vector<fmdp_action>& actions,
+                const double* host_statics) {
+    Model& m = c->model;
+    const fmdp_airspace& a = c->air;
+    m.box[0] = a.x0; m.box[1] = a.y0; m.box[2] = a.z0;
+    m.box[3] = a.x1; m.box[4] = a.y1; m.box[5] = a.z1;
+    m.dt = a.dt;
+    m.lg64 = std::log2(c->gamma);
+    m.lg32 = (float)m.lg64;
+    m.goal_reward = c->opt.goal_reward;
+    m.log2rg = c->opt.goal_reward > 0.0 ? std::log2(c->opt.goal_reward) : -INFINITY;
+    m.clearance = a.clearance_m;
+    m.deck = a.deck_value > 0.0 ? a.deck_value : 1000.0;
+    m.sep_h = c->sep.horiz_m;
+    m.sep_v = c->sep.vert_m;
+    m.A = (int32_t)actions.size();
+    m.combine = c->opt.combine;
+    for (size_t i = 0; i < actions.size(); ++i) {
+        m.dh[i] = (int32_t)std::lround(actions[i].dpsi_deg / 15.0);
+        m.climb[i] = actions[i].climb_mps;
+    }
+    m.n_wells = (int32_t)wells.size();
+    double rmax = 0.0, magmax = 0.0, taumax = 0.0;
+    for (size_t k = 0; k < wells.size(); ++k) {
+        const fmdp_well& w = wells[k];
+        m.w_tau[k] = (float)w.tau_s;
+        m.w_tau64[k] = w.tau_s;
+        m.w_R64[k] = w.radius_m;
+        m.w_R2[k] = (float)(w.radius_m * w.radius_m);
+        m.w_band[k] = kWellBand * m.w_R2[k];
+        m.w_L[k] = w.magnitude > 0.0 ? (float)std::log2(w.magnitude) : -INFINITY;
+        m.w_lg[k] = (float)std::log2(w.gamma);
+        rmax = std::max(rmax, w.radius_m);
+        magmax = std::max(magmax, w.magnitude);
+        taumax = std::max(taumax, std::fabs(w.tau_s));
+    }
+    m.reach_base = (float)(rmax + 1.0);
+    m.tau_absmax = (float)taumax;
+    m.n_static = a.n_static_wells;
+    for (int w = 0; w < a.n_static_wells; ++w) {
+        const double* s = host_statics + 6 * w;
+        m.st_R2[w] = (float)(s[3] * s[3]);
+        m.st_band[w] = kWellBand * m.st_R2[w];
+        m.st_L[w] = s[4] > 0.0 ? (float)std::log2(s[4]) : -INFINITY;
+        m.st_lg[w] = (float)std::log2(s[5]);
+        magmax = std::max(magmax, s[4]);
+    }
+    m.sum_ref = magmax > 0.0 ? (float)std::log2(magmax) : 0.0f;
+    m.sum_scale = std::exp2((double)m.sum_ref - 40.0);
+    m.hm_nx = a.heightmap ? a.hm_nx : 0;
+    m.hm_ny = a.heightmap ? a.hm_ny : 0;
+    m.hm_sx = a.heightmap ? (float)((a.hm_nx - 1) / (a.x1 - a.x0)) : 0.f;
+    m.hm_sy = a.heightmap ? (float)((a.hm_ny - 1) / (a.y1 - a.y0)) : 0.f;
+    m.hm = c->hm;
+    m.statics = c->statics;
+}
+
+TableView table_view(fmdp_ctx* c) {
+    TableView v;
+    v.X = c->X;
+    v.Y = c->Y;
+    v.Z = c->Z;
+    v.T_win = c->T_win;
+    v.S_pad = c->S_pad;
+    v.t_base = c->book.t_base;
+    return v;
+}
+
+// ------------------------------------------------------------------ profiling
+
+cudaEvent_t next_event(fmdp_ctx* c) {
+    if (c->ev_next == c->ev_pool.size()) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        c->ev_pool.push_back(e);
+    }
+    return c->ev_pool[c->ev_next++];
+}
+struct KernelTimer {
+    fmdp_ctx* c;
+    int kind;
+    cudaEvent_t a = nullptr;
+    KernelTimer(fmdp_ctx* c_, int k) : c(c_), kind(k) {
+        if (c->profiling) {
+            a = next_event(c);
+            CK(cudaEventRecord(a, c->stream));
+        }
+    }
+    void stop() {
+        if (c->profiling) {
+            cudaEvent_t b = next_event(c);
+            CK(cudaEventRecord(b, c->stream));
+            c->pending.push_back({kind, a, b});
+        }
+    }
+};
+void collect_timers(fmdp_ctx* c) {
+    for (auto& p : c->pending) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, p.a, p.b));
+        if (p.kind == 0) { c->stats.rollout_ms += ms; c->stats.rollout_launches++; }
+        else if (p.kind == 1) { c->stats.sepcheck_ms += ms; c->stats.sepcheck_launches++; }
+        else { c->stats.admit_ms += ms; c->stats.admit_launches++; }
+    }
+    c->pending.clear();
+    c->ev_next = 0;
+}
+
+// ------------------------------------------------------------------ launch geometry
+
+struct Geometry {
+    int32_t S_scan, cs, threads, chunk;
+    size_t smem;
+};
+
+Geometry geometry(fmdp_ctx* c, int32_t S_hw) {
+    Geometry g;
+    g.S_scan = round_up(std::max(S_hw, 0), 32);
+    int cs = c->opt.cluster_size;
+    if (cs <= 0) {
+        const int want = (g.S_scan + 1023) / 1024;
+        cs = 1;
+        while (cs < want && cs < kMaxCluster) cs *= 2;
+    }
+    cs = std::max(1, std::min(cs, kMaxCluster));
+    for (;;) {
+        g.cs = cs;
+        g.chunk = std::max(32, round_up((g.S_scan + cs - 1) / cs, 32));
+        g.threads = c->opt.threads_per_cta > 0 ? c->opt.threads_per_cta : (g.chunk > 512 ? 512 : 256);
+        g.smem = rollout_smem_bytes(g.chunk, g.threads);
+        if ((int)g.smem <= c->max_smem || cs >= kMaxCluster) break;
+        cs *= 2;  // partition too large for one CTA's shared memory: spread it wider
+    }
+    require((int)g.smem <= c->max_smem, FMDP_ERR_ARG, "plan table partition exceeds shared memory");
+    // the cluster must fit on one GPC: halve it until the hardware can place one
+    while (g.cs > 1 && rollout_max_active_clusters(g.cs, g.threads, g.smem) < 1) {
+        g.cs /= 2;
+        g.chunk = std::max(32, round_up((g.S_scan + g.cs - 1) / g.cs, 32));
+        g.smem = rollout_smem_bytes(g.chunk, g.threads);
+        require((int)g.smem <= c->max_smem, FMDP_ERR_ARG, "plan table partition exceeds shared memory");
+    }
+    c->last_cs = g.cs;
+    c->last_threads = g.threads;
+    c->last_chunk = g.chunk;
+    return g;
+}
+
+void check_request(fmdp_ctx* c, const fmdp_request& r) {
+    require(std::isfinite(r.ox) && std::isfinite(r.oy) && std::isfinite(r.oz) && std::isfinite(r.gx) &&
+                std::isfinite(r.gy) && std::isfinite(r.gz),
+            FMDP_ERR_ARG, "request coordinates must be finite");
+    require(std::isfinite(r.speed_mps) && r.speed_mps > 0.0, FMDP_ERR_ARG, "request speed must be > 0");
+    require(r.horizon >= 0 && r.horizon < (1 << 24), FMDP_ERR_ARG, "request horizon out of range");
+    const int64_t lo = c->book.t_base, hi = c->book.t_base + c->T_win;
+    require(r.depart_step >= lo && r.depart_step + (int64_t)r.horizon < hi, FMDP_ERR_RANGE,
+            "request steps fall outside the plan-table window");
+}
+
+int32_t take_slot(fmdp_ctx* c) {
+    require(!c->book.free_slots.empty(), FMDP_ERR_FULL, "no free plan slot");
+    const int32_t s = *c->book.free_slots.begin();
+    c->book.free_slots.erase(c->book.free_slots.begin());
+    return s;
+}
+
+void recompute_hw(fmdp_ctx* c) {
+    int32_t hw = 0;
+    for (auto& kv : c->book.plans) hw = std::max(hw, kv.second.slot + 1);
+    c->book.S_hw = hw;
+}
+
+// Enqueue rollout -> sep_check -> admission for n requests (device array c->reqs, slots in
+// c->slots) in FCFS order on the context's stream.
+void enqueue_sequence(fmdp_ctx* c, SeqBuffers& B, int32_t n, int32_t cap, const Geometry& g) {
+    const TableView tv = table_view(c);
+    CK(launch_sep_reset(B.sepo.p, n, c->stream));
+    for (int32_t i = 0; i < n; ++i) {
+        RolloutArgs ra{};
+        ra.m = c->model;
+        ra.tab = tv;
+        ra.S_scan = g.S_scan;
+        ra.chunk = g.chunk;
+        ra.cs = g.cs;
+        ra.cap = cap;
+        ra.reqs = B.reqs.p + i;
+        ra.n_req = 1;
+        ra.trace = 0;
+        ra.traj = B.traj.p + (size_t)i * cap * 3;
+        ra.acts = B.acts.p + (size_t)i * cap;
+        ra.out = B.rout.p + i;
+        ra.err = c->err;
+        {
+            KernelTimer t(c, 0);
+            CK(launch_rollout(ra, g.threads, g.smem, c->stream));
+            t.stop();
+        }
+        SepArgs sa{};
+        sa.m = c->model;
+        sa.tab = tv;
+        sa.S_scan = g.S_scan;
+        sa.cap = cap;
+        sa.traj = ra.traj;
+        sa.rout = ra.out;
+        sa.reqs = ra.reqs;
+        sa.out = B.sepo.p + i;
+        {
+            KernelTimer t(c, 1);
+            CK(launch_sepcheck(sa, 1, cap, c->stream));
+            t.stop();
+        }
+        AdmitArgs aa{};
+        aa.tab = tv;
+        aa.cap = cap;
+        aa.traj = ra.traj;
+        aa.rout = ra.out;
+        aa.reqs = ra.reqs;
+        aa.slots = B.slots.p + i;
+        aa.sep = sa.out;
+        aa.force = 0;
+        {
+            KernelTimer t(c, 2);
+            CK(launch_admit(aa, 1, cap, c->stream));
+            t.stop();
+        }
+    }
+}
+
+int32_t read_error_word(fmdp_ctx* c) {
+    int32_t e = 0;
+    CK(cudaMemcpyAsync(&e, c->err, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (e != 0) {
+        CK(cudaMemsetAsync(c->err, 0, sizeof(int32_t), c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    }
+    return e;
+}
+
+void fill_result(const RolloutOut& ro, const SepOut& so, fmdp_result* res) {
+    res->verdict = so.verdict >= 0 ? so.verdict : (ro.status == kStatusCaptured ? FMDP_ADMITTED : ro.status);
+    res->n_points = ro.n_points;
+    res->first_conflict_step = so.first_conflict == INT_MAX ? -1 : so.first_conflict;
+    res->first_terrain_step = so.first_terrain == INT_MAX ? -1 : so.first_terrain;
+    float mh, mv;
+    std::memcpy(&mh, &so.min_h_bits, 4);
+    std::memcpy(&mv, &so.min_v_bits, 4);
+    res->min_sep_h = mh;
+    res->min_sep_v = mv;
+    res->near_ties = ro.near_ties;
+}
+
+// Plans n requests (already validated) in FCFS order; results and trajectories to the
+// caller's buffers when res != nullptr. With staged = true the requests already sit in
+// c->stg.reqs on the device and trajectories stay there. Returns the number admitted.
+int32_t run_fcfs(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_result* res, bool staged) {
+    SeqBuffers& B = staged ? c->stg : c->seq;
+    const bool keep_on_device = staged;
+    int32_t admitted = 0;
+    int32_t done = 0;
+    while (done < n) {
+        const int32_t m = std::min<int32_t>(n - done, (int32_t)c->book.free_slots.size());
+        require(m > 0, FMDP_ERR_FULL, "no free plan slot");
+        std::vector<int32_t> sl(m);
+        int32_t hw = c->book.S_hw;
+        int32_t cap = 1;
+        for (int32_t i = 0; i < m; ++i) {
+            sl[i] = take_slot(c);
+            hw = std::max(hw, sl[i] + 1);
+            cap = std::max(cap, reqs[done + i].horizon + 1);
+        }
+        try {
+            const Geometry g = geometry(c, hw);
+            if (staged) {
+                require(m == n && done == 0, FMDP_ERR_FULL, "not enough free slots for the staged run");
+            } else {
+                B.reqs.ensure(m);
+                B.traj.ensure((size_t)m * cap * 3);
+                B.acts.ensure((size_t)m * cap);
+                B.rout.ensure(m);
+                B.sepo.ensure(m);
+                CK(cudaMemcpyAsync(B.reqs.p, reqs + done, m * sizeof(fmdp_request), cudaMemcpyHostToDevice,
+                                   c->stream));
+            }
+            B.slots.ensure(m);
+            CK(cudaMemcpyAsync(B.slots.p, sl.data(), m * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+            enqueue_sequence(c, B, m, cap, g);
+            c->h_rout.ensure(m);
+            c->h_sep.ensure(m);
+            CK(cudaMemcpyAsync(c->h_rout.p, B.rout.p, m * sizeof(RolloutOut), cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaMemcpyAsync(c->h_sep.p, B.sepo.p, m * sizeof(SepOut), cudaMemcpyDeviceToHost, c->stream));
+            if (res && !keep_on_device) {
+                c->h_traj.ensure((size_t)m * cap * 3);
+                c->h_acts.ensure((size_t)m * cap);
+                CK(cudaMemcpyAsync(c->h_traj.p, B.traj.p, (size_t)m * cap * 3 * sizeof(float),
+                                   cudaMemcpyDeviceToHost, c->stream));
+                CK(cudaMemcpyAsync(c->h_acts.p, B.acts.p, (size_t)m * cap, cudaMemcpyDeviceToHost, c->stream));
+            }
+            CK(cudaStreamSynchronize(c->stream));
+            if (c->profiling) collect_timers(c);
+            const int32_t ew = read_error_word(c);
+            require(ew == 0, FMDP_ERR_TIMEOUT, "a bounded device wait expired during a rollout");
+        } catch (...) {
+            for (int32_t s : sl) c->book.free_slots.insert(s);
+            throw;
+        }
+        for (int32_t i = 0; i < m; ++i) {
+            const RolloutOut& ro = c->h_rout.p[i];
+            const SepOut& so = c->h_sep.p[i];
+            const fmdp_request& rq = reqs[done + i];
+            c->stats.rollout_steps += ro.steps;
+            c->stats.slots_scanned += (int64_t)ro.steps * round_up(std::max(hw, 0), 32);
+            c->stats.sep_pairs += (int64_t)ro.n_points * round_up(std::max(hw, 0), 32);
+            uint64_t id = 0;
+            if (so.verdict == FMDP_ADMITTED) {
+                id = c->book.next_id++;
+                c->book.plans[id] = PlanMeta{sl[i], rq.depart_step, ro.n_points};
+                c->book.S_hw = std::max(c->book.S_hw, sl[i] + 1);
+                ++admitted;
+            } else {
+                c->book.free_slots.insert(sl[i]);
+            }
+            if (res) {
+                fmdp_result* o = res + done + i;
+                fill_result(ro, so, o);
+                o->plan_id = id;
+                o->replanned = 0;
+                if (!keep_on_device) {
+                    if (o->xyz)
+                        std::memcpy(o->xyz, c->h_traj.p + (size_t)i * cap * 3, (size_t)ro.n_points * 3 * sizeof(float));
+                    if (o->actions && ro.n_points > 1)
+                        std::memcpy(o->actions, c->h_acts.p + (size_t)i * cap, (size_t)(ro.n_points - 1));
+                }
+            }
+        }
+        if (keep_on_device) c->staged_cap = cap;
+        done += m;
+    }
+    return admitted;
+}
+
+void store_plans(fmdp_ctx* c, int32_t n_plans, const int64_t* t0s, const int32_t* counts, const float* xyz,
+                 uint64_t* ids_out) {
+    require(n_plans >= 0, FMDP_ERR_ARG, "n_plans < 0");
+    if (n_plans == 0) return;
+    require(t0s && counts && xyz, FMDP_ERR_ARG, "null plan arrays");
+    require((size_t)n_plans <= c->book.free_slots.size(), FMDP_ERR_FULL, "not enough free plan slots");
+    std::vector<int64_t> offs(n_plans);
+    int64_t total = 0;
+    int32_t maxc = 0;
+    const int64_t lo = c->book.t_base, hi = c->book.t_base + c->T_win;
+    for (int32_t i = 0; i < n_plans; ++i) {
+        require(counts[i] >= 1, FMDP_ERR_ARG, "a plan needs at least one point");
+        require(t0s[i] >= lo && t0s[i] + counts[i] <= hi, FMDP_ERR_RANGE, "plan steps fall outside the window");
+        offs[i] = total;
+        total += counts[i];
+        maxc = std::max(maxc, counts[i]);
+    }
+    for (int64_t i = 0; i < 3 * total; ++i) require(std::isfinite(xyz[i]), FMDP_ERR_ARG, "plan points must be finite");
+    std::vector<int32_t> sl(n_plans);
+    for (int32_t i = 0; i < n_plans; ++i) sl[i] = take_slot(c);
+    try {
+        c->traj.ensure((size_t)total * 3);
+        c->t0s.ensure(n_plans);
+        c->offs.ensure(n_plans);
+        c->counts.ensure(n_plans);
+        c->slots.ensure(n_plans);
+        CK(cudaMemcpyAsync(c->traj.p, xyz, (size_t)total * 3 * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(c->t0s.p, t0s, n_plans * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(c->offs.p, offs.data(), n_plans * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(c->counts.p, counts, n_plans * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(c->slots.p, sl.data(), n_plans * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+        AdmitArgs aa{};
+        aa.tab = table_view(c);
+        aa.cap = 0;
+        aa.traj = c->traj.p;
+        aa.slots = c->slots.p;
+        aa.force = 1;
+        aa.t0s = c->t0s.p;
+        aa.counts = c->counts.p;
+        aa.offs = c->offs.p;
+        CK(launch_admit(aa, n_plans, maxc, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    } catch (...) {
+        for (int32_t s : sl) c->book.free_slots.insert(s);
+        throw;
+    }
+    for (int32_t i = 0; i < n_plans; ++i) {
+        const uint64_t id = c->book.next_id++;
+        c->book.plans[id] = PlanMeta{sl[i], t0s[i], counts[i]};
+        c->book.S_hw = std::max(c->book.S_hw, sl[i] + 1);
+        if (ids_out) ids_out[i] = id;
+    }
+}
+
+// clears table rows for steps [a, b) (clipped to one window length)
+void clear_rows(fmdp_ctx* c, int64_t a, int64_t b) {
+    if (b <= a) return;
+    if (b - a >= c->T_win) {
+        const size_t n = (size_t)c->T_win * c->S_pad;
+        CK(launch_fill_nan(c->X, n, c->stream));
+        CK(launch_fill_nan(c->Y, n, c->stream));
+        CK(launch_fill_nan(c->Z, n, c->stream));
+        return;
+    }
+    int64_t ra = a % c->T_win;
+    if (ra < 0) ra += c->T_win;
+    int64_t len = b - a;
+    while (len > 0) {
+        const int64_t run = std::min<int64_t>(len, c->T_win - ra);
+        const size_t off = (size_t)ra * c->S_pad, n = (size_t)run * c->S_pad;
+        CK(launch_fill_nan(c->X + off, n, c->stream));
+        CK(launch_fill_nan(c->Y + off, n, c->stream));
+        CK(launch_fill_nan(c->Z + off, n, c->stream));
+        len -= run;
+        ra = 0;
+    }
+}
+
+void destroy_ctx(fmdp_ctx* c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    for (float* p : {c->X, c->Y, c->Z, c->sX, c->sY, c->sZ})
+        if (p) cudaFree(p);
+    if (c->hm) cudaFree(c->hm);
+    if (c->statics) cudaFree(c->statics);
+    if (c->err) cudaFree(c->err);
+    c->seq.release(); c->stg.release();
+    c->reqs.release(); c->traj.release(); c->acts.release(); c->rout.release(); c->sepo.release();
+    c->slots.release(); c->t0s.release(); c->offs.release(); c->counts.release();
+    c->q_trace.release(); c->st_trace.release(); c->hd_trace.release(); c->tie_trace.release();
+    c->h_traj.release(); c->h_acts.release(); c->h_rout.release(); c->h_sep.release();
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    if (c->own) cudaStreamDestroy(c->own);
+    delete c;
+}
+
+template <class F>
+fmdp_status guard(fmdp_ctx* c, F&& f) {
+    try {
+        f();
+        if (c) c->err_msg.clear();
+        return FMDP_OK;
+    } catch (const ApiError& e) {
+        if (c) c->err_msg = e.what();
+        return e.code;
+    } catch (const std::bad_alloc&) {
+        if (c) c->err_msg = "host allocation failed";
+        return FMDP_ERR_OOM;
+    } catch (const std::exception& e) {
+        if (c) c->err_msg = e.what();
+        return FMDP_ERR_ARG;
+    } catch (...) {
+        if (c) c->err_msg = "unknown error";
+        return FMDP_ERR_ARG;
+    }
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+
+extern "C" {
+
+void fmdp_options_default(fmdp_options* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->combine = 0;
+    o->wells = nullptr;
+    o->n_wells = 0;
+    o->goal_reward = 200.0;
+    o->lookahead_W = 1;
+}
+
+fmdp_status fmdp_create(const fmdp_airspace* air, double gamma, const fmdp_action* actions, int32_t n_actions,
+                        const fmdp_sep* sep, const fmdp_options* options, fmdp_ctx** out) {
+    if (!out) return FMDP_ERR_ARG;
+    *out = nullptr;
+    fmdp_ctx* c = nullptr;
+    try {
+        c = new fmdp_ctx();
+    } catch (...) {
+        return FMDP_ERR_OOM;
+    }
+    fmdp_status st = guard(c, [&] {
+        require(air && actions && sep, FMDP_ERR_ARG, "null airspace, actions or separation");
+        const fmdp_airspace& a = *air;
+        require(std::isfinite(a.x0) && std::isfinite(a.x1) && a.x1 > a.x0 && std::isfinite(a.y0) &&
+                    std::isfinite(a.y1) && a.y1 > a.y0 && std::isfinite(a.z0) && std::isfinite(a.z1) && a.z1 > a.z0,
+                FMDP_ERR_ARG, "airspace box must be finite with x1>x0, y1>y0, z1>z0");
+        require(std::isfinite(a.dt) && a.dt > 0.0, FMDP_ERR_ARG, "dt must be > 0");
+        require(gamma > 0.0 && gamma < 1.0, FMDP_ERR_ARG, "gamma must lie in (0, 1)");
+        require(n_actions >= 1 && n_actions <= kMaxActions, FMDP_ERR_ARG, "1 to 32 actions");
+        require(a.n_slices_window >= 4 && a.n_slices_window <= (1 << 24), FMDP_ERR_ARG, "window must hold >= 4 steps");
+        require(a.max_slots >= 1 && a.max_slots <= (1 << 24), FMDP_ERR_ARG, "max_slots out of range");
+        require(sep->horiz_m > 0.0 && sep->vert_m > 0.0, FMDP_ERR_ARG, "separation minima must be > 0");
+        require(a.n_static_wells >= 0 && a.n_static_wells <= kMaxStatic, FMDP_ERR_ARG, "at most 64 static wells");
+        require(a.n_static_wells == 0 || a.static_wells, FMDP_ERR_ARG, "null static wells");
+        require(!a.heightmap || (a.hm_nx >= 2 && a.hm_ny >= 2), FMDP_ERR_ARG, "heightmap needs >= 2x2 nodes");
+        std::vector<fmdp_action> acts(actions, actions + n_actions);
+        for (auto& ac : acts) {
+            const double q = ac.dpsi_deg / 15.0;
+            require(std::isfinite(q) && std::fabs(q - std::round(q)) < 1e-9 && std::fabs(ac.dpsi_deg) <= 180.0,
+                    FMDP_ERR_ARG, "heading changes must be multiples of 15 degrees within +-180");
+            require(std::isfinite(ac.climb_mps), FMDP_ERR_ARG, "climb rate must be finite");
+        }
+        fmdp_options o;
+        if (options) o = *options; else fmdp_options_default(&o);
+        require(o.combine == 0 || o.combine == 1, FMDP_ERR_ARG, "combine must be 0 (max) or 1 (sum)");
+        require(o.lookahead_W == 0 || o.lookahead_W == 1, FMDP_ERR_ARG, "only lookahead_W = 1 is implemented");
+        require(o.goal_reward >= 0.0 && std::isfinite(o.goal_reward), FMDP_ERR_ARG, "goal reward must be >= 0");
+        require(o.cluster_size >= 0 && o.cluster_size <= kMaxCluster, FMDP_ERR_ARG, "cluster size 0..16");
+        require(o.threads_per_cta == 0 || (o.threads_per_cta >= 64 && o.threads_per_cta <= 512 &&
+                                           o.threads_per_cta % 32 == 0),
+                FMDP_ERR_ARG, "threads per CTA: 0 or a multiple of 32 in [64, 512]");
+        std::vector<fmdp_well> wells;
+        if (o.wells && o.n_wells > 0) {
+            wells.assign(o.wells, o.wells + o.n_wells);
+        } else {
+            for (double t : {-5.0, 0.0, 5.0, 10.0, 15.0}) wells.push_back({t, 300.0 + 10.0 * t, 1000.0, 0.97});
+        }
+        require(wells.size() <= (size_t)kMaxWells, FMDP_ERR_ARG, "at most 8 wells per plan");
+        for (auto& w : wells)
+            require(w.radius_m > 0.0 && w.magnitude >= 0.0 && w.gamma > 0.0 && w.gamma < 1.0 &&
+                        std::isfinite(w.tau_s),
+                    FMDP_ERR_ARG, "well needs radius > 0, magnitude >= 0, gamma in (0,1)");
+        for (int w = 0; w < a.n_static_wells; ++w) {
+            const double* s = a.static_wells + 6 * w;
+            require(std::isfinite(s[0]) && std::isfinite(s[1]) && std::isfinite(s[2]) && s[3] > 0.0 && s[4] >= 0.0 &&
+                        s[5] > 0.0 && s[5] < 1.0,
+                    FMDP_ERR_ARG, "static well needs finite centre, R > 0, |r| >= 0, gamma in (0,1)");
+        }
+        c->air = a;
+        c->air.heightmap = nullptr;
+        c->air.static_wells = nullptr;
+        c->gamma = gamma;
+        c->sep = *sep;
+        c->opt = o;
+        c->opt.wells = nullptr;
+        c->A = n_actions;
+
+        CK(cudaGetDevice(&c->device));
+        CK(cudaDeviceGetAttribute(&c->max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
+        CK(cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking));
+        c->stream = c->own;
+        CK(prepare_rollout_kernel((size_t)c->max_smem));
+
+        c->T_win = a.n_slices_window;
+        c->S_max = a.max_slots;
+        c->S_pad = round_up(a.max_slots, 32);
+        const size_t plane = (size_t)c->T_win * c->S_pad;
+        CK(cudaMalloc(&c->X, plane * sizeof(float)));
+        CK(cudaMalloc(&c->Y, plane * sizeof(float)));
+        CK(cudaMalloc(&c->Z, plane * sizeof(float)));
+        CK(launch_fill_nan(c->X, plane, c->stream));
+        CK(launch_fill_nan(c->Y, plane, c->stream));
+        CK(launch_fill_nan(c->Z, plane, c->stream));
+        if (a.heightmap) {
+            const size_t nh = (size_t)a.hm_nx * a.hm_ny;
+            CK(cudaMalloc(&c->hm, nh * sizeof(float)));
+            CK(cudaMemcpyAsync(c->hm, a.heightmap, nh * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+            c->air.heightmap = c->hm;
+        }
+        if (a.n_static_wells > 0) {
+            CK(cudaMalloc(&c->statics, (size_t)a.n_static_wells * 6 * sizeof(double)));
+            CK(cudaMemcpyAsync(c->statics, a.static_wells, (size_t)a.n_static_wells * 6 * sizeof(double),
+                               cudaMemcpyHostToDevice, c->stream));
+            c->air.static_wells = c->statics;
+        }
+        CK(cudaMalloc(&c->err, sizeof(int32_t)));
+        CK(cudaMemsetAsync(c->err, 0, sizeof(int32_t), c->stream));
+        for (int32_t s = 0; s < c->S_max; ++s) c->book.free_slots.insert(c->book.free_slots.end(), s);
+        fill_model(c, wells, acts, a.static_wells);
+        CK(cudaStreamSynchronize(c->stream));
+    });
+    if (st != FMDP_OK) {
+        g_create_error = c->err_msg;  // fmdp_last_error(NULL) reports it
+        destroy_ctx(c);
+        return st;
+    }
+    *out = c;
+    return FMDP_OK;
+}
+
+void fmdp_destroy(fmdp_ctx* ctx) { destroy_ctx(ctx); }
+
+const char* fmdp_last_error(fmdp_ctx* ctx) { return ctx ? ctx->err_msg.c_str() : g_create_error.c_str(); }
+
+fmdp_status fmdp_set_stream(fmdp_ctx* c, void* stream) {
+    if (!c) return FMDP_ERR_ARG;
+    return guard(c, [&] {
+        CK(cudaStreamSynchronize(c->stream));
+        c->stream = stream ? reinterpret_cast<cudaStream_t>(stream) : c->own;
+    });
+}
+
+fmdp_status fmdp_add_plan(fmdp_ctx* c, int64_t t0, const float* xyz, int32_t n, uint64_t* id_out) {
+    if (!c) return FMDP_ERR_ARG;
+    return guard(c, [&] { store_plans(c, 1, &t0, &n, xyz, id_out); });
+}
+
+fmdp_status fmdp_add_plans(fmdp_ctx* c, int32_t n_plans, const int64_t* t0s, const int32_t* counts, const float* xyz,
+                           uint64_t* ids_out) {
+    if (!c) return FMDP_ERR_ARG;
+    return guard(c, [&] { store_plans(c, n_plans, t0s, counts, xyz, ids_out); });
+}
+
+fmdp_status fmdp_schedule(fmdp_ctx* c, const fmdp_request* req, fmdp_result* res) {
+    if (!c) return FMDP_ERR_ARG;
+    return guard(c, [&] {
+        require(req && res, FMDP_ERR_ARG, "null request or result");
+        check_request(c, *req);
+        run_fcfs(c, req, 1, res, false);
+    });
+}
+
+fmdp_status fmdp_schedule_many(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_result* res) {
+    if (!c) return FMDP_ERR_ARG;
+    return guard(c, [&] {
+        require(n >= 0 && (n == 0 || (reqs && res)), FMDP_ERR_ARG, "null requests or results");
+        for (int32_t i = 0; i < n; ++i) check_request(c, reqs[i]);
+        run_fcfs(c, reqs, n, res, false);
+    });
+}
+
+fmdp_status fmdp_stage_requests(fmdp_ctx* c, const fmdp_request* reqs, int32_t n) {
+    if (!c) return FMDP_ERR_ARG;
+    return guard(c, [&] {
+        require(n >= 0 && (n == 0 || reqs), FMDP_ERR_ARG, "null requests");
+        int32_t cap = 1;
+        for (int32_t i = 0; i < n; ++i) {
+            check_request(c, reqs[i]);
+            cap = std::max(cap, reqs[i].horizon + 1);
+        }
+        c->staged.assign(reqs, reqs + n);
+        c->staged_done = false;
+        // requests go to device memory now; buffers are sized so the timed run allocates nothing
+        c->stg.reqs.ensure(n);
+        c->stg.slots.ensure(n);
+        c->stg.traj.ensure((size_t)n * cap * 3);
+        c->stg.acts.ensure((size_t)n * cap);
+        c->stg.rout.ensure(n);
+        c->stg.sepo.ensure(n);
+        c->h_rout.ensure(n);
+        c->h_sep.ensure(n);
+        if (n > 0)
+            CK(cudaMemcpyAsync(c->stg.reqs.p, reqs, n * sizeof(fmdp_request), cudaMemcpyHostToDevice, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    });
+}
+
+fmdp_status fmdp_schedule_staged(fmdp_ctx* c, int32_t* n_admitted) {
+    if (!c) return FMDP_ERR_ARG;
+    return guard(c, [&] {
+        const int32_t n = (int32_t)c->staged.size();
+        require(n > 0, FMDP_ERR_ARG, "no staged requests");
+        require((size_t)n <= c->book.free_slots.size(), FMDP_ERR_FULL, "not enough free slots for the staged run");
+        const int32_t adm = run_fcfs(c, c->staged.data(), n, nullptr, true);
+        c->staged_done = true;
+        if (n_admitted) *n_admitted = adm;
+    });
+}
+
+fmdp_status fmdp_fetch_staged(fmdp_ctx* c, fmdp_result* res, int32_t n) {
+    if (!c) return FMDP_ERR_ARG;
+    return guard(c, [&] {
+        require(c->staged_done, FMDP_ERR_ARG, "no finished staged run");
+        require(res && n == (int32_t)c->staged.size(), FMDP_ERR_ARG, "result count must equal the staged count");
+        const int32_t cap = c->staged_cap;
+        c->h_traj.ensure((size_t)n * cap * 3);
+        c->h_acts.ensure((size_t)n * cap);
+        CK(cudaMemcpyAsync(c->h_traj.p, c->stg.traj.p, (size_t)n * cap * 3 * sizeof(float), cudaMemcpyDeviceToHost,
+                           c->stream));
+        CK(cudaMemcpyAsync(c->h_acts.p, c->stg.acts.p, (size_t)n * cap, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaMemcpyAsync(c->h_rout.p, c->stg.rout.p, n * sizeof(RolloutOut), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaMemcpyAsync(c->h_sep.p, c->stg.sepo.p, n * sizeof(SepOut), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        for (int32_t i = 0; i < n; ++i) {
+            const RolloutOut& ro = c->h_rout.p[i];
+            fill_result(ro, c->h_sep.p[i], res + i);
+            res[i].plan_id = 0;
+            res[i].replanned = 0;
+            if (res[i].xyz) std::memcpy(res[i].xyz, c->h_traj.p + (size_t)i * cap * 3, (size_t)ro.n_points * 12);
+            if (res[i].actions && ro.n_points > 1)
+                std::memcpy(res[i].actions, c->h_acts.p + (size_t)i * cap, (size_t)ro.n_points - 1);
+        }
+    });
+}
+
+fmdp_status fmdp_schedule_batch(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_result* res) {
+    // first version: the exact sequential FCFS chain (speculative batching is layered on it)
+    return fmdp_schedule_many(c, reqs, n, res);
+}
+
+fmdp_status fmdp_query_plans(fmdp_ctx* c, int64_t t_begin, int64_t t_end, uint64_t* ids, int32_t cap,
+                             int32_t* n_out) {
+    if (!c) return FMDP_ERR_ARG;
+    return guard(c, [&] {
+        require(n_out && (cap == 0 || ids) && cap >= 0, FMDP_ERR_ARG, "null output");
+        int32_t n = 0;
+        for (auto& kv : c->book.plans) {
+            const PlanMeta& p = kv.second;
+            if (p.t0 < t_end && p.t0 + p.n > t_begin) {
+                if (n < cap) ids[n] = kv.first;
+                ++n;
+            }
+        }
+        *n_out = n;
+    });
+}
+
+fmdp_status fmdp_get_plan(fmdp_ctx* c, uint64_t id, int64_t* t0_out, float* xyz, int32_t cap, int32_t* n_out) {
+    if (!c) return FMDP_ERR_ARG;
+    return guard(c, [&] {
+        auto it = c->book.plans.find(id);
+        require(it != c->book.plans.end(), FMDP_ERR_NOTFOUND, "no such plan");
+        const PlanMeta& p = it->second;
+        if (t0_out) *t0_out = p.t0;
+        if (n_out) *n_out = p.n;
+        if (!xyz) return;
+        require(cap >= p.n, FMDP_ERR_ARG, "xyz capacity too small");
+        require(p.t0 >= c->book.t_base, FMDP_ERR_RANGE, "plan start has left the window");
+        c->h_traj.ensure((size_t)p.n * 3);
+        float* planes[3] = {c->X, c->Y, c->Z};
+        int64_t r0 = p.t0 % c->T_win;
+        int64_t left = p.n, k0 = 0;
+        while (left > 0) {
+            const int64_t run = std::min<int64_t>(left, c->T_win - r0);
+            for (int q = 0; q < 3; ++q) {
+                CK(cudaMemcpy2DAsync(c->h_traj.p + (size_t)q * p.n + k0, sizeof(float),
+                                     planes[q] + (size_t)r0 * c->S_pad + p.slot, (size_t)c->S_pad * sizeof(float),
+                                     sizeof(float), (size_t)run, cudaMemcpyDeviceToHost, c->stream));
+            }
+            left -= run;
+            k0 += run;
+            r0 = 0;
+        }
+        CK(cudaStreamSynchronize(c->stream));
+        for (int32_t k = 0; k < p.n; ++k)
+            for (int q = 0; q < 3; ++q) xyz[3 * k + q] = c->h_traj.p[(size_t)q * p.n + k];
+    });
+}
+
+fmdp_status fmdp_expire(fmdp_ctx* c, int64_t t_now) {
+    if (!c) return FMDP_ERR_ARG;
+    return guard(c, [&] {
+        if (t_now <= c->book.t_base) return;
+        for (auto it = c->book.plans.begin(); it != c->book.plans.end();) {
+            if (it->second.t0 + it->second.n - 1 < t_now) {
+                c->book.free_slots.insert(it->second.slot);
+                it = c->book.plans.erase(it);
+            } else {
+                ++it;
+            }
+        }
+        clear_rows(c, c->book.t_base, t_now);
+        c->book.t_base = t_now;
+        recompute_hw(c);
+        CK(cudaStreamSynchronize(c->stream));
+    });
+}
+
+fmdp_status fmdp_snapshot(fmdp_ctx* c) {
+    if (!c) return FMDP_ERR_ARG;
+    return guard(c, [&] {
+        const size_t plane = (size_t)c->T_win * c->S_pad * sizeof(float);
+        if (!c->sX) {
+            CK(cudaMalloc(&c->sX, plane));
+            CK(cudaMalloc(&c->sY, plane));
+            CK(cudaMalloc(&c->sZ, plane));
+        }
+        CK(cudaMemcpyAsync(c->sX, c->X, plane, cudaMemcpyDeviceToDevice, c->stream));
+        CK(cudaMemcpyAsync(c->sY, c->Y, plane, cudaMemcpyDeviceToDevice, c->stream));
+        CK(cudaMemcpyAsync(c->sZ, c->Z, plane, cudaMemcpyDeviceToDevice, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        c->snap = c->book;
+        c->has_snap = true;
+    });
+}
+
+fmdp_status fmdp_restore(fmdp_ctx* c) {
+    if (!c) return FMDP_ERR_ARG;
+    return guard(c, [&] {
+        require(c->has_snap, FMDP_ERR_ARG, "no snapshot");
+        const size_t plane = (size_t)c->T_win * c->S_pad * sizeof(float);
+        CK(cudaMemcpyAsync(c->X, c->sX, plane, cudaMemcpyDeviceToDevice, c->stream));
+        CK(cudaMemcpyAsync(c->Y, c->sY, plane, cudaMemcpyDeviceToDevice, c->stream));
+        CK(cudaMemcpyAsync(c->Z, c->sZ, plane, cudaMemcpyDeviceToDevice, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        c->book = c->snap;
+    });
+}
+
+fmdp_status fmdp_clear(fmdp_ctx* c) {
+    if (!c) return FMDP_ERR_ARG;
+    return guard(c, [&] {
+        const size_t plane = (size_t)c->T_win * c->S_pad;
+        CK(launch_fill_nan(c->X, plane, c->stream));
+        CK(launch_fill_nan(c->Y, plane, c->stream));
+        CK(launch_fill_nan(c->Z, plane, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        const int64_t tb = c->book.t_base;
+        c->book = Book();
+        c->book.t_base = tb;
+        for (int32_t s = 0; s < c->S_max; ++s) c->book.free_slots.insert(c->book.free_slots.end(), s);
+    });
+}
+
+fmdp_status fmdp_rollout_trace(fmdp_ctx* c, const fmdp_request* req, fmdp_result* res, double* q, double* states,
+                               int32_t* headings, uint8_t* tie_flags) {
+    if (!c) return FMDP_ERR_ARG;
+    return guard(c, [&] {
+        require(req && res, FMDP_ERR_ARG, "null request or result");
+        check_request(c, *req);
+        const int32_t cap = req->horizon + 1;
+        const Geometry g = geometry(c, c->book.S_hw);
+        c->reqs.ensure(1);
+        c->traj.ensure((size_t)cap * 3);
+        c->acts.ensure((size_t)cap);
+        c->rout.ensure(1);
+        c->q_trace.ensure((size_t)cap * c->A);
+        c->st_trace.ensure((size_t)cap * 3);
+        c->hd_trace.ensure((size_t)cap);
+        c->tie_trace.ensure((size_t)cap);
+        CK(cudaMemcpyAsync(c->reqs.p, req, sizeof(fmdp_request), cudaMemcpyHostToDevice, c->stream));
+        RolloutArgs ra{};
+        ra.m = c->model;
+        ra.tab = table_view(c);
+        ra.S_scan = g.S_scan;
+        ra.chunk = g.chunk;
+        ra.cs = g.cs;
+        ra.cap = cap;
+        ra.reqs = c->reqs.p;
+        ra.n_req = 1;
+        ra.trace = 1;
+        ra.traj = c->traj.p;
+        ra.acts = c->acts.p;
+        ra.out = c->rout.p;
+        ra.q_trace = c->q_trace.p;
+        ra.st_trace = c->st_trace.p;
+        ra.hd_trace = c->hd_trace.p;
+        ra.tie_trace = c->tie_trace.p;
+        ra.err = c->err;
+        CK(launch_rollout(ra, g.threads, g.smem, c->stream));
+        RolloutOut ro;
+        CK(cudaMemcpyAsync(&ro, c->rout.p, sizeof(ro), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        require(read_error_word(c) == 0, FMDP_ERR_TIMEOUT, "a bounded device wait expired during a rollout");
+        const int32_t np = ro.n_points, ns = np - 1;
+        if (res->xyz) CK(cudaMemcpy(res->xyz, c->traj.p, (size_t)np * 12, cudaMemcpyDeviceToHost));
+        if (res->actions && ns > 0) CK(cudaMemcpy(res->actions, c->acts.p, (size_t)ns, cudaMemcpyDeviceToHost));
+        const int32_t qrows = ro.status == FMDP_REJ_NO_ACTION ? ns + 1 : ns;
+        if (q && qrows > 0) CK(cudaMemcpy(q, c->q_trace.p, (size_t)qrows * c->A * sizeof(double), cudaMemcpyDeviceToHost));
+        if (states) CK(cudaMemcpy(states, c->st_trace.p, (size_t)np * 3 * sizeof(double), cudaMemcpyDeviceToHost));
+        if (headings) CK(cudaMemcpy(headings, c->hd_trace.p, (size_t)np * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        if (tie_flags && ns > 0) CK(cudaMemcpy(tie_flags, c->tie_trace.p, (size_t)ns, cudaMemcpyDeviceToHost));
+        res->verdict = ro.status == kStatusCaptured ? FMDP_ADMITTED : ro.status;
+        res->n_points = np;
+        res->plan_id = 0;
+        res->first_conflict_step = -1;
+        res->first_terrain_step = -1;
+        res->min_sep_h = INFINITY;
+        res->min_sep_v = INFINITY;
+        res->near_ties = ro.near_ties;
+        res->replanned = 0;
+    });
+}
+
+fmdp_status fmdp_sep_check(fmdp_ctx* c, int64_t t0, const float* xyz, int32_t n, fmdp_sep_report* out) {
+    if (!c) return FMDP_ERR_ARG;
+    return guard(c, [&] {
+        require(xyz && out && n >= 1, FMDP_ERR_ARG, "null trajectory or output");
+        const int32_t S_scan = round_up(c->book.S_hw, 32);
+        c->traj.ensure((size_t)n * 3);
+        c->sepo.ensure(1);
+        CK(cudaMemcpyAsync(c->traj.p, xyz, (size_t)n * 12, cudaMemcpyHostToDevice, c->stream));
+        CK(launch_sep_reset(c->sepo.p, 1, c->stream));
+        SepArgs sa{};
+        sa.m = c->model;
+        sa.tab = table_view(c);
+        sa.S_scan = S_scan;
+        sa.cap = n;
+        sa.traj = c->traj.p;
+        sa.rout = nullptr;
+        sa.reqs = nullptr;
+        sa.t0_fixed = t0;
+        sa.n_fixed = n;
+        sa.out = c->sepo.p;
+        {
+            KernelTimer t(c, 1);
+            CK(launch_sepcheck(sa, 1, n, c->stream));
+            t.stop();
+        }
+        SepOut so;
+        CK(cudaMemcpyAsync(&so, c->sepo.p, sizeof(so), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        if (c->profiling) collect_timers(c);
+        c->stats.sep_pairs += (int64_t)n * S_scan;
+        out->first_conflict_step = so.first_conflict == INT_MAX ? -1 : so.first_conflict;
+        out->first_terrain_step = so.first_terrain == INT_MAX ? -1 : so.first_terrain;
+        out->conflicts = (int64_t)so.conflicts;
+        float mh, mv;
+        std::memcpy(&mh, &so.min_h_bits, 4);
+        std::memcpy(&mv, &so.min_v_bits, 4);
+        out->min_sep_h = mh;
+        out->min_sep_v = mv;
+    });
+}
+
+fmdp_status fmdp_set_profiling(fmdp_ctx* c, int32_t on) {
+    if (!c) return FMDP_ERR_ARG;
+    return guard(c, [&] {
+        c->profiling = on != 0;
+        c->stats = fmdp_stats{};
+        c->pending.clear();
+        c->ev_next = 0;
+    });
+}
+
+fmdp_status fmdp_get_stats(fmdp_ctx* c, fmdp_stats* out) {
+    if (!c || !out) return FMDP_ERR_ARG;
+    return guard(c, [&] {
+        *out = c->stats;
+        out->cluster_size = c->last_cs;
+        out->threads_per_cta = c->last_threads;
+        out->slots_per_cta = c->last_chunk;
+    });
+}
+
+}  // extern "C"

@@ -1,0 +1,185 @@
+// Internal types and device helpers of libfmdp (GB300, sm_103a).
+//
+// Device layout of the known-plan table (the paper's intruder peaks P^I are never
+// materialised, Table 1): three fp32 planes X, Y, Z of shape [T_win][S_pad]; row
+// (t mod T_win) holds every slot's position at time step t, NaN where the slot has
+// no sample. A plan occupies one slot (column) for its whole life.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/fmdp.h"
+
+namespace fmdp {
+
+constexpr int kMaxActions = 32;  // one lane of a warp per action
+constexpr int kMaxWells = 8;
+constexpr int kMaxStatic = 64;
+constexpr int kHeadings = 24;    // 15-degree heading table
+constexpr int kRing = 4;         // slice buffers per CTA (two in use, two in flight)
+constexpr int kMaxCluster = 16;
+constexpr float kWellBand = 4e-5f;  // |d^2 - R^2| <= kWellBand * R^2 -> FP64 re-evaluation
+constexpr float kSepBand = 0.05f;   // metres around a separation threshold -> FP64
+constexpr float kClrBand = 0.05f;   // metres around the clearance threshold -> FP64
+constexpr double kTieRel = 1e-4;    // near-tie bar on the top-2 action values
+constexpr int kStatusCaptured = 0;
+
+// Constants of a scheduler, passed by value into every kernel.
+struct Model {
+    double box[6];
+    double dt;
+    double lg64;        // log2(gamma) of the goal peak
+    double log2rg;      // log2(goal_reward)
+    double goal_reward;
+    double clearance, deck;
+    double sep_h, sep_v;
+    double sum_scale;   // 2^(sum_ref - 40): value of one unit of the sum mode's fixed point
+    float lg32;
+    float hm_sx, hm_sy; // heightmap nodes per metre along x, y
+    float reach_base;   // max_k R_k + 1 m margin (coarse cull radius without motion terms)
+    float tau_absmax;   // max_k |tau_k|
+    float sum_ref;      // log2 of the largest |r| (fixed-point reference of the sum mode)
+    int32_t A;
+    int32_t combine;
+    int32_t n_wells;
+    int32_t n_static;
+    int32_t hm_nx, hm_ny;
+    const float* hm;        // device heightmap or nullptr
+    const double* statics;  // device [n_static][6] or nullptr
+    int32_t dh[kMaxActions];
+    double climb[kMaxActions];
+    float w_tau[kMaxWells], w_R2[kMaxWells], w_band[kMaxWells], w_L[kMaxWells], w_lg[kMaxWells];
+    double w_tau64[kMaxWells], w_R64[kMaxWells];
+    float st_R2[kMaxStatic], st_band[kMaxStatic], st_L[kMaxStatic], st_lg[kMaxStatic];
+};
+
+struct TableView {
+    float* X;
+    float* Y;
+    float* Z;
+    int32_t T_win, S_pad;
+    int64_t t_base;
+};
+
+struct RolloutOut {
+    int32_t n_points;
+    int32_t status;  // kStatusCaptured, FMDP_REJ_HORIZON or FMDP_REJ_NO_ACTION
+    int32_t near_ties;
+    int32_t steps;
+};
+
+struct SepOut {
+    int32_t first_conflict;  // INT_MAX when none
+    int32_t first_terrain;   // INT_MAX when none
+    unsigned long long conflicts;
+    uint32_t min_h_bits;     // fp32 bits, +inf when none (non-negative floats order as ints)
+    uint32_t min_v_bits;
+    int32_t verdict;
+    int32_t pad;
+};
+
+struct RolloutArgs {
+    Model m;
+    TableView tab;
+    int32_t S_scan;   // slots scanned per step (multiple of 32)
+    int32_t chunk;    // slots per CTA (multiple of 32)
+    int32_t cs;       // CTAs per request (cluster size)
+    int32_t cap;      // trajectory capacity per request (points)
+    const fmdp_request* reqs;
+    int32_t n_req;
+    int32_t trace;
+    float* traj;      // [n_req][cap][3]
+    uint8_t* acts;    // [n_req][cap]
+    RolloutOut* out;  // [n_req]
+    double* q_trace;  // [cap][A] (request 0 only) or nullptr
+    double* st_trace; // [cap][3]
+    int32_t* hd_trace;
+    uint8_t* tie_trace;
+    int32_t* err;     // device error word
+};
+
+struct SepArgs {
+    Model m;
+    TableView tab;
+    int32_t S_scan;
+    int32_t cap;
+    const float* traj;          // [n][cap][3]
+    const RolloutOut* rout;     // n_points per request (nullptr: use n_fixed)
+    const fmdp_request* reqs;   // t0 = depart_step (nullptr: use t0_fixed)
+    int64_t t0_fixed;
+    int32_t n_fixed;
+    SepOut* out;
+};
+
+struct AdmitArgs {
+    TableView tab;
+    int32_t cap;
+    const float* traj;
+    const RolloutOut* rout;
+    const fmdp_request* reqs;
+    const int32_t* slots;  // slot per request
+    SepOut* sep;           // verdict written here
+    int32_t force;         // 1: store unconditionally (known plans)
+    const int64_t* t0s;    // force mode: per plan t0
+    const int32_t* counts; // force mode: per plan count
+    const int64_t* offs;   // force mode: per plan offset into traj (points)
+};
+
+// kernel launchers (rollout.cu / tables.cu)
+cudaError_t launch_rollout(const RolloutArgs& a, int threads, size_t smem, cudaStream_t s);
+size_t rollout_smem_bytes(int chunk, int threads);
+cudaError_t prepare_rollout_kernel(size_t smem);
+int rollout_max_active_clusters(int cs, int threads, size_t smem);
+cudaError_t launch_sepcheck(const SepArgs& a, int n_req, int max_points, cudaStream_t s);
+cudaError_t launch_sep_reset(SepOut* out, int n, cudaStream_t s);
+cudaError_t launch_admit(const AdmitArgs& a, int n_req, int max_points, cudaStream_t s);
+cudaError_t launch_fill_nan(float* p, size_t n, cudaStream_t s);
+
+// ---------------------------------------------------------------- device helpers
+
+__device__ __forceinline__ int float_key(float f) {
+    int i = __float_as_int(f);
+    return i >= 0 ? i : i ^ 0x7fffffff;
+}
+__device__ __forceinline__ float key_float(int k) {
+    return __int_as_float(k >= 0 ? k : k ^ 0x7fffffff);
+}
+
+// 2^n as a double, for n in the normal range.
+__device__ __forceinline__ double pow2i(int n) {
+    return __hiloint2double((n + 1023) << 20, 0);
+}
+// x * 2^n with gradual underflow for very negative n.
+__device__ __forceinline__ double scale2(double x, int n) {
+    if (n >= -1022 && n <= 1023) return x * pow2i(n);
+    if (n < -1022) return (x * pow2i(-600)) * pow2i(n + 600 < -1022 ? -1022 : n + 600);
+    return x * pow2i(1023);
+}
+
+// Bilinear terrain height in FP64, evaluated in exactly the order written (no FMA).
+__device__ __forceinline__ double terrain64(const Model& m, double x, double y) {
+    const int nx = m.hm_nx, ny = m.hm_ny;
+    double fx = __dmul_rn(__ddiv_rn(__dsub_rn(x, m.box[0]), __dsub_rn(m.box[3], m.box[0])), (double)(nx - 1));
+    double fy = __dmul_rn(__ddiv_rn(__dsub_rn(y, m.box[1]), __dsub_rn(m.box[4], m.box[1])), (double)(ny - 1));
+    double flx = floor(fx), fly = floor(fy);
+    int ix = (int)flx, iy = (int)fly;
+    if (flx < 0.0) ix = 0;
+    if (fly < 0.0) iy = 0;
+    if (ix > nx - 2) ix = nx - 2;
+    if (iy > ny - 2) iy = ny - 2;
+    double ax = __dsub_rn(fx, (double)ix), ay = __dsub_rn(fy, (double)iy);
+    const float* r0 = m.hm + (size_t)iy * nx + ix;
+    const float* r1 = r0 + nx;
+    double h00 = __ldg(r0), h10 = __ldg(r0 + 1), h01 = __ldg(r1), h11 = __ldg(r1 + 1);
+    double bx = __dsub_rn(1.0, ax), by = __dsub_rn(1.0, ay);
+    double lo = __dadd_rn(__dmul_rn(bx, h00), __dmul_rn(ax, h10));
+    double hi = __dadd_rn(__dmul_rn(bx, h01), __dmul_rn(ax, h11));
+    return __dadd_rn(__dmul_rn(by, lo), __dmul_rn(ay, hi));
+}
+
+__device__ __forceinline__ double norm3_64(double dx, double dy, double dz) {
+    return __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
+}
+
+}  // namespace fmdp

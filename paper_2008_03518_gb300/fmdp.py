@@ -1,0 +1,402 @@
+"""ctypes binding of libfmdp.so: the same entry points as include/fmdp.h.
+
+Argument marshalling only: every step of planning runs in the library's CUDA kernels.
+There is no CPU fallback; constructing a Scheduler without the compiled library or
+without a CUDA device raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+ADMITTED, REJ_CONFLICT, REJ_TERRAIN, REJ_HORIZON, REJ_NO_ACTION = range(5)
+STATUS_NAMES = {0: "OK", -1: "ERR_ARG", -2: "ERR_OOM", -3: "ERR_CUDA", -4: "ERR_TIMEOUT", -5: "ERR_FULL",
+                -6: "ERR_RANGE", -7: "ERR_NOTFOUND"}
+
+
+class FmdpError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_fp = ctypes.POINTER(ctypes.c_float)
+
+
+class Airspace(ctypes.Structure):
+    _fields_ = [("x0", ctypes.c_double), ("y0", ctypes.c_double), ("z0", ctypes.c_double),
+                ("x1", ctypes.c_double), ("y1", ctypes.c_double), ("z1", ctypes.c_double),
+                ("dt", ctypes.c_double), ("n_slices_window", ctypes.c_int32), ("max_slots", ctypes.c_int32),
+                ("heightmap", _fp), ("hm_nx", ctypes.c_int32), ("hm_ny", ctypes.c_int32),
+                ("clearance_m", ctypes.c_double), ("deck_value", ctypes.c_double),
+                ("static_wells", _dp), ("n_static_wells", ctypes.c_int32)]
+
+
+class Action(ctypes.Structure):
+    _fields_ = [("dpsi_deg", ctypes.c_double), ("climb_mps", ctypes.c_double)]
+
+
+class Sep(ctypes.Structure):
+    _fields_ = [("horiz_m", ctypes.c_double), ("vert_m", ctypes.c_double)]
+
+
+class Well(ctypes.Structure):
+    _fields_ = [("tau_s", ctypes.c_double), ("radius_m", ctypes.c_double), ("magnitude", ctypes.c_double),
+                ("gamma", ctypes.c_double)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("combine", ctypes.c_int32), ("wells", ctypes.POINTER(Well)), ("n_wells", ctypes.c_int32),
+                ("goal_reward", ctypes.c_double), ("lookahead_W", ctypes.c_int32),
+                ("cluster_size", ctypes.c_int32), ("threads_per_cta", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("req_id", ctypes.c_uint64), ("ox", ctypes.c_double), ("oy", ctypes.c_double),
+                ("oz", ctypes.c_double), ("gx", ctypes.c_double), ("gy", ctypes.c_double), ("gz", ctypes.c_double),
+                ("speed_mps", ctypes.c_double), ("depart_step", ctypes.c_int64), ("horizon", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("verdict", ctypes.c_int32), ("n_points", ctypes.c_int32), ("plan_id", ctypes.c_uint64),
+                ("first_conflict_step", ctypes.c_int32), ("first_terrain_step", ctypes.c_int32),
+                ("min_sep_h", ctypes.c_double), ("min_sep_v", ctypes.c_double), ("near_ties", ctypes.c_int32),
+                ("replanned", ctypes.c_int32), ("xyz", _fp), ("actions", ctypes.POINTER(ctypes.c_uint8))]
+
+
+class SepReport(ctypes.Structure):
+    _fields_ = [("first_conflict_step", ctypes.c_int32), ("first_terrain_step", ctypes.c_int32),
+                ("conflicts", ctypes.c_int64), ("min_sep_h", ctypes.c_double), ("min_sep_v", ctypes.c_double)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("rollout_launches", ctypes.c_int64), ("sepcheck_launches", ctypes.c_int64),
+                ("admit_launches", ctypes.c_int64), ("rollout_ms", ctypes.c_double),
+                ("sepcheck_ms", ctypes.c_double), ("admit_ms", ctypes.c_double),
+                ("rollout_steps", ctypes.c_int64), ("slots_scanned", ctypes.c_int64),
+                ("sep_pairs", ctypes.c_int64), ("cluster_size", ctypes.c_int32),
+                ("threads_per_cta", ctypes.c_int32), ("slots_per_cta", ctypes.c_int32)]
+
+
+# every exported symbol of include/fmdp.h
+EXPORTS = ("fmdp_options_default", "fmdp_create", "fmdp_destroy", "fmdp_last_error", "fmdp_set_stream",
+           "fmdp_add_plan", "fmdp_add_plans", "fmdp_schedule", "fmdp_schedule_many", "fmdp_schedule_batch",
+           "fmdp_stage_requests", "fmdp_schedule_staged", "fmdp_fetch_staged", "fmdp_query_plans",
+           "fmdp_get_plan", "fmdp_expire", "fmdp_snapshot", "fmdp_restore", "fmdp_clear", "fmdp_rollout_trace",
+           "fmdp_sep_check", "fmdp_set_profiling", "fmdp_get_stats")
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB_PATH
+
+
+def load(build_if_missing: bool = True):
+    """Loads libfmdp.so (building it first if allowed). Raises if it cannot be loaded."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing and _build.stale():
+        _build.build()
+    if not os.path.exists(_build.LIB_PATH):
+        raise RuntimeError("libfmdp.so is not built; run paper_2008_03518_gb300.build.build()")
+    L = ctypes.CDLL(_build.LIB_PATH)
+    P, c = ctypes.POINTER, ctypes
+    vp = c.c_void_p
+    L.fmdp_options_default.argtypes = [P(Options)]
+    L.fmdp_options_default.restype = None
+    L.fmdp_create.argtypes = [P(Airspace), c.c_double, P(Action), c.c_int32, P(Sep), P(Options), P(vp)]
+    L.fmdp_destroy.argtypes = [vp]
+    L.fmdp_destroy.restype = None
+    L.fmdp_last_error.argtypes = [vp]
+    L.fmdp_last_error.restype = c.c_char_p
+    L.fmdp_set_stream.argtypes = [vp, vp]
+    L.fmdp_add_plan.argtypes = [vp, c.c_int64, _fp, c.c_int32, P(c.c_uint64)]
+    L.fmdp_add_plans.argtypes = [vp, c.c_int32, P(c.c_int64), P(c.c_int32), _fp, P(c.c_uint64)]
+    for name in ("fmdp_schedule_many", "fmdp_schedule_batch"):
+        getattr(L, name).argtypes = [vp, P(Request), c.c_int32, P(Result)]
+    L.fmdp_schedule.argtypes = [vp, P(Request), P(Result)]
+    L.fmdp_stage_requests.argtypes = [vp, P(Request), c.c_int32]
+    L.fmdp_schedule_staged.argtypes = [vp, P(c.c_int32)]
+    L.fmdp_fetch_staged.argtypes = [vp, P(Result), c.c_int32]
+    L.fmdp_query_plans.argtypes = [vp, c.c_int64, c.c_int64, P(c.c_uint64), c.c_int32, P(c.c_int32)]
+    L.fmdp_get_plan.argtypes = [vp, c.c_uint64, P(c.c_int64), _fp, c.c_int32, P(c.c_int32)]
+    L.fmdp_expire.argtypes = [vp, c.c_int64]
+    for name in ("fmdp_snapshot", "fmdp_restore", "fmdp_clear"):
+        getattr(L, name).argtypes = [vp]
+    L.fmdp_rollout_trace.argtypes = [vp, P(Request), P(Result), _dp, _dp, P(c.c_int32), P(c.c_uint8)]
+    L.fmdp_sep_check.argtypes = [vp, c.c_int64, _fp, c.c_int32, P(SepReport)]
+    L.fmdp_set_profiling.argtypes = [vp, c.c_int32]
+    L.fmdp_get_stats.argtypes = [vp, P(Stats)]
+    for name in EXPORTS:
+        f = getattr(L, name)
+        if f.restype is ctypes.c_int:  # default restype: all statuses are int32
+            f.restype = c.c_int32
+    _lib = L
+    return L
+
+
+def _ptr(a, ctype):
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def make_request(r, req_id=None) -> Request:
+    """Request from a structured record / dict with keys ox..gz, speed, depart, horizon."""
+    def g(*names):
+        for n in names:
+            try:
+                return r[n]
+            except (KeyError, ValueError, IndexError):
+                continue
+        raise KeyError(names)
+    rid = req_id if req_id is not None else int(g("req_id")) if _has(r, "req_id") else 0
+    return Request(int(rid), float(g("ox")), float(g("oy")), float(g("oz")), float(g("gx")), float(g("gy")),
+                   float(g("gz")), float(g("speed_mps", "speed")), int(g("depart_step", "depart")),
+                   int(g("horizon")), 0)
+
+
+def _has(r, name):
+    try:
+        r[name]
+        return True
+    except (KeyError, ValueError, IndexError):
+        return False
+
+
+def _result_dict(res: Result, xyz=None, acts=None):
+    d = {k: getattr(res, k) for k, _ in Result._fields_ if k not in ("xyz", "actions")}
+    n = res.n_points
+    if xyz is not None:
+        d["xyz"] = xyz[:n].copy()
+    if acts is not None:
+        d["actions"] = acts[: max(n - 1, 0)].copy()
+    return d
+
+
+class Scheduler:
+    """One FastMDP FCFS scheduler (one CUDA context's worth of device state)."""
+
+    def __init__(self, box, dt, gamma, actions, sep, n_slices_window=4096, max_slots=4096, heightmap=None,
+                 clearance=0.0, deck_value=1000.0, static_wells=None, combine=0, wells=None, goal_reward=200.0,
+                 cluster_size=0, threads_per_cta=0):
+        self._L = load()
+        air = Airspace()
+        air.x0, air.y0, air.z0, air.x1, air.y1, air.z1 = map(float, box)
+        air.dt = float(dt)
+        air.n_slices_window = int(n_slices_window)
+        air.max_slots = int(max_slots)
+        self._keep = []
+        if heightmap is not None:
+            hm = np.ascontiguousarray(heightmap, dtype=np.float32)
+            self._keep.append(hm)
+            air.heightmap = _ptr(hm, ctypes.c_float)
+            air.hm_ny, air.hm_nx = hm.shape
+        air.clearance_m = float(clearance)
+        air.deck_value = float(deck_value)
+        if static_wells is not None and len(static_wells):
+            sw = np.ascontiguousarray(static_wells, dtype=np.float64).reshape(-1, 6)
+            self._keep.append(sw)
+            air.static_wells = _ptr(sw, ctypes.c_double)
+            air.n_static_wells = sw.shape[0]
+        acts = (Action * len(actions))(*[Action(float(a), float(c)) for a, c in actions])
+        sp = Sep(float(sep[0]), float(sep[1]))
+        opt = Options()
+        self._L.fmdp_options_default(ctypes.byref(opt))
+        opt.combine = int(combine)
+        opt.goal_reward = float(goal_reward)
+        opt.cluster_size = int(cluster_size)
+        opt.threads_per_cta = int(threads_per_cta)
+        if wells is not None:
+            warr = (Well * len(wells))(*[Well(*map(float, w)) for w in wells])
+            self._keep.append(warr)
+            opt.wells = ctypes.cast(warr, ctypes.POINTER(Well))
+            opt.n_wells = len(wells)
+        h = ctypes.c_void_p()
+        st = self._L.fmdp_create(ctypes.byref(air), float(gamma), acts, len(actions), ctypes.byref(sp),
+                                 ctypes.byref(opt), ctypes.byref(h))
+        if st != 0:
+            raise FmdpError(st, self._L.fmdp_last_error(None).decode())
+        self._h = h
+        self.n_actions = len(actions)
+
+    @classmethod
+    def from_scenario(cls, sc, add_plans=True, **kw):
+        args = dict(box=sc.box, dt=sc.dt, gamma=sc.gamma, actions=sc.actions, sep=sc.sep,
+                    n_slices_window=sc.n_slices_window, max_slots=sc.max_slots or 4096, heightmap=sc.heightmap,
+                    clearance=sc.clearance, static_wells=sc.static_wells, goal_reward=sc.goal_reward)
+        args.update(kw)
+        s = cls(**args)
+        if add_plans and sc.plans:
+            s.add_plans([(p.t0, p.xyz) for p in sc.plans])
+        return s
+
+    # ------------------------------------------------------------ lifetime
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.fmdp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _check(self, st):
+        if st != 0:
+            raise FmdpError(st, self._L.fmdp_last_error(self._h).decode())
+
+    def set_stream(self, stream_ptr):
+        self._check(self._L.fmdp_set_stream(self._h, ctypes.c_void_p(stream_ptr or None)))
+
+    # ------------------------------------------------------------ plans
+    def add_plan(self, t0, xyz):
+        xyz = np.ascontiguousarray(xyz, dtype=np.float32).reshape(-1, 3)
+        pid = ctypes.c_uint64()
+        self._check(self._L.fmdp_add_plan(self._h, int(t0), _ptr(xyz, ctypes.c_float), xyz.shape[0],
+                                          ctypes.byref(pid)))
+        return pid.value
+
+    def add_plans(self, plans):
+        if not plans:
+            return np.zeros(0, dtype=np.uint64)
+        t0 = np.array([int(t) for t, _ in plans], dtype=np.int64)
+        pts = [np.ascontiguousarray(x, dtype=np.float32).reshape(-1, 3) for _, x in plans]
+        cnt = np.array([p.shape[0] for p in pts], dtype=np.int32)
+        xyz = np.ascontiguousarray(np.concatenate(pts, axis=0))
+        ids = np.zeros(len(plans), dtype=np.uint64)
+        self._check(self._L.fmdp_add_plans(self._h, len(plans), _ptr(t0, ctypes.c_int64), _ptr(cnt, ctypes.c_int32),
+                                           _ptr(xyz, ctypes.c_float), _ptr(ids, ctypes.c_uint64)))
+        return ids
+
+    def query_plans(self, t_begin, t_end):
+        n = ctypes.c_int32()
+        self._check(self._L.fmdp_query_plans(self._h, int(t_begin), int(t_end), None, 0, ctypes.byref(n)))
+        ids = np.zeros(max(n.value, 1), dtype=np.uint64)
+        self._check(self._L.fmdp_query_plans(self._h, int(t_begin), int(t_end), _ptr(ids, ctypes.c_uint64),
+                                             ids.size, ctypes.byref(n)))
+        return ids[: n.value]
+
+    def get_plan(self, pid):
+        t0, n = ctypes.c_int64(), ctypes.c_int32()
+        self._check(self._L.fmdp_get_plan(self._h, int(pid), ctypes.byref(t0), None, 0, ctypes.byref(n)))
+        xyz = np.zeros((n.value, 3), dtype=np.float32)
+        self._check(self._L.fmdp_get_plan(self._h, int(pid), ctypes.byref(t0), _ptr(xyz, ctypes.c_float), n.value,
+                                          ctypes.byref(n)))
+        return t0.value, xyz
+
+    def expire(self, t_now):
+        self._check(self._L.fmdp_expire(self._h, int(t_now)))
+
+    def snapshot(self):
+        self._check(self._L.fmdp_snapshot(self._h))
+
+    def restore(self):
+        self._check(self._L.fmdp_restore(self._h))
+
+    def clear(self):
+        self._check(self._L.fmdp_clear(self._h))
+
+    # ------------------------------------------------------------ planning
+    def schedule(self, req):
+        r = make_request(req)
+        cap = r.horizon + 1
+        xyz = np.zeros((cap, 3), dtype=np.float32)
+        acts = np.zeros(max(cap, 1), dtype=np.uint8)
+        res = Result()
+        res.xyz = _ptr(xyz, ctypes.c_float)
+        res.actions = _ptr(acts, ctypes.c_uint8)
+        self._check(self._L.fmdp_schedule(self._h, ctypes.byref(r), ctypes.byref(res)))
+        return _result_dict(res, xyz, acts)
+
+    def _many(self, fn, reqs):
+        n = len(reqs)
+        rq = (Request * n)(*[make_request(reqs[i]) for i in range(n)])
+        cap = max([rq[i].horizon for i in range(n)] + [0]) + 1
+        xyz = np.zeros((n, cap, 3), dtype=np.float32)
+        acts = np.zeros((n, cap), dtype=np.uint8)
+        res = (Result * n)()
+        for i in range(n):
+            res[i].xyz = _ptr(xyz[i], ctypes.c_float)
+            res[i].actions = _ptr(acts[i], ctypes.c_uint8)
+        self._check(fn(self._h, rq, n, res))
+        return [_result_dict(res[i], xyz[i], acts[i]) for i in range(n)]
+
+    def schedule_many(self, reqs):
+        return self._many(self._L.fmdp_schedule_many, reqs)
+
+    def schedule_batch(self, reqs):
+        return self._many(self._L.fmdp_schedule_batch, reqs)
+
+    def stage(self, reqs):
+        n = len(reqs)
+        self._staged = (Request * n)(*[make_request(reqs[i]) for i in range(n)])
+        self._check(self._L.fmdp_stage_requests(self._h, self._staged, n))
+
+    def schedule_staged(self):
+        n = ctypes.c_int32()
+        self._check(self._L.fmdp_schedule_staged(self._h, ctypes.byref(n)))
+        return n.value
+
+    def fetch_staged(self):
+        n = len(self._staged)
+        cap = max([self._staged[i].horizon for i in range(n)] + [0]) + 1
+        xyz = np.zeros((n, cap, 3), dtype=np.float32)
+        acts = np.zeros((n, cap), dtype=np.uint8)
+        res = (Result * n)()
+        for i in range(n):
+            res[i].xyz = _ptr(xyz[i], ctypes.c_float)
+            res[i].actions = _ptr(acts[i], ctypes.c_uint8)
+        self._check(self._L.fmdp_fetch_staged(self._h, res, n))
+        return [_result_dict(res[i], xyz[i], acts[i]) for i in range(n)]
+
+    def rollout_trace(self, req):
+        r = make_request(req)
+        cap = r.horizon + 1
+        A = self.n_actions
+        xyz = np.zeros((cap, 3), dtype=np.float32)
+        acts = np.zeros(max(cap, 1), dtype=np.uint8)
+        q = np.zeros((cap, A))
+        states = np.zeros((cap, 3))
+        heads = np.zeros(cap, dtype=np.int32)
+        ties = np.zeros(max(cap, 1), dtype=np.uint8)
+        res = Result()
+        res.xyz = _ptr(xyz, ctypes.c_float)
+        res.actions = _ptr(acts, ctypes.c_uint8)
+        self._check(self._L.fmdp_rollout_trace(self._h, ctypes.byref(r), ctypes.byref(res), _ptr(q, ctypes.c_double),
+                                               _ptr(states, ctypes.c_double), _ptr(heads, ctypes.c_int32),
+                                               _ptr(ties, ctypes.c_uint8)))
+        d = _result_dict(res, xyz, acts)
+        n = res.n_points
+        d.update(q=q[: n - 1], states=states[:n], headings=heads[:n],
+                 ties=ties[: n - 1].astype(bool))
+        return d
+
+    def sep_check(self, t0, xyz):
+        xyz = np.ascontiguousarray(xyz, dtype=np.float32).reshape(-1, 3)
+        rep = SepReport()
+        self._check(self._L.fmdp_sep_check(self._h, int(t0), _ptr(xyz, ctypes.c_float), xyz.shape[0],
+                                           ctypes.byref(rep)))
+        return {k: getattr(rep, k) for k, _ in SepReport._fields_}
+
+    # ------------------------------------------------------------ profiling
+    def set_profiling(self, on=True):
+        self._check(self._L.fmdp_set_profiling(self._h, 1 if on else 0))
+
+    def stats(self):
+        s = Stats()
+        self._check(self._L.fmdp_get_stats(self._h, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in Stats._fields_}

@@ -1,0 +1,88 @@
+"""CPU-side checks of the C-ABI library: it builds, loads, exports every entry point
+declared in include/fmdp.h, its ctypes structures match the C layout, and it refuses
+to run without a GPU (no CPU fallback). No compute call is made here."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2008_03518_gb300 import build, fmdp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "fmdp.h")
+
+
+def header_functions():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(fmdp_[a-z_]+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return fmdp.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = header_functions()
+    assert len(names) >= 20
+    assert sorted(fmdp.EXPORTS) == names
+    out = subprocess.run(["nm", "-D", "--defined-only", build.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (fmdp_\w+)", out))
+    for n in names:
+        assert n in exported, n
+        assert getattr(lib, n) is not None
+
+
+def test_struct_layouts_match_header_sizes():
+    src = r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "fmdp.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(fmdp_airspace), sizeof(fmdp_action), sizeof(fmdp_sep),
+         sizeof(fmdp_well), sizeof(fmdp_options), sizeof(fmdp_request), sizeof(fmdp_result),
+         sizeof(fmdp_sep_report), sizeof(fmdp_stats));
+  printf("%zu %zu %zu\n", offsetof(fmdp_result, xyz), offsetof(fmdp_request, depart_step), offsetof(fmdp_airspace, static_wells));
+  return 0;
+}'''
+    import tempfile
+    d = tempfile.mkdtemp()
+    c = os.path.join(d, "sz.c")
+    open(c, "w").write(src)
+    exe = os.path.join(d, "sz")
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+    sizes, offs = [list(map(int, line.split())) for line in subprocess.run([exe], capture_output=True, text=True).stdout.splitlines()]
+    py = [ctypes.sizeof(t) for t in (fmdp.Airspace, fmdp.Action, fmdp.Sep, fmdp.Well, fmdp.Options, fmdp.Request,
+                                     fmdp.Result, fmdp.SepReport, fmdp.Stats)]
+    assert py == sizes
+    assert offs == [fmdp.Result.xyz.offset, fmdp.Request.depart_step.offset, fmdp.Airspace.static_wells.offset]
+
+
+def test_options_default_is_the_paper_setting(lib):
+    o = fmdp.Options()
+    lib.fmdp_options_default(ctypes.byref(o))
+    assert o.combine == 0 and o.n_wells == 0 and o.goal_reward == 200.0 and o.lookahead_W == 1
+
+
+def test_null_arguments_are_rejected_without_a_device(lib):
+    assert lib.fmdp_create(None, 0.99, None, 0, None, None, None) == -1
+    h = ctypes.c_void_p()
+    assert lib.fmdp_create(None, 0.99, None, 0, None, None, ctypes.byref(h)) == -1
+    assert h.value is None
+    assert lib.fmdp_schedule(None, None, None) == -1
+    assert lib.fmdp_add_plan(None, 0, None, 0, None) == -1
+
+
+def test_no_cpu_fallback_without_gpu():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2008_03518_gb300 import scenarios as S
+    sc = S.c1_plain_small()
+    with pytest.raises(fmdp.FmdpError) as e:
+        fmdp.Scheduler.from_scenario(sc)
+    assert e.value.status == -3  # FMDP_ERR_CUDA: no device, and nothing runs on the CPU
