@@ -202,8 +202,15 @@ typedef struct {
     int64_t slots_scanned;                    /* (step, slot) pairs scanned by rollouts */
     int64_t sep_pairs;                        /* (sample, slot) pairs scanned by sep_check */
     int32_t cluster_size, threads_per_cta, slots_per_cta;
+    int32_t reserved;
+    int64_t phase_cycles[6];  /* on = 2: summed SM cycles of rollout phases: control warp waiting
+                                 at the step barrier, control per-action work, control waiting
+                                 for the scanners, exchange + argmax + advance, one scanner
+                                 warp's cull + wells, producer issue + wait */
 } fmdp_stats;
-/* Per-kernel CUDA-event timing on the context's stream (off by default). */
+/* on = 1: per-kernel CUDA-event timing on the context's stream; on = 2: additionally
+ * per-phase cycle counters inside the rollout kernel (diagnostic, slows it slightly);
+ * 0: off (default). Resets the statistics. */
 fmdp_status fmdp_set_profiling(fmdp_ctx* ctx, int32_t on);
 fmdp_status fmdp_get_stats(fmdp_ctx* ctx, fmdp_stats* out);
 

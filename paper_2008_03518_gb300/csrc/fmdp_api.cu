@@ -171,6 +171,8 @@ struct fmdp_ctx {
 
     // profiling
     bool profiling = false;
+    bool phase_timing = false;
+    DevArray<unsigned long long> phase;
     fmdp_stats stats{};
     std::vector<cudaEvent_t> ev_pool;
     struct Pending { int kind; cudaEvent_t a, b; };
@@ -296,7 +298,7 @@ void collect_timers(fmdp_ctx* c) {
 // ------------------------------------------------------------------ launch geometry
 
 struct Geometry {
-    int32_t S_scan, cs, threads, chunk;
+    int32_t S_scan, cs, threads, chunk, ring;
     size_t smem;
 };
 
@@ -310,21 +312,23 @@ Geometry geometry(fmdp_ctx* c, int32_t S_hw) {
         while (cs < want && cs < kMaxCluster) cs *= 2;
     }
     cs = std::max(1, std::min(cs, kMaxCluster));
-    for (;;) {
-        g.cs = cs;
-        g.chunk = std::max(32, round_up((g.S_scan + cs - 1) / cs, 32));
+    // deepest ring (8, else 4 slices) whose partition fits one CTA's shared memory
+    auto fit = [&](int cs_) {
+        g.cs = cs_;
+        g.chunk = std::max(32, round_up((g.S_scan + cs_ - 1) / cs_, 32));
         g.threads = c->opt.threads_per_cta > 0 ? c->opt.threads_per_cta : (g.chunk > 512 ? 512 : 256);
-        g.smem = rollout_smem_bytes(g.chunk, g.threads);
-        if ((int)g.smem <= c->max_smem || cs >= kMaxCluster) break;
-        cs *= 2;  // partition too large for one CTA's shared memory: spread it wider
-    }
+        for (int depth : {8, 4}) {
+            g.ring = depth;
+            g.smem = rollout_smem_bytes(g.chunk, depth);
+            if ((int)g.smem <= c->max_smem) return true;
+        }
+        return false;
+    };
+    while (!fit(cs) && cs < kMaxCluster) cs *= 2;  // partition too large: spread it wider
     require((int)g.smem <= c->max_smem, FMDP_ERR_ARG, "plan table partition exceeds shared memory");
     // the cluster must fit on one GPC: halve it until the hardware can place one
     while (g.cs > 1 && rollout_max_active_clusters(g.cs, g.threads, g.smem) < 1) {
-        g.cs /= 2;
-        g.chunk = std::max(32, round_up((g.S_scan + g.cs - 1) / g.cs, 32));
-        g.smem = rollout_smem_bytes(g.chunk, g.threads);
-        require((int)g.smem <= c->max_smem, FMDP_ERR_ARG, "plan table partition exceeds shared memory");
+        require(fit(g.cs / 2), FMDP_ERR_ARG, "plan table partition exceeds shared memory");
     }
     c->last_cs = g.cs;
     c->last_threads = g.threads;
@@ -368,6 +372,7 @@ void enqueue_sequence(fmdp_ctx* c, SeqBuffers& B, int32_t n, int32_t cap, const 
         ra.S_scan = g.S_scan;
         ra.chunk = g.chunk;
         ra.cs = g.cs;
+        ra.ring = g.ring;
         ra.cap = cap;
         ra.reqs = B.reqs.p + i;
         ra.n_req = 1;
@@ -376,6 +381,7 @@ void enqueue_sequence(fmdp_ctx* c, SeqBuffers& B, int32_t n, int32_t cap, const 
         ra.acts = B.acts.p + (size_t)i * cap;
         ra.out = B.rout.p + i;
         ra.err = c->err;
+        ra.phase = c->phase_timing ? c->phase.p : nullptr;
         {
             KernelTimer t(c, 0);
             CK(launch_rollout(ra, g.threads, g.smem, c->stream));
@@ -615,6 +621,7 @@ void destroy_ctx(fmdp_ctx* c) {
     c->reqs.release(); c->traj.release(); c->acts.release(); c->rout.release(); c->sepo.release();
     c->slots.release(); c->t0s.release(); c->offs.release(); c->counts.release();
     c->q_trace.release(); c->st_trace.release(); c->hd_trace.release(); c->tie_trace.release();
+    c->phase.release();
     c->h_traj.release(); c->h_acts.release(); c->h_rout.release(); c->h_sep.release();
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     if (c->own) cudaStreamDestroy(c->own);
@@ -696,9 +703,9 @@ fmdp_status fmdp_create(const fmdp_airspace* air, double gamma, const fmdp_actio
         require(o.lookahead_W == 0 || o.lookahead_W == 1, FMDP_ERR_ARG, "only lookahead_W = 1 is implemented");
         require(o.goal_reward >= 0.0 && std::isfinite(o.goal_reward), FMDP_ERR_ARG, "goal reward must be >= 0");
         require(o.cluster_size >= 0 && o.cluster_size <= kMaxCluster, FMDP_ERR_ARG, "cluster size 0..16");
-        require(o.threads_per_cta == 0 || (o.threads_per_cta >= 64 && o.threads_per_cta <= 512 &&
+        require(o.threads_per_cta == 0 || (o.threads_per_cta >= 128 && o.threads_per_cta <= 512 &&
                                            o.threads_per_cta % 32 == 0),
-                FMDP_ERR_ARG, "threads per CTA: 0 or a multiple of 32 in [64, 512]");
+                FMDP_ERR_ARG, "threads per CTA: 0 or a multiple of 32 in [128, 512]");
         std::vector<fmdp_well> wells;
         if (o.wells && o.n_wells > 0) {
             wells.assign(o.wells, o.wells + o.n_wells);
@@ -1015,6 +1022,7 @@ fmdp_status fmdp_rollout_trace(fmdp_ctx* c, const fmdp_request* req, fmdp_result
         ra.S_scan = g.S_scan;
         ra.chunk = g.chunk;
         ra.cs = g.cs;
+        ra.ring = g.ring;
         ra.cap = cap;
         ra.reqs = c->reqs.p;
         ra.n_req = 1;
@@ -1097,9 +1105,15 @@ fmdp_status fmdp_set_profiling(fmdp_ctx* c, int32_t on) {
     if (!c) return FMDP_ERR_ARG;
     return guard(c, [&] {
         c->profiling = on != 0;
+        c->phase_timing = on == 2;
         c->stats = fmdp_stats{};
         c->pending.clear();
         c->ev_next = 0;
+        if (c->phase_timing) {
+            c->phase.ensure(6);
+            CK(cudaMemsetAsync(c->phase.p, 0, 6 * sizeof(unsigned long long), c->stream));
+            CK(cudaStreamSynchronize(c->stream));
+        }
     });
 }
 
@@ -1107,6 +1121,12 @@ fmdp_status fmdp_get_stats(fmdp_ctx* c, fmdp_stats* out) {
     if (!c || !out) return FMDP_ERR_ARG;
     return guard(c, [&] {
         *out = c->stats;
+        if (c->phase_timing) {
+            unsigned long long ph[6];
+            CK(cudaMemcpyAsync(ph, c->phase.p, sizeof(ph), cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaStreamSynchronize(c->stream));
+            for (int i = 0; i < 6; ++i) out->phase_cycles[i] = (int64_t)ph[i];
+        }
         out->cluster_size = c->last_cs;
         out->threads_per_cta = c->last_threads;
         out->slots_per_cta = c->last_chunk;

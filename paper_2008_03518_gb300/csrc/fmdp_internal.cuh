@@ -85,6 +85,7 @@ struct RolloutArgs {
     int32_t S_scan;   // slots scanned per step (multiple of 32)
     int32_t chunk;    // slots per CTA (multiple of 32)
     int32_t cs;       // CTAs per request (cluster size)
+    int32_t ring;     // slice buffers per CTA: 4 or 8
     int32_t cap;      // trajectory capacity per request (points)
     const fmdp_request* reqs;
     int32_t n_req;
@@ -97,6 +98,7 @@ struct RolloutArgs {
     int32_t* hd_trace;
     uint8_t* tie_trace;
     int32_t* err;     // device error word
+    unsigned long long* phase;  // [6] per-phase cycle counters (diagnostic) or nullptr
 };
 
 struct SepArgs {
@@ -128,7 +130,7 @@ struct AdmitArgs {
 
 // kernel launchers (rollout.cu / tables.cu)
 cudaError_t launch_rollout(const RolloutArgs& a, int threads, size_t smem, cudaStream_t s);
-size_t rollout_smem_bytes(int chunk, int threads);
+size_t rollout_smem_bytes(int chunk, int depth);
 cudaError_t prepare_rollout_kernel(size_t smem);
 int rollout_max_active_clusters(int cs, int threads, size_t smem);
 cudaError_t launch_sepcheck(const SepArgs& a, int n_req, int max_points, cudaStream_t s);

@@ -1,26 +1,30 @@
 // Persistent FastMDP rollout kernel (sm_103a).
 //
 // One thread-block cluster plans one request from departure to capture, horizon or
-// dead end, without returning to the host (the paper's CPU loop of Fig. 3 runs nine
+// dead end without returning to the host (the paper's CPU loop of Fig. 3 runs nine
 // kernels and a device-to-host copy per step; here the whole loop is one launch).
 //
-// Per step k (state s at time t = depart + k, successors at t + 1):
-//   staging   slices t+1 (well positions) and t+2 (plan velocity) of this CTA's slot
-//             partition arrive by TMA bulk copies into a 4-deep shared-memory ring; the
-//             producer runs two steps ahead because the table does not depend on s;
-//   cull      every slot whose wells cannot reach any successor is dropped by one
-//             distance test (radius max_k R_k + |tau|max |v| + step + 1 m);
-//   wells     near slots x actions x wells (Alg. 5-7, Table 3): lane a of a warp scores
-//             action a; log2 of |r| gamma^d is max-reduced per action (Alg. 8 max);
-//   exchange  per-action maxima are combined across the cluster through DSMEM;
-//   combine   warp 0 of every CTA forms Q = goal - penalty - hard deck (Alg. 1, 8),
-//             takes the argmax (Alg. 9, lowest index on ties) and advances the FP64
-//             state exactly as the forward projection defines it (Alg. 3).
+// Roles inside each CTA (the CTA owns a contiguous partition of the plan-table slots):
+//   warp 0      control: per-action work that does not depend on other plans (box test,
+//               goal term, terrain clearance, static wells; Alg. 1, Alg. 4, Alg. 6) while
+//               the other warps scan, then the exchange, argmax and state advance;
+//   warps 1..   scanners: stride over the partition's slots of slice t+1 (wells) and t+2
+//               (plan velocity); a slot whose wells cannot reach any successor is culled
+//               with one distance test, and for each near slot the whole warp evaluates
+//               the five wells of Table 3 with lane a scoring action a (Alg. 5-7);
+//   warp 1 l.0  producer: TMA bulk copies of upcoming slices into an 8-deep ring (the
+//               table does not depend on the aircraft, so it runs steps ahead).
+// Per-action maxima of log2(|r| gamma^d) are combined within the CTA by shared-memory
+// atomics and across the cluster by DSMEM pushes (st.async + mbarrier), so no cluster-wide
+// barrier is needed per step.
 //
-// Exactness: the state advance, box test, capture test and every threshold decision
-// (well edge, terrain clearance) are evaluated in FP64 with explicitly rounded
-// operations in the order the method defines them, so decisions match an FP64
-// evaluation bit for bit; magnitudes of the well values are fp32 (relative error ~1e-6).
+// Numerics. GB300 executes FP64 at 1/64 of the FP32 rate with ~63-cycle latency, so the
+// serial per-step chain is FP32: the state is carried as an exact FP64 triple (advanced by
+// three rounded adds, exactly as the method defines it) plus a double-float copy for
+// plan offsets; action values are compared through a (sign, log2|Q|) key. Every threshold
+// decision (box edge, well edge, clearance, capture) whose FP32 estimate lies within a
+// thin band of the threshold is re-evaluated in FP64 in the method's operation order, so
+// decisions match an FP64 evaluation bit for bit.
 #include <cfloat>
 #include <climits>
 
@@ -29,6 +33,11 @@
 namespace fmdp {
 
 namespace {
+
+constexpr int kRingDepth = 8;  // maximum ring depth (slices in flight + in use)
+constexpr unsigned kFull = 0xffffffffu;
+constexpr float kBoxBand = 0.01f;  // metres: FP32 box test margin before an exact check
+constexpr float kCapBand = 0.5f;   // metres: FP32 capture margin before an exact check
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -92,70 +101,100 @@ __device__ __forceinline__ uint32_t cluster_rank() {
 __device__ __forceinline__ void cluster_barrier() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
-__device__ __forceinline__ uint32_t dsmem_addr(const void* local, uint32_t rank) {
+__device__ __forceinline__ uint32_t dsmem_addr(uint32_t local, uint32_t rank) {
     uint32_t r;
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(local)), "r"(rank));
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
     return r;
 }
-__device__ __forceinline__ int dsmem_ld_s32(uint32_t addr) {
-    int v;
-    asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
-    return v;
+__device__ __forceinline__ void st_async_s32(uint32_t addr, int v, uint32_t bar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.s32 [%0], %1, [%2];" ::"r"(addr), "r"(v),
+                 "r"(bar)
+                 : "memory");
 }
-__device__ __forceinline__ unsigned long long dsmem_ld_u64(uint32_t addr) {
-    unsigned long long v;
-    asm volatile("ld.shared::cluster.u64 %0, [%1];" : "=l"(v) : "r"(addr) : "memory");
-    return v;
+__device__ __forceinline__ void st_async_u64(uint32_t addr, unsigned long long v, uint32_t bar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b64 [%0], %1, [%2];" ::"r"(addr), "l"(v),
+                 "r"(bar)
+                 : "memory");
 }
 
+// ---- double-float (fp32 pair) arithmetic: exact sums of fp32 numbers
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    e = __fsub_rn(b, __fsub_rn(s, a));
+}
+// (hi, lo) += (dh, dl)
+__device__ __forceinline__ void df_add(float& hi, float& lo, float dh, float dl) {
+    float s, e;
+    two_sum(hi, dh, s, e);
+    e = __fadd_rn(e, __fadd_rn(lo, dl));
+    fast_two_sum(s, e, hi, lo);
+}
+__device__ __forceinline__ float approx_sqrt(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
+
 struct StepState {
-    double s[3];      // current state (FP64)
-    double e2;        // |goal - s|^2, FP64 in the method's order
-    double cap2;      // (speed * dt)^2
-    double step;      // speed * dt
-    float s_hi[3], s_lo[3];  // s = s_hi + s_lo (fp32 pair) for fp32 plan offsets
-    float G[3];       // goal - s, fp32
-    float Gn;         // |G|
-    int h;            // heading index (15-degree units relative to the initial bearing)
+    double s[3];       // exact state (FP64)
+    double cap2;       // (speed * dt)^2
+    double step;       // speed * dt
+    float s_hi[3], s_lo[3];  // double-float copy of s
+    float G_hi[3], G_lo[3];  // goal - s, double-float
+    float phi;         // log2 of the goal term at s minus n0, in [0, 1)
+    int n0;            // integer part of log2 of the goal term at s
+    int h;             // heading index (15-degree units from the initial bearing)
     int done;
     int status;
     int n_points;
     int near_ties;
     int steps;
-    int abort_flag[2];  // this CTA's staging timed out in step k (indexed by k & 1)
-    int cnt[2];       // near-list counters (double buffered by scan round)
-    int ent_valid[kRing];
+    int ent_valid[kRingDepth];
+    int abort_flag[2];  // staging of step k timed out (indexed by k & 1)
+    int last_best;      // action chosen in the previous step (99: none)
 };
 
 // Shared-memory carve-up (identical on host and device).
 struct Layout {
-    size_t ring, bars, st, tabs, keys, sums, sq, nl, total;
-    int nl_cap;
+    size_t ring, bars, xbar, st, tabs, keys, sums, xkeys, xsums, xab, stat, aux, total;
 };
-__host__ __device__ inline Layout make_layout(int chunk, int threads) {
+__host__ __device__ inline Layout make_layout(int chunk, int depth) {
     Layout L;
     size_t o = 0;
+    auto al = [&](size_t a) { o = (o + a - 1) & ~(a - 1); };
     L.ring = o;
-    o += (size_t)kRing * 3 * chunk * sizeof(float);
-    o = (o + 15) & ~size_t(15);
+    o += (size_t)depth * 3 * chunk * sizeof(float);
+    al(16);
     L.bars = o;
-    o += kRing * sizeof(uint64_t);
+    o += kRingDepth * sizeof(uint64_t);
+    L.xbar = o;
+    o += 2 * sizeof(uint64_t);
+    al(16);
     L.st = o;
-    o += (sizeof(StepState) + 15) & ~size_t(15);
-    L.tabs = o;  // Dx[24], Dy[24], dz64[32] doubles, then dx32[24], dy32[24], dz32[32] floats
-    o += (24 + 24 + 32) * sizeof(double) + (24 + 24 + 32) * sizeof(float);
-    o = (o + 15) & ~size_t(15);
+    o += sizeof(StepState);
+    al(16);
+    L.tabs = o;  // Dx[24] Dy[24] Dz[32] doubles; dxh dxl dyh dyl [24] dzh dzl [32] floats
+    o += (24 + 24 + 32) * sizeof(double) + (4 * 24 + 2 * 32) * sizeof(float);
+    al(16);
     L.keys = o;
-    o += 2 * kMaxActions * sizeof(int);
-    o = (o + 15) & ~size_t(15);
+    o += kMaxActions * sizeof(int);
+    al(16);
     L.sums = o;
-    o += 2 * kMaxActions * sizeof(unsigned long long);
-    L.sq = o;
-    o += kMaxStatic * 3 * sizeof(float);
-    o = (o + 15) & ~size_t(15);
-    L.nl_cap = 2 * threads;
-    L.nl = o;
-    o += (size_t)L.nl_cap * 7 * sizeof(float);
+    o += kMaxActions * sizeof(unsigned long long);
+    L.xkeys = o;
+    o += 2 * kMaxCluster * kMaxActions * sizeof(int);
+    al(16);
+    L.xsums = o;
+    o += 2 * kMaxCluster * kMaxActions * sizeof(unsigned long long);
+    L.xab = o;
+    o += 2 * kMaxCluster * sizeof(int);
+    al(16);
+    L.stat = o;  // static-well centres as double-float: hi[64][3], lo[64][3]
+    o += 2 * kMaxStatic * 3 * sizeof(float);
+    al(16);
+    L.aux = o;   // valid, Delta, deck, key, class, log2|Q|, log2 scale: [7][32] words
+    o += 7 * kMaxActions * sizeof(int);
     L.total = (o + 127) & ~size_t(127);
     return L;
 }
@@ -205,9 +244,165 @@ __device__ __noinline__ bool static_inside_exact(const Model& m, const StepState
     return norm3_64(__dsub_rn(x, c[0]), __dsub_rn(y, c[1]), __dsub_rn(z, c[2])) < c[3];
 }
 
+__device__ __noinline__ bool box_inside_exact(const Model& m, const StepState* st, double Dx, double Dy, double Dz) {
+    const double x = __dadd_rn(st->s[0], Dx), y = __dadd_rn(st->s[1], Dy), z = __dadd_rn(st->s[2], Dz);
+    return x >= m.box[0] && x <= m.box[3] && y >= m.box[1] && y <= m.box[4] && z >= m.box[2] && z <= m.box[5];
+}
+
+__device__ __noinline__ float deck_exact(const Model& m, const StepState* st, double Dx, double Dy, double Dz) {
+    const double x = __dadd_rn(st->s[0], Dx), y = __dadd_rn(st->s[1], Dy), z = __dadd_rn(st->s[2], Dz);
+    const double c = __dsub_rn(z, terrain64(m, x, y));
+    return c < m.clearance ? (float)__dsub_rn(m.deck, c) : 0.f;
+}
+
+__device__ __noinline__ bool capture_exact(const StepState* st, const fmdp_request& req) {
+    const double ex = __dsub_rn(req.gx, st->s[0]), ey = __dsub_rn(req.gy, st->s[1]), ez = __dsub_rn(req.gz, st->s[2]);
+    return __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez)) <= st->cap2;
+}
+
+__device__ __noinline__ bool capture_exact_at(double x, double y, double z, const fmdp_request& req, double cap2) {
+    const double ex = __dsub_rn(req.gx, x), ey = __dsub_rn(req.gy, y), ez = __dsub_rn(req.gz, z);
+    return __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez)) <= cap2;
+}
+
+// log2 of the goal term, log2|r| + |G| log2(gamma), from a double-float goal vector G, split
+// into an integer n0 and a fraction phi in [0, 1) (fp32 pair arithmetic, ~1e-12 relative).
+__device__ __forceinline__ void goal_log_split(float Ghx, float Ghy, float Ghz, float Glx, float Gly, float Glz,
+                                               float lg_hi, float lg_lo, float l2r_hi, float l2r_lo, int& n0,
+                                               float& phi) {
+    const float p0 = Ghx * Ghx, p1 = Ghy * Ghy, p2 = Ghz * Ghz;
+    const float e0 = fmaf(Ghx, Ghx, -p0), e1 = fmaf(Ghy, Ghy, -p1), e2 = fmaf(Ghz, Ghz, -p2);
+    float s1, t1, s2, t2;
+    two_sum(p0, p1, s1, t1);
+    two_sum(s1, p2, s2, t2);
+    const float lo = t1 + t2 + e0 + e1 + e2 + 2.f * (Ghx * Glx + Ghy * Gly + Ghz * Glz);
+    float Sh, Sl;
+    fast_two_sum(s2, lo, Sh, Sl);
+    const float rt = approx_sqrt(Sh);
+    const float rr = fmaf(-rt, rt, Sh);
+    const float rl = rt > 0.f ? (rr + Sl) * (0.5f * rsqrtf(Sh)) : 0.f;
+    const float p = rt * lg_hi;
+    const float pe = fmaf(rt, lg_hi, -p);
+    const float lo2 = pe + rt * lg_lo + rl * lg_hi;
+    float Lh, Le;
+    two_sum(p, l2r_hi, Lh, Le);
+    Le = Le + (lo2 + l2r_lo);
+    float LH, LL;
+    fast_two_sum(Lh, Le, LH, LL);
+    float fl = floorf(LH);
+    float fr = (LH - fl) + LL;
+    if (fr >= 1.f) { fr -= 1.f; fl += 1.f; }
+    if (fr < 0.f) { fr += 1.f; fl -= 1.f; }
+    n0 = (int)fl;
+    phi = fr;
+}
+
+// Clearance penalty decided in FP64 at an exact successor (band around the threshold).
+__device__ __noinline__ float deck_exact_at(const Model& m, double X, double Y, double Z) {
+    const double c64 = __dsub_rn(Z, terrain64(m, X, Y));
+    return c64 < m.clearance ? (float)__dsub_rn(m.deck, c64) : 0.f;
+}
+
+// Static negative peaks (restricted volumes / terrain wells) for one action.
+__device__ __noinline__ void fold_statics(const Model& m, const StepState* st, const float* sch, const float* scl,
+                                          float shx, float shy, float shz, float slx, float sly, float slz,
+                                          float dxa, float dya, float dza, double Dxh, double Dyh, double Dza,
+                                          float& mloc, unsigned long long& sloc) {
+    for (int w = 0; w < m.n_static; ++w) {
+        const float qx = (sch[3 * w] - shx) + (scl[3 * w] - slx);
+        const float qy = (sch[3 * w + 1] - shy) + (scl[3 * w + 1] - sly);
+        const float qz = (sch[3 * w + 2] - shz) + (scl[3 * w + 2] - slz);
+        const float ex = dxa - qx, ey = dya - qy, ez = dza - qz;
+        const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+        const float R2 = m.st_R2[w], bw = m.st_band[w];
+        if (d2 < R2 + bw) {
+            const bool inside = d2 < R2 - bw ? true : static_inside_exact(m, st, Dxh, Dyh, Dza, w);
+            if (inside) {
+                const float l = fmaf(approx_sqrt(d2), m.st_lg[w], m.st_L[w]);
+                mloc = fmaxf(mloc, l);
+                if (m.combine) {
+                    const float t = exp2f(l - m.sum_ref) * 1099511627776.0f;
+                    sloc += (unsigned long long)__float2ull_rn(t);
+                }
+            }
+        }
+    }
+}
+
+// FP64 action value for the trace output only (never used for the decision).
+__device__ __noinline__ double trace_q(const Model& m, bool has_goal, int n0, float phi, float Dl, float Lp,
+                                       unsigned long long ssum, float Vd) {
+    double g = 0.0;
+    if (has_goal) g = exp2((double)n0 + (double)phi + (double)Dl * m.lg64);
+    double P = 0.0;
+    if (m.combine) P = (double)ssum * m.sum_scale;
+    else if (Lp > -INFINITY) P = exp2((double)Lp);
+    return __dsub_rn(__dsub_rn(g, P), (double)Vd);
+}
+
+// Diagnostic near-tie flag of the two best actions:
+// (Q1 - Q2) < 1e-4 * max(|Q1|, |Q2|, T1, T2), evaluated on log-magnitudes.
+__device__ __noinline__ bool near_tie(int c1, int c2, float la1, float la2, float lt1, float lt2) {
+    const float lsc = fmaxf(fmaxf(la1, la2), fmaxf(lt1, lt2));
+    const float hi = fmaxf(la1, la2), lo = fminf(la1, la2);
+    float lgap;
+    if (c1 == c2 && c1 != 1) lgap = hi + __log2f(fmaxf(1.f - exp2f(lo - hi), 1e-30f));
+    else lgap = hi + __log2f(1.f + exp2f(lo - hi));
+    return lgap < lsc - 13.287712f;  // log2(1e-4)
+}
+
+// Near-tie flag of the previous step from the keys the control warp stored (warp-wide call).
+__device__ __forceinline__ void deferred_tie(StepState* st, const uint32_t* qkey_s, const int* cls_s,
+                                             const float* la_s, const float* lt_s, int lane, uint8_t* trace_slot) {
+    const int b = st->last_best;
+    if (b >= 99) return;
+    const uint32_t qk = qkey_s[lane];
+    const uint32_t k2nd = __reduce_max_sync(kFull, lane == b ? 0u : qk);
+    const unsigned sm2 = __ballot_sync(kFull, qk == k2nd && k2nd != 0u && lane != b);
+    if (lane == 0) {
+        bool tie = false;
+        if (sm2) {
+            const int sec = __ffs(sm2) - 1;
+            tie = near_tie(cls_s[b], cls_s[sec], la_s[b], la_s[sec], lt_s[b], lt_s[sec]);
+        }
+        if (tie) st->near_ties += 1;
+        if (trace_slot) *trace_slot = tie ? 1 : 0;
+    }
+}
+
+// Monotone 32-bit argmax key: valid actions > 0; Q > 0 above Q = 0 above Q < 0; within a
+// class ordered by k2 (one float bit dropped, 2.4e-7 of log2|Q|).
+__device__ __forceinline__ uint32_t action_key(int cls, float k2) {
+    const uint32_t u = ((uint32_t)float_key(k2) ^ 0x80000000u) >> 1;
+    if (cls == 2) return 0x80000000u | u;
+    if (cls == 1) return 0x80000000u;
+    return u;
+}
+
 __device__ __forceinline__ unsigned long long sum_term(float l, float ref) {
     const float t = exp2f(l - ref) * 1099511627776.0f;  // 2^40 fixed point
     return (unsigned long long)__float2ull_rn(t);
+}
+
+// Scores one well of a plan for this lane's action: max-fold of log2(|r| gamma^d).
+__device__ __forceinline__ void fold_well(const Model& m, int w, float qx, float qy, float qz, float vx, float vy,
+                                          float vz, float dxa, float dya, float dza, float& mloc,
+                                          unsigned long long& sloc, bool& band) {
+    const float tau = m.w_tau[w];
+    const float ex = dxa - fmaf(tau, vx, qx);
+    const float ey = dya - fmaf(tau, vy, qy);
+    const float ez = dza - fmaf(tau, vz, qz);
+    const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+    const float R2 = m.w_R2[w], bw = m.w_band[w];
+    if (d2 < R2 + bw) {
+        if (d2 < R2 - bw) {
+            const float l = fmaf(approx_sqrt(d2), m.w_lg[w], m.w_L[w]);
+            mloc = fmaxf(mloc, l);
+            if (m.combine) sloc += sum_term(l, m.sum_ref);
+        } else {
+            band = true;
+        }
+    }
 }
 
 }  // namespace
@@ -225,30 +420,46 @@ __global__ void __launch_bounds__(512, 1) rollout_kernel(const __grid_constant__
     const int chunk = a.chunk;
     const int c_begin = (int)rank * chunk;
     const int c_len = max(0, min(chunk, a.S_scan - c_begin));
-    const Layout L = make_layout(chunk, NT);
+    const int depth = a.ring;                    // 4 or 8 slices
+    const int dshift = depth == 8 ? 3 : 2;
+    const Layout L = make_layout(chunk, depth);
 
     float* ring = reinterpret_cast<float*>(smem + L.ring);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.bars);
+    uint64_t* xbar = reinterpret_cast<uint64_t*>(smem + L.xbar);
     StepState* st = reinterpret_cast<StepState*>(smem + L.st);
     double* Dx = reinterpret_cast<double*>(smem + L.tabs);
     double* Dy = Dx + 24;
     double* Dz = Dy + 24;
-    float* dx32 = reinterpret_cast<float*>(Dz + 32);
-    float* dy32 = dx32 + 24;
-    float* dz32 = dy32 + 24;
-    int* keys = reinterpret_cast<int*>(smem + L.keys);                                   // [2][32]
-    unsigned long long* sums = reinterpret_cast<unsigned long long*>(smem + L.sums);     // [2][32]
-    float* sq = reinterpret_cast<float*>(smem + L.sq);                                   // [64][3]
-    int* nl_slot = reinterpret_cast<int*>(smem + L.nl);
-    float* nl_f = reinterpret_cast<float*>(nl_slot + L.nl_cap);  // 6 planes: qx qy qz vx vy vz
-    const int NL = L.nl_cap;
+    float* dxh = reinterpret_cast<float*>(Dz + 32);
+    float* dxl = dxh + 24;
+    float* dyh = dxl + 24;
+    float* dyl = dyh + 24;
+    float* dzh = dyl + 24;
+    float* dzl = dzh + 32;
+    int* keys = reinterpret_cast<int*>(smem + L.keys);
+    unsigned long long* sums = reinterpret_cast<unsigned long long*>(smem + L.sums);
+    int* xkeys = reinterpret_cast<int*>(smem + L.xkeys);                                 // [2][16][32]
+    unsigned long long* xsums = reinterpret_cast<unsigned long long*>(smem + L.xsums);   // [2][16][32]
+    int* xab = reinterpret_cast<int*>(smem + L.xab);                                     // [2][16]
+    float* sch = reinterpret_cast<float*>(smem + L.stat);
+    float* scl = sch + 3 * kMaxStatic;
+    int* valid_s = reinterpret_cast<int*>(smem + L.aux);
+    float* Dl_s = reinterpret_cast<float*>(valid_s + kMaxActions);
+    float* Vd_s = Dl_s + kMaxActions;
+    uint32_t* qkey_s = reinterpret_cast<uint32_t*>(Vd_s + kMaxActions);
+    int* cls_s = reinterpret_cast<int*>(qkey_s + kMaxActions);
+    float* la_s = reinterpret_cast<float*>(cls_s + kMaxActions);
+    float* lt_s = la_s + kMaxActions;
 
     const bool lead = (rank == 0);
     float* traj = a.traj + (size_t)r * a.cap * 3;
     uint8_t* acts = a.acts + (size_t)r * a.cap;
     const int64_t t_lo = a.tab.t_base, t_hi = a.tab.t_base + a.tab.T_win;
+    const int64_t last_j = (int64_t)req.horizon + 1;
+    const int KEY_NONE = float_key(-INFINITY);
 
-    // ---- prologue: heading table (exact), action offsets, initial state
+    // ---------------------------------------------------------------- prologue
     if (tid < kHeadings) {
         const double dx = __dsub_rn(req.gx, req.ox), dy = __dsub_rn(req.gy, req.oy);
         const double Lh = __dsqrt_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
@@ -259,42 +470,57 @@ __global__ void __launch_bounds__(512, 1) rollout_kernel(const __grid_constant__
         const double C = __dsub_rn(__dmul_rn(c0, ck), __dmul_rn(s0, sk));
         const double S = __dadd_rn(__dmul_rn(s0, ck), __dmul_rn(c0, sk));
         const double step = __dmul_rn(req.speed_mps, m.dt);
-        Dx[tid] = __dmul_rn(step, C);
-        Dy[tid] = __dmul_rn(step, S);
-        dx32[tid] = (float)Dx[tid];
-        dy32[tid] = (float)Dy[tid];
+        const double X = __dmul_rn(step, C), Y = __dmul_rn(step, S);
+        Dx[tid] = X;
+        Dy[tid] = Y;
+        dxh[tid] = (float)X;
+        dxl[tid] = (float)__dsub_rn(X, (double)dxh[tid]);
+        dyh[tid] = (float)Y;
+        dyl[tid] = (float)__dsub_rn(Y, (double)dyh[tid]);
     }
     if (tid < kMaxActions) {
         const double dz = tid < A ? __dmul_rn(m.climb[tid], m.dt) : 0.0;
         Dz[tid] = dz;
-        dz32[tid] = (float)dz;
-        keys[tid] = keys[kMaxActions + tid] = float_key(-INFINITY);
-        sums[tid] = sums[kMaxActions + tid] = 0ull;
+        dzh[tid] = (float)dz;
+        dzl[tid] = (float)__dsub_rn(dz, (double)dzh[tid]);
+        keys[tid] = KEY_NONE;
+        sums[tid] = 0ull;
+    }
+    for (int w = tid; w < m.n_static; w += NT) {
+        const double* c = m.statics + 6 * w;
+        for (int q = 0; q < 3; ++q) {
+            sch[3 * w + q] = (float)c[q];
+            scl[3 * w + q] = (float)__dsub_rn(c[q], (double)sch[3 * w + q]);
+        }
     }
     if (tid == 0) {
-        for (int e = 0; e < kRing; ++e) mbar_init(&bars[e], 1);
+        for (int e = 0; e < kRingDepth; ++e) mbar_init(&bars[e], 1);
+        mbar_init(&xbar[0], 1);
+        mbar_init(&xbar[1], 1);
         mbar_fence_init();
         const double step = __dmul_rn(req.speed_mps, m.dt);
         st->step = step;
         st->cap2 = __dmul_rn(step, step);
-        st->s[0] = req.ox; st->s[1] = req.oy; st->s[2] = req.oz;
-        const double ex = __dsub_rn(req.gx, req.ox), ey = __dsub_rn(req.gy, req.oy), ez = __dsub_rn(req.gz, req.oz);
-        st->e2 = __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez));
-        for (int i = 0; i < 3; ++i) {
-            st->s_hi[i] = (float)st->s[i];
-            st->s_lo[i] = (float)__dsub_rn(st->s[i], (double)st->s_hi[i]);
+        const double s0[3] = {req.ox, req.oy, req.oz};
+        const double g0[3] = {req.gx, req.gy, req.gz};
+        for (int q = 0; q < 3; ++q) {
+            st->s[q] = s0[q];
+            st->s_hi[q] = (float)s0[q];
+            st->s_lo[q] = (float)__dsub_rn(s0[q], (double)st->s_hi[q]);
+            const double G = __dsub_rn(g0[q], s0[q]);
+            st->G_hi[q] = (float)G;
+            st->G_lo[q] = (float)__dsub_rn(G, (double)st->G_hi[q]);
         }
-        st->G[0] = (float)ex; st->G[1] = (float)ey; st->G[2] = (float)ez;
-        st->Gn = sqrtf(st->G[0] * st->G[0] + st->G[1] * st->G[1] + st->G[2] * st->G[2]);
         st->h = 0;
-        const bool captured = st->e2 <= st->cap2;
+        const bool captured = capture_exact(st, req);
         st->done = captured || req.horizon <= 0;
         st->status = captured ? kStatusCaptured : FMDP_REJ_HORIZON;
         st->n_points = 1;
         st->near_ties = 0;
         st->steps = 0;
         st->abort_flag[0] = st->abort_flag[1] = 0;
-        st->cnt[0] = st->cnt[1] = 0;
+        st->last_best = 99;
+        for (int e = 0; e < kRingDepth; ++e) st->ent_valid[e] = 0;
         if (lead) {
             traj[0] = (float)req.ox; traj[1] = (float)req.oy; traj[2] = (float)req.oz;
             if (a.trace && r == 0) {
@@ -303,394 +529,441 @@ __global__ void __launch_bounds__(512, 1) rollout_kernel(const __grid_constant__
             }
         }
     }
-    for (int w = tid; w < m.n_static; w += NT) {
-        const double* c = m.statics + 6 * w;
-        sq[3 * w] = (float)__dsub_rn(c[0], req.ox);
-        sq[3 * w + 1] = (float)__dsub_rn(c[1], req.oy);
-        sq[3 * w + 2] = (float)__dsub_rn(c[2], req.oz);
+    if (cs > 1) cluster_barrier(); else __syncthreads();  // mbarriers initialised cluster-wide
+
+    // ---- producer state (thread 32: warp 1, lane 0)
+    const bool producer = (tid == 32);
+    int64_t issued = 0, waited = 0;
+    int64_t next_row = 0;  // ring row of slice `issued + 1`
+    auto entry_of = [&](int64_t j) { return (int)((j - 1) & (depth - 1)); };
+    auto parity_of = [&](int64_t j) { return (uint32_t)(((j - 1) >> dshift) & 1); };
+    auto issue_upto = [&](int64_t jmax) {
+        for (int64_t j = issued + 1; j <= jmax && j <= last_j; ++j) {
+            const int e = entry_of(j);
+            const int64_t T = req.depart_step + j;
+            const bool valid = c_len > 0 && T >= t_lo && T < t_hi;
+            st->ent_valid[e] = valid ? 1 : 0;
+            if (valid) {
+                const size_t off = (size_t)next_row * a.tab.S_pad + c_begin;
+                const uint32_t bytes = (uint32_t)c_len * 4u;
+                float* dst = ring + (size_t)e * 3 * chunk;
+                mbar_arrive_expect_tx(&bars[e], 3u * bytes);
+                tma_bulk_load(dst, a.tab.X + off, bytes, &bars[e]);
+                tma_bulk_load(dst + chunk, a.tab.Y + off, bytes, &bars[e]);
+                tma_bulk_load(dst + 2 * chunk, a.tab.Z + off, bytes, &bars[e]);
+            } else {
+                mbar_arrive(&bars[e]);
+            }
+            issued = j;
+            if (++next_row == a.tab.T_win) next_row = 0;
+        }
+    };
+    // returns 1 on timeout
+    auto wait_upto = [&](int64_t jneed) -> int {
+        while (waited < jneed && waited < issued) {
+            const int64_t j = waited + 1;
+            if (!mbar_wait_bounded(&bars[entry_of(j)], parity_of(j))) {
+                atomicExch(a.err, FMDP_ERR_TIMEOUT);
+                for (int e = 0; e < depth; ++e) st->ent_valid[e] = 0;
+                return 1;
+            }
+            waited = j;
+        }
+        return 0;
+    };
+    bool stalled = false;
+    if (producer && !st->done) {
+        const int64_t T1 = req.depart_step + 1;
+        int64_t row = T1 % a.tab.T_win;
+        if (row < 0) row += a.tab.T_win;
+        next_row = row;
+        issue_upto(depth);
+        stalled = wait_upto(2) != 0;
+        st->abort_flag[0] = stalled ? 1 : 0;
+    }
+
+    // ---- per-lane action constants (every warp: lane a scores action a)
+    const int my_dh = lane < A ? m.dh[lane] : 0;
+    const float my_dzh = dzh[lane], my_dzl = dzl[lane];
+    const double my_Dz = Dz[lane];
+    float dzmax = 0.f;
+    for (int i = 0; i < A; ++i) dzmax = fmaxf(dzmax, fabsf(dzh[i]));
+    const float stepf = (float)st->step;
+    const double cap2 = st->cap2;
+    const float reach0 = m.reach_base + stepf + dzmax;
+    const float inv_dt = (float)(1.0 / m.dt);
+    float ghi[3], glo[3];  // goal as double-float
+    {
+        const double g0[3] = {req.gx, req.gy, req.gz};
+        for (int q = 0; q < 3; ++q) {
+            ghi[q] = (float)g0[q];
+            glo[q] = (float)__dsub_rn(g0[q], (double)ghi[q]);
+        }
+    }
+    const float box0 = (float)m.box[0], box1 = (float)m.box[1], box2 = (float)m.box[2];
+    const float box3 = (float)m.box[3], box4 = (float)m.box[4], box5 = (float)m.box[5];
+    const float lg_hi = (float)m.lg64, lg_lo = (float)(m.lg64 - (double)(float)m.lg64);
+    const bool has_goal = m.goal_reward > 0.0;
+    const float l2r_hi = has_goal ? (float)m.log2rg : 0.f;
+    const float l2r_lo = has_goal ? (float)(m.log2rg - (double)(float)m.log2rg) : 0.f;
+    const float clr = (float)m.clearance, deckf = (float)m.deck;
+    const float* __restrict__ hm = m.hm;
+    const int hm_nx = m.hm_nx, hm_ny = m.hm_ny;
+    const float hm_sx = m.hm_sx, hm_sy = m.hm_sy;
+    const int n_static = m.n_static, n_wells = m.n_wells, combine = m.combine;
+    const float lg32 = m.lg32, sum_ref = m.sum_ref, tau_absmax = m.tau_absmax;
+    const bool trace0 = a.trace && lead && r == 0;
+    if (tid == 0) {
+        int n0;
+        float phi;
+        goal_log_split(st->G_hi[0], st->G_hi[1], st->G_hi[2], st->G_lo[0], st->G_lo[1], st->G_lo[2], lg_hi, lg_lo,
+                       l2r_hi, l2r_lo, n0, phi);
+        st->n0 = n0;
+        st->phi = phi;
     }
     __syncthreads();
 
-    // producer: slice j >= 1 (time depart + j) into ring entry (j - 1) % kRing; its mbarrier
-    // phase parity is ((j - 1) / kRing) & 1
-    const int64_t last_j = (int64_t)req.horizon + 1;
-    auto entry_of = [](int64_t j) { return (int)((j - 1) % kRing); };
-    auto parity_of = [](int64_t j) { return (uint32_t)(((j - 1) / kRing) & 1); };
-    auto issue = [&](int64_t j) {
-        const int e = entry_of(j);
-        const int64_t T = req.depart_step + j;
-        const bool valid = c_len > 0 && T >= t_lo && T < t_hi;
-        st->ent_valid[e] = valid ? 1 : 0;
-        if (valid) {
-            int64_t row = T % a.tab.T_win;
-            if (row < 0) row += a.tab.T_win;
-            const size_t off = (size_t)row * a.tab.S_pad + c_begin;
-            const uint32_t bytes = (uint32_t)c_len * 4u;
-            float* dst = ring + (size_t)e * 3 * chunk;
-            mbar_arrive_expect_tx(&bars[e], 3u * bytes);
-            tma_bulk_load(dst, a.tab.X + off, bytes, &bars[e]);
-            tma_bulk_load(dst + chunk, a.tab.Y + off, bytes, &bars[e]);
-            tma_bulk_load(dst + 2 * chunk, a.tab.Z + off, bytes, &bars[e]);
-        } else {
-            mbar_arrive(&bars[e]);
-        }
-    };
-    int64_t issued = 0;  // highest slice index issued (thread 0)
-    int64_t waited = 0;  // highest slice index waited for (thread 0)
-    if (tid == 0 && !st->done) {
-        for (int64_t j = 1; j < kRing && j <= last_j; ++j) { issue(j); issued = j; }
-    }
+    const bool timing = a.phase != nullptr && lead;
+    unsigned long long ph[6] = {0, 0, 0, 0, 0, 0};
+    long long tp = 0;
 
-    // A staging wait that runs out (it never should) does not break the loop on its own:
-    // the CTA flags it for this step, the flags of all CTAs are combined after the same
-    // cluster barrier as the action values, and every CTA of the cluster then stops at the
-    // same step, so the cluster barriers stay matched.
-    int round = 0;
-    bool stalled = false;
-    for (int k = 0;; ++k) {
-        if (tid == 0 && !st->done) {
-            int timed_out = 0;
-            if (!stalled) {
-                const int64_t jn = (int64_t)k + kRing;
-                if (jn <= last_j) { issue(jn); issued = jn; }
-                const int64_t need = min((int64_t)k + 2, last_j);
-                while (waited < need) {
-                    const int64_t j = waited + 1;
-                    if (!mbar_wait_bounded(&bars[entry_of(j)], parity_of(j))) {
-                        timed_out = 1;
-                        stalled = true;
-                        atomicExch(a.err, FMDP_ERR_TIMEOUT);
-                        for (int e = 0; e < kRing; ++e) st->ent_valid[e] = 0;
-                        break;
-                    }
-                    waited = j;
-                }
-            } else {
-                timed_out = 1;
-            }
-            st->abort_flag[k & 1] = timed_out;
-        }
-        __syncthreads();  // S1: state, ring entries and flags published
+    // ---------------------------------------------------------------- step loop
+    int k = 0;
+    for (;; ++k) {
+        if (timing && tid == 0) tp = clock64();
+        __syncthreads();  // S1: state and ring entries published
+        if (timing && tid == 0) { const long long t = clock64(); ph[0] += t - tp; tp = t; }
         if (st->done) break;
-
-        const int e1 = entry_of(k + 1), e2 = entry_of(k + 2);
-        const bool v1 = st->ent_valid[e1] != 0;
-        const bool v2 = (k + 2 <= last_j) && st->ent_valid[e2] != 0;
-        // acquire the async-proxy writes that the producer observed complete
-        if (v1) mbar_test_wait(&bars[e1], parity_of(k + 1));
-        if (v2) mbar_test_wait(&bars[e2], parity_of(k + 2));
-
         const int par = k & 1;
+        const int h = st->h;
+        int hn = h + my_dh;  // heading index after the action's turn, wrapped to [0, 24)
+        hn += hn < 0 ? 24 : 0;
+        hn -= hn >= 24 ? 24 : 0;
+        const float dxa = dxh[hn], dya = dyh[hn], dza = my_dzh;  // fp32 of the exact offsets
         const float shx = st->s_hi[0], shy = st->s_hi[1], shz = st->s_hi[2];
         const float slx = st->s_lo[0], sly = st->s_lo[1], slz = st->s_lo[2];
-        const int h = st->h;
-        const float dtf = (float)m.dt;
-        const float stepf = (float)st->step;
-        // cull radius without the plan's motion: max_k R_k + 1 m + largest successor offset
-        float dzmax = 0.f;
-        for (int i = 0; i < A; ++i) dzmax = fmaxf(dzmax, fabsf(dz32[i]));
-        const float reach0 = m.reach_base + stepf + dzmax;
-
-        // per-lane action constants
-        int hn = 0;
-        float dxa = 0.f, dya = 0.f, dza = 0.f;
-        double DXa = 0.0, DYa = 0.0, DZa = 0.0;
-        if (lane < A) {
-            hn = ((h + m.dh[lane]) % 24 + 24) % 24;
-            dxa = dx32[hn]; dya = dy32[hn]; dza = dz32[lane];
-            DXa = Dx[hn]; DYa = Dy[hn]; DZa = Dz[lane];
-        }
         float mloc = -INFINITY;
         unsigned long long sloc = 0ull;
 
-        const float* X1 = ring + (size_t)e1 * 3 * chunk;
-        const float* Y1 = X1 + chunk;
-        const float* Z1 = Y1 + chunk;
-        const float* X2 = ring + (size_t)e2 * 3 * chunk;
-        const float* Y2 = X2 + chunk;
-        const float* Z2 = Y2 + chunk;
-        const int per_round = 2 * NT;
-        const int scan_len = v1 ? c_len : 0;
-        for (int base = 0; base < scan_len; base += per_round) {
-            const int cpar = round & 1;
-            // ---- cull
+        // control warp: the successor of action `lane` as a complete next-step state, kept in
+        // registers until the combine publishes the winner's
+        bool capn = false;
+        double X = 0.0, Y = 0.0, Z = 0.0;
+        float nhx = 0.f, nlx = 0.f, nhy = 0.f, nly = 0.f, nhz = 0.f, nlz = 0.f;
+        float Gnhx = 0.f, Gnlx = 0.f, Gnhy = 0.f, Gnly = 0.f, Gnhz = 0.f, Gnlz = 0.f;
+        int n0n = 0;
+        float phin = 0.f;
+
+        if (warp == 0) {
+            if (lane < A) {
+                // exact successor (Alg. 3) and its double-float copy
+                X = __dadd_rn(st->s[0], Dx[hn]);
+                Y = __dadd_rn(st->s[1], Dy[hn]);
+                Z = __dadd_rn(st->s[2], my_Dz);
+                nhx = shx; nlx = slx; df_add(nhx, nlx, dxh[hn], dxl[hn]);
+                nhy = shy; nly = sly; df_add(nhy, nly, dyh[hn], dyl[hn]);
+                nhz = shz; nlz = slz; df_add(nhz, nlz, my_dzh, my_dzl);
+                // goal vector at the successor, its goal-term split and capture test
+                Gnhx = ghi[0]; Gnlx = glo[0]; df_add(Gnhx, Gnlx, -nhx, -nlx);
+                Gnhy = ghi[1]; Gnly = glo[1]; df_add(Gnhy, Gnly, -nhy, -nly);
+                Gnhz = ghi[2]; Gnlz = glo[2]; df_add(Gnhz, Gnlz, -nhz, -nlz);
+                goal_log_split(Gnhx, Gnhy, Gnhz, Gnlx, Gnly, Gnlz, lg_hi, lg_lo, l2r_hi, l2r_lo, n0n, phin);
+                const float gx = Gnhx + Gnlx, gy = Gnhy + Gnly, gz = Gnhz + Gnlz;
+                if (approx_sqrt(gx * gx + gy * gy + gz * gz) < stepf + kCapBand)
+                    capn = capture_exact_at(X, Y, Z, req, cap2);
+            }
+            if (timing && tid == 0) { const long long t = clock64(); ph[1] += t - tp; tp = t; }
+        } else if (warp == 1) {
+            // evaluator warp: near-tie flag of the previous step (diagnostic, off the critical
+            // path), then the per-action terms that do not involve other plans
+            if (k > 0) deferred_tie(st, qkey_s, cls_s, la_s, lt_s, lane, trace0 ? a.tie_trace + (k - 1) : nullptr);
+            if (lane < A) {
+                // successor estimate (fp32); terrain loads first, they are the longest wait
+                const float sx = shx + (slx + dxa), sy = shy + (sly + dya), sz = shz + (slz + dza);
+                float h00 = 0.f, h10 = 0.f, h01 = 0.f, h11 = 0.f, ax = 0.f, ay = 0.f;
+                if (hm) {
+                    const float gxf = (sx - box0) * hm_sx;
+                    const float gyf = (sy - box1) * hm_sy;
+                    int ix = (int)floorf(gxf), iy = (int)floorf(gyf);
+                    ix = min(max(ix, 0), hm_nx - 2);
+                    iy = min(max(iy, 0), hm_ny - 2);
+                    ax = gxf - (float)ix;
+                    ay = gyf - (float)iy;
+                    const float* r0 = hm + (size_t)iy * hm_nx + ix;
+                    h00 = __ldg(r0);
+                    h10 = __ldg(r0 + 1);
+                    h01 = __ldg(r0 + hm_nx);
+                    h11 = __ldg(r0 + hm_nx + 1);
+                }
+                // box validity: fp32 margin, exact comparison near a face
+                const float mlo = fminf(fminf(sx - box0, sy - box1), sz - box2);
+                const float mhi = fminf(fminf(box3 - sx, box4 - sy), box5 - sz);
+                const float mb = fminf(mlo, mhi);
+                bool valid;
+                if (mb > kBoxBand) valid = true;
+                else if (mb < -kBoxBand) valid = false;
+                else valid = box_inside_exact(m, st, Dx[hn], Dy[hn], my_Dz);
+                // goal distance change Delta = |G - delta| - |G| at the current state
+                const float Gx = st->G_hi[0] + st->G_lo[0], Gy = st->G_hi[1] + st->G_lo[1],
+                            Gz = st->G_hi[2] + st->G_lo[2];
+                const float Gn = approx_sqrt(Gx * Gx + Gy * Gy + Gz * Gz);
+                const float fx = Gx - dxa, fy = Gy - dya, fz = Gz - dza;
+                const float da = approx_sqrt(fx * fx + fy * fy + fz * fz);
+                const float num = (dxa * dxa + dya * dya + dza * dza) - 2.0f * (Gx * dxa + Gy * dya + Gz * dza);
+                const float den = da + Gn;
+                const float Dl = den > 0.f ? __fdividef(num, den) : 0.f;
+                // hard deck: terrain clearance at the successor (Alg. 1)
+                float Vd = 0.f;
+                if (hm) {
+                    const float hz = (1.f - ay) * ((1.f - ax) * h00 + ax * h10) + ay * ((1.f - ax) * h01 + ax * h11);
+                    const float c = sz - hz;
+                    if (fabsf(c - clr) < kClrBand) Vd = deck_exact(m, st, Dx[hn], Dy[hn], my_Dz);
+                    else if (c < clr) Vd = deckf - c;
+                }
+                valid_s[lane] = valid ? 1 : 0;
+                Dl_s[lane] = Dl;
+                Vd_s[lane] = Vd;
+                // static negative peaks (restricted volumes / terrain wells), CTA 0 only
+                if (lead && n_static > 0)
+                    fold_statics(m, st, sch, scl, shx, shy, shz, slx, sly, slz, dxa, dya, dza, Dx[hn], Dy[hn], my_Dz,
+                                 mloc, sloc);
+            }
+        } else {
+            // ---- scanners: cull, then wells of near slots with lanes as actions
+            const long long ts = (timing && tid == NT - 32) ? clock64() : 0;
+            const int e1 = entry_of(k + 1), e2 = entry_of(k + 2);
+            const bool v1 = st->ent_valid[e1] != 0;
+            const bool v2 = (k + 2 <= last_j) && st->ent_valid[e2] != 0;
+            if (v1) mbar_test_wait(&bars[e1], parity_of(k + 1));
+            if (v2) mbar_test_wait(&bars[e2], parity_of(k + 2));
+            const float* X1 = ring + (size_t)e1 * 3 * chunk;
+            const float* Y1 = X1 + chunk;
+            const float* Z1 = Y1 + chunk;
+            const float* X2 = ring + (size_t)e2 * 3 * chunk;
+            const float* Y2 = X2 + chunk;
+            const float* Z2 = Y2 + chunk;
+            const int scan_len = v1 ? c_len : 0;
+            const int nscan = NW - 2;
+            constexpr int U = 4;  // slots per lane per pass (independent chains)
+            for (int base = (warp - 2) * 32 * U; base < scan_len; base += nscan * 32 * U) {
+                float qx[U], qy[U], qz[U], vx[U], vy[U], vz[U];
+                bool near[U];
 #pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const int i = base + tid + u * NT;
-                bool near = false;
-                float qx = 0.f, qy = 0.f, qz = 0.f, vx = 0.f, vy = 0.f, vz = 0.f;
-                if (i < scan_len) {
-                    const float p1x = X1[i], p1y = Y1[i], p1z = Z1[i];
-                    qx = (p1x - shx) - slx;
-                    qy = (p1y - shy) - sly;
-                    qz = (p1z - shz) - slz;
-                    if (v2) {
-                        const float p2x = X2[i];
-                        if (p2x == p2x) {
-                            vx = (p2x - p1x) / dtf;
-                            vy = (Y2[i] - p1y) / dtf;
-                            vz = (Z2[i] - p1z) / dtf;
+                for (int u = 0; u < U; ++u) {
+                    const int i = base + u * 32 + lane;
+                    near[u] = false;
+                    qx[u] = qy[u] = qz[u] = vx[u] = vy[u] = vz[u] = 0.f;
+                    if (i < scan_len) {
+                        const float p1x = X1[i], p1y = Y1[i], p1z = Z1[i];
+                        qx[u] = (p1x - shx) - slx;
+                        qy[u] = (p1y - shy) - sly;
+                        qz[u] = (p1z - shz) - slz;
+                        if (v2) {
+                            const float p2x = X2[i];
+                            if (p2x == p2x) {
+                                vx[u] = (p2x - p1x) * inv_dt;
+                                vy[u] = (Y2[i] - p1y) * inv_dt;
+                                vz[u] = (Z2[i] - p1z) * inv_dt;
+                            }
                         }
+                        const float reach =
+                            fmaf(tau_absmax, approx_sqrt(vx[u] * vx[u] + vy[u] * vy[u] + vz[u] * vz[u]), reach0);
+                        near[u] = (qx[u] * qx[u] + qy[u] * qy[u] + qz[u] * qz[u]) < reach * reach;  // NaN: false
                     }
-                    const float vn = sqrtf(vx * vx + vy * vy + vz * vz);
-                    const float reach = fmaf(m.tau_absmax, vn, reach0);
-                    near = (qx * qx + qy * qy + qz * qz) < reach * reach;  // NaN: false
                 }
-                const unsigned mask = __ballot_sync(0xffffffffu, near);
-                int pos0 = 0;
-                if (lane == 0 && mask) pos0 = atomicAdd(&st->cnt[cpar], __popc(mask));
-                pos0 = __shfl_sync(0xffffffffu, pos0, 0);
-                if (near) {
-                    const int pos = pos0 + __popc(mask & ((1u << lane) - 1u));
-                    nl_slot[pos] = i;
-                    nl_f[pos] = qx; nl_f[NL + pos] = qy; nl_f[2 * NL + pos] = qz;
-                    nl_f[3 * NL + pos] = vx; nl_f[4 * NL + pos] = vy; nl_f[5 * NL + pos] = vz;
-                }
-            }
-            __syncthreads();  // S2: near list complete
-            const int n_near = st->cnt[cpar];
-            if (tid == 0) st->cnt[cpar ^ 1] = 0;
-            // ---- wells of near slots: warp per slot, lane per action
-            for (int ei = warp; ei < n_near; ei += NW) {
-                const float qx = nl_f[ei], qy = nl_f[NL + ei], qz = nl_f[2 * NL + ei];
-                const float vx = nl_f[3 * NL + ei], vy = nl_f[4 * NL + ei], vz = nl_f[5 * NL + ei];
-                if (lane < A) {
-                    for (int w = 0; w < m.n_wells; ++w) {
-                        const float tau = m.w_tau[w];
-                        const float ex = dxa - fmaf(tau, vx, qx);
-                        const float ey = dya - fmaf(tau, vy, qy);
-                        const float ez = dza - fmaf(tau, vz, qz);
-                        const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-                        const float R2 = m.w_R2[w], band = m.w_band[w];
-                        if (d2 < R2 + band) {
-                            bool inside = d2 < R2 - band;
-                            if (!inside) {
-                                const int i = nl_slot[ei];
-                                const bool has2 = v2 && (X2[i] == X2[i]);
-                                inside = well_inside_exact(m, st, DXa, DYa, DZa, X1[i], Y1[i], Z1[i],
-                                                           has2 ? X2[i] : 0.f, has2 ? Y2[i] : 0.f,
-                                                           has2 ? Z2[i] : 0.f, has2, w);
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    unsigned mask = __ballot_sync(kFull, near[u]);
+                    while (mask) {
+                        const int b = __ffs(mask) - 1;
+                        mask &= mask - 1;
+                        const float bqx = __shfl_sync(kFull, qx[u], b), bqy = __shfl_sync(kFull, qy[u], b),
+                                    bqz = __shfl_sync(kFull, qz[u], b);
+                        const float bvx = __shfl_sync(kFull, vx[u], b), bvy = __shfl_sync(kFull, vy[u], b),
+                                    bvz = __shfl_sync(kFull, vz[u], b);
+                        if (lane < A) {
+                            float mb = -INFINITY;
+                            unsigned long long sb = 0ull;
+                            for (int w = 0; w < n_wells; ++w) {
+                                bool bw = false;
+                                fold_well(m, w, bqx, bqy, bqz, bvx, bvy, bvz, dxa, dya, dza, mb, sb, bw);
+                                if (bw) {
+                                    // within the FP32 band of the radius: decide in FP64
+                                    const int ii = base + u * 32 + b;
+                                    const bool has2 = v2 && (X2[ii] == X2[ii]);
+                                    if (well_inside_exact(m, st, Dx[hn], Dy[hn], my_Dz, X1[ii], Y1[ii], Z1[ii],
+                                                          has2 ? X2[ii] : 0.f, has2 ? Y2[ii] : 0.f,
+                                                          has2 ? Z2[ii] : 0.f, has2, w)) {
+                                        const float tau = m.w_tau[w];
+                                        const float ex = dxa - fmaf(tau, bvx, bqx), ey = dya - fmaf(tau, bvy, bqy),
+                                                    ez = dza - fmaf(tau, bvz, bqz);
+                                        const float l = fmaf(approx_sqrt(fmaf(ex, ex, fmaf(ey, ey, ez * ez))),
+                                                             m.w_lg[w], m.w_L[w]);
+                                        mb = fmaxf(mb, l);
+                                        if (m.combine) sb += sum_term(l, m.sum_ref);
+                                    }
+                                }
                             }
-                            if (inside) {
-                                const float l = fmaf(__fsqrt_rn(d2), m.w_lg[w], m.w_L[w]);
-                                mloc = fmaxf(mloc, l);
-                                if (m.combine) sloc += sum_term(l, m.sum_ref);
-                            }
+                            mloc = fmaxf(mloc, mb);
+                            sloc += sb;
                         }
                     }
                 }
             }
-            ++round;
-            __syncthreads();  // list consumed
-        }
-        // ---- static wells (restricted volumes / terrain peaks): CTA 0 of the cluster
-        if (lead && m.n_static > 0 && lane < A) {
-            for (int w = warp; w < m.n_static; w += NW) {
-                const float ex = dxa - sq[3 * w], ey = dya - sq[3 * w + 1], ez = dza - sq[3 * w + 2];
-                const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-                const float R2 = m.st_R2[w], band = m.st_band[w];
-                if (d2 < R2 + band) {
-                    bool inside = d2 < R2 - band;
-                    if (!inside) inside = static_inside_exact(m, st, DXa, DYa, DZa, w);
-                    if (inside) {
-                        const float l = fmaf(__fsqrt_rn(d2), m.st_lg[w], m.st_L[w]);
-                        mloc = fmaxf(mloc, l);
-                        if (m.combine) sloc += sum_term(l, m.sum_ref);
-                    }
-                }
-            }
+            if (ts) ph[4] += clock64() - ts;
         }
         if (lane < A) {
-            if (mloc > -INFINITY) atomicMax(&keys[par * kMaxActions + lane], float_key(mloc));
-            if (sloc) atomicAdd(&sums[par * kMaxActions + lane], sloc);
+            if (mloc > -INFINITY) atomicMax(&keys[lane], float_key(mloc));
+            if (sloc) atomicAdd(&sums[lane], sloc);
         }
-        if (cs > 1) cluster_barrier(); else __syncthreads();  // S3: per-action partials complete
+        __syncwarp();
+        if (timing && tid == 0) tp = clock64();
+        __syncthreads();  // S3: per-action partials of this CTA complete
+        if (timing && tid == 0) { const long long t = clock64(); ph[2] += t - tp; tp = t; }
 
-        // ---- combine, argmax, advance (warp 0 of every CTA, identical results)
         if (warp == 0) {
-            const bool act = lane < A;
-            int key = float_key(-INFINITY);
-            unsigned long long ssum = 0ull;
-            int any_abort = 0;
-            if (lane < cs) {
-                any_abort = cs > 1 ? dsmem_ld_s32(dsmem_addr(&st->abort_flag[par], lane)) : st->abort_flag[par];
-            }
-            any_abort = __any_sync(0xffffffffu, any_abort != 0);
-            if (act) {
-                if (cs > 1) {
-                    for (int q = 0; q < cs; ++q) {
-                        key = max(key, dsmem_ld_s32(dsmem_addr(&keys[par * kMaxActions + lane], q)));
-                        if (m.combine) ssum += dsmem_ld_u64(dsmem_addr(&sums[par * kMaxActions + lane], q));
+            // ---- exchange across the cluster (DSMEM push, one hop) or read locally
+            int key = lane < A ? keys[lane] : KEY_NONE;
+            unsigned long long ssum = lane < A ? sums[lane] : 0ull;
+            int ab = st->abort_flag[par];
+            if (lane < A) { keys[lane] = KEY_NONE; sums[lane] = 0ull; }
+            if (cs > 1) {
+                const uint32_t bytes = (uint32_t)cs * ((uint32_t)A * (m.combine ? 12u : 4u) + 4u);
+                if (lane == 0) mbar_arrive_expect_tx(&xbar[par], bytes);
+                const uint32_t kslot = smem_u32(&xkeys[(par * kMaxCluster + (int)rank) * kMaxActions + lane]);
+                const uint32_t sslot = smem_u32(&xsums[(par * kMaxCluster + (int)rank) * kMaxActions + lane]);
+                const uint32_t aslot = smem_u32(&xab[par * kMaxCluster + (int)rank]);
+                const uint32_t bslot = smem_u32(&xbar[par]);
+                for (int q = 0; q < cs; ++q) {
+                    const uint32_t rb = dsmem_addr(bslot, (uint32_t)q);
+                    if (lane < A) {
+                        st_async_s32(dsmem_addr(kslot, (uint32_t)q), key, rb);
+                        if (m.combine) st_async_u64(dsmem_addr(sslot, (uint32_t)q), ssum, rb);
                     }
+                    if (lane == 31) st_async_s32(dsmem_addr(aslot, (uint32_t)q), ab, rb);
+                }
+                if (!mbar_wait_bounded(&xbar[par], (uint32_t)((k >> 1) & 1))) {
+                    atomicExch(a.err, FMDP_ERR_TIMEOUT);
+                    ab = 1;
                 } else {
-                    key = keys[par * kMaxActions + lane];
-                    ssum = sums[par * kMaxActions + lane];
-                }
-            }
-            // penalty P of negative peaks (FP64 magnitude of the fp32 log-domain aggregate)
-            double P = 0.0;
-            if (m.combine) {
-                P = (double)ssum * m.sum_scale;
-            } else {
-                const float Lp = key_float(key);
-                if (Lp > -INFINITY) {
-                    const float kf = floorf(Lp);
-                    P = scale2((double)exp2f(Lp - kf), (int)kf);
-                }
-            }
-            // successor (exact), validity (box)
-            const double x = __dadd_rn(st->s[0], DXa), y = __dadd_rn(st->s[1], DYa), z = __dadd_rn(st->s[2], DZa);
-            const bool valid = act && x >= m.box[0] && x <= m.box[3] && y >= m.box[1] && y <= m.box[4] &&
-                               z >= m.box[2] && z <= m.box[5];
-            // goal distance change Delta = |G - delta| - |G| in fp32 (G = goal - s)
-            const float gX = st->G[0], gY = st->G[1], gZ = st->G[2], gN = st->Gn;
-            const float fx = gX - dxa, fy = gY - dya, fz = gZ - dza;
-            const float da = sqrtf(fx * fx + fy * fy + fz * fz);
-            const float num = (dxa * dxa + dya * dya + dza * dza) - 2.0f * (gX * dxa + gY * dya + gZ * dza);
-            const float den = da + gN;
-            const float Dlt = den > 0.f ? num / den : 0.f;
-            // hard deck: terrain clearance at the successor
-            double V = 0.0;
-            if (m.hm && act) {
-                const float gxf = (float)__dsub_rn(x, m.box[0]) * m.hm_sx;
-                const float gyf = (float)__dsub_rn(y, m.box[1]) * m.hm_sy;
-                int ix = (int)floorf(gxf), iy = (int)floorf(gyf);
-                ix = min(max(ix, 0), m.hm_nx - 2);
-                iy = min(max(iy, 0), m.hm_ny - 2);
-                const float ax = gxf - (float)ix, ay = gyf - (float)iy;
-                const float* r0 = m.hm + (size_t)iy * m.hm_nx + ix;
-                const float h00 = __ldg(r0), h10 = __ldg(r0 + 1), h01 = __ldg(r0 + m.hm_nx), h11 = __ldg(r0 + m.hm_nx + 1);
-                const float hz = (1.f - ay) * ((1.f - ax) * h00 + ax * h10) + ay * ((1.f - ax) * h01 + ax * h11);
-                const float c = (float)z - hz;
-                const float clr = (float)m.clearance;
-                if (fabsf(c - clr) < kClrBand) {
-                    const double c64 = __dsub_rn(z, terrain64(m, x, y));
-                    V = c64 < m.clearance ? __dsub_rn(m.deck, c64) : 0.0;
-                } else if (c < clr) {
-                    V = m.deck - (double)c;
-                }
-            }
-            const double N = P + V;
-            const unsigned pen = __ballot_sync(0xffffffffu, valid && N > 0.0);
-            const bool full = a.trace || pen != 0u || !(m.goal_reward > 0.0);
-            int best = 99, second = 99;
-            bool tie = false;
-            double Qa = -INFINITY;
-            if (!full) {
-                // all valid successors are free of penalties: Q = g is decreasing in the goal distance
-                float kb = valid ? Dlt : INFINITY;
-                int ib = valid ? lane : 99;
-                for (int off = 16; off; off >>= 1) {
-                    const float ok = __shfl_xor_sync(0xffffffffu, kb, off);
-                    const int oi = __shfl_xor_sync(0xffffffffu, ib, off);
-                    if (ok < kb || (ok == kb && oi < ib)) { kb = ok; ib = oi; }
-                }
-                best = ib;
-                float k2 = (valid && lane != best) ? Dlt : INFINITY;
-                int i2 = (valid && lane != best) ? lane : 99;
-                for (int off = 16; off; off >>= 1) {
-                    const float ok = __shfl_xor_sync(0xffffffffu, k2, off);
-                    const int oi = __shfl_xor_sync(0xffffffffu, i2, off);
-                    if (ok < k2 || (ok == k2 && oi < i2)) { k2 = ok; i2 = oi; }
-                }
-                second = i2;
-                if (best < 99 && second < 99) {
-                    const float gap = 1.0f - exp2f(-(k2 - kb) * fabsf(m.lg32));
-                    tie = gap < (float)kTieRel;
-                }
-            } else {
-                // full FP64 values: g = 2^(Lg0 + Delta * log2 gamma), Lg0 from the exact |goal - s|
-                double Lg0 = 0.0;
-                if (lane == 0) Lg0 = m.log2rg + __dsqrt_rn(st->e2) * m.lg64;
-                Lg0 = __shfl_sync(0xffffffffu, Lg0, 0);
-                double g = 0.0;
-                if (m.goal_reward > 0.0) {
-                    const double n0 = floor(Lg0);
-                    const float phi = (float)(Lg0 - n0);
-                    g = scale2((double)exp2f(fmaf(Dlt, m.lg32, phi)), (int)n0);
-                }
-                Qa = valid ? __dsub_rn(__dsub_rn(g, P), V) : -INFINITY;
-                const double T = fmax(g, N);
-                double qb = valid ? Qa : -INFINITY;
-                int ib = valid ? lane : 99;
-                for (int off = 16; off; off >>= 1) {
-                    const double oq = __shfl_xor_sync(0xffffffffu, qb, off);
-                    const int oi = __shfl_xor_sync(0xffffffffu, ib, off);
-                    if (oq > qb || (oq == qb && oi < ib)) { qb = oq; ib = oi; }
-                }
-                best = ib;
-                double q2 = (valid && lane != best) ? Qa : -INFINITY;
-                int i2 = (valid && lane != best) ? lane : 99;
-                for (int off = 16; off; off >>= 1) {
-                    const double oq = __shfl_xor_sync(0xffffffffu, q2, off);
-                    const int oi = __shfl_xor_sync(0xffffffffu, i2, off);
-                    if (oq > q2 || (oq == q2 && oi < i2)) { q2 = oq; i2 = oi; }
-                }
-                second = i2;
-                if (best < 99 && second < 99) {
-                    const double T1 = __shfl_sync(0xffffffffu, T, best);
-                    const double T2 = __shfl_sync(0xffffffffu, T, second);
-                    const double sc = fmax(fmax(fabs(qb), fabs(q2)), fmax(T1, T2));
-                    tie = (qb - q2) < kTieRel * sc;
-                }
-                if (a.trace && lead && r == 0 && act) a.q_trace[(size_t)k * A + lane] = Qa;
-            }
-            if (any_abort) {
-                if (lane == 0) { st->done = 1; st->status = FMDP_REJ_NO_ACTION; st->steps = k; }
-            } else if (best >= 99) {
-                if (lane == 0) { st->done = 1; st->status = FMDP_REJ_NO_ACTION; st->steps = k; }
-            } else {
-                const double nx = __shfl_sync(0xffffffffu, x, best);
-                const double ny = __shfl_sync(0xffffffffu, y, best);
-                const double nz = __shfl_sync(0xffffffffu, z, best);
-                const int nh = __shfl_sync(0xffffffffu, hn, best);
-                if (lane == 0) {
-                    st->s[0] = nx; st->s[1] = ny; st->s[2] = nz;
-                    st->h = nh;
-                    const double ex = __dsub_rn(req.gx, nx), ey = __dsub_rn(req.gy, ny), ez = __dsub_rn(req.gz, nz);
-                    const double e2 = __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez));
-                    st->e2 = e2;
-                    st->s_hi[0] = (float)nx; st->s_hi[1] = (float)ny; st->s_hi[2] = (float)nz;
-                    st->s_lo[0] = (float)__dsub_rn(nx, (double)st->s_hi[0]);
-                    st->s_lo[1] = (float)__dsub_rn(ny, (double)st->s_hi[1]);
-                    st->s_lo[2] = (float)__dsub_rn(nz, (double)st->s_hi[2]);
-                    const float Gx = (float)ex, Gy = (float)ey, Gz = (float)ez;
-                    st->G[0] = Gx; st->G[1] = Gy; st->G[2] = Gz;
-                    st->Gn = sqrtf(Gx * Gx + Gy * Gy + Gz * Gz);
-                    const int np = st->n_points;
-                    st->n_points = np + 1;
-                    if (tie) st->near_ties += 1;
-                    const bool captured = e2 <= st->cap2;
-                    const bool last = (k + 1) >= req.horizon;
-                    st->done = captured || last;
-                    st->status = captured ? kStatusCaptured : FMDP_REJ_HORIZON;
-                    st->steps = k + 1;
-                    if (lead) {
-                        traj[3 * np] = (float)nx; traj[3 * np + 1] = (float)ny; traj[3 * np + 2] = (float)nz;
-                        acts[k] = (uint8_t)best;
-                        if (a.trace && r == 0) {
-                            a.st_trace[3 * np] = nx; a.st_trace[3 * np + 1] = ny; a.st_trace[3 * np + 2] = nz;
-                            a.hd_trace[np] = nh;
-                            a.tie_trace[k] = tie ? 1 : 0;
+                    key = KEY_NONE;
+                    ssum = 0ull;
+                    int any = 0;
+                    for (int q = 0; q < cs; ++q) {
+                        if (lane < A) {
+                            key = max(key, xkeys[(par * kMaxCluster + q) * kMaxActions + lane]);
+                            ssum += xsums[(par * kMaxCluster + q) * kMaxActions + lane];
                         }
+                        any |= xab[par * kMaxCluster + q];
+                    }
+                    ab = any;
+                }
+            }
+            ab = __any_sync(kFull, ab != 0) ? 1 : 0;
+
+            // ---- action values as (sign class, log2 |Q|) keys; Q = g - P - V (Alg. 1, Alg. 8)
+            const int n0 = st->n0;
+            const float phi = st->phi;
+            const bool valid = lane < A && valid_s[lane] != 0;
+            const float Dl = Dl_s[lane], Vd = Vd_s[lane];
+            float Lp;
+            if (combine) Lp = ssum ? __log2f((float)ssum) + (sum_ref - 40.0f) : -INFINITY;
+            else Lp = key_float(key);
+            const float logN = Vd > 0.f ? __log2f(exp2f(Lp) + Vd) : Lp;  // log2 of N = P + V
+            const float lgh = phi + Dl * lg32;                             // log2(g) - n0
+            int cls;   // 2: Q > 0, 1: Q = 0, 0: Q < 0
+            float k2;  // larger is better within a class
+            float la;  // log2 |Q|
+            if (logN == -INFINITY) {
+                cls = has_goal ? 2 : 1;
+                k2 = has_goal ? lgh : 0.f;
+                la = has_goal ? lgh + (float)n0 : -INFINITY;
+            } else {
+                const float gh = has_goal ? exp2f(lgh) : 0.f;
+                const float Nh = exp2f(logN - (float)n0);
+                const float d = gh - Nh;
+                if (has_goal && d > 0.f) {
+                    cls = 2;
+                    k2 = __log2f(d);
+                    la = k2 + (float)n0;
+                } else if (d == 0.f) {
+                    cls = 1;
+                    k2 = 0.f;
+                    la = -INFINITY;
+                } else {
+                    cls = 0;
+                    const float rat = (has_goal && Nh < INFINITY) ? __fdividef(gh, Nh) : 0.f;
+                    la = logN + __log2f(1.f - rat);
+                    k2 = -la;
+                }
+            }
+            const uint32_t qkey = (lane < A && valid) ? action_key(cls, k2) : 0u;
+            const uint32_t kmax = __reduce_max_sync(kFull, qkey);
+            const unsigned bm = __ballot_sync(kFull, qkey == kmax && kmax != 0u);
+            const int best = bm ? __ffs(bm) - 1 : 99;
+            if (ab || best >= 99) {
+                if (lane == 0) { st->done = 1; st->status = FMDP_REJ_NO_ACTION; st->steps = k; }
+            } else if (lane == best) {
+                // the winning lane publishes its successor as the next state
+                st->s[0] = X; st->s[1] = Y; st->s[2] = Z;
+                st->s_hi[0] = nhx; st->s_lo[0] = nlx;
+                st->s_hi[1] = nhy; st->s_lo[1] = nly;
+                st->s_hi[2] = nhz; st->s_lo[2] = nlz;
+                st->G_hi[0] = Gnhx; st->G_lo[0] = Gnlx;
+                st->G_hi[1] = Gnhy; st->G_lo[1] = Gnly;
+                st->G_hi[2] = Gnhz; st->G_lo[2] = Gnlz;
+                st->n0 = n0n;
+                st->phi = phin;
+                st->h = hn;
+                const bool last = (k + 1) >= req.horizon;
+                st->done = capn || last;
+                st->status = capn ? kStatusCaptured : FMDP_REJ_HORIZON;
+                st->steps = k + 1;
+                const int np = k + 1;  // one point per step after the origin
+                st->n_points = np + 1;
+                if (lead) {
+                    traj[3 * np] = (float)X;
+                    traj[3 * np + 1] = (float)Y;
+                    traj[3 * np + 2] = (float)Z;
+                    acts[k] = (uint8_t)best;
+                    if (a.trace && r == 0) {
+                        a.st_trace[3 * np] = X;
+                        a.st_trace[3 * np + 1] = Y;
+                        a.st_trace[3 * np + 2] = Z;
+                        a.hd_trace[np] = hn;
                     }
                 }
-                for (int w = lane; w < m.n_static; w += 32) {
-                    const double* c = m.statics + 6 * w;
-                    sq[3 * w] = (float)__dsub_rn(c[0], nx);
-                    sq[3 * w + 1] = (float)__dsub_rn(c[1], ny);
-                    sq[3 * w + 2] = (float)__dsub_rn(c[2], nz);
-                }
             }
-            if (act) {
-                keys[(par ^ 1) * kMaxActions + lane] = float_key(-INFINITY);
-                sums[(par ^ 1) * kMaxActions + lane] = 0ull;
+            // keys of this step for the evaluator warp's deferred near-tie flag
+            qkey_s[lane] = qkey;
+            cls_s[lane] = cls;
+            la_s[lane] = la;
+            lt_s[lane] = fmaxf(has_goal ? lgh + (float)n0 : -INFINITY, logN);  // log2 max(g, N)
+            if (lane == 0) st->last_best = (ab || best >= 99) ? 99 : best;
+            if (trace0 && lane < A)  // FP64 action values for the trace (not used for the decision)
+                a.q_trace[(size_t)k * A + lane] = valid ? trace_q(m, has_goal, n0, phi, Dl, Lp, ssum, Vd) : -INFINITY;
+            if (timing && tid == 0) ph[3] += clock64() - tp;
+        } else if (producer) {
+            // ---- producer: slices needed two or more steps ahead
+            const long long t0 = timing ? clock64() : 0;
+            int to = 0;
+            if (!stalled) {
+                issue_upto((int64_t)k + 1 + depth);
+                to = wait_upto((int64_t)k + 3);
+                if (to) stalled = true;
+            } else {
+                to = 1;
             }
+            st->abort_flag[par ^ 1] = to;
+            if (timing) ph[5] += clock64() - t0;
         }
+        __syncwarp();  // reconverge the control warp and the producer's warp before S1
     }
 
-    // drain: every issued copy must land before the CTA exits
-    if (tid == 0) {
+    // ---- epilogue: near-tie flag of the last step, drain the ring, outputs
+    if (warp == 1 && k > 0) deferred_tie(st, qkey_s, cls_s, la_s, lt_s, lane, trace0 ? a.tie_trace + (k - 1) : nullptr);
+    __syncthreads();
+    if (producer) {
         while (waited < issued) {
             const int64_t j = waited + 1;
             if (!mbar_wait_bounded(&bars[entry_of(j)], parity_of(j))) {
@@ -699,19 +972,22 @@ __global__ void __launch_bounds__(512, 1) rollout_kernel(const __grid_constant__
             }
             waited = j;
         }
-        if (lead) {
-            RolloutOut o;
-            o.n_points = st->n_points;
-            o.status = st->status;
-            o.near_ties = st->near_ties;
-            o.steps = st->steps;
-            a.out[r] = o;
-        }
     }
-    if (cs > 1) cluster_barrier();  // peers may still read this CTA's shared memory
+    if (tid == 0 && lead) {
+        RolloutOut o;
+        o.n_points = st->n_points;
+        o.status = st->status;
+        o.near_ties = st->near_ties;
+        o.steps = st->steps;
+        a.out[r] = o;
+    }
+    if (timing && (tid == 0 || tid == NT - 32 || producer))
+        for (int i = 0; i < 6; ++i)
+            if (ph[i]) atomicAdd(&a.phase[i], ph[i]);
+    if (cs > 1) cluster_barrier();  // peers may still address this CTA's shared memory
 }
 
-size_t rollout_smem_bytes(int chunk, int threads) { return make_layout(chunk, threads).total; }
+size_t rollout_smem_bytes(int chunk, int depth) { return make_layout(chunk, depth).total; }
 
 cudaError_t prepare_rollout_kernel(size_t smem) {
     cudaError_t e = cudaFuncSetAttribute(rollout_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -81,7 +81,8 @@ class Stats(ctypes.Structure):
                 ("sepcheck_ms", ctypes.c_double), ("admit_ms", ctypes.c_double),
                 ("rollout_steps", ctypes.c_int64), ("slots_scanned", ctypes.c_int64),
                 ("sep_pairs", ctypes.c_int64), ("cluster_size", ctypes.c_int32),
-                ("threads_per_cta", ctypes.c_int32), ("slots_per_cta", ctypes.c_int32)]
+                ("threads_per_cta", ctypes.c_int32), ("slots_per_cta", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("phase_cycles", ctypes.c_int64 * 6)]
 
 
 # every exported symbol of include/fmdp.h
@@ -394,9 +395,11 @@ class Scheduler:
 
     # ------------------------------------------------------------ profiling
     def set_profiling(self, on=True):
-        self._check(self._L.fmdp_set_profiling(self._h, 1 if on else 0))
+        self._check(self._L.fmdp_set_profiling(self._h, int(on)))
 
     def stats(self):
         s = Stats()
         self._check(self._L.fmdp_get_stats(self._h, ctypes.byref(s)))
-        return {k: getattr(s, k) for k, _ in Stats._fields_}
+        d = {k: getattr(s, k) for k, _ in Stats._fields_ if k != "phase_cycles"}
+        d["phase_cycles"] = list(s.phase_cycles)
+        return d

@@ -74,8 +74,8 @@ def _depart(req):
 
 def fcfs_parity(gpu, o, reqs, trace_q=False, gpu_results=None):
     """FCFS over reqs on both sides; the oracle follows the GPU at near-ties and stores
-    what it admits. Returns (verdicts, followed near-ties)."""
-    verdicts, followed = [], 0
+    what it admits. Returns (verdicts, followed near-ties, steps)."""
+    verdicts, followed, steps = [], 0, 0
     for i, r in enumerate(reqs):
         if trace_q:
             t = gpu.rollout_trace(r)
@@ -90,5 +90,6 @@ def fcfs_parity(gpu, o, reqs, trace_q=False, gpu_results=None):
         if v == ADMITTED:
             o.add_plan(_depart(r), d["xyz"])
         followed += d["followed_ties"]
+        steps += max(int(g["n_points"]) - 1, 0)
         verdicts.append(v)
-    return verdicts, followed
+    return verdicts, followed, steps
