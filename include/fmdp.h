@@ -195,6 +195,29 @@ typedef struct {
 fmdp_status fmdp_sep_check(fmdp_ctx* ctx, int64_t t0_step, const float* xyz, int32_t n,
                            fmdp_sep_report* out);
 
+/* ---- allocation-free separation check (no counterpart in the paper) ----
+ * Same check and report as fmdp_sep_check, for callers that cannot allocate device memory
+ * while they run: flight or ground software that must fix its memory footprint at start-up
+ * (certified or real-time code that forbids allocation after initialisation), and code
+ * that must not pay for, or be synchronised by, cudaMalloc/cudaFree on its path.
+ * fmdp_sep_check stages the trajectory and its accumulators in device memory that the
+ * library allocates and grows on demand; this variant stages them in one fixed scratch
+ * array that is part of the loaded library image, and allocates nothing.
+ *   - At most FMDP_NOALLOC_MAX_POINTS samples (xyz: host, 3*n fp32); a larger n returns
+ *     FMDP_ERR_ARG and planning state is untouched. out: host report.
+ *   - The scratch array (about 192 KiB, held by every GPU that loads the library until
+ *     the process exits) is shared by every call on that device and keeps the last call's
+ *     contents; each call clears the accumulators it needs. Calls whose device work
+ *     overlaps (several host threads, or several contexts on one device) race on the
+ *     array and must be serialised by the caller.
+ *   - The first call on a device is a set-up call: it looks up the array's device address,
+ *     and with lazy module loading that is also when the driver places the array in device
+ *     memory. Make that first call during start-up, before any stream capture; later calls
+ *     take no device memory. */
+#define FMDP_NOALLOC_MAX_POINTS 16384
+fmdp_status fmdp_sep_check_noalloc(fmdp_ctx* ctx, int64_t t0_step, const float* xyz, int32_t n,
+                                   fmdp_sep_report* out);
+
 typedef struct {
     int64_t rollout_launches, sepcheck_launches, admit_launches;
     double rollout_ms, sepcheck_ms, admit_ms; /* summed CUDA-event durations */

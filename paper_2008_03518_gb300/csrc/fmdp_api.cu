@@ -651,6 +651,17 @@ fmdp_status guard(fmdp_ctx* c, F&& f) {
 
 }  // namespace
 
+// Accessors for the allocation-free entry point (noalloc.cu).
+namespace fmdp {
+void ctx_sep_view(fmdp_ctx* c, SepView* v) {
+    v->m = c->model;
+    v->tab = table_view(c);
+    v->S_scan = round_up(c->book.S_hw, 32);
+    v->stream = c->stream;
+}
+void ctx_set_error(fmdp_ctx* c, const char* msg) { c->err_msg = msg ? msg : ""; }
+}  // namespace fmdp
+
 // ====================================================================== C ABI
 
 extern "C" {

@@ -128,6 +128,16 @@ struct AdmitArgs {
     const int64_t* offs;   // force mode: per plan offset into traj (points)
 };
 
+// What a separation check needs from a context (implemented in fmdp_api.cu).
+struct SepView {
+    Model m;
+    TableView tab;
+    int32_t S_scan;
+    cudaStream_t stream;
+};
+void ctx_sep_view(fmdp_ctx* ctx, SepView* v);
+void ctx_set_error(fmdp_ctx* ctx, const char* msg);
+
 // kernel launchers (rollout.cu / tables.cu)
 cudaError_t launch_rollout(const RolloutArgs& a, int threads, size_t smem, cudaStream_t s);
 size_t rollout_smem_bytes(int chunk, int depth);

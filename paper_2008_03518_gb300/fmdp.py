@@ -90,7 +90,9 @@ EXPORTS = ("fmdp_options_default", "fmdp_create", "fmdp_destroy", "fmdp_last_err
            "fmdp_add_plan", "fmdp_add_plans", "fmdp_schedule", "fmdp_schedule_many", "fmdp_schedule_batch",
            "fmdp_stage_requests", "fmdp_schedule_staged", "fmdp_fetch_staged", "fmdp_query_plans",
            "fmdp_get_plan", "fmdp_expire", "fmdp_snapshot", "fmdp_restore", "fmdp_clear", "fmdp_rollout_trace",
-           "fmdp_sep_check", "fmdp_set_profiling", "fmdp_get_stats")
+           "fmdp_sep_check", "fmdp_sep_check_noalloc", "fmdp_set_profiling", "fmdp_get_stats")
+
+NOALLOC_MAX_POINTS = 16384  # FMDP_NOALLOC_MAX_POINTS
 
 _lib = None
 
@@ -134,6 +136,7 @@ def load(build_if_missing: bool = True):
         getattr(L, name).argtypes = [vp]
     L.fmdp_rollout_trace.argtypes = [vp, P(Request), P(Result), _dp, _dp, P(c.c_int32), P(c.c_uint8)]
     L.fmdp_sep_check.argtypes = [vp, c.c_int64, _fp, c.c_int32, P(SepReport)]
+    L.fmdp_sep_check_noalloc.argtypes = [vp, c.c_int64, _fp, c.c_int32, P(SepReport)]
     L.fmdp_set_profiling.argtypes = [vp, c.c_int32]
     L.fmdp_get_stats.argtypes = [vp, P(Stats)]
     for name in EXPORTS:
@@ -391,6 +394,14 @@ class Scheduler:
         rep = SepReport()
         self._check(self._L.fmdp_sep_check(self._h, int(t0), _ptr(xyz, ctypes.c_float), xyz.shape[0],
                                            ctypes.byref(rep)))
+        return {k: getattr(rep, k) for k, _ in SepReport._fields_}
+
+    def sep_check_noalloc(self, t0, xyz):
+        """fmdp_sep_check_noalloc: the same check using the library's fixed scratch array."""
+        xyz = np.ascontiguousarray(xyz, dtype=np.float32).reshape(-1, 3)
+        rep = SepReport()
+        self._check(self._L.fmdp_sep_check_noalloc(self._h, int(t0), _ptr(xyz, ctypes.c_float), xyz.shape[0],
+                                                   ctypes.byref(rep)))
         return {k: getattr(rep, k) for k, _ in SepReport._fields_}
 
     # ------------------------------------------------------------ profiling
