@@ -88,7 +88,7 @@ typedef struct {
     double goal_reward;       /* |r| of the goal peak (Table 3: 200) */
     int32_t lookahead_W;      /* lookahead window; only 1 is implemented */
     int32_t cluster_size;     /* CTAs cooperating on one rollout (0 = automatic) */
-    int32_t threads_per_cta;  /* 0 = automatic */
+    int32_t threads_per_cta;  /* 0 = automatic; else a multiple of 32 in [128, 384] */
     int32_t reserved;
 } fmdp_options;
 

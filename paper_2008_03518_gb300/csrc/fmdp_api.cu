@@ -316,7 +316,7 @@ Geometry geometry(fmdp_ctx* c, int32_t S_hw) {
     auto fit = [&](int cs_) {
         g.cs = cs_;
         g.chunk = std::max(32, round_up((g.S_scan + cs_ - 1) / cs_, 32));
-        g.threads = c->opt.threads_per_cta > 0 ? c->opt.threads_per_cta : (g.chunk > 512 ? 512 : 256);
+        g.threads = c->opt.threads_per_cta > 0 ? c->opt.threads_per_cta : (g.chunk > 256 ? 384 : 256);
         for (int depth : {8, 4}) {
             g.ring = depth;
             g.smem = rollout_smem_bytes(g.chunk, depth);
@@ -714,9 +714,9 @@ fmdp_status fmdp_create(const fmdp_airspace* air, double gamma, const fmdp_actio
         require(o.lookahead_W == 0 || o.lookahead_W == 1, FMDP_ERR_ARG, "only lookahead_W = 1 is implemented");
         require(o.goal_reward >= 0.0 && std::isfinite(o.goal_reward), FMDP_ERR_ARG, "goal reward must be >= 0");
         require(o.cluster_size >= 0 && o.cluster_size <= kMaxCluster, FMDP_ERR_ARG, "cluster size 0..16");
-        require(o.threads_per_cta == 0 || (o.threads_per_cta >= 128 && o.threads_per_cta <= 512 &&
+        require(o.threads_per_cta == 0 || (o.threads_per_cta >= 128 && o.threads_per_cta <= 384 &&
                                            o.threads_per_cta % 32 == 0),
-                FMDP_ERR_ARG, "threads per CTA: 0 or a multiple of 32 in [128, 512]");
+                FMDP_ERR_ARG, "threads per CTA: 0 or a multiple of 32 in [128, 384]");
         std::vector<fmdp_well> wells;
         if (o.wells && o.n_wells > 0) {
             wells.assign(o.wells, o.wells + o.n_wells);

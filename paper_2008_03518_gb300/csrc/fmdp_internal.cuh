@@ -98,6 +98,9 @@ struct RolloutArgs {
     int32_t* hd_trace;
     uint8_t* tie_trace;
     int32_t* err;     // device error word
+    int32_t* queue;   // batch mode: request counter the CTAs pull from (nullptr: one cluster per request)
+    const int32_t* idx;    // batch mode: request index of work item w (nullptr: identity)
+    const int32_t* n_dev;  // batch mode: number of work items, read on the device (nullptr: n_req)
     unsigned long long* phase;  // [6] per-phase cycle counters (diagnostic) or nullptr
 };
 
@@ -112,6 +115,8 @@ struct SepArgs {
     int64_t t0_fixed;
     int32_t n_fixed;
     SepOut* out;
+    const int32_t* idx;    // request index of work item z (nullptr: identity)
+    const int32_t* n_dev;  // number of work items on the device (nullptr: all launched)
 };
 
 struct AdmitArgs {
@@ -126,6 +131,26 @@ struct AdmitArgs {
     const int64_t* t0s;    // force mode: per plan t0
     const int32_t* counts; // force mode: per plan count
     const int64_t* offs;   // force mode: per plan offset into traj (points)
+    const int32_t* idx;    // request index of work item y (nullptr: identity)
+    const int32_t* n_dev;  // number of work items on the device (nullptr: all launched)
+};
+
+// Speculative batching: could request j's trajectory (as a stored plan) change request k's
+// plan or verdict? out[w*n + v] for work items w (k) and v (j), j < k in arrival order.
+struct InfluenceArgs {
+    const float* traj;          // [n_all][cap][3]
+    const RolloutOut* rout;     // n_points per request
+    const fmdp_request* reqs;
+    int32_t cap;
+    const int32_t* idx;         // request index of work item
+    const int32_t* n_dev;       // number of work items
+    float reach_base;           // max_k R_k + 1 m
+    float tau_absmax;
+    float dzmax;                // largest climb * dt
+    float sep_h, sep_v;
+    float dt;
+    uint8_t* out;               // [n][n]
+    int32_t n_cap;              // row stride of out
 };
 
 // What a separation check needs from a context (implemented in fmdp_api.cu).
@@ -147,6 +172,8 @@ cudaError_t launch_sepcheck(const SepArgs& a, int n_req, int max_points, cudaStr
 cudaError_t launch_sep_reset(SepOut* out, int n, cudaStream_t s);
 cudaError_t launch_admit(const AdmitArgs& a, int n_req, int max_points, cudaStream_t s);
 cudaError_t launch_fill_nan(float* p, size_t n, cudaStream_t s);
+cudaError_t launch_influence(const InfluenceArgs& a, int n_max, int max_points, cudaStream_t s);
+cudaError_t launch_sep_reset_idx(SepOut* out, const int32_t* idx, const int32_t* n_dev, int n_max, cudaStream_t s);
 
 // ---------------------------------------------------------------- device helpers
 

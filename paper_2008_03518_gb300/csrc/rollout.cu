@@ -157,7 +157,7 @@ struct StepState {
 
 // Shared-memory carve-up (identical on host and device).
 struct Layout {
-    size_t ring, bars, xbar, st, tabs, keys, sums, xkeys, xsums, xab, stat, aux, total;
+    size_t ring, bars, xbar, st, tabs, keys, sums, xkeys, xsums, xab, stat, aux, misc, total;
 };
 __host__ __device__ inline Layout make_layout(int chunk, int depth) {
     Layout L;
@@ -195,6 +195,8 @@ __host__ __device__ inline Layout make_layout(int chunk, int depth) {
     al(16);
     L.aux = o;   // valid, Delta, deck, key, class, log2|Q|, log2 scale: [7][32] words
     o += 7 * kMaxActions * sizeof(int);
+    L.misc = o;  // work-queue slot of the persistent batch mode
+    o += 16;
     L.total = (o + 127) & ~size_t(127);
     return L;
 }
@@ -407,14 +409,13 @@ __device__ __forceinline__ void fold_well(const Model& m, int w, float qx, float
 
 }  // namespace
 
-__global__ void __launch_bounds__(512, 1) rollout_kernel(const __grid_constant__ RolloutArgs a) {
-    extern __shared__ __align__(128) unsigned char smem[];
+// Plans request r with this CTA (and its cluster peers). Every thread of the cluster calls
+// it; all shared memory it uses is re-initialised, so a CTA can plan requests back to back.
+__device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, unsigned char* smem) {
     const Model& m = a.m;
     const int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31, warp = tid >> 5, NW = NT >> 5;
     const int cs = a.cs;
     const uint32_t rank = cs > 1 ? cluster_rank() : 0u;
-    const int r = blockIdx.x / cs;
-    if (r >= a.n_req) return;  // uniform over the cluster
     const fmdp_request req = a.reqs[r];
     const int A = m.A;
     const int chunk = a.chunk;
@@ -744,7 +745,7 @@ __global__ void __launch_bounds__(512, 1) rollout_kernel(const __grid_constant__
             const float* Z2 = Y2 + chunk;
             const int scan_len = v1 ? c_len : 0;
             const int nscan = NW - 2;
-            constexpr int U = 4;  // slots per lane per pass (independent chains)
+            constexpr int U = 2;  // slots per lane per pass (independent chains)
             for (int base = (warp - 2) * 32 * U; base < scan_len; base += nscan * 32 * U) {
                 float qx[U], qy[U], qz[U], vx[U], vy[U], vz[U];
                 bool near[U];
@@ -985,6 +986,29 @@ __global__ void __launch_bounds__(512, 1) rollout_kernel(const __grid_constant__
         for (int i = 0; i < 6; ++i)
             if (ph[i]) atomicAdd(&a.phase[i], ph[i]);
     if (cs > 1) cluster_barrier();  // peers may still address this CTA's shared memory
+}
+
+// One launch plans a set of requests. Without a work queue, cluster c plans request c.
+// With a work queue (batch mode, one CTA per request), resident CTAs pull request indices
+// from a device counter until none are left, which balances requests of uneven horizon.
+__global__ void __launch_bounds__(384, 1) rollout_kernel(const __grid_constant__ RolloutArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    if (a.queue == nullptr) {
+        const int r = blockIdx.x / a.cs;
+        if (r < a.n_req) plan_request(a, r, smem);  // uniform over the cluster
+        return;
+    }
+    const Layout L = make_layout(a.chunk, a.ring);
+    volatile int* next = reinterpret_cast<volatile int*>(smem + L.misc);
+    const int n = a.n_dev ? *a.n_dev : a.n_req;
+    for (;;) {
+        if (threadIdx.x == 0) *next = atomicAdd(a.queue, 1);
+        __syncthreads();
+        const int w = *next;
+        __syncthreads();
+        if (w >= n) break;
+        plan_request(a, a.idx ? a.idx[w] : w, smem);
+    }
 }
 
 size_t rollout_smem_bytes(int chunk, int depth) { return make_layout(chunk, depth).total; }

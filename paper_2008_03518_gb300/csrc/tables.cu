@@ -26,7 +26,8 @@ __device__ __forceinline__ int64_t ring_row(int64_t T, int32_t T_win) {
 }  // namespace
 
 __global__ void __launch_bounds__(kSepThreads) sepcheck_kernel(const __grid_constant__ SepArgs a) {
-    const int r = blockIdx.z;
+    if (a.n_dev && (int)blockIdx.z >= *a.n_dev) return;
+    const int r = a.idx ? a.idx[blockIdx.z] : (int)blockIdx.z;
     const int k = blockIdx.x;
     const int n = a.rout ? a.rout[r].n_points : a.n_fixed;
     if (k >= n) return;
@@ -115,8 +116,9 @@ __global__ void sep_reset_kernel(SepOut* out, int n) {
 // rollout status and separation check; an admitted trajectory is scattered into its
 // slot column. In force mode, known plans are stored unconditionally.
 __global__ void admit_kernel(const __grid_constant__ AdmitArgs a) {
-    const int r = blockIdx.y;
-    const int slot = a.slots[r];
+    if (a.n_dev && (int)blockIdx.y >= *a.n_dev) return;
+    const int r = a.idx ? a.idx[blockIdx.y] : (int)blockIdx.y;
+    const int slot = a.slots[r];  // per request (index mode) or per work item (pointer-offset mode)
     int n;
     int64_t t0;
     size_t off;
@@ -159,10 +161,15 @@ cudaError_t launch_sepcheck(const SepArgs& a, int n_req, int max_points, cudaStr
     for (int r0 = 0; r0 < n_req; r0 += 65535) {
         SepArgs b = a;
         const int nr = min(65535, n_req - r0);
-        b.traj = a.traj + (size_t)r0 * a.cap * 3;
-        if (a.rout) b.rout = a.rout + r0;
-        if (a.reqs) b.reqs = a.reqs + r0;
-        b.out = a.out + r0;
+        if (a.idx) {
+            b.idx = a.idx + r0;  // work items are mapped to requests; n_dev caps the total
+            if (r0 > 0 && a.n_dev) return cudaErrorInvalidValue;
+        } else {
+            b.traj = a.traj + (size_t)r0 * a.cap * 3;
+            if (a.rout) b.rout = a.rout + r0;
+            if (a.reqs) b.reqs = a.reqs + r0;
+            b.out = a.out + r0;
+        }
         sepcheck_kernel<<<dim3((unsigned)max_points, (unsigned)tiles, (unsigned)nr), kSepThreads, 0, s>>>(b);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -182,6 +189,13 @@ cudaError_t launch_admit(const AdmitArgs& a, int n_req, int max_points, cudaStre
     for (int r0 = 0; r0 < n_req; r0 += 65535) {
         AdmitArgs b = a;
         const int nr = min(65535, n_req - r0);
+        if (a.idx) {
+            if (r0 > 0) return cudaErrorInvalidValue;
+            admit_kernel<<<dim3((unsigned)bx, (unsigned)nr), 256, 0, s>>>(b);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+            continue;
+        }
         b.slots = a.slots + r0;
         if (a.force) {
             b.t0s = a.t0s + r0;
@@ -198,6 +212,79 @@ cudaError_t launch_admit(const AdmitArgs& a, int n_req, int max_points, cudaStre
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+// Influence of request j's speculative trajectory on request k's (j before k in arrival
+// order). k's plan could differ from its speculative one only if some state of k lies
+// within reach of a well of j one step later (|s_k(t) - p_j(t+1)| < max R + |tau|max |v_j|
+// + successor offset + margin), and its verdict only if its origin conflicts with j. A
+// conservative test: a false positive costs one more speculative round, never a result.
+__global__ void __launch_bounds__(128) influence_kernel(const __grid_constant__ InfluenceArgs a) {
+    const int n = *a.n_dev;
+    const int w = blockIdx.x, v = blockIdx.y;  // k = item w, j = item v
+    if (w >= n || v >= n) return;
+    const int k = a.idx[w], j = a.idx[v];
+    __shared__ int hit;
+    if (threadIdx.x == 0) hit = 0;
+    __syncthreads();
+    if (j < k) {
+        const int nk = a.rout[k].n_points, nj = a.rout[j].n_points;
+        const int64_t tk = a.reqs[k].depart_step, tj = a.reqs[j].depart_step;
+        const float rho = (float)(a.reqs[k].speed_mps * a.dt) + a.dzmax + 1.0f;
+        const float* pk = a.traj + (size_t)k * a.cap * 3;
+        const float* pj = a.traj + (size_t)j * a.cap * 3;
+        // origin conflict (verdict only): j at k's departure step
+        if (threadIdx.x == 0) {
+            const int64_t i0 = tk - tj;
+            if (i0 >= 0 && i0 < nj) {
+                const float dx = pk[0] - pj[3 * i0], dy = pk[1] - pj[3 * i0 + 1], dz = pk[2] - pj[3 * i0 + 2];
+                if (dx * dx + dy * dy < (a.sep_h + 1.f) * (a.sep_h + 1.f) && fabsf(dz) < a.sep_v + 1.f) hit = 1;
+            }
+        }
+        // wells of j at t+1 against k's state at t, for every state of k
+        for (int i = threadIdx.x; i < nk && !hit; i += blockDim.x) {
+            const int64_t t1 = tk + i + 1 - tj;  // index of j's sample at t+1
+            if (t1 < 0 || t1 >= nj) continue;
+            const float* q1 = pj + 3 * t1;
+            float vx = 0.f, vy = 0.f, vz = 0.f;
+            if (t1 + 1 < nj) {
+                vx = (q1[3] - q1[0]) / a.dt;
+                vy = (q1[4] - q1[1]) / a.dt;
+                vz = (q1[5] - q1[2]) / a.dt;
+            }
+            const float reach = a.reach_base + a.tau_absmax * sqrtf(vx * vx + vy * vy + vz * vz) + rho;
+            const float dx = pk[3 * i] - q1[0], dy = pk[3 * i + 1] - q1[1], dz = pk[3 * i + 2] - q1[2];
+            if (dx * dx + dy * dy + dz * dz < reach * reach) hit = 1;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) a.out[(size_t)w * a.n_cap + v] = (uint8_t)hit;
+}
+
+__global__ void sep_reset_idx_kernel(SepOut* out, const int32_t* idx, const int32_t* n_dev, int n_max) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= n_max || w >= *n_dev) return;
+    SepOut o;
+    o.first_conflict = INT_MAX;
+    o.first_terrain = INT_MAX;
+    o.conflicts = 0ull;
+    o.min_h_bits = 0x7f800000u;
+    o.min_v_bits = 0x7f800000u;
+    o.verdict = -1;
+    o.pad = 0;
+    out[idx[w]] = o;
+}
+
+cudaError_t launch_influence(const InfluenceArgs& a, int n_max, int /*max_points*/, cudaStream_t s) {
+    if (n_max <= 0) return cudaSuccess;
+    influence_kernel<<<dim3((unsigned)n_max, (unsigned)n_max), 128, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sep_reset_idx(SepOut* out, const int32_t* idx, const int32_t* n_dev, int n_max, cudaStream_t s) {
+    if (n_max <= 0) return cudaSuccess;
+    sep_reset_idx_kernel<<<(n_max + 255) / 256, 256, 0, s>>>(out, idx, n_dev, n_max);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_fill_nan(float* p, size_t n, cudaStream_t s) {
