@@ -89,7 +89,8 @@ typedef struct {
     int32_t lookahead_W;      /* lookahead window; only 1 is implemented */
     int32_t cluster_size;     /* CTAs cooperating on one rollout (0 = automatic) */
     int32_t threads_per_cta;  /* 0 = automatic; else a multiple of 32 in [128, 384] */
-    int32_t reserved;
+    int32_t batch_size;       /* fmdp_schedule_batch: requests per speculative batch
+                                 (0 = 256; at most 1024) */
 } fmdp_options;
 
 /* Fills *o with the defaults (max combine, Table 3 wells, goal 200, W = 1, automatic). */
@@ -136,7 +137,7 @@ typedef struct {
     double min_sep_h;            /* min horizontal distance to a plan within vert_m (inf if none) */
     double min_sep_v;            /* min |dz| to a plan within horiz_m (inf if none) */
     int32_t near_ties;           /* steps whose top-2 action values differed by < 1e-4 rel. */
-    int32_t replanned;           /* batch mode: 1 if the speculative plan was redone */
+    int32_t replanned;           /* batch mode: times the speculative plan was redone */
     float* xyz;                  /* caller-owned [horizon+1][3] or NULL: trajectory samples */
     uint8_t* actions;            /* caller-owned [horizon] or NULL: chosen action indices */
 } fmdp_result;
@@ -147,10 +148,16 @@ fmdp_status fmdp_schedule(fmdp_ctx* ctx, const fmdp_request* req, fmdp_result* r
  * fmdp_schedule. The whole sequence is enqueued on the device without host round trips. */
 fmdp_status fmdp_schedule_many(fmdp_ctx* ctx, const fmdp_request* reqs, int32_t n,
                                fmdp_result* res);
-/* Batched speculative FCFS: all n requests are planned concurrently against the table as
- * it stands, then re-checked in array order; a request whose plan could have been changed
- * by an earlier admitted request of the batch is re-planned. Results are identical to
- * fmdp_schedule_many. */
+/* Batched speculative FCFS (no counterpart in the paper, which plans requests one at a
+ * time, Sec. V): the requests are taken in batches of options.batch_size. Each batch is
+ * planned concurrently against the table as it stands (one persistent rollout launch
+ * whose clusters pull requests from a device queue, replayed as a CUDA graph), then
+ * re-checked in array order: a request is final when no request admitted before it in
+ * the batch can reach one of its successor states with a well or come within the
+ * separation minima of it; the first request that fails the test, and every later one
+ * that an admission may have changed, is planned again against the grown table. Results
+ * (verdicts, trajectories, plan ids) are identical to fmdp_schedule_many.
+ * On an error, requests finalised before it stay admitted. */
 fmdp_status fmdp_schedule_batch(fmdp_ctx* ctx, const fmdp_request* reqs, int32_t n,
                                 fmdp_result* res);
 
@@ -230,6 +237,11 @@ typedef struct {
                                  at the step barrier, control per-action work, control waiting
                                  for the scanners, exchange + argmax + advance, one scanner
                                  warp's cull + wells, producer issue + wait */
+    int64_t batch_waves;         /* speculative waves run by fmdp_schedule_batch */
+    int64_t batch_rollouts;      /* rollouts run by those waves (first plans and re-plans) */
+    int64_t batch_replans;       /* re-plans among them */
+    int64_t influence_launches;  /* influence-test launches (on = 1) */
+    double influence_ms;         /* their summed CUDA-event durations */
 } fmdp_stats;
 /* on = 1: per-kernel CUDA-event timing on the context's stream; on = 2: additionally
  * per-phase cycle counters inside the rollout kernel (diagnostic, slows it slightly);

@@ -110,6 +110,39 @@ struct SeqBuffers {
     }
 };
 
+// Device and pinned buffers of one speculative batch (fmdp_schedule_batch). The index
+// block holds four arrays of n_cap entries: work items to plan, the unresolved requests
+// in arrival order, the requests to store, and each request's slot.
+struct BatchBuffers {
+    int32_t n_cap = 0, cap = 0;
+    DevArray<fmdp_request> reqs;
+    DevArray<float> traj;
+    DevArray<uint8_t> acts;
+    DevArray<RolloutOut> rout;
+    DevArray<SepOut> sepo;
+    DevArray<int32_t> idx;   // [4][n_cap]
+    DevArray<int32_t> ctr;   // queue counter, n_todo, n_unresolved, n_store
+    DevArray<uint8_t> infl;  // [n_cap][n_cap]
+    PinnedArray<int32_t> h_idx, h_ctr;
+    PinnedArray<uint8_t> h_infl;
+    PinnedArray<RolloutOut> h_rout;
+    PinnedArray<SepOut> h_sep;
+    PinnedArray<float> h_traj;
+    PinnedArray<uint8_t> h_acts;
+    void release() {
+        reqs.release(); traj.release(); acts.release(); rout.release(); sepo.release();
+        idx.release(); ctr.release(); infl.release();
+        h_idx.release(); h_ctr.release(); h_infl.release(); h_rout.release(); h_sep.release();
+        h_traj.release(); h_acts.release();
+    }
+};
+
+// One instantiated wave graph and the launch parameters it was captured with.
+struct WaveGraph {
+    std::vector<int64_t> key;
+    cudaGraphExec_t exec = nullptr;
+};
+
 thread_local std::string g_create_error;
 
 }  // namespace
@@ -156,6 +189,11 @@ struct fmdp_ctx {
     PinnedArray<uint8_t> h_acts;
     PinnedArray<RolloutOut> h_rout;
     PinnedArray<SepOut> h_sep;
+
+    // speculative batches
+    BatchBuffers bat;
+    std::vector<WaveGraph> graphs;  // most recent first
+    bool use_graphs = true;
 
     // staged (device-resident) requests
     std::vector<fmdp_request> staged;
@@ -270,13 +308,13 @@ struct KernelTimer {
     int kind;
     cudaEvent_t a = nullptr;
     KernelTimer(fmdp_ctx* c_, int k) : c(c_), kind(k) {
-        if (c->profiling) {
+        if (c->profiling && kind >= 0) {
             a = next_event(c);
             CK(cudaEventRecord(a, c->stream));
         }
     }
     void stop() {
-        if (c->profiling) {
+        if (c->profiling && kind >= 0) {
             cudaEvent_t b = next_event(c);
             CK(cudaEventRecord(b, c->stream));
             c->pending.push_back({kind, a, b});
@@ -289,7 +327,8 @@ void collect_timers(fmdp_ctx* c) {
         CK(cudaEventElapsedTime(&ms, p.a, p.b));
         if (p.kind == 0) { c->stats.rollout_ms += ms; c->stats.rollout_launches++; }
         else if (p.kind == 1) { c->stats.sepcheck_ms += ms; c->stats.sepcheck_launches++; }
-        else { c->stats.admit_ms += ms; c->stats.admit_launches++; }
+        else if (p.kind == 2) { c->stats.admit_ms += ms; c->stats.admit_launches++; }
+        else { c->stats.influence_ms += ms; c->stats.influence_launches++; }
     }
     c->pending.clear();
     c->ev_next = 0;
@@ -302,6 +341,21 @@ struct Geometry {
     size_t smem;
 };
 
+// Partition g.S_scan slots over clusters of cs CTAs: the deepest ring (8, else 4 slices)
+// whose partition fits one CTA's shared memory. False when neither fits.
+bool fit_geometry(fmdp_ctx* c, Geometry& g, int cs) {
+    g.cs = cs;
+    g.chunk = std::max(32, round_up((g.S_scan + cs - 1) / cs, 32));
+    g.threads = c->opt.threads_per_cta > 0 ? c->opt.threads_per_cta : (g.chunk > 256 ? 384 : 256);
+    for (int depth : {8, 4}) {
+        g.ring = depth;
+        g.smem = rollout_smem_bytes(g.chunk, depth);
+        if ((int)g.smem <= c->max_smem) return true;
+    }
+    return false;
+}
+
+// Latency geometry (one request at a time): about 1024 slots per CTA.
 Geometry geometry(fmdp_ctx* c, int32_t S_hw) {
     Geometry g;
     g.S_scan = round_up(std::max(S_hw, 0), 32);
@@ -312,18 +366,7 @@ Geometry geometry(fmdp_ctx* c, int32_t S_hw) {
         while (cs < want && cs < kMaxCluster) cs *= 2;
     }
     cs = std::max(1, std::min(cs, kMaxCluster));
-    // deepest ring (8, else 4 slices) whose partition fits one CTA's shared memory
-    auto fit = [&](int cs_) {
-        g.cs = cs_;
-        g.chunk = std::max(32, round_up((g.S_scan + cs_ - 1) / cs_, 32));
-        g.threads = c->opt.threads_per_cta > 0 ? c->opt.threads_per_cta : (g.chunk > 256 ? 384 : 256);
-        for (int depth : {8, 4}) {
-            g.ring = depth;
-            g.smem = rollout_smem_bytes(g.chunk, depth);
-            if ((int)g.smem <= c->max_smem) return true;
-        }
-        return false;
-    };
+    auto fit = [&](int cs_) { return fit_geometry(c, g, cs_); };
     while (!fit(cs) && cs < kMaxCluster) cs *= 2;  // partition too large: spread it wider
     require((int)g.smem <= c->max_smem, FMDP_ERR_ARG, "plan table partition exceeds shared memory");
     // the cluster must fit on one GPC: halve it until the hardware can place one
@@ -531,6 +574,378 @@ int32_t run_fcfs(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_result* 
     return admitted;
 }
 
+// ------------------------------------------------------------------ speculative batches
+//
+// A batch is planned in waves. Every wave plans its work items concurrently against the
+// table as it stands (one persistent rollout launch pulling items from a queue), checks
+// their separation, and tests every pair of unresolved requests for influence. The host
+// then walks the unresolved requests in arrival order: a request is final when no request
+// admitted earlier in the same walk influences it, and the walk stops at the first one
+// that is influenced. Admitted requests are stored at the start of the next wave; a
+// request left unresolved is planned again only if one of them influences it, otherwise
+// its plan stays exact against the grown table. Each wave finalises at least one request.
+
+constexpr int32_t kBatchDefault = 256;
+constexpr int32_t kBatchMax = 1024;
+constexpr int kSepPointBlocks = 64;  // sep_check blocks per request along its trajectory
+
+// Batch geometry: the narrowest cluster whose partition fits one CTA's shared memory, so
+// that as many rollouts as possible run side by side.
+Geometry geometry_batch(fmdp_ctx* c, int32_t S) {
+    Geometry g;
+    g.S_scan = std::min(round_up(std::max(S, 0), 32), c->S_pad);
+    int cs = c->opt.cluster_size > 0 ? c->opt.cluster_size : 1;
+    while (!(fit_geometry(c, g, cs) && rollout_max_active_clusters(cs, g.threads, g.smem) >= 1)) {
+        require(cs < kMaxCluster, FMDP_ERR_ARG, "plan table partition exceeds shared memory");
+        cs *= 2;
+    }
+    c->last_cs = g.cs;
+    c->last_threads = g.threads;
+    c->last_chunk = g.chunk;
+    return g;
+}
+
+int32_t host_verdict(const RolloutOut& ro, const SepOut& so) {  // the admission kernel's rule
+    if (ro.status != kStatusCaptured) return ro.status;
+    if (so.first_conflict != INT_MAX) return FMDP_REJ_CONFLICT;
+    if (so.first_terrain != INT_MAX) return FMDP_REJ_TERRAIN;
+    return FMDP_ADMITTED;
+}
+
+// One wave on the context's stream: store the requests admitted by the previous walk,
+// plan the work items, check their separation, test influence among the unresolved
+// requests, and bring rollout, separation and influence results back to pinned memory.
+// Every count is read on the device, so the sequence can be captured once and replayed.
+void enqueue_wave(fmdp_ctx* c, const Geometry& g, int n_clusters, BatchBuffers& B, bool timed) {
+    const int32_t n_cap = B.n_cap, cap = B.cap;
+    cudaStream_t s = c->stream;
+    int32_t* todo = B.idx.p;
+    int32_t* unres = todo + n_cap;
+    int32_t* store = unres + n_cap;
+    int32_t* slots = store + n_cap;
+    const TableView tv = table_view(c);
+    CK(cudaMemcpyAsync(B.idx.p, B.h_idx.p, 4 * (size_t)n_cap * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(B.ctr.p, B.h_ctr.p, 4 * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    {
+        AdmitArgs aa{};
+        aa.tab = tv;
+        aa.cap = cap;
+        aa.traj = B.traj.p;
+        aa.rout = B.rout.p;
+        aa.reqs = B.reqs.p;
+        aa.slots = slots;
+        aa.sep = B.sepo.p;
+        aa.force = 0;
+        aa.idx = store;
+        aa.n_dev = B.ctr.p + 3;
+        KernelTimer t(c, timed ? 2 : -1);
+        CK(launch_admit(aa, n_cap, cap, s));
+        t.stop();
+    }
+    CK(launch_sep_reset_idx(B.sepo.p, todo, B.ctr.p + 1, n_cap, s));
+    {
+        RolloutArgs ra{};
+        ra.m = c->model;
+        ra.tab = tv;
+        ra.S_scan = g.S_scan;
+        ra.chunk = g.chunk;
+        ra.cs = g.cs;
+        ra.ring = g.ring;
+        ra.cap = cap;
+        ra.reqs = B.reqs.p;
+        ra.n_req = n_cap;
+        ra.traj = B.traj.p;
+        ra.acts = B.acts.p;
+        ra.out = B.rout.p;
+        ra.err = c->err;
+        ra.phase = (timed && c->phase_timing) ? c->phase.p : nullptr;
+        ra.queue = B.ctr.p;
+        ra.idx = todo;
+        ra.n_dev = B.ctr.p + 1;
+        KernelTimer t(c, timed ? 0 : -1);
+        CK(launch_rollout(ra, g.threads, g.smem, s, n_clusters));
+        t.stop();
+    }
+    {
+        SepArgs sa{};
+        sa.m = c->model;
+        sa.tab = tv;
+        sa.S_scan = g.S_scan;
+        sa.cap = cap;
+        sa.traj = B.traj.p;
+        sa.rout = B.rout.p;
+        sa.reqs = B.reqs.p;
+        sa.out = B.sepo.p;
+        sa.idx = todo;
+        sa.n_dev = B.ctr.p + 1;
+        KernelTimer t(c, timed ? 1 : -1);
+        CK(launch_sepcheck(sa, n_cap, kSepPointBlocks, s));
+        t.stop();
+    }
+    {
+        InfluenceArgs ia{};
+        ia.traj = B.traj.p;
+        ia.rout = B.rout.p;
+        ia.reqs = B.reqs.p;
+        ia.cap = cap;
+        ia.idx = unres;
+        ia.n_dev = B.ctr.p + 2;
+        ia.reach_base = c->model.reach_base;
+        ia.tau_absmax = c->model.tau_absmax;
+        float dzmax = 0.f;
+        for (int i = 0; i < c->model.A; ++i) dzmax = std::max(dzmax, (float)std::fabs(c->model.climb[i] * c->model.dt));
+        ia.dzmax = dzmax;
+        ia.sep_h = (float)c->sep.horiz_m;
+        ia.sep_v = (float)c->sep.vert_m;
+        ia.dt = (float)c->model.dt;
+        ia.out = B.infl.p;
+        ia.n_cap = n_cap;
+        KernelTimer t(c, timed ? 3 : -1);
+        CK(launch_influence(ia, n_cap, cap, s));
+        t.stop();
+    }
+    CK(cudaMemcpyAsync(B.h_rout.p, B.rout.p, n_cap * sizeof(RolloutOut), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(B.h_sep.p, B.sepo.p, n_cap * sizeof(SepOut), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(B.h_infl.p, B.infl.p, (size_t)n_cap * n_cap, cudaMemcpyDeviceToHost, s));
+}
+
+// The wave sequence as an instantiated CUDA graph, captured on a private stream the first
+// time these launch parameters occur and replayed on the context's stream afterwards.
+cudaGraphExec_t wave_graph(fmdp_ctx* c, const Geometry& g, int n_clusters, BatchBuffers& B) {
+    const TableView tv = table_view(c);
+    const std::vector<int64_t> key = {g.S_scan, g.cs, g.threads, g.chunk, g.ring, (int64_t)g.smem, n_clusters,
+                                      B.n_cap, B.cap, (int64_t)(uintptr_t)B.idx.p, (int64_t)(uintptr_t)B.traj.p,
+                                      (int64_t)(uintptr_t)B.reqs.p, (int64_t)(uintptr_t)B.h_idx.p,
+                                      (int64_t)(uintptr_t)B.h_infl.p, (int64_t)(uintptr_t)tv.X, tv.t_base};
+    for (size_t i = 0; i < c->graphs.size(); ++i)
+        if (c->graphs[i].key == key) {
+            std::swap(c->graphs[i], c->graphs[0]);
+            return c->graphs[0].exec;
+        }
+    cudaStream_t cap_stream = nullptr;
+    CK(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
+    cudaStream_t user = c->stream;
+    c->stream = cap_stream;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        try {
+            enqueue_wave(c, g, n_clusters, B, false);
+        } catch (...) {
+            cudaStreamEndCapture(cap_stream, &graph);
+            if (graph) cudaGraphDestroy(graph);
+            c->stream = user;
+            cudaStreamDestroy(cap_stream);
+            throw;
+        }
+        e = cudaStreamEndCapture(cap_stream, &graph);
+    }
+    c->stream = user;
+    cudaStreamDestroy(cap_stream);
+    CK(e);
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    CK(e);
+    c->graphs.insert(c->graphs.begin(), WaveGraph{key, exec});
+    while (c->graphs.size() > 4) {
+        cudaGraphExecDestroy(c->graphs.back().exec);
+        c->graphs.pop_back();
+    }
+    return exec;
+}
+
+// Plans one batch (n <= kBatchMax requests, already validated) in FCFS order with exact
+// sequential results. Returns the number admitted.
+int32_t run_batch_chunk(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_result* res) {
+    BatchBuffers& B = c->bat;
+    int32_t cap = 1;
+    for (int32_t i = 0; i < n; ++i) cap = std::max(cap, reqs[i].horizon + 1);
+    // buffer shapes in buckets, so that graphs are reused from batch to batch
+    B.n_cap = std::max(B.n_cap, round_up(n, 64));
+    B.cap = std::max(B.cap, round_up(cap, 256));
+    const int32_t n_cap = B.n_cap;
+    B.reqs.ensure(n_cap);
+    B.traj.ensure((size_t)n_cap * B.cap * 3);
+    B.acts.ensure((size_t)n_cap * B.cap);
+    B.rout.ensure(n_cap);
+    B.sepo.ensure(n_cap);
+    B.idx.ensure(4 * (size_t)n_cap);
+    B.ctr.ensure(4);
+    B.infl.ensure((size_t)n_cap * n_cap);
+    B.h_idx.ensure(4 * (size_t)n_cap);
+    B.h_ctr.ensure(4);
+    B.h_infl.ensure((size_t)n_cap * n_cap);
+    B.h_rout.ensure(n_cap);
+    B.h_sep.ensure(n_cap);
+
+    // the batch admits at most n plans, into the lowest free slots: scan up to that bound
+    require((size_t)n <= c->book.free_slots.size(), FMDP_ERR_FULL, "not enough free plan slots for the batch");
+    int32_t bound = c->book.S_hw;
+    {
+        auto it = c->book.free_slots.begin();
+        for (int32_t i = 0; i < n; ++i, ++it) bound = std::max(bound, *it + 1);
+    }
+    const Geometry g = geometry_batch(c, round_up(bound, 512));
+    const int n_clusters = std::max(1, std::min(n, rollout_max_active_clusters(g.cs, g.threads, g.smem)));
+    const bool graphs = c->use_graphs && !c->profiling;
+
+    CK(cudaMemcpyAsync(B.reqs.p, reqs, n * sizeof(fmdp_request), cudaMemcpyHostToDevice, c->stream));
+    std::vector<int32_t> U(n), todo(n), store, adm_all, slot_of(n, -1), replans(n, 0), verdict(n, -1);
+    std::vector<uint64_t> ids(n, 0);
+    std::vector<RolloutOut> fin_ro(n);
+    std::vector<SepOut> fin_so(n);
+    for (int32_t i = 0; i < n; ++i) U[i] = todo[i] = i;
+    std::vector<std::pair<uint64_t, int32_t>> pending;  // admitted, not yet stored: (id, slot)
+    int32_t admitted = 0;
+    try {
+        while (!U.empty()) {
+            int32_t* hi = B.h_idx.p;
+            std::copy(todo.begin(), todo.end(), hi);
+            std::copy(U.begin(), U.end(), hi + n_cap);
+            std::copy(store.begin(), store.end(), hi + 2 * n_cap);
+            for (int32_t i = 0; i < n; ++i) hi[3 * n_cap + i] = slot_of[i];
+            B.h_ctr.p[0] = 0;
+            B.h_ctr.p[1] = (int32_t)todo.size();
+            B.h_ctr.p[2] = (int32_t)U.size();
+            B.h_ctr.p[3] = (int32_t)store.size();
+            if (graphs) CK(cudaGraphLaunch(wave_graph(c, g, n_clusters, B), c->stream));
+            else enqueue_wave(c, g, n_clusters, B, true);
+            CK(cudaStreamSynchronize(c->stream));
+            if (c->profiling) collect_timers(c);
+            require(read_error_word(c) == 0, FMDP_ERR_TIMEOUT, "a bounded device wait expired during a rollout");
+            pending.clear();  // the previous walk's admissions are now in the table
+            c->stats.batch_waves++;
+            for (int32_t r : todo) {
+                const RolloutOut& ro = B.h_rout.p[r];
+                c->stats.rollout_steps += ro.steps;
+                c->stats.slots_scanned += (int64_t)ro.steps * g.S_scan;
+                c->stats.sep_pairs += (int64_t)ro.n_points * g.S_scan;
+                c->stats.batch_rollouts++;
+            }
+            // walk the unresolved requests in arrival order
+            store.clear();
+            std::vector<size_t> adm_pos;  // positions in U admitted by this walk
+            size_t pos = 0;
+            for (; pos < U.size(); ++pos) {
+                const uint8_t* row = B.h_infl.p + pos * n_cap;
+                bool hit = false;
+                for (size_t v : adm_pos) hit = hit || row[v];
+                if (hit) break;
+                const int32_t k = U[pos];
+                fin_ro[k] = B.h_rout.p[k];
+                fin_so[k] = B.h_sep.p[k];
+                verdict[k] = host_verdict(fin_ro[k], fin_so[k]);
+                if (verdict[k] == FMDP_ADMITTED) {
+                    const int32_t slot = take_slot(c);
+                    require(slot < g.S_scan, FMDP_ERR_ARG, "internal: batch slot beyond the scanned range");
+                    const uint64_t id = c->book.next_id++;
+                    c->book.plans[id] = PlanMeta{slot, reqs[k].depart_step, fin_ro[k].n_points};
+                    c->book.S_hw = std::max(c->book.S_hw, slot + 1);
+                    pending.push_back({id, slot});
+                    slot_of[k] = slot;
+                    ids[k] = id;
+                    store.push_back(k);
+                    adm_all.push_back(k);
+                    adm_pos.push_back(pos);
+                    ++admitted;
+                }
+            }
+            // what stays unresolved is planned again only where an admission may change it
+            std::vector<int32_t> nU, ntodo;
+            for (size_t w = pos; w < U.size(); ++w) {
+                const uint8_t* row = B.h_infl.p + w * n_cap;
+                bool hit = false;
+                for (size_t v : adm_pos) hit = hit || row[v];
+                nU.push_back(U[w]);
+                if (hit) {
+                    ntodo.push_back(U[w]);
+                    ++replans[U[w]];
+                    c->stats.batch_replans++;
+                }
+            }
+            U.swap(nU);
+            todo.swap(ntodo);
+        }
+        // epilogue: store the last walk's admissions, then fold the batch's admissions into
+        // every request's minimum separations
+        std::copy(adm_all.begin(), adm_all.end(), B.h_idx.p);
+        std::copy(store.begin(), store.end(), B.h_idx.p + 2 * n_cap);
+        for (int32_t i = 0; i < n; ++i) B.h_idx.p[3 * n_cap + i] = slot_of[i];
+        B.h_ctr.p[3] = (int32_t)store.size();
+        CK(cudaMemcpyAsync(B.idx.p, B.h_idx.p, 4 * (size_t)n_cap * sizeof(int32_t), cudaMemcpyHostToDevice,
+                           c->stream));
+        CK(cudaMemcpyAsync(B.ctr.p, B.h_ctr.p, 4 * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+        if (!store.empty()) {
+            AdmitArgs aa{};
+            aa.tab = table_view(c);
+            aa.cap = B.cap;
+            aa.traj = B.traj.p;
+            aa.rout = B.rout.p;
+            aa.reqs = B.reqs.p;
+            aa.slots = B.idx.p + 3 * n_cap;
+            aa.sep = B.sepo.p;
+            aa.idx = B.idx.p + 2 * n_cap;
+            aa.n_dev = B.ctr.p + 3;
+            KernelTimer t(c, 2);
+            CK(launch_admit(aa, n_cap, B.cap, c->stream));
+            t.stop();
+        }
+        MinSepArgs ma{};
+        ma.traj = B.traj.p;
+        ma.rout = B.rout.p;
+        ma.reqs = B.reqs.p;
+        ma.cap = B.cap;
+        ma.n = n;
+        ma.adm = B.idx.p;
+        ma.n_adm = (int32_t)adm_all.size();
+        ma.sep_h = c->sep.horiz_m;
+        ma.sep_v = c->sep.vert_m;
+        ma.out = B.sepo.p;
+        CK(launch_batch_minsep(ma, c->stream));
+        CK(cudaMemcpyAsync(B.h_sep.p, B.sepo.p, n * sizeof(SepOut), cudaMemcpyDeviceToHost, c->stream));
+        bool want_points = false;
+        for (int32_t i = 0; res && i < n; ++i) want_points = want_points || res[i].xyz || res[i].actions;
+        if (want_points) {
+            B.h_traj.ensure((size_t)n * B.cap * 3);
+            B.h_acts.ensure((size_t)n * B.cap);
+            CK(cudaMemcpyAsync(B.h_traj.p, B.traj.p, (size_t)n * B.cap * 3 * sizeof(float), cudaMemcpyDeviceToHost,
+                               c->stream));
+            CK(cudaMemcpyAsync(B.h_acts.p, B.acts.p, (size_t)n * B.cap, cudaMemcpyDeviceToHost, c->stream));
+        }
+        CK(cudaStreamSynchronize(c->stream));
+        if (c->profiling) collect_timers(c);
+        pending.clear();
+    } catch (...) {
+        for (auto& pr : pending) {  // admissions whose plans never reached the table
+            c->book.plans.erase(pr.first);
+            c->book.free_slots.insert(pr.second);
+        }
+        recompute_hw(c);
+        throw;
+    }
+    for (int32_t i = 0; res && i < n; ++i) {
+        fmdp_result* o = res + i;
+        SepOut so = B.h_sep.p[i];  // the final plan's report with the batch's admissions folded in
+        so.verdict = verdict[i];
+        fill_result(fin_ro[i], so, o);
+        o->plan_id = ids[i];
+        o->replanned = replans[i];
+        const int32_t np = fin_ro[i].n_points;
+        if (o->xyz) std::memcpy(o->xyz, B.h_traj.p + (size_t)i * B.cap * 3, (size_t)np * 3 * sizeof(float));
+        if (o->actions && np > 1) std::memcpy(o->actions, B.h_acts.p + (size_t)i * B.cap, (size_t)(np - 1));
+    }
+    return admitted;
+}
+
+int32_t run_batch(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_result* res) {
+    const int32_t bs = c->opt.batch_size > 0 ? c->opt.batch_size : kBatchDefault;
+    int32_t admitted = 0;
+    for (int32_t b0 = 0; b0 < n; b0 += bs)
+        admitted += run_batch_chunk(c, reqs + b0, std::min(bs, n - b0), res ? res + b0 : nullptr);
+    return admitted;
+}
+
 void store_plans(fmdp_ctx* c, int32_t n_plans, const int64_t* t0s, const int32_t* counts, const float* xyz,
                  uint64_t* ids_out) {
     require(n_plans >= 0, FMDP_ERR_ARG, "n_plans < 0");
@@ -617,7 +1032,9 @@ void destroy_ctx(fmdp_ctx* c) {
     if (c->hm) cudaFree(c->hm);
     if (c->statics) cudaFree(c->statics);
     if (c->err) cudaFree(c->err);
-    c->seq.release(); c->stg.release();
+    c->seq.release(); c->stg.release(); c->bat.release();
+    for (auto& g : c->graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
     c->reqs.release(); c->traj.release(); c->acts.release(); c->rout.release(); c->sepo.release();
     c->slots.release(); c->t0s.release(); c->offs.release(); c->counts.release();
     c->q_trace.release(); c->st_trace.release(); c->hd_trace.release(); c->tie_trace.release();
@@ -717,6 +1134,7 @@ fmdp_status fmdp_create(const fmdp_airspace* air, double gamma, const fmdp_actio
         require(o.threads_per_cta == 0 || (o.threads_per_cta >= 128 && o.threads_per_cta <= 384 &&
                                            o.threads_per_cta % 32 == 0),
                 FMDP_ERR_ARG, "threads per CTA: 0 or a multiple of 32 in [128, 384]");
+        require(o.batch_size >= 0 && o.batch_size <= kBatchMax, FMDP_ERR_ARG, "batch size 0..1024");
         std::vector<fmdp_well> wells;
         if (o.wells && o.n_wells > 0) {
             wells.assign(o.wells, o.wells + o.n_wells);
@@ -892,8 +1310,12 @@ fmdp_status fmdp_fetch_staged(fmdp_ctx* c, fmdp_result* res, int32_t n) {
 }
 
 fmdp_status fmdp_schedule_batch(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_result* res) {
-    // first version: the exact sequential FCFS chain (speculative batching is layered on it)
-    return fmdp_schedule_many(c, reqs, n, res);
+    if (!c) return FMDP_ERR_ARG;
+    return guard(c, [&] {
+        require(n >= 0 && (n == 0 || (reqs && res)), FMDP_ERR_ARG, "null requests or results");
+        for (int32_t i = 0; i < n; ++i) check_request(c, reqs[i]);
+        run_batch(c, reqs, n, res);
+    });
 }
 
 fmdp_status fmdp_query_plans(fmdp_ctx* c, int64_t t_begin, int64_t t_end, uint64_t* ids, int32_t cap,

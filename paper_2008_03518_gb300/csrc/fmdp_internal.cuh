@@ -164,7 +164,9 @@ void ctx_sep_view(fmdp_ctx* ctx, SepView* v);
 void ctx_set_error(fmdp_ctx* ctx, const char* msg);
 
 // kernel launchers (rollout.cu / tables.cu)
-cudaError_t launch_rollout(const RolloutArgs& a, int threads, size_t smem, cudaStream_t s);
+// n_clusters > 0: persistent launch of that many clusters (work-queue mode), else one
+// cluster per request.
+cudaError_t launch_rollout(const RolloutArgs& a, int threads, size_t smem, cudaStream_t s, int n_clusters = 0);
 size_t rollout_smem_bytes(int chunk, int depth);
 cudaError_t prepare_rollout_kernel(size_t smem);
 int rollout_max_active_clusters(int cs, int threads, size_t smem);
@@ -172,6 +174,18 @@ cudaError_t launch_sepcheck(const SepArgs& a, int n_req, int max_points, cudaStr
 cudaError_t launch_sep_reset(SepOut* out, int n, cudaStream_t s);
 cudaError_t launch_admit(const AdmitArgs& a, int n_req, int max_points, cudaStream_t s);
 cudaError_t launch_fill_nan(float* p, size_t n, cudaStream_t s);
+// Batch epilogue: minimum separations to the batch's own admissions.
+struct MinSepArgs {
+    const float* traj;       // [n][cap][3]
+    const RolloutOut* rout;
+    const fmdp_request* reqs;
+    int32_t cap, n;
+    const int32_t* adm;      // admitted request indices, ascending
+    int32_t n_adm;
+    double sep_h, sep_v;
+    SepOut* out;             // [n]
+};
+cudaError_t launch_batch_minsep(const MinSepArgs& a, cudaStream_t s);
 cudaError_t launch_influence(const InfluenceArgs& a, int n_max, int max_points, cudaStream_t s);
 cudaError_t launch_sep_reset_idx(SepOut* out, const int32_t* idx, const int32_t* n_dev, int n_max, cudaStream_t s);
 

@@ -106,6 +106,14 @@ __device__ __forceinline__ uint32_t dsmem_addr(uint32_t local, uint32_t rank) {
     asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
     return r;
 }
+__device__ __forceinline__ int ld_cluster_s32(uint32_t addr) {
+    int v;
+    asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+    return v;
+}
+__device__ __forceinline__ void mbar_inval(uint64_t* bar) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 __device__ __forceinline__ void st_async_s32(uint32_t addr, int v, uint32_t bar) {
     asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.s32 [%0], %1, [%2];" ::"r"(addr), "r"(v),
                  "r"(bar)
@@ -300,11 +308,6 @@ __device__ __forceinline__ void goal_log_split(float Ghx, float Ghy, float Ghz, 
 }
 
 // Clearance penalty decided in FP64 at an exact successor (band around the threshold).
-__device__ __noinline__ float deck_exact_at(const Model& m, double X, double Y, double Z) {
-    const double c64 = __dsub_rn(Z, terrain64(m, X, Y));
-    return c64 < m.clearance ? (float)__dsub_rn(m.deck, c64) : 0.f;
-}
-
 // Static negative peaks (restricted volumes / terrain wells) for one action.
 __device__ __noinline__ void fold_statics(const Model& m, const StepState* st, const float* sch, const float* scl,
                                           float shx, float shy, float shz, float slx, float sly, float slz,
@@ -985,12 +988,18 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
     if (timing && (tid == 0 || tid == NT - 32 || producer))
         for (int i = 0; i < 6; ++i)
             if (ph[i]) atomicAdd(&a.phase[i], ph[i]);
-    if (cs > 1) cluster_barrier();  // peers may still address this CTA's shared memory
+    if (cs > 1) cluster_barrier(); else __syncthreads();  // peers may still address this CTA's shared memory
+    if (a.queue && tid == 0) {  // the next request of this CTA initialises them again
+        for (int e = 0; e < kRingDepth; ++e) mbar_inval(&bars[e]);
+        mbar_inval(&xbar[0]);
+        mbar_inval(&xbar[1]);
+    }
 }
 
 // One launch plans a set of requests. Without a work queue, cluster c plans request c.
-// With a work queue (batch mode, one CTA per request), resident CTAs pull request indices
-// from a device counter until none are left, which balances requests of uneven horizon.
+// With a work queue (batch mode), each resident cluster pulls work items from a device
+// counter until none are left, which balances requests of uneven horizon: the lead CTA
+// takes the item and its peers read it from the lead's shared memory.
 __global__ void __launch_bounds__(384, 1) rollout_kernel(const __grid_constant__ RolloutArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     if (a.queue == nullptr) {
@@ -999,13 +1008,22 @@ __global__ void __launch_bounds__(384, 1) rollout_kernel(const __grid_constant__
         return;
     }
     const Layout L = make_layout(a.chunk, a.ring);
-    volatile int* next = reinterpret_cast<volatile int*>(smem + L.misc);
+    int* next = reinterpret_cast<int*>(smem + L.misc);
     const int n = a.n_dev ? *a.n_dev : a.n_req;
+    const bool lead = a.cs == 1 || cluster_rank() == 0;
     for (;;) {
-        if (threadIdx.x == 0) *next = atomicAdd(a.queue, 1);
-        __syncthreads();
-        const int w = *next;
-        __syncthreads();
+        if (threadIdx.x == 0 && lead)  // after a device error, stop taking work
+            *next = *reinterpret_cast<volatile int32_t*>(a.err) != 0 ? n : atomicAdd(a.queue, 1);
+        int w;
+        if (a.cs > 1) {
+            cluster_barrier();
+            w = ld_cluster_s32(dsmem_addr(smem_u32(next), 0));
+            cluster_barrier();  // every CTA has read the item before the lead takes the next
+        } else {
+            __syncthreads();
+            w = *reinterpret_cast<volatile int*>(next);
+            __syncthreads();
+        }
         if (w >= n) break;
         plan_request(a, a.idx ? a.idx[w] : w, smem);
     }
@@ -1039,9 +1057,9 @@ int rollout_max_active_clusters(int cs, int threads, size_t smem) {
     return n;
 }
 
-cudaError_t launch_rollout(const RolloutArgs& a, int threads, size_t smem, cudaStream_t s) {
+cudaError_t launch_rollout(const RolloutArgs& a, int threads, size_t smem, cudaStream_t s, int n_clusters) {
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(a.n_req * a.cs), 1, 1);
+    cfg.gridDim = dim3((unsigned)((n_clusters > 0 ? n_clusters : a.n_req) * a.cs), 1, 1);
     cfg.blockDim = dim3((unsigned)threads, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;

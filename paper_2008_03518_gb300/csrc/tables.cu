@@ -23,36 +23,65 @@ __device__ __forceinline__ int64_t ring_row(int64_t T, int32_t T_win) {
     return r < 0 ? r + T_win : r;
 }
 
+// Separation minima of one sample pair with explicit rounding (no contraction), so that
+// every kernel that measures the same pair gets the same bits. Thresholds in the band
+// around H^2 and V are decided again in FP64 from the same fp32 inputs.
+struct SepConsts {
+    float H2, Vm, hband;
+    double H2d, Vd;
+};
+__device__ __forceinline__ SepConsts sep_consts(double sep_h, double sep_v) {
+    SepConsts k;
+    const float H = (float)sep_h;
+    k.H2 = __fmul_rn(H, H);
+    k.Vm = (float)sep_v;
+    k.hband = 2.0f * H * kSepBand + kSepBand * kSepBand;
+    k.H2d = __dmul_rn(sep_h, sep_h);
+    k.Vd = sep_v;
+    return k;
+}
+// h2: squared horizontal distance, dz: |vertical distance|; hin / vin: inside the minima
+__device__ __forceinline__ void sep_pair(const SepConsts& k, float px, float py, float pz, float qx, float qy,
+                                         float qz, float& h2, float& dz, bool& hin, bool& vin) {
+    const float dx = __fsub_rn(px, qx), dy = __fsub_rn(py, qy);
+    dz = fabsf(__fsub_rn(pz, qz));
+    h2 = __fmaf_rn(dx, dx, __fmul_rn(dy, dy));
+    hin = h2 < k.H2;  // NaN (empty slot): false
+    vin = dz < k.Vm;
+    if (fabsf(h2 - k.H2) < k.hband) {
+        const double ex = __dsub_rn((double)px, (double)qx);
+        const double ey = __dsub_rn((double)py, (double)qy);
+        hin = __dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)) < k.H2d;
+    }
+    if (fabsf(dz - k.Vm) < kSepBand) vin = fabs(__dsub_rn((double)pz, (double)qz)) < k.Vd;
+}
+
 }  // namespace
 
+// Grid: x strides over the trajectory's samples (one block per sample when gridDim.x covers
+// them all), y over 1024-slot tiles, z over requests.
 __global__ void __launch_bounds__(kSepThreads) sepcheck_kernel(const __grid_constant__ SepArgs a) {
     if (a.n_dev && (int)blockIdx.z >= *a.n_dev) return;
     const int r = a.idx ? a.idx[blockIdx.z] : (int)blockIdx.z;
-    const int k = blockIdx.x;
     const int n = a.rout ? a.rout[r].n_points : a.n_fixed;
-    if (k >= n) return;
     const int64_t t0 = a.reqs ? a.reqs[r].depart_step : a.t0_fixed;
-    const float* p = a.traj + ((size_t)r * a.cap + k) * 3;
-    const float px = p[0], py = p[1], pz = p[2];
     SepOut* out = a.out + r;
     const Model& m = a.m;
-
-    if (blockIdx.y == 0 && threadIdx.x == 0 && m.hm) {
-        if ((double)pz < terrain64(m, (double)px, (double)py)) atomicMin(&out->first_terrain, k);
-    }
-    const int64_t T = t0 + k;
-    if (T < a.tab.t_base || T >= a.tab.t_base + a.tab.T_win) return;
-    const size_t rowoff = (size_t)ring_row(T, a.tab.T_win) * a.tab.S_pad;
-
-    const float H = (float)m.sep_h, Vm = (float)m.sep_v;
-    const float H2 = H * H;
-    const float hband = 2.0f * H * kSepBand + kSepBand * kSepBand;
-    const double H2d = __dmul_rn(m.sep_h, m.sep_h);
+    const SepConsts sk = sep_consts(m.sep_h, m.sep_v);
+    const int s0 = (blockIdx.y * kSepThreads + threadIdx.x) * kSepSlotsPerThread;
 
     int first = INT_MAX;
     unsigned cnt = 0;
     float minh = INFINITY, minv = INFINITY;
-    const int s0 = (blockIdx.y * kSepThreads + threadIdx.x) * kSepSlotsPerThread;
+    for (int k = blockIdx.x; k < n; k += gridDim.x) {
+    const float* p = a.traj + ((size_t)r * a.cap + k) * 3;
+    const float px = p[0], py = p[1], pz = p[2];
+    if (blockIdx.y == 0 && threadIdx.x == 0 && m.hm) {
+        if ((double)pz < terrain64(m, (double)px, (double)py)) atomicMin(&out->first_terrain, k);
+    }
+    const int64_t T = t0 + k;
+    if (T < a.tab.t_base || T >= a.tab.t_base + a.tab.T_win) continue;
+    const size_t rowoff = (size_t)ring_row(T, a.tab.T_win) * a.tab.S_pad;
     if (s0 < a.S_scan) {
         const float4 X4 = *reinterpret_cast<const float4*>(a.tab.X + rowoff + s0);
         const float4 Y4 = *reinterpret_cast<const float4*>(a.tab.Y + rowoff + s0);
@@ -62,23 +91,16 @@ __global__ void __launch_bounds__(kSepThreads) sepcheck_kernel(const __grid_cons
         const float qz[4] = {Z4.x, Z4.y, Z4.z, Z4.w};
 #pragma unroll
         for (int u = 0; u < kSepSlotsPerThread; ++u) {
-            const float dx = px - qx[u], dy = py - qy[u];
-            const float dz = fabsf(pz - qz[u]);
-            const float h2 = dx * dx + dy * dy;
-            bool hin = h2 < H2;  // NaN (empty slot): false
-            bool vin = dz < Vm;
-            if (fabsf(h2 - H2) < hband) {
-                const double ex = __dsub_rn((double)px, (double)qx[u]);
-                const double ey = __dsub_rn((double)py, (double)qy[u]);
-                hin = __dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)) < H2d;
-            }
-            if (fabsf(dz - Vm) < kSepBand) vin = fabs(__dsub_rn((double)pz, (double)qz[u])) < m.sep_v;
+            float h2, dz;
+            bool hin, vin;
+            sep_pair(sk, px, py, pz, qx[u], qy[u], qz[u], h2, dz, hin, vin);
             if (vin) minh = fminf(minh, sqrtf(h2));
             if (hin) {
                 minv = fminf(minv, dz);
-                if (vin) { ++cnt; first = k; }
+                if (vin) { ++cnt; first = min(first, k); }
             }
         }
+    }
     }
     // warp reduction, then one atomic per warp and quantity
     for (int off = 16; off; off >>= 1) {
@@ -214,11 +236,58 @@ cudaError_t launch_admit(const AdmitArgs& a, int n_req, int max_points, cudaStre
     return cudaSuccess;
 }
 
+// Minimum separations of each request of a batch to the requests admitted before it in the
+// same batch (at common steps), folded into its separation report. A request's plan and
+// verdict are final once no earlier admission influences it, but its minimum distances
+// to plans far away still see every earlier admission, as a sequential run would.
+__global__ void __launch_bounds__(256) batch_minsep_kernel(const __grid_constant__ MinSepArgs a) {
+    const int k = blockIdx.x;
+    if (k >= a.n) return;
+    const SepConsts sk = sep_consts(a.sep_h, a.sep_v);
+    const int nk = a.rout[k].n_points;
+    const int64_t tk = a.reqs[k].depart_step;
+    const float* pk = a.traj + (size_t)k * a.cap * 3;
+    float minh = INFINITY, minv = INFINITY;
+    for (int q = 0; q < a.n_adm; ++q) {
+        const int j = a.adm[q];
+        if (j >= k) break;  // admitted requests in arrival order
+        const int nj = a.rout[j].n_points;
+        const int64_t tj = a.reqs[j].depart_step;
+        const float* pj = a.traj + (size_t)j * a.cap * 3;
+        const int64_t lo = max(tk, tj), hi = min(tk + nk, tj + nj);
+        for (int64_t t = lo + threadIdx.x; t < hi; t += blockDim.x) {
+            const float* p = pk + 3 * (t - tk);
+            const float* q3 = pj + 3 * (t - tj);
+            float h2, dz;
+            bool hin, vin;
+            sep_pair(sk, p[0], p[1], p[2], q3[0], q3[1], q3[2], h2, dz, hin, vin);
+            if (vin) minh = fminf(minh, sqrtf(h2));
+            if (hin) minv = fminf(minv, dz);
+        }
+    }
+    for (int off = 16; off; off >>= 1) {
+        minh = fminf(minh, __shfl_xor_sync(0xffffffffu, minh, off));
+        minv = fminf(minv, __shfl_xor_sync(0xffffffffu, minv, off));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (minh < INFINITY) atomicMin(&a.out[k].min_h_bits, __float_as_uint(minh));
+        if (minv < INFINITY) atomicMin(&a.out[k].min_v_bits, __float_as_uint(minv));
+    }
+}
+
+cudaError_t launch_batch_minsep(const MinSepArgs& a, cudaStream_t s) {
+    if (a.n <= 0 || a.n_adm <= 0) return cudaSuccess;
+    batch_minsep_kernel<<<a.n, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
 // Influence of request j's speculative trajectory on request k's (j before k in arrival
-// order). k's plan could differ from its speculative one only if some state of k lies
-// within reach of a well of j one step later (|s_k(t) - p_j(t+1)| < max R + |tau|max |v_j|
-// + successor offset + margin), and its verdict only if its origin conflicts with j. A
-// conservative test: a false positive costs one more speculative round, never a result.
+// order). With j stored as a plan, k's rollout could choose differently only at a step
+// whose state lies within reach of one of j's wells one step later
+// (|s_k(t) - p_j(t+1)| < max R + max|tau| |v_j| + successor offset + 1 m), since a well
+// out of reach of every successor adds an exact zero to the value; k's verdict could change
+// only where the two trajectories come within the separation minima (+1 m) at the same
+// step. A false positive costs one more speculative round, never a result.
 __global__ void __launch_bounds__(128) influence_kernel(const __grid_constant__ InfluenceArgs a) {
     const int n = *a.n_dev;
     const int w = blockIdx.x, v = blockIdx.y;  // k = item w, j = item v
@@ -227,23 +296,23 @@ __global__ void __launch_bounds__(128) influence_kernel(const __grid_constant__ 
     __shared__ int hit;
     if (threadIdx.x == 0) hit = 0;
     __syncthreads();
-    if (j < k) {
-        const int nk = a.rout[k].n_points, nj = a.rout[j].n_points;
-        const int64_t tk = a.reqs[k].depart_step, tj = a.reqs[j].depart_step;
+    const int nk = j < k ? a.rout[k].n_points : 0, nj = j < k ? a.rout[j].n_points : 0;
+    const int64_t tk = a.reqs[k].depart_step, tj = a.reqs[j].depart_step;
+    if (nk > 0 && nj > 0 && tk < tj + nj && tj < tk + nk) {  // lifetimes overlap
         const float rho = (float)(a.reqs[k].speed_mps * a.dt) + a.dzmax + 1.0f;
         const float* pk = a.traj + (size_t)k * a.cap * 3;
         const float* pj = a.traj + (size_t)j * a.cap * 3;
-        // origin conflict (verdict only): j at k's departure step
-        if (threadIdx.x == 0) {
-            const int64_t i0 = tk - tj;
-            if (i0 >= 0 && i0 < nj) {
-                const float dx = pk[0] - pj[3 * i0], dy = pk[1] - pj[3 * i0 + 1], dz = pk[2] - pj[3 * i0 + 2];
-                if (dx * dx + dy * dy < (a.sep_h + 1.f) * (a.sep_h + 1.f) && fabsf(dz) < a.sep_v + 1.f) hit = 1;
-            }
-        }
-        // wells of j at t+1 against k's state at t, for every state of k
+        const float H = a.sep_h + 1.f, V = a.sep_v + 1.f;
         for (int i = threadIdx.x; i < nk && !hit; i += blockDim.x) {
-            const int64_t t1 = tk + i + 1 - tj;  // index of j's sample at t+1
+            const float sx = pk[3 * i], sy = pk[3 * i + 1], sz = pk[3 * i + 2];
+            // separation of the two trajectories at the same step (k's verdict)
+            const int64_t t0 = tk + i - tj;
+            if (t0 >= 0 && t0 < nj) {
+                const float dx = sx - pj[3 * t0], dy = sy - pj[3 * t0 + 1], dz = sz - pj[3 * t0 + 2];
+                if (dx * dx + dy * dy < H * H && fabsf(dz) < V) hit = 1;
+            }
+            // wells of j one step later against k's state (k's action choice at this step)
+            const int64_t t1 = t0 + 1;
             if (t1 < 0 || t1 >= nj) continue;
             const float* q1 = pj + 3 * t1;
             float vx = 0.f, vy = 0.f, vz = 0.f;
@@ -253,7 +322,7 @@ __global__ void __launch_bounds__(128) influence_kernel(const __grid_constant__ 
                 vz = (q1[5] - q1[2]) / a.dt;
             }
             const float reach = a.reach_base + a.tau_absmax * sqrtf(vx * vx + vy * vy + vz * vz) + rho;
-            const float dx = pk[3 * i] - q1[0], dy = pk[3 * i + 1] - q1[1], dz = pk[3 * i + 2] - q1[2];
+            const float dx = sx - q1[0], dy = sy - q1[1], dz = sz - q1[2];
             if (dx * dx + dy * dy + dz * dz < reach * reach) hit = 1;
         }
     }

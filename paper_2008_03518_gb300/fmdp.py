@@ -53,7 +53,7 @@ class Well(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("combine", ctypes.c_int32), ("wells", ctypes.POINTER(Well)), ("n_wells", ctypes.c_int32),
                 ("goal_reward", ctypes.c_double), ("lookahead_W", ctypes.c_int32),
-                ("cluster_size", ctypes.c_int32), ("threads_per_cta", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("cluster_size", ctypes.c_int32), ("threads_per_cta", ctypes.c_int32), ("batch_size", ctypes.c_int32)]
 
 
 class Request(ctypes.Structure):
@@ -82,7 +82,9 @@ class Stats(ctypes.Structure):
                 ("rollout_steps", ctypes.c_int64), ("slots_scanned", ctypes.c_int64),
                 ("sep_pairs", ctypes.c_int64), ("cluster_size", ctypes.c_int32),
                 ("threads_per_cta", ctypes.c_int32), ("slots_per_cta", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("phase_cycles", ctypes.c_int64 * 6)]
+                ("reserved", ctypes.c_int32), ("phase_cycles", ctypes.c_int64 * 6),
+                ("batch_waves", ctypes.c_int64), ("batch_rollouts", ctypes.c_int64), ("batch_replans", ctypes.c_int64),
+                ("influence_launches", ctypes.c_int64), ("influence_ms", ctypes.c_double)]
 
 
 # every exported symbol of include/fmdp.h
@@ -189,7 +191,7 @@ class Scheduler:
 
     def __init__(self, box, dt, gamma, actions, sep, n_slices_window=4096, max_slots=4096, heightmap=None,
                  clearance=0.0, deck_value=1000.0, static_wells=None, combine=0, wells=None, goal_reward=200.0,
-                 cluster_size=0, threads_per_cta=0):
+                 cluster_size=0, threads_per_cta=0, batch_size=0):
         self._L = load()
         air = Airspace()
         air.x0, air.y0, air.z0, air.x1, air.y1, air.z1 = map(float, box)
@@ -217,6 +219,7 @@ class Scheduler:
         opt.goal_reward = float(goal_reward)
         opt.cluster_size = int(cluster_size)
         opt.threads_per_cta = int(threads_per_cta)
+        opt.batch_size = int(batch_size)
         if wells is not None:
             warr = (Well * len(wells))(*[Well(*map(float, w)) for w in wells])
             self._keep.append(warr)
@@ -326,24 +329,29 @@ class Scheduler:
         self._check(self._L.fmdp_schedule(self._h, ctypes.byref(r), ctypes.byref(res)))
         return _result_dict(res, xyz, acts)
 
-    def _many(self, fn, reqs):
+    def _many(self, fn, reqs, points=True):
         n = len(reqs)
         rq = (Request * n)(*[make_request(reqs[i]) for i in range(n)])
+        res = (Result * n)()
+        if not points:  # verdicts and counts only
+            self._check(fn(self._h, rq, n, res))
+            return [_result_dict(res[i]) for i in range(n)]
         cap = max([rq[i].horizon for i in range(n)] + [0]) + 1
         xyz = np.zeros((n, cap, 3), dtype=np.float32)
         acts = np.zeros((n, cap), dtype=np.uint8)
-        res = (Result * n)()
         for i in range(n):
             res[i].xyz = _ptr(xyz[i], ctypes.c_float)
             res[i].actions = _ptr(acts[i], ctypes.c_uint8)
         self._check(fn(self._h, rq, n, res))
         return [_result_dict(res[i], xyz[i], acts[i]) for i in range(n)]
 
-    def schedule_many(self, reqs):
-        return self._many(self._L.fmdp_schedule_many, reqs)
+    def schedule_many(self, reqs, points=True):
+        """FCFS in array order, one request after the other on the device."""
+        return self._many(self._L.fmdp_schedule_many, reqs, points)
 
-    def schedule_batch(self, reqs):
-        return self._many(self._L.fmdp_schedule_batch, reqs)
+    def schedule_batch(self, reqs, points=True):
+        """FCFS in array order through speculative batches; identical results."""
+        return self._many(self._L.fmdp_schedule_batch, reqs, points)
 
     def stage(self, reqs):
         n = len(reqs)

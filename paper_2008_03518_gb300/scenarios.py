@@ -265,6 +265,28 @@ def c3_batched(seed: int = 103, n_plans: int = 20000, n_requests: int = 1024) ->
                     max_slots=n_plans + n_requests + 128)
 
 
+def crowded_batch(seed: int = 104, n_plans: int = 200, n_requests: int = 48, spread_m: float = 1500.0,
+                  depart_window: int = 30) -> Scenario:
+    """C1's airspace and plan mix, with requests that leave one small region within a
+    short window towards goals all around it, so that their paths cross while they fly
+    (a stress case for speculative batching: many requests influence one another)."""
+    rng = np.random.default_rng(seed)
+    box = (0.0, 0.0, 0.0, 10000.0, 10000.0, 500.0)
+    plans = straight_plans(rng, box, n_plans, 50.0, 450.0, 20.0, 40.0, 0, 600, 1.0)
+    req = np.zeros(n_requests, dtype=REQUEST_DTYPE)
+    cx, cy = 5000.0, 5000.0
+    for i in range(n_requests):
+        r, a = spread_m * np.sqrt(rng.uniform()), rng.uniform(0.0, 2.0 * np.pi)
+        ox, oy = cx + r * np.cos(a), cy + r * np.sin(a)
+        b, L = rng.uniform(0.0, 2.0 * np.pi), rng.uniform(3000.0, 4500.0)
+        gx, gy = cx + L * np.cos(b), cy + L * np.sin(b)
+        req[i] = (1 + i, ox, oy, rng.uniform(150.0, 350.0), gx, gy, rng.uniform(150.0, 350.0),
+                  rng.uniform(20.0, 40.0), int(rng.integers(0, depart_window + 1)), 900)
+    return Scenario(f"crowded_10km_{n_plans}plans_{n_requests}req_A15", box, 1.0, 0.99,
+                    action_grid((-2.0, 0.0, 2.0)), (150.0, 30.0), plans, req, n_slices_window=2048,
+                    max_slots=n_plans + n_requests + 64)
+
+
 def sort_plans_by_departure(plans: List[Plan]) -> List[Plan]:
     """Stable order by departure step (slot allocation then groups plans in time)."""
     order = sorted(range(len(plans)), key=lambda i: (plans[i].t0, i))

@@ -1,0 +1,160 @@
+"""Batched speculative FCFS (fmdp_schedule_batch) against sequential FCFS.
+
+The batch path plans many requests at once against the table as it stands and replans
+only those an earlier admission of the same batch may have changed. Its results must be
+identical, bit for bit, to planning the requests one after the other (fmdp_schedule_many,
+itself checked against the FP64 oracle in test_gpu_parity.py), and the table it leaves
+must hold the same plans. The crowded scenario makes the requests' paths cross so that
+the replan path is exercised; a few cases also go straight to the oracle.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from oracle import ADMITTED  # noqa: E402
+from paper_2008_03518_gb300 import scenarios as S  # noqa: E402
+from paper_2008_03518_gb300.fmdp import FmdpError, Scheduler  # noqa: E402
+
+from parity_util import fcfs_parity, oracle_for  # noqa: E402
+
+KEYS = ("verdict", "n_points", "first_conflict_step", "first_terrain_step", "plan_id", "near_ties",
+        "min_sep_h", "min_sep_v")
+
+
+def same_results(a, b):
+    assert len(a) == len(b)
+    for i, (x, y) in enumerate(zip(a, b)):
+        for k in KEYS:
+            assert x[k] == y[k] or (np.isnan(x[k]) and np.isnan(y[k])), (i, k, x[k], y[k])
+        np.testing.assert_array_equal(x["xyz"], y["xyz"], err_msg=f"request {i}")
+        np.testing.assert_array_equal(x["actions"], y["actions"], err_msg=f"request {i}")
+
+
+def table_of(s, t_end=1 << 40):
+    ids = s.query_plans(-(1 << 40), t_end)
+    out = {}
+    for i in ids:
+        try:
+            out[int(i)] = s.get_plan(i)
+        except FmdpError as e:  # a plan that started before the window's first step
+            out[int(i)] = (e.status, np.zeros((0, 3), np.float32))
+    return out
+
+
+def same_tables(a, b):
+    assert a.keys() == b.keys()
+    for k in a:
+        assert a[k][0] == b[k][0]
+        np.testing.assert_array_equal(a[k][1], b[k][1])
+
+
+def run_both(sc, reqs=None, **kw):
+    reqs = sc.requests if reqs is None else reqs
+    with Scheduler.from_scenario(sc, **kw) as s1:
+        many = s1.schedule_many(reqs)
+        t1 = table_of(s1)
+    with Scheduler.from_scenario(sc, **kw) as s2:
+        bat = s2.schedule_batch(reqs)
+        t2 = table_of(s2)
+        st = s2.stats()
+    return many, bat, t1, t2, st
+
+
+@pytest.mark.parametrize("batch_size", [0, 16])
+def test_batch_equals_sequential_c1(batch_size):
+    sc = S.c1_plain_small()
+    many, bat, t1, t2, st = run_both(sc, batch_size=batch_size)
+    same_results(many, bat)
+    same_tables(t1, t2)
+    assert sum(r["verdict"] == ADMITTED for r in bat) > 0
+    assert st["batch_rollouts"] >= len(sc.requests)
+
+
+@pytest.mark.parametrize("cs", [0, 2, 4])
+def test_crowded_batch_replans_and_matches(cs):
+    sc = S.crowded_batch()
+    many, bat, t1, t2, st = run_both(sc, cluster_size=cs)
+    same_results(many, bat)
+    same_tables(t1, t2)
+    # the paths cross: some requests were planned again, and the walk took several waves
+    assert st["batch_replans"] > 0 and st["batch_waves"] > 1
+    assert sum(r["replanned"] for r in bat) == st["batch_replans"]
+    assert st["batch_rollouts"] == len(sc.requests) + st["batch_replans"]
+
+
+def test_crowded_batch_against_the_oracle():
+    sc = S.crowded_batch(n_requests=24)
+    with Scheduler.from_scenario(sc) as s:
+        bat = s.schedule_batch(sc.requests)
+        st = s.stats()
+    assert st["batch_replans"] > 0
+    o = oracle_for(sc)
+    verdicts, followed, steps = fcfs_parity(None, o, sc.requests, gpu_results=bat)
+    assert ADMITTED in verdicts
+    assert followed <= max(5, steps // 1000)
+
+
+def test_graph_replay_equals_eager_launches():
+    sc = S.crowded_batch(seed=105, n_requests=40)
+    with Scheduler.from_scenario(sc) as s:
+        s.snapshot()
+        g1 = s.schedule_batch(sc.requests)  # captured graph
+        s.restore()
+        g2 = s.schedule_batch(sc.requests)  # replayed graph
+        s.restore()
+        s.set_profiling(1)                  # eager launches with event timing
+        e = s.schedule_batch(sc.requests)
+        st = s.stats()
+    same_results(g1, g2)
+    same_results(g1, e)
+    assert st["rollout_launches"] >= 1 and st["influence_launches"] >= 1
+
+
+def test_consecutive_batches_with_expiry_and_edge_cases():
+    sc = S.crowded_batch(seed=106, n_requests=30)
+    reqs = sc.requests.copy()
+    reqs[3]["horizon"] = 0                      # no step: rejected on the horizon at once
+    reqs[7]["horizon"] = 5                      # too short to reach the goal
+    reqs[9]["gx"], reqs[9]["gy"] = reqs[9]["ox"], reqs[9]["oy"]  # starts at its goal (x, y)
+    reqs[9]["gz"] = reqs[9]["oz"]
+    first, second = reqs[:17], reqs[17:]
+    second = second.copy()
+    second["depart"] += 200
+    out = []
+    for fn in ("schedule_many", "schedule_batch"):
+        with Scheduler.from_scenario(sc, batch_size=8) as s:
+            a = getattr(s, fn)(first)
+            assert getattr(s, fn)(first[:0]) == []
+            s.expire(150)
+            b = getattr(s, fn)(second)
+            out.append((a + b, table_of(s)))
+    same_results(out[0][0], out[1][0])
+    same_tables(out[0][1], out[1][1])
+    assert out[1][0][3]["n_points"] == 1 and out[1][0][9]["n_points"] == 1
+
+
+def test_c3_full_size_batch_of_256():
+    """20k known plans, one batch of 256 requests with horizons U[60,1800]: identical to
+    sequential FCFS; the requests ahead of the first admission go to the oracle too."""
+    sc = S.c3_batched(n_requests=256)
+    reqs = sc.requests.copy()
+    order = np.argsort(reqs["horizon"], kind="stable")  # short horizons first: cheap oracle prefix
+    reqs = reqs[np.concatenate([order[:6], np.sort(order[6:])])]
+    with Scheduler.from_scenario(sc) as s:
+        s.snapshot()
+        many = s.schedule_many(reqs)
+        t1 = table_of(s)
+        s.restore()
+        bat = s.schedule_batch(reqs)
+        t2 = table_of(s)
+        st = s.stats()
+    same_results(many, bat)
+    same_tables(t1, t2)
+    assert st["batch_rollouts"] >= 256
+    o = oracle_for(sc)
+    fcfs_parity(None, o, reqs[:6], gpu_results=bat[:6])
