@@ -4,12 +4,16 @@ Workload (default): the 30 km x 30 km x 1 km airspace with a 512^2 fractal heigh
 3000 seeded multi-leg known plans and 1000 FCFS requests with 25 actions and horizons up
 to 1800 steps. One step = one whole FCFS pass: the plan table is restored to the 3000
 known plans (device copy) and the 1000 requests are planned, checked and admitted in
-order on the GPU. value = requests planned per second (admitted + rejected).
+arrival order on the GPU, through speculative batches of 256 whose results are identical
+to planning them one after the other. value = requests planned per second (admitted +
+rejected).
 
-  value  : requests already resident in device memory, trajectories left on the device
-  e2e    : through the C ABI with host buffers: known plans uploaded from host memory,
-           requests uploaded, trajectories and verdicts copied back, every step
-  roofline: the rollout kernel (dominant), CUDA-event durations over the timed region
+  value    : requests already resident in device memory, trajectories left on the device
+  modes    : the same workload planned one request at a time (plain sequential FCFS), and
+             the 20k-known-plan workload (batches of 256, horizons U[60,1800]) batched
+  e2e      : through the C ABI with host buffers: known plans uploaded from host memory,
+             requests uploaded, trajectories and verdicts copied back, every step
+  roofline : the rollout kernel (dominant), CUDA-event durations of a profiled step
   cpu_baseline: the FP64 oracle on this host's cores on a bounded sample
 
 --impl reference runs the FP64 CPU oracle as the reference arm (rank 0 only).
@@ -155,9 +159,23 @@ def workload_config(sc, n_req):
             "actions": len(sc.actions), "max_horizon": int(sc.requests["horizon"].max()),
             "airspace_km": [round((sc.box[3] - sc.box[0]) / 1000), round((sc.box[4] - sc.box[1]) / 1000),
                             round((sc.box[5] - sc.box[2]) / 1000, 1)],
-            "mode": "plain FCFS (one persistent rollout per request, sequential admission)",
+            "mode": "FCFS through speculative batches of 256 (results identical to sequential FCFS)",
             "l2": "plan table (3 x 4096 x S fp32 planes) larger than L2 and rewritten by the restore every step",
             "parallelism": "replicas"}
+
+
+def timed(stream, fn, k, barrier):
+    import torch
+
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    out = None
+    for _ in range(k):
+        out = fn()
+    e1.record(stream)
+    barrier()
+    return e0.elapsed_time(e1), out
 
 
 def main():
@@ -171,6 +189,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-modes", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -197,6 +216,13 @@ def main():
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
+    def max_over_ranks(ms):
+        if world > 1:
+            t = torch.tensor([ms], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
     from paper_2008_03518_gb300.fmdp import Scheduler
 
     s = Scheduler.from_scenario(sc)
@@ -204,52 +230,82 @@ def main():
     s.set_stream(stream.cuda_stream)
     s.snapshot()
     s.stage(sc.requests)
+    n_req = len(sc.requests)
 
-    def step():
+    def step(batched=True):
         s.restore()
-        return s.schedule_staged()
+        return s.schedule_staged(batched)
 
     for _ in range(args.warmup):
         step()
+    s.set_profiling(0)  # resets the counters
     clocks = ClockSampler(local_rank if world == 1 else 0)
     clocks.start()
-    s.set_profiling(True)
-    barrier()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    admitted = 0
-    for _ in range(args.steps):
-        admitted = step()
-    ev1.record(stream)
-    barrier()
-    ms = ev0.elapsed_time(ev1)
-    st = s.stats()
-    s.set_profiling(False)
+    ms, admitted = timed(stream, step, args.steps, barrier)
     clk = clocks.stop()
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    n_req = len(sc.requests)
+    st = s.stats()
+    ms = max_over_ranks(ms)
     value = world * n_req * args.steps / (ms / 1e3)
+    gpu_launches = st["kernel_launches"]
+    batch_stats = {"waves_per_step": st["batch_waves"] / args.steps,
+                   "rollouts_per_step": st["batch_rollouts"] / args.steps,
+                   "replans_per_step": st["batch_replans"] / args.steps}
 
-    # ---- roofline of the rollout kernel over the timed region
+    # ---- roofline of the rollout kernel: one more step, launched eagerly with CUDA events
+    s.set_profiling(1)
+    step()
+    kt = s.stats()
+    s.set_profiling(0)
     peaks, peak_kind = measured_peaks()
-    launches = max(st["rollout_launches"], 1)
-    avg_ms = st["rollout_ms"] / launches
-    bytes_per_launch = 12.0 * st["slots_scanned"] / launches
+    launches = max(kt["rollout_launches"], 1)
+    avg_ms = kt["rollout_ms"] / launches
+    bytes_per_launch = 12.0 * kt["slots_scanned"] / launches
     achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
     tr = traffic_from_profile(os.path.join(ROOT, "paper_2008_03518_gb300", "csrc", "rollout.cu"))
+    kernel_ms = {k: kt[k] for k in ("rollout_ms", "sepcheck_ms", "admit_ms", "influence_ms")}
     roofline = {"kernel": "rollout_kernel", "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
                 "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
-                "traffic": (tr * st["slots_scanned"] / launches) if tr is not None else None,
+                "traffic": (tr * kt["slots_scanned"] / launches) if tr is not None else None,
                 "peak_source": peak_kind,
                 "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_ms,
-                "cluster_size": st["cluster_size"], "threads_per_cta": st["threads_per_cta"],
-                "slots_per_cta": st["slots_per_cta"], "steps_per_launch": st["rollout_steps"] / launches,
-                "us_per_rollout_step": 1e3 * st["rollout_ms"] / max(st["rollout_steps"], 1),
-                "share_of_step": st["rollout_ms"] / ms}
-    gpu_launches = st["rollout_launches"] + st["sepcheck_launches"] + st["admit_launches"] + args.steps
+                "launches_per_step": launches, "cluster_size": kt["cluster_size"],
+                "threads_per_cta": kt["threads_per_cta"], "slots_per_cta": kt["slots_per_cta"],
+                "rollout_steps_per_step": kt["rollout_steps"],
+                "share_of_kernel_time": kt["rollout_ms"] / max(sum(kernel_ms.values()), 1e-9),
+                "kernel_ms_per_step": kernel_ms}
+
+    # ---- other modes of the metric: plain sequential FCFS, and 20k known plans batched
+    modes = None
+    if not args.no_modes:
+        modes = {}
+        step(False)
+        mseq, _ = timed(stream, lambda: step(False), 1, barrier)
+        mseq = max_over_ranks(mseq)
+        modes["plain_sequential"] = {"known_plans": len(sc.plans), "value": world * n_req / (mseq / 1e3),
+                                     "unit": UNIT, "ms_per_step": mseq,
+                                     "mode": "one request at a time, each rollout one cluster launch"}
+        modes["batched"] = {"known_plans": len(sc.plans), "value": value, "unit": UNIT}
+        sc3 = S.c3_batched(n_requests=512)
+        s3 = Scheduler.from_scenario(sc3)
+        s3.set_stream(stream.cuda_stream)
+        s3.snapshot()
+        s3.stage(sc3.requests)
+
+        def step3():
+            s3.restore()
+            return s3.schedule_staged(True)
+
+        step3()
+        s3.set_profiling(0)
+        m3, adm3 = timed(stream, step3, 2, barrier)
+        st3 = s3.stats()
+        m3 = max_over_ranks(m3)
+        modes["batched_20k"] = {"known_plans": len(sc3.plans), "value": world * 512 * 2 / (m3 / 1e3),
+                                "unit": UNIT, "ms_per_step": m3 / 2, "requests_per_step": 512,
+                                "batch": 256, "admitted_per_step": adm3,
+                                "waves_per_step": st3["batch_waves"] / 2,
+                                "replans_per_step": st3["batch_replans"] / 2, "workload": sc3.name}
+        s3.close()
 
     # ---- end to end through the C ABI with host buffers
     e2e = None
@@ -261,28 +317,21 @@ def main():
         def e2e_step():
             s.clear()
             s.add_plans(plans)
-            res = s.schedule_many(sc.requests)
+            res = s.schedule_batch(sc.requests)
             return sum(r["xyz"].nbytes + r["actions"].nbytes + 48 for r in res)
 
-        for _ in range(1):
-            e2e_step()
-        barrier()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
+        e2e_step()
         k = max(1, min(args.steps, 3))
-        for _ in range(k):
-            d2h = e2e_step()
-        e1.record(stream)
-        barrier()
-        ems = e0.elapsed_time(e1)
+        ems, d2h = timed(stream, e2e_step, k, barrier)
+        ems = max_over_ranks(ems)
         e2e = {"value": world * n_req * k / (ems / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "steps": k}
+               "d2h_bytes_per_step": d2h, "steps": k, "api": "fmdp_clear + fmdp_add_plans + fmdp_schedule_batch"}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(sc, n_req),
-            "admitted_per_step": admitted, "e2e": e2e, "gpu_launches": gpu_launches, "roofline": roofline,
-            "clocks": clk}
+            "admitted_per_step": admitted, "batch": batch_stats, "modes": modes, "e2e": e2e,
+            "gpu_launches": gpu_launches, "roofline": roofline, "clocks": clk}
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(sc, args.cpu_seconds)
     if rank == 0:

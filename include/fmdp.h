@@ -163,10 +163,11 @@ fmdp_status fmdp_schedule_batch(fmdp_ctx* ctx, const fmdp_request* reqs, int32_t
 
 /* Device-resident variant used for kernel-side timing: fmdp_stage_requests copies the
  * requests into library-owned device memory; fmdp_schedule_staged plans them in FCFS
- * order like fmdp_schedule_many but leaves trajectories on the device (only verdicts and
- * counts come back); fmdp_fetch_staged copies results of the last staged run. */
+ * order, like fmdp_schedule_many (batched = 0) or fmdp_schedule_batch (batched = 1), but
+ * leaves trajectories on the device (only verdicts and counts come back);
+ * fmdp_fetch_staged copies results of the last staged run. */
 fmdp_status fmdp_stage_requests(fmdp_ctx* ctx, const fmdp_request* reqs, int32_t n);
-fmdp_status fmdp_schedule_staged(fmdp_ctx* ctx, int32_t* n_admitted_out);
+fmdp_status fmdp_schedule_staged(fmdp_ctx* ctx, int32_t batched, int32_t* n_admitted_out);
 fmdp_status fmdp_fetch_staged(fmdp_ctx* ctx, fmdp_result* res, int32_t n);
 
 /* Ids of stored plans with at least one sample in [t_begin, t_end). */
@@ -242,6 +243,7 @@ typedef struct {
     int64_t batch_replans;       /* re-plans among them */
     int64_t influence_launches;  /* influence-test launches (on = 1) */
     double influence_ms;         /* their summed CUDA-event durations */
+    int64_t kernel_launches;     /* every kernel launch of the library, graph nodes included */
 } fmdp_stats;
 /* on = 1: per-kernel CUDA-event timing on the context's stream; on = 2: additionally
  * per-phase cycle counters inside the rollout kernel (diagnostic, slows it slightly);

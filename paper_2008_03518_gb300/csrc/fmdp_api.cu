@@ -36,6 +36,12 @@ void cuda_check(cudaError_t e, const char* what) {
     }
 }
 #define CK(x) cuda_check((x), #x)
+// a kernel launch of the library on context c (counted unless it is being captured)
+#define LAUNCH(c, x)                                             \
+    do {                                                         \
+        cuda_check((x), #x);                                     \
+        if (!(c)->capturing) (c)->stats.kernel_launches++;       \
+    } while (0)
 
 void require(bool ok, fmdp_status code, const std::string& msg) {
     if (!ok) throw ApiError(code, msg);
@@ -110,17 +116,20 @@ struct SeqBuffers {
     }
 };
 
-// Device and pinned buffers of one speculative batch (fmdp_schedule_batch). The index
-// block holds four arrays of n_cap entries: work items to plan, the unresolved requests
-// in arrival order, the requests to store, and each request's slot.
+// Device and pinned buffers of speculative batching (fmdp_schedule_batch). Per-request
+// arrays cover every request of the call (rq_cap entries, trajectories of cap samples),
+// so that batches of one call index them by request number. The index block holds the
+// work items to plan, the unresolved requests in arrival order and the requests to store
+// (n_cap entries each, one batch), then each request's slot (rq_cap entries).
 struct BatchBuffers {
-    int32_t n_cap = 0, cap = 0;
+    int32_t n_cap = 0, rq_cap = 0, cap = 0;
+    const fmdp_request* rq = nullptr;  // requests on the device (own copy or the staged ones)
     DevArray<fmdp_request> reqs;
     DevArray<float> traj;
     DevArray<uint8_t> acts;
     DevArray<RolloutOut> rout;
     DevArray<SepOut> sepo;
-    DevArray<int32_t> idx;   // [4][n_cap]
+    DevArray<int32_t> idx;   // [3][n_cap] + [rq_cap]
     DevArray<int32_t> ctr;   // queue counter, n_todo, n_unresolved, n_store
     DevArray<uint8_t> infl;  // [n_cap][n_cap]
     PinnedArray<int32_t> h_idx, h_ctr;
@@ -194,11 +203,14 @@ struct fmdp_ctx {
     BatchBuffers bat;
     std::vector<WaveGraph> graphs;  // most recent first
     bool use_graphs = true;
+    bool capturing = false;
 
     // staged (device-resident) requests
     std::vector<fmdp_request> staged;
     int32_t staged_cap = 0;
     bool staged_done = false;
+    bool staged_batched = false;
+    std::vector<fmdp_result> staged_res;  // batched staged runs: results without points
 
     // snapshot
     float* sX = nullptr;
@@ -407,7 +419,7 @@ void recompute_hw(fmdp_ctx* c) {
 // c->slots) in FCFS order on the context's stream.
 void enqueue_sequence(fmdp_ctx* c, SeqBuffers& B, int32_t n, int32_t cap, const Geometry& g) {
     const TableView tv = table_view(c);
-    CK(launch_sep_reset(B.sepo.p, n, c->stream));
+    LAUNCH(c, launch_sep_reset(B.sepo.p, n, c->stream));
     for (int32_t i = 0; i < n; ++i) {
         RolloutArgs ra{};
         ra.m = c->model;
@@ -427,7 +439,7 @@ void enqueue_sequence(fmdp_ctx* c, SeqBuffers& B, int32_t n, int32_t cap, const 
         ra.phase = c->phase_timing ? c->phase.p : nullptr;
         {
             KernelTimer t(c, 0);
-            CK(launch_rollout(ra, g.threads, g.smem, c->stream));
+            LAUNCH(c, launch_rollout(ra, g.threads, g.smem, c->stream));
             t.stop();
         }
         SepArgs sa{};
@@ -441,7 +453,7 @@ void enqueue_sequence(fmdp_ctx* c, SeqBuffers& B, int32_t n, int32_t cap, const 
         sa.out = B.sepo.p + i;
         {
             KernelTimer t(c, 1);
-            CK(launch_sepcheck(sa, 1, cap, c->stream));
+            LAUNCH(c, launch_sepcheck(sa, 1, cap, c->stream));
             t.stop();
         }
         AdmitArgs aa{};
@@ -455,7 +467,7 @@ void enqueue_sequence(fmdp_ctx* c, SeqBuffers& B, int32_t n, int32_t cap, const 
         aa.force = 0;
         {
             KernelTimer t(c, 2);
-            CK(launch_admit(aa, 1, cap, c->stream));
+            LAUNCH(c, launch_admit(aa, 1, cap, c->stream));
             t.stop();
         }
     }
@@ -588,6 +600,7 @@ int32_t run_fcfs(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_result* 
 constexpr int32_t kBatchDefault = 256;
 constexpr int32_t kBatchMax = 1024;
 constexpr int kSepPointBlocks = 64;  // sep_check blocks per request along its trajectory
+constexpr int kWaveKernels = 5;      // kernels of one wave: admit, reset, rollout, sep_check, influence
 
 // Batch geometry: the narrowest cluster whose partition fits one CTA's shared memory, so
 // that as many rollouts as possible run side by side.
@@ -616,6 +629,8 @@ int32_t host_verdict(const RolloutOut& ro, const SepOut& so) {  // the admission
 // plan the work items, check their separation, test influence among the unresolved
 // requests, and bring rollout, separation and influence results back to pinned memory.
 // Every count is read on the device, so the sequence can be captured once and replayed.
+size_t idx_words(const BatchBuffers& B) { return 3 * (size_t)B.n_cap + B.rq_cap; }
+
 void enqueue_wave(fmdp_ctx* c, const Geometry& g, int n_clusters, BatchBuffers& B, bool timed) {
     const int32_t n_cap = B.n_cap, cap = B.cap;
     cudaStream_t s = c->stream;
@@ -624,7 +639,7 @@ void enqueue_wave(fmdp_ctx* c, const Geometry& g, int n_clusters, BatchBuffers& 
     int32_t* store = unres + n_cap;
     int32_t* slots = store + n_cap;
     const TableView tv = table_view(c);
-    CK(cudaMemcpyAsync(B.idx.p, B.h_idx.p, 4 * (size_t)n_cap * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(B.idx.p, B.h_idx.p, idx_words(B) * sizeof(int32_t), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(B.ctr.p, B.h_ctr.p, 4 * sizeof(int32_t), cudaMemcpyHostToDevice, s));
     {
         AdmitArgs aa{};
@@ -632,17 +647,17 @@ void enqueue_wave(fmdp_ctx* c, const Geometry& g, int n_clusters, BatchBuffers& 
         aa.cap = cap;
         aa.traj = B.traj.p;
         aa.rout = B.rout.p;
-        aa.reqs = B.reqs.p;
+        aa.reqs = B.rq;
         aa.slots = slots;
         aa.sep = B.sepo.p;
         aa.force = 0;
         aa.idx = store;
         aa.n_dev = B.ctr.p + 3;
         KernelTimer t(c, timed ? 2 : -1);
-        CK(launch_admit(aa, n_cap, cap, s));
+        LAUNCH(c, launch_admit(aa, n_cap, cap, s));
         t.stop();
     }
-    CK(launch_sep_reset_idx(B.sepo.p, todo, B.ctr.p + 1, n_cap, s));
+    LAUNCH(c, launch_sep_reset_idx(B.sepo.p, todo, B.ctr.p + 1, n_cap, s));
     {
         RolloutArgs ra{};
         ra.m = c->model;
@@ -652,7 +667,7 @@ void enqueue_wave(fmdp_ctx* c, const Geometry& g, int n_clusters, BatchBuffers& 
         ra.cs = g.cs;
         ra.ring = g.ring;
         ra.cap = cap;
-        ra.reqs = B.reqs.p;
+        ra.reqs = B.rq;
         ra.n_req = n_cap;
         ra.traj = B.traj.p;
         ra.acts = B.acts.p;
@@ -663,7 +678,7 @@ void enqueue_wave(fmdp_ctx* c, const Geometry& g, int n_clusters, BatchBuffers& 
         ra.idx = todo;
         ra.n_dev = B.ctr.p + 1;
         KernelTimer t(c, timed ? 0 : -1);
-        CK(launch_rollout(ra, g.threads, g.smem, s, n_clusters));
+        LAUNCH(c, launch_rollout(ra, g.threads, g.smem, s, n_clusters));
         t.stop();
     }
     {
@@ -674,19 +689,19 @@ void enqueue_wave(fmdp_ctx* c, const Geometry& g, int n_clusters, BatchBuffers& 
         sa.cap = cap;
         sa.traj = B.traj.p;
         sa.rout = B.rout.p;
-        sa.reqs = B.reqs.p;
+        sa.reqs = B.rq;
         sa.out = B.sepo.p;
         sa.idx = todo;
         sa.n_dev = B.ctr.p + 1;
         KernelTimer t(c, timed ? 1 : -1);
-        CK(launch_sepcheck(sa, n_cap, kSepPointBlocks, s));
+        LAUNCH(c, launch_sepcheck(sa, n_cap, kSepPointBlocks, s));
         t.stop();
     }
     {
         InfluenceArgs ia{};
         ia.traj = B.traj.p;
         ia.rout = B.rout.p;
-        ia.reqs = B.reqs.p;
+        ia.reqs = B.rq;
         ia.cap = cap;
         ia.idx = unres;
         ia.n_dev = B.ctr.p + 2;
@@ -701,11 +716,11 @@ void enqueue_wave(fmdp_ctx* c, const Geometry& g, int n_clusters, BatchBuffers& 
         ia.out = B.infl.p;
         ia.n_cap = n_cap;
         KernelTimer t(c, timed ? 3 : -1);
-        CK(launch_influence(ia, n_cap, cap, s));
+        LAUNCH(c, launch_influence(ia, n_cap, cap, s));
         t.stop();
     }
-    CK(cudaMemcpyAsync(B.h_rout.p, B.rout.p, n_cap * sizeof(RolloutOut), cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(B.h_sep.p, B.sepo.p, n_cap * sizeof(SepOut), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(B.h_rout.p, B.rout.p, B.rq_cap * sizeof(RolloutOut), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(B.h_sep.p, B.sepo.p, B.rq_cap * sizeof(SepOut), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(B.h_infl.p, B.infl.p, (size_t)n_cap * n_cap, cudaMemcpyDeviceToHost, s));
 }
 
@@ -714,8 +729,9 @@ void enqueue_wave(fmdp_ctx* c, const Geometry& g, int n_clusters, BatchBuffers& 
 cudaGraphExec_t wave_graph(fmdp_ctx* c, const Geometry& g, int n_clusters, BatchBuffers& B) {
     const TableView tv = table_view(c);
     const std::vector<int64_t> key = {g.S_scan, g.cs, g.threads, g.chunk, g.ring, (int64_t)g.smem, n_clusters,
-                                      B.n_cap, B.cap, (int64_t)(uintptr_t)B.idx.p, (int64_t)(uintptr_t)B.traj.p,
-                                      (int64_t)(uintptr_t)B.reqs.p, (int64_t)(uintptr_t)B.h_idx.p,
+                                      B.n_cap, B.rq_cap, B.cap, (int64_t)(uintptr_t)B.idx.p,
+                                      (int64_t)(uintptr_t)B.traj.p, (int64_t)(uintptr_t)B.rq,
+                                      (int64_t)(uintptr_t)B.rout.p, (int64_t)(uintptr_t)B.h_idx.p,
                                       (int64_t)(uintptr_t)B.h_infl.p, (int64_t)(uintptr_t)tv.X, tv.t_base};
     for (size_t i = 0; i < c->graphs.size(); ++i)
         if (c->graphs[i].key == key) {
@@ -729,15 +745,18 @@ cudaGraphExec_t wave_graph(fmdp_ctx* c, const Geometry& g, int n_clusters, Batch
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
+        c->capturing = true;
         try {
             enqueue_wave(c, g, n_clusters, B, false);
         } catch (...) {
+            c->capturing = false;
             cudaStreamEndCapture(cap_stream, &graph);
             if (graph) cudaGraphDestroy(graph);
             c->stream = user;
             cudaStreamDestroy(cap_stream);
             throw;
         }
+        c->capturing = false;
         e = cudaStreamEndCapture(cap_stream, &graph);
     }
     c->stream = user;
@@ -755,30 +774,12 @@ cudaGraphExec_t wave_graph(fmdp_ctx* c, const Geometry& g, int n_clusters, Batch
     return exec;
 }
 
-// Plans one batch (n <= kBatchMax requests, already validated) in FCFS order with exact
-// sequential results. Returns the number admitted.
-int32_t run_batch_chunk(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_result* res) {
+// Plans requests [b0, b0 + n) of the call (n <= kBatchMax, validated, already on the
+// device in B.rq) as one speculative batch, with exact sequential FCFS results. Results go
+// to res[b0 ...] without sample points. Returns the number admitted.
+int32_t run_batch_chunk(fmdp_ctx* c, const fmdp_request* reqs, int32_t b0, int32_t n, fmdp_result* res) {
     BatchBuffers& B = c->bat;
-    int32_t cap = 1;
-    for (int32_t i = 0; i < n; ++i) cap = std::max(cap, reqs[i].horizon + 1);
-    // buffer shapes in buckets, so that graphs are reused from batch to batch
-    B.n_cap = std::max(B.n_cap, round_up(n, 64));
-    B.cap = std::max(B.cap, round_up(cap, 256));
     const int32_t n_cap = B.n_cap;
-    B.reqs.ensure(n_cap);
-    B.traj.ensure((size_t)n_cap * B.cap * 3);
-    B.acts.ensure((size_t)n_cap * B.cap);
-    B.rout.ensure(n_cap);
-    B.sepo.ensure(n_cap);
-    B.idx.ensure(4 * (size_t)n_cap);
-    B.ctr.ensure(4);
-    B.infl.ensure((size_t)n_cap * n_cap);
-    B.h_idx.ensure(4 * (size_t)n_cap);
-    B.h_ctr.ensure(4);
-    B.h_infl.ensure((size_t)n_cap * n_cap);
-    B.h_rout.ensure(n_cap);
-    B.h_sep.ensure(n_cap);
-
     // the batch admits at most n plans, into the lowest free slots: scan up to that bound
     require((size_t)n <= c->book.free_slots.size(), FMDP_ERR_FULL, "not enough free plan slots for the batch");
     int32_t bound = c->book.S_hw;
@@ -790,12 +791,11 @@ int32_t run_batch_chunk(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_r
     const int n_clusters = std::max(1, std::min(n, rollout_max_active_clusters(g.cs, g.threads, g.smem)));
     const bool graphs = c->use_graphs && !c->profiling;
 
-    CK(cudaMemcpyAsync(B.reqs.p, reqs, n * sizeof(fmdp_request), cudaMemcpyHostToDevice, c->stream));
+    // request numbers are global (b0 ...); per-request host state is indexed by r - b0
     std::vector<int32_t> U(n), todo(n), store, adm_all, slot_of(n, -1), replans(n, 0), verdict(n, -1);
     std::vector<uint64_t> ids(n, 0);
     std::vector<RolloutOut> fin_ro(n);
-    std::vector<SepOut> fin_so(n);
-    for (int32_t i = 0; i < n; ++i) U[i] = todo[i] = i;
+    for (int32_t i = 0; i < n; ++i) U[i] = todo[i] = b0 + i;
     std::vector<std::pair<uint64_t, int32_t>> pending;  // admitted, not yet stored: (id, slot)
     int32_t admitted = 0;
     try {
@@ -804,13 +804,17 @@ int32_t run_batch_chunk(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_r
             std::copy(todo.begin(), todo.end(), hi);
             std::copy(U.begin(), U.end(), hi + n_cap);
             std::copy(store.begin(), store.end(), hi + 2 * n_cap);
-            for (int32_t i = 0; i < n; ++i) hi[3 * n_cap + i] = slot_of[i];
+            for (int32_t i = 0; i < n; ++i) hi[3 * n_cap + b0 + i] = slot_of[i];
             B.h_ctr.p[0] = 0;
             B.h_ctr.p[1] = (int32_t)todo.size();
             B.h_ctr.p[2] = (int32_t)U.size();
             B.h_ctr.p[3] = (int32_t)store.size();
-            if (graphs) CK(cudaGraphLaunch(wave_graph(c, g, n_clusters, B), c->stream));
-            else enqueue_wave(c, g, n_clusters, B, true);
+            if (graphs) {
+                CK(cudaGraphLaunch(wave_graph(c, g, n_clusters, B), c->stream));
+                c->stats.kernel_launches += kWaveKernels;
+            } else {
+                enqueue_wave(c, g, n_clusters, B, true);
+            }
             CK(cudaStreamSynchronize(c->stream));
             if (c->profiling) collect_timers(c);
             require(read_error_word(c) == 0, FMDP_ERR_TIMEOUT, "a bounded device wait expired during a rollout");
@@ -832,19 +836,18 @@ int32_t run_batch_chunk(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_r
                 bool hit = false;
                 for (size_t v : adm_pos) hit = hit || row[v];
                 if (hit) break;
-                const int32_t k = U[pos];
-                fin_ro[k] = B.h_rout.p[k];
-                fin_so[k] = B.h_sep.p[k];
-                verdict[k] = host_verdict(fin_ro[k], fin_so[k]);
-                if (verdict[k] == FMDP_ADMITTED) {
+                const int32_t k = U[pos], q = k - b0;
+                fin_ro[q] = B.h_rout.p[k];
+                verdict[q] = host_verdict(fin_ro[q], B.h_sep.p[k]);
+                if (verdict[q] == FMDP_ADMITTED) {
                     const int32_t slot = take_slot(c);
                     require(slot < g.S_scan, FMDP_ERR_ARG, "internal: batch slot beyond the scanned range");
                     const uint64_t id = c->book.next_id++;
-                    c->book.plans[id] = PlanMeta{slot, reqs[k].depart_step, fin_ro[k].n_points};
+                    c->book.plans[id] = PlanMeta{slot, reqs[k].depart_step, fin_ro[q].n_points};
                     c->book.S_hw = std::max(c->book.S_hw, slot + 1);
                     pending.push_back({id, slot});
-                    slot_of[k] = slot;
-                    ids[k] = id;
+                    slot_of[q] = slot;
+                    ids[q] = id;
                     store.push_back(k);
                     adm_all.push_back(k);
                     adm_pos.push_back(pos);
@@ -860,7 +863,7 @@ int32_t run_batch_chunk(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_r
                 nU.push_back(U[w]);
                 if (hit) {
                     ntodo.push_back(U[w]);
-                    ++replans[U[w]];
+                    ++replans[U[w] - b0];
                     c->stats.batch_replans++;
                 }
             }
@@ -871,10 +874,9 @@ int32_t run_batch_chunk(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_r
         // every request's minimum separations
         std::copy(adm_all.begin(), adm_all.end(), B.h_idx.p);
         std::copy(store.begin(), store.end(), B.h_idx.p + 2 * n_cap);
-        for (int32_t i = 0; i < n; ++i) B.h_idx.p[3 * n_cap + i] = slot_of[i];
+        for (int32_t i = 0; i < n; ++i) B.h_idx.p[3 * n_cap + b0 + i] = slot_of[i];
         B.h_ctr.p[3] = (int32_t)store.size();
-        CK(cudaMemcpyAsync(B.idx.p, B.h_idx.p, 4 * (size_t)n_cap * sizeof(int32_t), cudaMemcpyHostToDevice,
-                           c->stream));
+        CK(cudaMemcpyAsync(B.idx.p, B.h_idx.p, idx_words(B) * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
         CK(cudaMemcpyAsync(B.ctr.p, B.h_ctr.p, 4 * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
         if (!store.empty()) {
             AdmitArgs aa{};
@@ -882,37 +884,29 @@ int32_t run_batch_chunk(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_r
             aa.cap = B.cap;
             aa.traj = B.traj.p;
             aa.rout = B.rout.p;
-            aa.reqs = B.reqs.p;
+            aa.reqs = B.rq;
             aa.slots = B.idx.p + 3 * n_cap;
             aa.sep = B.sepo.p;
             aa.idx = B.idx.p + 2 * n_cap;
             aa.n_dev = B.ctr.p + 3;
             KernelTimer t(c, 2);
-            CK(launch_admit(aa, n_cap, B.cap, c->stream));
+            LAUNCH(c, launch_admit(aa, n_cap, B.cap, c->stream));
             t.stop();
         }
         MinSepArgs ma{};
         ma.traj = B.traj.p;
         ma.rout = B.rout.p;
-        ma.reqs = B.reqs.p;
+        ma.reqs = B.rq;
         ma.cap = B.cap;
+        ma.k0 = b0;
         ma.n = n;
         ma.adm = B.idx.p;
         ma.n_adm = (int32_t)adm_all.size();
         ma.sep_h = c->sep.horiz_m;
         ma.sep_v = c->sep.vert_m;
         ma.out = B.sepo.p;
-        CK(launch_batch_minsep(ma, c->stream));
-        CK(cudaMemcpyAsync(B.h_sep.p, B.sepo.p, n * sizeof(SepOut), cudaMemcpyDeviceToHost, c->stream));
-        bool want_points = false;
-        for (int32_t i = 0; res && i < n; ++i) want_points = want_points || res[i].xyz || res[i].actions;
-        if (want_points) {
-            B.h_traj.ensure((size_t)n * B.cap * 3);
-            B.h_acts.ensure((size_t)n * B.cap);
-            CK(cudaMemcpyAsync(B.h_traj.p, B.traj.p, (size_t)n * B.cap * 3 * sizeof(float), cudaMemcpyDeviceToHost,
-                               c->stream));
-            CK(cudaMemcpyAsync(B.h_acts.p, B.acts.p, (size_t)n * B.cap, cudaMemcpyDeviceToHost, c->stream));
-        }
+        LAUNCH(c, launch_batch_minsep(ma, c->stream));
+        CK(cudaMemcpyAsync(B.h_sep.p + b0, B.sepo.p + b0, n * sizeof(SepOut), cudaMemcpyDeviceToHost, c->stream));
         CK(cudaStreamSynchronize(c->stream));
         if (c->profiling) collect_timers(c);
         pending.clear();
@@ -924,25 +918,69 @@ int32_t run_batch_chunk(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_r
         recompute_hw(c);
         throw;
     }
-    for (int32_t i = 0; res && i < n; ++i) {
-        fmdp_result* o = res + i;
-        SepOut so = B.h_sep.p[i];  // the final plan's report with the batch's admissions folded in
+    for (int32_t i = 0; i < n; ++i) {
+        fmdp_result* o = res + b0 + i;
+        SepOut so = B.h_sep.p[b0 + i];  // the final plan's report with the batch's admissions folded in
         so.verdict = verdict[i];
         fill_result(fin_ro[i], so, o);
         o->plan_id = ids[i];
         o->replanned = replans[i];
-        const int32_t np = fin_ro[i].n_points;
-        if (o->xyz) std::memcpy(o->xyz, B.h_traj.p + (size_t)i * B.cap * 3, (size_t)np * 3 * sizeof(float));
-        if (o->actions && np > 1) std::memcpy(o->actions, B.h_acts.p + (size_t)i * B.cap, (size_t)(np - 1));
     }
     return admitted;
 }
 
-int32_t run_batch(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_result* res) {
+// Speculative batching over n validated requests (host copies in reqs; on the device in
+// dev_reqs, or copied there when it is null). Results to res; sample points to the
+// callers' buffers named in res unless keep_points, which leaves them in the batch
+// buffers for fmdp_fetch_staged. Returns the number admitted.
+int32_t run_batch(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_result* res,
+                  const fmdp_request* dev_reqs, bool keep_points) {
+    if (n <= 0) return 0;
+    BatchBuffers& B = c->bat;
     const int32_t bs = c->opt.batch_size > 0 ? c->opt.batch_size : kBatchDefault;
+    int32_t cap = 1;
+    for (int32_t i = 0; i < n; ++i) cap = std::max(cap, reqs[i].horizon + 1);
+    // buffer shapes in buckets, so that graphs are reused from call to call
+    B.n_cap = std::max(B.n_cap, round_up(std::min(n, bs), 64));
+    B.rq_cap = std::max(B.rq_cap, round_up(n, 256));
+    B.cap = std::max(B.cap, round_up(cap, 256));
+    const size_t R = B.rq_cap;
+    B.traj.ensure(R * B.cap * 3);
+    B.acts.ensure(R * B.cap);
+    B.rout.ensure(R);
+    B.sepo.ensure(R);
+    B.idx.ensure(idx_words(B));
+    B.ctr.ensure(4);
+    B.infl.ensure((size_t)B.n_cap * B.n_cap);
+    B.h_idx.ensure(idx_words(B));
+    B.h_ctr.ensure(4);
+    B.h_infl.ensure((size_t)B.n_cap * B.n_cap);
+    B.h_rout.ensure(R);
+    B.h_sep.ensure(R);
+    if (dev_reqs) {
+        B.rq = dev_reqs;
+    } else {
+        B.reqs.ensure(R);
+        CK(cudaMemcpyAsync(B.reqs.p, reqs, n * sizeof(fmdp_request), cudaMemcpyHostToDevice, c->stream));
+        B.rq = B.reqs.p;
+    }
     int32_t admitted = 0;
-    for (int32_t b0 = 0; b0 < n; b0 += bs)
-        admitted += run_batch_chunk(c, reqs + b0, std::min(bs, n - b0), res ? res + b0 : nullptr);
+    for (int32_t b0 = 0; b0 < n; b0 += bs) admitted += run_batch_chunk(c, reqs, b0, std::min(bs, n - b0), res);
+    bool want_points = false;
+    for (int32_t i = 0; !keep_points && i < n; ++i) want_points = want_points || res[i].xyz || res[i].actions;
+    if (want_points) {
+        B.h_traj.ensure((size_t)n * B.cap * 3);
+        B.h_acts.ensure((size_t)n * B.cap);
+        CK(cudaMemcpyAsync(B.h_traj.p, B.traj.p, (size_t)n * B.cap * 3 * sizeof(float), cudaMemcpyDeviceToHost,
+                           c->stream));
+        CK(cudaMemcpyAsync(B.h_acts.p, B.acts.p, (size_t)n * B.cap, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        for (int32_t i = 0; i < n; ++i) {
+            const int32_t np = res[i].n_points;
+            if (res[i].xyz) std::memcpy(res[i].xyz, B.h_traj.p + (size_t)i * B.cap * 3, (size_t)np * 12);
+            if (res[i].actions && np > 1) std::memcpy(res[i].actions, B.h_acts.p + (size_t)i * B.cap, (size_t)(np - 1));
+        }
+    }
     return admitted;
 }
 
@@ -986,7 +1024,7 @@ void store_plans(fmdp_ctx* c, int32_t n_plans, const int64_t* t0s, const int32_t
         aa.t0s = c->t0s.p;
         aa.counts = c->counts.p;
         aa.offs = c->offs.p;
-        CK(launch_admit(aa, n_plans, maxc, c->stream));
+        LAUNCH(c, launch_admit(aa, n_plans, maxc, c->stream));
         CK(cudaStreamSynchronize(c->stream));
     } catch (...) {
         for (int32_t s : sl) c->book.free_slots.insert(s);
@@ -1005,9 +1043,9 @@ void clear_rows(fmdp_ctx* c, int64_t a, int64_t b) {
     if (b <= a) return;
     if (b - a >= c->T_win) {
         const size_t n = (size_t)c->T_win * c->S_pad;
-        CK(launch_fill_nan(c->X, n, c->stream));
-        CK(launch_fill_nan(c->Y, n, c->stream));
-        CK(launch_fill_nan(c->Z, n, c->stream));
+        LAUNCH(c, launch_fill_nan(c->X, n, c->stream));
+        LAUNCH(c, launch_fill_nan(c->Y, n, c->stream));
+        LAUNCH(c, launch_fill_nan(c->Z, n, c->stream));
         return;
     }
     int64_t ra = a % c->T_win;
@@ -1016,9 +1054,9 @@ void clear_rows(fmdp_ctx* c, int64_t a, int64_t b) {
     while (len > 0) {
         const int64_t run = std::min<int64_t>(len, c->T_win - ra);
         const size_t off = (size_t)ra * c->S_pad, n = (size_t)run * c->S_pad;
-        CK(launch_fill_nan(c->X + off, n, c->stream));
-        CK(launch_fill_nan(c->Y + off, n, c->stream));
-        CK(launch_fill_nan(c->Z + off, n, c->stream));
+        LAUNCH(c, launch_fill_nan(c->X + off, n, c->stream));
+        LAUNCH(c, launch_fill_nan(c->Y + off, n, c->stream));
+        LAUNCH(c, launch_fill_nan(c->Z + off, n, c->stream));
         len -= run;
         ra = 0;
     }
@@ -1174,9 +1212,9 @@ fmdp_status fmdp_create(const fmdp_airspace* air, double gamma, const fmdp_actio
         CK(cudaMalloc(&c->X, plane * sizeof(float)));
         CK(cudaMalloc(&c->Y, plane * sizeof(float)));
         CK(cudaMalloc(&c->Z, plane * sizeof(float)));
-        CK(launch_fill_nan(c->X, plane, c->stream));
-        CK(launch_fill_nan(c->Y, plane, c->stream));
-        CK(launch_fill_nan(c->Z, plane, c->stream));
+        LAUNCH(c, launch_fill_nan(c->X, plane, c->stream));
+        LAUNCH(c, launch_fill_nan(c->Y, plane, c->stream));
+        LAUNCH(c, launch_fill_nan(c->Z, plane, c->stream));
         if (a.heightmap) {
             const size_t nh = (size_t)a.hm_nx * a.hm_ny;
             CK(cudaMalloc(&c->hm, nh * sizeof(float)));
@@ -1271,13 +1309,21 @@ fmdp_status fmdp_stage_requests(fmdp_ctx* c, const fmdp_request* reqs, int32_t n
     });
 }
 
-fmdp_status fmdp_schedule_staged(fmdp_ctx* c, int32_t* n_admitted) {
+fmdp_status fmdp_schedule_staged(fmdp_ctx* c, int32_t batched, int32_t* n_admitted) {
     if (!c) return FMDP_ERR_ARG;
     return guard(c, [&] {
         const int32_t n = (int32_t)c->staged.size();
         require(n > 0, FMDP_ERR_ARG, "no staged requests");
         require((size_t)n <= c->book.free_slots.size(), FMDP_ERR_FULL, "not enough free slots for the staged run");
-        const int32_t adm = run_fcfs(c, c->staged.data(), n, nullptr, true);
+        c->staged_done = false;
+        int32_t adm;
+        if (batched) {
+            c->staged_res.assign(n, fmdp_result{});
+            adm = run_batch(c, c->staged.data(), n, c->staged_res.data(), c->stg.reqs.p, true);
+        } else {
+            adm = run_fcfs(c, c->staged.data(), n, nullptr, true);
+        }
+        c->staged_batched = batched != 0;
         c->staged_done = true;
         if (n_admitted) *n_admitted = adm;
     });
@@ -1288,6 +1334,26 @@ fmdp_status fmdp_fetch_staged(fmdp_ctx* c, fmdp_result* res, int32_t n) {
     return guard(c, [&] {
         require(c->staged_done, FMDP_ERR_ARG, "no finished staged run");
         require(res && n == (int32_t)c->staged.size(), FMDP_ERR_ARG, "result count must equal the staged count");
+        if (c->staged_batched) {
+            const BatchBuffers& B = c->bat;
+            c->h_traj.ensure((size_t)n * B.cap * 3);
+            c->h_acts.ensure((size_t)n * B.cap);
+            CK(cudaMemcpyAsync(c->h_traj.p, B.traj.p, (size_t)n * B.cap * 3 * sizeof(float), cudaMemcpyDeviceToHost,
+                               c->stream));
+            CK(cudaMemcpyAsync(c->h_acts.p, B.acts.p, (size_t)n * B.cap, cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaStreamSynchronize(c->stream));
+            for (int32_t i = 0; i < n; ++i) {
+                float* xyz = res[i].xyz;
+                uint8_t* acts = res[i].actions;
+                res[i] = c->staged_res[i];
+                res[i].xyz = xyz;
+                res[i].actions = acts;
+                const int32_t np = res[i].n_points;
+                if (xyz) std::memcpy(xyz, c->h_traj.p + (size_t)i * B.cap * 3, (size_t)np * 12);
+                if (acts && np > 1) std::memcpy(acts, c->h_acts.p + (size_t)i * B.cap, (size_t)np - 1);
+            }
+            return;
+        }
         const int32_t cap = c->staged_cap;
         c->h_traj.ensure((size_t)n * cap * 3);
         c->h_acts.ensure((size_t)n * cap);
@@ -1314,7 +1380,7 @@ fmdp_status fmdp_schedule_batch(fmdp_ctx* c, const fmdp_request* reqs, int32_t n
     return guard(c, [&] {
         require(n >= 0 && (n == 0 || (reqs && res)), FMDP_ERR_ARG, "null requests or results");
         for (int32_t i = 0; i < n; ++i) check_request(c, reqs[i]);
-        run_batch(c, reqs, n, res);
+        run_batch(c, reqs, n, res, nullptr, false);
     });
 }
 
@@ -1421,9 +1487,9 @@ fmdp_status fmdp_clear(fmdp_ctx* c) {
     if (!c) return FMDP_ERR_ARG;
     return guard(c, [&] {
         const size_t plane = (size_t)c->T_win * c->S_pad;
-        CK(launch_fill_nan(c->X, plane, c->stream));
-        CK(launch_fill_nan(c->Y, plane, c->stream));
-        CK(launch_fill_nan(c->Z, plane, c->stream));
+        LAUNCH(c, launch_fill_nan(c->X, plane, c->stream));
+        LAUNCH(c, launch_fill_nan(c->Y, plane, c->stream));
+        LAUNCH(c, launch_fill_nan(c->Z, plane, c->stream));
         CK(cudaStreamSynchronize(c->stream));
         const int64_t tb = c->book.t_base;
         c->book = Book();
@@ -1468,7 +1534,7 @@ fmdp_status fmdp_rollout_trace(fmdp_ctx* c, const fmdp_request* req, fmdp_result
         ra.hd_trace = c->hd_trace.p;
         ra.tie_trace = c->tie_trace.p;
         ra.err = c->err;
-        CK(launch_rollout(ra, g.threads, g.smem, c->stream));
+        LAUNCH(c, launch_rollout(ra, g.threads, g.smem, c->stream));
         RolloutOut ro;
         CK(cudaMemcpyAsync(&ro, c->rout.p, sizeof(ro), cudaMemcpyDeviceToHost, c->stream));
         CK(cudaStreamSynchronize(c->stream));
@@ -1501,7 +1567,7 @@ fmdp_status fmdp_sep_check(fmdp_ctx* c, int64_t t0, const float* xyz, int32_t n,
         c->traj.ensure((size_t)n * 3);
         c->sepo.ensure(1);
         CK(cudaMemcpyAsync(c->traj.p, xyz, (size_t)n * 12, cudaMemcpyHostToDevice, c->stream));
-        CK(launch_sep_reset(c->sepo.p, 1, c->stream));
+        LAUNCH(c, launch_sep_reset(c->sepo.p, 1, c->stream));
         SepArgs sa{};
         sa.m = c->model;
         sa.tab = table_view(c);
@@ -1515,7 +1581,7 @@ fmdp_status fmdp_sep_check(fmdp_ctx* c, int64_t t0, const float* xyz, int32_t n,
         sa.out = c->sepo.p;
         {
             KernelTimer t(c, 1);
-            CK(launch_sepcheck(sa, 1, n, c->stream));
+            LAUNCH(c, launch_sepcheck(sa, 1, n, c->stream));
             t.stop();
         }
         SepOut so;

@@ -179,7 +179,7 @@ struct MinSepArgs {
     const float* traj;       // [n][cap][3]
     const RolloutOut* rout;
     const fmdp_request* reqs;
-    int32_t cap, n;
+    int32_t cap, k0, n;      // requests k0 .. k0 + n - 1
     const int32_t* adm;      // admitted request indices, ascending
     int32_t n_adm;
     double sep_h, sep_v;

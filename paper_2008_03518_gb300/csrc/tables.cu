@@ -241,8 +241,8 @@ cudaError_t launch_admit(const AdmitArgs& a, int n_req, int max_points, cudaStre
 // verdict are final once no earlier admission influences it, but its minimum distances
 // to plans far away still see every earlier admission, as a sequential run would.
 __global__ void __launch_bounds__(256) batch_minsep_kernel(const __grid_constant__ MinSepArgs a) {
-    const int k = blockIdx.x;
-    if (k >= a.n) return;
+    if ((int)blockIdx.x >= a.n) return;
+    const int k = a.k0 + (int)blockIdx.x;
     const SepConsts sk = sep_consts(a.sep_h, a.sep_v);
     const int nk = a.rout[k].n_points;
     const int64_t tk = a.reqs[k].depart_step;

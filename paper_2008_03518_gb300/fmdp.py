@@ -84,7 +84,8 @@ class Stats(ctypes.Structure):
                 ("threads_per_cta", ctypes.c_int32), ("slots_per_cta", ctypes.c_int32),
                 ("reserved", ctypes.c_int32), ("phase_cycles", ctypes.c_int64 * 6),
                 ("batch_waves", ctypes.c_int64), ("batch_rollouts", ctypes.c_int64), ("batch_replans", ctypes.c_int64),
-                ("influence_launches", ctypes.c_int64), ("influence_ms", ctypes.c_double)]
+                ("influence_launches", ctypes.c_int64), ("influence_ms", ctypes.c_double),
+                ("kernel_launches", ctypes.c_int64)]
 
 
 # every exported symbol of include/fmdp.h
@@ -129,7 +130,7 @@ def load(build_if_missing: bool = True):
         getattr(L, name).argtypes = [vp, P(Request), c.c_int32, P(Result)]
     L.fmdp_schedule.argtypes = [vp, P(Request), P(Result)]
     L.fmdp_stage_requests.argtypes = [vp, P(Request), c.c_int32]
-    L.fmdp_schedule_staged.argtypes = [vp, P(c.c_int32)]
+    L.fmdp_schedule_staged.argtypes = [vp, c.c_int32, P(c.c_int32)]
     L.fmdp_fetch_staged.argtypes = [vp, P(Result), c.c_int32]
     L.fmdp_query_plans.argtypes = [vp, c.c_int64, c.c_int64, P(c.c_uint64), c.c_int32, P(c.c_int32)]
     L.fmdp_get_plan.argtypes = [vp, c.c_uint64, P(c.c_int64), _fp, c.c_int32, P(c.c_int32)]
@@ -358,9 +359,9 @@ class Scheduler:
         self._staged = (Request * n)(*[make_request(reqs[i]) for i in range(n)])
         self._check(self._L.fmdp_stage_requests(self._h, self._staged, n))
 
-    def schedule_staged(self):
+    def schedule_staged(self, batched=False):
         n = ctypes.c_int32()
-        self._check(self._L.fmdp_schedule_staged(self._h, ctypes.byref(n)))
+        self._check(self._L.fmdp_schedule_staged(self._h, int(bool(batched)), ctypes.byref(n)))
         return n.value
 
     def fetch_staged(self):

@@ -158,3 +158,22 @@ def test_c3_full_size_batch_of_256():
     assert st["batch_rollouts"] >= 256
     o = oracle_for(sc)
     fcfs_parity(None, o, reqs[:6], gpu_results=bat[:6])
+
+
+@pytest.mark.parametrize("batch_size", [0, 16])
+def test_staged_batch_equals_sequential(batch_size):
+    """The device-resident batched run (requests staged once, trajectories left on the
+    device and fetched afterwards) gives the sequential results."""
+    sc = S.c1_plain_small()
+    with Scheduler.from_scenario(sc, batch_size=batch_size) as s:
+        s.snapshot()
+        many = s.schedule_many(sc.requests)
+        s.restore()
+        s.stage(sc.requests)
+        s.set_profiling(0)
+        n_adm = s.schedule_staged(batched=True)
+        st = s.stats()
+        got = s.fetch_staged()
+    same_results(many, got)
+    assert n_adm == sum(r["verdict"] == ADMITTED for r in many)
+    assert st["batch_waves"] >= 1 and st["kernel_launches"] >= 5 * st["batch_waves"]
