@@ -154,12 +154,13 @@ def run_reference(args, sc):
     print(json.dumps(line), flush=True)
 
 
-def workload_config(sc, n_req):
+def workload_config(sc, n_req, mode="batched"):
     return {"workload": sc.name, "known_plans": len(sc.plans), "requests_per_step": n_req,
             "actions": len(sc.actions), "max_horizon": int(sc.requests["horizon"].max()),
             "airspace_km": [round((sc.box[3] - sc.box[0]) / 1000), round((sc.box[4] - sc.box[1]) / 1000),
                             round((sc.box[5] - sc.box[2]) / 1000, 1)],
-            "mode": "FCFS through speculative batches of 256 (results identical to sequential FCFS)",
+            "mode": ("FCFS through speculative batches of 256 (results identical to sequential FCFS)"
+                     if mode == "batched" else "FCFS one request at a time"),
             "l2": "plan table (3 x 4096 x S fp32 planes) larger than L2 and rewritten by the restore every step",
             "parallelism": "replicas"}
 
@@ -190,6 +191,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-modes", action="store_true")
+    ap.add_argument("--mode", default="batched", choices=["batched", "sequential"],
+                    help="path timed for value: speculative batches (default) or one request at a time")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -232,7 +235,7 @@ def main():
     s.stage(sc.requests)
     n_req = len(sc.requests)
 
-    def step(batched=True):
+    def step(batched=args.mode == "batched"):
         s.restore()
         return s.schedule_staged(batched)
 
@@ -329,7 +332,7 @@ def main():
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(sc, n_req),
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(sc, n_req, args.mode),
             "admitted_per_step": admitted, "batch": batch_stats, "modes": modes, "e2e": e2e,
             "gpu_launches": gpu_launches, "roofline": roofline, "clocks": clk}
     if rank == 0 and world == 1 and not args.no_cpu:

@@ -91,6 +91,15 @@ typedef struct {
     int32_t threads_per_cta;  /* 0 = automatic; else a multiple of 32 in [128, 384] */
     int32_t batch_size;       /* fmdp_schedule_batch: requests per speculative batch
                                  (0 = 256; at most 1024) */
+    int32_t full_scan;        /* 1: rollouts scan every slot of each step (no spatial index);
+                                 0: they read the plans near the state from the index. Same
+                                 results either way. */
+    double index_vmax_mps;    /* index: plans faster than this (m/s) are scanned at every
+                                 step (0 = 50) */
+    double index_cell_m;      /* index: cell edge in metres (0 = automatic) */
+    int32_t index_stage_items; /* index: plan samples a rollout step stages in shared memory
+                                  (0 = 1536; more are read from global memory) */
+    int32_t reserved;
 } fmdp_options;
 
 /* Fills *o with the defaults (max combine, Table 3 wells, goal 200, W = 1, automatic). */
@@ -244,6 +253,7 @@ typedef struct {
     int64_t influence_launches;  /* influence-test launches (on = 1) */
     double influence_ms;         /* their summed CUDA-event durations */
     int64_t kernel_launches;     /* every kernel launch of the library, graph nodes included */
+    int64_t items_scanned;       /* indexed rollouts: plan samples read by their steps (on >= 1) */
 } fmdp_stats;
 /* on = 1: per-kernel CUDA-event timing on the context's stream; on = 2: additionally
  * per-phase cycle counters inside the rollout kernel (diagnostic, slows it slightly);

@@ -180,6 +180,18 @@ struct fmdp_ctx {
     double* statics = nullptr;
     int32_t* err = nullptr;
 
+    // spatial index of the plan table (one CSR per ring row)
+    bool index_on = false;
+    int32_t* ix_cstart = nullptr;
+    int32_t* ix_nextra = nullptr;
+    int32_t* ix_dirty = nullptr;
+    float4* ix_items = nullptr;
+    int32_t ix_ncx = 0, ix_ncy = 0, ix_ncell = 0;
+    float ix_x0 = 0.f, ix_y0 = 0.f, ix_inv = 0.f, ix_vmax = 0.f;
+    size_t ix_smem = 0;
+    int32_t icap = 1536;
+    unsigned long long* items_ctr = nullptr;
+
     // work buffers
     SeqBuffers seq;     // fmdp_schedule / fmdp_schedule_many
     SeqBuffers stg;     // staged (device-resident) runs
@@ -346,6 +358,83 @@ void collect_timers(fmdp_ctx* c) {
     c->ev_next = 0;
 }
 
+// ------------------------------------------------------------------ spatial index
+
+constexpr int32_t kExtraLimit = 48;  // appended items per row before the row is rebuilt
+
+IndexArgs index_args(fmdp_ctx* c) {
+    IndexArgs a{};
+    a.tab = table_view(c);
+    a.cstart = c->ix_cstart;
+    a.nextra = c->ix_nextra;
+    a.dirty = c->ix_dirty;
+    a.items = c->ix_items;
+    a.ncx = c->ix_ncx;
+    a.ncy = c->ix_ncy;
+    a.ncell = c->ix_ncell;
+    a.x0 = c->ix_x0;
+    a.y0 = c->ix_y0;
+    a.inv_cell = c->ix_inv;
+    a.vmax = c->ix_vmax;
+    a.inv_dt = (float)(1.0 / c->air.dt);
+    a.extra_limit = kExtraLimit;
+    return a;
+}
+
+IndexView index_view(fmdp_ctx* c) {
+    IndexView v{};
+    v.cstart = c->ix_cstart;
+    v.nextra = c->ix_nextra;
+    v.items = c->ix_items;
+    v.ncx = c->ix_ncx;
+    v.ncy = c->ix_ncy;
+    v.ncell = c->ix_ncell;
+    v.x0 = c->ix_x0;
+    v.y0 = c->ix_y0;
+    v.inv_cell = c->ix_inv;
+    v.vmax = c->ix_vmax;
+    return v;
+}
+
+void set_index_args(fmdp_ctx* c, RolloutArgs& ra) {
+    ra.indexed = c->index_on ? 1 : 0;
+    ra.icap = c->icap;
+    ra.iv = index_view(c);
+    ra.items_ctr = (c->index_on && c->profiling && !c->capturing) ? c->items_ctr : nullptr;
+}
+
+// rebuilds the index rows of steps [a, b) (at most one window length)
+void index_rebuild(fmdp_ctx* c, int64_t a, int64_t b, bool dirty_only) {
+    if (!c->index_on || b <= a) return;
+    const int32_t n = (int32_t)std::min<int64_t>(b - a, c->T_win);
+    LAUNCH(c, launch_index_build(index_args(c), a, n, dirty_only ? 1 : 0, c->ix_smem, c->stream));
+}
+void index_rebuild_all(fmdp_ctx* c) { index_rebuild(c, c->book.t_base, c->book.t_base + c->T_win, false); }
+void index_reset(fmdp_ctx* c) {
+    if (!c->index_on) return;
+    CK(cudaMemsetAsync(c->ix_cstart, 0, ((size_t)c->T_win * (c->ix_ncell + 1) + 16) * sizeof(int32_t), c->stream));
+    CK(cudaMemsetAsync(c->ix_nextra, 0, ((size_t)c->T_win + 16) * sizeof(int32_t), c->stream));
+    CK(cudaMemsetAsync(c->ix_dirty, 0, (size_t)c->T_win * sizeof(int32_t), c->stream));
+}
+// Appends admitted trajectories (request work items; see IndexAppendArgs) to the extra
+// lists of their rows, then rebuilds the rows that grew past the limit among [a, b).
+void index_append_admitted(fmdp_ctx* c, const float* traj, int32_t cap, const RolloutOut* rout,
+                           const fmdp_request* reqs, const SepOut* sep, const int32_t* idx, const int32_t* n_dev,
+                           int32_t n_items, int64_t a, int64_t b) {
+    if (!c->index_on) return;
+    IndexAppendArgs ia{};
+    ia.ix = index_args(c);
+    ia.traj = traj;
+    ia.cap = cap;
+    ia.rout = rout;
+    ia.reqs = reqs;
+    ia.sep = sep;
+    ia.idx = idx;
+    ia.n_dev = n_dev;
+    LAUNCH(c, launch_index_append(ia, n_items, cap, c->stream));
+    index_rebuild(c, a, b, true);
+}
+
 // ------------------------------------------------------------------ launch geometry
 
 struct Geometry {
@@ -361,14 +450,31 @@ bool fit_geometry(fmdp_ctx* c, Geometry& g, int cs) {
     g.threads = c->opt.threads_per_cta > 0 ? c->opt.threads_per_cta : (g.chunk > 256 ? 384 : 256);
     for (int depth : {8, 4}) {
         g.ring = depth;
-        g.smem = rollout_smem_bytes(g.chunk, depth);
+        g.smem = rollout_smem_bytes(g.chunk, depth, 0);
         if ((int)g.smem <= c->max_smem) return true;
     }
     return false;
 }
 
+// Indexed geometry: one CTA per request staging only the plans near its state.
+Geometry geometry_indexed(fmdp_ctx* c, int32_t S_scan) {
+    Geometry g;
+    g.S_scan = S_scan;
+    g.cs = 1;
+    g.chunk = 0;
+    g.ring = 4;
+    g.threads = c->opt.threads_per_cta > 0 ? c->opt.threads_per_cta : 384;
+    g.smem = rollout_smem_bytes(0, 0, c->icap);
+    require((int)g.smem <= c->max_smem, FMDP_ERR_ARG, "index staging buffers exceed shared memory");
+    c->last_cs = 1;
+    c->last_threads = g.threads;
+    c->last_chunk = 0;
+    return g;
+}
+
 // Latency geometry (one request at a time): about 1024 slots per CTA.
 Geometry geometry(fmdp_ctx* c, int32_t S_hw) {
+    if (c->index_on) return geometry_indexed(c, round_up(std::max(S_hw, 0), 32));
     Geometry g;
     g.S_scan = round_up(std::max(S_hw, 0), 32);
     int cs = c->opt.cluster_size;
@@ -417,7 +523,8 @@ void recompute_hw(fmdp_ctx* c) {
 
 // Enqueue rollout -> sep_check -> admission for n requests (device array c->reqs, slots in
 // c->slots) in FCFS order on the context's stream.
-void enqueue_sequence(fmdp_ctx* c, SeqBuffers& B, int32_t n, int32_t cap, const Geometry& g) {
+void enqueue_sequence(fmdp_ctx* c, SeqBuffers& B, const fmdp_request* host_reqs, int32_t n, int32_t cap,
+                      const Geometry& g) {
     const TableView tv = table_view(c);
     LAUNCH(c, launch_sep_reset(B.sepo.p, n, c->stream));
     for (int32_t i = 0; i < n; ++i) {
@@ -436,6 +543,7 @@ void enqueue_sequence(fmdp_ctx* c, SeqBuffers& B, int32_t n, int32_t cap, const 
         ra.acts = B.acts.p + (size_t)i * cap;
         ra.out = B.rout.p + i;
         ra.err = c->err;
+        set_index_args(c, ra);
         ra.phase = c->phase_timing ? c->phase.p : nullptr;
         {
             KernelTimer t(c, 0);
@@ -470,6 +578,10 @@ void enqueue_sequence(fmdp_ctx* c, SeqBuffers& B, int32_t n, int32_t cap, const 
             LAUNCH(c, launch_admit(aa, 1, cap, c->stream));
             t.stop();
         }
+        // an admitted trajectory joins the index before the next request plans
+        const int64_t d0 = host_reqs[i].depart_step;
+        index_append_admitted(c, ra.traj, cap, ra.out, ra.reqs, sa.out, nullptr, nullptr, 1, d0,
+                              d0 + host_reqs[i].horizon + 1);
     }
 }
 
@@ -531,7 +643,7 @@ int32_t run_fcfs(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_result* 
             }
             B.slots.ensure(m);
             CK(cudaMemcpyAsync(B.slots.p, sl.data(), m * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
-            enqueue_sequence(c, B, m, cap, g);
+            enqueue_sequence(c, B, reqs + done, m, cap, g);
             c->h_rout.ensure(m);
             c->h_sep.ensure(m);
             CK(cudaMemcpyAsync(c->h_rout.p, B.rout.p, m * sizeof(RolloutOut), cudaMemcpyDeviceToHost, c->stream));
@@ -599,12 +711,13 @@ int32_t run_fcfs(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_result* 
 
 constexpr int32_t kBatchDefault = 256;
 constexpr int32_t kBatchMax = 1024;
-constexpr int kSepPointBlocks = 64;  // sep_check blocks per request along its trajectory
-constexpr int kWaveKernels = 5;      // kernels of one wave: admit, reset, rollout, sep_check, influence
+// kernels of one wave: admit, reset, rollout, sep_check, influence (+ index append, rebuild)
+int wave_kernels(const fmdp_ctx* c) { return c->index_on ? 7 : 5; }
 
 // Batch geometry: the narrowest cluster whose partition fits one CTA's shared memory, so
 // that as many rollouts as possible run side by side.
 Geometry geometry_batch(fmdp_ctx* c, int32_t S) {
+    if (c->index_on) return geometry_indexed(c, std::min(round_up(std::max(S, 0), 32), c->S_pad));
     Geometry g;
     g.S_scan = std::min(round_up(std::max(S, 0), 32), c->S_pad);
     int cs = c->opt.cluster_size > 0 ? c->opt.cluster_size : 1;
@@ -656,6 +769,8 @@ void enqueue_wave(fmdp_ctx* c, const Geometry& g, int n_clusters, BatchBuffers& 
         KernelTimer t(c, timed ? 2 : -1);
         LAUNCH(c, launch_admit(aa, n_cap, cap, s));
         t.stop();
+        index_append_admitted(c, B.traj.p, cap, B.rout.p, B.rq, B.sepo.p, store, B.ctr.p + 3, n_cap,
+                              c->book.t_base, c->book.t_base + c->T_win);
     }
     LAUNCH(c, launch_sep_reset_idx(B.sepo.p, todo, B.ctr.p + 1, n_cap, s));
     {
@@ -673,6 +788,7 @@ void enqueue_wave(fmdp_ctx* c, const Geometry& g, int n_clusters, BatchBuffers& 
         ra.acts = B.acts.p;
         ra.out = B.rout.p;
         ra.err = c->err;
+        set_index_args(c, ra);
         ra.phase = (timed && c->phase_timing) ? c->phase.p : nullptr;
         ra.queue = B.ctr.p;
         ra.idx = todo;
@@ -682,19 +798,26 @@ void enqueue_wave(fmdp_ctx* c, const Geometry& g, int n_clusters, BatchBuffers& 
         t.stop();
     }
     {
-        SepArgs sa{};
+        SepRowsArgs sa{};
         sa.m = c->model;
         sa.tab = tv;
         sa.S_scan = g.S_scan;
-        sa.cap = cap;
         sa.traj = B.traj.p;
+        sa.cap = cap;
         sa.rout = B.rout.p;
         sa.reqs = B.rq;
-        sa.out = B.sepo.p;
         sa.idx = todo;
         sa.n_dev = B.ctr.p + 1;
+        sa.n_max = n_cap;
+        sa.out = B.sepo.p;
+        if (c->index_on) {
+            sa.items = c->ix_items;
+            sa.cstart = c->ix_cstart;
+            sa.nextra = c->ix_nextra;
+            sa.ncell = c->ix_ncell;
+        }
         KernelTimer t(c, timed ? 1 : -1);
-        LAUNCH(c, launch_sepcheck(sa, n_cap, kSepPointBlocks, s));
+        LAUNCH(c, launch_sepcheck_rows(sa, s));
         t.stop();
     }
     {
@@ -811,7 +934,7 @@ int32_t run_batch_chunk(fmdp_ctx* c, const fmdp_request* reqs, int32_t b0, int32
             B.h_ctr.p[3] = (int32_t)store.size();
             if (graphs) {
                 CK(cudaGraphLaunch(wave_graph(c, g, n_clusters, B), c->stream));
-                c->stats.kernel_launches += kWaveKernels;
+                c->stats.kernel_launches += wave_kernels(c);
             } else {
                 enqueue_wave(c, g, n_clusters, B, true);
             }
@@ -892,6 +1015,8 @@ int32_t run_batch_chunk(fmdp_ctx* c, const fmdp_request* reqs, int32_t b0, int32
             KernelTimer t(c, 2);
             LAUNCH(c, launch_admit(aa, n_cap, B.cap, c->stream));
             t.stop();
+            index_append_admitted(c, B.traj.p, B.cap, B.rout.p, B.rq, B.sepo.p, aa.idx, aa.n_dev, n_cap,
+                                  c->book.t_base, c->book.t_base + c->T_win);
         }
         MinSepArgs ma{};
         ma.traj = B.traj.p;
@@ -1025,6 +1150,26 @@ void store_plans(fmdp_ctx* c, int32_t n_plans, const int64_t* t0s, const int32_t
         aa.counts = c->counts.p;
         aa.offs = c->offs.p;
         LAUNCH(c, launch_admit(aa, n_plans, maxc, c->stream));
+        if (c->index_on) {
+            int64_t tlo = t0s[0], thi = t0s[0];
+            for (int32_t i = 0; i < n_plans; ++i) {
+                tlo = std::min(tlo, t0s[i]);
+                thi = std::max(thi, t0s[i] + counts[i]);
+            }
+            if (n_plans <= 8) {  // a few plans: append them to their rows' extra lists
+                IndexAppendArgs ia{};
+                ia.ix = index_args(c);
+                ia.traj = c->traj.p;
+                ia.force = 1;
+                ia.t0s = c->t0s.p;
+                ia.counts = c->counts.p;
+                ia.offs = c->offs.p;
+                LAUNCH(c, launch_index_append(ia, n_plans, maxc, c->stream));
+                index_rebuild(c, tlo, thi, true);
+            } else {
+                index_rebuild(c, tlo, thi, false);
+            }
+        }
         CK(cudaStreamSynchronize(c->stream));
     } catch (...) {
         for (int32_t s : sl) c->book.free_slots.insert(s);
@@ -1038,7 +1183,7 @@ void store_plans(fmdp_ctx* c, int32_t n_plans, const int64_t* t0s, const int32_t
     }
 }
 
-// clears table rows for steps [a, b) (clipped to one window length)
+// clears table rows for steps [a, b) (clipped to one window length), index rows with them
 void clear_rows(fmdp_ctx* c, int64_t a, int64_t b) {
     if (b <= a) return;
     if (b - a >= c->T_win) {
@@ -1046,6 +1191,7 @@ void clear_rows(fmdp_ctx* c, int64_t a, int64_t b) {
         LAUNCH(c, launch_fill_nan(c->X, n, c->stream));
         LAUNCH(c, launch_fill_nan(c->Y, n, c->stream));
         LAUNCH(c, launch_fill_nan(c->Z, n, c->stream));
+        index_reset(c);
         return;
     }
     int64_t ra = a % c->T_win;
@@ -1060,6 +1206,7 @@ void clear_rows(fmdp_ctx* c, int64_t a, int64_t b) {
         len -= run;
         ra = 0;
     }
+    index_rebuild(c, a, b, false);  // the cleared rows hold no items
 }
 
 void destroy_ctx(fmdp_ctx* c) {
@@ -1070,6 +1217,9 @@ void destroy_ctx(fmdp_ctx* c) {
     if (c->hm) cudaFree(c->hm);
     if (c->statics) cudaFree(c->statics);
     if (c->err) cudaFree(c->err);
+    for (void* p : {(void*)c->ix_cstart, (void*)c->ix_nextra, (void*)c->ix_dirty, (void*)c->ix_items,
+                    (void*)c->items_ctr})
+        if (p) cudaFree(p);
     c->seq.release(); c->stg.release(); c->bat.release();
     for (auto& g : c->graphs)
         if (g.exec) cudaGraphExecDestroy(g.exec);
@@ -1173,6 +1323,9 @@ fmdp_status fmdp_create(const fmdp_airspace* air, double gamma, const fmdp_actio
                                            o.threads_per_cta % 32 == 0),
                 FMDP_ERR_ARG, "threads per CTA: 0 or a multiple of 32 in [128, 384]");
         require(o.batch_size >= 0 && o.batch_size <= kBatchMax, FMDP_ERR_ARG, "batch size 0..1024");
+        require(o.index_stage_items >= 0 && o.index_stage_items <= 3000, FMDP_ERR_ARG,
+                "index stage items 0..3000");
+        require(o.index_vmax_mps >= 0.0 && o.index_cell_m >= 0.0, FMDP_ERR_ARG, "index bounds must be >= 0");
         std::vector<fmdp_well> wells;
         if (o.wells && o.n_wells > 0) {
             wells.assign(o.wells, o.wells + o.n_wells);
@@ -1204,6 +1357,7 @@ fmdp_status fmdp_create(const fmdp_airspace* air, double gamma, const fmdp_actio
         CK(cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking));
         c->stream = c->own;
         CK(prepare_rollout_kernel((size_t)c->max_smem));
+        CK(prepare_sepcheck_rows(sepcheck_rows_smem(kBatchMax)));
 
         c->T_win = a.n_slices_window;
         c->S_max = a.max_slots;
@@ -1231,6 +1385,36 @@ fmdp_status fmdp_create(const fmdp_airspace* air, double gamma, const fmdp_actio
         CK(cudaMemsetAsync(c->err, 0, sizeof(int32_t), c->stream));
         for (int32_t s = 0; s < c->S_max; ++s) c->book.free_slots.insert(c->book.free_slots.end(), s);
         fill_model(c, wells, acts, a.static_wells);
+        c->index_on = o.full_scan == 0;
+        if (c->index_on) {
+            c->icap = o.index_stage_items > 0 ? o.index_stage_items : 1536;
+            // cells of about 0.6 query radii (a query then spans 3 to 5 cell rows); at most 16384
+            const double vmax = o.index_vmax_mps > 0.0 ? o.index_vmax_mps : 50.0;
+            const double W = a.x1 - a.x0, H = a.y1 - a.y0;
+            double cell = o.index_cell_m;
+            if (!(cell > 0.0)) {
+                const double rq = (double)c->model.reach_base + (double)c->model.tau_absmax * vmax + 80.0 * a.dt + 10.0;
+                cell = std::max(0.6 * rq, std::max(W, H) / 256.0);
+            }
+            while (std::ceil(W / cell) * std::ceil(H / cell) > 16384.0) cell *= 1.25;
+            c->ix_ncx = std::max(1, (int)std::ceil(W / cell));
+            c->ix_ncy = std::max(1, (int)std::ceil(H / cell));
+            c->ix_ncell = c->ix_ncx * c->ix_ncy;
+            c->ix_x0 = (float)a.x0;
+            c->ix_y0 = (float)a.y0;
+            c->ix_inv = (float)(1.0 / cell);
+            c->ix_vmax = (float)vmax;
+            // 16 words of padding: rollouts stage aligned 16-byte blocks around the words they need
+            CK(cudaMalloc(&c->ix_cstart, ((size_t)c->T_win * (c->ix_ncell + 1) + 16) * sizeof(int32_t)));
+            CK(cudaMalloc(&c->ix_nextra, ((size_t)c->T_win + 16) * sizeof(int32_t)));
+            CK(cudaMalloc(&c->ix_dirty, (size_t)c->T_win * sizeof(int32_t)));
+            CK(cudaMalloc(&c->ix_items, plane * 2 * sizeof(float4)));
+            CK(cudaMalloc(&c->items_ctr, sizeof(unsigned long long)));
+            CK(cudaMemsetAsync(c->items_ctr, 0, sizeof(unsigned long long), c->stream));
+            c->ix_smem = index_build_smem(c->ix_ncell);
+            CK(prepare_index_kernels(c->ix_smem));
+            index_reset(c);
+        }
         CK(cudaStreamSynchronize(c->stream));
     });
     if (st != FMDP_OK) {
@@ -1478,8 +1662,9 @@ fmdp_status fmdp_restore(fmdp_ctx* c) {
         CK(cudaMemcpyAsync(c->X, c->sX, plane, cudaMemcpyDeviceToDevice, c->stream));
         CK(cudaMemcpyAsync(c->Y, c->sY, plane, cudaMemcpyDeviceToDevice, c->stream));
         CK(cudaMemcpyAsync(c->Z, c->sZ, plane, cudaMemcpyDeviceToDevice, c->stream));
-        CK(cudaStreamSynchronize(c->stream));
         c->book = c->snap;
+        index_rebuild_all(c);
+        CK(cudaStreamSynchronize(c->stream));
     });
 }
 
@@ -1490,6 +1675,7 @@ fmdp_status fmdp_clear(fmdp_ctx* c) {
         LAUNCH(c, launch_fill_nan(c->X, plane, c->stream));
         LAUNCH(c, launch_fill_nan(c->Y, plane, c->stream));
         LAUNCH(c, launch_fill_nan(c->Z, plane, c->stream));
+        index_reset(c);
         CK(cudaStreamSynchronize(c->stream));
         const int64_t tb = c->book.t_base;
         c->book = Book();
@@ -1534,6 +1720,7 @@ fmdp_status fmdp_rollout_trace(fmdp_ctx* c, const fmdp_request* req, fmdp_result
         ra.hd_trace = c->hd_trace.p;
         ra.tie_trace = c->tie_trace.p;
         ra.err = c->err;
+        set_index_args(c, ra);
         LAUNCH(c, launch_rollout(ra, g.threads, g.smem, c->stream));
         RolloutOut ro;
         CK(cudaMemcpyAsync(&ro, c->rout.p, sizeof(ro), cudaMemcpyDeviceToHost, c->stream));
@@ -1608,6 +1795,7 @@ fmdp_status fmdp_set_profiling(fmdp_ctx* c, int32_t on) {
         c->stats = fmdp_stats{};
         c->pending.clear();
         c->ev_next = 0;
+        if (c->items_ctr) CK(cudaMemsetAsync(c->items_ctr, 0, sizeof(unsigned long long), c->stream));
         if (c->phase_timing) {
             c->phase.ensure(6);
             CK(cudaMemsetAsync(c->phase.p, 0, 6 * sizeof(unsigned long long), c->stream));
@@ -1625,6 +1813,12 @@ fmdp_status fmdp_get_stats(fmdp_ctx* c, fmdp_stats* out) {
             CK(cudaMemcpyAsync(ph, c->phase.p, sizeof(ph), cudaMemcpyDeviceToHost, c->stream));
             CK(cudaStreamSynchronize(c->stream));
             for (int i = 0; i < 6; ++i) out->phase_cycles[i] = (int64_t)ph[i];
+        }
+        if (c->items_ctr) {
+            unsigned long long n = 0;
+            CK(cudaMemcpyAsync(&n, c->items_ctr, sizeof(n), cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaStreamSynchronize(c->stream));
+            out->items_scanned = (int64_t)n;
         }
         out->cluster_size = c->last_cs;
         out->threads_per_cta = c->last_threads;

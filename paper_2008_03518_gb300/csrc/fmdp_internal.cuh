@@ -62,6 +62,22 @@ struct TableView {
     int64_t t_base;
 };
 
+// Spatial index of the plan table (one per ring row, rebuilt or appended as rows change).
+// Row r holds one item per slot with a sample at the row's step T: the sample p(T) and the
+// same slot's sample p(T+1) (NaN when there is none), 32 bytes. Items are grouped by the
+// 2-D cell of p(T) (ncx x ncy cells of `cell` metres over the airspace box, positions
+// outside the box clamped to the edge cells), in cell order; after the last cell comes the
+// extra list, scanned for every query: items moving faster than vmax (their wells reach
+// further than the cell query covers) and items appended since the row was last rebuilt.
+struct IndexView {
+    const int32_t* cstart;  // [T_win][ncell + 1]: first item of each cell; [ncell] = extra list start
+    const int32_t* nextra;  // [T_win]: items in the extra list
+    const float4* items;    // [T_win][S_pad][2]: {x, y, z, 0} at T and at T + 1
+    int32_t ncx, ncy, ncell;
+    float x0, y0, inv_cell;  // cell of x: floor((x - x0) * inv_cell), clamped
+    float vmax;              // speed bound of the items outside the extra list (m/s)
+};
+
 struct RolloutOut {
     int32_t n_points;
     int32_t status;  // kStatusCaptured, FMDP_REJ_HORIZON or FMDP_REJ_NO_ACTION
@@ -102,6 +118,10 @@ struct RolloutArgs {
     const int32_t* idx;    // batch mode: request index of work item w (nullptr: identity)
     const int32_t* n_dev;  // batch mode: number of work items, read on the device (nullptr: n_req)
     unsigned long long* phase;  // [6] per-phase cycle counters (diagnostic) or nullptr
+    int32_t indexed;  // 1: stage the items near the state from the spatial index (cs must be 1)
+    int32_t icap;     // indexed mode: items per staging buffer in shared memory
+    IndexView iv;
+    unsigned long long* items_ctr;  // indexed mode: items read by the steps (statistics) or nullptr
 };
 
 struct SepArgs {
@@ -167,13 +187,73 @@ void ctx_set_error(fmdp_ctx* ctx, const char* msg);
 // n_clusters > 0: persistent launch of that many clusters (work-queue mode), else one
 // cluster per request.
 cudaError_t launch_rollout(const RolloutArgs& a, int threads, size_t smem, cudaStream_t s, int n_clusters = 0);
-size_t rollout_smem_bytes(int chunk, int depth);
+size_t rollout_smem_bytes(int chunk, int depth, int icap);
 cudaError_t prepare_rollout_kernel(size_t smem);
 int rollout_max_active_clusters(int cs, int threads, size_t smem);
 cudaError_t launch_sepcheck(const SepArgs& a, int n_req, int max_points, cudaStream_t s);
 cudaError_t launch_sep_reset(SepOut* out, int n, cudaStream_t s);
 cudaError_t launch_admit(const AdmitArgs& a, int n_req, int max_points, cudaStream_t s);
 cudaError_t launch_fill_nan(float* p, size_t n, cudaStream_t s);
+
+// Spatial index maintenance. Rows are named by absolute step T (ring row T mod T_win).
+struct IndexArgs {
+    TableView tab;
+    int32_t* cstart;
+    int32_t* nextra;
+    int32_t* dirty;        // [T_win]: row must be rebuilt before its next use
+    float4* items;
+    int32_t ncx, ncy, ncell;
+    float x0, y0, inv_cell, vmax, inv_dt;
+    int32_t extra_limit;   // appended items beyond this mark the row dirty
+};
+// Rebuilds the rows of steps [T0, T0 + n) (n <= T_win); dirty_only: only rows marked dirty
+// (and clears their marks).
+cudaError_t launch_index_build(const IndexArgs& a, int64_t T0, int32_t n, int dirty_only, size_t smem, cudaStream_t s);
+size_t index_build_smem(int ncell);
+cudaError_t prepare_index_kernels(size_t smem);
+// Appends the stored trajectories of the listed requests to the extra lists of their rows:
+// requests idx[0 .. *n_dev) (or 0 .. n-1), admitted ones only (SepOut verdict), samples
+// traj[r][0 .. rout[r].n_points) from step reqs[r].depart_step.
+struct IndexAppendArgs {
+    IndexArgs ix;
+    const float* traj;
+    int32_t cap;
+    const RolloutOut* rout;
+    const fmdp_request* reqs;
+    const SepOut* sep;
+    const int32_t* idx;
+    const int32_t* n_dev;
+    // force mode (known plans): n plans with t0s / counts / offs into traj
+    int32_t force;
+    const int64_t* t0s;
+    const int32_t* counts;
+    const int64_t* offs;
+};
+cudaError_t launch_index_append(const IndexAppendArgs& a, int n_items, int max_points, cudaStream_t s);
+// Separation check of a batch's work items, row by row: block b takes step t_base + b, the
+// samples of every work item at that step, and the row's plan samples (from the spatial
+// index when there is one, else the table planes). Same results as sepcheck_kernel.
+struct SepRowsArgs {
+    Model m;
+    TableView tab;
+    int32_t S_scan;
+    const float* traj;  // [n][cap][3]
+    int32_t cap;
+    const RolloutOut* rout;
+    const fmdp_request* reqs;
+    const int32_t* idx;    // work items
+    const int32_t* n_dev;  // their number (<= n_max)
+    int32_t n_max;
+    SepOut* out;
+    const float4* items;    // spatial index (nullptr: read the table planes)
+    const int32_t* cstart;
+    const int32_t* nextra;
+    int32_t ncell;
+};
+cudaError_t launch_sepcheck_rows(const SepRowsArgs& a, cudaStream_t s);
+size_t sepcheck_rows_smem(int n_max);
+cudaError_t prepare_sepcheck_rows(size_t smem);
+
 // Batch epilogue: minimum separations to the batch's own admissions.
 struct MinSepArgs {
     const float* traj;       // [n][cap][3]
@@ -230,6 +310,22 @@ __device__ __forceinline__ double terrain64(const Model& m, double x, double y) 
     double hi = __dadd_rn(__dmul_rn(bx, h01), __dmul_rn(ax, h11));
     return __dadd_rn(__dmul_rn(by, lo), __dmul_rn(ay, hi));
 }
+
+// Bilinear terrain height in fp32 (the same grid and clamping as terrain64). Its error
+// against terrain64 is below 0.05 m for heights of a few hundred metres on grids of up to a
+// few thousand cells a side; callers decide in fp32 outside a band and call terrain64 inside.
+__device__ __forceinline__ float terrain32(const Model& m, float x, float y) {
+    const float gxf = (x - (float)m.box[0]) * m.hm_sx;
+    const float gyf = (y - (float)m.box[1]) * m.hm_sy;
+    int ix = (int)floorf(gxf), iy = (int)floorf(gyf);
+    ix = min(max(ix, 0), m.hm_nx - 2);
+    iy = min(max(iy, 0), m.hm_ny - 2);
+    const float ax = gxf - (float)ix, ay = gyf - (float)iy;
+    const float* r0 = m.hm + (size_t)iy * m.hm_nx + ix;
+    const float h00 = __ldg(r0), h10 = __ldg(r0 + 1), h01 = __ldg(r0 + m.hm_nx), h11 = __ldg(r0 + m.hm_nx + 1);
+    return (1.f - ay) * ((1.f - ax) * h00 + ax * h10) + ay * ((1.f - ax) * h01 + ax * h11);
+}
+constexpr float kTerrBand = 0.25f;  // metres: fp32 terrain-collision margin before an FP64 check
 
 __device__ __forceinline__ double norm3_64(double dx, double dy, double dz) {
     return __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));

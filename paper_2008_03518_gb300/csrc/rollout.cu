@@ -98,6 +98,10 @@ __device__ __forceinline__ uint32_t cluster_rank() {
     asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
     return r;
 }
+// named CTA barrier over `threads` threads (a multiple of 32, whole warps)
+__device__ __forceinline__ void named_barrier(int id, int threads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
 __device__ __forceinline__ void cluster_barrier() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
@@ -164,15 +168,33 @@ struct StepState {
 };
 
 // Shared-memory carve-up (identical on host and device).
-struct Layout {
-    size_t ring, bars, xbar, st, tabs, keys, sums, xkeys, xsums, xab, stat, aux, misc, total;
+// Indexed mode: what one staging buffer holds. The first n_s of the `total` items are in
+// shared memory; the rest are read from the index in global memory through the ranges.
+constexpr int kMaxRanges = 8;
+struct IdxMeta {
+    int total, n_s, nr, pad;
+    long long row_off;  // first float4 of the row's items
+    int beg[kMaxRanges], cnt[kMaxRanges];
 };
-__host__ __device__ inline Layout make_layout(int chunk, int depth) {
+constexpr int kIBufs = 3;  // staging buffers: the step being scanned and the next two
+
+struct Layout {
+    size_t ring, ibuf, imeta, bars, xbar, st, tabs, keys, sums, xkeys, xsums, xab, stat, aux, misc, total;
+};
+// chunk, depth: full-scan slice ring (chunk = 0 in indexed mode); icap: indexed staging
+// buffer capacity in items (0 in full-scan mode)
+__host__ __device__ inline Layout make_layout(int chunk, int depth, int icap) {
     Layout L;
     size_t o = 0;
     auto al = [&](size_t a) { o = (o + a - 1) & ~(a - 1); };
     L.ring = o;
     o += (size_t)depth * 3 * chunk * sizeof(float);
+    al(128);
+    L.ibuf = o;  // [kIBufs][icap] items of two float4
+    o += icap > 0 ? (size_t)kIBufs * icap * 2 * sizeof(float4) : 0;
+    al(16);
+    L.imeta = o;
+    o += icap > 0 ? kIBufs * sizeof(IdxMeta) : 0;
     al(16);
     L.bars = o;
     o += kRingDepth * sizeof(uint64_t);
@@ -426,7 +448,11 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
     const int c_len = max(0, min(chunk, a.S_scan - c_begin));
     const int depth = a.ring;                    // 4 or 8 slices
     const int dshift = depth == 8 ? 3 : 2;
-    const Layout L = make_layout(chunk, depth);
+    const bool indexed = a.indexed != 0;
+    const int icap = a.icap;
+    const Layout L = make_layout(chunk, depth, indexed ? icap : 0);
+    float4* ibuf = reinterpret_cast<float4*>(smem + L.ibuf);
+    IdxMeta* imeta = reinterpret_cast<IdxMeta*>(smem + L.imeta);
 
     float* ring = reinterpret_cast<float*>(smem + L.ring);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.bars);
@@ -575,8 +601,123 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
         }
         return 0;
     };
+    // ---- indexed mode: the producer warp (warp 2) keeps a software pipeline over the spatial
+    // index. At step k (state s_k known) it reads the cell starts of the query for step k + 2
+    // (one cell row per lane), copies those items into a staging buffer, and waits for the
+    // items of step k + 1, copied one step earlier. It runs beside the step rather than in
+    // it: the other warps' reduction barrier leaves it out, and it joins them at the start
+    // of the next step. The query for step j, made from state s_a (a <= j - 1), covers every
+    // cell within Rq + (j - 1 - a) * step of s_a horizontally: an item whose wells can reach a
+    // successor of s_j lies within reach0 + tau_max * vmax of s_j (items outside the extra
+    // list move no faster than vmax), and s_j lies within (j - a) steps of s_a.
+    IdxMeta* imeta_all = imeta;
+    // pipeline state, identical in every lane of warp 2 (lane 0 waits, the warp follows)
+    uint32_t ifill[kIBufs] = {0u, 0u, 0u};
+    bool ipend[kIBufs] = {false, false, false};
+    const IndexView& iv = a.iv;
+    const int64_t cst_row_len = (int64_t)iv.ncell + 1;
+    auto row_of = [&](int64_t T) {
+        int64_t row = T % a.tab.T_win;
+        return row < 0 ? row + a.tab.T_win : row;
+    };
+    auto cell_of = [&](float v, float o, int n) {
+        const float f = floorf((v - o) * iv.inv_cell);
+        return f < 0.f ? 0 : (f > (float)(n - 1) ? n - 1 : (int)f);
+    };
+    auto excl_scan = [&](int v, int& total) {  // warp exclusive prefix sum
+        int x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(kFull, x, o);
+            if (lane >= o) x += y;
+        }
+        total = __shfl_sync(kFull, x, 31);
+        return x - v;
+    };
+    // bounded wait (lane 0) on a buffer's mbarrier; returns 1 on timeout, in every lane
+    auto wait_bar = [&](uint64_t* bar, uint32_t& fills, bool& pend) -> int {
+        if (!pend) return 0;
+        int bad = 0;
+        if (lane == 0) {
+            bad = mbar_wait_bounded(bar, fills & 1u) ? 0 : 1;
+            if (bad) atomicExch(a.err, FMDP_ERR_TIMEOUT);
+        }
+        bad = __shfl_sync(kFull, bad, 0);
+        ++fills;
+        pend = false;
+        return bad;
+    };
+    // lanes 0 .. kMaxRanges-1 each carry one item range (cnt 0: none): record them in
+    // buffer b's metadata and copy the first icap items into shared memory
+    auto issue_items = [&](int b, int my_beg, int my_cnt, long long row_off) {
+        IdxMeta& M = imeta_all[b];
+        int total;
+        const int off = excl_scan(lane < kMaxRanges ? my_cnt : 0, total);
+        const int n_s = min(total, icap);
+        if (lane < kMaxRanges) {
+            M.beg[lane] = my_beg;
+            M.cnt[lane] = my_cnt;
+        }
+        if (lane == 0) {
+            M.total = total;
+            M.n_s = n_s;
+            M.nr = kMaxRanges;
+            M.row_off = row_off;
+            if (a.items_ctr && total > 0) atomicAdd(a.items_ctr, (unsigned long long)total);
+            if (n_s > 0) mbar_arrive_expect_tx(&bars[b], (uint32_t)n_s * 32u);
+            else mbar_arrive(&bars[b]);
+        }
+        __syncwarp();
+        const int take = lane < kMaxRanges ? max(0, min(my_cnt, n_s - off)) : 0;
+        if (take > 0)
+            tma_bulk_load(ibuf + ((size_t)b * icap + off) * 2, iv.items + row_off + (long long)my_beg * 2,
+                          (uint32_t)take * 32u, &bars[b]);
+        ipend[b] = true;
+    };
+    // cell box of a query; lanes 0 .. nrows-1 take one cell row each (whole: one range over
+    // full cell rows, its two ends in lanes 0 and 1); the extra list is range kMaxRanges-1
+    struct Box { int cx0, cx1, cy0, cy1, nrows, whole; };
+    auto box_of = [&](float sx, float sy, float R) {
+        Box q;
+        q.cx0 = cell_of(sx - R, iv.x0, iv.ncx);
+        q.cx1 = cell_of(sx + R, iv.x0, iv.ncx);
+        q.cy0 = cell_of(sy - R, iv.y0, iv.ncy);
+        q.cy1 = cell_of(sy + R, iv.y0, iv.ncy);
+        q.nrows = q.cy1 - q.cy0 + 1;
+        q.whole = q.nrows > kMaxRanges - 1;
+        return q;
+    };
+    // prologue form: read the cell starts directly
+    auto issue_direct = [&](int b, int64_t T, float sx, float sy, float R) {
+        int my_beg = 0, my_cnt = 0;
+        long long row_off = 0;
+        if (T >= t_lo && T < t_hi) {
+            const int64_t row = row_of(T);
+            const int32_t* cs_row = iv.cstart + row * cst_row_len;
+            const Box q = box_of(sx, sy, R);
+            int e0 = 0, e1 = 0;
+            if (!q.whole && lane < q.nrows) {
+                e0 = cs_row[(q.cy0 + lane) * iv.ncx + q.cx0];
+                e1 = cs_row[(q.cy0 + lane) * iv.ncx + q.cx1 + 1];
+            } else if (q.whole && lane == 0) {
+                e0 = cs_row[q.cy0 * iv.ncx];
+                e1 = cs_row[(q.cy1 + 1) * iv.ncx];
+            } else if (lane == kMaxRanges - 1) {
+                e0 = cs_row[iv.ncell];
+                e1 = e0 + iv.nextra[row];
+            }
+            my_beg = e0;
+            my_cnt = max(0, e1 - e0);
+            row_off = (long long)row * a.tab.S_pad * 2;
+        }
+        issue_items(b, my_beg, my_cnt, row_off);
+    };
+    // all outstanding copies, before the buffers are reused or the CTA leaves
+    auto drain = [&]() {
+        for (int b = 0; b < kIBufs; ++b) wait_bar(&bars[b], ifill[b], ipend[b]);
+    };
+
     bool stalled = false;
-    if (producer && !st->done) {
+    if (producer && !indexed && !st->done) {
         const int64_t T1 = req.depart_step + 1;
         int64_t row = T1 % a.tab.T_win;
         if (row < 0) row += a.tab.T_win;
@@ -596,6 +737,16 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
     const double cap2 = st->cap2;
     const float reach0 = m.reach_base + stepf + dzmax;
     const float inv_dt = (float)(1.0 / m.dt);
+    const float Rq = reach0 + m.tau_absmax * a.iv.vmax * 1.0001f + stepf + 2.0f;  // indexed query radius
+    if (indexed && warp == 2 && !st->done) {
+        // steps 0 and 1 from the origin
+        const float ox = (float)req.ox, oy = (float)req.oy;
+        issue_direct(0, req.depart_step + 1, ox, oy, Rq);
+        issue_direct(1, req.depart_step + 2, ox, oy, Rq);
+        const int to = wait_bar(&bars[0], ifill[0], ipend[0]);
+        if (lane == 0) st->abort_flag[0] = to;
+        stalled = to != 0;
+    }
     float ghi[3], glo[3];  // goal as double-float
     {
         const double g0[3] = {req.gx, req.gy, req.gz};
@@ -732,9 +883,114 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
                     fold_statics(m, st, sch, scl, shx, shy, shz, slx, sly, slz, dxa, dya, dza, Dx[hn], Dy[hn], my_Dz,
                                  mloc, sloc);
             }
+        } else if (indexed && warp == 2) {
+            // ---- indexed mode: the pipeline (items for k + 2, wait for k + 1)
+            int to = 1;
+            if (!stalled) {
+                issue_direct((k + 2) % kIBufs, req.depart_step + k + 3, shx + slx, shy + sly, Rq + stepf);
+                const int b1 = (k + 1) % kIBufs;
+                to = wait_bar(&bars[b1], ifill[b1], ipend[b1]);
+                if (to) stalled = true;
+            }
+            if (lane == 0) st->abort_flag[par ^ 1] = to;
         } else {
             // ---- scanners: cull, then wells of near slots with lanes as actions
             const long long ts = (timing && tid == NT - 32) ? clock64() : 0;
+            // wells of one near slot or item ii (lanes = actions); p1 / p2: its samples at
+            // t + 1 and t + 2, used again for the FP64 decision inside a radius band
+            auto fold_near = [&](auto&& item_at, int ii, float bqx, float bqy, float bqz, float bvx, float bvy,
+                                 float bvz) {
+                if (lane >= A) return;
+                float mb = -INFINITY;
+                unsigned long long sb = 0ull;
+                for (int w = 0; w < n_wells; ++w) {
+                    bool bw = false;
+                    fold_well(m, w, bqx, bqy, bqz, bvx, bvy, bvz, dxa, dya, dza, mb, sb, bw);
+                    if (bw) {
+                        float p1x, p1y, p1z, p2x, p2y, p2z;
+                        item_at(ii, p1x, p1y, p1z, p2x, p2y, p2z);
+                        const bool has2 = p2x == p2x;
+                        if (well_inside_exact(m, st, Dx[hn], Dy[hn], my_Dz, p1x, p1y, p1z, has2 ? p2x : 0.f,
+                                              has2 ? p2y : 0.f, has2 ? p2z : 0.f, has2, w)) {
+                            const float tau = m.w_tau[w];
+                            const float ex = dxa - fmaf(tau, bvx, bqx), ey = dya - fmaf(tau, bvy, bqy),
+                                        ez = dza - fmaf(tau, bvz, bqz);
+                            const float l =
+                                fmaf(approx_sqrt(fmaf(ex, ex, fmaf(ey, ey, ez * ez))), m.w_lg[w], m.w_L[w]);
+                            mb = fmaxf(mb, l);
+                            if (m.combine) sb += sum_term(l, m.sum_ref);
+                        }
+                    }
+                }
+                mloc = fmaxf(mloc, mb);
+                sloc += sb;
+            };
+            if (indexed) {
+                // items staged for this step (buffer par), the overflow read from the index
+                const int b = k % kIBufs;
+                const IdxMeta& M = imeta[b];
+                const int total = M.total, n_s = M.n_s;
+                const float4* sb4 = ibuf + (size_t)b * icap * 2;
+                auto item_at = [&](int i, float& p1x, float& p1y, float& p1z, float& p2x, float& p2y, float& p2z) {
+                    float4 P1, P2;
+                    if (i < n_s) {
+                        P1 = sb4[2 * i];
+                        P2 = sb4[2 * i + 1];
+                    } else {
+                        int q = 0, off = i;
+                        while (q < M.nr - 1 && off >= M.cnt[q]) { off -= M.cnt[q]; ++q; }
+                        const float4* g = a.iv.items + M.row_off + 2ll * (M.beg[q] + off);
+                        P1 = g[0];
+                        P2 = g[1];
+                    }
+                    p1x = P1.x; p1y = P1.y; p1z = P1.z;
+                    p2x = P2.x; p2y = P2.y; p2z = P2.z;
+                };
+                // items interleaved over the scanner warps (item i to warp i mod nscan): the
+                // items within reach, each costing a well evaluation per action, sit next to
+                // one another in the index (same cells), so this spreads them over the warps
+                const int nscan = NW - 3, sw = warp - 3;
+                const int wn = total > sw ? (total - sw + nscan - 1) / nscan : 0;  // items of this warp
+                constexpr int U = 2;
+                for (int base = 0; base < wn; base += 32 * U) {
+                    float qx[U], qy[U], qz[U], vx[U], vy[U], vz[U];
+                    bool near[U];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const int j = base + u * 32 + lane;
+                        const int i = sw + j * nscan;
+                        near[u] = false;
+                        qx[u] = qy[u] = qz[u] = vx[u] = vy[u] = vz[u] = 0.f;
+                        if (j < wn) {
+                            float p1x, p1y, p1z, p2x, p2y, p2z;
+                            item_at(i, p1x, p1y, p1z, p2x, p2y, p2z);
+                            qx[u] = (p1x - shx) - slx;
+                            qy[u] = (p1y - shy) - sly;
+                            qz[u] = (p1z - shz) - slz;
+                            if (p2x == p2x) {
+                                vx[u] = (p2x - p1x) * inv_dt;
+                                vy[u] = (p2y - p1y) * inv_dt;
+                                vz[u] = (p2z - p1z) * inv_dt;
+                            }
+                            const float reach =
+                                fmaf(tau_absmax, approx_sqrt(vx[u] * vx[u] + vy[u] * vy[u] + vz[u] * vz[u]), reach0);
+                            near[u] = (qx[u] * qx[u] + qy[u] * qy[u] + qz[u] * qz[u]) < reach * reach;
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        unsigned mask = __ballot_sync(kFull, near[u]);
+                        while (mask) {
+                            const int b = __ffs(mask) - 1;
+                            mask &= mask - 1;
+                            const int ii = sw + (base + u * 32 + b) * nscan;
+                            fold_near(item_at, ii, __shfl_sync(kFull, qx[u], b), __shfl_sync(kFull, qy[u], b),
+                                      __shfl_sync(kFull, qz[u], b), __shfl_sync(kFull, vx[u], b),
+                                      __shfl_sync(kFull, vy[u], b), __shfl_sync(kFull, vz[u], b));
+                        }
+                    }
+                }
+            } else {
             const int e1 = entry_of(k + 1), e2 = entry_of(k + 2);
             const bool v1 = st->ent_valid[e1] != 0;
             const bool v2 = (k + 2 <= last_j) && st->ent_valid[e2] != 0;
@@ -746,6 +1002,11 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
             const float* X2 = ring + (size_t)e2 * 3 * chunk;
             const float* Y2 = X2 + chunk;
             const float* Z2 = Y2 + chunk;
+            auto item_at = [&](int i, float& p1x, float& p1y, float& p1z, float& p2x, float& p2y, float& p2z) {
+                p1x = X1[i]; p1y = Y1[i]; p1z = Z1[i];
+                if (v2) { p2x = X2[i]; p2y = Y2[i]; p2z = Z2[i]; }
+                else { p2x = p2y = p2z = __int_as_float(0x7fc00000); }
+            };
             const int scan_len = v1 ? c_len : 0;
             const int nscan = NW - 2;
             constexpr int U = 2;  // slots per lane per pass (independent chains)
@@ -781,38 +1042,13 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
                     while (mask) {
                         const int b = __ffs(mask) - 1;
                         mask &= mask - 1;
-                        const float bqx = __shfl_sync(kFull, qx[u], b), bqy = __shfl_sync(kFull, qy[u], b),
-                                    bqz = __shfl_sync(kFull, qz[u], b);
-                        const float bvx = __shfl_sync(kFull, vx[u], b), bvy = __shfl_sync(kFull, vy[u], b),
-                                    bvz = __shfl_sync(kFull, vz[u], b);
-                        if (lane < A) {
-                            float mb = -INFINITY;
-                            unsigned long long sb = 0ull;
-                            for (int w = 0; w < n_wells; ++w) {
-                                bool bw = false;
-                                fold_well(m, w, bqx, bqy, bqz, bvx, bvy, bvz, dxa, dya, dza, mb, sb, bw);
-                                if (bw) {
-                                    // within the FP32 band of the radius: decide in FP64
-                                    const int ii = base + u * 32 + b;
-                                    const bool has2 = v2 && (X2[ii] == X2[ii]);
-                                    if (well_inside_exact(m, st, Dx[hn], Dy[hn], my_Dz, X1[ii], Y1[ii], Z1[ii],
-                                                          has2 ? X2[ii] : 0.f, has2 ? Y2[ii] : 0.f,
-                                                          has2 ? Z2[ii] : 0.f, has2, w)) {
-                                        const float tau = m.w_tau[w];
-                                        const float ex = dxa - fmaf(tau, bvx, bqx), ey = dya - fmaf(tau, bvy, bqy),
-                                                    ez = dza - fmaf(tau, bvz, bqz);
-                                        const float l = fmaf(approx_sqrt(fmaf(ex, ex, fmaf(ey, ey, ez * ez))),
-                                                             m.w_lg[w], m.w_L[w]);
-                                        mb = fmaxf(mb, l);
-                                        if (m.combine) sb += sum_term(l, m.sum_ref);
-                                    }
-                                }
-                            }
-                            mloc = fmaxf(mloc, mb);
-                            sloc += sb;
-                        }
+                        const int ii = base + u * 32 + b;
+                        fold_near(item_at, ii, __shfl_sync(kFull, qx[u], b), __shfl_sync(kFull, qy[u], b),
+                                  __shfl_sync(kFull, qz[u], b), __shfl_sync(kFull, vx[u], b),
+                                  __shfl_sync(kFull, vy[u], b), __shfl_sync(kFull, vz[u], b));
                     }
                 }
+            }
             }
             if (ts) ph[4] += clock64() - ts;
         }
@@ -822,7 +1058,13 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
         }
         __syncwarp();
         if (timing && tid == 0) tp = clock64();
-        __syncthreads();  // S3: per-action partials of this CTA complete
+        // S3: per-action partials of this CTA complete (indexed mode: the producer warp, which
+        // adds no partials, goes on to the next step's start instead)
+        if (indexed) {
+            if (warp != 2) named_barrier(1, NT - 32);
+        } else {
+            __syncthreads();
+        }
         if (timing && tid == 0) { const long long t = clock64(); ph[2] += t - tp; tp = t; }
 
         if (warp == 0) {
@@ -947,7 +1189,7 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
             if (trace0 && lane < A)  // FP64 action values for the trace (not used for the decision)
                 a.q_trace[(size_t)k * A + lane] = valid ? trace_q(m, has_goal, n0, phi, Dl, Lp, ssum, Vd) : -INFINITY;
             if (timing && tid == 0) ph[3] += clock64() - tp;
-        } else if (producer) {
+        } else if (producer && !indexed) {
             // ---- producer: slices needed two or more steps ahead
             const long long t0 = timing ? clock64() : 0;
             int to = 0;
@@ -967,6 +1209,7 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
     // ---- epilogue: near-tie flag of the last step, drain the ring, outputs
     if (warp == 1 && k > 0) deferred_tie(st, qkey_s, cls_s, la_s, lt_s, lane, trace0 ? a.tie_trace + (k - 1) : nullptr);
     __syncthreads();
+    if (indexed && warp == 2) drain();
     if (producer) {
         while (waited < issued) {
             const int64_t j = waited + 1;
@@ -1007,7 +1250,7 @@ __global__ void __launch_bounds__(384, 1) rollout_kernel(const __grid_constant__
         if (r < a.n_req) plan_request(a, r, smem);  // uniform over the cluster
         return;
     }
-    const Layout L = make_layout(a.chunk, a.ring);
+    const Layout L = make_layout(a.chunk, a.ring, a.indexed ? a.icap : 0);
     int* next = reinterpret_cast<int*>(smem + L.misc);
     const int n = a.n_dev ? *a.n_dev : a.n_req;
     const bool lead = a.cs == 1 || cluster_rank() == 0;
@@ -1029,7 +1272,7 @@ __global__ void __launch_bounds__(384, 1) rollout_kernel(const __grid_constant__
     }
 }
 
-size_t rollout_smem_bytes(int chunk, int depth) { return make_layout(chunk, depth).total; }
+size_t rollout_smem_bytes(int chunk, int depth, int icap) { return make_layout(chunk, depth, icap).total; }
 
 cudaError_t prepare_rollout_kernel(size_t smem) {
     cudaError_t e = cudaFuncSetAttribute(rollout_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -70,15 +70,27 @@ __global__ void __launch_bounds__(kSepThreads) sepcheck_kernel(const __grid_cons
     const SepConsts sk = sep_consts(m.sep_h, m.sep_v);
     const int s0 = (blockIdx.y * kSepThreads + threadIdx.x) * kSepSlotsPerThread;
 
+    // terrain collision (z below the surface): the first tile's blocks, one sample per
+    // thread; fp32 outside a band around the surface, FP64 inside it
+    if (blockIdx.y == 0 && m.hm) {
+        int tfirst = INT_MAX;
+        for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+            const float* p = a.traj + ((size_t)r * a.cap + k) * 3;
+            const float c = p[2] - terrain32(m, p[0], p[1]);
+            bool below = c < 0.f;
+            if (fabsf(c) < kTerrBand) below = (double)p[2] < terrain64(m, (double)p[0], (double)p[1]);
+            if (below) tfirst = min(tfirst, k);
+        }
+        for (int off = 16; off; off >>= 1) tfirst = min(tfirst, __shfl_xor_sync(0xffffffffu, tfirst, off));
+        if ((threadIdx.x & 31) == 0 && tfirst != INT_MAX) atomicMin(&out->first_terrain, tfirst);
+    }
+
     int first = INT_MAX;
     unsigned cnt = 0;
     float minh = INFINITY, minv = INFINITY;
     for (int k = blockIdx.x; k < n; k += gridDim.x) {
     const float* p = a.traj + ((size_t)r * a.cap + k) * 3;
     const float px = p[0], py = p[1], pz = p[2];
-    if (blockIdx.y == 0 && threadIdx.x == 0 && m.hm) {
-        if ((double)pz < terrain64(m, (double)px, (double)py)) atomicMin(&out->first_terrain, k);
-    }
     const int64_t T = t0 + k;
     if (T < a.tab.t_base || T >= a.tab.t_base + a.tab.T_win) continue;
     const size_t rowoff = (size_t)ring_row(T, a.tab.T_win) * a.tab.S_pad;
@@ -234,6 +246,131 @@ cudaError_t launch_admit(const AdmitArgs& a, int n_req, int max_points, cudaStre
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+// Row-major separation check (batch waves). Each block gathers the work items' samples at
+// its step into shared memory, one thread per sample, then streams the row's plan samples
+// through shared memory in tiles; a thread keeps its sample's count, minima and conflict
+// flag in registers (the minimum horizontal distance as a squared distance: the square
+// root is monotone, so the root of the minimum is the minimum of the roots) and folds them
+// into its request's report once at the end.
+constexpr int kRowThreads = 256;
+constexpr int kRowTile = 2048;
+
+size_t sepcheck_rows_smem(int n_max) {
+    return (size_t)kRowTile * sizeof(float4) + (size_t)n_max * (sizeof(float4) + 2 * sizeof(int)) + 16;
+}
+
+__global__ void __launch_bounds__(kRowThreads) sepcheck_rows_kernel(const __grid_constant__ SepRowsArgs a) {
+    extern __shared__ __align__(16) unsigned char srm[];
+    float4* tile = reinterpret_cast<float4*>(srm);
+    float4* pts = tile + kRowTile;
+    int* pr = reinterpret_cast<int*>(pts + a.n_max);
+    int* pk = pr + a.n_max;
+    int* npts_s = pk + a.n_max;
+    const int tid = threadIdx.x, NT = blockDim.x;
+    const int32_t W = a.tab.T_win;
+    const int64_t T = a.tab.t_base + blockIdx.x;
+    int64_t row = T % W;
+    if (row < 0) row += W;
+    if (tid == 0) *npts_s = 0;
+    __syncthreads();
+    const int n = *a.n_dev;
+    for (int w = tid; w < n; w += NT) {
+        const int r = a.idx[w];
+        const int64_t d = a.reqs[r].depart_step;
+        const int np = a.rout[r].n_points;
+        if (T >= d && T < d + np) {
+            const int q = atomicAdd(npts_s, 1);
+            const int k = (int)(T - d);
+            const float* p = a.traj + ((size_t)r * a.cap + k) * 3;
+            pts[q] = make_float4(p[0], p[1], p[2], 0.f);
+            pr[q] = r;
+            pk[q] = k;
+        }
+    }
+    __syncthreads();
+    const int npts = *npts_s;
+    if (npts == 0) return;
+    const Model& m = a.m;
+    const SepConsts sk = sep_consts(m.sep_h, m.sep_v);
+    // terrain collision of each sample (fp32 outside a band, FP64 inside)
+    if (m.hm) {
+        for (int q = tid; q < npts; q += NT) {
+            const float4 P = pts[q];
+            const float c = P.z - terrain32(m, P.x, P.y);
+            bool below = c < 0.f;
+            if (fabsf(c) < kTerrBand) below = (double)P.z < terrain64(m, (double)P.x, (double)P.y);
+            if (below) atomicMin(&a.out[pr[q]].first_terrain, pk[q]);
+        }
+    }
+    // plan samples of the row: index items (one per finite sample) or the table planes
+    int nslots;
+    const float4* it = nullptr;
+    if (a.items) {
+        const int32_t* cs_row = a.cstart + row * (int64_t)(a.ncell + 1);
+        nslots = cs_row[a.ncell] + a.nextra[row];
+        it = a.items + (size_t)row * a.tab.S_pad * 2;
+    } else {
+        nslots = a.S_scan;
+    }
+    const size_t poff = (size_t)row * a.tab.S_pad;
+    // thread t: sample pg + t % P of the current group of P samples, slots of group t / P
+    // (G = NT / P groups share out each tile); lanes of a warp read the same slot
+    for (int pg = 0; pg < npts; pg += NT) {
+        const int P = min(NT, npts - pg);
+        const int G = NT / P;
+        const int q = pg + tid % P, g = tid / P;
+        const bool act = g < G;
+        const float4 P4 = act ? pts[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+        unsigned cnt = 0;
+        float minh2 = INFINITY, minv = INFINITY;
+        for (int s0 = 0; s0 < nslots; s0 += kRowTile) {
+            const int tn = min(kRowTile, nslots - s0);
+            __syncthreads();
+            for (int j = tid; j < tn; j += NT) {
+                if (it) {
+                    tile[j] = it[2 * (size_t)(s0 + j)];
+                } else {
+                    const size_t o = poff + s0 + j;
+                    tile[j] = make_float4(a.tab.X[o], a.tab.Y[o], a.tab.Z[o], 0.f);
+                }
+            }
+            __syncthreads();
+            if (act) {
+#pragma unroll 4
+                for (int j = g; j < tn; j += G) {
+                    const float4 Q = tile[j];
+                    float h2, dz;
+                    bool hin, vin;
+                    sep_pair(sk, P4.x, P4.y, P4.z, Q.x, Q.y, Q.z, h2, dz, hin, vin);
+                    if (vin) minh2 = fminf(minh2, h2);
+                    if (hin) {
+                        minv = fminf(minv, dz);
+                        cnt += vin ? 1u : 0u;
+                    }
+                }
+            }
+        }
+        if (act) {
+            SepOut* o = a.out + pr[q];
+            if (cnt) {
+                atomicAdd(&o->conflicts, (unsigned long long)cnt);
+                atomicMin(&o->first_conflict, pk[q]);
+            }
+            if (minh2 < INFINITY) atomicMin(&o->min_h_bits, __float_as_uint(sqrtf(minh2)));
+            if (minv < INFINITY) atomicMin(&o->min_v_bits, __float_as_uint(minv));
+        }
+    }
+}
+
+cudaError_t prepare_sepcheck_rows(size_t smem) {
+    return cudaFuncSetAttribute(sepcheck_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+cudaError_t launch_sepcheck_rows(const SepRowsArgs& a, cudaStream_t s) {
+    sepcheck_rows_kernel<<<(unsigned)a.tab.T_win, kRowThreads, sepcheck_rows_smem(a.n_max), s>>>(a);
+    return cudaGetLastError();
 }
 
 // Minimum separations of each request of a batch to the requests admitted before it in the

@@ -53,7 +53,9 @@ class Well(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("combine", ctypes.c_int32), ("wells", ctypes.POINTER(Well)), ("n_wells", ctypes.c_int32),
                 ("goal_reward", ctypes.c_double), ("lookahead_W", ctypes.c_int32),
-                ("cluster_size", ctypes.c_int32), ("threads_per_cta", ctypes.c_int32), ("batch_size", ctypes.c_int32)]
+                ("cluster_size", ctypes.c_int32), ("threads_per_cta", ctypes.c_int32), ("batch_size", ctypes.c_int32),
+                ("full_scan", ctypes.c_int32), ("index_vmax_mps", ctypes.c_double), ("index_cell_m", ctypes.c_double),
+                ("index_stage_items", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class Request(ctypes.Structure):
@@ -85,7 +87,7 @@ class Stats(ctypes.Structure):
                 ("reserved", ctypes.c_int32), ("phase_cycles", ctypes.c_int64 * 6),
                 ("batch_waves", ctypes.c_int64), ("batch_rollouts", ctypes.c_int64), ("batch_replans", ctypes.c_int64),
                 ("influence_launches", ctypes.c_int64), ("influence_ms", ctypes.c_double),
-                ("kernel_launches", ctypes.c_int64)]
+                ("kernel_launches", ctypes.c_int64), ("items_scanned", ctypes.c_int64)]
 
 
 # every exported symbol of include/fmdp.h
@@ -192,7 +194,8 @@ class Scheduler:
 
     def __init__(self, box, dt, gamma, actions, sep, n_slices_window=4096, max_slots=4096, heightmap=None,
                  clearance=0.0, deck_value=1000.0, static_wells=None, combine=0, wells=None, goal_reward=200.0,
-                 cluster_size=0, threads_per_cta=0, batch_size=0):
+                 cluster_size=0, threads_per_cta=0, batch_size=0, full_scan=False, index_vmax_mps=0.0,
+                 index_cell_m=0.0, index_stage_items=0):
         self._L = load()
         air = Airspace()
         air.x0, air.y0, air.z0, air.x1, air.y1, air.z1 = map(float, box)
@@ -221,6 +224,10 @@ class Scheduler:
         opt.cluster_size = int(cluster_size)
         opt.threads_per_cta = int(threads_per_cta)
         opt.batch_size = int(batch_size)
+        opt.full_scan = int(bool(full_scan))
+        opt.index_vmax_mps = float(index_vmax_mps)
+        opt.index_cell_m = float(index_cell_m)
+        opt.index_stage_items = int(index_stage_items)
         if wells is not None:
             warr = (Well * len(wells))(*[Well(*map(float, w)) for w in wells])
             self._keep.append(warr)

@@ -96,8 +96,10 @@ def test_c1_lockstep_q_and_fcfs(c1):
 
 @pytest.mark.parametrize("cs", [1, 2, 4, 8, 16])
 def test_cluster_split_is_bit_identical(c1, cs):
+    """Full-scan rollouts: the slot range split over clusters of 1 to 16 CTAs."""
     sc = c1
-    with Scheduler.from_scenario(sc, cluster_size=1) as ref, Scheduler.from_scenario(sc, cluster_size=cs) as s:
+    with Scheduler.from_scenario(sc, cluster_size=1, full_scan=True) as ref, \
+            Scheduler.from_scenario(sc, cluster_size=cs, full_scan=True) as s:
         for r in sc.requests[:6]:
             a, b = ref.rollout_trace(r), s.rollout_trace(r)
             np.testing.assert_array_equal(a["xyz"], b["xyz"])
