@@ -95,13 +95,13 @@ class ClockSampler:
 
 
 def traffic_from_profile(kernel_src):
-    """Per-launch DRAM traffic recorded from an ncu capture, valid only while the kernel's
-    source is unchanged (the profile records the source digest)."""
+    """DRAM traffic per algorithmic byte recorded from an ncu capture, valid only while the
+    kernel's source is unchanged (the profile records the source digest)."""
     digest = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
     path = os.path.join(ROOT, "profiles", "rollout_kernel_c2.md")
     try:
         for line in open(path):
-            if line.startswith("traffic_bytes_per_slot_step:"):
+            if line.startswith("traffic_per_algorithmic_byte:"):
                 parts = dict(kv.split("=") for kv in line.split(":", 1)[1].split())
                 if parts.get("src") == digest:
                     return float(parts["value"])
@@ -262,18 +262,23 @@ def main():
     peaks, peak_kind = measured_peaks()
     launches = max(kt["rollout_launches"], 1)
     avg_ms = kt["rollout_ms"] / launches
-    bytes_per_launch = 12.0 * kt["slots_scanned"] / launches
+    # algorithmic bytes: the plan samples the steps must read (32-byte index items near the
+    # state with the spatial index; 12-byte table samples of every slot without it)
+    indexed = kt["items_scanned"] > 0
+    bytes_per_launch = (32.0 * kt["items_scanned"] if indexed else 12.0 * kt["slots_scanned"]) / launches
     achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
     tr = traffic_from_profile(os.path.join(ROOT, "paper_2008_03518_gb300", "csrc", "rollout.cu"))
     kernel_ms = {k: kt[k] for k in ("rollout_ms", "sepcheck_ms", "admit_ms", "influence_ms")}
     roofline = {"kernel": "rollout_kernel", "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
                 "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
-                "traffic": (tr * kt["slots_scanned"] / launches) if tr is not None else None,
+                "traffic": (tr * bytes_per_launch) if tr is not None else None,
                 "peak_source": peak_kind,
                 "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_ms,
                 "launches_per_step": launches, "cluster_size": kt["cluster_size"],
                 "threads_per_cta": kt["threads_per_cta"], "slots_per_cta": kt["slots_per_cta"],
-                "rollout_steps_per_step": kt["rollout_steps"],
+                "rollout_steps_per_step": kt["rollout_steps"], "indexed": indexed,
+                "plan_samples_per_rollout_step": (kt["items_scanned"] if indexed else kt["slots_scanned"])
+                / max(kt["rollout_steps"], 1),
                 "share_of_kernel_time": kt["rollout_ms"] / max(sum(kernel_ms.values()), 1e-9),
                 "kernel_ms_per_step": kernel_ms}
 

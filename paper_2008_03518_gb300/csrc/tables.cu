@@ -40,6 +40,20 @@ __device__ __forceinline__ SepConsts sep_consts(double sep_h, double sep_v) {
     k.Vd = sep_v;
     return k;
 }
+// FP64 decisions inside the bands, kept out of line: inlined, the compiler may evaluate
+// them for every pair (predicated), and FP64 runs at a small fraction of the FP32 rate here
+__device__ __noinline__ bool hin_exact(float px, float py, float qx, float qy, double H2d) {
+    const double ex = __dsub_rn((double)px, (double)qx);
+    const double ey = __dsub_rn((double)py, (double)qy);
+    return __dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)) < H2d;
+}
+__device__ __noinline__ bool vin_exact(float pz, float qz, double Vd) {
+    return fabs(__dsub_rn((double)pz, (double)qz)) < Vd;
+}
+__device__ __noinline__ bool below_terrain_exact(const Model& m, float x, float y, float z) {
+    return (double)z < terrain64(m, (double)x, (double)y);
+}
+
 // h2: squared horizontal distance, dz: |vertical distance|; hin / vin: inside the minima
 __device__ __forceinline__ void sep_pair(const SepConsts& k, float px, float py, float pz, float qx, float qy,
                                          float qz, float& h2, float& dz, bool& hin, bool& vin) {
@@ -48,12 +62,8 @@ __device__ __forceinline__ void sep_pair(const SepConsts& k, float px, float py,
     h2 = __fmaf_rn(dx, dx, __fmul_rn(dy, dy));
     hin = h2 < k.H2;  // NaN (empty slot): false
     vin = dz < k.Vm;
-    if (fabsf(h2 - k.H2) < k.hband) {
-        const double ex = __dsub_rn((double)px, (double)qx);
-        const double ey = __dsub_rn((double)py, (double)qy);
-        hin = __dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)) < k.H2d;
-    }
-    if (fabsf(dz - k.Vm) < kSepBand) vin = fabs(__dsub_rn((double)pz, (double)qz)) < k.Vd;
+    if (fabsf(h2 - k.H2) < k.hband) hin = hin_exact(px, py, qx, qy, k.H2d);
+    if (fabsf(dz - k.Vm) < kSepBand) vin = vin_exact(pz, qz, k.Vd);
 }
 
 }  // namespace
@@ -78,7 +88,7 @@ __global__ void __launch_bounds__(kSepThreads) sepcheck_kernel(const __grid_cons
             const float* p = a.traj + ((size_t)r * a.cap + k) * 3;
             const float c = p[2] - terrain32(m, p[0], p[1]);
             bool below = c < 0.f;
-            if (fabsf(c) < kTerrBand) below = (double)p[2] < terrain64(m, (double)p[0], (double)p[1]);
+            if (fabsf(c) < kTerrBand) below = below_terrain_exact(m, p[0], p[1], p[2]);
             if (below) tfirst = min(tfirst, k);
         }
         for (int off = 16; off; off >>= 1) tfirst = min(tfirst, __shfl_xor_sync(0xffffffffu, tfirst, off));
@@ -300,7 +310,7 @@ __global__ void __launch_bounds__(kRowThreads) sepcheck_rows_kernel(const __grid
             const float4 P = pts[q];
             const float c = P.z - terrain32(m, P.x, P.y);
             bool below = c < 0.f;
-            if (fabsf(c) < kTerrBand) below = (double)P.z < terrain64(m, (double)P.x, (double)P.y);
+            if (fabsf(c) < kTerrBand) below = below_terrain_exact(m, P.x, P.y, P.z);
             if (below) atomicMin(&a.out[pr[q]].first_terrain, pk[q]);
         }
     }
