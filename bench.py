@@ -191,6 +191,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-modes", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=2.0, help="arrival window per serving rate")
+    ap.add_argument("--time-scale", type=float, default=60.0, help="simulated seconds per wall second (serving)")
     ap.add_argument("--mode", default="batched", choices=["batched", "sequential"],
                     help="path timed for value: speculative batches (default) or one request at a time")
     args = ap.parse_args()
@@ -315,6 +317,30 @@ def main():
                                 "replans_per_step": st3["batch_replans"] / 2, "workload": sc3.name}
         s3.close()
 
+        # serving: Poisson arrivals against a sliding-window table (60 km, 40k known plans,
+        # room for 100k), continuous batching; each result equals one-at-a-time FCFS
+        sc4 = S.c4_serving()
+        s4 = Scheduler.from_scenario(sc4)
+        s4.set_stream(stream.cuda_stream)
+        s4.snapshot()
+        serving = {}
+        for rate in (50, 200, 1000, 2000):
+            arr = S.poisson_arrivals(900 + rate, float(rate), args.serve_seconds)
+            rq = S.serving_requests(sc4, arr, 901 + rate, time_scale=args.time_scale)
+            s4.restore()
+            barrier()
+            _, lat, rep = s4.serve(rq, arr, time_scale=args.time_scale, max_in_flight=512, points=False)
+            serving[str(rate)] = {"requests": len(rq), "throughput_rps": rep["throughput_rps"],
+                                  "latency_p50_ms": rep["latency_p50_ms"], "latency_p99_ms": rep["latency_p99_ms"],
+                                  "latency_max_ms": rep["latency_max_ms"], "admitted": rep["admitted"],
+                                  "waves": rep["waves"], "replans": rep["replans"],
+                                  "max_in_flight_seen": rep["max_in_flight_seen"], "expiries": rep["expiries"],
+                                  "plans_expired": rep["plans_expired"]}
+        modes["serving"] = {"known_plans": len(sc4.plans), "max_plans": sc4.max_slots, "workload": sc4.name,
+                            "arrivals": f"Poisson, {args.serve_seconds} s per rate",
+                            "time_scale": args.time_scale, "rates_per_s": serving}
+        s4.close()
+
     # ---- end to end through the C ABI with host buffers
     e2e = None
     if not args.no_e2e:
@@ -335,11 +361,15 @@ def main():
         e2e = {"value": world * n_req * k / (ems / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "steps": k, "api": "fmdp_clear + fmdp_add_plans + fmdp_schedule_batch"}
 
+    p99 = None
+    if modes and "serving" in modes:
+        p99 = {r: v["latency_p99_ms"] for r, v in modes["serving"]["rates_per_s"].items()}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(sc, n_req, args.mode),
             "admitted_per_step": admitted, "batch": batch_stats, "modes": modes, "e2e": e2e,
-            "gpu_launches": gpu_launches, "roofline": roofline, "clocks": clk}
+            "gpu_launches": gpu_launches, "roofline": roofline, "clocks": clk,
+            "p99_latency_ms_by_rate": p99}
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(sc, args.cpu_seconds)
     if rank == 0:

@@ -170,6 +170,45 @@ fmdp_status fmdp_schedule_many(fmdp_ctx* ctx, const fmdp_request* reqs, int32_t 
 fmdp_status fmdp_schedule_batch(fmdp_ctx* ctx, const fmdp_request* reqs, int32_t n,
                                 fmdp_result* res);
 
+/* ---- serving (no counterpart in the paper, which plans requests one at a time) ----
+ * fmdp_serve replays an arrival trace against the live table with continuous batching:
+ * request i becomes visible arrival_s[i] seconds (wall clock) after the call starts
+ * (array order = arrival order = first-come-first-served order; arrival_s non-decreasing).
+ * Visible requests join the set of unresolved requests on the device whenever the set
+ * has room (max_in_flight) and the table has free slots for all of them (memory-based
+ * admission: max_active_plans); each speculative wave plans the newly joined and the
+ * influenced requests together, and requests are finalised in arrival order as the
+ * waves resolve them. A simulated clock (sim_start_step + time_scale x wall seconds, in
+ * steps) expires plans that ended before it, never past the earliest departure still
+ * pending. Results (res) equal fmdp_schedule_many over the same requests in the same
+ * order; latency_ms[i] (optional) is the wall time from arrival to result. Every request
+ * must fit the plan-table window at the start of the call. */
+typedef struct {
+    double time_scale;        /* simulated seconds per wall-clock second (0 = 1) */
+    int64_t sim_start_step;   /* simulated step at the start (default: the window's first) */
+    int32_t sim_start_set;    /* 1: use sim_start_step; 0: the window's first step */
+    int32_t max_in_flight;    /* unresolved requests at most (0 = batch size; <= 1024) */
+    int32_t max_active_plans; /* stored plans at most (0 = max_slots) */
+    int32_t expire_quantum;   /* steps the clock advances between expiries (0 = 60) */
+} fmdp_serve_options;
+
+typedef struct {
+    double wall_s;                 /* from the start of the call to the last result */
+    double throughput_rps;         /* requests / wall_s */
+    double latency_p50_ms, latency_p99_ms, latency_mean_ms, latency_max_ms;
+    int64_t waves, rollouts, replans;
+    int64_t expiries, plans_expired;
+    int64_t final_t_base;          /* the window's first step at the end */
+    int32_t admitted, rejected;
+    int32_t max_in_flight_seen;    /* largest unresolved set */
+    int32_t deferred_for_memory;   /* requests that waited for free plan slots */
+} fmdp_serve_report;
+
+void fmdp_serve_options_default(fmdp_serve_options* o);
+fmdp_status fmdp_serve(fmdp_ctx* ctx, const fmdp_request* reqs, const double* arrival_s, int32_t n,
+                       const fmdp_serve_options* opt, fmdp_result* res, double* latency_ms,
+                       fmdp_serve_report* report);
+
 /* Device-resident variant used for kernel-side timing: fmdp_stage_requests copies the
  * requests into library-owned device memory; fmdp_schedule_staged plans them in FCFS
  * order, like fmdp_schedule_many (batched = 0) or fmdp_schedule_batch (batched = 1), but

@@ -7,6 +7,8 @@
 // device, so a whole sequence of requests is enqueued on one stream with no host round
 // trip; the host only reads verdicts back at the end to update its bookkeeping.
 #include <algorithm>
+#include <chrono>
+#include <thread>
 #include <climits>
 #include <cmath>
 #include <cstdio>
@@ -132,6 +134,7 @@ struct BatchBuffers {
     DevArray<int32_t> idx;   // [3][n_cap] + [rq_cap]
     DevArray<int32_t> ctr;   // queue counter, n_todo, n_unresolved, n_store
     DevArray<uint8_t> infl;  // [n_cap][n_cap]
+    DevArray<int32_t> adm;   // admissions of a run, for the minimum-separation epilogue
     PinnedArray<int32_t> h_idx, h_ctr;
     PinnedArray<uint8_t> h_infl;
     PinnedArray<RolloutOut> h_rout;
@@ -140,7 +143,7 @@ struct BatchBuffers {
     PinnedArray<uint8_t> h_acts;
     void release() {
         reqs.release(); traj.release(); acts.release(); rout.release(); sepo.release();
-        idx.release(); ctr.release(); infl.release();
+        idx.release(); ctr.release(); infl.release(); adm.release();
         h_idx.release(); h_ctr.release(); h_infl.release(); h_rout.release(); h_sep.release();
         h_traj.release(); h_acts.release();
     }
@@ -897,107 +900,119 @@ cudaGraphExec_t wave_graph(fmdp_ctx* c, const Geometry& g, int n_clusters, Batch
     return exec;
 }
 
-// Plans requests [b0, b0 + n) of the call (n <= kBatchMax, validated, already on the
-// device in B.rq) as one speculative batch, with exact sequential FCFS results. Results go
-// to res[b0 ...] without sample points. Returns the number admitted.
-int32_t run_batch_chunk(fmdp_ctx* c, const fmdp_request* reqs, int32_t b0, int32_t n, fmdp_result* res) {
-    BatchBuffers& B = c->bat;
-    const int32_t n_cap = B.n_cap;
-    // the batch admits at most n plans, into the lowest free slots: scan up to that bound
-    require((size_t)n <= c->book.free_slots.size(), FMDP_ERR_FULL, "not enough free plan slots for the batch");
-    int32_t bound = c->book.S_hw;
-    {
-        auto it = c->book.free_slots.begin();
-        for (int32_t i = 0; i < n; ++i, ++it) bound = std::max(bound, *it + 1);
-    }
-    const Geometry g = geometry_batch(c, round_up(bound, 512));
-    const int n_clusters = std::max(1, std::min(n, rollout_max_active_clusters(g.cs, g.threads, g.smem)));
-    const bool graphs = c->use_graphs && !c->profiling;
-
-    // request numbers are global (b0 ...); per-request host state is indexed by r - b0
-    std::vector<int32_t> U(n), todo(n), store, adm_all, slot_of(n, -1), replans(n, 0), verdict(n, -1);
-    std::vector<uint64_t> ids(n, 0);
-    std::vector<RolloutOut> fin_ro(n);
-    for (int32_t i = 0; i < n; ++i) U[i] = todo[i] = b0 + i;
+// The speculative state of one call (batches or a serving run): the unresolved requests in
+// arrival order (U), those to plan in the next wave (todo), the previous walk's admissions
+// still to store, and each request's outcome. Request numbers are the call's (0 .. n-1).
+struct Speculator {
+    fmdp_ctx* c;
+    BatchBuffers& B;
+    const fmdp_request* reqs;  // host copies, all requests of the call
+    Geometry g;
+    int n_clusters = 1;
+    bool graphs = false;
+    std::vector<int32_t> U, todo, store, adm_all;
+    std::vector<int32_t> slot_of, replans, verdict;
+    std::vector<uint64_t> ids;
+    std::vector<RolloutOut> fin_ro;
     std::vector<std::pair<uint64_t, int32_t>> pending;  // admitted, not yet stored: (id, slot)
     int32_t admitted = 0;
-    try {
-        while (!U.empty()) {
-            int32_t* hi = B.h_idx.p;
-            std::copy(todo.begin(), todo.end(), hi);
-            std::copy(U.begin(), U.end(), hi + n_cap);
-            std::copy(store.begin(), store.end(), hi + 2 * n_cap);
-            for (int32_t i = 0; i < n; ++i) hi[3 * n_cap + b0 + i] = slot_of[i];
-            B.h_ctr.p[0] = 0;
-            B.h_ctr.p[1] = (int32_t)todo.size();
-            B.h_ctr.p[2] = (int32_t)U.size();
-            B.h_ctr.p[3] = (int32_t)store.size();
-            if (graphs) {
-                CK(cudaGraphLaunch(wave_graph(c, g, n_clusters, B), c->stream));
-                c->stats.kernel_launches += wave_kernels(c);
-            } else {
-                enqueue_wave(c, g, n_clusters, B, true);
-            }
-            CK(cudaStreamSynchronize(c->stream));
-            if (c->profiling) collect_timers(c);
-            require(read_error_word(c) == 0, FMDP_ERR_TIMEOUT, "a bounded device wait expired during a rollout");
-            pending.clear();  // the previous walk's admissions are now in the table
-            c->stats.batch_waves++;
-            for (int32_t r : todo) {
-                const RolloutOut& ro = B.h_rout.p[r];
-                c->stats.rollout_steps += ro.steps;
-                c->stats.slots_scanned += (int64_t)ro.steps * g.S_scan;
-                c->stats.sep_pairs += (int64_t)ro.n_points * g.S_scan;
-                c->stats.batch_rollouts++;
-            }
-            // walk the unresolved requests in arrival order
-            store.clear();
-            std::vector<size_t> adm_pos;  // positions in U admitted by this walk
-            size_t pos = 0;
-            for (; pos < U.size(); ++pos) {
-                const uint8_t* row = B.h_infl.p + pos * n_cap;
-                bool hit = false;
-                for (size_t v : adm_pos) hit = hit || row[v];
-                if (hit) break;
-                const int32_t k = U[pos], q = k - b0;
-                fin_ro[q] = B.h_rout.p[k];
-                verdict[q] = host_verdict(fin_ro[q], B.h_sep.p[k]);
-                if (verdict[q] == FMDP_ADMITTED) {
-                    const int32_t slot = take_slot(c);
-                    require(slot < g.S_scan, FMDP_ERR_ARG, "internal: batch slot beyond the scanned range");
-                    const uint64_t id = c->book.next_id++;
-                    c->book.plans[id] = PlanMeta{slot, reqs[k].depart_step, fin_ro[q].n_points};
-                    c->book.S_hw = std::max(c->book.S_hw, slot + 1);
-                    pending.push_back({id, slot});
-                    slot_of[q] = slot;
-                    ids[q] = id;
-                    store.push_back(k);
-                    adm_all.push_back(k);
-                    adm_pos.push_back(pos);
-                    ++admitted;
-                }
-            }
-            // what stays unresolved is planned again only where an admission may change it
-            std::vector<int32_t> nU, ntodo;
-            for (size_t w = pos; w < U.size(); ++w) {
-                const uint8_t* row = B.h_infl.p + w * n_cap;
-                bool hit = false;
-                for (size_t v : adm_pos) hit = hit || row[v];
-                nU.push_back(U[w]);
-                if (hit) {
-                    ntodo.push_back(U[w]);
-                    ++replans[U[w] - b0];
-                    c->stats.batch_replans++;
-                }
-            }
-            U.swap(nU);
-            todo.swap(ntodo);
+
+    Speculator(fmdp_ctx* c_, const fmdp_request* reqs_, int32_t n)
+        : c(c_), B(c_->bat), reqs(reqs_), slot_of(n, -1), replans(n, 0), verdict(n, -1), ids(n, 0), fin_ro(n) {}
+
+    void set_geometry(const Geometry& g_) {
+        g = g_;
+        n_clusters = std::max(1, std::min(B.n_cap, rollout_max_active_clusters(g.cs, g.threads, g.smem)));
+        graphs = c->use_graphs && !c->profiling;
+    }
+    void add(int32_t r) {  // a request joins the end of the unresolved list
+        U.push_back(r);
+        todo.push_back(r);
+    }
+    void upload_lists() {
+        const int32_t n_cap = B.n_cap;
+        int32_t* hi = B.h_idx.p;
+        std::copy(todo.begin(), todo.end(), hi);
+        std::copy(U.begin(), U.end(), hi + n_cap);
+        std::copy(store.begin(), store.end(), hi + 2 * n_cap);
+        for (int32_t r : store) hi[3 * n_cap + r] = slot_of[r];
+        B.h_ctr.p[0] = 0;
+        B.h_ctr.p[1] = (int32_t)todo.size();
+        B.h_ctr.p[2] = (int32_t)U.size();
+        B.h_ctr.p[3] = (int32_t)store.size();
+    }
+    // One wave and its walk: `resolved` receives the requests finalised, in order.
+    void wave(std::vector<int32_t>& resolved) {
+        const int32_t n_cap = B.n_cap;
+        upload_lists();
+        if (graphs) {
+            CK(cudaGraphLaunch(wave_graph(c, g, n_clusters, B), c->stream));
+            c->stats.kernel_launches += wave_kernels(c);
+        } else {
+            enqueue_wave(c, g, n_clusters, B, true);
         }
-        // epilogue: store the last walk's admissions, then fold the batch's admissions into
-        // every request's minimum separations
-        std::copy(adm_all.begin(), adm_all.end(), B.h_idx.p);
+        CK(cudaStreamSynchronize(c->stream));
+        if (c->profiling) collect_timers(c);
+        require(read_error_word(c) == 0, FMDP_ERR_TIMEOUT, "a bounded device wait expired during a rollout");
+        pending.clear();  // the previous walk's admissions are now in the table
+        c->stats.batch_waves++;
+        for (int32_t r : todo) {
+            const RolloutOut& ro = B.h_rout.p[r];
+            c->stats.rollout_steps += ro.steps;
+            c->stats.slots_scanned += (int64_t)ro.steps * g.S_scan;
+            c->stats.sep_pairs += (int64_t)ro.n_points * g.S_scan;
+            c->stats.batch_rollouts++;
+        }
+        // walk the unresolved requests in arrival order
+        store.clear();
+        std::vector<size_t> adm_pos;  // positions in U admitted by this walk
+        size_t pos = 0;
+        for (; pos < U.size(); ++pos) {
+            const uint8_t* row = B.h_infl.p + pos * n_cap;
+            bool hit = false;
+            for (size_t v : adm_pos) hit = hit || row[v];
+            if (hit) break;
+            const int32_t k = U[pos];
+            fin_ro[k] = B.h_rout.p[k];
+            verdict[k] = host_verdict(fin_ro[k], B.h_sep.p[k]);
+            if (verdict[k] == FMDP_ADMITTED) {
+                const int32_t slot = take_slot(c);
+                require(slot < g.S_scan, FMDP_ERR_ARG, "internal: batch slot beyond the scanned range");
+                const uint64_t id = c->book.next_id++;
+                c->book.plans[id] = PlanMeta{slot, reqs[k].depart_step, fin_ro[k].n_points};
+                c->book.S_hw = std::max(c->book.S_hw, slot + 1);
+                pending.push_back({id, slot});
+                slot_of[k] = slot;
+                ids[k] = id;
+                store.push_back(k);
+                adm_all.push_back(k);
+                adm_pos.push_back(pos);
+                ++admitted;
+            }
+            resolved.push_back(k);
+        }
+        // what stays unresolved is planned again only where an admission may change it
+        std::vector<int32_t> nU, ntodo;
+        for (size_t w = pos; w < U.size(); ++w) {
+            const uint8_t* row = B.h_infl.p + w * n_cap;
+            bool hit = false;
+            for (size_t v : adm_pos) hit = hit || row[v];
+            nU.push_back(U[w]);
+            if (hit) {
+                ntodo.push_back(U[w]);
+                ++replans[U[w]];
+                c->stats.batch_replans++;
+            }
+        }
+        U.swap(nU);
+        todo.swap(ntodo);
+    }
+    // Stores the last walk's admissions, then folds the admissions of requests [k0, k0 + n)'s
+    // own run into their minimum separations and brings their reports back.
+    void finish(int32_t k0, int32_t n) {
+        const int32_t n_cap = B.n_cap;
         std::copy(store.begin(), store.end(), B.h_idx.p + 2 * n_cap);
-        for (int32_t i = 0; i < n; ++i) B.h_idx.p[3 * n_cap + b0 + i] = slot_of[i];
+        for (int32_t r : store) B.h_idx.p[3 * n_cap + r] = slot_of[r];
         B.h_ctr.p[3] = (int32_t)store.size();
         CK(cudaMemcpyAsync(B.idx.p, B.h_idx.p, idx_words(B) * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
         CK(cudaMemcpyAsync(B.ctr.p, B.h_ctr.p, 4 * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
@@ -1018,56 +1033,59 @@ int32_t run_batch_chunk(fmdp_ctx* c, const fmdp_request* reqs, int32_t b0, int32
             index_append_admitted(c, B.traj.p, B.cap, B.rout.p, B.rq, B.sepo.p, aa.idx, aa.n_dev, n_cap,
                                   c->book.t_base, c->book.t_base + c->T_win);
         }
+        // the admission list may be longer than the index block's first array: own buffer
+        B.adm.ensure(std::max<size_t>(adm_all.size(), 1));
+        if (!adm_all.empty())
+            CK(cudaMemcpyAsync(B.adm.p, adm_all.data(), adm_all.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                               c->stream));
         MinSepArgs ma{};
         ma.traj = B.traj.p;
         ma.rout = B.rout.p;
         ma.reqs = B.rq;
         ma.cap = B.cap;
-        ma.k0 = b0;
+        ma.k0 = k0;
         ma.n = n;
-        ma.adm = B.idx.p;
+        ma.adm = B.adm.p;
         ma.n_adm = (int32_t)adm_all.size();
         ma.sep_h = c->sep.horiz_m;
         ma.sep_v = c->sep.vert_m;
         ma.out = B.sepo.p;
         LAUNCH(c, launch_batch_minsep(ma, c->stream));
-        CK(cudaMemcpyAsync(B.h_sep.p + b0, B.sepo.p + b0, n * sizeof(SepOut), cudaMemcpyDeviceToHost, c->stream));
-        CK(cudaStreamSynchronize(c->stream));
+        CK(cudaMemcpyAsync(B.h_sep.p + k0, B.sepo.p + k0, n * sizeof(SepOut), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));  // adm_all may be released after this
         if (c->profiling) collect_timers(c);
         pending.clear();
-    } catch (...) {
-        for (auto& pr : pending) {  // admissions whose plans never reached the table
+        store.clear();
+    }
+    void rollback() {  // admissions whose plans never reached the table
+        for (auto& pr : pending) {
             c->book.plans.erase(pr.first);
             c->book.free_slots.insert(pr.second);
         }
+        pending.clear();
         recompute_hw(c);
-        throw;
     }
-    for (int32_t i = 0; i < n; ++i) {
-        fmdp_result* o = res + b0 + i;
-        SepOut so = B.h_sep.p[b0 + i];  // the final plan's report with the batch's admissions folded in
-        so.verdict = verdict[i];
-        fill_result(fin_ro[i], so, o);
-        o->plan_id = ids[i];
-        o->replanned = replans[i];
+    void results(int32_t k0, int32_t n, fmdp_result* res) {
+        for (int32_t k = k0; k < k0 + n; ++k) {
+            fmdp_result* o = res + k;
+            SepOut so = B.h_sep.p[k];  // the final plan's report with the run's admissions folded in
+            so.verdict = verdict[k];
+            fill_result(fin_ro[k], so, o);
+            o->plan_id = ids[k];
+            o->replanned = replans[k];
+        }
     }
-    return admitted;
-}
+};
 
-// Speculative batching over n validated requests (host copies in reqs; on the device in
-// dev_reqs, or copied there when it is null). Results to res; sample points to the
-// callers' buffers named in res unless keep_points, which leaves them in the batch
-// buffers for fmdp_fetch_staged. Returns the number admitted.
-int32_t run_batch(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_result* res,
-                  const fmdp_request* dev_reqs, bool keep_points) {
-    if (n <= 0) return 0;
+// Sizes the call-wide batch buffers for n requests of trajectories up to cap_needed samples
+// and puts the requests on the device (their copy in dev_reqs, or uploaded).
+void batch_prepare(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, int32_t n_batch, const fmdp_request* dev_reqs) {
     BatchBuffers& B = c->bat;
-    const int32_t bs = c->opt.batch_size > 0 ? c->opt.batch_size : kBatchDefault;
     int32_t cap = 1;
     for (int32_t i = 0; i < n; ++i) cap = std::max(cap, reqs[i].horizon + 1);
     // buffer shapes in buckets, so that graphs are reused from call to call
-    B.n_cap = std::max(B.n_cap, round_up(std::min(n, bs), 64));
-    B.rq_cap = std::max(B.rq_cap, round_up(n, 256));
+    B.n_cap = std::max(B.n_cap, round_up(std::max(n_batch, 1), 64));
+    B.rq_cap = std::max(B.rq_cap, round_up(std::max(n, 1), 256));
     B.cap = std::max(B.cap, round_up(cap, 256));
     const size_t R = B.rq_cap;
     B.traj.ensure(R * B.cap * 3);
@@ -1089,24 +1107,187 @@ int32_t run_batch(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_result*
         CK(cudaMemcpyAsync(B.reqs.p, reqs, n * sizeof(fmdp_request), cudaMemcpyHostToDevice, c->stream));
         B.rq = B.reqs.p;
     }
-    int32_t admitted = 0;
-    for (int32_t b0 = 0; b0 < n; b0 += bs) admitted += run_batch_chunk(c, reqs, b0, std::min(bs, n - b0), res);
+}
+
+// Geometry of the call: the scanned slot range covers every slot the call may fill (the
+// lowest free slots) or, with the spatial index, the whole table.
+Geometry batch_geometry(fmdp_ctx* c, int32_t n_new) {
+    if (c->index_on) return geometry_batch(c, c->S_pad);
+    require((size_t)n_new <= c->book.free_slots.size(), FMDP_ERR_FULL, "not enough free plan slots for the batch");
+    int32_t bound = c->book.S_hw;
+    auto it = c->book.free_slots.begin();
+    for (int32_t i = 0; i < n_new; ++i, ++it) bound = std::max(bound, *it + 1);
+    return geometry_batch(c, round_up(bound, 512));
+}
+
+void copy_points_back(fmdp_ctx* c, int32_t n, fmdp_result* res) {
+    BatchBuffers& B = c->bat;
     bool want_points = false;
-    for (int32_t i = 0; !keep_points && i < n; ++i) want_points = want_points || res[i].xyz || res[i].actions;
-    if (want_points) {
-        B.h_traj.ensure((size_t)n * B.cap * 3);
-        B.h_acts.ensure((size_t)n * B.cap);
-        CK(cudaMemcpyAsync(B.h_traj.p, B.traj.p, (size_t)n * B.cap * 3 * sizeof(float), cudaMemcpyDeviceToHost,
-                           c->stream));
-        CK(cudaMemcpyAsync(B.h_acts.p, B.acts.p, (size_t)n * B.cap, cudaMemcpyDeviceToHost, c->stream));
-        CK(cudaStreamSynchronize(c->stream));
-        for (int32_t i = 0; i < n; ++i) {
-            const int32_t np = res[i].n_points;
-            if (res[i].xyz) std::memcpy(res[i].xyz, B.h_traj.p + (size_t)i * B.cap * 3, (size_t)np * 12);
-            if (res[i].actions && np > 1) std::memcpy(res[i].actions, B.h_acts.p + (size_t)i * B.cap, (size_t)(np - 1));
+    for (int32_t i = 0; i < n; ++i) want_points = want_points || res[i].xyz || res[i].actions;
+    if (!want_points) return;
+    B.h_traj.ensure((size_t)n * B.cap * 3);
+    B.h_acts.ensure((size_t)n * B.cap);
+    CK(cudaMemcpyAsync(B.h_traj.p, B.traj.p, (size_t)n * B.cap * 3 * sizeof(float), cudaMemcpyDeviceToHost,
+                       c->stream));
+    CK(cudaMemcpyAsync(B.h_acts.p, B.acts.p, (size_t)n * B.cap, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (int32_t i = 0; i < n; ++i) {
+        const int32_t np = res[i].n_points;
+        if (res[i].xyz) std::memcpy(res[i].xyz, B.h_traj.p + (size_t)i * B.cap * 3, (size_t)np * 12);
+        if (res[i].actions && np > 1) std::memcpy(res[i].actions, B.h_acts.p + (size_t)i * B.cap, (size_t)(np - 1));
+    }
+}
+
+// Speculative batching over n validated requests (host copies in reqs; on the device in
+// dev_reqs, or copied there when it is null), in consecutive batches of the option's size.
+// Results to res; sample points to the callers' buffers named in res unless keep_points,
+// which leaves them in the batch buffers for fmdp_fetch_staged. Returns the number admitted.
+int32_t run_batch(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_result* res,
+                  const fmdp_request* dev_reqs, bool keep_points) {
+    if (n <= 0) return 0;
+    const int32_t bs = c->opt.batch_size > 0 ? c->opt.batch_size : kBatchDefault;
+    batch_prepare(c, reqs, n, std::min(n, bs), dev_reqs);
+    Speculator sp(c, reqs, n);
+    std::vector<int32_t> resolved;
+    for (int32_t b0 = 0; b0 < n; b0 += bs) {
+        const int32_t m = std::min(bs, n - b0);
+        sp.set_geometry(batch_geometry(c, m));
+        for (int32_t i = 0; i < m; ++i) sp.add(b0 + i);
+        sp.adm_all.clear();
+        try {
+            while (!sp.U.empty()) sp.wave(resolved);
+            sp.finish(b0, m);
+        } catch (...) {
+            sp.rollback();
+            throw;
         }
     }
-    return admitted;
+    sp.results(0, n, res);
+    if (!keep_points) copy_points_back(c, n, res);
+    return sp.admitted;
+}
+
+// ------------------------------------------------------------------ serving loop
+
+void expire_to(fmdp_ctx* c, int64_t t_now, int64_t* n_expired);  // below
+
+// Continuous batching over an arrival trace (see fmdp_serve in the header).
+void run_serve(fmdp_ctx* c, const fmdp_request* reqs, const double* arrival_s, int32_t n,
+               const fmdp_serve_options& o, fmdp_result* res, double* latency_ms, fmdp_serve_report* rep) {
+    using clk = std::chrono::steady_clock;
+    const int32_t bs = c->opt.batch_size > 0 ? c->opt.batch_size : kBatchDefault;
+    const int32_t in_flight = std::max(1, std::min(o.max_in_flight > 0 ? o.max_in_flight : bs, kBatchMax));
+    const int32_t max_active = o.max_active_plans > 0 ? std::min(o.max_active_plans, c->S_max) : c->S_max;
+    const double scale = o.time_scale > 0.0 ? o.time_scale : 1.0;
+    const int64_t quantum = o.expire_quantum > 0 ? o.expire_quantum : 60;
+    const int64_t sim0 = o.sim_start_set ? o.sim_start_step : c->book.t_base;
+    batch_prepare(c, reqs, n, in_flight, nullptr);
+    Speculator sp(c, reqs, n);
+    sp.set_geometry(batch_geometry(c, 0));
+    // earliest departure among requests i .. n-1 (the clock never expires past it)
+    std::vector<int64_t> dep_suffix(n + 1, INT64_MAX);
+    for (int32_t i = n - 1; i >= 0; --i) dep_suffix[i] = std::min(dep_suffix[i + 1], reqs[i].depart_step);
+    std::vector<double> done_at(n, -1.0);
+    std::vector<int32_t> resolved;
+    std::vector<uint8_t> deferred(n, 0);
+    int32_t next = 0, completed = 0;
+    int64_t expiries = 0, expired = 0;
+    int32_t max_seen = 0;
+    const fmdp_stats st0 = c->stats;
+    const auto t0 = clk::now();
+    auto elapsed = [&]() { return std::chrono::duration<double>(clk::now() - t0).count(); };
+    try {
+        while (completed < n) {
+            const double now = elapsed();
+            // expiry: up to the clock, never past a departure still to plan or to store
+            int64_t first_open = sp.U.empty() ? next : sp.U.front();
+            int64_t limit = sim0 + (int64_t)std::floor(now * scale / c->air.dt);
+            limit = std::min(limit, dep_suffix[std::min<int64_t>(first_open, n)]);
+            for (int32_t r : sp.store) limit = std::min(limit, reqs[r].depart_step);
+            if (limit >= c->book.t_base + quantum) {
+                expire_to(c, limit, &expired);
+                ++expiries;
+                sp.set_geometry(batch_geometry(c, 0));
+            }
+            // admission: arrived requests join while the set has room and slots remain for all
+            bool blocked = false;
+            while (next < n && arrival_s[next] <= now && (int32_t)sp.U.size() < in_flight) {
+                const int64_t active = (int64_t)c->book.plans.size();
+                const int64_t room = std::min<int64_t>((int64_t)c->book.free_slots.size(), max_active - active);
+                if ((int64_t)sp.U.size() + 1 > room) {
+                    blocked = true;
+                    if (!deferred[next]) deferred[next] = 1;
+                    break;
+                }
+                sp.add(next++);
+            }
+            max_seen = std::max(max_seen, (int32_t)sp.U.size());
+            if (!sp.U.empty()) {
+                resolved.clear();
+                sp.wave(resolved);
+                const double t = elapsed();
+                for (int32_t k : resolved) done_at[k] = t;
+                completed += (int32_t)resolved.size();
+                continue;
+            }
+            if (next >= n) break;
+            if (blocked) {
+                // nothing in flight and no room: only the clock can free slots, by expiring a
+                // plan that ends before the next departure
+                int64_t first_end = INT64_MAX;
+                for (auto& kv : c->book.plans) first_end = std::min(first_end, kv.second.t0 + kv.second.n);
+                require(first_end <= dep_suffix[next], FMDP_ERR_FULL, "plan table full and no plan can expire");
+                std::this_thread::sleep_for(std::chrono::microseconds(200));
+                continue;
+            }
+            const double wait = arrival_s[next] - elapsed();
+            if (wait > 0) std::this_thread::sleep_for(std::chrono::duration<double>(std::min(wait, 0.01)));
+        }
+        sp.finish(0, n);
+    } catch (...) {
+        sp.rollback();
+        throw;
+    }
+    sp.results(0, n, res);
+    copy_points_back(c, n, res);
+    // report
+    std::vector<double> lat(n);
+    double mx = 0.0, sum = 0.0, last = 0.0;
+    for (int32_t i = 0; i < n; ++i) {
+        lat[i] = 1e3 * std::max(0.0, done_at[i] - arrival_s[i]);
+        if (latency_ms) latency_ms[i] = lat[i];
+        mx = std::max(mx, lat[i]);
+        sum += lat[i];
+        last = std::max(last, done_at[i]);
+    }
+    if (rep) {
+        std::vector<double> sorted = lat;
+        std::sort(sorted.begin(), sorted.end());
+        auto pct = [&](double q) {
+            if (sorted.empty()) return 0.0;
+            const size_t i = (size_t)std::min<double>((double)sorted.size() - 1, std::ceil(q * sorted.size()) - 1);
+            return sorted[i];
+        };
+        *rep = fmdp_serve_report{};
+        rep->wall_s = last;
+        rep->throughput_rps = last > 0.0 ? n / last : 0.0;
+        rep->latency_p50_ms = pct(0.50);
+        rep->latency_p99_ms = pct(0.99);
+        rep->latency_mean_ms = n ? sum / n : 0.0;
+        rep->latency_max_ms = mx;
+        rep->waves = c->stats.batch_waves - st0.batch_waves;
+        rep->rollouts = c->stats.batch_rollouts - st0.batch_rollouts;
+        rep->replans = c->stats.batch_replans - st0.batch_replans;
+        rep->expiries = expiries;
+        rep->plans_expired = expired;
+        rep->final_t_base = c->book.t_base;
+        rep->admitted = sp.admitted;
+        rep->rejected = n - sp.admitted;
+        rep->max_in_flight_seen = max_seen;
+        int32_t nd = 0;
+        for (uint8_t d : deferred) nd += d;
+        rep->deferred_for_memory = nd;
+    }
 }
 
 void store_plans(fmdp_ctx* c, int32_t n_plans, const int64_t* t0s, const int32_t* counts, const float* xyz,
@@ -1207,6 +1388,25 @@ void clear_rows(fmdp_ctx* c, int64_t a, int64_t b) {
         ra = 0;
     }
     index_rebuild(c, a, b, false);  // the cleared rows hold no items
+}
+
+void expire_to(fmdp_ctx* c, int64_t t_now, int64_t* n_expired) {
+    if (t_now <= c->book.t_base) return;
+    int64_t n = 0;
+    for (auto it = c->book.plans.begin(); it != c->book.plans.end();) {
+        if (it->second.t0 + it->second.n - 1 < t_now) {
+            c->book.free_slots.insert(it->second.slot);
+            it = c->book.plans.erase(it);
+            ++n;
+        } else {
+            ++it;
+        }
+    }
+    clear_rows(c, c->book.t_base, t_now);
+    c->book.t_base = t_now;
+    recompute_hw(c);
+    CK(cudaStreamSynchronize(c->stream));
+    if (n_expired) *n_expired += n;
 }
 
 void destroy_ctx(fmdp_ctx* c) {
@@ -1619,21 +1819,33 @@ fmdp_status fmdp_get_plan(fmdp_ctx* c, uint64_t id, int64_t* t0_out, float* xyz,
 
 fmdp_status fmdp_expire(fmdp_ctx* c, int64_t t_now) {
     if (!c) return FMDP_ERR_ARG;
+    return guard(c, [&] { expire_to(c, t_now, nullptr); });
+}
+
+fmdp_status fmdp_serve(fmdp_ctx* c, const fmdp_request* reqs, const double* arrival_s, int32_t n,
+                       const fmdp_serve_options* opt, fmdp_result* res, double* latency_ms,
+                       fmdp_serve_report* report) {
+    if (!c) return FMDP_ERR_ARG;
     return guard(c, [&] {
-        if (t_now <= c->book.t_base) return;
-        for (auto it = c->book.plans.begin(); it != c->book.plans.end();) {
-            if (it->second.t0 + it->second.n - 1 < t_now) {
-                c->book.free_slots.insert(it->second.slot);
-                it = c->book.plans.erase(it);
-            } else {
-                ++it;
-            }
+        require(n >= 0 && (n == 0 || (reqs && arrival_s && res)), FMDP_ERR_ARG, "null requests, arrivals or results");
+        fmdp_serve_options o;
+        if (opt) o = *opt; else fmdp_serve_options_default(&o);
+        require(o.time_scale >= 0.0 && o.max_in_flight >= 0 && o.max_in_flight <= kBatchMax &&
+                    o.max_active_plans >= 0 && o.expire_quantum >= 0,
+                FMDP_ERR_ARG, "serve options out of range");
+        for (int32_t i = 0; i < n; ++i) {
+            check_request(c, reqs[i]);
+            require(std::isfinite(arrival_s[i]) && arrival_s[i] >= 0.0 && (i == 0 || arrival_s[i] >= arrival_s[i - 1]),
+                    FMDP_ERR_ARG, "arrival times must be finite, >= 0 and non-decreasing");
         }
-        clear_rows(c, c->book.t_base, t_now);
-        c->book.t_base = t_now;
-        recompute_hw(c);
-        CK(cudaStreamSynchronize(c->stream));
+        run_serve(c, reqs, arrival_s, n, o, res, latency_ms, report);
     });
+}
+
+void fmdp_serve_options_default(fmdp_serve_options* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->time_scale = 1.0;
 }
 
 fmdp_status fmdp_snapshot(fmdp_ctx* c) {

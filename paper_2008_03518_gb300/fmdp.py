@@ -77,6 +77,22 @@ class SepReport(ctypes.Structure):
                 ("conflicts", ctypes.c_int64), ("min_sep_h", ctypes.c_double), ("min_sep_v", ctypes.c_double)]
 
 
+class ServeOptions(ctypes.Structure):
+    _fields_ = [("time_scale", ctypes.c_double), ("sim_start_step", ctypes.c_int64), ("sim_start_set", ctypes.c_int32),
+                ("max_in_flight", ctypes.c_int32), ("max_active_plans", ctypes.c_int32),
+                ("expire_quantum", ctypes.c_int32)]
+
+
+class ServeReport(ctypes.Structure):
+    _fields_ = [("wall_s", ctypes.c_double), ("throughput_rps", ctypes.c_double),
+                ("latency_p50_ms", ctypes.c_double), ("latency_p99_ms", ctypes.c_double),
+                ("latency_mean_ms", ctypes.c_double), ("latency_max_ms", ctypes.c_double),
+                ("waves", ctypes.c_int64), ("rollouts", ctypes.c_int64), ("replans", ctypes.c_int64),
+                ("expiries", ctypes.c_int64), ("plans_expired", ctypes.c_int64), ("final_t_base", ctypes.c_int64),
+                ("admitted", ctypes.c_int32), ("rejected", ctypes.c_int32), ("max_in_flight_seen", ctypes.c_int32),
+                ("deferred_for_memory", ctypes.c_int32)]
+
+
 class Stats(ctypes.Structure):
     _fields_ = [("rollout_launches", ctypes.c_int64), ("sepcheck_launches", ctypes.c_int64),
                 ("admit_launches", ctypes.c_int64), ("rollout_ms", ctypes.c_double),
@@ -94,6 +110,7 @@ class Stats(ctypes.Structure):
 EXPORTS = ("fmdp_options_default", "fmdp_create", "fmdp_destroy", "fmdp_last_error", "fmdp_set_stream",
            "fmdp_add_plan", "fmdp_add_plans", "fmdp_schedule", "fmdp_schedule_many", "fmdp_schedule_batch",
            "fmdp_stage_requests", "fmdp_schedule_staged", "fmdp_fetch_staged", "fmdp_query_plans",
+           "fmdp_serve", "fmdp_serve_options_default",
            "fmdp_get_plan", "fmdp_expire", "fmdp_snapshot", "fmdp_restore", "fmdp_clear", "fmdp_rollout_trace",
            "fmdp_sep_check", "fmdp_sep_check_noalloc", "fmdp_set_profiling", "fmdp_get_stats")
 
@@ -133,6 +150,10 @@ def load(build_if_missing: bool = True):
     L.fmdp_schedule.argtypes = [vp, P(Request), P(Result)]
     L.fmdp_stage_requests.argtypes = [vp, P(Request), c.c_int32]
     L.fmdp_schedule_staged.argtypes = [vp, c.c_int32, P(c.c_int32)]
+    L.fmdp_serve_options_default.argtypes = [P(ServeOptions)]
+    L.fmdp_serve_options_default.restype = None
+    L.fmdp_serve.argtypes = [vp, P(Request), P(c.c_double), c.c_int32, P(ServeOptions), P(Result), P(c.c_double),
+                             P(ServeReport)]
     L.fmdp_fetch_staged.argtypes = [vp, P(Result), c.c_int32]
     L.fmdp_query_plans.argtypes = [vp, c.c_int64, c.c_int64, P(c.c_uint64), c.c_int32, P(c.c_int32)]
     L.fmdp_get_plan.argtypes = [vp, c.c_uint64, P(c.c_int64), _fp, c.c_int32, P(c.c_int32)]
@@ -360,6 +381,38 @@ class Scheduler:
     def schedule_batch(self, reqs, points=True):
         """FCFS in array order through speculative batches; identical results."""
         return self._many(self._L.fmdp_schedule_batch, reqs, points)
+
+    def serve(self, reqs, arrival_s, time_scale=1.0, max_in_flight=0, max_active_plans=0, expire_quantum=0,
+              sim_start_step=None, points=True):
+        """Continuous-batching serving run over an arrival trace (seconds after the call).
+        Returns (results, latency_ms, report)."""
+        n = len(reqs)
+        rq = (Request * n)(*[make_request(reqs[i]) for i in range(n)])
+        arr = np.ascontiguousarray(arrival_s, dtype=np.float64)
+        assert arr.shape == (n,)
+        o = ServeOptions()
+        self._L.fmdp_serve_options_default(ctypes.byref(o))
+        o.time_scale = float(time_scale)
+        o.max_in_flight = int(max_in_flight)
+        o.max_active_plans = int(max_active_plans)
+        o.expire_quantum = int(expire_quantum)
+        if sim_start_step is not None:
+            o.sim_start_set = 1
+            o.sim_start_step = int(sim_start_step)
+        res = (Result * n)()
+        cap = max([rq[i].horizon for i in range(n)] + [0]) + 1
+        xyz = np.zeros((n, cap, 3), dtype=np.float32) if points else None
+        acts = np.zeros((n, cap), dtype=np.uint8) if points else None
+        if points:
+            for i in range(n):
+                res[i].xyz = _ptr(xyz[i], ctypes.c_float)
+                res[i].actions = _ptr(acts[i], ctypes.c_uint8)
+        lat = np.zeros(n, dtype=np.float64)
+        rep = ServeReport()
+        self._check(self._L.fmdp_serve(self._h, rq, _ptr(arr, ctypes.c_double), n, ctypes.byref(o), res,
+                                       _ptr(lat, ctypes.c_double), ctypes.byref(rep)))
+        out = [_result_dict(res[i], xyz[i] if points else None, acts[i] if points else None) for i in range(n)]
+        return out, lat, {k: getattr(rep, k) for k, _ in ServeReport._fields_}
 
     def stage(self, reqs):
         n = len(reqs)

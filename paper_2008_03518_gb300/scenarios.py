@@ -287,6 +287,40 @@ def crowded_batch(seed: int = 104, n_plans: int = 200, n_requests: int = 48, spr
                     max_slots=n_plans + n_requests + 64)
 
 
+def c4_serving(seed: int = 104, n_plans: int = 40000) -> Scenario:
+    """Serving airspace: 60 km x 60 km x 1 km, C2-style terrain stretched over it, `n_plans`
+    multi-leg known plans departing U[0, 1800] s, a window of 4096 steps and room for
+    100k plans (the sliding-window table). Requests come from `serving_requests`."""
+    hm = fractal_heightmap(seed)
+    rng = np.random.default_rng(seed + 1000)
+    box = (0.0, 0.0, 0.0, 60000.0, 60000.0, 1000.0)
+    plans = multileg_plans(rng, box, n_plans, hm, tlo=0, thi=1800)
+    return Scenario(f"c4_serving_60km_{n_plans}plans_A25", box, 1.0, 0.99,
+                    action_grid((-4.0, -2.0, 0.0, 2.0, 4.0)), (150.0, 30.0), plans,
+                    np.zeros(0, dtype=REQUEST_DTYPE), heightmap=hm, clearance=60.0, n_slices_window=4096,
+                    max_slots=100000)
+
+
+def poisson_arrivals(seed: int, rate_per_s: float, duration_s: float) -> np.ndarray:
+    """Arrival times (s) of a Poisson process of the given rate over [0, duration)."""
+    rng = np.random.default_rng(seed)
+    n = max(1, int(rate_per_s * duration_s * 1.5) + 16)
+    t = np.cumsum(rng.exponential(1.0 / rate_per_s, size=n))
+    return t[t < duration_s]
+
+
+def serving_requests(sc: Scenario, arrival_s: np.ndarray, seed: int, time_scale: float,
+                     lead_s=(120.0, 600.0), horizon_range=(60, 1200), reach_frac=0.5) -> np.ndarray:
+    """One request per arrival: it departs `lead` simulated seconds after its arrival on the
+    simulated clock (arrival x time_scale), towards a destination reach_frac v H away."""
+    rng = np.random.default_rng(seed)
+    req = make_requests(rng, sc.box, len(arrival_s), hm=sc.heightmap, zspan=(60.0, 500.0), tlo=0, thi=0,
+                        horizon_range=horizon_range, reach_frac=reach_frac)
+    lead = rng.uniform(*lead_s, size=len(arrival_s))
+    req["depart"] = np.floor((arrival_s * time_scale + lead) / sc.dt).astype(np.int64)
+    return req
+
+
 def sort_plans_by_departure(plans: List[Plan]) -> List[Plan]:
     """Stable order by departure step (slot allocation then groups plans in time)."""
     order = sorted(range(len(plans)), key=lambda i: (plans[i].t0, i))
