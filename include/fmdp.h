@@ -147,6 +147,8 @@ typedef struct {
     double min_sep_v;            /* min |dz| to a plan within horiz_m (inf if none) */
     int32_t near_ties;           /* steps whose top-2 action values differed by < 1e-4 rel. */
     int32_t replanned;           /* batch mode: times the speculative plan was redone */
+    int32_t source;              /* 0: FastMDP rollout; 1: accepted learned proposal */
+    int32_t reserved;
     float* xyz;                  /* caller-owned [horizon+1][3] or NULL: trajectory samples */
     uint8_t* actions;            /* caller-owned [horizon] or NULL: chosen action indices */
 } fmdp_result;
@@ -208,6 +210,58 @@ void fmdp_serve_options_default(fmdp_serve_options* o);
 fmdp_status fmdp_serve(fmdp_ctx* ctx, const fmdp_request* reqs, const double* arrival_s, int32_t n,
                        const fmdp_serve_options* opt, fmdp_result* res, double* latency_ms,
                        fmdp_serve_report* report);
+
+/* ---- learned proposal (no counterpart in the paper) ----
+ * A multilayer perceptron (128 -> 256 -> 256 -> 256 -> 256 -> 25, ReLU, bf16 weights, fp32
+ * accumulation) maps features of a state (own and goal terms; the nearest plan sample of
+ * the next step in each of 20 sectors around the aircraft) to action logits. It is trained
+ * on FastMDP's own action choices (Alg. 1), rolls out a whole trajectory by its argmax over
+ * the actions that stay in the box, and the proposal is accepted when it reaches the goal,
+ * passes the separation and terrain checks, and takes at most (1 + slack) times the fewest
+ * steps any trajectory needs (which bounds its cost gap to FastMDP by the same factor);
+ * otherwise FastMDP plans the request. Parameters: per layer W (in x out, row-major) then
+ * b (out), FMDP_MLP_PARAMS floats. */
+#define FMDP_MLP_PARAMS 236825
+typedef struct {
+    int32_t n;                      /* requests */
+    int32_t accepted;               /* proposals accepted */
+    int32_t proposals_captured;     /* proposals that reached the goal */
+    int32_t fastmdp_captured;       /* FastMDP plans that reached the goal (evaluate) */
+    double mean_gap, max_gap;       /* (proposal steps - FastMDP steps) / FastMDP steps over
+                                       accepted proposals whose FastMDP plan also captured */
+    int64_t proposal_steps, fastmdp_steps;
+    double proposal_ms, fastmdp_ms; /* CUDA-event time of the two rollout passes (evaluate) */
+} fmdp_learned_report;
+
+/* Plans the requests with FastMDP against the table as it stands (nothing is admitted) and
+ * appends one training row per rollout step: the features of the state and FastMDP's
+ * action. n_rows_out: rows in the training set after the call. */
+fmdp_status fmdp_learned_collect(fmdp_ctx* ctx, const fmdp_request* reqs, int32_t n, int32_t* n_rows_out);
+/* Copies up to max_rows training rows out (X: [rows][128] fp32 of the stored bf16 values). */
+fmdp_status fmdp_learned_rows(fmdp_ctx* ctx, float* X, uint8_t* y, int32_t max_rows, int32_t* n_out);
+fmdp_status fmdp_learned_clear_rows(fmdp_ctx* ctx);
+/* Seeded He-normal weights and zero biases. */
+fmdp_status fmdp_learned_init(fmdp_ctx* ctx, uint64_t seed);
+fmdp_status fmdp_learned_set_params(fmdp_ctx* ctx, const float* params, int32_t n);
+fmdp_status fmdp_learned_get_params(fmdp_ctx* ctx, float* params, int32_t n);
+/* Adam on the mean cross-entropy of the training set, shuffled with `seed` each epoch;
+ * loss_per_epoch (optional, epochs floats): mean batch loss of each epoch. */
+fmdp_status fmdp_learned_train(fmdp_ctx* ctx, int32_t epochs, int32_t batch, float lr, uint64_t seed,
+                               float* loss_per_epoch);
+/* Loss and gradient on the given rows (host X [rows][128], bf16-rounded on the device; y),
+ * without changing the parameters (gradient checks). */
+fmdp_status fmdp_learned_loss_grad(fmdp_ctx* ctx, const float* X, const uint8_t* y, int32_t rows, float* loss,
+                                   float* grad);
+/* Proposals and FastMDP plans for every request against the table as it stands (nothing is
+ * admitted): acceptance and cost gap. accepted, steps_p, steps_f: optional, n entries. */
+fmdp_status fmdp_learned_evaluate(fmdp_ctx* ctx, const fmdp_request* reqs, int32_t n, double slack,
+                                  fmdp_learned_report* report, int32_t* accepted, int32_t* steps_p,
+                                  int32_t* steps_f);
+/* First-come-first-served scheduling where each request takes its accepted proposal, else
+ * its FastMDP plan (res[i].source says which), through speculative batches; results equal
+ * taking the requests one at a time with the same rule. */
+fmdp_status fmdp_schedule_learned(fmdp_ctx* ctx, const fmdp_request* reqs, int32_t n, double slack,
+                                  fmdp_result* res, fmdp_learned_report* report);
 
 /* Device-resident variant used for kernel-side timing: fmdp_stage_requests copies the
  * requests into library-owned device memory; fmdp_schedule_staged plans them in FCFS

@@ -14,7 +14,11 @@ features(...)   the 128 inputs at one state: 8 own/goal terms, then 20 sectors a
                 (speed along its heading), both scaled by (1 - distance / R_F), so an empty
                 or distant sector reads zero;
 mlp_forward     128 -> 256 -> 256 -> 256 -> 256 -> 25, ReLU between layers;
-loss_and_grad   mean softmax cross-entropy over a batch and its exact gradient.
+loss_and_grad   mean softmax cross-entropy over a batch and its exact gradient; with
+                round_fn (bf16 below) the same computation with the bf16 network's rounding
+                points stated: hidden activations after ReLU, and the output gradients of a
+                layer where they enter a matrix product (its bias gradient uses them unrounded).
+bf16            round to the nearest bfloat16 (ties to even), as a float64 array.
 
 Parameter vector: for each layer l, W_l (in x out, row-major) then b_l (out).
 """
@@ -42,22 +46,32 @@ def unpack(params, dims=DIMS):
     return out
 
 
-def mlp_forward(params, X, dims=DIMS):
+def bf16(x):
+    a = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    a = (a + 0x7FFF + ((a >> 16) & 1)) & 0xFFFF0000
+    return a.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _identity(x):
+    return x
+
+
+def mlp_forward(params, X, dims=DIMS, round_fn=_identity):
     """Logits for the rows of X; also the hidden activations (post-ReLU) per layer."""
     layers = unpack(params, dims)
     h = np.asarray(X, dtype=np.float64)
     acts = [h]
     for i, (W, b) in enumerate(layers):
         z = h @ W + b
-        h = z if i == len(layers) - 1 else np.maximum(z, 0.0)
+        h = z if i == len(layers) - 1 else round_fn(np.maximum(z, 0.0))
         acts.append(h)
     return h, acts
 
 
-def loss_and_grad(params, X, y, dims=DIMS, n_valid=None):
+def loss_and_grad(params, X, y, dims=DIMS, n_valid=None, round_fn=_identity):
     """Mean cross-entropy of softmax(logits) against labels y, and d loss / d params.
     Logits at or beyond n_valid (an action set smaller than the output) are masked."""
-    logits, acts = mlp_forward(params, X, dims)
+    logits, acts = mlp_forward(params, X, dims, round_fn)
     B = logits.shape[0]
     if n_valid is not None and n_valid < logits.shape[1]:
         logits = logits.copy()
@@ -74,11 +88,12 @@ def loss_and_grad(params, X, y, dims=DIMS, n_valid=None):
     for i in range(len(layers) - 1, -1, -1):
         W, _ = layers[i]
         h_in = acts[i]
-        gW = h_in.T @ g
+        gr = round_fn(g)
+        gW = h_in.T @ gr
         gb = g.sum(axis=0)
         grads.append((gW, gb))
         if i > 0:
-            g = (g @ W.T) * (acts[i] > 0.0)
+            g = (gr @ W.T) * (acts[i] > 0.0)
     grads.reverse()
     flat = np.concatenate([np.concatenate([gW.ravel(), gb]) for gW, gb in grads])
     return loss, flat

@@ -20,7 +20,7 @@
 #include <string>
 #include <vector>
 
-#include "fmdp_internal.cuh"
+#include "learned.cuh"
 
 using namespace fmdp;
 
@@ -141,8 +141,9 @@ struct BatchBuffers {
     PinnedArray<SepOut> h_sep;
     PinnedArray<float> h_traj;
     PinnedArray<uint8_t> h_acts;
+    PinnedArray<int32_t> h_acc;  // learned mode: accepted proposals
     void release() {
-        reqs.release(); traj.release(); acts.release(); rout.release(); sepo.release();
+        reqs.release(); traj.release(); acts.release(); rout.release(); sepo.release(); h_acc.release();
         idx.release(); ctr.release(); infl.release(); adm.release();
         h_idx.release(); h_ctr.release(); h_infl.release(); h_rout.release(); h_sep.release();
         h_traj.release(); h_acts.release();
@@ -171,6 +172,7 @@ struct fmdp_ctx {
     cudaStream_t stream = nullptr;
     int device = 0;
     int max_smem = 0;
+    int n_sm = 1;
 
     // device plan table
     float* X = nullptr;
@@ -213,6 +215,28 @@ struct fmdp_ctx {
     PinnedArray<uint8_t> h_acts;
     PinnedArray<RolloutOut> h_rout;
     PinnedArray<SepOut> h_sep;
+
+    // learned proposal: fp32 parameters, gradients and Adam moments; bf16 copies (training
+    // layout and the policy kernel's chunks); the training set; per-request proposal buffers
+    bool mlp_ready = false;
+    DevArray<float> mlp_p, mlp_g, mlp_m1, mlp_m2;
+    DevArray<__nv_bfloat16> mlp_wt, mlp_wp;
+    int64_t adam_t = 0;
+    DevArray<__nv_bfloat16> tX;
+    DevArray<uint8_t> ty;
+    int64_t t_rows = 0;
+    DevArray<__nv_bfloat16> trX, trH, trdZ;
+    DevArray<float> trZ, trdZf, trdH, tr_loss;
+    DevArray<int32_t> tr_idx;
+    DevArray<uint8_t> tr_y;
+    DevArray<float> p_traj;
+    DevArray<uint8_t> p_acts;
+    DevArray<RolloutOut> p_rout;
+    DevArray<SepOut> p_sep;
+    DevArray<int32_t> p_acc, p_queue, p_ident;
+    DevArray<int64_t> row0;
+    bool learned_mode = false;  // the batch in flight takes accepted proposals
+    double slack = 0.05;
 
     // speculative batches
     BatchBuffers bat;
@@ -715,7 +739,7 @@ int32_t run_fcfs(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_result* 
 constexpr int32_t kBatchDefault = 256;
 constexpr int32_t kBatchMax = 1024;
 // kernels of one wave: admit, reset, rollout, sep_check, influence (+ index append, rebuild)
-int wave_kernels(const fmdp_ctx* c) { return c->index_on ? 7 : 5; }
+int wave_kernels(const fmdp_ctx* c) { return (c->index_on ? 7 : 5) + (c->learned_mode ? 4 : 0); }
 
 // Batch geometry: the narrowest cluster whose partition fits one CTA's shared memory, so
 // that as many rollouts as possible run side by side.
@@ -747,6 +771,12 @@ int32_t host_verdict(const RolloutOut& ro, const SepOut& so) {  // the admission
 // Every count is read on the device, so the sequence can be captured once and replayed.
 size_t idx_words(const BatchBuffers& B) { return 3 * (size_t)B.n_cap + B.rq_cap; }
 
+double climb_step(const fmdp_ctx* c) {
+    double m = 0.0;
+    for (int i = 0; i < c->model.A; ++i) m = std::max(m, std::fabs(c->model.climb[i] * c->model.dt));
+    return m;
+}
+
 void enqueue_wave(fmdp_ctx* c, const Geometry& g, int n_clusters, BatchBuffers& B, bool timed) {
     const int32_t n_cap = B.n_cap, cap = B.cap;
     cudaStream_t s = c->stream;
@@ -776,6 +806,67 @@ void enqueue_wave(fmdp_ctx* c, const Geometry& g, int n_clusters, BatchBuffers& 
                               c->book.t_base, c->book.t_base + c->T_win);
     }
     LAUNCH(c, launch_sep_reset_idx(B.sepo.p, todo, B.ctr.p + 1, n_cap, s));
+    if (c->learned_mode) {
+        // proposals for the work items, their separation check, and the judge, which copies
+        // accepted proposals over the items' FastMDP buffers and marks them to skip FastMDP
+        LAUNCH(c, launch_sep_reset_idx(c->p_sep.p, todo, B.ctr.p + 1, n_cap, s));
+        CK(cudaMemsetAsync(c->p_queue.p, 0, sizeof(int32_t), s));
+        PolicyArgs pa{};
+        pa.m = c->model;
+        pa.tab = tv;
+        pa.iv = index_view(c);
+        pa.Wp = c->mlp_wp.p;
+        pa.params = c->mlp_p.p;
+        pa.reqs = B.rq;
+        pa.idx = todo;
+        pa.n_items = n_cap;
+        pa.n_dev = B.ctr.p + 1;
+        pa.queue = c->p_queue.p;
+        pa.cap = cap;
+        pa.traj = c->p_traj.p;
+        pa.acts = c->p_acts.p;
+        pa.out = c->p_rout.p;
+        pa.err = c->err;
+        LAUNCH(c, launch_policy(pa, std::min(c->n_sm, (n_cap + kPolicyRows - 1) / kPolicyRows), s));
+        SepRowsArgs sp{};
+        sp.m = c->model;
+        sp.tab = tv;
+        sp.S_scan = g.S_scan;
+        sp.traj = c->p_traj.p;
+        sp.cap = cap;
+        sp.rout = c->p_rout.p;
+        sp.reqs = B.rq;
+        sp.idx = todo;
+        sp.n_dev = B.ctr.p + 1;
+        sp.n_max = n_cap;
+        sp.out = c->p_sep.p;
+        if (c->index_on) {
+            sp.items = c->ix_items;
+            sp.cstart = c->ix_cstart;
+            sp.nextra = c->ix_nextra;
+            sp.ncell = c->ix_ncell;
+        }
+        LAUNCH(c, launch_sepcheck_rows(sp, s));
+        JudgeArgs ja{};
+        ja.reqs = B.rq;
+        ja.idx = todo;
+        ja.n_dev = B.ctr.p + 1;
+        ja.n = n_cap;
+        ja.traj_p = c->p_traj.p;
+        ja.acts_p = c->p_acts.p;
+        ja.rout_p = c->p_rout.p;
+        ja.sep_p = c->p_sep.p;
+        ja.traj = B.traj.p;
+        ja.acts = B.acts.p;
+        ja.rout = B.rout.p;
+        ja.sep = B.sepo.p;
+        ja.accepted = c->p_acc.p;
+        ja.cap = cap;
+        ja.dt = c->air.dt;
+        ja.slack = c->slack;
+        ja.climb_step = climb_step(c);
+        LAUNCH(c, launch_judge(ja, cap, s));
+    }
     {
         RolloutArgs ra{};
         ra.m = c->model;
@@ -796,6 +887,7 @@ void enqueue_wave(fmdp_ctx* c, const Geometry& g, int n_clusters, BatchBuffers& 
         ra.queue = B.ctr.p;
         ra.idx = todo;
         ra.n_dev = B.ctr.p + 1;
+        ra.skip = c->learned_mode ? c->p_acc.p : nullptr;
         KernelTimer t(c, timed ? 0 : -1);
         LAUNCH(c, launch_rollout(ra, g.threads, g.smem, s, n_clusters));
         t.stop();
@@ -813,6 +905,7 @@ void enqueue_wave(fmdp_ctx* c, const Geometry& g, int n_clusters, BatchBuffers& 
         sa.n_dev = B.ctr.p + 1;
         sa.n_max = n_cap;
         sa.out = B.sepo.p;
+        sa.skip = c->learned_mode ? c->p_acc.p : nullptr;
         if (c->index_on) {
             sa.items = c->ix_items;
             sa.cstart = c->ix_cstart;
@@ -831,7 +924,8 @@ void enqueue_wave(fmdp_ctx* c, const Geometry& g, int n_clusters, BatchBuffers& 
         ia.cap = cap;
         ia.idx = unres;
         ia.n_dev = B.ctr.p + 2;
-        ia.reach_base = c->model.reach_base;
+        // a proposal also reads the plans within the feature radius of its states
+        ia.reach_base = c->learned_mode ? std::max(c->model.reach_base, kRF + 1.0f) : c->model.reach_base;
         ia.tau_absmax = c->model.tau_absmax;
         float dzmax = 0.f;
         for (int i = 0; i < c->model.A; ++i) dzmax = std::max(dzmax, (float)std::fabs(c->model.climb[i] * c->model.dt));
@@ -848,6 +942,8 @@ void enqueue_wave(fmdp_ctx* c, const Geometry& g, int n_clusters, BatchBuffers& 
     CK(cudaMemcpyAsync(B.h_rout.p, B.rout.p, B.rq_cap * sizeof(RolloutOut), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(B.h_sep.p, B.sepo.p, B.rq_cap * sizeof(SepOut), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(B.h_infl.p, B.infl.p, (size_t)n_cap * n_cap, cudaMemcpyDeviceToHost, s));
+    if (c->learned_mode)
+        CK(cudaMemcpyAsync(B.h_acc.p, c->p_acc.p, B.rq_cap * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
 }
 
 // The wave sequence as an instantiated CUDA graph, captured on a private stream the first
@@ -858,7 +954,9 @@ cudaGraphExec_t wave_graph(fmdp_ctx* c, const Geometry& g, int n_clusters, Batch
                                       B.n_cap, B.rq_cap, B.cap, (int64_t)(uintptr_t)B.idx.p,
                                       (int64_t)(uintptr_t)B.traj.p, (int64_t)(uintptr_t)B.rq,
                                       (int64_t)(uintptr_t)B.rout.p, (int64_t)(uintptr_t)B.h_idx.p,
-                                      (int64_t)(uintptr_t)B.h_infl.p, (int64_t)(uintptr_t)tv.X, tv.t_base};
+                                      (int64_t)(uintptr_t)B.h_infl.p, (int64_t)(uintptr_t)tv.X, tv.t_base,
+                                      c->learned_mode ? 1 : 0, (int64_t)(uintptr_t)c->p_traj.p,
+                                      (int64_t)(uintptr_t)c->p_acc.p, (int64_t)(c->slack * 1e9)};
     for (size_t i = 0; i < c->graphs.size(); ++i)
         if (c->graphs[i].key == key) {
             std::swap(c->graphs[i], c->graphs[0]);
@@ -957,6 +1055,7 @@ struct Speculator {
         pending.clear();  // the previous walk's admissions are now in the table
         c->stats.batch_waves++;
         for (int32_t r : todo) {
+            if (c->learned_mode && B.h_acc.p[r]) continue;  // no FastMDP rollout ran
             const RolloutOut& ro = B.h_rout.p[r];
             c->stats.rollout_steps += ro.steps;
             c->stats.slots_scanned += (int64_t)ro.steps * g.S_scan;
@@ -1147,6 +1246,17 @@ int32_t run_batch(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_result*
     if (n <= 0) return 0;
     const int32_t bs = c->opt.batch_size > 0 ? c->opt.batch_size : kBatchDefault;
     batch_prepare(c, reqs, n, std::min(n, bs), dev_reqs);
+    if (c->learned_mode) {
+        const size_t R = c->bat.rq_cap;
+        c->p_traj.ensure(R * c->bat.cap * 3);
+        c->p_acts.ensure(R * c->bat.cap);
+        c->p_rout.ensure(R);
+        c->p_sep.ensure(R);
+        c->p_acc.ensure(R);
+        c->p_queue.ensure(1);
+        c->bat.h_acc.ensure(R);
+        CK(cudaMemsetAsync(c->p_acc.p, 0, R * sizeof(int32_t), c->stream));
+    }
     Speculator sp(c, reqs, n);
     std::vector<int32_t> resolved;
     for (int32_t b0 = 0; b0 < n; b0 += bs) {
@@ -1165,6 +1275,322 @@ int32_t run_batch(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_result*
     sp.results(0, n, res);
     if (!keep_points) copy_points_back(c, n, res);
     return sp.admitted;
+}
+
+
+// ------------------------------------------------------------------ learned proposal
+
+// platform-independent random numbers (splitmix64; Box-Muller normals)
+struct SplitMix {
+    uint64_t s;
+    uint64_t next() {
+        uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    }
+    double uniform() { return (double)(next() >> 11) * (1.0 / 9007199254740992.0); }
+    double normal() {
+        const double u1 = std::max(uniform(), 1e-300), u2 = uniform();
+        return std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2);
+    }
+};
+
+size_t wt_offset(int l) {
+    size_t o = 0;
+    for (int i = 0; i < l; ++i) o += (size_t)layer_in(i) * layer_out_pad(i);
+    return o;
+}
+
+void mlp_ensure(fmdp_ctx* c) {
+    const size_t P = n_params_total();
+    c->mlp_p.ensure(P);
+    c->mlp_g.ensure(P);
+    c->mlp_m1.ensure(P);
+    c->mlp_m2.ensure(P);
+    c->mlp_wt.ensure(wt_offset(kLayers));
+    c->mlp_wp.ensure(wp_total());
+    c->tr_loss.ensure(1);
+}
+
+void mlp_upload(fmdp_ctx* c, const float* params) {
+    mlp_ensure(c);
+    const size_t P = n_params_total();
+    CK(cudaMemcpyAsync(c->mlp_p.p, params, P * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemsetAsync(c->mlp_m1.p, 0, P * sizeof(float), c->stream));
+    CK(cudaMemsetAsync(c->mlp_m2.p, 0, P * sizeof(float), c->stream));
+    c->adam_t = 0;
+    LAUNCH(c, launch_export_weights(c->mlp_p.p, c->mlp_wt.p, c->mlp_wp.p, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->mlp_ready = true;
+}
+
+// forward and backward of one batch (X: B rows of bf16 features on the device, y labels):
+// the batch's mean loss is added to tr_loss[0], the gradient written to mlp_g
+void mlp_fwd_bwd(fmdp_ctx* c, const __nv_bfloat16* X, const uint8_t* y, int B) {
+    cudaStream_t s = c->stream;
+    c->trH.ensure((size_t)4 * B * kHid);
+    c->trZ.ensure((size_t)B * kHid);
+    c->trdZ.ensure((size_t)B * kHid);
+    c->trdZf.ensure((size_t)B * kHid);
+    c->trdH.ensure((size_t)B * kHid);
+    auto H = [&](int l) -> const __nv_bfloat16* { return l == 0 ? X : c->trH.p + (size_t)(l - 1) * B * kHid; };
+    auto ldH = [&](int l) { return l == 0 ? kFeat : kHid; };
+    const __nv_bfloat16* Wt = c->mlp_wt.p;
+    const float* P = c->mlp_p.p;
+    float* G = c->mlp_g.p;
+    for (int l = 0; l < kLayers - 1; ++l) {
+        LAUNCH(c, launch_gemm_bf16(B, kHid, layer_in(l), H(l), ldH(l), 1, Wt + wt_offset(l), kHid, 1, c->trZ.p, kHid, 0, s));
+        LAUNCH(c, launch_bias_act(c->trZ.p, P + param_offset_b(l), c->trH.p + (size_t)l * B * kHid, B, kHid, kHid, kHid,
+                                  1, s));
+    }
+    const int L4 = kLayers - 1;
+    LAUNCH(c, launch_gemm_bf16(B, kOutPad, kHid, H(L4), kHid, 1, Wt + wt_offset(L4), kOutPad, 1, c->trZ.p, kOutPad, 0, s));
+    LAUNCH(c, launch_softmax_ce(c->trZ.p, kOutPad, P + param_offset_b(L4), y, B, c->A, c->trdZ.p, kOutPad, c->trdZf.p,
+                                c->tr_loss.p, s));
+    for (int l = kLayers - 1; l >= 0; --l) {
+        const int ld_dz = l == kLayers - 1 ? kOutPad : kHid, out = layer_out(l);
+        LAUNCH(c, launch_gemm_bf16(layer_in(l), out, B, H(l), 1, ldH(l), c->trdZ.p, ld_dz, 1, G + param_offset_W(l), out,
+                                   0, s));
+        LAUNCH(c, launch_colsum(c->trdZf.p, B, out, ld_dz, G + param_offset_b(l), s));
+        if (l > 0) {
+            LAUNCH(c, launch_gemm_bf16(B, layer_in(l), out, c->trdZ.p, ld_dz, 1, Wt + wt_offset(l), 1,
+                                       layer_out_pad(l), c->trdH.p, kHid, 0, s));
+            LAUNCH(c, launch_relu_bwd(c->trdH.p, H(l), B, kHid, c->trdZ.p, c->trdZf.p, s));
+        }
+    }
+}
+
+void mlp_train(fmdp_ctx* c, int32_t epochs, int32_t batch, float lr, uint64_t seed, float* losses) {
+    require(c->mlp_ready, FMDP_ERR_ARG, "the proposal network has no parameters (init or set them first)");
+    require(c->t_rows > 0, FMDP_ERR_ARG, "no training rows (collect first)");
+    require(epochs >= 0 && batch >= 1 && batch <= 8192 && lr > 0.f, FMDP_ERR_ARG, "training options out of range");
+    const int64_t rows = c->t_rows;
+    c->tr_idx.ensure(rows);
+    c->trX.ensure((size_t)batch * kFeat);
+    c->tr_y.ensure(batch);
+    std::vector<int32_t> perm(rows);
+    SplitMix rng{seed};
+    for (int32_t e = 0; e < epochs; ++e) {
+        for (int64_t i = 0; i < rows; ++i) perm[i] = (int32_t)i;
+        for (int64_t i = rows - 1; i > 0; --i) std::swap(perm[i], perm[(int64_t)(rng.next() % (uint64_t)(i + 1))]);
+        CK(cudaMemcpyAsync(c->tr_idx.p, perm.data(), rows * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemsetAsync(c->tr_loss.p, 0, sizeof(float), c->stream));
+        int64_t nb = 0;
+        for (int64_t b0 = 0; b0 < rows; b0 += batch, ++nb) {
+            const int Bn = (int)std::min<int64_t>(batch, rows - b0);
+            LAUNCH(c, launch_gather_rows(c->tX.p, c->tr_idx.p + b0, Bn, c->trX.p, c->ty.p, c->tr_y.p, c->stream));
+            mlp_fwd_bwd(c, c->trX.p, c->tr_y.p, Bn);
+            LAUNCH(c, launch_adam(c->mlp_p.p, c->mlp_g.p, c->mlp_m1.p, c->mlp_m2.p, n_params_total(), lr, 0.9f, 0.999f,
+                                  1e-8f, (int)++c->adam_t, c->stream));
+            LAUNCH(c, launch_export_weights(c->mlp_p.p, c->mlp_wt.p, c->mlp_wp.p, c->stream));
+        }
+        float tot = 0.f;
+        CK(cudaMemcpyAsync(&tot, c->tr_loss.p, sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        if (losses) losses[e] = nb ? tot / (float)nb : 0.f;
+    }
+    CK(cudaStreamSynchronize(c->stream));
+}
+
+// grows a device array to `want` elements, keeping its first `keep` elements
+template <class T>
+void grow_keep(fmdp_ctx* c, DevArray<T>& a, size_t want, size_t keep) {
+    if (want <= a.n) return;
+    DevArray<T> b;
+    b.ensure(std::max(want, a.n * 2));
+    if (keep) CK(cudaMemcpyAsync(b.p, a.p, keep * sizeof(T), cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    a.release();
+    a.p = b.p;
+    a.n = b.n;
+    b.p = nullptr;
+    b.n = 0;
+}
+
+// FastMDP rollouts of every request against the table as it stands (persistent work-queue
+// launch; nothing is checked or admitted); trajectories in the batch buffers
+void plan_all_fastmdp(fmdp_ctx* c, int32_t n) {
+    BatchBuffers& B = c->bat;
+    const Geometry g = batch_geometry(c, 0);
+    const int n_clusters = std::max(1, std::min(n, rollout_max_active_clusters(g.cs, g.threads, g.smem)));
+    CK(cudaMemsetAsync(B.ctr.p, 0, sizeof(int32_t), c->stream));
+    RolloutArgs ra{};
+    ra.m = c->model;
+    ra.tab = table_view(c);
+    ra.S_scan = g.S_scan;
+    ra.chunk = g.chunk;
+    ra.cs = g.cs;
+    ra.ring = g.ring;
+    ra.cap = B.cap;
+    ra.reqs = B.rq;
+    ra.n_req = n;
+    ra.traj = B.traj.p;
+    ra.acts = B.acts.p;
+    ra.out = B.rout.p;
+    ra.err = c->err;
+    set_index_args(c, ra);
+    ra.queue = B.ctr.p;
+    LAUNCH(c, launch_rollout(ra, g.threads, g.smem, c->stream, n_clusters));
+}
+
+void learned_collect(fmdp_ctx* c, const fmdp_request* reqs, int32_t n) {
+    require(c->index_on, FMDP_ERR_ARG, "the learned proposal reads the spatial index (full_scan must be 0)");
+    if (n <= 0) return;
+    batch_prepare(c, reqs, n, 64, nullptr);
+    BatchBuffers& B = c->bat;
+    plan_all_fastmdp(c, n);
+    CK(cudaMemcpyAsync(B.h_rout.p, B.rout.p, n * sizeof(RolloutOut), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    require(read_error_word(c) == 0, FMDP_ERR_TIMEOUT, "a bounded device wait expired during a rollout");
+    std::vector<int64_t> row0(n);
+    int64_t rows = c->t_rows;
+    for (int32_t i = 0; i < n; ++i) {
+        row0[i] = rows;
+        rows += std::max(B.h_rout.p[i].n_points - 1, 0);
+    }
+    grow_keep(c, c->tX, (size_t)rows * kFeat, (size_t)c->t_rows * kFeat);
+    grow_keep(c, c->ty, (size_t)rows, (size_t)c->t_rows);
+    c->row0.ensure(n);
+    CK(cudaMemcpyAsync(c->row0.p, row0.data(), n * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
+    CollectArgs ca{};
+    ca.m = c->model;
+    ca.tab = table_view(c);
+    ca.iv = index_view(c);
+    ca.traj = B.traj.p;
+    ca.acts = B.acts.p;
+    ca.cap = B.cap;
+    ca.rout = B.rout.p;
+    ca.reqs = B.rq;
+    ca.row0 = c->row0.p;
+    ca.X = c->tX.p;
+    ca.y = c->ty.p;
+    ca.n = n;
+    LAUNCH(c, launch_collect(ca, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->t_rows = rows;
+}
+
+void learned_evaluate(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, double slack, fmdp_learned_report* rep,
+                      int32_t* accepted, int32_t* steps_p, int32_t* steps_f) {
+    require(c->index_on, FMDP_ERR_ARG, "the learned proposal reads the spatial index (full_scan must be 0)");
+    require(c->mlp_ready, FMDP_ERR_ARG, "the proposal network has no parameters (init or set them first)");
+    require(slack >= 0.0, FMDP_ERR_ARG, "slack must be >= 0");
+    fmdp_learned_report r{};
+    r.n = n;
+    if (n <= 0) {
+        if (rep) *rep = r;
+        return;
+    }
+    batch_prepare(c, reqs, n, 64, nullptr);
+    BatchBuffers& B = c->bat;
+    const size_t R = B.rq_cap;
+    c->p_traj.ensure(R * B.cap * 3);
+    c->p_acts.ensure(R * B.cap);
+    c->p_rout.ensure(R);
+    c->p_sep.ensure(R);
+    c->p_acc.ensure(R);
+    c->p_queue.ensure(1);
+    c->p_ident.ensure(R);
+    std::vector<int32_t> ident(n);
+    for (int32_t i = 0; i < n; ++i) ident[i] = i;
+    CK(cudaMemcpyAsync(c->p_ident.p, ident.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+    cudaEvent_t e[4];
+    for (auto& ev : e) CK(cudaEventCreate(&ev));
+    // proposals for every request
+    CK(cudaMemsetAsync(c->p_queue.p, 0, sizeof(int32_t), c->stream));
+    PolicyArgs pa{};
+    pa.m = c->model;
+    pa.tab = table_view(c);
+    pa.iv = index_view(c);
+    pa.Wp = c->mlp_wp.p;
+    pa.params = c->mlp_p.p;
+    pa.reqs = B.rq;
+    pa.n_items = n;
+    pa.queue = c->p_queue.p;
+    pa.cap = B.cap;
+    pa.traj = c->p_traj.p;
+    pa.acts = c->p_acts.p;
+    pa.out = c->p_rout.p;
+    pa.err = c->err;
+    CK(cudaEventRecord(e[0], c->stream));
+    LAUNCH(c, launch_policy(pa, std::min(c->n_sm, (n + kPolicyRows - 1) / kPolicyRows), c->stream));
+    CK(cudaEventRecord(e[1], c->stream));
+    // their separation checks and the judge (decisions only), in chunks of the row kernel's size
+    LAUNCH(c, launch_sep_reset(c->p_sep.p, n, c->stream));
+    for (int32_t o = 0; o < n; o += kBatchMax) {
+        const int32_t m = std::min<int32_t>(kBatchMax, n - o);
+        B.h_ctr.p[1] = m;
+        CK(cudaMemcpyAsync(B.ctr.p + 1, &B.h_ctr.p[1], sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+        SepRowsArgs sp{};
+        sp.m = c->model;
+        sp.tab = table_view(c);
+        sp.S_scan = c->S_pad;
+        sp.traj = c->p_traj.p;
+        sp.cap = B.cap;
+        sp.rout = c->p_rout.p;
+        sp.reqs = B.rq;
+        sp.idx = c->p_ident.p + o;
+        sp.n_dev = B.ctr.p + 1;
+        sp.n_max = m;
+        sp.out = c->p_sep.p;
+        sp.items = c->ix_items;
+        sp.cstart = c->ix_cstart;
+        sp.nextra = c->ix_nextra;
+        sp.ncell = c->ix_ncell;
+        LAUNCH(c, launch_sepcheck_rows(sp, c->stream));
+        CK(cudaStreamSynchronize(c->stream));  // the count word is reused by the next chunk
+    }
+    JudgeArgs ja{};
+    ja.reqs = B.rq;
+    ja.n = n;
+    ja.traj_p = c->p_traj.p;
+    ja.acts_p = c->p_acts.p;
+    ja.rout_p = c->p_rout.p;
+    ja.sep_p = c->p_sep.p;
+    ja.accepted = c->p_acc.p;
+    ja.cap = B.cap;
+    ja.dt = c->air.dt;
+    ja.slack = slack;
+    ja.climb_step = climb_step(c);
+    LAUNCH(c, launch_judge(ja, B.cap, c->stream));
+    // FastMDP plans of every request
+    CK(cudaEventRecord(e[2], c->stream));
+    plan_all_fastmdp(c, n);
+    CK(cudaEventRecord(e[3], c->stream));
+    std::vector<RolloutOut> rp(n), rf(n);
+    std::vector<int32_t> acc(n);
+    CK(cudaMemcpyAsync(rp.data(), c->p_rout.p, n * sizeof(RolloutOut), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(rf.data(), B.rout.p, n * sizeof(RolloutOut), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(acc.data(), c->p_acc.p, n * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    float ms1 = 0.f, ms2 = 0.f;
+    CK(cudaEventElapsedTime(&ms1, e[0], e[1]));
+    CK(cudaEventElapsedTime(&ms2, e[2], e[3]));
+    for (auto& ev : e) cudaEventDestroy(ev);
+    require(read_error_word(c) == 0, FMDP_ERR_TIMEOUT, "a bounded device wait expired during a rollout");
+    double gap_sum = 0.0;
+    int32_t gap_n = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        r.accepted += acc[i];
+        r.proposals_captured += rp[i].status == kStatusCaptured;
+        r.fastmdp_captured += rf[i].status == kStatusCaptured;
+        r.proposal_steps += rp[i].steps;
+        r.fastmdp_steps += rf[i].steps;
+        if (acc[i] && rf[i].status == kStatusCaptured && rf[i].steps > 0) {
+            const double gap = (double)(rp[i].steps - rf[i].steps) / rf[i].steps;
+            gap_sum += gap;
+            r.max_gap = gap_n ? std::max(r.max_gap, gap) : gap;
+            ++gap_n;
+        }
+        if (accepted) accepted[i] = acc[i];
+        if (steps_p) steps_p[i] = rp[i].steps;
+        if (steps_f) steps_f[i] = rf[i].steps;
+    }
+    r.mean_gap = gap_n ? gap_sum / gap_n : 0.0;
+    r.proposal_ms = ms1;
+    r.fastmdp_ms = ms2;
+    if (rep) *rep = r;
 }
 
 // ------------------------------------------------------------------ serving loop
@@ -1421,6 +1847,11 @@ void destroy_ctx(fmdp_ctx* c) {
                     (void*)c->items_ctr})
         if (p) cudaFree(p);
     c->seq.release(); c->stg.release(); c->bat.release();
+    c->mlp_p.release(); c->mlp_g.release(); c->mlp_m1.release(); c->mlp_m2.release(); c->mlp_wt.release();
+    c->mlp_wp.release(); c->tX.release(); c->ty.release(); c->trX.release(); c->trH.release(); c->trdZ.release();
+    c->trZ.release(); c->trdZf.release(); c->trdH.release(); c->tr_loss.release(); c->tr_idx.release();
+    c->tr_y.release(); c->p_traj.release(); c->p_acts.release(); c->p_rout.release(); c->p_sep.release();
+    c->p_acc.release(); c->p_queue.release(); c->p_ident.release(); c->row0.release();
     for (auto& g : c->graphs)
         if (g.exec) cudaGraphExecDestroy(g.exec);
     c->reqs.release(); c->traj.release(); c->acts.release(); c->rout.release(); c->sepo.release();
@@ -1554,10 +1985,12 @@ fmdp_status fmdp_create(const fmdp_airspace* air, double gamma, const fmdp_actio
 
         CK(cudaGetDevice(&c->device));
         CK(cudaDeviceGetAttribute(&c->max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
+        CK(cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device));
         CK(cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking));
         c->stream = c->own;
         CK(prepare_rollout_kernel((size_t)c->max_smem));
         CK(prepare_sepcheck_rows(sepcheck_rows_smem(kBatchMax)));
+        CK(prepare_policy_kernel());
 
         c->T_win = a.n_slices_window;
         c->S_max = a.max_slots;
@@ -1839,6 +2272,145 @@ fmdp_status fmdp_serve(fmdp_ctx* c, const fmdp_request* reqs, const double* arri
                     FMDP_ERR_ARG, "arrival times must be finite, >= 0 and non-decreasing");
         }
         run_serve(c, reqs, arrival_s, n, o, res, latency_ms, report);
+    });
+}
+
+fmdp_status fmdp_learned_collect(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, int32_t* n_rows_out) {
+    if (!c) return FMDP_ERR_ARG;
+    return guard(c, [&] {
+        require(n >= 0 && (n == 0 || reqs), FMDP_ERR_ARG, "null requests");
+        for (int32_t i = 0; i < n; ++i) check_request(c, reqs[i]);
+        learned_collect(c, reqs, n);
+        require(c->t_rows < INT32_MAX, FMDP_ERR_FULL, "training set too large");
+        if (n_rows_out) *n_rows_out = (int32_t)c->t_rows;
+    });
+}
+
+fmdp_status fmdp_learned_rows(fmdp_ctx* c, float* X, uint8_t* y, int32_t max_rows, int32_t* n_out) {
+    if (!c) return FMDP_ERR_ARG;
+    return guard(c, [&] {
+        require(max_rows >= 0 && n_out, FMDP_ERR_ARG, "null output");
+        const int64_t m = std::min<int64_t>(max_rows, c->t_rows);
+        if (m > 0 && X) {
+            std::vector<__nv_bfloat16> h((size_t)m * kFeat);
+            CK(cudaMemcpyAsync(h.data(), c->tX.p, h.size() * sizeof(__nv_bfloat16), cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaStreamSynchronize(c->stream));
+            for (size_t i = 0; i < h.size(); ++i) X[i] = __bfloat162float(h[i]);
+        }
+        if (m > 0 && y) {
+            CK(cudaMemcpyAsync(y, c->ty.p, (size_t)m, cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaStreamSynchronize(c->stream));
+        }
+        *n_out = (int32_t)m;
+    });
+}
+
+fmdp_status fmdp_learned_clear_rows(fmdp_ctx* c) {
+    if (!c) return FMDP_ERR_ARG;
+    return guard(c, [&] { c->t_rows = 0; });
+}
+
+fmdp_status fmdp_learned_init(fmdp_ctx* c, uint64_t seed) {
+    if (!c) return FMDP_ERR_ARG;
+    return guard(c, [&] {
+        std::vector<float> prm(n_params_total(), 0.f);
+        SplitMix rng{seed};
+        for (int l = 0; l < kLayers; ++l) {
+            const double sd = std::sqrt(2.0 / layer_in(l));
+            float* W = prm.data() + param_offset_W(l);
+            for (size_t i = 0; i < (size_t)layer_in(l) * layer_out(l); ++i) W[i] = (float)(sd * rng.normal());
+        }
+        mlp_upload(c, prm.data());
+    });
+}
+
+fmdp_status fmdp_learned_set_params(fmdp_ctx* c, const float* params, int32_t n) {
+    if (!c) return FMDP_ERR_ARG;
+    return guard(c, [&] {
+        require(params && n == (int32_t)n_params_total(), FMDP_ERR_ARG, "expected FMDP_MLP_PARAMS parameters");
+        for (int32_t i = 0; i < n; ++i) require(std::isfinite(params[i]), FMDP_ERR_ARG, "parameters must be finite");
+        mlp_upload(c, params);
+    });
+}
+
+fmdp_status fmdp_learned_get_params(fmdp_ctx* c, float* params, int32_t n) {
+    if (!c) return FMDP_ERR_ARG;
+    return guard(c, [&] {
+        require(params && n == (int32_t)n_params_total(), FMDP_ERR_ARG, "expected FMDP_MLP_PARAMS parameters");
+        require(c->mlp_ready, FMDP_ERR_ARG, "the proposal network has no parameters");
+        CK(cudaMemcpyAsync(params, c->mlp_p.p, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    });
+}
+
+fmdp_status fmdp_learned_train(fmdp_ctx* c, int32_t epochs, int32_t batch, float lr, uint64_t seed,
+                               float* loss_per_epoch) {
+    if (!c) return FMDP_ERR_ARG;
+    return guard(c, [&] { mlp_train(c, epochs, batch, lr, seed, loss_per_epoch); });
+}
+
+fmdp_status fmdp_learned_loss_grad(fmdp_ctx* c, const float* X, const uint8_t* y, int32_t rows, float* loss,
+                                   float* grad) {
+    if (!c) return FMDP_ERR_ARG;
+    return guard(c, [&] {
+        require(X && y && loss && grad && rows >= 1 && rows <= 8192, FMDP_ERR_ARG, "null arrays or rows out of range");
+        require(c->mlp_ready, FMDP_ERR_ARG, "the proposal network has no parameters");
+        for (int32_t i = 0; i < rows; ++i) require(y[i] < c->A, FMDP_ERR_ARG, "label beyond the action set");
+        std::vector<__nv_bfloat16> h((size_t)rows * kFeat);
+        for (size_t i = 0; i < h.size(); ++i) h[i] = __float2bfloat16_rn(X[i]);
+        c->trX.ensure((size_t)rows * kFeat);
+        c->tr_y.ensure(rows);
+        CK(cudaMemcpyAsync(c->trX.p, h.data(), h.size() * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(c->tr_y.p, y, rows, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemsetAsync(c->tr_loss.p, 0, sizeof(float), c->stream));
+        mlp_fwd_bwd(c, c->trX.p, c->tr_y.p, rows);
+        CK(cudaMemcpyAsync(loss, c->tr_loss.p, sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaMemcpyAsync(grad, c->mlp_g.p, n_params_total() * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    });
+}
+
+fmdp_status fmdp_learned_evaluate(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, double slack,
+                                  fmdp_learned_report* report, int32_t* accepted, int32_t* steps_p,
+                                  int32_t* steps_f) {
+    if (!c) return FMDP_ERR_ARG;
+    return guard(c, [&] {
+        require(n >= 0 && (n == 0 || reqs), FMDP_ERR_ARG, "null requests");
+        for (int32_t i = 0; i < n; ++i) check_request(c, reqs[i]);
+        learned_evaluate(c, reqs, n, slack, report, accepted, steps_p, steps_f);
+    });
+}
+
+fmdp_status fmdp_schedule_learned(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, double slack, fmdp_result* res,
+                                  fmdp_learned_report* report) {
+    if (!c) return FMDP_ERR_ARG;
+    return guard(c, [&] {
+        require(n >= 0 && (n == 0 || (reqs && res)), FMDP_ERR_ARG, "null requests or results");
+        require(c->index_on, FMDP_ERR_ARG, "the learned proposal reads the spatial index (full_scan must be 0)");
+        require(c->mlp_ready, FMDP_ERR_ARG, "the proposal network has no parameters (init or set them first)");
+        require(slack >= 0.0 && std::isfinite(slack), FMDP_ERR_ARG, "slack must be >= 0");
+        for (int32_t i = 0; i < n; ++i) check_request(c, reqs[i]);
+        c->learned_mode = true;
+        c->slack = slack;
+        try {
+            run_batch(c, reqs, n, res, nullptr, false);
+        } catch (...) {
+            c->learned_mode = false;
+            throw;
+        }
+        c->learned_mode = false;
+        std::vector<int32_t> acc(std::max(n, 1));
+        if (n > 0) {
+            CK(cudaMemcpyAsync(acc.data(), c->p_acc.p, n * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaStreamSynchronize(c->stream));
+        }
+        fmdp_learned_report r{};
+        r.n = n;
+        for (int32_t i = 0; i < n; ++i) {
+            res[i].source = acc[i] ? 1 : 0;
+            r.accepted += acc[i] ? 1 : 0;
+        }
+        if (report) *report = r;
     });
 }
 

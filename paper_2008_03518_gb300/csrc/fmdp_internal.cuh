@@ -122,6 +122,7 @@ struct RolloutArgs {
     int32_t icap;     // indexed mode: items per staging buffer in shared memory
     IndexView iv;
     unsigned long long* items_ctr;  // indexed mode: items read by the steps (statistics) or nullptr
+    const int32_t* skip;            // batch mode: request r is not planned when skip[r] (nullptr: none)
 };
 
 struct SepArgs {
@@ -249,6 +250,7 @@ struct SepRowsArgs {
     const int32_t* cstart;
     const int32_t* nextra;
     int32_t ncell;
+    const int32_t* skip;    // request r is not checked when skip[r] (nullptr: none)
 };
 cudaError_t launch_sepcheck_rows(const SepRowsArgs& a, cudaStream_t s);
 size_t sepcheck_rows_smem(int n_max);
@@ -326,6 +328,26 @@ __device__ __forceinline__ float terrain32(const Model& m, float x, float y) {
     return (1.f - ay) * ((1.f - ax) * h00 + ax * h10) + ay * ((1.f - ax) * h01 + ax * h11);
 }
 constexpr float kTerrBand = 0.25f;  // metres: fp32 terrain-collision margin before an FP64 check
+
+// cos / sin of k * 15 degrees from their surd forms (exact IEEE operations only).
+__device__ __forceinline__ void unit15(int k, double& ck, double& sk) {
+    const double r2 = __dsqrt_rn(2.0), r3 = __dsqrt_rn(3.0), r6 = __dsqrt_rn(6.0);
+    const double c15 = __ddiv_rn(__dadd_rn(r6, r2), 4.0), s15 = __ddiv_rn(__dsub_rn(r6, r2), 4.0);
+    const int m = k % 6, quad = k / 6;
+    double qc, qs;
+    switch (m) {
+        case 0: qc = 1.0; qs = 0.0; break;
+        case 1: qc = c15; qs = s15; break;
+        case 2: qc = __ddiv_rn(r3, 2.0); qs = 0.5; break;
+        case 3: qc = __ddiv_rn(r2, 2.0); qs = __ddiv_rn(r2, 2.0); break;
+        case 4: qc = 0.5; qs = __ddiv_rn(r3, 2.0); break;
+        default: qc = s15; qs = c15; break;
+    }
+    if (quad == 0) { ck = qc; sk = qs; }
+    else if (quad == 1) { ck = -qs; sk = qc; }
+    else if (quad == 2) { ck = -qc; sk = -qs; }
+    else { ck = qs; sk = -qc; }
+}
 
 __device__ __forceinline__ double norm3_64(double dx, double dy, double dz) {
     return __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));

@@ -231,25 +231,6 @@ __host__ __device__ inline Layout make_layout(int chunk, int depth, int icap) {
     return L;
 }
 
-// cos / sin of k * 15 degrees from their surd forms (exact IEEE operations only).
-__device__ void unit15(int k, double& ck, double& sk) {
-    const double r2 = __dsqrt_rn(2.0), r3 = __dsqrt_rn(3.0), r6 = __dsqrt_rn(6.0);
-    const double c15 = __ddiv_rn(__dadd_rn(r6, r2), 4.0), s15 = __ddiv_rn(__dsub_rn(r6, r2), 4.0);
-    const int m = k % 6, quad = k / 6;
-    double qc, qs;
-    switch (m) {
-        case 0: qc = 1.0; qs = 0.0; break;
-        case 1: qc = c15; qs = s15; break;
-        case 2: qc = __ddiv_rn(r3, 2.0); qs = 0.5; break;
-        case 3: qc = __ddiv_rn(r2, 2.0); qs = __ddiv_rn(r2, 2.0); break;
-        case 4: qc = 0.5; qs = __ddiv_rn(r3, 2.0); break;
-        default: qc = s15; qs = c15; break;
-    }
-    if (quad == 0) { ck = qc; sk = qs; }
-    else if (quad == 1) { ck = -qs; sk = qc; }
-    else if (quad == 2) { ck = -qc; sk = -qs; }
-    else { ck = qs; sk = -qc; }
-}
 
 // Exact (FP64, method order) well-edge decision for a plan well.
 __device__ __noinline__ bool well_inside_exact(const Model& m, const StepState* st, double Dx, double Dy,
@@ -1268,7 +1249,9 @@ __global__ void __launch_bounds__(384, 1) rollout_kernel(const __grid_constant__
             __syncthreads();
         }
         if (w >= n) break;
-        plan_request(a, a.idx ? a.idx[w] : w, smem);
+        const int r = a.idx ? a.idx[w] : w;
+        if (a.skip && a.skip[r]) continue;  // uniform over the cluster: every CTA read the same item
+        plan_request(a, r, smem);
     }
 }
 

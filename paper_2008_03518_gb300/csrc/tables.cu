@@ -288,6 +288,7 @@ __global__ void __launch_bounds__(kRowThreads) sepcheck_rows_kernel(const __grid
     const int n = *a.n_dev;
     for (int w = tid; w < n; w += NT) {
         const int r = a.idx[w];
+        if (a.skip && a.skip[r]) continue;
         const int64_t d = a.reqs[r].depart_step;
         const int np = a.rout[r].n_points;
         if (T >= d && T < d + np) {

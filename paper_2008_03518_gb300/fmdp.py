@@ -69,12 +69,23 @@ class Result(ctypes.Structure):
     _fields_ = [("verdict", ctypes.c_int32), ("n_points", ctypes.c_int32), ("plan_id", ctypes.c_uint64),
                 ("first_conflict_step", ctypes.c_int32), ("first_terrain_step", ctypes.c_int32),
                 ("min_sep_h", ctypes.c_double), ("min_sep_v", ctypes.c_double), ("near_ties", ctypes.c_int32),
-                ("replanned", ctypes.c_int32), ("xyz", _fp), ("actions", ctypes.POINTER(ctypes.c_uint8))]
+                ("replanned", ctypes.c_int32), ("source", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("xyz", _fp), ("actions", ctypes.POINTER(ctypes.c_uint8))]
 
 
 class SepReport(ctypes.Structure):
     _fields_ = [("first_conflict_step", ctypes.c_int32), ("first_terrain_step", ctypes.c_int32),
                 ("conflicts", ctypes.c_int64), ("min_sep_h", ctypes.c_double), ("min_sep_v", ctypes.c_double)]
+
+
+MLP_PARAMS = 236825
+
+
+class LearnedReport(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("accepted", ctypes.c_int32), ("proposals_captured", ctypes.c_int32),
+                ("fastmdp_captured", ctypes.c_int32), ("mean_gap", ctypes.c_double), ("max_gap", ctypes.c_double),
+                ("proposal_steps", ctypes.c_int64), ("fastmdp_steps", ctypes.c_int64),
+                ("proposal_ms", ctypes.c_double), ("fastmdp_ms", ctypes.c_double)]
 
 
 class ServeOptions(ctypes.Structure):
@@ -111,6 +122,9 @@ EXPORTS = ("fmdp_options_default", "fmdp_create", "fmdp_destroy", "fmdp_last_err
            "fmdp_add_plan", "fmdp_add_plans", "fmdp_schedule", "fmdp_schedule_many", "fmdp_schedule_batch",
            "fmdp_stage_requests", "fmdp_schedule_staged", "fmdp_fetch_staged", "fmdp_query_plans",
            "fmdp_serve", "fmdp_serve_options_default",
+           "fmdp_learned_collect", "fmdp_learned_rows", "fmdp_learned_clear_rows", "fmdp_learned_init",
+           "fmdp_learned_set_params", "fmdp_learned_get_params", "fmdp_learned_train", "fmdp_learned_loss_grad",
+           "fmdp_learned_evaluate", "fmdp_schedule_learned",
            "fmdp_get_plan", "fmdp_expire", "fmdp_snapshot", "fmdp_restore", "fmdp_clear", "fmdp_rollout_trace",
            "fmdp_sep_check", "fmdp_sep_check_noalloc", "fmdp_set_profiling", "fmdp_get_stats")
 
@@ -150,6 +164,17 @@ def load(build_if_missing: bool = True):
     L.fmdp_schedule.argtypes = [vp, P(Request), P(Result)]
     L.fmdp_stage_requests.argtypes = [vp, P(Request), c.c_int32]
     L.fmdp_schedule_staged.argtypes = [vp, c.c_int32, P(c.c_int32)]
+    L.fmdp_learned_collect.argtypes = [vp, P(Request), c.c_int32, P(c.c_int32)]
+    L.fmdp_learned_rows.argtypes = [vp, _fp, P(c.c_uint8), c.c_int32, P(c.c_int32)]
+    L.fmdp_learned_clear_rows.argtypes = [vp]
+    L.fmdp_learned_init.argtypes = [vp, c.c_uint64]
+    L.fmdp_learned_set_params.argtypes = [vp, _fp, c.c_int32]
+    L.fmdp_learned_get_params.argtypes = [vp, _fp, c.c_int32]
+    L.fmdp_learned_train.argtypes = [vp, c.c_int32, c.c_int32, c.c_float, c.c_uint64, _fp]
+    L.fmdp_learned_loss_grad.argtypes = [vp, _fp, P(c.c_uint8), c.c_int32, _fp, _fp]
+    L.fmdp_learned_evaluate.argtypes = [vp, P(Request), c.c_int32, c.c_double, P(LearnedReport), P(c.c_int32),
+                                        P(c.c_int32), P(c.c_int32)]
+    L.fmdp_schedule_learned.argtypes = [vp, P(Request), c.c_int32, c.c_double, P(Result), P(LearnedReport)]
     L.fmdp_serve_options_default.argtypes = [P(ServeOptions)]
     L.fmdp_serve_options_default.restype = None
     L.fmdp_serve.argtypes = [vp, P(Request), P(c.c_double), c.c_int32, P(ServeOptions), P(Result), P(c.c_double),
@@ -413,6 +438,74 @@ class Scheduler:
                                        _ptr(lat, ctypes.c_double), ctypes.byref(rep)))
         out = [_result_dict(res[i], xyz[i] if points else None, acts[i] if points else None) for i in range(n)]
         return out, lat, {k: getattr(rep, k) for k, _ in ServeReport._fields_}
+
+    # ---- learned proposal
+    def learned_collect(self, reqs):
+        """FastMDP rollouts of the requests against the table as it stands (nothing admitted);
+        appends their (features, action) rows to the training set. Returns the row count."""
+        n = len(reqs)
+        rq = (Request * n)(*[make_request(reqs[i]) for i in range(n)])
+        rows = ctypes.c_int32()
+        self._check(self._L.fmdp_learned_collect(self._h, rq, n, ctypes.byref(rows)))
+        return rows.value
+
+    def learned_rows(self, max_rows):
+        X = np.zeros((max_rows, 128), dtype=np.float32)
+        y = np.zeros(max_rows, dtype=np.uint8)
+        n = ctypes.c_int32()
+        self._check(self._L.fmdp_learned_rows(self._h, _ptr(X, ctypes.c_float), _ptr(y, ctypes.c_uint8), max_rows,
+                                              ctypes.byref(n)))
+        return X[: n.value], y[: n.value]
+
+    def learned_clear_rows(self):
+        self._check(self._L.fmdp_learned_clear_rows(self._h))
+
+    def learned_init(self, seed=1):
+        self._check(self._L.fmdp_learned_init(self._h, int(seed)))
+
+    def learned_set_params(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        self._check(self._L.fmdp_learned_set_params(self._h, _ptr(p, ctypes.c_float), p.size))
+
+    def learned_get_params(self):
+        p = np.zeros(MLP_PARAMS, dtype=np.float32)
+        self._check(self._L.fmdp_learned_get_params(self._h, _ptr(p, ctypes.c_float), p.size))
+        return p
+
+    def learned_train(self, epochs=4, batch=256, lr=1e-3, seed=1):
+        losses = np.zeros(max(epochs, 1), dtype=np.float32)
+        self._check(self._L.fmdp_learned_train(self._h, int(epochs), int(batch), float(lr), int(seed),
+                                               _ptr(losses, ctypes.c_float)))
+        return losses[:epochs]
+
+    def learned_loss_grad(self, X, y):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        y = np.ascontiguousarray(y, dtype=np.uint8)
+        loss = np.zeros(1, dtype=np.float32)
+        g = np.zeros(MLP_PARAMS, dtype=np.float32)
+        self._check(self._L.fmdp_learned_loss_grad(self._h, _ptr(X, ctypes.c_float), _ptr(y, ctypes.c_uint8),
+                                                   X.shape[0], _ptr(loss, ctypes.c_float), _ptr(g, ctypes.c_float)))
+        return float(loss[0]), g
+
+    def learned_evaluate(self, reqs, slack=0.05):
+        n = len(reqs)
+        rq = (Request * n)(*[make_request(reqs[i]) for i in range(n)])
+        rep = LearnedReport()
+        acc = np.zeros(max(n, 1), dtype=np.int32)
+        sp = np.zeros(max(n, 1), dtype=np.int32)
+        sf = np.zeros(max(n, 1), dtype=np.int32)
+        self._check(self._L.fmdp_learned_evaluate(self._h, rq, n, float(slack), ctypes.byref(rep),
+                                                  _ptr(acc, ctypes.c_int32), _ptr(sp, ctypes.c_int32),
+                                                  _ptr(sf, ctypes.c_int32)))
+        return {k: getattr(rep, k) for k, _ in LearnedReport._fields_}, acc[:n], sp[:n], sf[:n]
+
+    def schedule_learned(self, reqs, slack=0.05, points=True):
+        """FCFS where each request takes its accepted proposal, else its FastMDP plan."""
+        n = len(reqs)
+        rep = LearnedReport()
+        out = self._many(lambda h, rq, nn, res: self._L.fmdp_schedule_learned(h, rq, nn, float(slack), res,
+                                                                              ctypes.byref(rep)), reqs, points)
+        return out, {k: getattr(rep, k) for k, _ in LearnedReport._fields_}
 
     def stage(self, reqs):
         n = len(reqs)

@@ -105,3 +105,23 @@ def test_features_are_invariant_to_rotating_the_scene():
     f1 = L.features(s, np.cos(h), np.sin(h), 30.0, goal, BOX, p1, p2)
     f2 = L.features(rot(s), np.cos(h + a), np.sin(h + a), 30.0, rot(goal), BOX, rot(p1), rot(p2))
     np.testing.assert_allclose(f1, f2, atol=1e-9)
+
+
+def test_rounding_mode_reduces_to_the_exact_gradient_and_stays_close():
+    rng = np.random.default_rng(6)
+    dims = (16, 32, 32, 10)
+    p = _rand_params(dims, rng, scale=0.3)
+    X = rng.normal(size=(40, 16))
+    # labels from a teacher network: a gradient with signal, not just cancelling noise
+    teacher = _rand_params(dims, rng, scale=0.3)
+    y = np.argmax(L.mlp_forward(teacher, X, dims)[0], axis=1)
+    l0, g0 = L.loss_and_grad(p, X, y, dims)
+    l1, g1 = L.loss_and_grad(p, X, y, dims, round_fn=lambda v: v)
+    assert l0 == l1 and np.array_equal(g0, g1)
+    l2, g2 = L.loss_and_grad(p, X, y, dims, round_fn=L.bf16)
+    assert abs(l2 - l0) < 1e-2 * l0
+    assert np.linalg.norm(g2 - g0) < 2e-2 * np.linalg.norm(g0)
+    # bf16: 8 significant bits, ties to even
+    v = np.array([1.0, 1.0 + 2 ** -8, 1.0 + 3 * 2 ** -8, 1.0 + 2 ** -7, -3.14159])
+    np.testing.assert_array_equal(L.bf16(v)[:4], [1.0, 1.0, 1.0 + 2 ** -6, 1.0 + 2 ** -7])
+    assert abs(L.bf16(v)[4] + 3.140625) < 1e-12
