@@ -165,6 +165,41 @@ def workload_config(sc, n_req, mode="batched"):
             "parallelism": "replicas"}
 
 
+def learned_mode(S, s, sc, stream, barrier, max_over_ranks, world, train_requests):
+    """The learned proposal on a workload: trained on FastMDP rollouts of other requests
+    against the known plans, then evaluated (acceptance, cost gap against FastMDP) and
+    timed as learned FCFS (accepted proposal, else FastMDP) over the workload's requests."""
+    import numpy as np
+
+    s.restore()
+    t0 = time.perf_counter()
+    rows = s.learned_collect(train_requests(np.random.default_rng(2020)))
+    s.learned_init(7)
+    losses = s.learned_train(epochs=12, batch=512, lr=2e-3, seed=8)
+    train_s = time.perf_counter() - t0
+    s.learned_clear_rows()
+    s.restore()
+    rep, acc, sp, sf = s.learned_evaluate(sc.requests)
+    s.restore()
+    s.schedule_learned(sc.requests, points=False)  # warm-up
+    s.restore()
+    ms, (res, lrep) = timed(stream, lambda: s.schedule_learned(sc.requests, points=False), 1, barrier)
+    ms = max_over_ranks(ms)
+    s.restore()
+    n = len(sc.requests)
+    return {"known_plans": len(sc.plans), "value": world * n / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+            "requests": n, "accepted": int(lrep["accepted"]), "acceptance_rate": lrep["accepted"] / max(n, 1),
+            "admitted": sum(r["verdict"] == 0 for r in res),
+            "evaluate": {"accepted": rep["accepted"], "proposals_reaching_goal": rep["proposals_captured"],
+                         "fastmdp_reaching_goal": rep["fastmdp_captured"], "mean_cost_gap": rep["mean_gap"],
+                         "max_cost_gap": rep["max_gap"], "proposal_rollout_ms": rep["proposal_ms"],
+                         "fastmdp_rollout_ms": rep["fastmdp_ms"],
+                         "proposal_steps": rep["proposal_steps"], "fastmdp_steps": rep["fastmdp_steps"]},
+            "training": {"rows": rows, "epochs": 12, "final_loss": float(losses[-1]), "seconds": train_s,
+                         "requests": "400 (3k) / 256 (20k) other seeded requests, FastMDP rollouts"},
+            "judge": "reaches the goal, no conflict or terrain, steps <= 1.05 x fewest possible (gap <= 5 %)"}
+
+
 def timed(stream, fn, k, barrier):
     import torch
 
@@ -295,6 +330,10 @@ def main():
                                      "unit": UNIT, "ms_per_step": mseq,
                                      "mode": "one request at a time, each rollout one cluster launch"}
         modes["batched"] = {"known_plans": len(sc.plans), "value": value, "unit": UNIT}
+        modes["learned"] = learned_mode(S, s, sc, stream, barrier, max_over_ranks, world,
+                                        lambda rng: S.make_requests(rng, sc.box, 400, hm=sc.heightmap,
+                                                                    zspan=(60.0, 500.0), tlo=0, thi=1800,
+                                                                    horizon=1800, id0=10 ** 6))
         sc3 = S.c3_batched(n_requests=512)
         s3 = Scheduler.from_scenario(sc3)
         s3.set_stream(stream.cuda_stream)
@@ -310,6 +349,11 @@ def main():
         m3, adm3 = timed(stream, step3, 2, barrier)
         st3 = s3.stats()
         m3 = max_over_ranks(m3)
+        modes["learned_20k"] = learned_mode(S, s3, sc3, stream, barrier, max_over_ranks, world,
+                                            lambda rng: S.make_requests(rng, sc3.box, 256, hm=sc3.heightmap,
+                                                                        zspan=(60.0, 500.0), tlo=0, thi=1800,
+                                                                        horizon_range=(60, 1800), reach_frac=0.8,
+                                                                        id0=10 ** 6))
         modes["batched_20k"] = {"known_plans": len(sc3.plans), "value": world * 512 * 2 / (m3 / 1e3),
                                 "unit": UNIT, "ms_per_step": m3 / 2, "requests_per_step": 512,
                                 "batch": 256, "admitted_per_step": adm3,

@@ -827,7 +827,8 @@ void enqueue_wave(fmdp_ctx* c, const Geometry& g, int n_clusters, BatchBuffers& 
         pa.acts = c->p_acts.p;
         pa.out = c->p_rout.p;
         pa.err = c->err;
-        LAUNCH(c, launch_policy(pa, std::min(c->n_sm, (n_cap + kPolicyRows - 1) / kPolicyRows), s));
+        pa.rows = policy_rows_for(n_cap, c->n_sm);
+        LAUNCH(c, launch_policy(pa, std::min(c->n_sm, (n_cap + pa.rows - 1) / pa.rows), s));
         SepRowsArgs sp{};
         sp.m = c->model;
         sp.tab = tv;
@@ -1513,8 +1514,9 @@ void learned_evaluate(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, double s
     pa.acts = c->p_acts.p;
     pa.out = c->p_rout.p;
     pa.err = c->err;
+    pa.rows = policy_rows_for(n, c->n_sm);
     CK(cudaEventRecord(e[0], c->stream));
-    LAUNCH(c, launch_policy(pa, std::min(c->n_sm, (n + kPolicyRows - 1) / kPolicyRows), c->stream));
+    LAUNCH(c, launch_policy(pa, std::min(c->n_sm, (n + pa.rows - 1) / pa.rows), c->stream));
     CK(cudaEventRecord(e[1], c->stream));
     // their separation checks and the judge (decisions only), in chunks of the row kernel's size
     LAUNCH(c, launch_sep_reset(c->p_sep.p, n, c->stream));

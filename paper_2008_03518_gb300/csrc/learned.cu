@@ -388,6 +388,8 @@ __global__ void __launch_bounds__(kPolicyThreads, 1) policy_kernel(const __grid_
     const int g = lane >> 2, t = lane & 3;
     const Model& m = a.m;
     const int A = m.A;
+    const int G = a.rows;    // rows carried by this CTA (a multiple of 16, at most kPolicyRows)
+    const int MT = G >> 4;   // 16-row tiles
     const float inv_dt = (float)(1.0 / m.dt);
     if (tid < 24) unit15(tid, cks[2 * tid], cks[2 * tid + 1]);
     if (tid < kPolicyRows) rows[tid].req = -1;
@@ -421,7 +423,7 @@ __global__ void __launch_bounds__(kPolicyThreads, 1) policy_kernel(const __grid_
     if (tid == 0) issue_chunk(0);
     for (;;) {
         // ---- refill empty rows from the work queue (one thread per row)
-        if (tid < kPolicyRows && rows[tid].req < 0 && misc[1]) {
+        if (tid < G && rows[tid].req < 0 && misc[1]) {
             const int w = atomicAdd(a.queue, 1);
             if (w < (a.n_dev ? *a.n_dev : a.n_items)) {
                 const int r = a.idx ? a.idx[w] : w;
@@ -461,7 +463,7 @@ __global__ void __launch_bounds__(kPolicyThreads, 1) policy_kernel(const __grid_
         }
         __syncthreads();
         int any = 0;
-        for (int i = lane; i < kPolicyRows; i += 32) any |= rows[i].req >= 0;
+        for (int i = lane; i < G; i += 32) any |= rows[i].req >= 0;
         any = __any_sync(kFull, any);
         const int more = misc[1];
         __syncthreads();
@@ -469,7 +471,7 @@ __global__ void __launch_bounds__(kPolicyThreads, 1) policy_kernel(const __grid_
         if (!any) continue;
         if (failed) break;
         // ---- features of every active row (one warp per row) into act[0]
-        for (int rr = warp; rr < kPolicyRows; rr += NWp) {
+        for (int rr = warp; rr < G; rr += NWp) {
             __nv_bfloat16* xr = act + (size_t)rr * kActPad;
             const PolicyRow R = rows[rr];
             if (R.req < 0) {
@@ -516,6 +518,7 @@ __global__ void __launch_bounds__(kPolicyThreads, 1) policy_kernel(const __grid_
                             uint32_t af[4][4], bf[4][2];
 #pragma unroll
                             for (int mt = 0; mt < 4; ++mt) {
+                                if (mt >= MT) break;
                                 const __nv_bfloat16* r0 = xin + (size_t)(mt * 16 + g) * kActPad + kc * kChunkK + kk;
                                 af[mt][0] = ld32(r0 + 2 * t);
                                 af[mt][1] = ld32(r0 + 8 * kActPad + 2 * t);
@@ -531,9 +534,10 @@ __global__ void __launch_bounds__(kPolicyThreads, 1) policy_kernel(const __grid_
 #pragma unroll
                             for (int mt = 0; mt < 4; ++mt)
 #pragma unroll
-                                for (int nt = 0; nt < 4; ++nt) mma_bf16(acc[mt][nt], af[mt], bf[nt]);
+                                for (int nt = 0; nt < 4; ++nt)
+                                    if (mt < MT) mma_bf16(acc[mt][nt], af[mt], bf[nt]);
                         }
-                    } else if (warp < 4) {
+                    } else if (warp < MT) {
                         // last layer: warp takes rows [16 warp, 16 warp + 16), all 32 columns
 #pragma unroll
                         for (int kk = 0; kk < kChunkK; kk += 16) {
@@ -566,11 +570,12 @@ __global__ void __launch_bounds__(kPolicyThreads, 1) policy_kernel(const __grid_
                     for (int nt = 0; nt < 4; ++nt)
 #pragma unroll
                         for (int q = 0; q < 4; ++q) {
+                            if (mt >= MT) continue;
                             const int r = mt * 16 + g + (q >= 2 ? 8 : 0);
                             const int col = warp * 32 + nt * 8 + 2 * t + (q & 1);
                             xout[(size_t)r * kActPad + col] = __float2bfloat16_rn(fmaxf(acc[mt][nt][q] + bias[col], 0.f));
                         }
-            } else if (warp < 4) {
+            } else if (warp < MT) {
 #pragma unroll
                 for (int nt = 0; nt < 4; ++nt)
 #pragma unroll
@@ -584,7 +589,7 @@ __global__ void __launch_bounds__(kPolicyThreads, 1) policy_kernel(const __grid_
         }
         if (failed) break;
         // ---- argmax over the actions that keep the successor inside the box (one warp per row)
-        for (int rr = warp; rr < kPolicyRows; rr += NWp) {
+        for (int rr = warp; rr < G; rr += NWp) {
             const PolicyRow R = rows[rr];
             if (R.req < 0) continue;
             float v = -INFINITY;
@@ -608,7 +613,7 @@ __global__ void __launch_bounds__(kPolicyThreads, 1) policy_kernel(const __grid_
         }
         __syncthreads();
         // ---- exact FP64 advance of the chosen action (FastMDP's successor rule, Alg. 1)
-        if (tid < kPolicyRows && rows[tid].req >= 0) {
+        if (tid < G && rows[tid].req >= 0) {
             PolicyRow& R = rows[tid];
             const fmdp_request q = a.reqs[R.req];
             const int ch = choice[tid];

@@ -215,7 +215,14 @@ struct PolicyArgs {
     uint8_t* acts;            // [n][cap]
     RolloutOut* out;          // [n]
     int32_t* err;
+    int32_t rows;             // requests per CTA: 16, 32 or 64
 };
+// rows per CTA for n work items on n_sm multiprocessors: the largest of 16, 32, 64 that
+// still gives every multiprocessor a CTA, else 16
+inline int policy_rows_for(int n, int n_sm) {
+    for (int g : {64, 32}) if ((n + g - 1) / g >= n_sm) return g;
+    return 16;
+}
 size_t policy_smem_bytes();
 cudaError_t prepare_policy_kernel();
 cudaError_t launch_policy(const PolicyArgs& a, int n_ctas, cudaStream_t s);
