@@ -227,6 +227,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-modes", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="arrival window per serving rate")
+    ap.add_argument("--modes", default="sequential,learned,batched20k,learned20k,serving",
+                    help="comma-separated extra modes to run")
     ap.add_argument("--time-scale", type=float, default=60.0, help="simulated seconds per wall second (serving)")
     ap.add_argument("--mode", default="batched", choices=["batched", "sequential"],
                     help="path timed for value: speculative batches (default) or one request at a time")
@@ -321,19 +323,24 @@ def main():
 
     # ---- other modes of the metric: plain sequential FCFS, and 20k known plans batched
     modes = None
-    if not args.no_modes:
+    want = set(args.modes.split(",")) if not args.no_modes else set()
+    if want:
         modes = {}
+    if "sequential" in want:
         step(False)
         mseq, _ = timed(stream, lambda: step(False), 1, barrier)
         mseq = max_over_ranks(mseq)
         modes["plain_sequential"] = {"known_plans": len(sc.plans), "value": world * n_req / (mseq / 1e3),
                                      "unit": UNIT, "ms_per_step": mseq,
                                      "mode": "one request at a time, each rollout one cluster launch"}
+    if want:
         modes["batched"] = {"known_plans": len(sc.plans), "value": value, "unit": UNIT}
+    if "learned" in want:
         modes["learned"] = learned_mode(S, s, sc, stream, barrier, max_over_ranks, world,
                                         lambda rng: S.make_requests(rng, sc.box, 400, hm=sc.heightmap,
                                                                     zspan=(60.0, 500.0), tlo=0, thi=1800,
                                                                     horizon=1800, id0=10 ** 6))
+    if "batched20k" in want or "learned20k" in want:
         sc3 = S.c3_batched(n_requests=512)
         s3 = Scheduler.from_scenario(sc3)
         s3.set_stream(stream.cuda_stream)
@@ -349,11 +356,12 @@ def main():
         m3, adm3 = timed(stream, step3, 2, barrier)
         st3 = s3.stats()
         m3 = max_over_ranks(m3)
-        modes["learned_20k"] = learned_mode(S, s3, sc3, stream, barrier, max_over_ranks, world,
-                                            lambda rng: S.make_requests(rng, sc3.box, 256, hm=sc3.heightmap,
-                                                                        zspan=(60.0, 500.0), tlo=0, thi=1800,
-                                                                        horizon_range=(60, 1800), reach_frac=0.8,
-                                                                        id0=10 ** 6))
+        if "learned20k" in want:
+            modes["learned_20k"] = learned_mode(S, s3, sc3, stream, barrier, max_over_ranks, world,
+                                                lambda rng: S.make_requests(rng, sc3.box, 256, hm=sc3.heightmap,
+                                                                            zspan=(60.0, 500.0), tlo=0, thi=1800,
+                                                                            horizon_range=(60, 1800),
+                                                                            reach_frac=0.8, id0=10 ** 6))
         modes["batched_20k"] = {"known_plans": len(sc3.plans), "value": world * 512 * 2 / (m3 / 1e3),
                                 "unit": UNIT, "ms_per_step": m3 / 2, "requests_per_step": 512,
                                 "batch": 256, "admitted_per_step": adm3,
@@ -361,6 +369,7 @@ def main():
                                 "replans_per_step": st3["batch_replans"] / 2, "workload": sc3.name}
         s3.close()
 
+    if "serving" in want:
         # serving: Poisson arrivals against a sliding-window table (60 km, 40k known plans,
         # room for 100k), continuous batching; each result equals one-at-a-time FCFS
         sc4 = S.c4_serving()

@@ -327,11 +327,15 @@ constexpr int kActPad = kHid + 8;  // bf16 per activation row (bank-conflict-fre
 struct PolicyRow {
     double s[3];
     double c0, s0, step, cap2;
+    double gx, gy, gz;          // the request's goal, kept so a step reads no request
+    int64_t t1;                 // time step of the next sample
+    float speed;
+    int32_t horizon;
     int32_t req, k, h, status;  // req < 0: empty
 };
 
 struct PolicyLayout {
-    size_t act, wbuf, logits, feat, skey, rows, cks, choice, bars, misc, total;
+    size_t act, wbuf, logits, feat, skey, rows, cks, bias, climb, dh, choice, bars, misc, total;
 };
 __host__ __device__ inline PolicyLayout policy_layout() {
     PolicyLayout L;
@@ -341,7 +345,7 @@ __host__ __device__ inline PolicyLayout policy_layout() {
     o += (size_t)2 * kPolicyRows * kActPad * sizeof(__nv_bfloat16);
     al(128);
     L.wbuf = o;
-    o += (size_t)2 * kHid * kChunkPad * sizeof(__nv_bfloat16);
+    o += (size_t)kWBufs * kHid * kChunkPad * sizeof(__nv_bfloat16);
     al(16);
     L.logits = o;
     o += (size_t)kPolicyRows * kOutPad * sizeof(float);
@@ -356,11 +360,18 @@ __host__ __device__ inline PolicyLayout policy_layout() {
     al(16);
     L.cks = o;  // cos, sin of 15 degree steps (FP64)
     o += 48 * sizeof(double);
+    L.climb = o;  // climb x dt per action (FP64)
+    o += kMaxActions * sizeof(double);
+    L.bias = o;  // every layer's bias (fp32), in parameter order
+    o += (size_t)((kLayers - 1) * kHid + kOutPad) * sizeof(float);
+    L.dh = o;
+    o += kMaxActions * sizeof(int);
+    al(16);
     L.choice = o;
     o += kPolicyRows * sizeof(int);
     al(16);
     L.bars = o;
-    o += 2 * sizeof(uint64_t);
+    o += kWBufs * sizeof(uint64_t);
     L.misc = o;
     o += 16;
     L.total = (o + 127) & ~size_t(127);
@@ -384,6 +395,9 @@ __global__ void __launch_bounds__(kPolicyThreads, 1) policy_kernel(const __grid_
     int* choice = reinterpret_cast<int*>(psm + L.choice);
     uint64_t* bars = reinterpret_cast<uint64_t*>(psm + L.bars);
     int* misc = reinterpret_cast<int*>(psm + L.misc);
+    double* climb_dt = reinterpret_cast<double*>(psm + L.climb);
+    float* bias_s = reinterpret_cast<float*>(psm + L.bias);
+    int* dh_s = reinterpret_cast<int*>(psm + L.dh);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, NWp = kPolicyThreads / 32;
     const int g = lane >> 2, t = lane & 3;
     const Model& m = a.m;
@@ -393,14 +407,21 @@ __global__ void __launch_bounds__(kPolicyThreads, 1) policy_kernel(const __grid_
     const float inv_dt = (float)(1.0 / m.dt);
     if (tid < 24) unit15(tid, cks[2 * tid], cks[2 * tid + 1]);
     if (tid < kPolicyRows) rows[tid].req = -1;
+    if (tid < kMaxActions) {
+        climb_dt[tid] = tid < A ? __dmul_rn(m.climb[tid], m.dt) : 0.0;
+        dh_s[tid] = tid < A ? m.dh[tid] : 0;
+    }
+    for (int l = 0, o = 0; l < kLayers; o += layer_out(l), ++l)
+        for (int j = tid; j < layer_out(l); j += kPolicyThreads) bias_s[o + j] = a.params[param_offset_b(l) + j];
     if (tid == 0) {
-        bar_init(&bars[0]);
-        bar_init(&bars[1]);
-        misc[0] = 0;  // items left to pull: 1 while the queue may hold work
-        misc[1] = 1;
+        for (int b = 0; b < kWBufs; ++b) bar_init(&bars[b]);
+        misc[0] = 0;
+        misc[1] = 1;  // 1 while the queue may hold work
     }
     __syncthreads();
-    uint32_t uses[2] = {0u, 0u};
+    // weight chunks are numbered across steps (cg); chunk cg uses buffer cg % kWBufs and is
+    // that buffer's (cg / kWBufs)-th fill
+    long long cg = 0;
     // the weight stream of one step: chunk c of layer l_of(c)
     constexpr int kChunks = kFeat / kChunkK + (kLayers - 1) * (kHid / kChunkK);
     auto chunk_layer = [&](int c, int& l, int& kc) {
@@ -411,16 +432,18 @@ __global__ void __launch_bounds__(kPolicyThreads, 1) policy_kernel(const __grid_
             ++l;
         }
     };
-    auto issue_chunk = [&](int c) {  // thread 0
+    auto issue_chunk = [&](long long q) {  // thread 0: global chunk q
         int l, kc;
-        chunk_layer(c, l, kc);
+        chunk_layer((int)(q % kChunks), l, kc);
+        const int b = (int)(q % kWBufs);
         const uint32_t bytes = (uint32_t)(wp_chunk_elems(l) * sizeof(__nv_bfloat16));
-        bar_expect(&bars[c & 1], bytes);
-        bulk_load(wbuf + (size_t)(c & 1) * kHid * kChunkPad, a.Wp + wp_layer_offset(l) + (size_t)kc * wp_chunk_elems(l),
-                  bytes, &bars[c & 1]);
+        bar_expect(&bars[b], bytes);
+        bulk_load(wbuf + (size_t)b * kHid * kChunkPad, a.Wp + wp_layer_offset(l) + (size_t)kc * wp_chunk_elems(l),
+                  bytes, &bars[b]);
     };
     bool failed = false;
-    if (tid == 0) issue_chunk(0);
+    if (tid == 0)
+        for (int q = 0; q < kWBufs - 1; ++q) issue_chunk(q);
     for (;;) {
         // ---- refill empty rows from the work queue (one thread per row)
         if (tid < G && rows[tid].req < 0 && misc[1]) {
@@ -441,6 +464,12 @@ __global__ void __launch_bounds__(kPolicyThreads, 1) policy_kernel(const __grid_
                 R.s0 = Lh > 0.0 ? __ddiv_rn(dy, Lh) : 0.0;
                 R.step = __dmul_rn(q.speed_mps, m.dt);
                 R.cap2 = __dmul_rn(R.step, R.step);
+                R.gx = q.gx;
+                R.gy = q.gy;
+                R.gz = q.gz;
+                R.t1 = q.depart_step + 1;
+                R.speed = (float)q.speed_mps;
+                R.horizon = q.horizon;
                 float* tr = a.traj + (size_t)r * a.cap * 3;
                 tr[0] = (float)q.ox;
                 tr[1] = (float)q.oy;
@@ -478,18 +507,15 @@ __global__ void __launch_bounds__(kPolicyThreads, 1) policy_kernel(const __grid_
                 for (int i = lane; i < kFeat; i += 32) xr[i] = __float2bfloat16_rn(0.f);
                 continue;
             }
-            const fmdp_request q = a.reqs[R.req];
             float hc, hs;
             heading_cs((float)R.c0, (float)R.s0, R.h, hc, hs);
-            warp_features(m, a.iv, a.tab, q.depart_step + R.k + 1, (float)R.s[0], (float)R.s[1], (float)R.s[2], hc, hs,
-                          (float)q.speed_mps, (float)q.gx, (float)q.gy, (float)q.gz, inv_dt, feat + warp * kFeat,
-                          skey + warp * kSectors);
+            warp_features(m, a.iv, a.tab, R.t1 + R.k, (float)R.s[0], (float)R.s[1], (float)R.s[2], hc, hs, R.speed,
+                          (float)R.gx, (float)R.gy, (float)R.gz, inv_dt, feat + warp * kFeat, skey + warp * kSectors);
             for (int i = lane; i < kFeat; i += 32) xr[i] = __float2bfloat16_rn(feat[warp * kFeat + i]);
             __syncwarp();
         }
         __syncthreads();
         // ---- the MLP: layer by layer, weights streamed chunk by chunk
-        int c = 0;
         for (int l = 0; l < kLayers && !failed; ++l) {
             const __nv_bfloat16* xin = act + (size_t)(l & 1) * kPolicyRows * kActPad;
             __nv_bfloat16* xout = act + (size_t)((l + 1) & 1) * kPolicyRows * kActPad;
@@ -502,14 +528,15 @@ __global__ void __launch_bounds__(kPolicyThreads, 1) policy_kernel(const __grid_
 #pragma unroll
                     for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
             const int nk = layer_in(l) / kChunkK;
-            for (int kc = 0; kc < nk; ++kc, ++c) {
-                if (!bar_wait(&bars[c & 1], uses[c & 1] & 1u)) {
+            for (int kc = 0; kc < nk; ++kc, ++cg) {
+                const int buf = (int)(cg % kWBufs);
+                if (!bar_wait(&bars[buf], (uint32_t)((cg / kWBufs) & 1))) {
                     failed = true;
                     if (tid == 0) atomicExch(a.err, FMDP_ERR_TIMEOUT);
                 }
-                ++uses[c & 1];
-                if (tid == 0 && !failed) issue_chunk((c + 1) % kChunks);  // next chunk (wraps to the next step)
-                const __nv_bfloat16* wb = wbuf + (size_t)(c & 1) * kHid * kChunkPad;
+                // the buffer of chunk cg - 1 is free (all threads passed its end barrier)
+                if (tid == 0 && !failed) issue_chunk(cg + kWBufs - 1);
+                const __nv_bfloat16* wb = wbuf + (size_t)buf * kHid * kChunkPad;
                 if (!failed) {
                     if (!last) {
                         // warp: columns [32 warp, 32 warp + 32), all rows
@@ -562,7 +589,7 @@ __global__ void __launch_bounds__(kPolicyThreads, 1) policy_kernel(const __grid_
                 failed = __syncthreads_or(failed ? 1 : 0) != 0;
             }
             // epilogue: bias (+ ReLU) into the next activation buffer, or the logits
-            const float* bias = a.params + param_offset_b(l);
+            const float* bias = bias_s + l * kHid;
             if (!last) {
 #pragma unroll
                 for (int mt = 0; mt < 4; ++mt)
@@ -594,13 +621,13 @@ __global__ void __launch_bounds__(kPolicyThreads, 1) policy_kernel(const __grid_
             if (R.req < 0) continue;
             float v = -INFINITY;
             if (lane < A) {
-                int hn = R.h + m.dh[lane];
+                int hn = R.h + dh_s[lane];
                 hn += hn < 0 ? 24 : 0;
                 hn -= hn >= 24 ? 24 : 0;
                 const float C = (float)R.c0 * (float)cks[2 * hn] - (float)R.s0 * (float)cks[2 * hn + 1];
                 const float S = (float)R.s0 * (float)cks[2 * hn] + (float)R.c0 * (float)cks[2 * hn + 1];
                 const float x = (float)R.s[0] + (float)R.step * C, y = (float)R.s[1] + (float)R.step * S;
-                const float z = (float)R.s[2] + (float)(m.climb[lane] * m.dt);
+                const float z = (float)R.s[2] + (float)climb_dt[lane];
                 const float mg = 1.0f;  // metres kept from the box faces
                 const bool inside = x > (float)m.box[0] + mg && x < (float)m.box[3] - mg && y > (float)m.box[1] + mg &&
                                     y < (float)m.box[4] - mg && z > (float)m.box[2] + mg && z < (float)m.box[5] - mg;
@@ -615,21 +642,20 @@ __global__ void __launch_bounds__(kPolicyThreads, 1) policy_kernel(const __grid_
         // ---- exact FP64 advance of the chosen action (FastMDP's successor rule, Alg. 1)
         if (tid < G && rows[tid].req >= 0) {
             PolicyRow& R = rows[tid];
-            const fmdp_request q = a.reqs[R.req];
             const int ch = choice[tid];
             bool done = false;
             if (ch < 0) {
                 R.status = FMDP_REJ_NO_ACTION;
                 done = true;
             } else {
-                int hn = R.h + m.dh[ch];
+                int hn = R.h + dh_s[ch];
                 hn += hn < 0 ? 24 : 0;
                 hn -= hn >= 24 ? 24 : 0;
                 const double C = __dsub_rn(__dmul_rn(R.c0, cks[2 * hn]), __dmul_rn(R.s0, cks[2 * hn + 1]));
                 const double S = __dadd_rn(__dmul_rn(R.s0, cks[2 * hn]), __dmul_rn(R.c0, cks[2 * hn + 1]));
                 R.s[0] = __dadd_rn(R.s[0], __dmul_rn(R.step, C));
                 R.s[1] = __dadd_rn(R.s[1], __dmul_rn(R.step, S));
-                R.s[2] = __dadd_rn(R.s[2], __dmul_rn(m.climb[ch], m.dt));
+                R.s[2] = __dadd_rn(R.s[2], climb_dt[ch]);
                 R.h = hn;
                 a.acts[(size_t)R.req * a.cap + R.k] = (uint8_t)ch;
                 R.k += 1;
@@ -637,11 +663,11 @@ __global__ void __launch_bounds__(kPolicyThreads, 1) policy_kernel(const __grid_
                 tr[0] = (float)R.s[0];
                 tr[1] = (float)R.s[1];
                 tr[2] = (float)R.s[2];
-                const double ex = __dsub_rn(q.gx, R.s[0]), ey = __dsub_rn(q.gy, R.s[1]), ez = __dsub_rn(q.gz, R.s[2]);
+                const double ex = __dsub_rn(R.gx, R.s[0]), ey = __dsub_rn(R.gy, R.s[1]), ez = __dsub_rn(R.gz, R.s[2]);
                 if (__dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez)) <= R.cap2) {
                     R.status = kStatusCaptured;
                     done = true;
-                } else if (R.k >= q.horizon) {
+                } else if (R.k >= R.horizon) {
                     R.status = FMDP_REJ_HORIZON;
                     done = true;
                 }
@@ -658,17 +684,12 @@ __global__ void __launch_bounds__(kPolicyThreads, 1) policy_kernel(const __grid_
         }
         __syncthreads();
     }
-    // the chunk issued for a next step that never came: wait for it before leaving
+    // the chunks issued for a next step that never came: wait for them before leaving
     __syncthreads();
     if (tid == 0) {
-        int c_next = 0;
-        // uses[] counts completed waits per buffer; the one outstanding copy is for the chunk
-        // after the last consumed one
-        const uint32_t total = uses[0] + uses[1];
-        c_next = (int)(total % kChunks);
-        if (!failed) bar_wait(&bars[c_next & 1], uses[c_next & 1] & 1u);
-        bar_inval(&bars[0]);
-        bar_inval(&bars[1]);
+        if (!failed)
+            for (long long q = cg; q < cg + kWBufs - 1; ++q) bar_wait(&bars[q % kWBufs], (uint32_t)((q / kWBufs) & 1));
+        for (int b = 0; b < kWBufs; ++b) bar_inval(&bars[b]);
     }
 }
 

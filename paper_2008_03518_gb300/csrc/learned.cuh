@@ -55,7 +55,6 @@ __device__ inline void warp_features(const Model& m, const IndexView& iv, const 
                                      float sy, float sz, float hc, float hs, float speed, float gx, float gy, float gz,
                                      float inv_dt, float* out, unsigned long long* skey) {
     const int lane = threadIdx.x & 31;
-    const float nanv = __int_as_float(0x7fc00000);
     for (int i = lane; i < kFeat; i += 32) out[i] = 0.f;
     if (lane < kSectors) skey[lane] = ~0ull;
     if (lane == 0) {
@@ -86,45 +85,49 @@ __device__ inline void warp_features(const Model& m, const IndexView& iv, const 
     const int cx0 = cell_of(sx - kRF, iv.x0, iv.ncx), cx1 = cell_of(sx + kRF, iv.x0, iv.ncx);
     const int cy0 = cell_of(sy - kRF, iv.y0, iv.ncy), cy1 = cell_of(sy + kRF, iv.y0, iv.ncy);
     const float R2 = kRF * kRF;
-    // visits every item of the query: the cell rows' ranges, then the extra list
-    auto visit = [&](auto&& fn) {
-        for (int cy = cy0; cy <= cy1 + 1; ++cy) {
-            int b, e;
-            if (cy <= cy1) {
-                b = cs_row[cy * iv.ncx + cx0];
-                e = cs_row[cy * iv.ncx + cx1 + 1];
-            } else {
-                b = cs_row[iv.ncell];
-                e = b + iv.nextra[row];
-            }
-            for (int i = b + lane; i < e; i += 32) fn(it[2 * (size_t)i], it[2 * (size_t)i + 1]);
-        }
-    };
+    const unsigned full = 0xffffffffu;
     auto sector_of = [&](float rf, float rl, float rz) {
         const float az = atan2f(rl, rf);  // [-pi, pi]
         int k = (int)floorf((az + 3.14159265358979f) * (10.f / 6.28318530717959f));
         k = min(max(k, 0), 9);
         return k + (rz >= 0.f ? 10 : 0);
     };
-    visit([&](float4 P1, float4 P2) {
+    // The query's ranges: its cell rows (cells cx0..cx1 of a row are contiguous), then the
+    // extra list. They are taken 16 at a time; lanes 2q and 2q + 1 load range q's bounds
+    // together, and the lanes then share out the group's items as one flat list.
+    const int nrows = cy1 - cy0 + 1;
+    auto visit = [&](auto&& fn) {
+        for (int q0 = 0; q0 <= nrows; q0 += 16) {
+            const int q = q0 + (lane >> 1);
+            int v = 0;
+            if (q < nrows) {
+                v = cs_row[(cy0 + q) * iv.ncx + ((lane & 1) ? cx1 + 1 : cx0)];
+            } else if (q == nrows) {
+                v = (lane & 1) ? cs_row[iv.ncell] + iv.nextra[row] : cs_row[iv.ncell];
+            }
+            int beg[16], start[17];
+            start[0] = 0;
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                const int b = __shfl_sync(full, v, 2 * k), e = __shfl_sync(full, v, 2 * k + 1);
+                beg[k] = b;
+                start[k + 1] = start[k] + (q0 + k <= nrows ? max(0, e - b) : 0);
+            }
+            const int total = start[16];
+            for (int j = lane; j < total; j += 32) {
+                // the range holding flat item j: the last k whose start is at or before j
+                int i = beg[0] + j;
+#pragma unroll
+                for (int k = 1; k < 16; ++k)
+                    if (j >= start[k]) i = beg[k] + (j - start[k]);
+                fn(i);
+            }
+        }
+    };
+    // sector feature of the nearest sample P1 (and the same plan's next sample P2)
+    auto emit = [&](float4 P1, float4 P2, float d2, int sec) {
         const float rx = P1.x - sx, ry = P1.y - sy, rz = P1.z - sz;
-        const float d2 = rx * rx + ry * ry + rz * rz;
-        if (!(d2 < R2)) return;
         const float rf = rx * hc + ry * hs, rl = -rx * hs + ry * hc;
-        const unsigned long long key =
-            ((unsigned long long)__float_as_uint(d2) << 32) | sample_hash(P1.x, P1.y, P1.z);
-        atomicMin(&skey[sector_of(rf, rl, rz)], key);
-    });
-    __syncwarp();
-    visit([&](float4 P1, float4 P2) {
-        const float rx = P1.x - sx, ry = P1.y - sy, rz = P1.z - sz;
-        const float d2 = rx * rx + ry * ry + rz * rz;
-        if (!(d2 < R2)) return;
-        const float rf = rx * hc + ry * hs, rl = -rx * hs + ry * hc;
-        const int sec = sector_of(rf, rl, rz);
-        const unsigned long long key =
-            ((unsigned long long)__float_as_uint(d2) << 32) | sample_hash(P1.x, P1.y, P1.z);
-        if (key != skey[sec]) return;
         float vx = 0.f, vy = 0.f, vz = 0.f;
         if (P2.x == P2.x) {
             vx = (P2.x - P1.x) * inv_dt;
@@ -140,8 +143,50 @@ __device__ inline void warp_features(const Model& m, const IndexView& iv, const 
         o[3] = (vf - speed) * (1.f / 50.f) * w;
         o[4] = vl * (1.f / 50.f) * w;
         o[5] = vz * (1.f / 50.f) * w;
+    };
+    // key of sample P1: (squared distance, position hash), all-ones beyond R_F
+    auto key_of = [&](float4 P1, float& d2, int& sec) {
+        const float rx = P1.x - sx, ry = P1.y - sy, rz = P1.z - sz;
+        d2 = rx * rx + ry * ry + rz * rz;
+        if (!(d2 < R2)) return ~0ull;
+        sec = sector_of(rx * hc + ry * hs, -rx * hs + ry * hc, rz);
+        return ((unsigned long long)__float_as_uint(d2) << 32) | sample_hash(P1.x, P1.y, P1.z);
+    };
+    // pass 1: every sector's least key; a lane keeps its first two in-range samples
+    int ci0 = -1, ci1 = -1, cs0 = 0, cs1 = 0;
+    float cd0 = 0.f, cd1 = 0.f;
+    unsigned long long ck0 = 0, ck1 = 0;
+    float4 cp0 = make_float4(0.f, 0.f, 0.f, 0.f), cp1 = cp0;
+    bool over = false;
+    visit([&](int i) {
+        const float4 P1 = it[2 * (size_t)i];
+        float d2;
+        int sec;
+        const unsigned long long key = key_of(P1, d2, sec);
+        if (key == ~0ull) return;
+        atomicMin(&skey[sec], key);
+        if (ci0 < 0) {
+            ci0 = i, cs0 = sec, cd0 = d2, ck0 = key, cp0 = P1;
+        } else if (ci1 < 0) {
+            ci1 = i, cs1 = sec, cd1 = d2, ck1 = key, cp1 = P1;
+        } else {
+            over = true;
+        }
     });
-    (void)nanv;
+    __syncwarp();
+    // pass 2: the sector winners write their features
+    if (!__any_sync(full, over)) {
+        if (ci0 >= 0 && ck0 == skey[cs0]) emit(cp0, it[2 * (size_t)ci0 + 1], cd0, cs0);
+        if (ci1 >= 0 && ck1 == skey[cs1]) emit(cp1, it[2 * (size_t)ci1 + 1], cd1, cs1);
+    } else {
+        visit([&](int i) {
+            const float4 P1 = it[2 * (size_t)i];
+            float d2;
+            int sec;
+            const unsigned long long key = key_of(P1, d2, sec);
+            if (key != ~0ull && key == skey[sec]) emit(P1, it[2 * (size_t)i + 1], d2, sec);
+        });
+    }
     __syncwarp();
 }
 
@@ -197,7 +242,8 @@ cudaError_t launch_export_weights(const float* p, __nv_bfloat16* Wt, __nv_bfloat
 
 // Policy rollouts: each CTA carries kPolicyRows requests in lock step (one matrix row each)
 // and refills a finished row from the work queue.
-constexpr int kPolicyRows = 64;
+constexpr int kPolicyRows = 32;
+constexpr int kWBufs = 4;       // weight chunk buffers: three chunks stream while one is used
 constexpr int kPolicyThreads = 256;
 struct PolicyArgs {
     Model m;
@@ -215,14 +261,11 @@ struct PolicyArgs {
     uint8_t* acts;            // [n][cap]
     RolloutOut* out;          // [n]
     int32_t* err;
-    int32_t rows;             // requests per CTA: 16, 32 or 64
+    int32_t rows;             // requests per CTA: 16 or 32
 };
-// rows per CTA for n work items on n_sm multiprocessors: the largest of 16, 32, 64 that
-// still gives every multiprocessor a CTA, else 16
-inline int policy_rows_for(int n, int n_sm) {
-    for (int g : {64, 32}) if ((n + g - 1) / g >= n_sm) return g;
-    return 16;
-}
+// rows per CTA for n work items on n_sm multiprocessors: 32 when that still gives every
+// multiprocessor a CTA, else 16
+inline int policy_rows_for(int n, int n_sm) { return (n + 31) / 32 >= n_sm ? 32 : 16; }
 size_t policy_smem_bytes();
 cudaError_t prepare_policy_kernel();
 cudaError_t launch_policy(const PolicyArgs& a, int n_ctas, cudaStream_t s);
