@@ -226,6 +226,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-modes", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="batched mode: skip the launch-shape autotuner")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="arrival window per serving rate")
     ap.add_argument("--modes", default="sequential,learned,batched20k,learned20k,serving",
                     help="comma-separated extra modes to run")
@@ -273,6 +274,10 @@ def main():
     s.snapshot()
     s.stage(sc.requests)
     n_req = len(sc.requests)
+    tune = None
+    if args.mode == "batched" and not args.no_tune:
+        # launch shape of the batched rollout, tuned on the first batch (untimed set-up)
+        tune = s.autotune(sc.requests[:256])
 
     def step(batched=args.mode == "batched"):
         s.restore()
@@ -346,6 +351,7 @@ def main():
         s3.set_stream(stream.cuda_stream)
         s3.snapshot()
         s3.stage(sc3.requests)
+        tune3 = None if args.no_tune else s3.autotune(sc3.requests[:256])
 
         def step3():
             s3.restore()
@@ -366,7 +372,8 @@ def main():
                                 "unit": UNIT, "ms_per_step": m3 / 2, "requests_per_step": 512,
                                 "batch": 256, "admitted_per_step": adm3,
                                 "waves_per_step": st3["batch_waves"] / 2,
-                                "replans_per_step": st3["batch_replans"] / 2, "workload": sc3.name}
+                                "replans_per_step": st3["batch_replans"] / 2, "workload": sc3.name,
+                                "autotune": tune3}
         s3.close()
 
     if "serving" in want:
@@ -422,7 +429,7 @@ def main():
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(sc, n_req, args.mode),
             "admitted_per_step": admitted, "batch": batch_stats, "modes": modes, "e2e": e2e,
             "gpu_launches": gpu_launches, "roofline": roofline, "clocks": clk,
-            "p99_latency_ms_by_rate": p99}
+            "p99_latency_ms_by_rate": p99, "autotune": tune}
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(sc, args.cpu_seconds)
     if rank == 0:

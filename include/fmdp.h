@@ -263,6 +263,51 @@ fmdp_status fmdp_learned_evaluate(fmdp_ctx* ctx, const fmdp_request* reqs, int32
 fmdp_status fmdp_schedule_learned(fmdp_ctx* ctx, const fmdp_request* reqs, int32_t n, double slack,
                                   fmdp_result* res, fmdp_learned_report* report);
 
+/* ---- Autotuner of the batched rollout's launch shape (no counterpart in the paper; the
+ * rollout is Alg. 1 whatever the shape, and results are bit-identical across shapes).
+ *
+ * With the spatial index a speculative wave runs one CTA per request: a control warp, an
+ * evaluator warp, an index producer warp and (threads_per_cta / 32 - 3) scanner warps that
+ * share out the plan samples near the state, index_stage_items of them staged in shared
+ * memory per step. Fewer scanners and less staging let two or more CTAs share a
+ * multiprocessor, which pays when a wave holds more requests than there are
+ * multiprocessors; more scanners shorten each step, which is what a small wave (the
+ * re-plans of a speculative batch) needs. fmdp_autotune times the rollouts of the first W
+ * sample requests (nothing is admitted) under every candidate shape, threads per CTA in
+ * {128, 192, 256, 320, 384} x staged samples in {512, 1024, 1536, 2048}, for W = min(n,
+ * batch size) and its halvings down to 8, and caches the fastest shape under the key
+ * (n_actions, combine, plan-count bucket, wave-size bucket). Each wave of a batched call
+ * (fmdp_schedule_batch, fmdp_serve, fmdp_schedule_learned, staged batches) then launches
+ * with the cached shape of its key, or of the nearest tuned wave-size bucket;
+ * options.threads_per_cta and options.index_stage_items, when set, take precedence. */
+typedef struct {
+    int32_t n_actions, combine;
+    int32_t plans_bucket;        /* bit length of the number of stored plans */
+    int32_t wave_bucket;         /* bit length of the number of rollouts in a wave */
+    int32_t threads_per_cta;     /* the chosen shape */
+    int32_t index_stage_items;
+    double ms;                   /* the sample's rollout time under the chosen shape */
+} fmdp_tune_entry;
+typedef struct {
+    fmdp_tune_entry chosen;      /* the entry of the largest wave (sample requests) */
+    int32_t candidates;          /* (wave size, shape) pairs timed (0 when cached) */
+    int32_t entries;             /* wave-size buckets tuned by this call */
+    int32_t ctas_per_sm;         /* resident rollout CTAs per multiprocessor at the choice */
+    int32_t from_cache;          /* 1: the largest wave's key was cached and nothing was timed */
+    int32_t sample;              /* requests in the largest timed wave */
+    int32_t reserved;
+    double default_ms;           /* the largest wave at 384 threads and 1536 staged samples */
+} fmdp_tune_report;
+/* Requires the spatial index (options.full_scan = 0). sample: host requests, at least one;
+ * the largest timed wave is the first min(n, batch size). force = 1 re-times cached keys. */
+fmdp_status fmdp_autotune(fmdp_ctx* ctx, const fmdp_request* sample, int32_t n, int32_t force,
+                          fmdp_tune_report* report);
+/* Copies up to cap cache entries out (n_out: entries in the cache), or merges n entries in
+ * (a deployment can keep the cache between runs). Entries with shapes outside the candidate
+ * set are rejected with FMDP_ERR_ARG. */
+fmdp_status fmdp_tune_cache_get(fmdp_ctx* ctx, fmdp_tune_entry* out, int32_t cap, int32_t* n_out);
+fmdp_status fmdp_tune_cache_put(fmdp_ctx* ctx, const fmdp_tune_entry* in, int32_t n);
+
 /* Device-resident variant used for kernel-side timing: fmdp_stage_requests copies the
  * requests into library-owned device memory; fmdp_schedule_staged plans them in FCFS
  * order, like fmdp_schedule_many (batched = 0) or fmdp_schedule_batch (batched = 1), but

@@ -13,6 +13,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <array>
 #include <map>
 #include <new>
 #include <set>
@@ -194,8 +195,13 @@ struct fmdp_ctx {
     int32_t ix_ncx = 0, ix_ncy = 0, ix_ncell = 0;
     float ix_x0 = 0.f, ix_y0 = 0.f, ix_inv = 0.f, ix_vmax = 0.f;
     size_t ix_smem = 0;
-    int32_t icap = 1536;
+    int32_t icap_user = 0;  // options.index_stage_items (0: tuned or 1536)
     unsigned long long* items_ctr = nullptr;
+
+    // autotuner: the batched indexed rollout's shape per workload key, and the shape a
+    // tuning run is timing (0: none)
+    std::map<std::array<int32_t, 4>, fmdp_tune_entry> tune;
+    int32_t try_threads = 0, try_icap = 0;
 
     // work buffers
     SeqBuffers seq;     // fmdp_schedule / fmdp_schedule_many
@@ -423,9 +429,16 @@ IndexView index_view(fmdp_ctx* c) {
     return v;
 }
 
-void set_index_args(fmdp_ctx* c, RolloutArgs& ra) {
+// launch shape of a rollout
+struct Geometry {
+    int32_t S_scan, cs, threads, chunk, ring;
+    int32_t icap = 0;  // indexed mode: plan samples staged per step
+    size_t smem;
+};
+
+void set_index_args(fmdp_ctx* c, RolloutArgs& ra, const Geometry& g) {
     ra.indexed = c->index_on ? 1 : 0;
-    ra.icap = c->icap;
+    ra.icap = g.icap;
     ra.iv = index_view(c);
     ra.items_ctr = (c->index_on && c->profiling && !c->capturing) ? c->items_ctr : nullptr;
 }
@@ -464,11 +477,6 @@ void index_append_admitted(fmdp_ctx* c, const float* traj, int32_t cap, const Ro
 
 // ------------------------------------------------------------------ launch geometry
 
-struct Geometry {
-    int32_t S_scan, cs, threads, chunk, ring;
-    size_t smem;
-};
-
 // Partition g.S_scan slots over clusters of cs CTAs: the deepest ring (8, else 4 slices)
 // whose partition fits one CTA's shared memory. False when neither fits.
 bool fit_geometry(fmdp_ctx* c, Geometry& g, int cs) {
@@ -483,15 +491,59 @@ bool fit_geometry(fmdp_ctx* c, Geometry& g, int cs) {
     return false;
 }
 
-// Indexed geometry: one CTA per request staging only the plans near its state.
-Geometry geometry_indexed(fmdp_ctx* c, int32_t S_scan) {
+// autotuner key of the current table and batch size
+int32_t bit_length(int64_t v) {
+    int32_t b = 0;
+    while (v > 0) {
+        ++b;
+        v >>= 1;
+    }
+    return b;
+}
+int32_t batch_size_of(const fmdp_ctx* c) { return c->opt.batch_size > 0 ? c->opt.batch_size : 256; }
+std::array<int32_t, 4> tune_key(const fmdp_ctx* c, int32_t wave) {
+    return {c->A, c->opt.combine, bit_length((int64_t)c->book.plans.size()), bit_length(wave)};
+}
+// the cached shape for a wave of `wave` rollouts: its own bucket, else the nearest tuned one
+const fmdp_tune_entry* tune_lookup(const fmdp_ctx* c, int32_t wave) {
+    const auto k = tune_key(c, wave);
+    const fmdp_tune_entry* best = nullptr;
+    int32_t bd = INT_MAX;
+    for (const auto& kv : c->tune) {
+        if (kv.first[0] != k[0] || kv.first[1] != k[1] || kv.first[2] != k[2]) continue;
+        const int32_t d = std::abs(kv.first[3] - k[3]);
+        if (d < bd) {
+            bd = d;
+            best = &kv.second;
+        }
+    }
+    return best;
+}
+
+// Indexed geometry: one CTA per request staging only the plans near its state. A batched
+// launch of `wave` rollouts takes the autotuner's shape for its key; explicit options take
+// precedence.
+Geometry geometry_indexed(fmdp_ctx* c, int32_t S_scan, int32_t wave = 0) {
     Geometry g;
     g.S_scan = S_scan;
     g.cs = 1;
     g.chunk = 0;
     g.ring = 4;
-    g.threads = c->opt.threads_per_cta > 0 ? c->opt.threads_per_cta : 384;
-    g.smem = rollout_smem_bytes(0, 0, c->icap);
+    g.threads = 384;
+    g.icap = 1536;
+    if (wave > 0) {
+        if (const fmdp_tune_entry* e = tune_lookup(c, wave)) {
+            g.threads = e->threads_per_cta;
+            g.icap = e->index_stage_items;
+        }
+        if (c->try_threads > 0) {
+            g.threads = c->try_threads;
+            g.icap = c->try_icap;
+        }
+    }
+    if (c->opt.threads_per_cta > 0) g.threads = c->opt.threads_per_cta;
+    if (c->icap_user > 0) g.icap = c->icap_user;
+    g.smem = rollout_smem_bytes(0, 0, g.icap);
     require((int)g.smem <= c->max_smem, FMDP_ERR_ARG, "index staging buffers exceed shared memory");
     c->last_cs = 1;
     c->last_threads = g.threads;
@@ -570,7 +622,7 @@ void enqueue_sequence(fmdp_ctx* c, SeqBuffers& B, const fmdp_request* host_reqs,
         ra.acts = B.acts.p + (size_t)i * cap;
         ra.out = B.rout.p + i;
         ra.err = c->err;
-        set_index_args(c, ra);
+        set_index_args(c, ra, g);
         ra.phase = c->phase_timing ? c->phase.p : nullptr;
         {
             KernelTimer t(c, 0);
@@ -743,8 +795,8 @@ int wave_kernels(const fmdp_ctx* c) { return (c->index_on ? 7 : 5) + (c->learned
 
 // Batch geometry: the narrowest cluster whose partition fits one CTA's shared memory, so
 // that as many rollouts as possible run side by side.
-Geometry geometry_batch(fmdp_ctx* c, int32_t S) {
-    if (c->index_on) return geometry_indexed(c, std::min(round_up(std::max(S, 0), 32), c->S_pad));
+Geometry geometry_batch(fmdp_ctx* c, int32_t S, int32_t wave) {
+    if (c->index_on) return geometry_indexed(c, std::min(round_up(std::max(S, 0), 32), c->S_pad), std::max(wave, 1));
     Geometry g;
     g.S_scan = std::min(round_up(std::max(S, 0), 32), c->S_pad);
     int cs = c->opt.cluster_size > 0 ? c->opt.cluster_size : 1;
@@ -883,7 +935,7 @@ void enqueue_wave(fmdp_ctx* c, const Geometry& g, int n_clusters, BatchBuffers& 
         ra.acts = B.acts.p;
         ra.out = B.rout.p;
         ra.err = c->err;
-        set_index_args(c, ra);
+        set_index_args(c, ra, g);
         ra.phase = (timed && c->phase_timing) ? c->phase.p : nullptr;
         ra.queue = B.ctr.p;
         ra.idx = todo;
@@ -992,7 +1044,7 @@ cudaGraphExec_t wave_graph(fmdp_ctx* c, const Geometry& g, int n_clusters, Batch
     cudaGraphDestroy(graph);
     CK(e);
     c->graphs.insert(c->graphs.begin(), WaveGraph{key, exec});
-    while (c->graphs.size() > 4) {
+    while (c->graphs.size() > 8) {
         cudaGraphExecDestroy(c->graphs.back().exec);
         c->graphs.pop_back();
     }
@@ -1043,6 +1095,10 @@ struct Speculator {
     // One wave and its walk: `resolved` receives the requests finalised, in order.
     void wave(std::vector<int32_t>& resolved) {
         const int32_t n_cap = B.n_cap;
+        if (c->index_on) {  // the tuned shape for this wave's size
+            const Geometry gw = geometry_batch(c, c->S_pad, (int32_t)todo.size());
+            if (gw.threads != g.threads || gw.icap != g.icap) set_geometry(gw);
+        }
         upload_lists();
         if (graphs) {
             CK(cudaGraphLaunch(wave_graph(c, g, n_clusters, B), c->stream));
@@ -1211,13 +1267,13 @@ void batch_prepare(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, int32_t n_b
 
 // Geometry of the call: the scanned slot range covers every slot the call may fill (the
 // lowest free slots) or, with the spatial index, the whole table.
-Geometry batch_geometry(fmdp_ctx* c, int32_t n_new) {
-    if (c->index_on) return geometry_batch(c, c->S_pad);
+Geometry batch_geometry(fmdp_ctx* c, int32_t n_new, int32_t wave) {
+    if (c->index_on) return geometry_batch(c, c->S_pad, wave);
     require((size_t)n_new <= c->book.free_slots.size(), FMDP_ERR_FULL, "not enough free plan slots for the batch");
     int32_t bound = c->book.S_hw;
     auto it = c->book.free_slots.begin();
     for (int32_t i = 0; i < n_new; ++i, ++it) bound = std::max(bound, *it + 1);
-    return geometry_batch(c, round_up(bound, 512));
+    return geometry_batch(c, round_up(bound, 512), wave);
 }
 
 void copy_points_back(fmdp_ctx* c, int32_t n, fmdp_result* res) {
@@ -1262,7 +1318,7 @@ int32_t run_batch(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_result*
     std::vector<int32_t> resolved;
     for (int32_t b0 = 0; b0 < n; b0 += bs) {
         const int32_t m = std::min(bs, n - b0);
-        sp.set_geometry(batch_geometry(c, m));
+        sp.set_geometry(batch_geometry(c, m, m));
         for (int32_t i = 0; i < m; ++i) sp.add(b0 + i);
         sp.adm_all.clear();
         try {
@@ -1413,7 +1469,7 @@ void grow_keep(fmdp_ctx* c, DevArray<T>& a, size_t want, size_t keep) {
 // launch; nothing is checked or admitted); trajectories in the batch buffers
 void plan_all_fastmdp(fmdp_ctx* c, int32_t n) {
     BatchBuffers& B = c->bat;
-    const Geometry g = batch_geometry(c, 0);
+    const Geometry g = batch_geometry(c, 0, n);
     const int n_clusters = std::max(1, std::min(n, rollout_max_active_clusters(g.cs, g.threads, g.smem)));
     CK(cudaMemsetAsync(B.ctr.p, 0, sizeof(int32_t), c->stream));
     RolloutArgs ra{};
@@ -1430,9 +1486,111 @@ void plan_all_fastmdp(fmdp_ctx* c, int32_t n) {
     ra.acts = B.acts.p;
     ra.out = B.rout.p;
     ra.err = c->err;
-    set_index_args(c, ra);
+    set_index_args(c, ra, g);
     ra.queue = B.ctr.p;
     LAUNCH(c, launch_rollout(ra, g.threads, g.smem, c->stream, n_clusters));
+}
+
+// ---- autotuner of the batched indexed rollout (results do not depend on the shape)
+
+constexpr int32_t kTuneThreads[] = {128, 192, 256, 320, 384};
+constexpr int32_t kTuneStage[] = {512, 1024, 1536, 2048};
+
+bool tune_shape_ok(int32_t threads, int32_t icap) {
+    bool t = false, i = false;
+    for (int32_t v : kTuneThreads) t |= v == threads;
+    for (int32_t v : kTuneStage) i |= v == icap;
+    return t && i;
+}
+
+// Times the rollouts of the first W sample requests (one wave, nothing admitted) under each
+// candidate shape, for W = min(n, batch size) and its halvings down to 8, and caches the
+// fastest shape of each wave-size bucket. The report describes the largest wave.
+void autotune(fmdp_ctx* c, const fmdp_request* sample, int32_t n, bool force, fmdp_tune_report* rep) {
+    require(c->index_on, FMDP_ERR_ARG, "the autotuner covers the indexed rollout (full_scan must be 0)");
+    require(n >= 1 && sample, FMDP_ERR_ARG, "the autotuner needs at least one sample request");
+    fmdp_tune_report r{};
+    const int32_t m = std::min(n, batch_size_of(c));
+    r.sample = m;
+    const auto key = tune_key(c, m);
+    const auto hit = c->tune.find(key);
+    auto describe = [&](const fmdp_tune_entry& e) {
+        r.chosen = e;
+        c->try_threads = e.threads_per_cta;
+        c->try_icap = e.index_stage_items;
+        const Geometry g = batch_geometry(c, 0, m);
+        c->try_threads = c->try_icap = 0;
+        r.ctas_per_sm = rollout_max_active_clusters(1, g.threads, g.smem) / std::max(1, c->n_sm);
+    };
+    if (hit != c->tune.end() && !force) {
+        describe(hit->second);
+        r.from_cache = 1;
+        r.default_ms = -1.0;
+        if (rep) *rep = r;
+        return;
+    }
+    std::vector<int32_t> sizes;
+    for (int32_t w = m; w >= 1; w /= 2) {
+        sizes.push_back(w);
+        if (w <= 8) break;
+    }
+    batch_prepare(c, sample, m, m, nullptr);
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    try {
+        for (int32_t w : sizes) {
+            double best = 1e300;
+            int32_t bt = 384, bi = 1536;
+            for (int32_t th : kTuneThreads)
+                for (int32_t ic : kTuneStage) {
+                    if (rollout_smem_bytes(0, 0, ic) > (size_t)c->max_smem) continue;
+                    c->try_threads = th;
+                    c->try_icap = ic;
+                    plan_all_fastmdp(c, w);  // warm-up
+                    double t_min = 1e300;
+                    for (int rep_i = 0; rep_i < 2; ++rep_i) {
+                        CK(cudaEventRecord(e0, c->stream));
+                        plan_all_fastmdp(c, w);
+                        CK(cudaEventRecord(e1, c->stream));
+                        CK(cudaEventSynchronize(e1));
+                        float ms = 0.f;
+                        CK(cudaEventElapsedTime(&ms, e0, e1));
+                        t_min = std::min(t_min, (double)ms);
+                    }
+                    require(read_error_word(c) == 0, FMDP_ERR_TIMEOUT,
+                            "a bounded device wait expired during a rollout");
+                    ++r.candidates;
+                    if (w == m && th == 384 && ic == 1536) r.default_ms = t_min;
+                    if (t_min < best) {
+                        best = t_min;
+                        bt = th;
+                        bi = ic;
+                    }
+                }
+            c->try_threads = c->try_icap = 0;
+            const auto k = tune_key(c, w);
+            fmdp_tune_entry en{};
+            en.n_actions = k[0];
+            en.combine = k[1];
+            en.plans_bucket = k[2];
+            en.wave_bucket = k[3];
+            en.threads_per_cta = bt;
+            en.index_stage_items = bi;
+            en.ms = best;
+            c->tune[k] = en;
+            ++r.entries;
+        }
+    } catch (...) {
+        c->try_threads = c->try_icap = 0;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        throw;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    describe(c->tune[key]);
+    if (rep) *rep = r;
 }
 
 void learned_collect(fmdp_ctx* c, const fmdp_request* reqs, int32_t n) {
@@ -1611,7 +1769,7 @@ void run_serve(fmdp_ctx* c, const fmdp_request* reqs, const double* arrival_s, i
     const int64_t sim0 = o.sim_start_set ? o.sim_start_step : c->book.t_base;
     batch_prepare(c, reqs, n, in_flight, nullptr);
     Speculator sp(c, reqs, n);
-    sp.set_geometry(batch_geometry(c, 0));
+    sp.set_geometry(batch_geometry(c, 0, 1));
     // earliest departure among requests i .. n-1 (the clock never expires past it)
     std::vector<int64_t> dep_suffix(n + 1, INT64_MAX);
     for (int32_t i = n - 1; i >= 0; --i) dep_suffix[i] = std::min(dep_suffix[i + 1], reqs[i].depart_step);
@@ -1635,7 +1793,7 @@ void run_serve(fmdp_ctx* c, const fmdp_request* reqs, const double* arrival_s, i
             if (limit >= c->book.t_base + quantum) {
                 expire_to(c, limit, &expired);
                 ++expiries;
-                sp.set_geometry(batch_geometry(c, 0));
+                sp.set_geometry(batch_geometry(c, 0, 1));
             }
             // admission: arrived requests join while the set has room and slots remain for all
             bool blocked = false;
@@ -2022,7 +2180,7 @@ fmdp_status fmdp_create(const fmdp_airspace* air, double gamma, const fmdp_actio
         fill_model(c, wells, acts, a.static_wells);
         c->index_on = o.full_scan == 0;
         if (c->index_on) {
-            c->icap = o.index_stage_items > 0 ? o.index_stage_items : 1536;
+            c->icap_user = o.index_stage_items > 0 ? o.index_stage_items : 0;
             // cells of about 0.6 query radii (a query then spans 3 to 5 cell rows); at most 16384
             const double vmax = o.index_vmax_mps > 0.0 ? o.index_vmax_mps : 50.0;
             const double W = a.x1 - a.x0, H = a.y1 - a.y0;
@@ -2383,6 +2541,42 @@ fmdp_status fmdp_learned_evaluate(fmdp_ctx* c, const fmdp_request* reqs, int32_t
     });
 }
 
+fmdp_status fmdp_autotune(fmdp_ctx* c, const fmdp_request* sample, int32_t n, int32_t force,
+                          fmdp_tune_report* report) {
+    if (!c) return FMDP_ERR_ARG;
+    return guard(c, [&] {
+        require(n >= 1 && sample, FMDP_ERR_ARG, "the autotuner needs at least one sample request");
+        for (int32_t i = 0; i < n; ++i) check_request(c, sample[i]);
+        autotune(c, sample, n, force != 0, report);
+    });
+}
+
+fmdp_status fmdp_tune_cache_get(fmdp_ctx* c, fmdp_tune_entry* out, int32_t cap, int32_t* n_out) {
+    if (!c) return FMDP_ERR_ARG;
+    return guard(c, [&] {
+        require(cap >= 0 && (cap == 0 || out), FMDP_ERR_ARG, "null output");
+        int32_t i = 0;
+        for (const auto& kv : c->tune) {
+            if (i < cap) out[i] = kv.second;
+            ++i;
+        }
+        if (n_out) *n_out = i;
+    });
+}
+
+fmdp_status fmdp_tune_cache_put(fmdp_ctx* c, const fmdp_tune_entry* in, int32_t n) {
+    if (!c) return FMDP_ERR_ARG;
+    return guard(c, [&] {
+        require(n >= 0 && (n == 0 || in), FMDP_ERR_ARG, "null entries");
+        for (int32_t i = 0; i < n; ++i)
+            require(tune_shape_ok(in[i].threads_per_cta, in[i].index_stage_items) &&
+                        rollout_smem_bytes(0, 0, in[i].index_stage_items) <= (size_t)c->max_smem,
+                    FMDP_ERR_ARG, "tune entry outside the candidate shapes");
+        for (int32_t i = 0; i < n; ++i)
+            c->tune[{in[i].n_actions, in[i].combine, in[i].plans_bucket, in[i].wave_bucket}] = in[i];
+    });
+}
+
 fmdp_status fmdp_schedule_learned(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, double slack, fmdp_result* res,
                                   fmdp_learned_report* report) {
     if (!c) return FMDP_ERR_ARG;
@@ -2506,7 +2700,7 @@ fmdp_status fmdp_rollout_trace(fmdp_ctx* c, const fmdp_request* req, fmdp_result
         ra.hd_trace = c->hd_trace.p;
         ra.tie_trace = c->tie_trace.p;
         ra.err = c->err;
-        set_index_args(c, ra);
+        set_index_args(c, ra, g);
         LAUNCH(c, launch_rollout(ra, g.threads, g.smem, c->stream));
         RolloutOut ro;
         CK(cudaMemcpyAsync(&ro, c->rout.p, sizeof(ro), cudaMemcpyDeviceToHost, c->stream));

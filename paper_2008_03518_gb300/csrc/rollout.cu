@@ -1263,7 +1263,32 @@ cudaError_t prepare_rollout_kernel(size_t smem) {
     return cudaFuncSetAttribute(rollout_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
 }
 
+int rollout_max_active_clusters_query(int cs, int threads, size_t smem);
+
 int rollout_max_active_clusters(int cs, int threads, size_t smem) {
+    // the answer depends only on the launch shape and the device: remember it per thread
+    // (batched calls ask before every wave whose shape changed)
+    struct Memo {
+        int dev, cs, threads;
+        size_t smem;
+        int n;
+    };
+    thread_local Memo memo[16];
+    thread_local int memo_n = 0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    for (int i = 0; i < memo_n; ++i)
+        if (memo[i].dev == dev && memo[i].cs == cs && memo[i].threads == threads && memo[i].smem == smem)
+            return memo[i].n;
+    const int n = rollout_max_active_clusters_query(cs, threads, smem);
+    if (n > 0) {
+        memo[memo_n % 16] = Memo{dev, cs, threads, smem, n};
+        memo_n = memo_n < 16 ? memo_n + 1 : 16;
+    }
+    return n;
+}
+
+int rollout_max_active_clusters_query(int cs, int threads, size_t smem) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)cs, 1, 1);
     cfg.blockDim = dim3((unsigned)threads, 1, 1);

@@ -88,6 +88,22 @@ class LearnedReport(ctypes.Structure):
                 ("proposal_ms", ctypes.c_double), ("fastmdp_ms", ctypes.c_double)]
 
 
+class TuneEntry(ctypes.Structure):
+    _fields_ = [("n_actions", ctypes.c_int32), ("combine", ctypes.c_int32), ("plans_bucket", ctypes.c_int32),
+                ("wave_bucket", ctypes.c_int32), ("threads_per_cta", ctypes.c_int32),
+                ("index_stage_items", ctypes.c_int32), ("ms", ctypes.c_double)]
+
+
+class TuneReport(ctypes.Structure):
+    _fields_ = [("chosen", TuneEntry), ("candidates", ctypes.c_int32), ("entries", ctypes.c_int32),
+                ("ctas_per_sm", ctypes.c_int32), ("from_cache", ctypes.c_int32), ("sample", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("default_ms", ctypes.c_double)]
+
+
+def _entry_dict(e):
+    return {k: getattr(e, k) for k, _ in TuneEntry._fields_}
+
+
 class ServeOptions(ctypes.Structure):
     _fields_ = [("time_scale", ctypes.c_double), ("sim_start_step", ctypes.c_int64), ("sim_start_set", ctypes.c_int32),
                 ("max_in_flight", ctypes.c_int32), ("max_active_plans", ctypes.c_int32),
@@ -125,6 +141,7 @@ EXPORTS = ("fmdp_options_default", "fmdp_create", "fmdp_destroy", "fmdp_last_err
            "fmdp_learned_collect", "fmdp_learned_rows", "fmdp_learned_clear_rows", "fmdp_learned_init",
            "fmdp_learned_set_params", "fmdp_learned_get_params", "fmdp_learned_train", "fmdp_learned_loss_grad",
            "fmdp_learned_evaluate", "fmdp_schedule_learned",
+           "fmdp_autotune", "fmdp_tune_cache_get", "fmdp_tune_cache_put",
            "fmdp_get_plan", "fmdp_expire", "fmdp_snapshot", "fmdp_restore", "fmdp_clear", "fmdp_rollout_trace",
            "fmdp_sep_check", "fmdp_sep_check_noalloc", "fmdp_set_profiling", "fmdp_get_stats")
 
@@ -175,6 +192,9 @@ def load(build_if_missing: bool = True):
     L.fmdp_learned_evaluate.argtypes = [vp, P(Request), c.c_int32, c.c_double, P(LearnedReport), P(c.c_int32),
                                         P(c.c_int32), P(c.c_int32)]
     L.fmdp_schedule_learned.argtypes = [vp, P(Request), c.c_int32, c.c_double, P(Result), P(LearnedReport)]
+    L.fmdp_autotune.argtypes = [vp, P(Request), c.c_int32, c.c_int32, P(TuneReport)]
+    L.fmdp_tune_cache_get.argtypes = [vp, P(TuneEntry), c.c_int32, P(c.c_int32)]
+    L.fmdp_tune_cache_put.argtypes = [vp, P(TuneEntry), c.c_int32]
     L.fmdp_serve_options_default.argtypes = [P(ServeOptions)]
     L.fmdp_serve_options_default.restype = None
     L.fmdp_serve.argtypes = [vp, P(Request), P(c.c_double), c.c_int32, P(ServeOptions), P(Result), P(c.c_double),
@@ -506,6 +526,32 @@ class Scheduler:
         out = self._many(lambda h, rq, nn, res: self._L.fmdp_schedule_learned(h, rq, nn, float(slack), res,
                                                                               ctypes.byref(rep)), reqs, points)
         return out, {k: getattr(rep, k) for k, _ in LearnedReport._fields_}
+
+    def autotune(self, sample, force=False):
+        """Times one wave of the sample's rollouts under each launch shape and caches the
+        fastest for the current key; batched calls then use it."""
+        n = len(sample)
+        rq = (Request * max(n, 1))(*[make_request(sample[i]) for i in range(n)])
+        rep = TuneReport()
+        self._check(self._L.fmdp_autotune(self._h, rq, n, 1 if force else 0, ctypes.byref(rep)))
+        out = {k: getattr(rep, k) for k, _ in TuneReport._fields_ if k != "chosen"}
+        out["chosen"] = _entry_dict(rep.chosen)
+        return out
+
+    def tune_cache(self):
+        n = ctypes.c_int32(0)
+        self._check(self._L.fmdp_tune_cache_get(self._h, None, 0, ctypes.byref(n)))
+        buf = (TuneEntry * max(n.value, 1))()
+        self._check(self._L.fmdp_tune_cache_get(self._h, buf, n.value, ctypes.byref(n)))
+        return [_entry_dict(buf[i]) for i in range(n.value)]
+
+    def load_tune_cache(self, entries):
+        n = len(entries)
+        buf = (TuneEntry * max(n, 1))()
+        for i, e in enumerate(entries):
+            for k, _ in TuneEntry._fields_:
+                setattr(buf[i], k, e[k])
+        self._check(self._L.fmdp_tune_cache_put(self._h, buf, n))
 
     def stage(self, reqs):
         n = len(reqs)

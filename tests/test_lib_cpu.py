@@ -43,10 +43,10 @@ def test_struct_layouts_match_header_sizes():
 #include <stddef.h>
 #include "fmdp.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(fmdp_airspace), sizeof(fmdp_action),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(fmdp_airspace), sizeof(fmdp_action),
          sizeof(fmdp_sep), sizeof(fmdp_well), sizeof(fmdp_options), sizeof(fmdp_request), sizeof(fmdp_result),
          sizeof(fmdp_sep_report), sizeof(fmdp_stats), sizeof(fmdp_serve_options), sizeof(fmdp_serve_report),
-         sizeof(fmdp_learned_report));
+         sizeof(fmdp_learned_report), sizeof(fmdp_tune_entry), sizeof(fmdp_tune_report));
   printf("%zu %zu %zu\n", offsetof(fmdp_result, xyz), offsetof(fmdp_request, depart_step), offsetof(fmdp_airspace, static_wells));
   return 0;
 }'''
@@ -59,7 +59,7 @@ int main(void) {
     sizes, offs = [list(map(int, line.split())) for line in subprocess.run([exe], capture_output=True, text=True).stdout.splitlines()]
     py = [ctypes.sizeof(t) for t in (fmdp.Airspace, fmdp.Action, fmdp.Sep, fmdp.Well, fmdp.Options, fmdp.Request,
                                      fmdp.Result, fmdp.SepReport, fmdp.Stats, fmdp.ServeOptions,
-                                     fmdp.ServeReport, fmdp.LearnedReport)]
+                                     fmdp.ServeReport, fmdp.LearnedReport, fmdp.TuneEntry, fmdp.TuneReport)]
     assert py == sizes
     assert offs == [fmdp.Result.xyz.offset, fmdp.Request.depart_step.offset, fmdp.Airspace.static_wells.offset]
 
