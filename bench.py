@@ -228,7 +228,7 @@ def main():
     ap.add_argument("--no-modes", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="batched mode: skip the launch-shape autotuner")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="arrival window per serving rate")
-    ap.add_argument("--modes", default="sequential,learned,batched20k,learned20k,serving",
+    ap.add_argument("--modes", default="sequential,departures,learned,batched20k,learned20k,serving",
                     help="comma-separated extra modes to run")
     ap.add_argument("--time-scale", type=float, default=60.0, help="simulated seconds per wall second (serving)")
     ap.add_argument("--mode", default="batched", choices=["batched", "sequential"],
@@ -340,6 +340,24 @@ def main():
                                      "mode": "one request at a time, each rollout one cluster launch"}
     if want:
         modes["batched"] = {"known_plans": len(sc.plans), "value": value, "unit": UNIT}
+    if "departures" in want:
+        # departure-time candidates: each request's eight variants (0 .. 7 minutes later)
+        # planned together, the first admissible one admitted; requests in FCFS order
+        delays = [60 * k for k in range(8)]
+        nd = min(n_req, 128)
+
+        def dep_step():
+            s.restore()
+            _, ch, _ = s.schedule_departures(sc.requests[:nd], delays, points=False)
+            return ch
+
+        dep_step()
+        mdep, ch = timed(stream, dep_step, 1, barrier)
+        mdep = max_over_ranks(mdep)
+        modes["departures"] = {"known_plans": len(sc.plans), "value": world * nd / (mdep / 1e3), "unit": UNIT,
+                               "ms_per_step": mdep, "requests_per_step": nd, "delays_s": delays,
+                               "admitted": int((ch >= 0).sum()), "delayed": int((ch > 0).sum()),
+                               "mode": "each request's 8 departure variants planned in one launch, FCFS"}
     if "learned" in want:
         modes["learned"] = learned_mode(S, s, sc, stream, barrier, max_over_ranks, world,
                                         lambda rng: S.make_requests(rng, sc.box, 400, hm=sc.heightmap,

@@ -263,6 +263,26 @@ fmdp_status fmdp_learned_evaluate(fmdp_ctx* ctx, const fmdp_request* reqs, int32
 fmdp_status fmdp_schedule_learned(fmdp_ctx* ctx, const fmdp_request* reqs, int32_t n, double slack,
                                   fmdp_result* res, fmdp_learned_report* report);
 
+/* Departure-time candidates (the paper recommends a take-off time among several
+ * candidates, Sec. I, and schedules at different departure times in parallel, Sec. IV).
+ * For each request in FCFS (array) order, its n_delays variants departing delays[d] steps
+ * later are planned concurrently against the table as it stands (one persistent rollout
+ * launch and one separation check over all variants), and the first variant in the order
+ * of delays (the preferred first) whose plan is admissible is admitted. A rejected variant
+ * changes nothing, so each variant up to the chosen one has exactly the result that
+ * fmdp_schedule of it alone would give, and the call equals trying the variants one after
+ * another with fmdp_schedule until one is admitted.
+ *   delays: n_delays entries, 1 <= n_delays <= 1024, in steps (any sign); every variant's
+ *           steps must fall inside the table window (FMDP_ERR_RANGE otherwise, and nothing
+ *           is planned).
+ *   res[i]: the admitted variant's result (its plan_id set), else the first variant's
+ *           (verdict a rejection); xyz / actions buffers as for fmdp_schedule.
+ *   chosen: optional, n entries: index into delays of the admitted variant, -1 if none.
+ *   verdicts: optional, [n][n_delays]: every variant's verdict. */
+fmdp_status fmdp_schedule_departures(fmdp_ctx* ctx, const fmdp_request* reqs, int32_t n,
+                                     const int64_t* delays, int32_t n_delays, fmdp_result* res,
+                                     int32_t* chosen, int32_t* verdicts);
+
 /* ---- Autotuner of the batched rollout's launch shape (no counterpart in the paper; the
  * rollout is Alg. 1 whatever the shape, and results are bit-identical across shapes).
  *

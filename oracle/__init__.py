@@ -244,3 +244,20 @@ class Oracle:
         d.update(xyz=xyz[:n].copy(), actions=acts[:n - 1].copy())
         return d
 
+    def schedule_departures(self, req, delays):
+        """Departure-time candidates (Sec. I: a recommended take-off time among several
+        candidates; Sec. IV: scheduling at different departure times). The variants of req
+        departing delays[d] steps later are taken in the given order, each planned,
+        checked and admitted or rejected exactly as by schedule(); the first admitted one
+        ends the search (a rejected variant leaves the table as it was). Returns the index
+        of the admitted variant (-1 when none) and the results of the variants tried."""
+        fields = ("ox", "oy", "oz", "gx", "gy", "gz", "speed", "depart", "horizon")
+        tried = []
+        for d, delay in enumerate(delays):
+            v = {k: req[k] for k in fields}
+            v["depart"] = int(req["depart"]) + int(delay)
+            res = self.schedule(v)
+            tried.append(res)
+            if res["verdict"] == ADMITTED:
+                return d, tried
+        return -1, tried

@@ -1491,6 +1491,118 @@ void plan_all_fastmdp(fmdp_ctx* c, int32_t n) {
     LAUNCH(c, launch_rollout(ra, g.threads, g.smem, c->stream, n_clusters));
 }
 
+// ---- departure-time candidates
+
+// For each request in FCFS order: its variants departing delays[d] steps later, planned in
+// one persistent rollout launch and separation-checked together against the table as it
+// stands; the first admissible variant in the order of delays is admitted. Rejected
+// variants change nothing, so every variant up to the chosen one has the result that
+// fmdp_schedule of it alone would give.
+void run_departures(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, const int64_t* delays, int32_t D,
+                    fmdp_result* res, int32_t* chosen, int32_t* verdicts) {
+    std::vector<fmdp_request> cand(D);
+    std::vector<int32_t> ident(D);
+    for (int32_t d = 0; d < D; ++d) ident[d] = d;
+    c->p_ident.ensure(D);
+    CK(cudaMemcpyAsync(c->p_ident.p, ident.data(), D * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+    for (int32_t i = 0; i < n; ++i) {
+        for (int32_t d = 0; d < D; ++d) {
+            cand[d] = reqs[i];
+            cand[d].depart_step = reqs[i].depart_step + delays[d];
+        }
+        batch_prepare(c, cand.data(), D, D, nullptr);
+        BatchBuffers& B = c->bat;
+        const Geometry g = batch_geometry(c, 0, D);
+        plan_all_fastmdp(c, D);
+        LAUNCH(c, launch_sep_reset(B.sepo.p, D, c->stream));
+        B.h_ctr.p[1] = D;
+        CK(cudaMemcpyAsync(B.ctr.p + 1, &B.h_ctr.p[1], sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+        SepRowsArgs sa{};
+        sa.m = c->model;
+        sa.tab = table_view(c);
+        sa.S_scan = g.S_scan;
+        sa.traj = B.traj.p;
+        sa.cap = B.cap;
+        sa.rout = B.rout.p;
+        sa.reqs = B.rq;
+        sa.idx = c->p_ident.p;
+        sa.n_dev = B.ctr.p + 1;
+        sa.n_max = D;
+        sa.out = B.sepo.p;
+        if (c->index_on) {
+            sa.items = c->ix_items;
+            sa.cstart = c->ix_cstart;
+            sa.nextra = c->ix_nextra;
+            sa.ncell = c->ix_ncell;
+        }
+        LAUNCH(c, launch_sepcheck_rows(sa, c->stream));
+        CK(cudaMemcpyAsync(B.h_rout.p, B.rout.p, D * sizeof(RolloutOut), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaMemcpyAsync(B.h_sep.p, B.sepo.p, D * sizeof(SepOut), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        require(read_error_word(c) == 0, FMDP_ERR_TIMEOUT, "a bounded device wait expired during a rollout");
+        // the admission rule of the admit kernel, per variant
+        int32_t pick = -1;
+        std::vector<int32_t> vd(D);
+        for (int32_t d = 0; d < D; ++d) {
+            const RolloutOut& ro = B.h_rout.p[d];
+            const SepOut& so = B.h_sep.p[d];
+            vd[d] = ro.status != kStatusCaptured ? ro.status
+                    : so.first_conflict != INT_MAX ? FMDP_REJ_CONFLICT
+                    : so.first_terrain != INT_MAX ? FMDP_REJ_TERRAIN
+                                                  : FMDP_ADMITTED;
+            c->stats.rollout_steps += ro.steps;
+            if (verdicts) verdicts[(size_t)i * D + d] = vd[d];
+            if (pick < 0 && vd[d] == FMDP_ADMITTED) pick = d;
+        }
+        const int32_t show = pick >= 0 ? pick : 0;
+        uint64_t id = 0;
+        if (pick >= 0) {
+            const int32_t slot = take_slot(c);
+            try {
+                c->slots.ensure(1);
+                CK(cudaMemcpyAsync(c->slots.p, &slot, sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+                AdmitArgs aa{};
+                aa.tab = table_view(c);
+                aa.cap = B.cap;
+                aa.traj = B.traj.p + (size_t)pick * B.cap * 3;
+                aa.rout = B.rout.p + pick;
+                aa.reqs = B.rq + pick;
+                aa.slots = c->slots.p;
+                aa.sep = B.sepo.p + pick;
+                aa.force = 0;
+                LAUNCH(c, launch_admit(aa, 1, B.cap, c->stream));
+                const int64_t d0 = cand[pick].depart_step;
+                index_append_admitted(c, aa.traj, B.cap, aa.rout, aa.reqs, aa.sep, nullptr, nullptr, 1, d0,
+                                      d0 + cand[pick].horizon + 1);
+                CK(cudaStreamSynchronize(c->stream));
+            } catch (...) {
+                c->book.free_slots.insert(slot);
+                throw;
+            }
+            id = c->book.next_id++;
+            c->book.plans[id] = PlanMeta{slot, cand[pick].depart_step, B.h_rout.p[pick].n_points};
+            c->book.S_hw = std::max(c->book.S_hw, slot + 1);
+        }
+        if (chosen) chosen[i] = pick;
+        if (res) {
+            fmdp_result& r = res[i];
+            fill_result(B.h_rout.p[show], B.h_sep.p[show], &r);
+            r.verdict = vd[show];
+            r.plan_id = id;
+            r.replanned = 0;
+            r.source = 0;
+            const int32_t np = r.n_points;
+            if (r.xyz)
+                CK(cudaMemcpyAsync(r.xyz, B.traj.p + (size_t)show * B.cap * 3, (size_t)np * 3 * sizeof(float),
+                                   cudaMemcpyDeviceToHost, c->stream));
+            if (r.actions && np > 1)
+                CK(cudaMemcpyAsync(r.actions, B.acts.p + (size_t)show * B.cap, (size_t)(np - 1),
+                                   cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaStreamSynchronize(c->stream));
+        }
+    }
+}
+
 // ---- autotuner of the batched indexed rollout (results do not depend on the shape)
 
 constexpr int32_t kTuneThreads[] = {128, 192, 256, 320, 384};
@@ -2538,6 +2650,24 @@ fmdp_status fmdp_learned_evaluate(fmdp_ctx* c, const fmdp_request* reqs, int32_t
         require(n >= 0 && (n == 0 || reqs), FMDP_ERR_ARG, "null requests");
         for (int32_t i = 0; i < n; ++i) check_request(c, reqs[i]);
         learned_evaluate(c, reqs, n, slack, report, accepted, steps_p, steps_f);
+    });
+}
+
+fmdp_status fmdp_schedule_departures(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, const int64_t* delays,
+                                     int32_t n_delays, fmdp_result* res, int32_t* chosen, int32_t* verdicts) {
+    if (!c) return FMDP_ERR_ARG;
+    return guard(c, [&] {
+        require(n >= 0 && (n == 0 || (reqs && res)), FMDP_ERR_ARG, "null requests or results");
+        require(n_delays >= 1 && n_delays <= kBatchMax && delays, FMDP_ERR_ARG,
+                "between 1 and 1024 departure delays are required");
+        for (int32_t i = 0; i < n; ++i)
+            for (int32_t d = 0; d < n_delays; ++d) {
+                require(std::llabs(delays[d]) < (1ll << 40), FMDP_ERR_ARG, "departure delay out of range");
+                fmdp_request v = reqs[i];
+                v.depart_step += delays[d];
+                check_request(c, v);
+            }
+        run_departures(c, reqs, n, delays, n_delays, res, chosen, verdicts);
     });
 }
 

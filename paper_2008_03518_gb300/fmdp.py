@@ -141,7 +141,7 @@ EXPORTS = ("fmdp_options_default", "fmdp_create", "fmdp_destroy", "fmdp_last_err
            "fmdp_learned_collect", "fmdp_learned_rows", "fmdp_learned_clear_rows", "fmdp_learned_init",
            "fmdp_learned_set_params", "fmdp_learned_get_params", "fmdp_learned_train", "fmdp_learned_loss_grad",
            "fmdp_learned_evaluate", "fmdp_schedule_learned",
-           "fmdp_autotune", "fmdp_tune_cache_get", "fmdp_tune_cache_put",
+           "fmdp_autotune", "fmdp_tune_cache_get", "fmdp_tune_cache_put", "fmdp_schedule_departures",
            "fmdp_get_plan", "fmdp_expire", "fmdp_snapshot", "fmdp_restore", "fmdp_clear", "fmdp_rollout_trace",
            "fmdp_sep_check", "fmdp_sep_check_noalloc", "fmdp_set_profiling", "fmdp_get_stats")
 
@@ -193,6 +193,8 @@ def load(build_if_missing: bool = True):
                                         P(c.c_int32), P(c.c_int32)]
     L.fmdp_schedule_learned.argtypes = [vp, P(Request), c.c_int32, c.c_double, P(Result), P(LearnedReport)]
     L.fmdp_autotune.argtypes = [vp, P(Request), c.c_int32, c.c_int32, P(TuneReport)]
+    L.fmdp_schedule_departures.argtypes = [vp, P(Request), c.c_int32, P(c.c_int64), c.c_int32, P(Result),
+                                           P(c.c_int32), P(c.c_int32)]
     L.fmdp_tune_cache_get.argtypes = [vp, P(TuneEntry), c.c_int32, P(c.c_int32)]
     L.fmdp_tune_cache_put.argtypes = [vp, P(TuneEntry), c.c_int32]
     L.fmdp_serve_options_default.argtypes = [P(ServeOptions)]
@@ -518,6 +520,19 @@ class Scheduler:
                                                   _ptr(acc, ctypes.c_int32), _ptr(sp, ctypes.c_int32),
                                                   _ptr(sf, ctypes.c_int32)))
         return {k: getattr(rep, k) for k, _ in LearnedReport._fields_}, acc[:n], sp[:n], sf[:n]
+
+    def schedule_departures(self, reqs, delays, points=True):
+        """FCFS where each request takes the first admissible of its variants departing
+        delays[d] steps later (planned together). Returns (results, chosen, verdicts)."""
+        n = len(reqs)
+        dl = np.ascontiguousarray(delays, dtype=np.int64)
+        D = dl.size
+        chosen = np.zeros(max(n, 1), dtype=np.int32)
+        verd = np.zeros((max(n, 1), max(D, 1)), dtype=np.int32)
+        out = self._many(lambda h, rq, nn, res: self._L.fmdp_schedule_departures(
+            h, rq, nn, _ptr(dl, ctypes.c_int64), D, res, _ptr(chosen, ctypes.c_int32), _ptr(verd, ctypes.c_int32)),
+            reqs, points)
+        return out, chosen[:n], verd[:n, :D]
 
     def schedule_learned(self, reqs, slack=0.05, points=True):
         """FCFS where each request takes its accepted proposal, else its FastMDP plan."""
