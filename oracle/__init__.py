@@ -39,6 +39,7 @@ class OrcParams(ctypes.Structure):
         ("heightmap", ctypes.POINTER(ctypes.c_float)),
         ("n_static", ctypes.c_int32),
         ("static_wells", ctypes.POINTER(ctypes.c_double)),
+        ("lookahead_W", ctypes.c_int32),
     ]
 
 
@@ -117,8 +118,9 @@ class Oracle:
     """FP64 CPU oracle of FastMDP FCFS planning over a database of known plans."""
 
     def __init__(self, box, dt, gamma, actions, sep, wells=PAPER_WELLS, combine=0, goal_reward=200.0,
-                 heightmap=None, clearance=0.0, deck_value=1000.0, static_wells=None):
+                 heightmap=None, clearance=0.0, deck_value=1000.0, static_wells=None, lookahead_W=1):
         p = OrcParams()
+        p.lookahead_W = int(lookahead_W)
         p.x0, p.y0, p.z0, p.x1, p.y1, p.z1 = map(float, box)
         p.dt, p.gamma, p.goal_reward = float(dt), float(gamma), float(goal_reward)
         p.deck_value, p.clearance = float(deck_value), float(clearance)

@@ -22,7 +22,13 @@
  *     of the classes) or, as an option, the sum. V_deck is the hard-deck penalty of
  *     Alg. 1 evaluated at the successor against terrain clearance.
  *  4. Action selection (Alg. 1, Alg. 9): argmax over valid actions, lowest index on
- *     ties; the state advances to the chosen successor (window W = 1, see below).
+ *     ties; the state advances to the chosen successor.
+ *  4'. Lookahead window W (Sec. IV "Forward project", Alg. 9): each action is held for W
+ *     sub-steps of dt, giving W projected states x_1 .. x_W (x_j = x_(j-1) plus the same
+ *     per-step move); x_j is valued against the peaks at time t + j, and the action's
+ *     value is the largest of the values of its projected states inside the box. The
+ *     action is valid when x_1 is inside the box, and the state advances to x_1 of the
+ *     chosen action (one step of dt). W = 1 is items 2-4 above.
  *  5. Terminal test (Sec. IV "Determine terminal state", Sec. V): the goal is captured
  *     when within one step (speed*dt) of it; the request fails if the horizon runs out
  *     or no action is valid.
@@ -177,34 +183,25 @@ static double fold_peak(const orc_params* p, double agg, double d, double R, dou
     return val > agg ? val : agg;
 }
 
-int64_t orc_q_values(const orc_t* o, const double* s, int32_t h, int64_t t, double speed,
-                     const double* goal, const double* C, const double* S,
-                     double* Q, double* g, double* P, double* V, int32_t* valid, double* nxt) {
+/* The three terms of the value of a state (x, y, z) scored at time step tn: the goal
+ * peak (Alg. 4), the aggregate of negative peaks of the known plans present at tn and of
+ * the static wells (Alg. 5-7), and the hard-deck penalty (Alg. 1). */
+static void state_terms(const orc_t* o, double x, double y, double z, int64_t tn, const double* goal,
+                        double* g_out, double* P_out, double* V_out, int64_t* tests) {
     const orc_params* p = &o->p;
-    double step = speed * p->dt;
-    int64_t tests = 0;
-    for (int a = 0; a < p->n_actions; ++a) {
-        /* forward projection (Alg. 3): turn, then move */
-        int hn = ((h + o->dh[a]) % 24 + 24) % 24;
-        double x = s[0] + step * C[hn];
-        double y = s[1] + step * S[hn];
-        double z = s[2] + p->climb[a] * p->dt;
-        nxt[3 * a] = x; nxt[3 * a + 1] = y; nxt[3 * a + 2] = z;
-        int ok = x >= p->x0 && x <= p->x1 && y >= p->y0 && y <= p->y1 && z >= p->z0 && z <= p->z1;
-        valid[a] = ok;
-
+    {
         /* positive peak: the goal (Alg. 4), |r| gamma^d with infinite radius */
         double ex = goal[0] - x, ey = goal[1] - y, ez = goal[2] - z;
         double dg = sqrt(ex * ex + ey * ey + ez * ez);
-        g[a] = p->goal_reward * pow(p->gamma, dg);
+        *g_out = p->goal_reward * pow(p->gamma, dg);
 
         /* negative peaks of known plans (Alg. 7, Table 3 wells) */
         double agg = 0.0;
         for (int32_t j = 0; j < o->n_plans; ++j) {
             const orc_plan* pl = &o->plans[j];
             double p1[3], p2[3], v[3] = {0.0, 0.0, 0.0};
-            if (!plan_at(pl, t + 1, p1)) continue;
-            if (plan_at(pl, t + 2, p2)) {
+            if (!plan_at(pl, tn, p1)) continue;
+            if (plan_at(pl, tn + 1, p2)) {
                 v[0] = (p2[0] - p1[0]) / p->dt;
                 v[1] = (p2[1] - p1[1]) / p->dt;
                 v[2] = (p2[2] - p1[2]) / p->dt;
@@ -215,7 +212,7 @@ int64_t orc_q_values(const orc_t* o, const double* s, int32_t h, int64_t t, doub
                 double cz = p1[2] + p->w_tau[k] * v[2];
                 double dx = x - cx, dy = y - cy, dz = z - cz;
                 double d = sqrt(dx * dx + dy * dy + dz * dz);
-                ++tests;
+                ++*tests;
                 agg = fold_peak(p, agg, d, p->w_radius[k], p->w_mag[k], p->w_gamma[k]);
             }
         }
@@ -226,16 +223,57 @@ int64_t orc_q_values(const orc_t* o, const double* s, int32_t h, int64_t t, doub
             double d = sqrt(dx * dx + dy * dy + dz * dz);
             agg = fold_peak(p, agg, d, sw[3], sw[4], sw[5]);
         }
-        P[a] = agg;
+        *P_out = agg;
 
-        /* hard deck (Alg. 1) as terrain clearance at the successor */
+        /* hard deck (Alg. 1) as terrain clearance at the state */
         double vd = 0.0;
         if (p->hm_nx >= 2) {
             double c = z - orc_terrain(o, x, y);
             if (c < p->clearance) vd = p->deck_value - c;
         }
-        V[a] = vd;
-        Q[a] = ok ? g[a] - agg - vd : -INFINITY;
+        *V_out = vd;
+    }
+}
+
+static int in_box(const orc_params* p, double x, double y, double z) {
+    return x >= p->x0 && x <= p->x1 && y >= p->y0 && y <= p->y1 && z >= p->z0 && z <= p->z1;
+}
+
+int64_t orc_q_values(const orc_t* o, const double* s, int32_t h, int64_t t, double speed,
+                     const double* goal, const double* C, const double* S,
+                     double* Q, double* g, double* P, double* V, int32_t* valid, double* nxt) {
+    const orc_params* p = &o->p;
+    double step = speed * p->dt;
+    int W = p->lookahead_W > 1 ? p->lookahead_W : 1;
+    int64_t tests = 0;
+    for (int a = 0; a < p->n_actions; ++a) {
+        /* forward projection (Alg. 3): turn, then move */
+        int hn = ((h + o->dh[a]) % 24 + 24) % 24;
+        double x = s[0] + step * C[hn];
+        double y = s[1] + step * S[hn];
+        double z = s[2] + p->climb[a] * p->dt;
+        nxt[3 * a] = x; nxt[3 * a + 1] = y; nxt[3 * a + 2] = z;
+        int ok = in_box(p, x, y, z);
+        valid[a] = ok;
+        /* value of x_1, then of x_2 .. x_W (the action held), keeping the largest */
+        state_terms(o, x, y, z, t + 1, goal, &g[a], &P[a], &V[a], &tests);
+        double best = g[a] - P[a] - V[a];
+        for (int j = 2; j <= W; ++j) {
+            x = x + step * C[hn];
+            y = y + step * S[hn];
+            z = z + p->climb[a] * p->dt;
+            if (!in_box(p, x, y, z)) continue;
+            double gj, Pj, Vj;
+            state_terms(o, x, y, z, t + j, goal, &gj, &Pj, &Vj, &tests);
+            double vj = gj - Pj - Vj;
+            if (vj > best) {
+                best = vj;
+                g[a] = gj;
+                P[a] = Pj;
+                V[a] = Vj;
+            }
+        }
+        Q[a] = ok ? best : -INFINITY;
     }
     return tests;
 }

@@ -49,6 +49,7 @@ typedef struct {
     const float* heightmap;           /* [hm_ny][hm_nx], copied at create */
     int32_t n_static;
     const double* static_wells;       /* [n_static][6] x,y,z,R,|r|,gamma; copied at create */
+    int32_t lookahead_W;              /* projected sub-steps per action (0 or 1: one) */
 } orc_params;
 
 typedef struct {
