@@ -228,7 +228,7 @@ def main():
     ap.add_argument("--no-modes", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="batched mode: skip the launch-shape autotuner")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="arrival window per serving rate")
-    ap.add_argument("--modes", default="sequential,departures,learned,batched20k,learned20k,serving",
+    ap.add_argument("--modes", default="sequential,departures,lookahead,learned,batched20k,learned20k,serving",
                     help="comma-separated extra modes to run")
     ap.add_argument("--time-scale", type=float, default=60.0, help="simulated seconds per wall second (serving)")
     ap.add_argument("--mode", default="batched", choices=["batched", "sequential"],
@@ -358,6 +358,28 @@ def main():
                                "ms_per_step": mdep, "requests_per_step": nd, "delays_s": delays,
                                "admitted": int((ch >= 0).sum()), "delayed": int((ch > 0).sum()),
                                "mode": "each request's 8 departure variants planned in one launch, FCFS"}
+    if "lookahead" in want:
+        # the paper's fidelity: W = 10 sub-steps of 0.1 s, FCFS one request at a time
+        sce = S.e1_fine()
+        se = Scheduler.from_scenario(sce, lookahead_W=sce.meta["lookahead_W"])
+        se.set_stream(stream.cuda_stream)
+        se.snapshot()
+        se.set_profiling(1)
+        se.schedule_many(sce.requests, points=False)
+        steps_e = se.stats()["rollout_steps"]
+        se.set_profiling(0)
+
+        def la_step():
+            se.restore()
+            return se.schedule_many(sce.requests, points=False)
+
+        mla, _ = timed(stream, la_step, 1, barrier)
+        mla = max_over_ranks(mla)
+        modes["lookahead_w10_dt01"] = {"known_plans": len(sce.plans), "value": world * len(sce.requests) / (mla / 1e3),
+                                       "unit": UNIT, "ms_per_step": mla, "requests_per_step": len(sce.requests),
+                                       "rollout_steps_per_step": steps_e, "us_per_rollout_step": 1e3 * mla / max(steps_e, 1),
+                                       "workload": sce.name}
+        se.close()
     if "learned" in want:
         modes["learned"] = learned_mode(S, s, sc, stream, barrier, max_over_ranks, world,
                                         lambda rng: S.make_requests(rng, sc.box, 400, hm=sc.heightmap,

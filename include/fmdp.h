@@ -86,7 +86,13 @@ typedef struct {
     const fmdp_well* wells;   /* NULL: the paper's five wells (Table 3) */
     int32_t n_wells;          /* <= 8 */
     double goal_reward;       /* |r| of the goal peak (Table 3: 200) */
-    int32_t lookahead_W;      /* lookahead window; only 1 is implemented */
+    int32_t lookahead_W;      /* lookahead window W (Sec. IV "Forward project", Alg. 9): each
+                                 action is held for W steps of dt and valued by the largest
+                                 value along them; the state advances one step. 0 or 1: the
+                                 one-step rule; at most 16. W > 1 plans one request at a time
+                                 (fmdp_schedule_batch and staged batches give the same results
+                                 that way); fmdp_serve, the learned proposal, departure
+                                 candidates and the autotuner require W = 1. */
     int32_t cluster_size;     /* CTAs cooperating on one rollout (0 = automatic) */
     int32_t threads_per_cta;  /* 0 = automatic; else a multiple of 32 in [128, 384] */
     int32_t batch_size;       /* fmdp_schedule_batch: requests per speculative batch

@@ -501,6 +501,32 @@ int32_t bit_length(int64_t v) {
     return b;
 }
 int32_t batch_size_of(const fmdp_ctx* c) { return c->opt.batch_size > 0 ? c->opt.batch_size : 256; }
+// lookahead window of the rollouts (Sec. IV "Forward project"); 1 is the one-step rule
+int32_t window_of(const fmdp_ctx* c) { return c->opt.lookahead_W > 1 ? c->opt.lookahead_W : 1; }
+
+// The lookahead rollout of one request (W > 1), written like the rollout kernel's.
+void launch_window_rollout(fmdp_ctx* c, const Geometry& g, const fmdp_request* req_dev, int32_t cap, float* traj,
+                           uint8_t* acts, RolloutOut* out, bool trace) {
+    LookArgs la{};
+    la.m = c->model;
+    la.tab = table_view(c);
+    la.S_scan = g.S_scan;
+    la.W = window_of(c);
+    la.cap = cap;
+    la.n_req = 1;
+    la.trace = trace ? 1 : 0;
+    la.reqs = req_dev;
+    la.traj = traj;
+    la.acts = acts;
+    la.out = out;
+    if (trace) {
+        la.q_trace = c->q_trace.p;
+        la.st_trace = c->st_trace.p;
+        la.hd_trace = c->hd_trace.p;
+        la.tie_trace = c->tie_trace.p;
+    }
+    LAUNCH(c, launch_lookahead(la, c->stream));
+}
 std::array<int32_t, 4> tune_key(const fmdp_ctx* c, int32_t wave) {
     return {c->A, c->opt.combine, bit_length((int64_t)c->book.plans.size()), bit_length(wave)};
 }
@@ -626,7 +652,10 @@ void enqueue_sequence(fmdp_ctx* c, SeqBuffers& B, const fmdp_request* host_reqs,
         ra.phase = c->phase_timing ? c->phase.p : nullptr;
         {
             KernelTimer t(c, 0);
-            LAUNCH(c, launch_rollout(ra, g.threads, g.smem, c->stream));
+            if (window_of(c) > 1)
+                launch_window_rollout(c, g, ra.reqs, cap, ra.traj, ra.acts, ra.out, false);
+            else
+                LAUNCH(c, launch_rollout(ra, g.threads, g.smem, c->stream));
             t.stop();
         }
         SepArgs sa{};
@@ -2219,7 +2248,7 @@ fmdp_status fmdp_create(const fmdp_airspace* air, double gamma, const fmdp_actio
         fmdp_options o;
         if (options) o = *options; else fmdp_options_default(&o);
         require(o.combine == 0 || o.combine == 1, FMDP_ERR_ARG, "combine must be 0 (max) or 1 (sum)");
-        require(o.lookahead_W == 0 || o.lookahead_W == 1, FMDP_ERR_ARG, "only lookahead_W = 1 is implemented");
+        require(o.lookahead_W >= 0 && o.lookahead_W <= kMaxLookahead, FMDP_ERR_ARG, "lookahead_W must be 0 .. 16");
         require(o.goal_reward >= 0.0 && std::isfinite(o.goal_reward), FMDP_ERR_ARG, "goal reward must be >= 0");
         require(o.cluster_size >= 0 && o.cluster_size <= kMaxCluster, FMDP_ERR_ARG, "cluster size 0..16");
         require(o.threads_per_cta == 0 || (o.threads_per_cta >= 128 && o.threads_per_cta <= 384 &&
@@ -2263,6 +2292,7 @@ fmdp_status fmdp_create(const fmdp_airspace* air, double gamma, const fmdp_actio
         CK(prepare_rollout_kernel((size_t)c->max_smem));
         CK(prepare_sepcheck_rows(sepcheck_rows_smem(kBatchMax)));
         CK(prepare_policy_kernel());
+        CK(prepare_lookahead_kernel());
 
         c->T_win = a.n_slices_window;
         c->S_max = a.max_slots;
@@ -2406,6 +2436,7 @@ fmdp_status fmdp_schedule_staged(fmdp_ctx* c, int32_t batched, int32_t* n_admitt
         require((size_t)n <= c->book.free_slots.size(), FMDP_ERR_FULL, "not enough free slots for the staged run");
         c->staged_done = false;
         int32_t adm;
+        if (batched && window_of(c) > 1) batched = 0;  // lookahead rollouts run one request at a time
         if (batched) {
             c->staged_res.assign(n, fmdp_result{});
             adm = run_batch(c, c->staged.data(), n, c->staged_res.data(), c->stg.reqs.p, true);
@@ -2469,7 +2500,10 @@ fmdp_status fmdp_schedule_batch(fmdp_ctx* c, const fmdp_request* reqs, int32_t n
     return guard(c, [&] {
         require(n >= 0 && (n == 0 || (reqs && res)), FMDP_ERR_ARG, "null requests or results");
         for (int32_t i = 0; i < n; ++i) check_request(c, reqs[i]);
-        run_batch(c, reqs, n, res, nullptr, false);
+        if (window_of(c) > 1)  // lookahead rollouts: FCFS one request at a time (same results)
+            run_fcfs(c, reqs, n, res, false);
+        else
+            run_batch(c, reqs, n, res, nullptr, false);
     });
 }
 
@@ -2532,6 +2566,7 @@ fmdp_status fmdp_serve(fmdp_ctx* c, const fmdp_request* reqs, const double* arri
                        fmdp_serve_report* report) {
     if (!c) return FMDP_ERR_ARG;
     return guard(c, [&] {
+        require(window_of(c) == 1, FMDP_ERR_ARG, "this entry point plans with lookahead_W = 1");
         require(n >= 0 && (n == 0 || (reqs && arrival_s && res)), FMDP_ERR_ARG, "null requests, arrivals or results");
         fmdp_serve_options o;
         if (opt) o = *opt; else fmdp_serve_options_default(&o);
@@ -2550,6 +2585,7 @@ fmdp_status fmdp_serve(fmdp_ctx* c, const fmdp_request* reqs, const double* arri
 fmdp_status fmdp_learned_collect(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, int32_t* n_rows_out) {
     if (!c) return FMDP_ERR_ARG;
     return guard(c, [&] {
+        require(window_of(c) == 1, FMDP_ERR_ARG, "this entry point plans with lookahead_W = 1");
         require(n >= 0 && (n == 0 || reqs), FMDP_ERR_ARG, "null requests");
         for (int32_t i = 0; i < n; ++i) check_request(c, reqs[i]);
         learned_collect(c, reqs, n);
@@ -2647,6 +2683,7 @@ fmdp_status fmdp_learned_evaluate(fmdp_ctx* c, const fmdp_request* reqs, int32_t
                                   int32_t* steps_f) {
     if (!c) return FMDP_ERR_ARG;
     return guard(c, [&] {
+        require(window_of(c) == 1, FMDP_ERR_ARG, "this entry point plans with lookahead_W = 1");
         require(n >= 0 && (n == 0 || reqs), FMDP_ERR_ARG, "null requests");
         for (int32_t i = 0; i < n; ++i) check_request(c, reqs[i]);
         learned_evaluate(c, reqs, n, slack, report, accepted, steps_p, steps_f);
@@ -2657,6 +2694,7 @@ fmdp_status fmdp_schedule_departures(fmdp_ctx* c, const fmdp_request* reqs, int3
                                      int32_t n_delays, fmdp_result* res, int32_t* chosen, int32_t* verdicts) {
     if (!c) return FMDP_ERR_ARG;
     return guard(c, [&] {
+        require(window_of(c) == 1, FMDP_ERR_ARG, "this entry point plans with lookahead_W = 1");
         require(n >= 0 && (n == 0 || (reqs && res)), FMDP_ERR_ARG, "null requests or results");
         require(n_delays >= 1 && n_delays <= kBatchMax && delays, FMDP_ERR_ARG,
                 "between 1 and 1024 departure delays are required");
@@ -2675,6 +2713,7 @@ fmdp_status fmdp_autotune(fmdp_ctx* c, const fmdp_request* sample, int32_t n, in
                           fmdp_tune_report* report) {
     if (!c) return FMDP_ERR_ARG;
     return guard(c, [&] {
+        require(window_of(c) == 1, FMDP_ERR_ARG, "this entry point plans with lookahead_W = 1");
         require(n >= 1 && sample, FMDP_ERR_ARG, "the autotuner needs at least one sample request");
         for (int32_t i = 0; i < n; ++i) check_request(c, sample[i]);
         autotune(c, sample, n, force != 0, report);
@@ -2711,6 +2750,7 @@ fmdp_status fmdp_schedule_learned(fmdp_ctx* c, const fmdp_request* reqs, int32_t
                                   fmdp_learned_report* report) {
     if (!c) return FMDP_ERR_ARG;
     return guard(c, [&] {
+        require(window_of(c) == 1, FMDP_ERR_ARG, "this entry point plans with lookahead_W = 1");
         require(n >= 0 && (n == 0 || (reqs && res)), FMDP_ERR_ARG, "null requests or results");
         require(c->index_on, FMDP_ERR_ARG, "the learned proposal reads the spatial index (full_scan must be 0)");
         require(c->mlp_ready, FMDP_ERR_ARG, "the proposal network has no parameters (init or set them first)");
@@ -2831,7 +2871,10 @@ fmdp_status fmdp_rollout_trace(fmdp_ctx* c, const fmdp_request* req, fmdp_result
         ra.tie_trace = c->tie_trace.p;
         ra.err = c->err;
         set_index_args(c, ra, g);
-        LAUNCH(c, launch_rollout(ra, g.threads, g.smem, c->stream));
+        if (window_of(c) > 1)
+            launch_window_rollout(c, g, c->reqs.p, cap, c->traj.p, c->acts.p, c->rout.p, true);
+        else
+            LAUNCH(c, launch_rollout(ra, g.threads, g.smem, c->stream));
         RolloutOut ro;
         CK(cudaMemcpyAsync(&ro, c->rout.p, sizeof(ro), cudaMemcpyDeviceToHost, c->stream));
         CK(cudaStreamSynchronize(c->stream));

@@ -271,6 +271,30 @@ cudaError_t launch_batch_minsep(const MinSepArgs& a, cudaStream_t s);
 cudaError_t launch_influence(const InfluenceArgs& a, int n_max, int max_points, cudaStream_t s);
 cudaError_t launch_sep_reset_idx(SepOut* out, const int32_t* idx, const int32_t* n_dev, int n_max, cudaStream_t s);
 
+// Rollout with a lookahead window of W sub-steps (lookahead.cu): one CTA per request,
+// requests[0 .. n_req), trajectories of cap samples each; traces as for the rollout kernel.
+constexpr int kMaxLookahead = 16;
+struct LookArgs {
+    Model m;
+    TableView tab;
+    int32_t S_scan;  // slots scanned per slice
+    int32_t W;       // 1 .. kMaxLookahead
+    int32_t cap;
+    int32_t n_req;
+    int32_t trace;
+    const fmdp_request* reqs;
+    float* traj;
+    uint8_t* acts;
+    RolloutOut* out;
+    double* q_trace;
+    double* st_trace;
+    int32_t* hd_trace;
+    uint8_t* tie_trace;
+};
+size_t lookahead_smem_bytes(int A, int W);
+cudaError_t prepare_lookahead_kernel();
+cudaError_t launch_lookahead(const LookArgs& a, cudaStream_t s);
+
 // ---------------------------------------------------------------- device helpers
 
 __device__ __forceinline__ int float_key(float f) {

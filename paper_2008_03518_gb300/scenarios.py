@@ -236,6 +236,21 @@ def c1_plain_small(seed: int = 101) -> Scenario:
                     (150.0, 30.0), plans, reqs, n_slices_window=2048, max_slots=512)
 
 
+def e1_fine(seed: int = 106, n_plans: int = 60, n_requests: int = 12, lookahead_W: int = 10) -> Scenario:
+    """The paper's own fidelity (Sec. IV "Forward project": W = 10 sub-steps of dt = 0.1 s):
+    a 4 km x 4 km x 500 m box, straight known plans sampled every 0.1 s and departing within
+    the first minute, and requests of up to 300 s that cross their paths; 15 actions. The
+    lookahead window is a planning option (meta["lookahead_W"])."""
+    rng = np.random.default_rng(seed)
+    box = (0.0, 0.0, 0.0, 4000.0, 4000.0, 500.0)
+    dt = 0.1
+    plans = straight_plans(rng, box, n_plans, 100.0, 400.0, 20.0, 40.0, 0, 600, dt)
+    reqs = make_requests(rng, box, n_requests, zlo=100.0, zhi=400.0, tlo=0, thi=600, horizon=3000)
+    return Scenario(f"e1_fine_4km_{n_plans}plans_{n_requests}req_A15_dt0.1_W{lookahead_W}", box, dt, 0.99,
+                    action_grid((-2.0, 0.0, 2.0)), (150.0, 30.0), plans, reqs, n_slices_window=4096,
+                    max_slots=n_plans + n_requests + 32, meta={"lookahead_W": lookahead_W})
+
+
 def c2_plain_scale(seed: int = 102, n_plans: int = 3000, n_requests: int = 1000) -> Scenario:
     """30 km x 30 km x 1 km with a 512^2 fractal heightmap (0-300 m, 60 m clearance),
     multi-leg known plans, FCFS requests with 25 actions and horizons up to 1800 steps."""
