@@ -86,6 +86,9 @@ def lib():
                                   fp, dp, ip, ip, dp, dp, ip, P(OrcResult)]
         L.orc_sep_check.restype = ctypes.c_int64
         L.orc_sep_check.argtypes = [ctypes.c_void_p, ctypes.c_int64, fp, ctypes.c_int32, P(OrcResult)]
+        L.orc_cosim.restype = ctypes.c_int32
+        L.orc_cosim.argtypes = [ctypes.c_void_p, P(OrcRequest), ctypes.c_int32, ip, ctypes.c_int32, fp, ip, dp, dp,
+                                P(OrcResult)]
         L.orc_schedule.restype = ctypes.c_int32
         L.orc_schedule.argtypes = [ctypes.c_void_p, P(OrcRequest), ctypes.c_int32, fp, ip, P(OrcResult)]
         _lib = L
@@ -263,3 +266,55 @@ class Oracle:
             if res["verdict"] == ADMITTED:
                 return d, tried
         return -1, tried
+
+    def cosim(self, reqs, follow=None, trace=False):
+        """Co-simulation of a batch on one clock (Alg. 1 with the batch's aircraft as
+        each other's wells, Sec. V); nothing is admitted. follow: optional per-request
+        action sequences taken at near-ties. Returns one dict per request."""
+        n = len(reqs)
+        rq = (OrcRequest * n)(*[make_request(r) for r in reqs])
+        cap = max(int(r["horizon"]) for r in reqs) + 1
+        A = self.n_actions
+        xyz = np.zeros((n, cap, 3), dtype=np.float32)
+        acts = np.full((n, cap), -1, dtype=np.int32)
+        fol = None
+        if follow is not None:
+            fol = np.full((n, cap), -1, dtype=np.int32)
+            for i, f in enumerate(follow):
+                f = np.asarray(f, dtype=np.int32)
+                fol[i, :f.size] = f
+        qt = np.zeros((n, cap, A)) if trace else None
+        st = np.zeros((n, cap, A)) if trace else None
+        res = (OrcResult * n)()
+        if lib().orc_cosim(self._h, rq, n, _ptr(fol, ctypes.c_int32), cap, _ptr(xyz, ctypes.c_float),
+                           _ptr(acts, ctypes.c_int32), _ptr(qt, ctypes.c_double), _ptr(st, ctypes.c_double),
+                           res) != 0:
+            raise ValueError("oracle co-simulation rejected the requests")
+        out = []
+        for i in range(n):
+            d = _res_dict(res[i])
+            m = res[i].n_points
+            d.update(xyz=xyz[i, :m].copy(), actions=acts[i, :m - 1].copy())
+            if trace:
+                d.update(q=qt[i, :m - 1].copy(), scale=st[i, :m - 1].copy())
+            out.append(d)
+        return out
+
+    def schedule_cosim(self, reqs, follow=None):
+        """Co-simulation, then first-come-first-served admission in array order: a
+        captured trajectory is stored if it keeps separation from every stored plan
+        (earlier members of the batch included) and clears the terrain."""
+        out = self.cosim(reqs, follow)
+        for r, d in zip(reqs, out):
+            if d["captured"]:
+                chk = self.sep_check(int(r["depart"]), d["xyz"])
+                if chk["first_conflict"] >= 0:
+                    d["verdict"] = REJ_CONFLICT
+                elif chk["first_terrain"] >= 0:
+                    d["verdict"] = REJ_TERRAIN
+                else:
+                    d["verdict"] = ADMITTED
+                    self.add_plan(int(r["depart"]), d["xyz"])
+                d.update(first_conflict=chk["first_conflict"], first_terrain=chk["first_terrain"],
+                         min_sep_h=chk["min_sep_h"], min_sep_v=chk["min_sep_v"])
+        return out

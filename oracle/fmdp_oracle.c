@@ -186,8 +186,16 @@ static double fold_peak(const orc_params* p, double agg, double d, double R, dou
 /* The three terms of the value of a state (x, y, z) scored at time step tn: the goal
  * peak (Alg. 4), the aggregate of negative peaks of the known plans present at tn and of
  * the static wells (Alg. 5-7), and the hard-deck penalty (Alg. 1). */
+/* Extra negative peaks of one step: the wells of the other aircraft of a co-simulated batch
+ * (centres xc[3 * i], well row xk[i] of the well table). */
+typedef struct {
+    const double* xc;
+    const int32_t* xk;
+    int32_t n;
+} orc_extra;
+
 static void state_terms(const orc_t* o, double x, double y, double z, int64_t tn, const double* goal,
-                        double* g_out, double* P_out, double* V_out, int64_t* tests) {
+                        const orc_extra* ex_peaks, double* g_out, double* P_out, double* V_out, int64_t* tests) {
     const orc_params* p = &o->p;
     {
         /* positive peak: the goal (Alg. 4), |r| gamma^d with infinite radius */
@@ -216,6 +224,17 @@ static void state_terms(const orc_t* o, double x, double y, double z, int64_t tn
                 agg = fold_peak(p, agg, d, p->w_radius[k], p->w_mag[k], p->w_gamma[k]);
             }
         }
+        /* the other aircraft of a co-simulated batch (Alg. 1 "build neg rewards", Build
+         * Peaks kernel: Table 3 wells at their current position and velocity) */
+        if (ex_peaks)
+            for (int32_t i = 0; i < ex_peaks->n; ++i) {
+                const double* c = ex_peaks->xc + 3 * i;
+                int k = ex_peaks->xk[i];
+                double dx = x - c[0], dy = y - c[1], dz = z - c[2];
+                double d = sqrt(dx * dx + dy * dy + dz * dz);
+                ++*tests;
+                agg = fold_peak(p, agg, d, p->w_radius[k], p->w_mag[k], p->w_gamma[k]);
+            }
         /* static negative peaks: terrain / restricted volumes (Alg. 6) */
         for (int32_t w = 0; w < p->n_static; ++w) {
             const double* sw = &o->statics[6 * w];
@@ -239,9 +258,9 @@ static int in_box(const orc_params* p, double x, double y, double z) {
     return x >= p->x0 && x <= p->x1 && y >= p->y0 && y <= p->y1 && z >= p->z0 && z <= p->z1;
 }
 
-int64_t orc_q_values(const orc_t* o, const double* s, int32_t h, int64_t t, double speed,
-                     const double* goal, const double* C, const double* S,
-                     double* Q, double* g, double* P, double* V, int32_t* valid, double* nxt) {
+static int64_t q_values_x(const orc_t* o, const double* s, int32_t h, int64_t t, double speed,
+                          const double* goal, const double* C, const double* S, const orc_extra* ex_peaks,
+                          double* Q, double* g, double* P, double* V, int32_t* valid, double* nxt) {
     const orc_params* p = &o->p;
     double step = speed * p->dt;
     int W = p->lookahead_W > 1 ? p->lookahead_W : 1;
@@ -256,7 +275,7 @@ int64_t orc_q_values(const orc_t* o, const double* s, int32_t h, int64_t t, doub
         int ok = in_box(p, x, y, z);
         valid[a] = ok;
         /* value of x_1, then of x_2 .. x_W (the action held), keeping the largest */
-        state_terms(o, x, y, z, t + 1, goal, &g[a], &P[a], &V[a], &tests);
+        state_terms(o, x, y, z, t + 1, goal, ex_peaks, &g[a], &P[a], &V[a], &tests);
         double best = g[a] - P[a] - V[a];
         for (int j = 2; j <= W; ++j) {
             x = x + step * C[hn];
@@ -264,7 +283,7 @@ int64_t orc_q_values(const orc_t* o, const double* s, int32_t h, int64_t t, doub
             z = z + p->climb[a] * p->dt;
             if (!in_box(p, x, y, z)) continue;
             double gj, Pj, Vj;
-            state_terms(o, x, y, z, t + j, goal, &gj, &Pj, &Vj, &tests);
+            state_terms(o, x, y, z, t + j, goal, ex_peaks, &gj, &Pj, &Vj, &tests);
             double vj = gj - Pj - Vj;
             if (vj > best) {
                 best = vj;
@@ -276,6 +295,12 @@ int64_t orc_q_values(const orc_t* o, const double* s, int32_t h, int64_t t, doub
         Q[a] = ok ? best : -INFINITY;
     }
     return tests;
+}
+
+int64_t orc_q_values(const orc_t* o, const double* s, int32_t h, int64_t t, double speed,
+                     const double* goal, const double* C, const double* S,
+                     double* Q, double* g, double* P, double* V, int32_t* valid, double* nxt) {
+    return q_values_x(o, s, h, t, speed, goal, C, S, NULL, Q, g, P, V, valid, nxt);
 }
 
 static double term_scale(double g, double P, double V) {
@@ -422,5 +447,149 @@ int32_t orc_schedule(orc_t* o, const orc_request* r, int32_t cap, float* xyz, in
         else res->verdict = ORC_ADMITTED;
     }
     if (res->verdict == ORC_ADMITTED) res->plan_id = orc_add_plan(o, r->depart, xyz, res->n_points);
+    return 0;
+}
+
+/* Co-simulation of a batch (Alg. 1 "DistributedUam"; Sec. V, batches whose aircraft see
+ * each other). All aircraft step on one clock: at step t every aircraft in flight (departed,
+ * not finished) values its actions against the known plans, the static peaks and the
+ * Table 3 wells of every other aircraft in flight, centred at that aircraft's position at t
+ * plus tau times its velocity (its last move over dt; zero before its first move). Then all
+ * of them take their chosen actions together. Admission is left to the caller. */
+int32_t orc_cosim(const orc_t* o, const orc_request* reqs, int32_t n, const int32_t* follow, int32_t cap,
+                  float* xyz, int32_t* actions, double* q_trace, double* scale_trace, orc_result* res) {
+    const orc_params* p = &o->p;
+    const int A = p->n_actions, K = p->n_wells;
+    if (n <= 0) return 0;
+    for (int32_t i = 0; i < n; ++i)
+        if (reqs[i].horizon < 0 || cap < reqs[i].horizon + 1 || reqs[i].speed <= 0.0) return -1;
+    double* C = malloc(sizeof(double) * 24 * n);
+    double* S = malloc(sizeof(double) * 24 * n);
+    double* st = malloc(sizeof(double) * 3 * n);
+    double* prev = malloc(sizeof(double) * 3 * n);
+    int32_t* h = calloc(n, sizeof(int32_t));
+    int32_t* k = calloc(n, sizeof(int32_t));
+    int32_t* done = calloc(n, sizeof(int32_t));
+    int32_t* choice = malloc(sizeof(int32_t) * n);
+    double* nx = malloc(sizeof(double) * 3 * n);
+    double* xc = malloc(sizeof(double) * 3 * (size_t)K * n);
+    int32_t* xk = malloc(sizeof(int32_t) * (size_t)K * n);
+    int32_t* owner = malloc(sizeof(int32_t) * (size_t)K * n);
+    double* xc_i = malloc(sizeof(double) * 3 * (size_t)K * n);
+    int32_t* xk_i = malloc(sizeof(int32_t) * (size_t)K * n);
+    if (!C || !S || !st || !prev || !h || !k || !done || !choice || !nx || !xc || !xk || !owner || !xc_i || !xk_i) {
+        free(C); free(S); free(st); free(prev); free(h); free(k); free(done); free(choice); free(nx);
+        free(xc); free(xk); free(owner); free(xc_i); free(xk_i);
+        return -1;
+    }
+    int64_t t = reqs[0].depart;
+    for (int32_t i = 0; i < n; ++i) {
+        const orc_request* r = &reqs[i];
+        orc_heading_table(r->ox, r->oy, r->gx, r->gy, C + 24 * i, S + 24 * i);
+        st[3 * i] = r->ox; st[3 * i + 1] = r->oy; st[3 * i + 2] = r->oz;
+        memset(&res[i], 0, sizeof(orc_result));
+        res[i].verdict = -1;
+        res[i].mismatch_step = -1;
+        res[i].first_conflict = -1;
+        res[i].first_terrain = -1;
+        res[i].plan_id = -1;
+        res[i].n_points = 1;
+        if (xyz) {
+            xyz[(size_t)3 * cap * i] = (float)r->ox;
+            xyz[(size_t)3 * cap * i + 1] = (float)r->oy;
+            xyz[(size_t)3 * cap * i + 2] = (float)r->oz;
+        }
+        double step = r->speed * p->dt;
+        double ex = r->gx - r->ox, ey = r->gy - r->oy, ez = r->gz - r->oz;
+        if ((ex * ex + ey * ey + ez * ez) <= step * step) { done[i] = 1; res[i].captured = 1; }
+        else if (r->horizon <= 0) { done[i] = 1; res[i].verdict = ORC_REJ_HORIZON; }
+        if (r->depart < t) t = r->depart;
+    }
+    double Q[ORC_MAX_ACTIONS], g[ORC_MAX_ACTIONS], P[ORC_MAX_ACTIONS], V[ORC_MAX_ACTIONS];
+    double nxt[3 * ORC_MAX_ACTIONS];
+    int32_t valid[ORC_MAX_ACTIONS];
+    for (;;) {
+        int any = 0;
+        for (int32_t i = 0; i < n; ++i) any |= !done[i];
+        if (!any) break;
+        /* peaks of the aircraft in flight at t */
+        int32_t np = 0;
+        for (int32_t m = 0; m < n; ++m) {
+            if (done[m] || reqs[m].depart > t) continue;
+            double v[3] = {0.0, 0.0, 0.0};
+            if (k[m] > 0)
+                for (int c = 0; c < 3; ++c) v[c] = (st[3 * m + c] - prev[3 * m + c]) / p->dt;
+            for (int w = 0; w < K; ++w) {
+                for (int c = 0; c < 3; ++c) xc[3 * np + c] = st[3 * m + c] + p->w_tau[w] * v[c];
+                xk[np] = w;
+                owner[np] = m;
+                ++np;
+            }
+        }
+        /* every aircraft in flight chooses (against the others' peaks) */
+        for (int32_t i = 0; i < n; ++i) {
+            choice[i] = -1;
+            if (done[i] || reqs[i].depart > t) continue;
+            const orc_request* r = &reqs[i];
+            orc_extra ex = {xc_i, xk_i, 0};
+            for (int32_t q = 0; q < np; ++q) {
+                if (owner[q] == i) continue;
+                xc_i[3 * ex.n] = xc[3 * q]; xc_i[3 * ex.n + 1] = xc[3 * q + 1]; xc_i[3 * ex.n + 2] = xc[3 * q + 2];
+                xk_i[ex.n] = xk[q];
+                ++ex.n;
+            }
+            double goal[3] = {r->gx, r->gy, r->gz};
+            res[i].well_tests += q_values_x(o, st + 3 * i, h[i], t, r->speed, goal, C + 24 * i, S + 24 * i, &ex, Q, g,
+                                            P, V, valid, nxt);
+            int a1 = -1, a2 = -1;
+            for (int a = 0; a < A; ++a)
+                if (valid[a] && (a1 < 0 || Q[a] > Q[a1])) a1 = a;
+            const int kk = k[i];
+            if (q_trace) for (int a = 0; a < A; ++a) q_trace[((size_t)i * cap + kk) * A + a] = Q[a];
+            if (scale_trace)
+                for (int a = 0; a < A; ++a) scale_trace[((size_t)i * cap + kk) * A + a] = term_scale(g[a], P[a], V[a]);
+            if (a1 < 0) { choice[i] = -2; continue; }
+            for (int a = 0; a < A; ++a)
+                if (a != a1 && valid[a] && (a2 < 0 || Q[a] > Q[a2])) a2 = a;
+            double s1 = term_scale(g[a1], P[a1], V[a1]);
+            if (a2 >= 0 && near_tie(Q[a1], Q[a2], s1, term_scale(g[a2], P[a2], V[a2]))) res[i].near_ties++;
+            int chosen = a1;
+            const int32_t* fol = follow ? follow + (size_t)i * cap : NULL;
+            if (fol && fol[kk] >= 0 && fol[kk] != a1) {
+                int fa = fol[kk];
+                if (fa < A && valid[fa] && near_tie(Q[a1], Q[fa], s1, term_scale(g[fa], P[fa], V[fa]))) {
+                    chosen = fa;
+                    res[i].followed_ties++;
+                } else if (res[i].mismatch_step < 0) {
+                    res[i].mismatch_step = kk;
+                }
+            }
+            choice[i] = chosen;
+            nx[3 * i] = nxt[3 * chosen]; nx[3 * i + 1] = nxt[3 * chosen + 1]; nx[3 * i + 2] = nxt[3 * chosen + 2];
+        }
+        /* all of them move together */
+        for (int32_t i = 0; i < n; ++i) {
+            if (choice[i] == -1) continue;
+            const orc_request* r = &reqs[i];
+            if (choice[i] == -2) { done[i] = 1; res[i].verdict = ORC_REJ_NO_ACTION; continue; }
+            const int a = choice[i];
+            if (actions) actions[(size_t)i * cap + k[i]] = a;
+            for (int c = 0; c < 3; ++c) { prev[3 * i + c] = st[3 * i + c]; st[3 * i + c] = nx[3 * i + c]; }
+            h[i] = ((h[i] + o->dh[a]) % 24 + 24) % 24;
+            k[i] += 1;
+            res[i].n_points = k[i] + 1;
+            if (xyz) {
+                float* pt = xyz + ((size_t)i * cap + k[i]) * 3;
+                pt[0] = (float)st[3 * i]; pt[1] = (float)st[3 * i + 1]; pt[2] = (float)st[3 * i + 2];
+            }
+            double step = r->speed * p->dt;
+            double ex = r->gx - st[3 * i], ey = r->gy - st[3 * i + 1], ez = r->gz - st[3 * i + 2];
+            if ((ex * ex + ey * ey + ez * ez) <= step * step) { done[i] = 1; res[i].captured = 1; }
+            else if (k[i] >= r->horizon) { done[i] = 1; res[i].verdict = ORC_REJ_HORIZON; }
+        }
+        ++t;
+    }
+    free(C); free(S); free(st); free(prev); free(h); free(k); free(done); free(choice); free(nx);
+    free(xc); free(xk); free(owner); free(xc_i); free(xk_i);
     return 0;
 }

@@ -107,6 +107,13 @@ int32_t orc_rollout(const orc_t* o, const orc_request* r, const int32_t* follow,
  * of conflicting (point, plan) pairs. */
 int64_t orc_sep_check(const orc_t* o, int64_t t0, const float* xyz, int32_t n, orc_result* res);
 
+/* Co-simulation of n requests on one clock, each seeing the others' Table 3 wells at their
+ * current position and velocity (no admission). follow: optional [n][cap] actions (-1: none)
+ * taken at near-ties as in orc_rollout. Buffers [n][cap][3] / [n][cap] / [n][cap][A] (may be
+ * NULL); res[i].verdict is -1 for a captured request, else HORIZON or NO_ACTION. */
+int32_t orc_cosim(const orc_t* o, const orc_request* reqs, int32_t n, const int32_t* follow, int32_t cap,
+                  float* xyz, int32_t* actions, double* q_trace, double* scale_trace, orc_result* res);
+
 /* FCFS: rollout, separation check, and admission of a conflict-free trajectory. */
 int32_t orc_schedule(orc_t* o, const orc_request* r, int32_t cap, float* xyz, int32_t* actions,
                      orc_result* res);
