@@ -228,7 +228,7 @@ def main():
     ap.add_argument("--no-modes", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="batched mode: skip the launch-shape autotuner")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="arrival window per serving rate")
-    ap.add_argument("--modes", default="sequential,departures,lookahead,learned,batched20k,learned20k,serving",
+    ap.add_argument("--modes", default="sequential,departures,lookahead,cosim,learned,batched20k,learned20k,serving",
                     help="comma-separated extra modes to run")
     ap.add_argument("--time-scale", type=float, default=60.0, help="simulated seconds per wall second (serving)")
     ap.add_argument("--mode", default="batched", choices=["batched", "sequential"],
@@ -358,6 +358,22 @@ def main():
                                "ms_per_step": mdep, "requests_per_step": nd, "delays_s": delays,
                                "admitted": int((ch >= 0).sum()), "delayed": int((ch > 0).sum()),
                                "mode": "each request's 8 departure variants planned in one launch, FCFS"}
+    if "cosim" in want:
+        # batch co-simulation: 128 requests of the workload stepping on one clock, each seeing
+        # the others' wells, then admitted in array order
+        nc = min(n_req, 128)
+
+        def cs_step():
+            s.restore()
+            return s.schedule_cosim(sc.requests[:nc], points=False)
+
+        cs_step()
+        mcs, rcs = timed(stream, cs_step, 1, barrier)
+        mcs = max_over_ranks(mcs)
+        modes["cosim"] = {"known_plans": len(sc.plans), "value": world * nc / (mcs / 1e3), "unit": UNIT,
+                          "ms_per_step": mcs, "requests_per_step": nc,
+                          "admitted": int(sum(r["verdict"] == 0 for r in rcs)),
+                          "mode": "one cooperative launch, one CTA per request, grid barrier per step"}
     if "lookahead" in want:
         # the paper's fidelity: W = 10 sub-steps of 0.1 s, FCFS one request at a time
         sce = S.e1_fine()

@@ -289,6 +289,19 @@ fmdp_status fmdp_schedule_departures(fmdp_ctx* ctx, const fmdp_request* reqs, in
                                      const int64_t* delays, int32_t n_delays, fmdp_result* res,
                                      int32_t* chosen, int32_t* verdicts);
 
+/* Batch co-simulation (the paper's batches whose aircraft see each other, Sec. V, with
+ * Alg. 1 stepping every aircraft of the batch on one clock). The n requests are planned
+ * together from the earliest departure on: at each step every aircraft in flight (departed,
+ * not finished) values its actions against the stored plans, the static peaks and the
+ * Table 3 wells of every other aircraft in flight, centred at that aircraft's position plus
+ * tau times its last move over dt (zero before its first move); then all of them move. The
+ * finished trajectories are then checked and admitted in array order (first come, first
+ * served; each against the table including the members admitted before it). Results differ
+ * from fmdp_schedule_batch, whose requests do not see each other while they plan.
+ *   n: at most the number of CTAs one cooperative launch keeps resident (a few hundred;
+ *   FMDP_ERR_ARG beyond) and at most the free plan slots. Honours options.lookahead_W. */
+fmdp_status fmdp_schedule_cosim(fmdp_ctx* ctx, const fmdp_request* reqs, int32_t n, fmdp_result* res);
+
 /* ---- Autotuner of the batched rollout's launch shape (no counterpart in the paper; the
  * rollout is Alg. 1 whatever the shape, and results are bit-identical across shapes).
  *

@@ -203,6 +203,10 @@ struct fmdp_ctx {
     std::map<std::array<int32_t, 4>, fmdp_tune_entry> tune;
     int32_t try_threads = 0, try_icap = 0;
 
+    // batch co-simulation: per-step aircraft records and the grid barrier words
+    DevArray<double> cs_mem;
+    DevArray<int32_t> cs_bar;
+
     // work buffers
     SeqBuffers seq;     // fmdp_schedule / fmdp_schedule_many
     SeqBuffers stg;     // staged (device-resident) runs
@@ -629,7 +633,7 @@ void recompute_hw(fmdp_ctx* c) {
 // Enqueue rollout -> sep_check -> admission for n requests (device array c->reqs, slots in
 // c->slots) in FCFS order on the context's stream.
 void enqueue_sequence(fmdp_ctx* c, SeqBuffers& B, const fmdp_request* host_reqs, int32_t n, int32_t cap,
-                      const Geometry& g) {
+                      const Geometry& g, bool plan = true) {
     const TableView tv = table_view(c);
     LAUNCH(c, launch_sep_reset(B.sepo.p, n, c->stream));
     for (int32_t i = 0; i < n; ++i) {
@@ -650,7 +654,7 @@ void enqueue_sequence(fmdp_ctx* c, SeqBuffers& B, const fmdp_request* host_reqs,
         ra.err = c->err;
         set_index_args(c, ra, g);
         ra.phase = c->phase_timing ? c->phase.p : nullptr;
-        {
+        if (plan) {
             KernelTimer t(c, 0);
             if (window_of(c) > 1)
                 launch_window_rollout(c, g, ra.reqs, cap, ra.traj, ra.acts, ra.out, false);
@@ -720,7 +724,8 @@ void fill_result(const RolloutOut& ro, const SepOut& so, fmdp_result* res) {
 // Plans n requests (already validated) in FCFS order; results and trajectories to the
 // caller's buffers when res != nullptr. With staged = true the requests already sit in
 // c->stg.reqs on the device and trajectories stay there. Returns the number admitted.
-int32_t run_fcfs(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_result* res, bool staged) {
+int32_t run_fcfs(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_result* res, bool staged,
+                 bool cosim = false) {
     SeqBuffers& B = staged ? c->stg : c->seq;
     const bool keep_on_device = staged;
     int32_t admitted = 0;
@@ -751,7 +756,33 @@ int32_t run_fcfs(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_result* 
             }
             B.slots.ensure(m);
             CK(cudaMemcpyAsync(B.slots.p, sl.data(), m * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
-            enqueue_sequence(c, B, reqs + done, m, cap, g);
+            if (cosim) {  // all m requests fly together first; admission below in array order
+                require(m == n, FMDP_ERR_FULL, "not enough free slots for the co-simulated batch");
+                c->cs_mem.ensure((size_t)2 * n * 8);
+                c->cs_bar.ensure(2);
+                CK(cudaMemsetAsync(c->cs_bar.p, 0, 2 * sizeof(int32_t), c->stream));
+                LookArgs la{};
+                la.m = c->model;
+                la.tab = table_view(c);
+                la.S_scan = g.S_scan;
+                la.W = window_of(c);
+                la.cap = cap;
+                la.n_req = n;
+                la.reqs = B.reqs.p;
+                la.traj = B.traj.p;
+                la.acts = B.acts.p;
+                la.out = B.rout.p;
+                la.err = c->err;
+                la.cosim = 1;
+                la.t_start = reqs[0].depart_step;
+                for (int32_t i = 1; i < n; ++i) la.t_start = std::min(la.t_start, reqs[i].depart_step);
+                la.mem = c->cs_mem.p;
+                la.bar = c->cs_bar.p;
+                KernelTimer t(c, 0);
+                LAUNCH(c, launch_lookahead(la, c->stream));
+                t.stop();
+            }
+            enqueue_sequence(c, B, reqs + done, m, cap, g, !cosim);
             c->h_rout.ensure(m);
             c->h_sep.ensure(m);
             CK(cudaMemcpyAsync(c->h_rout.p, B.rout.p, m * sizeof(RolloutOut), cudaMemcpyDeviceToHost, c->stream));
@@ -2706,6 +2737,19 @@ fmdp_status fmdp_schedule_departures(fmdp_ctx* c, const fmdp_request* reqs, int3
                 check_request(c, v);
             }
         run_departures(c, reqs, n, delays, n_delays, res, chosen, verdicts);
+    });
+}
+
+fmdp_status fmdp_schedule_cosim(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_result* res) {
+    if (!c) return FMDP_ERR_ARG;
+    return guard(c, [&] {
+        require(n >= 0 && (n == 0 || (reqs && res)), FMDP_ERR_ARG, "null requests or results");
+        for (int32_t i = 0; i < n; ++i) check_request(c, reqs[i]);
+        if (n == 0) return;
+        const int32_t fit = lookahead_max_resident(c->A, window_of(c));
+        require(n <= fit, FMDP_ERR_ARG, "co-simulated batch larger than the CTAs one launch keeps resident");
+        require((size_t)n <= c->book.free_slots.size(), FMDP_ERR_FULL, "not enough free slots for the co-simulated batch");
+        run_fcfs(c, reqs, n, res, false, true);
     });
 }
 

@@ -290,8 +290,16 @@ struct LookArgs {
     double* st_trace;
     int32_t* hd_trace;
     uint8_t* tie_trace;
+    int32_t* err;
+    // co-simulation: the n_req CTAs (one cooperative launch) step on one clock from t_start
+    // and see each other's wells; each publishes its state per step in mem
+    int32_t cosim;
+    int64_t t_start;
+    double* mem;   // [2][n_req][8]: x, y, z, vx, vy, vz, flying, alive (by step parity)
+    int32_t* bar;  // [2]: arrivals, generation of the grid barrier (zero before launch)
 };
 size_t lookahead_smem_bytes(int A, int W);
+int lookahead_max_resident(int A, int W);  // CTAs of one cooperative launch that fit
 cudaError_t prepare_lookahead_kernel();
 cudaError_t launch_lookahead(const LookArgs& a, cudaStream_t s);
 

@@ -77,8 +77,37 @@ struct LookState {
     double step, cap2;
     float Gx, Gy, Gz, ds;  // goal - s (fp32) and its length
     float shx, shy, shz, slx, sly, slz;  // s as double-float
+    double prev[3];   // state one step earlier (co-simulation velocity)
     int h, k, done, status, choice, near_ties;
 };
+
+// Grid barrier of a cooperative launch (all CTAs resident), bounded: false when the wait
+// ran past about a second of SM cycles.
+__device__ bool look_grid_sync(int32_t* bar, int n_ctas, int& gen) {
+    __syncthreads();
+    int ok = 1;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const int g = gen;
+        if (atomicAdd(&bar[0], 1) == n_ctas - 1) {
+            atomicExch(&bar[0], 0);
+            __threadfence();
+            atomicExch(&bar[1], g + 1);
+        } else {
+            const long long t0 = clock64();
+            while (atomicAdd(&bar[1], 0) == g) {
+                if (clock64() - t0 > (1ll << 31)) {
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+        gen = g + 1;
+        __threadfence();
+    }
+    return __syncthreads_and(ok) != 0;
+}
 
 __device__ __forceinline__ unsigned long long look_sum_term(float l, float ref) {
     const float t = exp2f(l - ref) * 1099511627776.0f;  // 2^40 fixed point
@@ -98,6 +127,16 @@ __device__ __noinline__ bool look_well_exact(const Model& m, int w, double x, do
     const double cx = __dadd_rn((double)p1x, __dmul_rn(tau, vx));
     const double cy = __dadd_rn((double)p1y, __dmul_rn(tau, vy));
     const double cz = __dadd_rn((double)p1z, __dmul_rn(tau, vz));
+    return norm3_64(__dsub_rn(x, cx), __dsub_rn(y, cy), __dsub_rn(z, cz)) < m.w_R64[w];
+}
+
+// d < R for a well of another aircraft of a co-simulated batch: centre = s_m + tau * v_m.
+__device__ __noinline__ bool look_member_exact(const Model& m, int w, double x, double y, double z, double sx,
+                                               double sy, double sz, double vx, double vy, double vz) {
+    const double tau = m.w_tau64[w];
+    const double cx = __dadd_rn(sx, __dmul_rn(tau, vx));
+    const double cy = __dadd_rn(sy, __dmul_rn(tau, vy));
+    const double cz = __dadd_rn(sz, __dmul_rn(tau, vz));
     return norm3_64(__dsub_rn(x, cx), __dsub_rn(y, cy), __dsub_rn(z, cz)) < m.w_R64[w];
 }
 
@@ -147,6 +186,10 @@ __global__ void __launch_bounds__(kLookThreads) lookahead_kernel(const __grid_co
     const int KEY_NONE = float_key(-INFINITY);
     const float inv_dt = (float)(1.0 / m.dt);
     const int S = a.S_scan;
+    double* q_trace = a.trace ? a.q_trace + (size_t)r * a.cap * A : nullptr;
+    double* st_trace = a.trace ? a.st_trace + (size_t)r * a.cap * 3 : nullptr;
+    int32_t* hd_trace = a.trace ? a.hd_trace + (size_t)r * a.cap : nullptr;
+    uint8_t* tie_trace = a.trace ? a.tie_trace + (size_t)r * a.cap : nullptr;
 
     // ---- prologue: heading table (the bearing turned by k * 15 degrees), climb moves
     if (tid < kHeadings) {
@@ -178,11 +221,14 @@ __global__ void __launch_bounds__(kLookThreads) lookahead_kernel(const __grid_co
         traj[0] = (float)req.ox;
         traj[1] = (float)req.oy;
         traj[2] = (float)req.oz;
+        st->prev[0] = req.ox;
+        st->prev[1] = req.oy;
+        st->prev[2] = req.oz;
         if (a.trace) {
-            a.st_trace[0] = req.ox;
-            a.st_trace[1] = req.oy;
-            a.st_trace[2] = req.oz;
-            a.hd_trace[0] = 0;
+            st_trace[0] = req.ox;
+            st_trace[1] = req.oy;
+            st_trace[2] = req.oz;
+            hd_trace[0] = 0;
         }
         const double ex = __dsub_rn(req.gx, req.ox), ey = __dsub_rn(req.gy, req.oy), ez = __dsub_rn(req.gz, req.oz);
         const bool cap0 = __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez)) <= st->cap2;
@@ -195,7 +241,37 @@ __global__ void __launch_bounds__(kLookThreads) lookahead_kernel(const __grid_co
     for (int q = 0; q < A; ++q) lstep = fmaxf(lstep, fabsf((float)Dz[q]));
     lstep = sqrtf((float)(st->step * st->step) + lstep * lstep) * 1.0001f + 0.01f;
 
-    while (!st->done) {
+    int gen = 0;
+    const int n_mem = a.cosim ? a.n_req : 0;
+    for (int64_t tc = a.cosim ? a.t_start : req.depart_step;; ++tc) {
+        const double* recs = nullptr;  // co-simulation: every aircraft's record of this step
+        if (a.cosim) {
+            double* mine = a.mem + ((size_t)(tc & 1) * n_mem + r) * 8;
+            if (tid == 0) {
+                const bool flying = !st->done && tc >= req.depart_step;
+                for (int c = 0; c < 3; ++c) {
+                    mine[c] = st->s[c];
+                    mine[3 + c] = st->k > 0 ? __ddiv_rn(__dsub_rn(st->s[c], st->prev[c]), m.dt) : 0.0;
+                }
+                mine[6] = flying ? 1.0 : 0.0;
+                mine[7] = st->done ? 0.0 : 1.0;
+            }
+            if (!look_grid_sync(a.bar, a.n_req, gen)) {
+                if (tid == 0) {
+                    atomicExch(a.err, FMDP_ERR_TIMEOUT);
+                    st->done = 1;
+                }
+                __syncthreads();
+                break;
+            }
+            recs = a.mem + (size_t)(tc & 1) * n_mem * 8;
+            int alive = 0;
+            for (int q = tid; q < n_mem; q += kLookThreads) alive |= __ldcg(recs + (size_t)q * 8 + 7) != 0.0;
+            if (!__syncthreads_or(alive)) break;
+            if (st->done || tc < req.depart_step) continue;  // waiting for departure, or finished
+        } else if (st->done) {
+            break;
+        }
         const int k = st->k;
         const int64_t t = req.depart_step + k;
         // ---- 1. projected states (thread per action) and per-step constants
@@ -356,6 +432,72 @@ __global__ void __launch_bounds__(kLookThreads) lookahead_kernel(const __grid_co
                 }
             }
         }
+
+        // ---- 3'. co-simulation: the wells of every other aircraft in flight, at its
+        // position at t plus tau times its last move (the same peaks for every sub-step)
+        if (recs) {
+            const int nmp = W * n_mem;
+            for (int base = warp * 32; base < nmp; base += kLookThreads) {
+                const int idx = base + lane;
+                int j = 0;
+                bool near = false;
+                double msx = 0.0, msy = 0.0, msz = 0.0, mvx = 0.0, mvy = 0.0, mvz = 0.0;
+                if (idx < nmp) {
+                    j = idx / n_mem;
+                    const int mm = idx - j * n_mem;
+                    const double* rc = recs + (size_t)mm * 8;
+                    if (mm != r && __ldcg(rc + 6) != 0.0) {
+                        msx = __ldcg(rc);
+                        msy = __ldcg(rc + 1);
+                        msz = __ldcg(rc + 2);
+                        mvx = __ldcg(rc + 3);
+                        mvy = __ldcg(rc + 4);
+                        mvz = __ldcg(rc + 5);
+                        const float qx = (float)__dsub_rn(msx, st->s[0]), qy = (float)__dsub_rn(msy, st->s[1]),
+                                    qz = (float)__dsub_rn(msz, st->s[2]);
+                        const float vv = sqrtf((float)(mvx * mvx + mvy * mvy + mvz * mvz));
+                        const float reach = (float)(j + 1) * lstep + m.reach_base + m.tau_absmax * vv;
+                        near = qx * qx + qy * qy + qz * qz < reach * reach;
+                    }
+                }
+                unsigned mask = __ballot_sync(kFullMask, near);
+                while (mask) {
+                    const int b = __ffs(mask) - 1;
+                    mask &= mask - 1;
+                    const int jb = __shfl_sync(kFullMask, j, b);
+                    const double bsx = __shfl_sync(kFullMask, msx, b), bsy = __shfl_sync(kFullMask, msy, b),
+                                 bsz = __shfl_sync(kFullMask, msz, b);
+                    const double bvx = __shfl_sync(kFullMask, mvx, b), bvy = __shfl_sync(kFullMask, mvy, b),
+                                 bvz = __shfl_sync(kFullMask, mvz, b);
+                    if (lane < A) {
+                        const int q = lane * W + jb;
+                        const float qx = (float)__dsub_rn(bsx, st->s[0]), qy = (float)__dsub_rn(bsy, st->s[1]),
+                                    qz = (float)__dsub_rn(bsz, st->s[2]);
+                        const float vx = (float)bvx, vy = (float)bvy, vz = (float)bvz;
+                        const float px = ox[q], py = oy[q], pz = oz[q];
+                        float mb = -INFINITY;
+                        unsigned long long sb = 0ull;
+                        for (int w = 0; w < m.n_wells; ++w) {
+                            const float tau = m.w_tau[w];
+                            const float ux = px - fmaf(tau, vx, qx), uy = py - fmaf(tau, vy, qy),
+                                        uz = pz - fmaf(tau, vz, qz);
+                            const float d2 = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
+                            const float R2 = m.w_R2[w];
+                            bool in = d2 < R2;
+                            if (fabsf(d2 - R2) <= m.w_band[w])
+                                in = look_member_exact(m, w, X[q], Y[q], Z[q], bsx, bsy, bsz, bvx, bvy, bvz);
+                            if (in) {
+                                const float l = fmaf(sqrtf(d2), m.w_lg[w], m.w_L[w]);
+                                mb = fmaxf(mb, l);
+                                if (m.combine) sb += look_sum_term(l, m.sum_ref);
+                            }
+                        }
+                        if (mb > -INFINITY) atomicMax(&keys[q], float_key(mb));
+                        if (sb) atomicAdd(&sums[q], sb);
+                    }
+                }
+            }
+        }
         __syncthreads();
 
         // ---- penalty + deck per (action, sub-step), as log2
@@ -447,7 +589,7 @@ __global__ void __launch_bounds__(kLookThreads) lookahead_kernel(const __grid_co
             for (int o = 16; o; o >>= 1) q2 = fmax(q2, __shfl_xor_sync(kFullMask, q2, o));
             const unsigned b2 = __ballot_sync(kFullMask, lane < A && lane != a1 && q == q2 && q2 > -INFINITY);
             const int a2 = b2 ? __ffs(b2) - 1 : -1;
-            if (a.trace && lane < A) a.q_trace[(size_t)k * A + lane] = q;
+            if (a.trace && lane < A) q_trace[(size_t)k * A + lane] = q;
             if (lane == 0) {
                 bool tie = false;
                 if (a1 >= 0 && a2 >= 0) {
@@ -455,13 +597,16 @@ __global__ void __launch_bounds__(kLookThreads) lookahead_kernel(const __grid_co
                     sc = fmax(sc, fmax(Sa[a1], Sa[a2]));
                     tie = __dsub_rn(Qa[a1], Qa[a2]) < kTieRel * sc;
                 }
-                if (a.trace) a.tie_trace[k] = tie ? 1 : 0;
+                if (a.trace) tie_trace[k] = tie ? 1 : 0;
                 st->near_ties += tie ? 1 : 0;
                 if (a1 < 0) {
                     st->status = FMDP_REJ_NO_ACTION;
                     st->done = 1;
                 } else {
                     const int q0 = a1 * W;
+                    st->prev[0] = st->s[0];
+                    st->prev[1] = st->s[1];
+                    st->prev[2] = st->s[2];
                     st->s[0] = X[q0];
                     st->s[1] = Y[q0];
                     st->s[2] = Z[q0];
@@ -475,10 +620,10 @@ __global__ void __launch_bounds__(kLookThreads) lookahead_kernel(const __grid_co
                     traj[3 * np + 1] = (float)st->s[1];
                     traj[3 * np + 2] = (float)st->s[2];
                     if (a.trace) {
-                        a.st_trace[3 * np] = st->s[0];
-                        a.st_trace[3 * np + 1] = st->s[1];
-                        a.st_trace[3 * np + 2] = st->s[2];
-                        a.hd_trace[np] = hn;
+                        st_trace[3 * np] = st->s[0];
+                        st_trace[3 * np + 1] = st->s[1];
+                        st_trace[3 * np + 2] = st->s[2];
+                        hd_trace[np] = hn;
                     }
                     st->k = np;
                     const double ex = __dsub_rn(req.gx, st->s[0]), ey = __dsub_rn(req.gy, st->s[1]),
@@ -510,10 +655,36 @@ cudaError_t prepare_lookahead_kernel() {
                                 (int)look_layout(kMaxActions, kMaxLookahead).total);
 }
 
+int lookahead_max_resident(int A, int W) {
+    int per_sm = 0, dev = 0, n_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lookahead_kernel, kLookThreads,
+                                                      look_layout(A, W).total) != cudaSuccess ||
+        cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return per_sm * n_sm;
+}
+
 cudaError_t launch_lookahead(const LookArgs& a, cudaStream_t s) {
     if (a.n_req <= 0) return cudaSuccess;
-    lookahead_kernel<<<a.n_req, kLookThreads, look_layout(a.m.A, a.W).total, s>>>(a);
-    return cudaGetLastError();
+    if (!a.cosim) {
+        lookahead_kernel<<<a.n_req, kLookThreads, look_layout(a.m.A, a.W).total, s>>>(a);
+        return cudaGetLastError();
+    }
+    // co-simulation: every CTA must be resident at once (they wait for one another)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)a.n_req, 1, 1);
+    cfg.blockDim = dim3(kLookThreads, 1, 1);
+    cfg.dynamicSmemBytes = look_layout(a.m.A, a.W).total;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, lookahead_kernel, a);
 }
 
 }  // namespace fmdp
