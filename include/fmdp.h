@@ -302,6 +302,16 @@ fmdp_status fmdp_schedule_departures(fmdp_ctx* ctx, const fmdp_request* reqs, in
  *   FMDP_ERR_ARG beyond) and at most the free plan slots. Honours options.lookahead_W. */
 fmdp_status fmdp_schedule_cosim(fmdp_ctx* ctx, const fmdp_request* reqs, int32_t n, fmdp_result* res);
 
+/* Failure-detection self-test (no counterpart in the paper). Every wait of the library's
+ * kernels is bounded (about a second of SM cycles) and an expired wait ends the call with
+ * FMDP_ERR_TIMEOUT instead of hanging the device. This call makes one such wait run out on
+ * purpose without a fault: it co-simulates two requests whose grid barrier also waits for
+ * a third aircraft that is never launched, so every CTA's wait expires and the kernel
+ * returns. observed (optional) receives the status that call produced. Returns FMDP_OK
+ * when that status was FMDP_ERR_TIMEOUT and nothing was admitted; the context stays
+ * usable. Takes about one second. */
+fmdp_status fmdp_selftest_wait_timeout(fmdp_ctx* ctx, int32_t* observed);
+
 /* ---- Autotuner of the batched rollout's launch shape (no counterpart in the paper; the
  * rollout is Alg. 1 whatever the shape, and results are bit-identical across shapes).
  *

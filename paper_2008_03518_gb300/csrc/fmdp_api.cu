@@ -677,6 +677,7 @@ void enqueue_sequence(fmdp_ctx* c, SeqBuffers& B, const fmdp_request* host_reqs,
             t.stop();
         }
         AdmitArgs aa{};
+        aa.err = c->err;
         aa.tab = tv;
         aa.cap = cap;
         aa.traj = ra.traj;
@@ -725,7 +726,7 @@ void fill_result(const RolloutOut& ro, const SepOut& so, fmdp_result* res) {
 // caller's buffers when res != nullptr. With staged = true the requests already sit in
 // c->stg.reqs on the device and trajectories stay there. Returns the number admitted.
 int32_t run_fcfs(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_result* res, bool staged,
-                 bool cosim = false) {
+                 bool cosim = false, int32_t absent = 0) {
     SeqBuffers& B = staged ? c->stg : c->seq;
     const bool keep_on_device = staged;
     int32_t admitted = 0;
@@ -778,6 +779,7 @@ int32_t run_fcfs(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_result* 
                 for (int32_t i = 1; i < n; ++i) la.t_start = std::min(la.t_start, reqs[i].depart_step);
                 la.mem = c->cs_mem.p;
                 la.bar = c->cs_bar.p;
+                la.absent = absent;
                 KernelTimer t(c, 0);
                 LAUNCH(c, launch_lookahead(la, c->stream));
                 t.stop();
@@ -901,6 +903,7 @@ void enqueue_wave(fmdp_ctx* c, const Geometry& g, int n_clusters, BatchBuffers& 
     CK(cudaMemcpyAsync(B.ctr.p, B.h_ctr.p, 4 * sizeof(int32_t), cudaMemcpyHostToDevice, s));
     {
         AdmitArgs aa{};
+        aa.err = c->err;
         aa.tab = tv;
         aa.cap = cap;
         aa.traj = B.traj.p;
@@ -1234,6 +1237,7 @@ struct Speculator {
         CK(cudaMemcpyAsync(B.ctr.p, B.h_ctr.p, 4 * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
         if (!store.empty()) {
             AdmitArgs aa{};
+            aa.err = c->err;
             aa.tab = table_view(c);
             aa.cap = B.cap;
             aa.traj = B.traj.p;
@@ -1622,6 +1626,7 @@ void run_departures(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, const int6
                 c->slots.ensure(1);
                 CK(cudaMemcpyAsync(c->slots.p, &slot, sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
                 AdmitArgs aa{};
+                aa.err = c->err;
                 aa.tab = table_view(c);
                 aa.cap = B.cap;
                 aa.traj = B.traj.p + (size_t)pick * B.cap * 3;
@@ -2080,6 +2085,7 @@ void store_plans(fmdp_ctx* c, int32_t n_plans, const int64_t* t0s, const int32_t
         CK(cudaMemcpyAsync(c->counts.p, counts, n_plans * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
         CK(cudaMemcpyAsync(c->slots.p, sl.data(), n_plans * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
         AdmitArgs aa{};
+        aa.err = c->err;
         aa.tab = table_view(c);
         aa.cap = 0;
         aa.traj = c->traj.p;
@@ -2750,6 +2756,40 @@ fmdp_status fmdp_schedule_cosim(fmdp_ctx* c, const fmdp_request* reqs, int32_t n
         require(n <= fit, FMDP_ERR_ARG, "co-simulated batch larger than the CTAs one launch keeps resident");
         require((size_t)n <= c->book.free_slots.size(), FMDP_ERR_FULL, "not enough free slots for the co-simulated batch");
         run_fcfs(c, reqs, n, res, false, true);
+    });
+}
+
+fmdp_status fmdp_selftest_wait_timeout(fmdp_ctx* c, int32_t* observed) {
+    if (!c) return FMDP_ERR_ARG;
+    return guard(c, [&] {
+        // two requests far from everything, co-simulated with a barrier that also waits for
+        // a third aircraft that is never launched: every wait must run out and report
+        fmdp_request r[2] = {};
+        const double cx = 0.5 * (c->air.x0 + c->air.x1), cy = 0.5 * (c->air.y0 + c->air.y1);
+        const double cz = 0.5 * (c->air.z0 + c->air.z1);
+        for (int i = 0; i < 2; ++i) {
+            r[i].req_id = (uint64_t)(i + 1);
+            r[i].ox = cx;
+            r[i].oy = cy + (i ? 1.0 : -1.0);
+            r[i].oz = cz;
+            r[i].gx = cx + 1.0;
+            r[i].gy = r[i].oy;
+            r[i].gz = cz;
+            r[i].speed_mps = 1.0;
+            r[i].depart_step = c->book.t_base;
+            r[i].horizon = 4;
+            check_request(c, r[i]);
+        }
+        const size_t plans_before = c->book.plans.size();
+        int32_t st = FMDP_OK;
+        try {
+            run_fcfs(c, r, 2, nullptr, false, true, 1);
+        } catch (const ApiError& f) {
+            st = f.code;
+        }
+        if (observed) *observed = st;
+        require(st == FMDP_ERR_TIMEOUT, FMDP_ERR_CUDA, "the self-test wait did not report a timeout");
+        require(c->book.plans.size() == plans_before, FMDP_ERR_CUDA, "the self-test admitted a plan");
     });
 }
 

@@ -154,6 +154,7 @@ struct AdmitArgs {
     const int64_t* offs;   // force mode: per plan offset into traj (points)
     const int32_t* idx;    // request index of work item y (nullptr: identity)
     const int32_t* n_dev;  // number of work items on the device (nullptr: all launched)
+    const int32_t* err;    // device error word: nothing is stored once a wait has expired
 };
 
 // Speculative batching: could request j's trajectory (as a stored plan) change request k's
@@ -297,6 +298,7 @@ struct LookArgs {
     int64_t t_start;
     double* mem;   // [2][n_req][8]: x, y, z, vx, vy, vz, flying, alive (by step parity)
     int32_t* bar;  // [2]: arrivals, generation of the grid barrier (zero before launch)
+    int32_t absent;  // self-test only: arrivals the barrier waits for that never come
 };
 size_t lookahead_smem_bytes(int A, int W);
 int lookahead_max_resident(int A, int W);  // CTAs of one cooperative launch that fit

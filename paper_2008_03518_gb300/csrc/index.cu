@@ -11,6 +11,8 @@
 // grows past a limit is rebuilt.
 #include <climits>
 
+#include <mutex>
+
 #include "fmdp_internal.cuh"
 
 namespace fmdp {
@@ -179,8 +181,18 @@ __global__ void index_append_kernel(const __grid_constant__ IndexAppendArgs a) {
 
 size_t index_build_smem(int ncell) { return (size_t)(ncell + 1 + 32) * sizeof(int); }
 
+// The attribute belongs to the kernel, not to a context: every scheduler of the process
+// shares it, so it only ever grows (a later scheduler with a smaller grid must not shrink
+// what an earlier one launches with).
 cudaError_t prepare_index_kernels(size_t smem) {
-    return cudaFuncSetAttribute(index_build_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    static std::mutex mu;
+    static size_t granted = 0;
+    std::lock_guard<std::mutex> lock(mu);
+    if (smem <= granted) return cudaSuccess;
+    const cudaError_t e =
+        cudaFuncSetAttribute(index_build_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) granted = smem;
+    return e;
 }
 
 cudaError_t launch_index_build(const IndexArgs& a, int64_t T0, int32_t n, int dirty_only, size_t smem,

@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(kLookThreads) lookahead_kernel(const __grid_co
                 mine[6] = flying ? 1.0 : 0.0;
                 mine[7] = st->done ? 0.0 : 1.0;
             }
-            if (!look_grid_sync(a.bar, a.n_req, gen)) {
+            if (!look_grid_sync(a.bar, a.n_req + a.absent, gen)) {
                 if (tid == 0) {
                     atomicExch(a.err, FMDP_ERR_TIMEOUT);
                     st->done = 1;

@@ -161,6 +161,7 @@ __global__ void sep_reset_kernel(SepOut* out, int n) {
 // slot column. In force mode, known plans are stored unconditionally.
 __global__ void admit_kernel(const __grid_constant__ AdmitArgs a) {
     if (a.n_dev && (int)blockIdx.y >= *a.n_dev) return;
+    if (a.err && *(volatile const int32_t*)a.err != 0) return;  // a call whose wait expired stores nothing
     const int r = a.idx ? a.idx[blockIdx.y] : (int)blockIdx.y;
     const int slot = a.slots[r];  // per request (index mode) or per work item (pointer-offset mode)
     int n;

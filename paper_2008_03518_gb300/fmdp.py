@@ -142,7 +142,7 @@ EXPORTS = ("fmdp_options_default", "fmdp_create", "fmdp_destroy", "fmdp_last_err
            "fmdp_learned_set_params", "fmdp_learned_get_params", "fmdp_learned_train", "fmdp_learned_loss_grad",
            "fmdp_learned_evaluate", "fmdp_schedule_learned",
            "fmdp_autotune", "fmdp_tune_cache_get", "fmdp_tune_cache_put", "fmdp_schedule_departures",
-           "fmdp_schedule_cosim",
+           "fmdp_schedule_cosim", "fmdp_selftest_wait_timeout",
            "fmdp_get_plan", "fmdp_expire", "fmdp_snapshot", "fmdp_restore", "fmdp_clear", "fmdp_rollout_trace",
            "fmdp_sep_check", "fmdp_sep_check_noalloc", "fmdp_set_profiling", "fmdp_get_stats")
 
@@ -195,6 +195,7 @@ def load(build_if_missing: bool = True):
     L.fmdp_schedule_learned.argtypes = [vp, P(Request), c.c_int32, c.c_double, P(Result), P(LearnedReport)]
     L.fmdp_autotune.argtypes = [vp, P(Request), c.c_int32, c.c_int32, P(TuneReport)]
     L.fmdp_schedule_cosim.argtypes = [vp, P(Request), c.c_int32, P(Result)]
+    L.fmdp_selftest_wait_timeout.argtypes = [vp, P(c.c_int32)]
     L.fmdp_schedule_departures.argtypes = [vp, P(Request), c.c_int32, P(c.c_int64), c.c_int32, P(Result),
                                            P(c.c_int32), P(c.c_int32)]
     L.fmdp_tune_cache_get.argtypes = [vp, P(TuneEntry), c.c_int32, P(c.c_int32)]
@@ -523,6 +524,12 @@ class Scheduler:
                                                   _ptr(acc, ctypes.c_int32), _ptr(sp, ctypes.c_int32),
                                                   _ptr(sf, ctypes.c_int32)))
         return {k: getattr(rep, k) for k, _ in LearnedReport._fields_}, acc[:n], sp[:n], sf[:n]
+
+    def selftest_wait_timeout(self):
+        """Makes one bounded device wait run out on purpose; returns the status observed."""
+        st = ctypes.c_int32(0)
+        self._check(self._L.fmdp_selftest_wait_timeout(self._h, ctypes.byref(st)))
+        return st.value
 
     def schedule_cosim(self, reqs, points=True):
         """The batch co-simulated on one clock (each request sees the others' wells), then

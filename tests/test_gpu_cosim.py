@@ -74,3 +74,16 @@ def test_batch_too_large_for_one_launch_is_refused():
             s.schedule_cosim(many)
         assert e.value.status == -1
         assert len(s.query_plans(-(1 << 40), 1 << 40)) == len(sc.plans)
+
+
+def test_a_wait_that_runs_out_reports_a_timeout_and_the_context_survives():
+    """Failure detection without a fault: a grid barrier that waits for an aircraft that is
+    never launched expires (bounded wait), the call reports FMDP_ERR_TIMEOUT, and the same
+    context then plans normally."""
+    sc = S.crowded_batch(seed=141, n_requests=6)
+    with Scheduler.from_scenario(sc) as s:
+        assert s.selftest_wait_timeout() == -4
+        got = s.schedule_cosim(sc.requests)
+        assert all(g["n_points"] >= 1 for g in got)
+        alone = s.schedule(sc.requests[0])
+        assert alone["n_points"] >= 1

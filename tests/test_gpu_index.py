@@ -145,3 +145,17 @@ def test_fast_plans_in_the_extra_list_against_the_oracle():
     with Scheduler.from_scenario(sc, index_vmax_mps=25.0) as s:
         o = Oracle.from_scenario(sc)
         fcfs_parity(s, o, sc.requests, trace_q=True)
+
+
+def test_a_later_scheduler_with_a_smaller_index_leaves_the_earlier_one_working():
+    """Kernel attributes are shared by every scheduler of a process: creating one with a
+    smaller index grid must not shrink the shared memory the earlier one launches with."""
+    big = S.c2_plain_scale(n_plans=300, n_requests=4)
+    with Scheduler.from_scenario(big) as s1:
+        s1.snapshot()
+        small = S.c1_plain_small()
+        with Scheduler.from_scenario(small) as s2:
+            s2.schedule(small.requests[0])
+        s1.restore()  # rebuilds every index row of the larger grid
+        res = s1.schedule_many(big.requests[:2])
+    assert len(res) == 2
