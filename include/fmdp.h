@@ -323,7 +323,8 @@ fmdp_status fmdp_selftest_wait_timeout(fmdp_ctx* ctx, int32_t* observed);
  * multiprocessors; more scanners shorten each step, which is what a small wave (the
  * re-plans of a speculative batch) needs. fmdp_autotune times the rollouts of the first W
  * sample requests (nothing is admitted) under every candidate shape, threads per CTA in
- * {128, 192, 256, 320, 384} x staged samples in {512, 1024, 1536, 2048}, for W = min(n,
+ * {128, 192, 256, 320, 384} x staged samples in {512, 1024, 1536, 2048} (those whose
+ * staging buffers fit in shared memory), for W = min(n,
  * batch size) and its halvings down to 8, and caches the fastest shape under the key
  * (n_actions, combine, plan-count bucket, wave-size bucket). Each wave of a batched call
  * (fmdp_schedule_batch, fmdp_serve, fmdp_schedule_learned, staged batches) then launches

@@ -164,7 +164,7 @@ struct StepState {
     int steps;
     int ent_valid[kRingDepth];
     int abort_flag[2];  // staging of step k timed out (indexed by k & 1)
-    int last_best;      // action chosen in the previous step (99: none)
+    int last_best[2];   // action chosen at step k (99: none), by k & 1
 };
 
 // Shared-memory carve-up (identical on host and device).
@@ -223,8 +223,8 @@ __host__ __device__ inline Layout make_layout(int chunk, int depth, int icap) {
     L.stat = o;  // static-well centres as double-float: hi[64][3], lo[64][3]
     o += 2 * kMaxStatic * 3 * sizeof(float);
     al(16);
-    L.aux = o;   // valid, Delta, deck, key, class, log2|Q|, log2 scale: [7][32] words
-    o += 7 * kMaxActions * sizeof(int);
+    L.aux = o;   // valid, Delta, deck, goal term; key, class, log2|Q|, log2 scale by step parity
+    o += 12 * kMaxActions * sizeof(int);
     L.misc = o;  // work-queue slot of the persistent batch mode
     o += 16;
     L.total = (o + 127) & ~size_t(127);
@@ -360,10 +360,15 @@ __device__ __noinline__ bool near_tie(int c1, int c2, float la1, float la2, floa
 }
 
 // Near-tie flag of the previous step from the keys the control warp stored (warp-wide call).
-__device__ __forceinline__ void deferred_tie(StepState* st, const uint32_t* qkey_s, const int* cls_s,
-                                             const float* la_s, const float* lt_s, int lane, uint8_t* trace_slot) {
-    const int b = st->last_best;
+__device__ __forceinline__ void deferred_tie(StepState* st, const uint32_t* qkey_b, const int* cls_b,
+                                             const float* la_b, const float* lt_b, int par, int lane,
+                                             uint8_t* trace_slot) {
+    const int b = st->last_best[par];
     if (b >= 99) return;
+    const uint32_t* qkey_s = qkey_b + par * kMaxActions;
+    const int* cls_s = cls_b + par * kMaxActions;
+    const float* la_s = la_b + par * kMaxActions;
+    const float* lt_s = lt_b + par * kMaxActions;
     const uint32_t qk = qkey_s[lane];
     const uint32_t k2nd = __reduce_max_sync(kFull, lane == b ? 0u : qk);
     const unsigned sm2 = __ballot_sync(kFull, qk == k2nd && k2nd != 0u && lane != b);
@@ -458,10 +463,12 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
     int* valid_s = reinterpret_cast<int*>(smem + L.aux);
     float* Dl_s = reinterpret_cast<float*>(valid_s + kMaxActions);
     float* Vd_s = Dl_s + kMaxActions;
-    uint32_t* qkey_s = reinterpret_cast<uint32_t*>(Vd_s + kMaxActions);
-    int* cls_s = reinterpret_cast<int*>(qkey_s + kMaxActions);
-    float* la_s = reinterpret_cast<float*>(cls_s + kMaxActions);
-    float* lt_s = la_s + kMaxActions;
+    float* gh_s = Vd_s + kMaxActions;  // goal term at the successor over 2^n0
+    // keys of a step for the deferred near-tie flag, [2][32] by step parity
+    uint32_t* qkey_s = reinterpret_cast<uint32_t*>(gh_s + kMaxActions);
+    int* cls_s = reinterpret_cast<int*>(qkey_s + 2 * kMaxActions);
+    float* la_s = reinterpret_cast<float*>(cls_s + 2 * kMaxActions);
+    float* lt_s = la_s + 2 * kMaxActions;
 
     const bool lead = (rank == 0);
     float* traj = a.traj + (size_t)r * a.cap * 3;
@@ -530,7 +537,7 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
         st->near_ties = 0;
         st->steps = 0;
         st->abort_flag[0] = st->abort_flag[1] = 0;
-        st->last_best = 99;
+        st->last_best[0] = st->last_best[1] = 99;
         for (int e = 0; e < kRingDepth; ++e) st->ent_valid[e] = 0;
         if (lead) {
             traj[0] = (float)req.ox; traj[1] = (float)req.oy; traj[2] = (float)req.oz;
@@ -584,10 +591,10 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
     };
     // ---- indexed mode: the producer warp (warp 2) keeps a software pipeline over the spatial
     // index. At step k (state s_k known) it reads the cell starts of the query for step k + 2
-    // (one cell row per lane), copies those items into a staging buffer, and waits for the
-    // items of step k + 1, copied one step earlier. It runs beside the step rather than in
-    // it: the other warps' reduction barrier leaves it out, and it joins them at the start
-    // of the next step. The query for step j, made from state s_a (a <= j - 1), covers every
+    // (one cell row per lane; prefetched into L2 one step earlier), copies those items into a
+    // staging buffer, and waits for the items of step k + 1, copied one step earlier. It runs
+    // beside the step rather than in it: the other warps' reduction barrier leaves it out,
+    // and it joins them at the start of the next step. The query for step j, made from state s_a (a <= j - 1), covers every
     // cell within Rq + (j - 1 - a) * step of s_a horizontally: an item whose wells can reach a
     // successor of s_j lies within reach0 + tau_max * vmax of s_j (items outside the extra
     // list move no faster than vmax), and s_j lies within (j - a) steps of s_a.
@@ -667,12 +674,11 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
         q.whole = q.nrows > kMaxRanges - 1;
         return q;
     };
-    // prologue form: read the cell starts directly
-    auto issue_direct = [&](int b, int64_t T, float sx, float sy, float R) {
+    // read the cell starts of step T's query (ring row `row` = T mod T_win) and issue it
+    auto issue_direct = [&](int b, int64_t T, int64_t row, float sx, float sy, float R) {
         int my_beg = 0, my_cnt = 0;
         long long row_off = 0;
         if (T >= t_lo && T < t_hi) {
-            const int64_t row = row_of(T);
             const int32_t* cs_row = iv.cstart + row * cst_row_len;
             const Box q = box_of(sx, sy, R);
             int e0 = 0, e1 = 0;
@@ -691,6 +697,27 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
             row_off = (long long)row * a.tab.S_pad * 2;
         }
         issue_items(b, my_beg, my_cnt, row_off);
+    };
+    // L2 prefetch of the cell starts a query of step T would read (issued one step early, so
+    // that the next step's issue finds them in L2 instead of waiting on DRAM)
+    auto prefetch_cells = [&](int64_t T, int64_t row, float sx, float sy, float R) {
+        if (T < t_lo || T >= t_hi) return;
+        const int32_t* cs_row = iv.cstart + row * cst_row_len;
+        const Box q = box_of(sx, sy, R);
+        const int32_t* p0 = nullptr;
+        const int32_t* p1 = nullptr;
+        if (!q.whole && lane < q.nrows) {
+            p0 = cs_row + (q.cy0 + lane) * iv.ncx + q.cx0;
+            p1 = cs_row + (q.cy0 + lane) * iv.ncx + q.cx1 + 1;
+        } else if (q.whole && lane == 0) {
+            p0 = cs_row + q.cy0 * iv.ncx;
+            p1 = cs_row + (q.cy1 + 1) * iv.ncx;
+        } else if (lane == kMaxRanges - 1) {
+            p0 = cs_row + iv.ncell;
+            p1 = iv.nextra + row;
+        }
+        if (p0) asm volatile("prefetch.global.L2 [%0];" ::"l"(p0));
+        if (p1) asm volatile("prefetch.global.L2 [%0];" ::"l"(p1));
     };
     // all outstanding copies, before the buffers are reused or the CTA leaves
     auto drain = [&]() {
@@ -722,12 +749,15 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
     if (indexed && warp == 2 && !st->done) {
         // steps 0 and 1 from the origin
         const float ox = (float)req.ox, oy = (float)req.oy;
-        issue_direct(0, req.depart_step + 1, ox, oy, Rq);
-        issue_direct(1, req.depart_step + 2, ox, oy, Rq);
+        issue_direct(0, req.depart_step + 1, row_of(req.depart_step + 1), ox, oy, Rq);
+        issue_direct(1, req.depart_step + 2, row_of(req.depart_step + 2), ox, oy, Rq);
         const int to = wait_bar(&bars[0], ifill[0], ipend[0]);
         if (lane == 0) st->abort_flag[0] = to;
         stalled = to != 0;
     }
+    // ring row of the query the producer issues at step k (for step k + 2): advanced by one
+    // row per step, so the loop needs no 64-bit modulo
+    int64_t prow = indexed ? row_of(req.depart_step + 3) : 0;
     float ghi[3], glo[3];  // goal as double-float
     {
         const double g0[3] = {req.gx, req.gy, req.gz};
@@ -748,6 +778,7 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
     const float hm_sx = m.hm_sx, hm_sy = m.hm_sy;
     const int n_static = m.n_static, n_wells = m.n_wells, combine = m.combine;
     const float lg32 = m.lg32, sum_ref = m.sum_ref, tau_absmax = m.tau_absmax;
+    const float sum_unit = exp2f(sum_ref - 40.0f);  // value of one unit of the fixed-point sum
     const bool trace0 = a.trace && lead && r == 0;
     if (tid == 0) {
         int n0;
@@ -785,6 +816,8 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
         // registers until the combine publishes the winner's
         bool capn = false;
         double X = 0.0, Y = 0.0, Z = 0.0;
+        float tfx = 0.f, tfy = 0.f, tfz = 0.f;  // the successor as stored (fp32)
+        float sc0 = 0.f;                        // 2^-n0 of the current state
         float nhx = 0.f, nlx = 0.f, nhy = 0.f, nly = 0.f, nhz = 0.f, nlz = 0.f;
         float Gnhx = 0.f, Gnlx = 0.f, Gnhy = 0.f, Gnly = 0.f, Gnhz = 0.f, Gnlz = 0.f;
         int n0n = 0;
@@ -796,6 +829,10 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
                 X = __dadd_rn(st->s[0], Dx[hn]);
                 Y = __dadd_rn(st->s[1], Dy[hn]);
                 Z = __dadd_rn(st->s[2], my_Dz);
+                tfx = (float)X;
+                tfy = (float)Y;
+                tfz = (float)Z;
+                sc0 = exp2f((float)-st->n0);
                 nhx = shx; nlx = slx; df_add(nhx, nlx, dxh[hn], dxl[hn]);
                 nhy = shy; nly = sly; df_add(nhy, nly, dyh[hn], dyl[hn]);
                 nhz = shz; nlz = slz; df_add(nhz, nlz, my_dzh, my_dzl);
@@ -810,9 +847,9 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
             }
             if (timing && tid == 0) { const long long t = clock64(); ph[1] += t - tp; tp = t; }
         } else if (warp == 1) {
-            // evaluator warp: near-tie flag of the previous step (diagnostic, off the critical
-            // path), then the per-action terms that do not involve other plans
-            if (k > 0) deferred_tie(st, qkey_s, cls_s, la_s, lt_s, lane, trace0 ? a.tie_trace + (k - 1) : nullptr);
+            // evaluator warp: the per-action terms that do not involve other plans, and the
+            // goal term over 2^n0 for the combine (its near-tie flag of the previous step
+            // comes after the reduction barrier)
             if (lane < A) {
                 // successor estimate (fp32); terrain loads first, they are the longest wait
                 const float sx = shx + (slx + dxa), sy = shy + (sly + dya), sz = shz + (slz + dza);
@@ -859,6 +896,7 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
                 valid_s[lane] = valid ? 1 : 0;
                 Dl_s[lane] = Dl;
                 Vd_s[lane] = Vd;
+                gh_s[lane] = has_goal ? exp2f(st->phi + Dl * lg32) : 0.f;  // g / 2^n0
                 // static negative peaks (restricted volumes / terrain wells), CTA 0 only
                 if (lead && n_static > 0)
                     fold_statics(m, st, sch, scl, shx, shy, shz, slx, sly, slz, dxa, dya, dza, Dx[hn], Dy[hn], my_Dz,
@@ -868,7 +906,9 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
             // ---- indexed mode: the pipeline (items for k + 2, wait for k + 1)
             int to = 1;
             if (!stalled) {
-                issue_direct((k + 2) % kIBufs, req.depart_step + k + 3, shx + slx, shy + sly, Rq + stepf);
+                issue_direct((k + 2) % kIBufs, req.depart_step + k + 3, prow, shx + slx, shy + sly, Rq + stepf);
+                prow = prow + 1 == a.tab.T_win ? 0 : prow + 1;  // ring row of the next step's query
+                prefetch_cells(req.depart_step + k + 4, prow, shx + slx, shy + sly, Rq + 2.f * stepf);
                 const int b1 = (k + 1) % kIBufs;
                 to = wait_bar(&bars[b1], ifill[b1], ipend[b1]);
                 if (to) stalled = true;
@@ -1096,18 +1136,21 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
             float Lp;
             if (combine) Lp = ssum ? __log2f((float)ssum) + (sum_ref - 40.0f) : -INFINITY;
             else Lp = key_float(key);
-            const float logN = Vd > 0.f ? __log2f(exp2f(Lp) + Vd) : Lp;  // log2 of N = P + V
-            const float lgh = phi + Dl * lg32;                             // log2(g) - n0
+            const float lgh = phi + Dl * lg32;  // log2(g) - n0
+            // penalty + deck N, linear; the goal term g / 2^n0 comes from the evaluator
+            const bool pen = (combine ? ssum != 0ull : Lp > -INFINITY) || Vd > 0.f;
+            float Nl = 0.f;
+            if (pen) Nl = (combine ? (float)ssum * sum_unit : (Lp > -INFINITY ? exp2f(Lp) : 0.f)) + Vd;
             int cls;   // 2: Q > 0, 1: Q = 0, 0: Q < 0
             float k2;  // larger is better within a class
             float la;  // log2 |Q|
-            if (logN == -INFINITY) {
+            if (!pen) {
                 cls = has_goal ? 2 : 1;
                 k2 = has_goal ? lgh : 0.f;
                 la = has_goal ? lgh + (float)n0 : -INFINITY;
             } else {
-                const float gh = has_goal ? exp2f(lgh) : 0.f;
-                const float Nh = exp2f(logN - (float)n0);
+                const float gh = gh_s[lane];
+                const float Nh = Nl * sc0;  // N / 2^n0 (inf when that overflows fp32)
                 const float d = gh - Nh;
                 if (has_goal && d > 0.f) {
                     cls = 2;
@@ -1119,8 +1162,7 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
                     la = -INFINITY;
                 } else {
                     cls = 0;
-                    const float rat = (has_goal && Nh < INFINITY) ? __fdividef(gh, Nh) : 0.f;
-                    la = logN + __log2f(1.f - rat);
+                    la = Nh < INFINITY ? __log2f(-d) + (float)n0 : __log2f(Nl);  // log2 (N - g)
                     k2 = -la;
                 }
             }
@@ -1149,9 +1191,9 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
                 const int np = k + 1;  // one point per step after the origin
                 st->n_points = np + 1;
                 if (lead) {
-                    traj[3 * np] = (float)X;
-                    traj[3 * np + 1] = (float)Y;
-                    traj[3 * np + 2] = (float)Z;
+                    traj[3 * np] = tfx;
+                    traj[3 * np + 1] = tfy;
+                    traj[3 * np + 2] = tfz;
                     acts[k] = (uint8_t)best;
                     if (a.trace && r == 0) {
                         a.st_trace[3 * np] = X;
@@ -1162,15 +1204,21 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
                 }
             }
             // keys of this step for the evaluator warp's deferred near-tie flag
-            qkey_s[lane] = qkey;
-            cls_s[lane] = cls;
-            la_s[lane] = la;
-            lt_s[lane] = fmaxf(has_goal ? lgh + (float)n0 : -INFINITY, logN);  // log2 max(g, N)
-            if (lane == 0) st->last_best = (ab || best >= 99) ? 99 : best;
+            const float logN = pen ? __log2f(Nl) : -INFINITY;
+            qkey_s[par * kMaxActions + lane] = qkey;
+            cls_s[par * kMaxActions + lane] = cls;
+            la_s[par * kMaxActions + lane] = la;
+            lt_s[par * kMaxActions + lane] = fmaxf(has_goal ? lgh + (float)n0 : -INFINITY, logN);  // log2 max(g, N)
+            if (lane == 0) st->last_best[par] = (ab || best >= 99) ? 99 : best;
             if (trace0 && lane < A)  // FP64 action values for the trace (not used for the decision)
                 a.q_trace[(size_t)k * A + lane] = valid ? trace_q(m, has_goal, n0, phi, Dl, Lp, ssum, Vd) : -INFINITY;
             if (timing && tid == 0) ph[3] += clock64() - tp;
-        } else if (producer && !indexed) {
+        } else {
+            // evaluator warp: near-tie flag of the previous step, off the step's critical path
+            if (warp == 1 && k > 0)
+                deferred_tie(st, qkey_s, cls_s, la_s, lt_s, par ^ 1, lane, trace0 ? a.tie_trace + (k - 1) : nullptr);
+        }
+        if (producer && !indexed) {
             // ---- producer: slices needed two or more steps ahead
             const long long t0 = timing ? clock64() : 0;
             int to = 0;
@@ -1188,7 +1236,8 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
     }
 
     // ---- epilogue: near-tie flag of the last step, drain the ring, outputs
-    if (warp == 1 && k > 0) deferred_tie(st, qkey_s, cls_s, la_s, lt_s, lane, trace0 ? a.tie_trace + (k - 1) : nullptr);
+    if (warp == 1 && k > 0)
+        deferred_tie(st, qkey_s, cls_s, la_s, lt_s, (k - 1) & 1, lane, trace0 ? a.tie_trace + (k - 1) : nullptr);
     __syncthreads();
     if (indexed && warp == 2) drain();
     if (producer) {

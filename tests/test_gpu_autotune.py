@@ -60,9 +60,9 @@ def test_autotune_picks_a_candidate_caches_it_and_batches_use_it(crowded):
     with Scheduler.from_scenario(sc, batch_size=16) as s:
         rep = s.autotune(sc.requests)
         ch = rep["chosen"]
-        # waves of 16 and 8 rollouts, every shape
+        # waves of 16 and 8 rollouts, every shape whose staging fits in shared memory
         assert rep["from_cache"] == 0 and rep["entries"] == 2
-        assert rep["candidates"] == 2 * len(THREADS) * len(STAGE)
+        assert 2 * len(THREADS) * (len(STAGE) - 1) <= rep["candidates"] <= 2 * len(THREADS) * len(STAGE)
         assert rep["sample"] == 16
         assert ch["threads_per_cta"] in THREADS and ch["index_stage_items"] in STAGE
         assert 0 < ch["ms"] <= rep["default_ms"]  # the default shape is one of the candidates
