@@ -34,8 +34,7 @@ METRIC = "scheduled plans/s vs known-plan count (plain/batched/learned); p99 lat
 UNIT = "plans/s"
 
 
-def dist_env():
-    return int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
+from paper_2008_03518_gb300.replicas import Replicas, dist_env  # noqa: E402
 
 
 def measured_peaks():
@@ -249,22 +248,14 @@ def main():
 
     import torch
 
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl", device_id=torch.device("cuda", 0))
+    reps = Replicas("nccl")  # one process per GPU; replicas exchange nothing but timings
 
     def barrier():
-        if world > 1:
-            torch.distributed.barrier()
+        reps.barrier()
         torch.cuda.synchronize()
 
     def max_over_ranks(ms):
-        if world > 1:
-            t = torch.tensor([ms], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
+        return reps.max(ms)
 
     from paper_2008_03518_gb300.fmdp import Scheduler
 
@@ -491,8 +482,7 @@ def main():
     if rank == 0:
         print(json.dumps(line), flush=True)
     s.close()
-    if world > 1:
-        torch.distributed.destroy_process_group()
+    reps.close()
 
 
 if __name__ == "__main__":
