@@ -38,7 +38,7 @@ constexpr int kLookThreads = 256;
 constexpr unsigned kFullMask = 0xffffffffu;
 
 struct LookLayout {
-    size_t X, Y, Z, ox, oy, oz, inb, rel, lN, keys, sums, stat, Dx, Dy, Dz, Qa, Sa, misc, total;
+    size_t ox, oy, oz, inb, rel, lN, keys, sums, stat, Dx, Dy, Dz, Dh, Dz2, hna, sg, Lk, Lq, Ls, misc, total;
 };
 
 __host__ __device__ inline LookLayout look_layout(int A, int W) {
@@ -46,25 +46,28 @@ __host__ __device__ inline LookLayout look_layout(int A, int W) {
     const size_t AW = (size_t)A * W;
     size_t o = 0;
     auto al = [&](size_t a) { o = (o + a - 1) & ~(a - 1); };
-    L.X = o; o += AW * 8;
-    L.Y = o; o += AW * 8;
-    L.Z = o; o += AW * 8;
-    L.ox = o; o += AW * 4;
+    L.ox = o; o += AW * 4;    // offsets of the projected states from s (fp32)
     L.oy = o; o += AW * 4;
     L.oz = o; o += AW * 4;
-    L.inb = o; o += AW * 4;
-    L.rel = o; o += AW * 4;   // log2 of goal term at x_j minus log2 of goal term at s
+    L.inb = o; o += AW * 4;   // projected state inside the box
+    L.rel = o; o += AW * 4;   // log2 of the goal term at x_j minus log2 of the goal term at s
     L.lN = o; o += AW * 4;    // log2 of (penalty + deck) at x_j, -inf when zero
     L.keys = o; o += AW * 4;  // float keys of the largest well log-value (MAX)
     al(8);
     L.sums = o; o += AW * 8;  // fixed-point sums of well values (SUM)
     L.stat = o; o += (size_t)kMaxStatic * 3 * 4;  // static-well centres minus s (fp32)
     al(8);
-    L.Dx = o; o += kHeadings * 8;
+    L.Dx = o; o += kHeadings * 8;    // exact moves per heading (FP64)
     L.Dy = o; o += kHeadings * 8;
-    L.Dz = o; o += kMaxActions * 8;
-    L.Qa = o; o += kMaxActions * 8;
-    L.Sa = o; o += kMaxActions * 8;
+    L.Dz = o; o += kMaxActions * 8;  // exact climb per action (FP64)
+    L.Dh = o; o += kHeadings * 4 * 4;     // the moves as double-float: xh, xl, yh, yl per heading
+    L.Dz2 = o; o += kMaxActions * 2 * 4;  // climb as double-float
+    L.hna = o; o += kMaxActions * 4;      // heading index after each action's turn
+    L.sg = o; o += kMaxActions * 4;       // per action: sign class of Q (-1, 0, 1), -2 invalid
+    al(8);
+    L.Lk = o; o += kMaxActions * 8;       // per action: log2 |Q| (FP64, absolute)
+    L.Lq = o; o += kMaxActions * 8;       // per action: log2 of the term scale max(g, N)
+    L.Ls = o; o += kMaxActions * 8;       // per action: argmax key
     L.misc = o; o += 256;
     L.total = (o + 127) & ~size_t(127);
     return L;
@@ -73,12 +76,14 @@ __host__ __device__ inline LookLayout look_layout(int A, int W) {
 // Per-step shared scalars.
 struct LookState {
     double s[3];      // exact state
-    double lgs;       // log2 of the goal term at s
-    double step, cap2;
-    float Gx, Gy, Gz, ds;  // goal - s (fp32) and its length
-    float shx, shy, shz, slx, sly, slz;  // s as double-float
     double prev[3];   // state one step earlier (co-simulation velocity)
-    int h, k, done, status, choice, near_ties;
+    double step, cap2;
+    float shx, shy, shz, slx, sly, slz;  // s as double-float
+    float Ghx, Ghy, Ghz, Glx, Gly, Glz;  // goal - s as double-float
+    float Gx, Gy, Gz, ds, phi;           // goal - s (fp32), its length, log2 g(s) - n0
+    int n0;                              // integer part of log2 of the goal term at s
+    int h, k, done, status, near_ties;
+    int64_t row0;     // ring row of t + 1 for the current step
 };
 
 // Grid barrier of a cooperative launch (all CTAs resident), bounded: false when the wait
@@ -114,9 +119,76 @@ __device__ __forceinline__ unsigned long long look_sum_term(float l, float ref) 
     return (unsigned long long)__float2ull_rn(t);
 }
 
+// ---- double-float (fp32 pair) arithmetic: exact sums of fp32 numbers
+__device__ __forceinline__ void lk_two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void lk_fast_two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    e = __fsub_rn(b, __fsub_rn(s, a));
+}
+__device__ __forceinline__ void lk_df_add(float& hi, float& lo, float dh, float dl) {
+    float s, e;
+    lk_two_sum(hi, dh, s, e);
+    e = __fadd_rn(e, __fadd_rn(lo, dl));
+    lk_fast_two_sum(s, e, hi, lo);
+}
+// log2 of the goal term |r_g| gamma^|G| at a state whose goal vector is the double-float G,
+// split as n0 (integer) + phi (fraction in [0, 1)); also |G| in fp32
+__device__ __forceinline__ void lk_goal_log(const Model& m, float Ghx, float Ghy, float Ghz, float Glx, float Gly,
+                                            float Glz, int& n0, float& phi, float& dsf) {
+    const float lg_hi = (float)m.lg64, lg_lo = (float)(m.lg64 - (double)(float)m.lg64);
+    const float l2r_hi = (float)m.log2rg, l2r_lo = (float)(m.log2rg - (double)(float)m.log2rg);
+    const float p0 = Ghx * Ghx, p1 = Ghy * Ghy, p2 = Ghz * Ghz;
+    const float e0 = fmaf(Ghx, Ghx, -p0), e1 = fmaf(Ghy, Ghy, -p1), e2 = fmaf(Ghz, Ghz, -p2);
+    float s1, t1, s2, t2;
+    lk_two_sum(p0, p1, s1, t1);
+    lk_two_sum(s1, p2, s2, t2);
+    const float lo = t1 + t2 + e0 + e1 + e2 + 2.f * (Ghx * Glx + Ghy * Gly + Ghz * Glz);
+    float Sh, Sl;
+    lk_fast_two_sum(s2, lo, Sh, Sl);
+    const float rt = Sh > 0.f ? sqrtf(Sh) : 0.f;
+    const float rr = fmaf(-rt, rt, Sh);
+    const float rl = rt > 0.f ? (rr + Sl) * (0.5f / rt) : 0.f;
+    const float p = rt * lg_hi;
+    const float pe = fmaf(rt, lg_hi, -p);
+    const float lo2 = pe + rt * lg_lo + rl * lg_hi;
+    float Lh, Le;
+    lk_two_sum(p, l2r_hi, Lh, Le);
+    Le = Le + (lo2 + l2r_lo);
+    float LH, LL;
+    lk_fast_two_sum(Lh, Le, LH, LL);
+    float fl = floorf(LH);
+    float fr = (LH - fl) + LL;
+    if (fr >= 1.f) { fr -= 1.f; fl += 1.f; }
+    if (fr < 0.f) { fr += 1.f; fl -= 1.f; }
+    n0 = (int)fl;
+    phi = fr;
+    dsf = rt;
+}
+
+// The exact FP64 projected state x_(j+1) of a move (Dxa, Dya, Dza) from s: j + 1 rounded
+// additions, as the oracle forms it. Called only where an fp32 decision falls in its band.
+__device__ __noinline__ void look_state_exact(const double* s, double Dxa, double Dya, double Dza, int j, double& x,
+                                              double& y, double& z) {
+    x = s[0];
+    y = s[1];
+    z = s[2];
+    for (int i = 0; i <= j; ++i) {
+        x = __dadd_rn(x, Dxa);
+        y = __dadd_rn(y, Dya);
+        z = __dadd_rn(z, Dza);
+    }
+}
+
 // d < R for a plan well, in FP64 with the oracle's order of operations (no FMA).
-__device__ __noinline__ bool look_well_exact(const Model& m, int w, double x, double y, double z, float p1x, float p1y,
-                                             float p1z, float p2x, float p2y, float p2z, bool has2) {
+__device__ __noinline__ bool look_well_exact(const Model& m, int w, const double* s, double Dxa, double Dya, double Dza,
+                                             int j, float p1x, float p1y, float p1z, float p2x, float p2y, float p2z,
+                                             bool has2) {
+    double x, y, z;
+    look_state_exact(s, Dxa, Dya, Dza, j, x, y, z);
     double vx = 0.0, vy = 0.0, vz = 0.0;
     if (has2) {
         vx = __ddiv_rn(__dsub_rn((double)p2x, (double)p1x), m.dt);
@@ -131,8 +203,11 @@ __device__ __noinline__ bool look_well_exact(const Model& m, int w, double x, do
 }
 
 // d < R for a well of another aircraft of a co-simulated batch: centre = s_m + tau * v_m.
-__device__ __noinline__ bool look_member_exact(const Model& m, int w, double x, double y, double z, double sx,
-                                               double sy, double sz, double vx, double vy, double vz) {
+__device__ __noinline__ bool look_member_exact(const Model& m, int w, const double* s, double Dxa, double Dya,
+                                               double Dza, int j, double sx, double sy, double sz, double vx,
+                                               double vy, double vz) {
+    double x, y, z;
+    look_state_exact(s, Dxa, Dya, Dza, j, x, y, z);
     const double tau = m.w_tau64[w];
     const double cx = __dadd_rn(sx, __dmul_rn(tau, vx));
     const double cy = __dadd_rn(sy, __dmul_rn(tau, vy));
@@ -140,14 +215,64 @@ __device__ __noinline__ bool look_member_exact(const Model& m, int w, double x, 
     return norm3_64(__dsub_rn(x, cx), __dsub_rn(y, cy), __dsub_rn(z, cz)) < m.w_R64[w];
 }
 
-__device__ __noinline__ bool look_static_exact(const Model& m, int w, double x, double y, double z) {
+__device__ __noinline__ bool look_static_exact(const Model& m, int w, const double* s, double Dxa, double Dya,
+                                               double Dza, int j) {
+    double x, y, z;
+    look_state_exact(s, Dxa, Dya, Dza, j, x, y, z);
     const double* c = m.statics + 6 * w;
     return norm3_64(__dsub_rn(x, c[0]), __dsub_rn(y, c[1]), __dsub_rn(z, c[2])) < c[3];
 }
 
-__device__ __noinline__ float look_deck_exact(const Model& m, double x, double y, double z) {
+__device__ __noinline__ float look_deck_exact(const Model& m, const double* s, double Dxa, double Dya, double Dza,
+                                              int j) {
+    double x, y, z;
+    look_state_exact(s, Dxa, Dya, Dza, j, x, y, z);
     const double c = __dsub_rn(z, terrain64(m, x, y));
     return c < m.clearance ? (float)__dsub_rn(m.deck, c) : 0.f;
+}
+
+__device__ __noinline__ bool look_box_exact(const Model& m, const double* s, double Dxa, double Dya, double Dza,
+                                            int j) {
+    double x, y, z;
+    look_state_exact(s, Dxa, Dya, Dza, j, x, y, z);
+    return x >= m.box[0] && x <= m.box[3] && y >= m.box[1] && y <= m.box[4] && z >= m.box[2] && z <= m.box[5];
+}
+
+__device__ __noinline__ bool look_capture_exact(const double* s, const fmdp_request& req, double cap2) {
+    const double ex = __dsub_rn(req.gx, s[0]), ey = __dsub_rn(req.gy, s[1]), ez = __dsub_rn(req.gz, s[2]);
+    return __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez)) <= cap2;
+}
+
+// Monotone 64-bit argmax key of a value held as (sign class, log2 |Q|): valid keys are > 0,
+// Q > 0 above Q = 0 above Q < 0, and within a class ordered by Q (two low bits of log2 |Q|
+// dropped).
+__device__ __forceinline__ unsigned long long look_key(int sg, double L) {
+    unsigned long long u = (unsigned long long)__double_as_longlong(L);
+    u = (u >> 63) ? ~u : (u | 0x8000000000000000ull);  // increasing in L
+    if (sg > 0) return (3ull << 62) | (u >> 2);
+    if (sg == 0) return 2ull << 62;
+    return (1ull << 62) | ((~u) >> 2);  // larger |Q| is a worse negative value
+}
+
+// Near-tie test of the two best actions from their (sign, log2 |Q|) and log2 scales:
+// (Q1 - Q2) < 1e-4 * max(|Q1|, |Q2|, T1, T2), evaluated in the log domain.
+__device__ __noinline__ bool look_near_tie(int s1, double L1, double T1, int s2, double L2, double T2) {
+    double M = fmax(T1, T2);
+    if (s1 != 0) M = fmax(M, L1);
+    if (s2 != 0) M = fmax(M, L2);
+    double gap;  // log2 (Q1 - Q2)
+    if (s1 == s2) {
+        if (s1 == 0) return true;
+        const double hi = s1 > 0 ? L1 : L2, lo = s1 > 0 ? L2 : L1;  // Q1 >= Q2
+        if (hi == lo) return true;
+        gap = hi + (double)log2f(1.f - exp2f((float)(lo - hi)));
+    } else if (s1 > 0 && s2 < 0) {
+        const double hi = fmax(L1, L2), lo = fmin(L1, L2);
+        gap = hi + (double)log2f(1.f + exp2f((float)(lo - hi)));
+    } else {
+        gap = s1 == 0 ? L2 : L1;  // one of them is zero
+    }
+    return gap < M - 13.287712379549449;  // log2(1e-4)
 }
 
 }  // namespace
@@ -159,9 +284,6 @@ __global__ void __launch_bounds__(kLookThreads) lookahead_kernel(const __grid_co
     const Model& m = a.m;
     const int A = m.A, W = a.W, AW = A * W;
     const LookLayout L = look_layout(A, W);
-    double* X = reinterpret_cast<double*>(lsm + L.X);
-    double* Y = reinterpret_cast<double*>(lsm + L.Y);
-    double* Z = reinterpret_cast<double*>(lsm + L.Z);
     float* ox = reinterpret_cast<float*>(lsm + L.ox);
     float* oy = reinterpret_cast<float*>(lsm + L.oy);
     float* oz = reinterpret_cast<float*>(lsm + L.oz);
@@ -174,8 +296,13 @@ __global__ void __launch_bounds__(kLookThreads) lookahead_kernel(const __grid_co
     double* Dx = reinterpret_cast<double*>(lsm + L.Dx);
     double* Dy = reinterpret_cast<double*>(lsm + L.Dy);
     double* Dz = reinterpret_cast<double*>(lsm + L.Dz);
-    double* Qa = reinterpret_cast<double*>(lsm + L.Qa);
-    double* Sa = reinterpret_cast<double*>(lsm + L.Sa);
+    float* Dh = reinterpret_cast<float*>(lsm + L.Dh);    // [24][4]: xh, xl, yh, yl
+    float* Dz2 = reinterpret_cast<float*>(lsm + L.Dz2);  // [32][2]: zh, zl
+    int* hna = reinterpret_cast<int*>(lsm + L.hna);
+    int* sga = reinterpret_cast<int*>(lsm + L.sg);
+    double* Lka = reinterpret_cast<double*>(lsm + L.Lk);
+    double* Lqa = reinterpret_cast<double*>(lsm + L.Lq);
+    unsigned long long* Ksa = reinterpret_cast<unsigned long long*>(lsm + L.Ls);
     LookState* st = reinterpret_cast<LookState*>(lsm + L.misc);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int r = blockIdx.x;
@@ -190,6 +317,10 @@ __global__ void __launch_bounds__(kLookThreads) lookahead_kernel(const __grid_co
     double* st_trace = a.trace ? a.st_trace + (size_t)r * a.cap * 3 : nullptr;
     int32_t* hd_trace = a.trace ? a.hd_trace + (size_t)r * a.cap : nullptr;
     uint8_t* tie_trace = a.trace ? a.tie_trace + (size_t)r * a.cap : nullptr;
+    const float box0 = (float)m.box[0], box1 = (float)m.box[1], box2 = (float)m.box[2];
+    const float box3 = (float)m.box[3], box4 = (float)m.box[4], box5 = (float)m.box[5];
+    constexpr float kBoxBandL = 0.01f;  // metres from a box face: decided in FP64
+    constexpr float kCapBandL = 0.5f;   // metres around the capture radius: decided in FP64
 
     // ---- prologue: heading table (the bearing turned by k * 15 degrees), climb moves
     if (tid < kHeadings) {
@@ -205,10 +336,22 @@ __global__ void __launch_bounds__(kLookThreads) lookahead_kernel(const __grid_co
         const double C = __dsub_rn(__dmul_rn(c0, ck), __dmul_rn(s0, sk));
         const double Sn = __dadd_rn(__dmul_rn(s0, ck), __dmul_rn(c0, sk));
         const double step = __dmul_rn(req.speed_mps, m.dt);
-        Dx[tid] = __dmul_rn(step, C);
-        Dy[tid] = __dmul_rn(step, Sn);
+        const double X = __dmul_rn(step, C), Y = __dmul_rn(step, Sn);
+        Dx[tid] = X;
+        Dy[tid] = Y;
+        const float xh = (float)X, yh = (float)Y;
+        Dh[4 * tid] = xh;
+        Dh[4 * tid + 1] = (float)__dsub_rn(X, (double)xh);
+        Dh[4 * tid + 2] = yh;
+        Dh[4 * tid + 3] = (float)__dsub_rn(Y, (double)yh);
     }
-    if (tid < kMaxActions) Dz[tid] = tid < A ? __dmul_rn(m.climb[tid], m.dt) : 0.0;
+    if (tid < kMaxActions) {
+        const double dz = tid < A ? __dmul_rn(m.climb[tid], m.dt) : 0.0;
+        Dz[tid] = dz;
+        const float zh = (float)dz;
+        Dz2[2 * tid] = zh;
+        Dz2[2 * tid + 1] = (float)__dsub_rn(dz, (double)zh);
+    }
     if (tid == 0) {
         st->s[0] = req.ox;
         st->s[1] = req.oy;
@@ -224,6 +367,20 @@ __global__ void __launch_bounds__(kLookThreads) lookahead_kernel(const __grid_co
         st->prev[0] = req.ox;
         st->prev[1] = req.oy;
         st->prev[2] = req.oz;
+        const double s0[3] = {req.ox, req.oy, req.oz}, g0[3] = {req.gx, req.gy, req.gz};
+        float* sh = &st->shx;
+        float* sl = &st->slx;
+        float* gh = &st->Ghx;
+        float* gl = &st->Glx;
+        for (int c = 0; c < 3; ++c) {
+            sh[c] = (float)s0[c];
+            sl[c] = (float)__dsub_rn(s0[c], (double)sh[c]);
+            const double G = __dsub_rn(g0[c], s0[c]);
+            gh[c] = (float)G;
+            gl[c] = (float)__dsub_rn(G, (double)gh[c]);
+        }
+        int64_t row = (req.depart_step + 1) % a.tab.T_win;
+        st->row0 = row < 0 ? row + a.tab.T_win : row;
         if (a.trace) {
             st_trace[0] = req.ox;
             st_trace[1] = req.oy;
@@ -238,8 +395,9 @@ __global__ void __launch_bounds__(kLookThreads) lookahead_kernel(const __grid_co
     __syncthreads();
     // largest horizontal + vertical move of one sub-step (culling bound)
     float lstep = 0.f;
-    for (int q = 0; q < A; ++q) lstep = fmaxf(lstep, fabsf((float)Dz[q]));
-    lstep = sqrtf((float)(st->step * st->step) + lstep * lstep) * 1.0001f + 0.01f;
+    for (int q = 0; q < A; ++q) lstep = fmaxf(lstep, fabsf(Dz2[2 * q]));
+    const float stepf = (float)st->step;
+    lstep = sqrtf(stepf * stepf + lstep * lstep) * 1.0001f + 0.01f;
 
     int gen = 0;
     const int n_mem = a.cosim ? a.n_req : 0;
@@ -274,41 +432,23 @@ __global__ void __launch_bounds__(kLookThreads) lookahead_kernel(const __grid_co
         }
         const int k = st->k;
         const int64_t t = req.depart_step + k;
-        // ---- 1. projected states (thread per action) and per-step constants
+        const int64_t row0 = st->row0;  // ring row of t + 1
+        // ---- 1. per step: the goal term at s, static-well offsets, each action's heading
         if (tid < A) {
             int hn = st->h + m.dh[tid];
             hn += hn < 0 ? 24 : 0;
             hn -= hn >= 24 ? 24 : 0;
-            double x = st->s[0], y = st->s[1], z = st->s[2];
-            for (int j = 0; j < W; ++j) {
-                x = __dadd_rn(x, Dx[hn]);
-                y = __dadd_rn(y, Dy[hn]);
-                z = __dadd_rn(z, Dz[tid]);
-                const int q = tid * W + j;
-                X[q] = x;
-                Y[q] = y;
-                Z[q] = z;
-                ox[q] = (float)__dsub_rn(x, st->s[0]);
-                oy[q] = (float)__dsub_rn(y, st->s[1]);
-                oz[q] = (float)__dsub_rn(z, st->s[2]);
-                inb[q] = x >= m.box[0] && x <= m.box[3] && y >= m.box[1] && y <= m.box[4] && z >= m.box[2] &&
-                         z <= m.box[5];
-            }
+            hna[tid] = hn;
         } else if (tid == 64) {
-            const double Gx = __dsub_rn(req.gx, st->s[0]), Gy = __dsub_rn(req.gy, st->s[1]),
-                         Gz = __dsub_rn(req.gz, st->s[2]);
-            const double ds = norm3_64(Gx, Gy, Gz);
-            st->lgs = __dadd_rn(m.log2rg, __dmul_rn(ds, m.lg64));
-            st->Gx = (float)Gx;
-            st->Gy = (float)Gy;
-            st->Gz = (float)Gz;
-            st->ds = (float)ds;
-            st->shx = (float)st->s[0];
-            st->shy = (float)st->s[1];
-            st->shz = (float)st->s[2];
-            st->slx = (float)__dsub_rn(st->s[0], (double)st->shx);
-            st->sly = (float)__dsub_rn(st->s[1], (double)st->shy);
-            st->slz = (float)__dsub_rn(st->s[2], (double)st->shz);
+            int n0;
+            float phi, dsf;
+            lk_goal_log(m, st->Ghx, st->Ghy, st->Ghz, st->Glx, st->Gly, st->Glz, n0, phi, dsf);
+            st->n0 = n0;
+            st->phi = phi;
+            st->ds = dsf;
+            st->Gx = st->Ghx + st->Glx;
+            st->Gy = st->Ghy + st->Gly;
+            st->Gz = st->Ghz + st->Glz;
         } else if (tid >= 96 && tid - 96 < m.n_static) {
             const int w = tid - 96;
             const double* c = m.statics + 6 * w;
@@ -323,37 +463,54 @@ __global__ void __launch_bounds__(kLookThreads) lookahead_kernel(const __grid_co
         __syncthreads();
         const float shx = st->shx, shy = st->shy, shz = st->shz, slx = st->slx, sly = st->sly, slz = st->slz;
 
-        // ---- 2. goal term offsets and static wells per (action, sub-step)
+        // ---- 2. projected states (fp32 offsets (j + 1) * move), box test, goal-term offset,
+        // static wells, per (action, sub-step)
         for (int q = tid; q < AW; q += kLookThreads) {
-            const float px = ox[q], py = oy[q], pz = oz[q];
+            const int ac = q / W, j = q - ac * W;
+            const int hn = hna[ac];
+            const float fj = (float)(j + 1);
+            const float px = fmaf(fj, Dh[4 * hn], fj * Dh[4 * hn + 1]);
+            const float py = fmaf(fj, Dh[4 * hn + 2], fj * Dh[4 * hn + 3]);
+            const float pz = fmaf(fj, Dz2[2 * ac], fj * Dz2[2 * ac + 1]);
+            ox[q] = px;
+            oy[q] = py;
+            oz[q] = pz;
+            const float sx = shx + (slx + px), sy = shy + (sly + py), sz = shz + (slz + pz);
+            const float mb = fminf(fminf(fminf(sx - box0, sy - box1), sz - box2), fminf(fminf(box3 - sx, box4 - sy), box5 - sz));
+            int in;
+            if (mb > kBoxBandL) in = 1;
+            else if (mb < -kBoxBandL) in = 0;
+            else in = look_box_exact(m, st->s, Dx[hn], Dy[hn], Dz[ac], j) ? 1 : 0;
+            inb[q] = in;
             const float ex = st->Gx - px, ey = st->Gy - py, ez = st->Gz - pz;
             const float d = sqrtf(fmaf(ex, ex, fmaf(ey, ey, ez * ez)));
-            const float num = fmaf(px, px, fmaf(py, py, pz * pz)) -
-                              2.f * fmaf(st->Gx, px, fmaf(st->Gy, py, st->Gz * pz));
+            const float num = fmaf(px, px, fmaf(py, py, pz * pz)) - 2.f * fmaf(st->Gx, px, fmaf(st->Gy, py, st->Gz * pz));
             const float den = d + st->ds;
             const float dd = den > 0.f ? num / den : 0.f;  // d(x_j) - d(s)
             rel[q] = dd * m.lg32;
             // static negative peaks (restricted volumes / terrain wells)
-            float mb = -INFINITY;
+            float mbw = -INFINITY;
             unsigned long long sb = 0ull;
             for (int w = 0; w < m.n_static; ++w) {
                 const float ux = px - stc[3 * w], uy = py - stc[3 * w + 1], uz = pz - stc[3 * w + 2];
                 const float d2 = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
                 const float R2 = m.st_R2[w];
-                bool in = d2 < R2;
-                if (fabsf(d2 - R2) <= m.st_band[w]) in = look_static_exact(m, w, X[q], Y[q], Z[q]);
-                if (in) {
+                bool inw = d2 < R2;
+                if (fabsf(d2 - R2) <= m.st_band[w]) inw = look_static_exact(m, w, st->s, Dx[hn], Dy[hn], Dz[ac], j);
+                if (inw) {
                     const float l = fmaf(sqrtf(d2), m.st_lg[w], m.st_L[w]);
-                    mb = fmaxf(mb, l);
+                    mbw = fmaxf(mbw, l);
                     if (m.combine) sb += look_sum_term(l, m.sum_ref);
                 }
             }
-            if (mb > -INFINITY) atomicMax(&keys[q], float_key(mb));
+            if (mbw > -INFINITY) atomicMax(&keys[q], float_key(mbw));
             if (sb) atomicAdd(&sums[q], sb);
         }
+        __syncthreads();
 
         // ---- 3. plan wells: every (sub-step, slot) pair, warp-cooperative scoring
         const int npairs = W * S;
+        const int64_t t_hi = a.tab.t_base + a.tab.T_win;
         for (int base = warp * 32; base < npairs; base += kLookThreads) {
             const int idx = base + lane;
             int j = 0, i = 0;
@@ -363,17 +520,17 @@ __global__ void __launch_bounds__(kLookThreads) lookahead_kernel(const __grid_co
                 j = idx / S;
                 i = idx - j * S;
                 const int64_t t1 = t + j + 1, t2 = t1 + 1;
-                if (t1 >= a.tab.t_base && t1 < a.tab.t_base + a.tab.T_win) {
-                    int64_t r1 = t1 % a.tab.T_win;
-                    r1 += r1 < 0 ? a.tab.T_win : 0;
+                if (t1 >= a.tab.t_base && t1 < t_hi) {
+                    int64_t r1 = row0 + j;  // rows of t + j + 1 and t + j + 2 (j < T_win)
+                    r1 -= r1 >= a.tab.T_win ? a.tab.T_win : 0;
                     const size_t o1 = (size_t)r1 * a.tab.S_pad + i;
                     p1x = a.tab.X[o1];
                     p1y = a.tab.Y[o1];
                     p1z = a.tab.Z[o1];
                     p2x = __int_as_float(0x7fc00000);
-                    if (t2 < a.tab.t_base + a.tab.T_win) {
-                        int64_t r2 = t2 % a.tab.T_win;
-                        r2 += r2 < 0 ? a.tab.T_win : 0;
+                    if (t2 < t_hi) {
+                        int64_t r2 = r1 + 1;
+                        r2 -= r2 >= a.tab.T_win ? a.tab.T_win : 0;
                         const size_t o2 = (size_t)r2 * a.tab.S_pad + i;
                         p2x = a.tab.X[o2];
                         p2y = a.tab.Y[o2];
@@ -419,8 +576,11 @@ __global__ void __launch_bounds__(kLookThreads) lookahead_kernel(const __grid_co
                         const float d2 = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
                         const float R2 = m.w_R2[w];
                         bool in = d2 < R2;
-                        if (fabsf(d2 - R2) <= m.w_band[w])
-                            in = look_well_exact(m, w, X[q], Y[q], Z[q], b1x, b1y, b1z, b2x, b2y, b2z, has2);
+                        if (fabsf(d2 - R2) <= m.w_band[w]) {
+                            const int hn = hna[lane];
+                            in = look_well_exact(m, w, st->s, Dx[hn], Dy[hn], Dz[lane], jb, b1x, b1y, b1z, b2x, b2y,
+                                                 b2z, has2);
+                        }
                         if (in) {
                             const float l = fmaf(sqrtf(d2), m.w_lg[w], m.w_L[w]);
                             mb = fmaxf(mb, l);
@@ -484,8 +644,11 @@ __global__ void __launch_bounds__(kLookThreads) lookahead_kernel(const __grid_co
                             const float d2 = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
                             const float R2 = m.w_R2[w];
                             bool in = d2 < R2;
-                            if (fabsf(d2 - R2) <= m.w_band[w])
-                                in = look_member_exact(m, w, X[q], Y[q], Z[q], bsx, bsy, bsz, bvx, bvy, bvz);
+                            if (fabsf(d2 - R2) <= m.w_band[w]) {
+                                const int hn = hna[lane];
+                                in = look_member_exact(m, w, st->s, Dx[hn], Dy[hn], Dz[lane], jb, bsx, bsy, bsz, bvx,
+                                                       bvy, bvz);
+                            }
                             if (in) {
                                 const float l = fmaf(sqrtf(d2), m.w_lg[w], m.w_L[w]);
                                 mb = fmaxf(mb, l);
@@ -510,11 +673,14 @@ __global__ void __launch_bounds__(kLookThreads) lookahead_kernel(const __grid_co
             }
             float D = 0.f;
             if (m.hm) {
-                const float c32 = (float)Z[q] - terrain32(m, (float)X[q], (float)Y[q]);
-                if (fabsf(c32 - (float)m.clearance) <= kClrBand + kTerrBand)
-                    D = look_deck_exact(m, X[q], Y[q], Z[q]);
-                else if (c32 < (float)m.clearance)
+                const float sx = shx + (slx + ox[q]), sy = shy + (sly + oy[q]), sz = shz + (slz + oz[q]);
+                const float c32 = sz - terrain32(m, sx, sy);
+                if (fabsf(c32 - (float)m.clearance) <= kClrBand + kTerrBand) {
+                    const int ac = q / W, hn = hna[ac];
+                    D = look_deck_exact(m, st->s, Dx[hn], Dy[hn], Dz[ac], q - ac * W);
+                } else if (c32 < (float)m.clearance) {
                     D = (float)m.deck - c32;
+                }
             }
             const float N = P + D;
             lN[q] = N > 0.f ? log2f(N) : -INFINITY;
@@ -522,97 +688,119 @@ __global__ void __launch_bounds__(kLookThreads) lookahead_kernel(const __grid_co
         __syncthreads();
 
         // ---- 4. per action: the largest value over its projected states inside the box.
-        // A value g - N (goal term g = 2^Lg, penalty + deck N = 2^lN) is held as a sign and
-        // log2 |g - N|, which keeps the goal term's resolution when N at another sub-step
-        // is larger by hundreds of binary orders.
+        // Values are held relative to 2^n0 (n0: integer part of log2 of the goal term at s):
+        // g = 2^(phi + rel), N = 2^(lN - n0); g - N as (sign, log2 |g - N|), which keeps the
+        // goal term's resolution when N at another sub-step is larger by hundreds of binary
+        // orders. Only the winner per action is turned into an absolute FP64 log2.
         if (tid < A) {
             const int q0 = tid * W;
+            const float phi = st->phi, fn0 = (float)st->n0;
             int bs = -2;  // no candidate yet
-            double bL = 0.0, bsc = 0.0;
+            float bf = 0.f, bsf = 0.f;
+            bool babs = false;  // bf is an absolute log2 (penalty dominated) rather than relative to n0
             for (int j = 0; j < W; ++j) {
                 const int q = q0 + j;
                 if (j > 0 && !inb[q]) continue;
-                const double Lg = __dadd_rn(st->lgs, (double)rel[q]);
+                const float lg = phi + rel[q];  // log2 g - n0
                 const float ln = lN[q];
                 int sg;
-                double Lv, Ls;
+                float lv, lsc;
+                bool vabs = false;
                 if (ln == -INFINITY) {
                     sg = 1;
-                    Lv = Lg;
-                    Ls = Lg;
+                    lv = lg;
+                    lsc = lg;
                 } else {
-                    const double x = __dsub_rn((double)ln, Lg);  // log2 (N / g)
-                    Ls = fmax(Lg, (double)ln);
-                    if (x < -30.0) {
+                    const float lnr = ln - fn0;  // log2 N - n0
+                    const float x = lnr - lg;    // log2 (N / g)
+                    lsc = fmaxf(lg, lnr);
+                    if (x < -30.f) {
                         sg = 1;
-                        Lv = Lg;
-                    } else if (x > 30.0) {
+                        lv = lg;
+                    } else if (x > 30.f) {
                         sg = -1;
-                        Lv = (double)ln;
+                        lv = ln;
+                        vabs = true;
                     } else {
-                        const float r = exp2f((float)x);
-                        if (r < 1.f) {
+                        const float rr = exp2f(x);
+                        if (rr < 1.f) {
                             sg = 1;
-                            Lv = __dadd_rn(Lg, (double)log2f(1.f - r));
-                        } else if (r > 1.f) {
+                            lv = lg + log2f(1.f - rr);
+                        } else if (rr > 1.f) {
                             sg = -1;
-                            Lv = __dadd_rn(Lg, (double)log2f(r - 1.f));
+                            lv = lg + log2f(rr - 1.f);
                         } else {
                             sg = 0;
-                            Lv = 0.0;
+                            lv = 0.f;
                         }
                     }
                 }
+                const float lvr = vabs ? lv - fn0 : lv;  // for comparisons: relative to n0
+                const float blr = babs ? bf - fn0 : bf;
                 bool better;
                 if (bs == -2) better = true;
                 else if (sg != bs) better = sg > bs;
-                else better = sg > 0 ? Lv > bL : (sg < 0 ? Lv < bL : false);
+                else better = sg > 0 ? lvr > blr : (sg < 0 ? lvr < blr : false);
                 if (better) {
                     bs = sg;
-                    bL = Lv;
-                    bsc = Ls;
+                    bf = lv;
+                    babs = vabs;
+                    bsf = lsc;
                 }
             }
-            Qa[tid] = inb[q0] ? (bs == 0 ? 0.0 : (double)bs * exp2(bL)) : -INFINITY;
-            Sa[tid] = exp2(bsc);
+            const bool valid = inb[q0] != 0;
+            const double Lk = babs ? (double)bf : __dadd_rn((double)st->n0, (double)bf);
+            sga[tid] = valid ? bs : -2;
+            Lka[tid] = Lk;
+            Lqa[tid] = __dadd_rn((double)st->n0, (double)bsf);
+            Ksa[tid] = valid ? look_key(bs, Lk) : 0ull;
         }
         __syncthreads();
 
         // ---- 5. argmax, near-tie record, advance (warp 0)
         if (warp == 0) {
-            const double q = lane < A ? Qa[lane] : -INFINITY;
-            double mx = q;
-            for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(kFullMask, mx, o));
-            const unsigned bm = __ballot_sync(kFullMask, lane < A && q == mx && mx > -INFINITY);
+            const unsigned long long kq = lane < A ? Ksa[lane] : 0ull;
+            unsigned long long mx = kq;
+            for (int o = 16; o; o >>= 1) {
+                const unsigned long long y = __shfl_xor_sync(kFullMask, mx, o);
+                mx = y > mx ? y : mx;
+            }
+            const unsigned bm = __ballot_sync(kFullMask, lane < A && kq == mx && mx != 0ull);
             const int a1 = bm ? __ffs(bm) - 1 : -1;
-            double q2 = (lane < A && lane != a1) ? q : -INFINITY;
-            for (int o = 16; o; o >>= 1) q2 = fmax(q2, __shfl_xor_sync(kFullMask, q2, o));
-            const unsigned b2 = __ballot_sync(kFullMask, lane < A && lane != a1 && q == q2 && q2 > -INFINITY);
+            unsigned long long k2 = (lane < A && lane != a1) ? kq : 0ull;
+            for (int o = 16; o; o >>= 1) {
+                const unsigned long long y = __shfl_xor_sync(kFullMask, k2, o);
+                k2 = y > k2 ? y : k2;
+            }
+            const unsigned b2 = __ballot_sync(kFullMask, lane < A && lane != a1 && kq == k2 && k2 != 0ull);
             const int a2 = b2 ? __ffs(b2) - 1 : -1;
-            if (a.trace && lane < A) q_trace[(size_t)k * A + lane] = q;
+            if (a.trace && lane < A) {
+                const int sgl = sga[lane];
+                q_trace[(size_t)k * A + lane] = sgl == -2 ? -INFINITY : (sgl == 0 ? 0.0 : (double)sgl * exp2(Lka[lane]));
+            }
             if (lane == 0) {
                 bool tie = false;
-                if (a1 >= 0 && a2 >= 0) {
-                    double sc = fmax(fabs(Qa[a1]), fabs(Qa[a2]));
-                    sc = fmax(sc, fmax(Sa[a1], Sa[a2]));
-                    tie = __dsub_rn(Qa[a1], Qa[a2]) < kTieRel * sc;
-                }
+                if (a1 >= 0 && a2 >= 0) tie = look_near_tie(sga[a1], Lka[a1], Lqa[a1], sga[a2], Lka[a2], Lqa[a2]);
                 if (a.trace) tie_trace[k] = tie ? 1 : 0;
                 st->near_ties += tie ? 1 : 0;
                 if (a1 < 0) {
                     st->status = FMDP_REJ_NO_ACTION;
                     st->done = 1;
                 } else {
-                    const int q0 = a1 * W;
+                    const int hn = hna[a1];
+                    // exact advance (FP64, the oracle's x_1) and its double-float copies
                     st->prev[0] = st->s[0];
                     st->prev[1] = st->s[1];
                     st->prev[2] = st->s[2];
-                    st->s[0] = X[q0];
-                    st->s[1] = Y[q0];
-                    st->s[2] = Z[q0];
-                    int hn = st->h + m.dh[a1];
-                    hn += hn < 0 ? 24 : 0;
-                    hn -= hn >= 24 ? 24 : 0;
+                    st->s[0] = __dadd_rn(st->s[0], Dx[hn]);
+                    st->s[1] = __dadd_rn(st->s[1], Dy[hn]);
+                    st->s[2] = __dadd_rn(st->s[2], Dz[a1]);
+                    lk_df_add(st->shx, st->slx, Dh[4 * hn], Dh[4 * hn + 1]);
+                    lk_df_add(st->shy, st->sly, Dh[4 * hn + 2], Dh[4 * hn + 3]);
+                    lk_df_add(st->shz, st->slz, Dz2[2 * a1], Dz2[2 * a1 + 1]);
+                    lk_df_add(st->Ghx, st->Glx, -Dh[4 * hn], -Dh[4 * hn + 1]);
+                    lk_df_add(st->Ghy, st->Gly, -Dh[4 * hn + 2], -Dh[4 * hn + 3]);
+                    lk_df_add(st->Ghz, st->Glz, -Dz2[2 * a1], -Dz2[2 * a1 + 1]);
                     st->h = hn;
                     acts[k] = (uint8_t)a1;
                     const int np = k + 1;
@@ -626,9 +814,12 @@ __global__ void __launch_bounds__(kLookThreads) lookahead_kernel(const __grid_co
                         hd_trace[np] = hn;
                     }
                     st->k = np;
-                    const double ex = __dsub_rn(req.gx, st->s[0]), ey = __dsub_rn(req.gy, st->s[1]),
-                                 ez = __dsub_rn(req.gz, st->s[2]);
-                    if (__dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez)) <= st->cap2) {
+                    st->row0 = st->row0 + 1 == a.tab.T_win ? 0 : st->row0 + 1;
+                    const float gx = st->Ghx + st->Glx, gy = st->Ghy + st->Gly, gz = st->Ghz + st->Glz;
+                    const float gd = sqrtf(gx * gx + gy * gy + gz * gz);
+                    bool cap = false;
+                    if (gd < stepf + kCapBandL) cap = look_capture_exact(st->s, req, st->cap2);
+                    if (cap) {
                         st->status = kStatusCaptured;
                         st->done = 1;
                     } else if (np >= req.horizon) {
