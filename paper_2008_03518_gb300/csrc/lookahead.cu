@@ -38,7 +38,8 @@ constexpr int kLookThreads = 256;
 constexpr unsigned kFullMask = 0xffffffffu;
 
 struct LookLayout {
-    size_t ox, oy, oz, inb, rel, lN, keys, sums, stat, Dx, Dy, Dz, Dh, Dz2, hna, sg, Lk, Lq, Ls, misc, total;
+    size_t ox, oy, oz, inb, rel, lN, vsg, vlv, vlr, vls, keys, sums, stat, Dx, Dy, Dz, Dh, Dz2, hna, sg, Lk, Lq, Ls,
+        misc, total;
 };
 
 __host__ __device__ inline LookLayout look_layout(int A, int W) {
@@ -52,6 +53,10 @@ __host__ __device__ inline LookLayout look_layout(int A, int W) {
     L.inb = o; o += AW * 4;   // projected state inside the box
     L.rel = o; o += AW * 4;   // log2 of the goal term at x_j minus log2 of the goal term at s
     L.lN = o; o += AW * 4;    // log2 of (penalty + deck) at x_j, -inf when zero
+    L.vsg = o; o += AW * 4;   // value g - N at x_j: sign class (2 bits) and whether vlv is absolute
+    L.vlv = o; o += AW * 4;   // log2 |g - N| (relative to n0, or absolute when penalty dominated)
+    L.vlr = o; o += AW * 4;   // log2 |g - N| relative to n0 (for comparisons)
+    L.vls = o; o += AW * 4;   // log2 of the term scale max(g, N) relative to n0
     L.keys = o; o += AW * 4;  // float keys of the largest well log-value (MAX)
     al(8);
     L.sums = o; o += AW * 8;  // fixed-point sums of well values (SUM)
@@ -83,6 +88,9 @@ struct LookState {
     float Gx, Gy, Gz, ds, phi;           // goal - s (fp32), its length, log2 g(s) - n0
     int n0;                              // integer part of log2 of the goal term at s
     int h, k, done, status, near_ties;
+    int tie_k, tie_a1, tie_a2;  // near-tie test of step tie_k still to do (tie_k < 0: none)
+    int tie_s1, tie_s2;
+    double tie_L1, tie_L2, tie_T1, tie_T2;
     int64_t row0;     // ring row of t + 1 for the current step
 };
 
@@ -290,6 +298,10 @@ __global__ void __launch_bounds__(kLookThreads) lookahead_kernel(const __grid_co
     int* inb = reinterpret_cast<int*>(lsm + L.inb);
     float* rel = reinterpret_cast<float*>(lsm + L.rel);
     float* lN = reinterpret_cast<float*>(lsm + L.lN);
+    int* vsg = reinterpret_cast<int*>(lsm + L.vsg);
+    float* vlv = reinterpret_cast<float*>(lsm + L.vlv);
+    float* vlr = reinterpret_cast<float*>(lsm + L.vlr);
+    float* vls = reinterpret_cast<float*>(lsm + L.vls);
     int* keys = reinterpret_cast<int*>(lsm + L.keys);
     unsigned long long* sums = reinterpret_cast<unsigned long long*>(lsm + L.sums);
     float* stc = reinterpret_cast<float*>(lsm + L.stat);
@@ -317,6 +329,16 @@ __global__ void __launch_bounds__(kLookThreads) lookahead_kernel(const __grid_co
     double* st_trace = a.trace ? a.st_trace + (size_t)r * a.cap * 3 : nullptr;
     int32_t* hd_trace = a.trace ? a.hd_trace + (size_t)r * a.cap : nullptr;
     uint8_t* tie_trace = a.trace ? a.tie_trace + (size_t)r * a.cap : nullptr;
+    // near-tie flag of a finished step, taken off the step's chain (one thread)
+    auto deferred_tie = [&]() {
+        if (st->tie_k < 0) return;
+        bool tie = false;
+        if (st->tie_a1 >= 0 && st->tie_a2 >= 0)
+            tie = look_near_tie(st->tie_s1, st->tie_L1, st->tie_T1, st->tie_s2, st->tie_L2, st->tie_T2);
+        if (a.trace) tie_trace[st->tie_k] = tie ? 1 : 0;
+        st->near_ties += tie ? 1 : 0;
+        st->tie_k = -1;
+    };
     const float box0 = (float)m.box[0], box1 = (float)m.box[1], box2 = (float)m.box[2];
     const float box3 = (float)m.box[3], box4 = (float)m.box[4], box5 = (float)m.box[5];
     constexpr float kBoxBandL = 0.01f;  // metres from a box face: decided in FP64
@@ -359,6 +381,7 @@ __global__ void __launch_bounds__(kLookThreads) lookahead_kernel(const __grid_co
         st->h = 0;
         st->k = 0;
         st->near_ties = 0;
+        st->tie_k = -1;
         st->step = __dmul_rn(req.speed_mps, m.dt);
         st->cap2 = __dmul_rn(st->step, st->step);
         traj[0] = (float)req.ox;
@@ -398,6 +421,19 @@ __global__ void __launch_bounds__(kLookThreads) lookahead_kernel(const __grid_co
     for (int q = 0; q < A; ++q) lstep = fmaxf(lstep, fabsf(Dz2[2 * q]));
     const float stepf = (float)st->step;
     lstep = sqrtf(stepf * stepf + lstep * lstep) * 1.0001f + 0.01f;
+    // Wells of a plan sample (offset q from s, velocity v) that can reach a projected state
+    // within rho of s: centre within R + rho + 1 m. A well left out is more than 1 m outside
+    // its radius at every projected state, so no fp32 rounding or band decision can flip it.
+    auto well_mask = [&](float qx, float qy, float qz, float vx, float vy, float vz, float rho) {
+        unsigned msk = 0u;
+        for (int w = 0; w < m.n_wells; ++w) {
+            const float tau = m.w_tau[w];
+            const float cx = fmaf(tau, vx, qx), cy = fmaf(tau, vy, qy), cz = fmaf(tau, vz, qz);
+            const float lim = sqrtf(m.w_R2[w]) + rho + 1.f;
+            if (fmaf(cx, cx, fmaf(cy, cy, cz * cz)) < lim * lim) msk |= 1u << w;
+        }
+        return msk;
+    };
 
     int gen = 0;
     const int n_mem = a.cosim ? a.n_req : 0;
@@ -449,6 +485,8 @@ __global__ void __launch_bounds__(kLookThreads) lookahead_kernel(const __grid_co
             st->Gx = st->Ghx + st->Glx;
             st->Gy = st->Ghy + st->Gly;
             st->Gz = st->Ghz + st->Glz;
+        } else if (tid == 32) {
+            deferred_tie();  // the previous step's near-tie flag
         } else if (tid >= 96 && tid - 96 < m.n_static) {
             const int w = tid - 96;
             const double* c = m.statics + 6 * w;
@@ -514,7 +552,7 @@ __global__ void __launch_bounds__(kLookThreads) lookahead_kernel(const __grid_co
         for (int base = warp * 32; base < npairs; base += kLookThreads) {
             const int idx = base + lane;
             int j = 0, i = 0;
-            bool near = false;
+            unsigned wm = 0u;  // wells of this pair that can reach a projected state of sub-step j
             float p1x = 0.f, p1y = 0.f, p1z = 0.f, p2x = 0.f, p2y = 0.f, p2z = 0.f;
             if (idx < npairs) {
                 j = idx / S;
@@ -538,21 +576,22 @@ __global__ void __launch_bounds__(kLookThreads) lookahead_kernel(const __grid_co
                     }
                     if (p1x == p1x) {
                         const float qx = (p1x - shx) - slx, qy = (p1y - shy) - sly, qz = (p1z - shz) - slz;
-                        float vv = 0.f;
+                        float vx = 0.f, vy = 0.f, vz = 0.f;
                         if (p2x == p2x) {
-                            const float vx = (p2x - p1x) * inv_dt, vy = (p2y - p1y) * inv_dt, vz = (p2z - p1z) * inv_dt;
-                            vv = sqrtf(vx * vx + vy * vy + vz * vz);
+                            vx = (p2x - p1x) * inv_dt;
+                            vy = (p2y - p1y) * inv_dt;
+                            vz = (p2z - p1z) * inv_dt;
                         }
-                        const float reach = (float)(j + 1) * lstep + m.reach_base + m.tau_absmax * vv;
-                        near = qx * qx + qy * qy + qz * qz < reach * reach;
+                        wm = well_mask(qx, qy, qz, vx, vy, vz, (float)(j + 1) * lstep);
                     }
                 }
             }
-            unsigned mask = __ballot_sync(kFullMask, near);
+            unsigned mask = __ballot_sync(kFullMask, wm != 0u);
             while (mask) {
                 const int b = __ffs(mask) - 1;
                 mask &= mask - 1;
                 const int jb = __shfl_sync(kFullMask, j, b);
+                const unsigned bwm = __shfl_sync(kFullMask, wm, b);
                 const float b1x = __shfl_sync(kFullMask, p1x, b), b1y = __shfl_sync(kFullMask, p1y, b),
                             b1z = __shfl_sync(kFullMask, p1z, b);
                 const float b2x = __shfl_sync(kFullMask, p2x, b), b2y = __shfl_sync(kFullMask, p2y, b),
@@ -571,6 +610,7 @@ __global__ void __launch_bounds__(kLookThreads) lookahead_kernel(const __grid_co
                     float mb = -INFINITY;
                     unsigned long long sb = 0ull;
                     for (int w = 0; w < m.n_wells; ++w) {
+                        if (!((bwm >> w) & 1u)) continue;
                         const float tau = m.w_tau[w];
                         const float ux = px - fmaf(tau, vx, qx), uy = py - fmaf(tau, vy, qy), uz = pz - fmaf(tau, vz, qz);
                         const float d2 = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
@@ -600,7 +640,7 @@ __global__ void __launch_bounds__(kLookThreads) lookahead_kernel(const __grid_co
             for (int base = warp * 32; base < nmp; base += kLookThreads) {
                 const int idx = base + lane;
                 int j = 0;
-                bool near = false;
+                unsigned wm = 0u;
                 double msx = 0.0, msy = 0.0, msz = 0.0, mvx = 0.0, mvy = 0.0, mvz = 0.0;
                 if (idx < nmp) {
                     j = idx / n_mem;
@@ -615,16 +655,15 @@ __global__ void __launch_bounds__(kLookThreads) lookahead_kernel(const __grid_co
                         mvz = __ldcg(rc + 5);
                         const float qx = (float)__dsub_rn(msx, st->s[0]), qy = (float)__dsub_rn(msy, st->s[1]),
                                     qz = (float)__dsub_rn(msz, st->s[2]);
-                        const float vv = sqrtf((float)(mvx * mvx + mvy * mvy + mvz * mvz));
-                        const float reach = (float)(j + 1) * lstep + m.reach_base + m.tau_absmax * vv;
-                        near = qx * qx + qy * qy + qz * qz < reach * reach;
+                        wm = well_mask(qx, qy, qz, (float)mvx, (float)mvy, (float)mvz, (float)(j + 1) * lstep);
                     }
                 }
-                unsigned mask = __ballot_sync(kFullMask, near);
+                unsigned mask = __ballot_sync(kFullMask, wm != 0u);
                 while (mask) {
                     const int b = __ffs(mask) - 1;
                     mask &= mask - 1;
                     const int jb = __shfl_sync(kFullMask, j, b);
+                    const unsigned bwm = __shfl_sync(kFullMask, wm, b);
                     const double bsx = __shfl_sync(kFullMask, msx, b), bsy = __shfl_sync(kFullMask, msy, b),
                                  bsz = __shfl_sync(kFullMask, msz, b);
                     const double bvx = __shfl_sync(kFullMask, mvx, b), bvy = __shfl_sync(kFullMask, mvy, b),
@@ -638,6 +677,7 @@ __global__ void __launch_bounds__(kLookThreads) lookahead_kernel(const __grid_co
                         float mb = -INFINITY;
                         unsigned long long sb = 0ull;
                         for (int w = 0; w < m.n_wells; ++w) {
+                            if (!((bwm >> w) & 1u)) continue;
                             const float tau = m.w_tau[w];
                             const float ux = px - fmaf(tau, vx, qx), uy = py - fmaf(tau, vy, qy),
                                         uz = pz - fmaf(tau, vz, qz);
@@ -683,7 +723,46 @@ __global__ void __launch_bounds__(kLookThreads) lookahead_kernel(const __grid_co
                 }
             }
             const float N = P + D;
-            lN[q] = N > 0.f ? log2f(N) : -INFINITY;
+            const float ln = N > 0.f ? log2f(N) : -INFINITY;
+            lN[q] = ln;
+            // the value g - N at x_j relative to 2^n0 (g = 2^(phi + rel), N = 2^(ln - n0))
+            const float lg = st->phi + rel[q];
+            int sg;
+            float lv, lsc;
+            bool vabs = false;
+            if (ln == -INFINITY) {
+                sg = 1;
+                lv = lg;
+                lsc = lg;
+            } else {
+                const float lnr = ln - (float)st->n0;
+                const float x = lnr - lg;  // log2 (N / g)
+                lsc = fmaxf(lg, lnr);
+                if (x < -30.f) {
+                    sg = 1;
+                    lv = lg;
+                } else if (x > 30.f) {
+                    sg = -1;
+                    lv = ln;
+                    vabs = true;
+                } else {
+                    const float rr = exp2f(x);
+                    if (rr < 1.f) {
+                        sg = 1;
+                        lv = lg + log2f(1.f - rr);
+                    } else if (rr > 1.f) {
+                        sg = -1;
+                        lv = lg + log2f(rr - 1.f);
+                    } else {
+                        sg = 0;
+                        lv = 0.f;
+                    }
+                }
+            }
+            vsg[q] = (sg + 1) | (vabs ? 4 : 0);
+            vlv[q] = lv;
+            vlr[q] = vabs ? lv - (float)st->n0 : lv;
+            vls[q] = lsc;
         }
         __syncthreads();
 
@@ -694,65 +773,29 @@ __global__ void __launch_bounds__(kLookThreads) lookahead_kernel(const __grid_co
         // orders. Only the winner per action is turned into an absolute FP64 log2.
         if (tid < A) {
             const int q0 = tid * W;
-            const float phi = st->phi, fn0 = (float)st->n0;
-            int bs = -2;  // no candidate yet
-            float bf = 0.f, bsf = 0.f;
-            bool babs = false;  // bf is an absolute log2 (penalty dominated) rather than relative to n0
+            int bq = -1, bs = -2;
+            float br = 0.f;
             for (int j = 0; j < W; ++j) {
                 const int q = q0 + j;
                 if (j > 0 && !inb[q]) continue;
-                const float lg = phi + rel[q];  // log2 g - n0
-                const float ln = lN[q];
-                int sg;
-                float lv, lsc;
-                bool vabs = false;
-                if (ln == -INFINITY) {
-                    sg = 1;
-                    lv = lg;
-                    lsc = lg;
-                } else {
-                    const float lnr = ln - fn0;  // log2 N - n0
-                    const float x = lnr - lg;    // log2 (N / g)
-                    lsc = fmaxf(lg, lnr);
-                    if (x < -30.f) {
-                        sg = 1;
-                        lv = lg;
-                    } else if (x > 30.f) {
-                        sg = -1;
-                        lv = ln;
-                        vabs = true;
-                    } else {
-                        const float rr = exp2f(x);
-                        if (rr < 1.f) {
-                            sg = 1;
-                            lv = lg + log2f(1.f - rr);
-                        } else if (rr > 1.f) {
-                            sg = -1;
-                            lv = lg + log2f(rr - 1.f);
-                        } else {
-                            sg = 0;
-                            lv = 0.f;
-                        }
-                    }
-                }
-                const float lvr = vabs ? lv - fn0 : lv;  // for comparisons: relative to n0
-                const float blr = babs ? bf - fn0 : bf;
+                const int sg = (vsg[q] & 3) - 1;
+                const float lr = vlr[q];
                 bool better;
                 if (bs == -2) better = true;
                 else if (sg != bs) better = sg > bs;
-                else better = sg > 0 ? lvr > blr : (sg < 0 ? lvr < blr : false);
+                else better = sg > 0 ? lr > br : (sg < 0 ? lr < br : false);
                 if (better) {
+                    bq = q;
                     bs = sg;
-                    bf = lv;
-                    babs = vabs;
-                    bsf = lsc;
+                    br = lr;
                 }
             }
             const bool valid = inb[q0] != 0;
-            const double Lk = babs ? (double)bf : __dadd_rn((double)st->n0, (double)bf);
+            const bool babs = (vsg[bq] & 4) != 0;
+            const double Lk = babs ? (double)vlv[bq] : __dadd_rn((double)st->n0, (double)vlv[bq]);
             sga[tid] = valid ? bs : -2;
             Lka[tid] = Lk;
-            Lqa[tid] = __dadd_rn((double)st->n0, (double)bsf);
+            Lqa[tid] = __dadd_rn((double)st->n0, (double)vls[bq]);
             Ksa[tid] = valid ? look_key(bs, Lk) : 0ull;
         }
         __syncthreads();
@@ -779,10 +822,17 @@ __global__ void __launch_bounds__(kLookThreads) lookahead_kernel(const __grid_co
                 q_trace[(size_t)k * A + lane] = sgl == -2 ? -INFINITY : (sgl == 0 ? 0.0 : (double)sgl * exp2(Lka[lane]));
             }
             if (lane == 0) {
-                bool tie = false;
-                if (a1 >= 0 && a2 >= 0) tie = look_near_tie(sga[a1], Lka[a1], Lqa[a1], sga[a2], Lka[a2], Lqa[a2]);
-                if (a.trace) tie_trace[k] = tie ? 1 : 0;
-                st->near_ties += tie ? 1 : 0;
+                st->tie_k = k;  // tested during the next step (deferred_tie)
+                st->tie_a1 = a1;
+                st->tie_a2 = a2;
+                if (a1 >= 0 && a2 >= 0) {
+                    st->tie_s1 = sga[a1];
+                    st->tie_s2 = sga[a2];
+                    st->tie_L1 = Lka[a1];
+                    st->tie_L2 = Lka[a2];
+                    st->tie_T1 = Lqa[a1];
+                    st->tie_T2 = Lqa[a2];
+                }
                 if (a1 < 0) {
                     st->status = FMDP_REJ_NO_ACTION;
                     st->done = 1;
@@ -832,6 +882,7 @@ __global__ void __launch_bounds__(kLookThreads) lookahead_kernel(const __grid_co
         __syncthreads();
     }
     if (tid == 0) {
+        deferred_tie();
         RolloutOut o;
         o.n_points = st->k + 1;
         o.status = st->status;
