@@ -149,6 +149,7 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float dh, float dl)
 __device__ __forceinline__ float approx_sqrt(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
 
 struct StepState {
+    float wlim2[kMaxWells];  // per well: (R + largest successor offset + 1 m)^2, the reach test
     double s[3];       // exact state (FP64)
     double cap2;       // (speed * dt)^2
     double step;       // speed * dt
@@ -519,6 +520,16 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
         const double step = __dmul_rn(req.speed_mps, m.dt);
         st->step = step;
         st->cap2 = __dmul_rn(step, step);
+        {
+            // a successor lies within step + max |climb| dt of the state; a well whose centre
+            // is farther than R + that + 1 m misses every successor by more than 1 m
+            float dzm = 0.f;
+            for (int q = 0; q < A; ++q) dzm = fmaxf(dzm, fabsf((float)__dmul_rn(m.climb[q], m.dt)));
+            for (int w = 0; w < m.n_wells; ++w) {
+                const float lim = sqrtf(m.w_R2[w]) + (float)step + dzm + 1.f;
+                st->wlim2[w] = lim * lim;
+            }
+        }
         const double s0[3] = {req.ox, req.oy, req.oz};
         const double g0[3] = {req.gx, req.gy, req.gz};
         for (int q = 0; q < 3; ++q) {
@@ -919,12 +930,23 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
             const long long ts = (timing && tid == NT - 32) ? clock64() : 0;
             // wells of one near slot or item ii (lanes = actions); p1 / p2: its samples at
             // t + 1 and t + 2, used again for the FP64 decision inside a radius band
+            // wells of a near item (offset q, velocity v) whose centre is within reach of a successor
+            auto well_mask = [&](float qx_, float qy_, float qz_, float vx_, float vy_, float vz_) {
+                unsigned msk = 0u;
+                for (int w = 0; w < n_wells; ++w) {
+                    const float tau = m.w_tau[w];
+                    const float cx = fmaf(tau, vx_, qx_), cy = fmaf(tau, vy_, qy_), cz = fmaf(tau, vz_, qz_);
+                    if (fmaf(cx, cx, fmaf(cy, cy, cz * cz)) < st->wlim2[w]) msk |= 1u << w;
+                }
+                return msk;
+            };
             auto fold_near = [&](auto&& item_at, int ii, float bqx, float bqy, float bqz, float bvx, float bvy,
-                                 float bvz) {
+                                 float bvz, unsigned bwm) {
                 if (lane >= A) return;
                 float mb = -INFINITY;
                 unsigned long long sb = 0ull;
                 for (int w = 0; w < n_wells; ++w) {
+                    if (!((bwm >> w) & 1u)) continue;  // this well reaches no successor
                     bool bw = false;
                     fold_well(m, w, bqx, bqy, bqz, bvx, bvy, bvz, dxa, dya, dza, mb, sb, bw);
                     if (bw) {
@@ -976,6 +998,7 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
                 for (int base = 0; base < wn; base += 32 * U) {
                     float qx[U], qy[U], qz[U], vx[U], vy[U], vz[U];
                     bool near[U];
+                    unsigned wm[U];
 #pragma unroll
                     for (int u = 0; u < U; ++u) {
                         const int j = base + u * 32 + lane;
@@ -997,6 +1020,8 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
                                 fmaf(tau_absmax, approx_sqrt(vx[u] * vx[u] + vy[u] * vy[u] + vz[u] * vz[u]), reach0);
                             near[u] = (qx[u] * qx[u] + qy[u] * qy[u] + qz[u] * qz[u]) < reach * reach;
                         }
+                        wm[u] = near[u] ? well_mask(qx[u], qy[u], qz[u], vx[u], vy[u], vz[u]) : 0u;
+                        near[u] = wm[u] != 0u;
                     }
 #pragma unroll
                     for (int u = 0; u < U; ++u) {
@@ -1007,7 +1032,8 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
                             const int ii = sw + (base + u * 32 + b) * nscan;
                             fold_near(item_at, ii, __shfl_sync(kFull, qx[u], b), __shfl_sync(kFull, qy[u], b),
                                       __shfl_sync(kFull, qz[u], b), __shfl_sync(kFull, vx[u], b),
-                                      __shfl_sync(kFull, vy[u], b), __shfl_sync(kFull, vz[u], b));
+                                      __shfl_sync(kFull, vy[u], b), __shfl_sync(kFull, vz[u], b),
+                                      __shfl_sync(kFull, wm[u], b));
                         }
                     }
                 }
@@ -1034,6 +1060,7 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
             for (int base = (warp - 2) * 32 * U; base < scan_len; base += nscan * 32 * U) {
                 float qx[U], qy[U], qz[U], vx[U], vy[U], vz[U];
                 bool near[U];
+                unsigned wm[U];
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     const int i = base + u * 32 + lane;
@@ -1056,6 +1083,8 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
                             fmaf(tau_absmax, approx_sqrt(vx[u] * vx[u] + vy[u] * vy[u] + vz[u] * vz[u]), reach0);
                         near[u] = (qx[u] * qx[u] + qy[u] * qy[u] + qz[u] * qz[u]) < reach * reach;  // NaN: false
                     }
+                    wm[u] = near[u] ? well_mask(qx[u], qy[u], qz[u], vx[u], vy[u], vz[u]) : 0u;
+                    near[u] = wm[u] != 0u;
                 }
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
@@ -1066,7 +1095,8 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
                         const int ii = base + u * 32 + b;
                         fold_near(item_at, ii, __shfl_sync(kFull, qx[u], b), __shfl_sync(kFull, qy[u], b),
                                   __shfl_sync(kFull, qz[u], b), __shfl_sync(kFull, vx[u], b),
-                                  __shfl_sync(kFull, vy[u], b), __shfl_sync(kFull, vz[u], b));
+                                  __shfl_sync(kFull, vy[u], b), __shfl_sync(kFull, vz[u], b),
+                                  __shfl_sync(kFull, wm[u], b));
                     }
                 }
             }
