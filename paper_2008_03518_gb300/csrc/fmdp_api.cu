@@ -943,6 +943,9 @@ void enqueue_wave(fmdp_ctx* c, const Geometry& g, int n_clusters, BatchBuffers& 
         pa.out = c->p_rout.p;
         pa.err = c->err;
         pa.rows = policy_rows_for(n_cap, c->n_sm);
+        pa.step_bound = 1;  // learned FCFS: proposals beyond the judge's bound are never taken
+        pa.slack = c->slack;
+        pa.climb_step = climb_step(c);
         LAUNCH(c, launch_policy(pa, std::min(c->n_sm, (n_cap + pa.rows - 1) / pa.rows), s));
         SepRowsArgs sp{};
         sp.m = c->model;

@@ -318,6 +318,18 @@ cudaError_t launch_export_weights(const float* p, __nv_bfloat16* Wt, __nv_bfloat
     return cudaGetLastError();
 }
 
+// Largest step count the judge accepts for request q: (1 + slack) times the fewest steps
+// that can reach the capture ball (radius one step): horizontal motion is exactly one step
+// per step, vertical motion at most the largest climb.
+__device__ __noinline__ double judge_step_bound(const fmdp_request& q, double dt, double climb_step, double slack) {
+    const double step = q.speed_mps * dt;
+    const double dh = sqrt((q.gx - q.ox) * (q.gx - q.ox) + (q.gy - q.oy) * (q.gy - q.oy));
+    const double dz = fabs(q.gz - q.oz);
+    double kmin = fmax(0.0, ceil(dh / step - 1.0));
+    if (climb_step > 0.0) kmin = fmax(kmin, ceil((dz - step) / climb_step));
+    return floor((1.0 + slack) * kmin + 1e-9);
+}
+
 // ------------------------------------------------------------------ policy rollouts
 
 namespace {
@@ -470,6 +482,10 @@ __global__ void __launch_bounds__(kPolicyThreads, 1) policy_kernel(const __grid_
                 R.t1 = q.depart_step + 1;
                 R.speed = (float)q.speed_mps;
                 R.horizon = q.horizon;
+                if (a.step_bound) {  // the judge rejects anything longer: stop there
+                    const double b = judge_step_bound(q, m.dt, a.climb_step, a.slack);
+                    if (b < (double)R.horizon) R.horizon = (int32_t)fmax(b, 0.0);
+                }
                 float* tr = a.traj + (size_t)r * a.cap * 3;
                 tr[0] = (float)q.ox;
                 tr[1] = (float)q.oy;
@@ -477,7 +493,7 @@ __global__ void __launch_bounds__(kPolicyThreads, 1) policy_kernel(const __grid_
                 R.status = -1;
                 const double ex = __dsub_rn(q.gx, q.ox), ey = __dsub_rn(q.gy, q.oy), ez = __dsub_rn(q.gz, q.oz);
                 const bool cap0 = __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez)) <= R.cap2;
-                if (cap0 || q.horizon <= 0) {  // done before the first step
+                if (cap0 || R.horizon <= 0) {  // done before the first step
                     RolloutOut o;
                     o.n_points = 1;
                     o.status = cap0 ? kStatusCaptured : FMDP_REJ_HORIZON;
@@ -714,15 +730,8 @@ __global__ void judge_kernel(const __grid_constant__ JudgeArgs a) {
     if (threadIdx.x == 0) {
         const fmdp_request q = a.reqs[r];
         const SepOut sp = a.sep_p[r];
-        const double step = q.speed_mps * a.dt;
-        const double dh = sqrt((q.gx - q.ox) * (q.gx - q.ox) + (q.gy - q.oy) * (q.gy - q.oy));
-        const double dz = fabs(q.gz - q.oz);
-        // fewest steps that can reach the capture ball (radius one step): horizontal motion
-        // is exactly one step per step, vertical motion at most the largest climb
-        double kmin = fmax(0.0, ceil(dh / step - 1.0));
-        if (a.climb_step > 0.0) kmin = fmax(kmin, ceil((dz - step) / a.climb_step));
         const bool ok = rp.status == kStatusCaptured && sp.first_conflict == INT_MAX && sp.first_terrain == INT_MAX &&
-                        (double)rp.steps <= floor((1.0 + a.slack) * kmin + 1e-9);
+                        (double)rp.steps <= judge_step_bound(q, a.dt, a.climb_step, a.slack);
         ok_s = ok ? 1 : 0;
         a.accepted[r] = ok_s;
         if (ok && a.traj) {

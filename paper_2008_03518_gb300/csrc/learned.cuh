@@ -262,6 +262,9 @@ struct PolicyArgs {
     RolloutOut* out;          // [n]
     int32_t* err;
     int32_t rows;             // requests per CTA: 16 or 32
+    // 1: stop a proposal at the judge's step bound (a longer one would be rejected anyway)
+    int32_t step_bound;
+    double slack, climb_step;
 };
 // rows per CTA for n work items on n_sm multiprocessors: 32 when that still gives every
 // multiprocessor a CTA, else 16
