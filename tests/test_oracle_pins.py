@@ -6,6 +6,7 @@ method, so that a dropped term, a flipped sign, a wrong time index or a transpos
 operand in the oracle fails at least one of them.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -17,6 +18,18 @@ from paper_2008_03518_gb300 import scenarios as S
 pytestmark = pytest.mark.filterwarnings("ignore")
 
 ACT15 = S.action_grid((-2.0, 0.0, 2.0))
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def golden_rows(name):
+    """Rows of a fixture under tests/golden (whitespace-separated, '#' comments)."""
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.split("#", 1)[0].strip()
+            if line:
+                rows.append(line.split())
+    return rows
 BOX = (0.0, 0.0, 0.0, 10000.0, 10000.0, 500.0)
 
 
@@ -28,26 +41,30 @@ def req(ox, oy, oz, gx, gy, gz, speed=30.0, depart=0, horizon=600):
 
 
 def test_fig2a_risk_well_values():
-    """Fig. 2a plots the truncated risk well -2 * 0.7^|x-5| for 2 < x < 8 and 0 outside.
+    """Fig. 2 plots the truncated risk well -2 * 0.7^|x-5| for 2 < x < 8 and 0 outside
+    (tests/golden/fig2_risk_well.txt).
 
     A single static well {r=-2, gamma=.7, p=(5,0,0), R=3} and no goal reward must give
     exactly that curve as the value of a successor at (x, 0, 0)."""
+    (mag, dec, ctr, rad), = [list(map(float, r)) for r in golden_rows("fig2_risk_well.txt")]
     o = Oracle((-100, -100, -100, 100, 100, 100), 1.0, 0.99, [(0.0, 0.0)], (1.0, 1.0), wells=(),
-               goal_reward=0.0, static_wells=np.array([[5.0, 0.0, 0.0, 3.0, 2.0, 0.7]]))
+               goal_reward=0.0, static_wells=np.array([[ctr, 0.0, 0.0, rad, mag, dec]]))
     for x in (-1.0, 2.0, 2.0 + 1e-9, 2.5, 3.0, 4.2, 5.0, 5.5, 7.0, 7.999, 8.0, 9.5):
         # state one metre behind x, moving +x at 1 m/s: the only successor is (x, 0, 0)
         q = o.q_values([x - 1.0, 0.0, 0.0], 0, 0, 1.0, origin=[0.0, 0.0], goal=[1.0e3, 0.0, 0.0])
-        expect = -2.0 * 0.7 ** abs(x - 5.0) if 2.0 < x < 8.0 else 0.0
+        expect = -mag * dec ** abs(x - ctr) if ctr - rad < x < ctr + rad else 0.0
         assert q["valid"][0]
         assert q["Q"][0] == pytest.approx(expect, rel=1e-12, abs=1e-300), x
 
 
 def test_table3_default_wells():
     """Table 3, intruder row: magnitude -1000, decay .97, location p + v t, radius 300 + 10 t,
-    t in {-5, 0, 5, 10, 15}."""
-    assert PAPER_WELLS == ((-5.0, 250.0, 1000.0, 0.97), (0.0, 300.0, 1000.0, 0.97),
-                           (5.0, 350.0, 1000.0, 0.97), (10.0, 400.0, 1000.0, 0.97),
-                           (15.0, 450.0, 1000.0, 0.97))
+    t in {-5, 0, 5, 10, 15} (tests/golden/table3_intruder_wells.txt)."""
+    rows = tuple(tuple(map(float, r)) for r in golden_rows("table3_intruder_wells.txt"))
+    assert len(rows) == 5
+    for t, radius, _, _ in rows:
+        assert radius == 300.0 + 10.0 * t
+    assert PAPER_WELLS == rows
 
 
 def _line_plan(v_before, v_after, k_switch=50, n=100, z=200.0):
@@ -109,8 +126,19 @@ def test_classes_are_combined_by_max():
 
 def test_work_count_matches_table2_formula():
     """Table 2 counts 5 x N x A x R_i intruder-reward threads (13,500,000 at A = 1350,
-    R_i = 2000): every (action, intruder, well) triple is evaluated once per step."""
-    assert 5 * 1 * 1350 * 2000 == 13_500_000
+    R_i = 2000): every (action, intruder, well) triple is evaluated once per step. The
+    printed sample sizes (tests/golden/table1_table2_sizes.txt) follow from the same
+    counts: 5 wells of 6 FP64 fields per intruder, W projected states of 12 fields per
+    action."""
+    g = {k: int(v) for k, v in golden_rows("table1_table2_sizes.txt")}
+    N, A, Rt, Ri, W = g["N"], g["A"], g["R_t"], g["R_i"], g["W"]
+    assert g["table2_intruder_threads"] == len(PAPER_WELLS) * N * A * Ri
+    assert g["table2_terrain_threads"] == N * A * Rt
+    assert g["table2_forward_project_threads"] == N * A
+    assert g["table1_P_I_bytes"] == len(PAPER_WELLS) * Ri * 6 * 8
+    assert g["table1_P_T_bytes"] == Rt * 6 * 8
+    assert g["table1_Delta10_bytes"] == N * A * W * 12 * 8
+    assert g["table1_V_bytes"] == N * A * W * 8
     rng = np.random.default_rng(3)
     o = Oracle(BOX, 1.0, 0.99, ACT15, (150.0, 30.0))
     for _ in range(37):
