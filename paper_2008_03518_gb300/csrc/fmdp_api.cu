@@ -334,7 +334,7 @@ void fill_model(fmdp_ctx* c, const std::vector<fmdp_well>& wells, const std::vec
         magmax = std::max(magmax, s[4]);
     }
     m.sum_ref = magmax > 0.0 ? (float)std::log2(magmax) : 0.0f;
-    m.sum_scale = std::exp2((double)m.sum_ref - 40.0);
+    m.sum_scale = std::exp2((double)m.sum_ref - (double)kSumBits);
     m.hm_nx = a.heightmap ? a.hm_nx : 0;
     m.hm_ny = a.heightmap ? a.hm_ny : 0;
     m.hm_sx = a.heightmap ? (float)((a.hm_nx - 1) / (a.x1 - a.x0)) : 0.f;

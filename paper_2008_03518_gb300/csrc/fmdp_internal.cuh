@@ -24,6 +24,11 @@ constexpr float kSepBand = 0.05f;   // metres around a separation threshold -> F
 constexpr float kClrBand = 0.05f;   // metres around the clearance threshold -> FP64
 constexpr double kTieRel = 1e-4;    // near-tie bar on the top-2 action values
 constexpr int kStatusCaptured = 0;
+// SUM mode: well values are added as integers in units of 2^-kSumBits of the largest |r|
+// (exact and order-independent). 48 bits resolve a well's edge value to better than 1e-6
+// and leave room for 65536 full-strength terms per action and step.
+constexpr int kSumBits = 48;
+constexpr float kSumUnits = 281474976710656.0f;  // 2^48
 
 // Constants of a scheduler, passed by value into every kernel.
 struct Model {
@@ -34,7 +39,7 @@ struct Model {
     double goal_reward;
     double clearance, deck;
     double sep_h, sep_v;
-    double sum_scale;   // 2^(sum_ref - 40): value of one unit of the sum mode's fixed point
+    double sum_scale;   // 2^(sum_ref - kSumBits): value of one unit of the sum mode's fixed point
     float lg32;
     float hm_sx, hm_sy; // heightmap nodes per metre along x, y
     float reach_base;   // max_k R_k + 1 m margin (coarse cull radius without motion terms)

@@ -123,7 +123,7 @@ __device__ bool look_grid_sync(int32_t* bar, int n_ctas, int& gen) {
 }
 
 __device__ __forceinline__ unsigned long long look_sum_term(float l, float ref) {
-    const float t = exp2f(l - ref) * 1099511627776.0f;  // 2^40 fixed point
+    const float t = exp2f(l - ref) * kSumUnits;  // fixed point, 2^-kSumBits of the largest |r|
     return (unsigned long long)__float2ull_rn(t);
 }
 

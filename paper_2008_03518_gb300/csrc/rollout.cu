@@ -330,7 +330,7 @@ __device__ __noinline__ void fold_statics(const Model& m, const StepState* st, c
                 const float l = fmaf(approx_sqrt(d2), m.st_lg[w], m.st_L[w]);
                 mloc = fmaxf(mloc, l);
                 if (m.combine) {
-                    const float t = exp2f(l - m.sum_ref) * 1099511627776.0f;
+                    const float t = exp2f(l - m.sum_ref) * kSumUnits;
                     sloc += (unsigned long long)__float2ull_rn(t);
                 }
             }
@@ -394,7 +394,7 @@ __device__ __forceinline__ uint32_t action_key(int cls, float k2) {
 }
 
 __device__ __forceinline__ unsigned long long sum_term(float l, float ref) {
-    const float t = exp2f(l - ref) * 1099511627776.0f;  // 2^40 fixed point
+    const float t = exp2f(l - ref) * kSumUnits;  // fixed point, 2^-kSumBits of the largest |r|
     return (unsigned long long)__float2ull_rn(t);
 }
 
@@ -789,7 +789,7 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
     const float hm_sx = m.hm_sx, hm_sy = m.hm_sy;
     const int n_static = m.n_static, n_wells = m.n_wells, combine = m.combine;
     const float lg32 = m.lg32, sum_ref = m.sum_ref, tau_absmax = m.tau_absmax;
-    const float sum_unit = exp2f(sum_ref - 40.0f);  // value of one unit of the fixed-point sum
+    const float sum_unit = exp2f(sum_ref - (float)kSumBits);  // value of one unit of the fixed-point sum
     const bool trace0 = a.trace && lead && r == 0;
     if (tid == 0) {
         int n0;
@@ -1164,7 +1164,7 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
             const bool valid = lane < A && valid_s[lane] != 0;
             const float Dl = Dl_s[lane], Vd = Vd_s[lane];
             float Lp;
-            if (combine) Lp = ssum ? __log2f((float)ssum) + (sum_ref - 40.0f) : -INFINITY;
+            if (combine) Lp = ssum ? __log2f((float)ssum) + (sum_ref - (float)kSumBits) : -INFINITY;
             else Lp = key_float(key);
             const float lgh = phi + Dl * lg32;  // log2(g) - n0
             // penalty + deck N, linear; the goal term g / 2^n0 comes from the evaluator
