@@ -1043,9 +1043,19 @@ void enqueue_wave(fmdp_ctx* c, const Geometry& g, int n_clusters, BatchBuffers& 
         ia.cap = cap;
         ia.idx = unres;
         ia.n_dev = B.ctr.p + 2;
-        // a proposal also reads the plans within the feature radius of its states
-        ia.reach_base = c->learned_mode ? std::max(c->model.reach_base, kRF + 1.0f) : c->model.reach_base;
+        ia.reach_base = c->model.reach_base;
         ia.tau_absmax = c->model.tau_absmax;
+        ia.n_wells = c->model.n_wells;
+        for (int k = 0; k < c->model.n_wells; ++k) {
+            ia.w_tau[k] = c->model.w_tau[k];
+            ia.w_R[k] = (float)c->model.w_R64[k];
+        }
+        if (c->learned_mode) {  // a proposal also reads the plan samples within the feature radius
+            ia.feat_r = kRF + 1.0f;
+            ia.traj_p = c->p_traj.p;
+            ia.rout_p = c->p_rout.p;
+            ia.accepted = c->p_acc.p;
+        }
         float dzmax = 0.f;
         for (int i = 0; i < c->model.A; ++i) dzmax = std::max(dzmax, (float)std::fabs(c->model.climb[i] * c->model.dt));
         ia.dzmax = dzmax;

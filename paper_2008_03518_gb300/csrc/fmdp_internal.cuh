@@ -173,6 +173,13 @@ struct InfluenceArgs {
     const int32_t* n_dev;       // number of work items
     float reach_base;           // max_k R_k + 1 m
     float tau_absmax;
+    int32_t n_wells;            // > 0: test each well centre against its own radius
+    float w_tau[kMaxWells];     // well offsets along the plan's velocity (s)
+    float w_R[kMaxWells];       // well radii (m)
+    float feat_r;               // > 0: proposals read plan samples this close (m, + 1 m)
+    const float* traj_p;        // proposals [n_all][cap][3], or null
+    const RolloutOut* rout_p;   // proposals' n_points
+    const int32_t* accepted;    // 1 where the stored trajectory is the accepted proposal
     float dzmax;                // largest climb * dt
     float sep_h, sep_v;
     float dt;

@@ -432,11 +432,16 @@ cudaError_t launch_batch_minsep(const MinSepArgs& a, cudaStream_t s) {
 
 // Influence of request j's speculative trajectory on request k's (j before k in arrival
 // order). With j stored as a plan, k's rollout could choose differently only at a step
-// whose state lies within reach of one of j's wells one step later
-// (|s_k(t) - p_j(t+1)| < max R + max|tau| |v_j| + successor offset + 1 m), since a well
-// out of reach of every successor adds an exact zero to the value; k's verdict could change
-// only where the two trajectories come within the separation minima (+1 m) at the same
-// step. A false positive costs one more speculative round, never a result.
+// whose state lies within reach of one of j's wells one step later: well w is centred at
+// c_w = p_j(t+1) + tau_w v_j with radius R_w (Table 3), and it adds an exact zero to the
+// value of every successor when |s_k(t) - c_w| >= R_w + successor offset + 1 m. k's
+// verdict could change only where the two trajectories come within the separation minima
+// (+1 m) at the same step. In learned FCFS a proposal at state s(t) reads the plan samples
+// of step t+1 within the feature radius, so j may also change k's proposal where
+// |s(t) - p_j(t+1)| < radius + 1 m, along the stored trajectory and, when the judge
+// rejected k's proposal, along the proposal's own path (j can only add conflicts to an
+// unchanged proposal, so a rejected one stays rejected unless its features change).
+// A false positive costs one more speculative round, never a result.
 __global__ void __launch_bounds__(128) influence_kernel(const __grid_constant__ InfluenceArgs a) {
     const int n = *a.n_dev;
     const int w = blockIdx.x, v = blockIdx.y;  // k = item w, j = item v
@@ -470,9 +475,34 @@ __global__ void __launch_bounds__(128) influence_kernel(const __grid_constant__ 
                 vy = (q1[4] - q1[1]) / a.dt;
                 vz = (q1[5] - q1[2]) / a.dt;
             }
-            const float reach = a.reach_base + a.tau_absmax * sqrtf(vx * vx + vy * vy + vz * vz) + rho;
-            const float dx = sx - q1[0], dy = sy - q1[1], dz = sz - q1[2];
-            if (dx * dx + dy * dy + dz * dz < reach * reach) hit = 1;
+            if (a.n_wells > 0) {
+                for (int w = 0; w < a.n_wells; ++w) {
+                    const float r = a.w_R[w] + 1.f + rho;
+                    const float dx = sx - (q1[0] + a.w_tau[w] * vx), dy = sy - (q1[1] + a.w_tau[w] * vy),
+                                dz = sz - (q1[2] + a.w_tau[w] * vz);
+                    if (dx * dx + dy * dy + dz * dz < r * r) hit = 1;
+                }
+            } else {
+                const float reach = a.reach_base + a.tau_absmax * sqrtf(vx * vx + vy * vy + vz * vz) + rho;
+                const float dx = sx - q1[0], dy = sy - q1[1], dz = sz - q1[2];
+                if (dx * dx + dy * dy + dz * dz < reach * reach) hit = 1;
+            }
+            if (a.feat_r > 0.f) {
+                const float dx = sx - q1[0], dy = sy - q1[1], dz = sz - q1[2];
+                if (dx * dx + dy * dy + dz * dz < a.feat_r * a.feat_r) hit = 1;
+            }
+        }
+    }
+    const int np = (j < k && a.traj_p && !a.accepted[k]) ? a.rout_p[k].n_points : 0;
+    if (np > 0 && nj > 0 && tk < tj + nj && tj < tk + np) {  // the rejected proposal's path
+        const float* pk = a.traj_p + (size_t)k * a.cap * 3;
+        const float* pj = a.traj + (size_t)j * a.cap * 3;
+        for (int i = threadIdx.x; i < np && !hit; i += blockDim.x) {
+            const int64_t t1 = tk + i - tj + 1;
+            if (t1 < 0 || t1 >= nj) continue;
+            const float dx = pk[3 * i] - pj[3 * t1], dy = pk[3 * i + 1] - pj[3 * t1 + 1],
+                        dz = pk[3 * i + 2] - pj[3 * t1 + 2];
+            if (dx * dx + dy * dy + dz * dz < a.feat_r * a.feat_r) hit = 1;
         }
     }
     __syncthreads();

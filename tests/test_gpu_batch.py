@@ -177,3 +177,27 @@ def test_staged_batch_equals_sequential(batch_size):
     same_results(many, got)
     assert n_adm == sum(r["verdict"] == ADMITTED for r in many)
     assert st["batch_waves"] >= 1 and st["kernel_launches"] >= 5 * st["batch_waves"]
+
+
+def _side_by_side(offset_m, speed=30.0):
+    """Two requests flying east in an empty sky, `offset_m` apart, departing together."""
+    box = (0.0, 0.0, 0.0, 10000.0, 10000.0, 500.0)
+    req = np.zeros(2, dtype=S.REQUEST_DTYPE)
+    for i, y in enumerate((5000.0, 5000.0 + offset_m)):
+        req[i] = (i + 1, 1000.0, y, 200.0, 7000.0, y, 200.0, speed, 10, 600)
+    return S.Scenario("side_by_side", box, 1.0, 0.99, S.action_grid((-2.0, 0.0, 2.0)), (150.0, 30.0), [], req,
+                      n_slices_window=2048, max_slots=64)
+
+
+@pytest.mark.parametrize("offset,waves", [(700.0, 1), (300.0, 2)])
+def test_influence_follows_each_well(offset, waves):
+    """The first request's wells lie along its track (Table 3: centres p + tau v, radii
+    250-450 m). At 700 m abeam the second request is out of reach of every well, though
+    inside one ball of radius max R + max|tau| |v| around the first request, so both are
+    final after one wave; at 300 m the tau = 0 well reaches it and it is planned again."""
+    sc = _side_by_side(offset)
+    many, bat, t1, t2, st = run_both(sc)
+    same_results(many, bat)
+    same_tables(t1, t2)
+    assert [r["verdict"] for r in bat] == [ADMITTED, ADMITTED]
+    assert st["batch_waves"] == waves and st["batch_replans"] == waves - 1
