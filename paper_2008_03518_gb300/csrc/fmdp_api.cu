@@ -2083,7 +2083,9 @@ void store_plans(fmdp_ctx* c, int32_t n_plans, const int64_t* t0s, const int32_t
         total += counts[i];
         maxc = std::max(maxc, counts[i]);
     }
-    for (int64_t i = 0; i < 3 * total; ++i) require(std::isfinite(xyz[i]), FMDP_ERR_ARG, "plan points must be finite");
+    bool finite = true;  // one pass without early exit (vectorises)
+    for (int64_t i = 0; i < 3 * total; ++i) finite &= std::isfinite(xyz[i]);
+    require(finite, FMDP_ERR_ARG, "plan points must be finite");
     std::vector<int32_t> sl(n_plans);
     for (int32_t i = 0; i < n_plans; ++i) sl[i] = take_slot(c);
     try {

@@ -242,6 +242,63 @@ def make_request(r, req_id=None) -> Request:
                    int(g("horizon")), 0)
 
 
+# numpy mirrors of the ABI's request and result records (same offsets, natural alignment)
+_REQ_NP = np.dtype({"names": [f for f, _ in Request._fields_],
+                    "formats": ["<u8"] + ["<f8"] * 7 + ["<i8", "<i4", "<i4"],
+                    "offsets": [getattr(Request, f).offset for f, _ in Request._fields_],
+                    "itemsize": ctypes.sizeof(Request)})
+_RES_FIELDS = [f for f, _ in Result._fields_ if f not in ("xyz", "actions")]
+_RES_NP = np.dtype({"names": [f for f, _ in Result._fields_],
+                    "formats": ["<i4", "<i4", "<u8", "<i4", "<i4", "<f8", "<f8", "<i4", "<i4", "<i4", "<i4",
+                                "<u8", "<u8"],
+                    "offsets": [getattr(Result, f).offset for f, _ in Result._fields_],
+                    "itemsize": ctypes.sizeof(Result)})
+
+
+def _requests(reqs):
+    """ctypes array of n Requests. A structured numpy array with fields ox..gz, speed (or
+    speed_mps), depart (or depart_step), horizon and optionally req_id is converted column
+    by column; anything else record by record through make_request."""
+    n = len(reqs)
+    names = getattr(getattr(reqs, "dtype", None), "names", None) or ()
+    speed = "speed_mps" if "speed_mps" in names else "speed"
+    depart = "depart_step" if "depart_step" in names else "depart"
+    if all(k in names for k in ("ox", "oy", "oz", "gx", "gy", "gz", speed, depart, "horizon")):
+        arr = np.zeros(n, dtype=_REQ_NP)
+        if "req_id" in names:
+            arr["req_id"] = reqs["req_id"]
+        for k in ("ox", "oy", "oz", "gx", "gy", "gz"):
+            arr[k] = reqs[k]
+        arr["speed_mps"] = reqs[speed]
+        arr["depart_step"] = reqs[depart]
+        arr["horizon"] = reqs["horizon"]
+        return (Request * n).from_buffer(arr)
+    return (Request * n)(*[make_request(reqs[i]) for i in range(n)])
+
+
+def _results(res, n, xyz=None, acts=None):
+    """Result dicts from a ctypes Result array; sample points as views of xyz / acts."""
+    rv = np.frombuffer(res, dtype=_RES_NP, count=n)
+    cols = [rv[k].tolist() for k in _RES_FIELDS]
+    out = [dict(zip(_RES_FIELDS, vals)) for vals in zip(*cols)]
+    if xyz is not None:
+        npts = rv["n_points"].tolist()
+        for i, d in enumerate(out):
+            d["xyz"] = xyz[i, : npts[i]]
+            d["actions"] = acts[i, : max(npts[i] - 1, 0)]
+    return out
+
+
+def _point_buffers(res, n, cap):
+    """Per-request sample buffers [n][cap][3] and [n][cap], named in the results."""
+    xyz = np.zeros((n, cap, 3), dtype=np.float32)
+    acts = np.zeros((n, cap), dtype=np.uint8)
+    rv = np.frombuffer(res, dtype=_RES_NP, count=n)
+    rv["xyz"] = xyz.ctypes.data + np.arange(n, dtype=np.uint64) * np.uint64(cap * 12)
+    rv["actions"] = acts.ctypes.data + np.arange(n, dtype=np.uint64) * np.uint64(cap)
+    return xyz, acts
+
+
 def _has(r, name):
     try:
         r[name]
@@ -369,6 +426,23 @@ class Scheduler:
                                            _ptr(xyz, ctypes.c_float), _ptr(ids, ctypes.c_uint64)))
         return ids
 
+    def add_plans_packed(self, t0s, counts, xyz):
+        """Known plans in the C ABI's packed form: plan i starts at step t0s[i] and holds
+        counts[i] consecutive (x, y, z) samples of xyz (all plans back to back). The arrays
+        are passed as they are when their dtypes already match (int64, int32, float32), so
+        pinned host arrays are copied to the device directly."""
+        t0s = np.ascontiguousarray(t0s, dtype=np.int64)
+        counts = np.ascontiguousarray(counts, dtype=np.int32)
+        xyz = np.ascontiguousarray(xyz, dtype=np.float32)
+        if t0s.shape != counts.shape or t0s.ndim != 1 or xyz.size != 3 * int(counts.sum(dtype=np.int64)):
+            raise ValueError("t0s and counts need one entry per plan, xyz 3 values per sample")
+        ids = np.zeros(t0s.size, dtype=np.uint64)
+        if t0s.size:
+            self._check(self._L.fmdp_add_plans(self._h, t0s.size, _ptr(t0s, ctypes.c_int64),
+                                               _ptr(counts, ctypes.c_int32), _ptr(xyz, ctypes.c_float),
+                                               _ptr(ids, ctypes.c_uint64)))
+        return ids
+
     def query_plans(self, t_begin, t_end):
         n = ctypes.c_int32()
         self._check(self._L.fmdp_query_plans(self._h, int(t_begin), int(t_end), None, 0, ctypes.byref(n)))
@@ -411,19 +485,15 @@ class Scheduler:
 
     def _many(self, fn, reqs, points=True):
         n = len(reqs)
-        rq = (Request * n)(*[make_request(reqs[i]) for i in range(n)])
+        rq = _requests(reqs)
         res = (Result * n)()
         if not points:  # verdicts and counts only
             self._check(fn(self._h, rq, n, res))
-            return [_result_dict(res[i]) for i in range(n)]
-        cap = max([rq[i].horizon for i in range(n)] + [0]) + 1
-        xyz = np.zeros((n, cap, 3), dtype=np.float32)
-        acts = np.zeros((n, cap), dtype=np.uint8)
-        for i in range(n):
-            res[i].xyz = _ptr(xyz[i], ctypes.c_float)
-            res[i].actions = _ptr(acts[i], ctypes.c_uint8)
+            return _results(res, n)
+        cap = int(np.frombuffer(rq, dtype=_REQ_NP, count=n)["horizon"].max(initial=0)) + 1
+        xyz, acts = _point_buffers(res, n, cap)
         self._check(fn(self._h, rq, n, res))
-        return [_result_dict(res[i], xyz[i], acts[i]) for i in range(n)]
+        return _results(res, n, xyz, acts)
 
     def schedule_many(self, reqs, points=True):
         """FCFS in array order, one request after the other on the device."""
@@ -438,7 +508,7 @@ class Scheduler:
         """Continuous-batching serving run over an arrival trace (seconds after the call).
         Returns (results, latency_ms, report)."""
         n = len(reqs)
-        rq = (Request * n)(*[make_request(reqs[i]) for i in range(n)])
+        rq = _requests(reqs)
         arr = np.ascontiguousarray(arrival_s, dtype=np.float64)
         assert arr.shape == (n,)
         o = ServeOptions()
@@ -451,18 +521,13 @@ class Scheduler:
             o.sim_start_set = 1
             o.sim_start_step = int(sim_start_step)
         res = (Result * n)()
-        cap = max([rq[i].horizon for i in range(n)] + [0]) + 1
-        xyz = np.zeros((n, cap, 3), dtype=np.float32) if points else None
-        acts = np.zeros((n, cap), dtype=np.uint8) if points else None
-        if points:
-            for i in range(n):
-                res[i].xyz = _ptr(xyz[i], ctypes.c_float)
-                res[i].actions = _ptr(acts[i], ctypes.c_uint8)
+        cap = int(np.frombuffer(rq, dtype=_REQ_NP, count=n)["horizon"].max(initial=0)) + 1
+        xyz, acts = _point_buffers(res, n, cap) if points else (None, None)
         lat = np.zeros(n, dtype=np.float64)
         rep = ServeReport()
         self._check(self._L.fmdp_serve(self._h, rq, _ptr(arr, ctypes.c_double), n, ctypes.byref(o), res,
                                        _ptr(lat, ctypes.c_double), ctypes.byref(rep)))
-        out = [_result_dict(res[i], xyz[i] if points else None, acts[i] if points else None) for i in range(n)]
+        out = _results(res, n, xyz, acts)
         return out, lat, {k: getattr(rep, k) for k, _ in ServeReport._fields_}
 
     # ---- learned proposal
@@ -470,7 +535,7 @@ class Scheduler:
         """FastMDP rollouts of the requests against the table as it stands (nothing admitted);
         appends their (features, action) rows to the training set. Returns the row count."""
         n = len(reqs)
-        rq = (Request * n)(*[make_request(reqs[i]) for i in range(n)])
+        rq = _requests(reqs)
         rows = ctypes.c_int32()
         self._check(self._L.fmdp_learned_collect(self._h, rq, n, ctypes.byref(rows)))
         return rows.value
@@ -515,7 +580,7 @@ class Scheduler:
 
     def learned_evaluate(self, reqs, slack=0.05):
         n = len(reqs)
-        rq = (Request * n)(*[make_request(reqs[i]) for i in range(n)])
+        rq = _requests(reqs)
         rep = LearnedReport()
         acc = np.zeros(max(n, 1), dtype=np.int32)
         sp = np.zeros(max(n, 1), dtype=np.int32)
@@ -585,7 +650,7 @@ class Scheduler:
 
     def stage(self, reqs):
         n = len(reqs)
-        self._staged = (Request * n)(*[make_request(reqs[i]) for i in range(n)])
+        self._staged = _requests(reqs)
         self._check(self._L.fmdp_stage_requests(self._h, self._staged, n))
 
     def schedule_staged(self, batched=False):
@@ -595,15 +660,11 @@ class Scheduler:
 
     def fetch_staged(self):
         n = len(self._staged)
-        cap = max([self._staged[i].horizon for i in range(n)] + [0]) + 1
-        xyz = np.zeros((n, cap, 3), dtype=np.float32)
-        acts = np.zeros((n, cap), dtype=np.uint8)
+        cap = int(np.frombuffer(self._staged, dtype=_REQ_NP, count=n)["horizon"].max(initial=0)) + 1
         res = (Result * n)()
-        for i in range(n):
-            res[i].xyz = _ptr(xyz[i], ctypes.c_float)
-            res[i].actions = _ptr(acts[i], ctypes.c_uint8)
+        xyz, acts = _point_buffers(res, n, cap)
         self._check(self._L.fmdp_fetch_staged(self._h, res, n))
-        return [_result_dict(res[i], xyz[i], acts[i]) for i in range(n)]
+        return _results(res, n, xyz, acts)
 
     def rollout_trace(self, req):
         r = make_request(req)

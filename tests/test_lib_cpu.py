@@ -88,3 +88,33 @@ def test_no_cpu_fallback_without_gpu():
     with pytest.raises(fmdp.FmdpError) as e:
         fmdp.Scheduler.from_scenario(sc)
     assert e.value.status == -3  # FMDP_ERR_CUDA: no device, and nothing runs on the CPU
+
+
+def test_vectorised_request_and_result_marshalling():
+    """Requests converted column by column equal the record-by-record conversion byte for
+    byte; result buffers are named per request and read back as views."""
+    import numpy as np
+    from paper_2008_03518_gb300 import scenarios as S
+
+    reqs = S.c1_plain_small().requests
+    n = len(reqs)
+    fast = fmdp._requests(reqs)
+    slow = (fmdp.Request * n)(*[fmdp.make_request(r) for r in reqs])
+    assert bytes(fast) == bytes(slow)
+    as_dicts = [{k: reqs[k][i] for k in reqs.dtype.names} for i in range(3)]
+    assert bytes(fmdp._requests(as_dicts)) == bytes(slow)[: 3 * ctypes.sizeof(fmdp.Request)]
+
+    res = (fmdp.Result * 4)()
+    xyz, acts = fmdp._point_buffers(res, 4, 7)
+    for i in range(4):
+        assert ctypes.cast(res[i].xyz, ctypes.c_void_p).value == xyz[i].ctypes.data
+        assert ctypes.cast(res[i].actions, ctypes.c_void_p).value == acts[i].ctypes.data
+        res[i].verdict, res[i].n_points, res[i].plan_id = i - 1, i + 1, (1 << 63) + i
+        res[i].min_sep_h = 0.5 * i
+    xyz[2, :3] = 7.0
+    out = fmdp._results(res, 4, xyz, acts)
+    assert [d["verdict"] for d in out] == [-1, 0, 1, 2]
+    assert [d["plan_id"] for d in out] == [(1 << 63) + i for i in range(4)]
+    assert out[3]["min_sep_h"] == 1.5 and out[2]["xyz"].shape == (3, 3) and (out[2]["xyz"] == 7.0).all()
+    assert out[0]["actions"].shape == (0,) and out[3]["actions"].shape == (3,)
+    assert set(out[0]) == {f for f, _ in fmdp.Result._fields_}
