@@ -288,6 +288,16 @@ fmdp_status fmdp_schedule_learned(fmdp_ctx* ctx, const fmdp_request* reqs, int32
 fmdp_status fmdp_schedule_departures(fmdp_ctx* ctx, const fmdp_request* reqs, int32_t n,
                                      const int64_t* delays, int32_t n_delays, fmdp_result* res,
                                      int32_t* chosen, int32_t* verdicts);
+/* The same call through speculative batches (as fmdp_schedule_batch does for single
+ * requests): the variants of many requests are planned at once against the table as it
+ * stands, and a request's variants are planned again only where an admission of an earlier
+ * request of the batch may have changed them. A request is final when no earlier admission
+ * of the walk influences any of its variants. Results, chosen and verdicts are identical
+ * to fmdp_schedule_departures; res[i].replanned counts the re-plans of the variant shown.
+ * Batches hold max(1, batch_size / n_delays) requests; n * n_delays <= 2^24. */
+fmdp_status fmdp_schedule_departures_batch(fmdp_ctx* ctx, const fmdp_request* reqs, int32_t n,
+                                           const int64_t* delays, int32_t n_delays, fmdp_result* res,
+                                           int32_t* chosen, int32_t* verdicts);
 
 /* Batch co-simulation (the paper's batches whose aircraft see each other, Sec. V, with
  * Alg. 1 stepping every aircraft of the batch on one clock). The n requests are planned

@@ -1143,6 +1143,7 @@ struct Speculator {
     std::vector<RolloutOut> fin_ro;
     std::vector<std::pair<uint64_t, int32_t>> pending;  // admitted, not yet stored: (id, slot)
     int32_t admitted = 0;
+    size_t group = 1;  // work items per request (departure variants), added and resolved together
 
     Speculator(fmdp_ctx* c_, const fmdp_request* reqs_, int32_t n)
         : c(c_), B(c_->bat), reqs(reqs_), slot_of(n, -1), replans(n, 0), verdict(n, -1), ids(n, 0), fin_ro(n) {}
@@ -1195,33 +1196,44 @@ struct Speculator {
             c->stats.sep_pairs += (int64_t)ro.n_points * g.S_scan;
             c->stats.batch_rollouts++;
         }
-        // walk the unresolved requests in arrival order
+        // walk the unresolved requests in arrival order, a group of `group` consecutive work
+        // items at a time: a group is final when no admission earlier in the walk influences
+        // any of its items, and only its first admissible item is admitted
         store.clear();
         std::vector<size_t> adm_pos;  // positions in U admitted by this walk
         size_t pos = 0;
-        for (; pos < U.size(); ++pos) {
-            const uint8_t* row = B.h_infl.p + pos * n_cap;
+        for (; pos < U.size(); pos += group) {
             bool hit = false;
-            for (size_t v : adm_pos) hit = hit || row[v];
-            if (hit) break;
-            const int32_t k = U[pos];
-            fin_ro[k] = B.h_rout.p[k];
-            verdict[k] = host_verdict(fin_ro[k], B.h_sep.p[k]);
-            if (verdict[k] == FMDP_ADMITTED) {
-                const int32_t slot = take_slot(c);
-                require(slot < g.S_scan, FMDP_ERR_ARG, "internal: batch slot beyond the scanned range");
-                const uint64_t id = c->book.next_id++;
-                c->book.plans[id] = PlanMeta{slot, reqs[k].depart_step, fin_ro[k].n_points};
-                c->book.S_hw = std::max(c->book.S_hw, slot + 1);
-                pending.push_back({id, slot});
-                slot_of[k] = slot;
-                ids[k] = id;
-                store.push_back(k);
-                adm_all.push_back(k);
-                adm_pos.push_back(pos);
-                ++admitted;
+            for (size_t q = pos; q < pos + group; ++q) {
+                const uint8_t* row = B.h_infl.p + q * n_cap;
+                for (size_t v : adm_pos) hit = hit || row[v];
             }
-            resolved.push_back(k);
+            if (hit) break;
+            size_t pick = SIZE_MAX;
+            for (size_t q = pos; q < pos + group; ++q) {
+                const int32_t k = U[q];
+                fin_ro[k] = B.h_rout.p[k];
+                verdict[k] = host_verdict(fin_ro[k], B.h_sep.p[k]);
+                if (pick == SIZE_MAX && verdict[k] == FMDP_ADMITTED) pick = q;
+            }
+            for (size_t q = pos; q < pos + group; ++q) {
+                const int32_t k = U[q];
+                if (q == pick) {
+                    const int32_t slot = take_slot(c);
+                    require(slot < g.S_scan, FMDP_ERR_ARG, "internal: batch slot beyond the scanned range");
+                    const uint64_t id = c->book.next_id++;
+                    c->book.plans[id] = PlanMeta{slot, reqs[k].depart_step, fin_ro[k].n_points};
+                    c->book.S_hw = std::max(c->book.S_hw, slot + 1);
+                    pending.push_back({id, slot});
+                    slot_of[k] = slot;
+                    ids[k] = id;
+                    store.push_back(k);
+                    adm_all.push_back(k);
+                    adm_pos.push_back(q);
+                    ++admitted;
+                }
+                resolved.push_back(k);
+            }
         }
         // what stays unresolved is planned again only where an admission may change it
         std::vector<int32_t> nU, ntodo;
@@ -1678,6 +1690,73 @@ void run_departures(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, const int6
                                    cudaMemcpyDeviceToHost, c->stream));
             CK(cudaStreamSynchronize(c->stream));
         }
+    }
+}
+
+// Departure-time candidates through speculative batches. The variants are the work items
+// (request i's variant d is item i * D + d); a request's D items are added and resolved
+// together, and the walk admits its first admissible variant. An admission that influences
+// no item of a request leaves all its variants' plans and verdicts exact, so the results
+// equal run_departures.
+void run_departures_batch(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, const int64_t* delays, int32_t D,
+                          fmdp_result* res, int32_t* chosen, int32_t* verdicts) {
+    if (n <= 0) return;
+    const int32_t N = n * D;
+    std::vector<fmdp_request> cand((size_t)N);
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t d = 0; d < D; ++d) {
+            cand[(size_t)i * D + d] = reqs[i];
+            cand[(size_t)i * D + d].depart_step = reqs[i].depart_step + delays[d];
+        }
+    const int32_t bs = std::max(1, batch_size_of(c) / D) * D;  // whole requests per batch
+    batch_prepare(c, cand.data(), N, std::min(N, bs), nullptr);
+    Speculator sp(c, cand.data(), N);
+    sp.group = (size_t)D;
+    std::vector<int32_t> resolved;
+    for (int32_t b0 = 0; b0 < N; b0 += bs) {
+        const int32_t m = std::min(bs, N - b0);
+        sp.set_geometry(batch_geometry(c, m / D, m));  // at most one admission per request
+        for (int32_t i = 0; i < m; ++i) sp.add(b0 + i);
+        sp.adm_all.clear();
+        try {
+            while (!sp.U.empty()) sp.wave(resolved);
+            sp.finish(b0, m);
+        } catch (...) {
+            sp.rollback();
+            throw;
+        }
+    }
+    std::vector<fmdp_result> items((size_t)N);
+    sp.results(0, N, items.data());
+    BatchBuffers& B = c->bat;
+    bool want_points = false;
+    for (int32_t i = 0; i < n; ++i) want_points = want_points || res[i].xyz || res[i].actions;
+    if (want_points) {
+        B.h_traj.ensure((size_t)N * B.cap * 3);
+        B.h_acts.ensure((size_t)N * B.cap);
+        CK(cudaMemcpyAsync(B.h_traj.p, B.traj.p, (size_t)N * B.cap * 3 * sizeof(float), cudaMemcpyDeviceToHost,
+                           c->stream));
+        CK(cudaMemcpyAsync(B.h_acts.p, B.acts.p, (size_t)N * B.cap, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    }
+    for (int32_t i = 0; i < n; ++i) {
+        int32_t pick = -1;
+        for (int32_t d = 0; d < D; ++d) {
+            const size_t k = (size_t)i * D + d;
+            if (verdicts) verdicts[k] = items[k].verdict;
+            if (pick < 0 && sp.ids[k] != 0) pick = d;
+        }
+        if (chosen) chosen[i] = pick;
+        const size_t k = (size_t)i * D + (pick >= 0 ? pick : 0);
+        float* xyz = res[i].xyz;
+        uint8_t* acts = res[i].actions;
+        res[i] = items[k];
+        res[i].xyz = xyz;
+        res[i].actions = acts;
+        res[i].source = 0;
+        const int32_t np = res[i].n_points;
+        if (xyz) std::memcpy(xyz, B.h_traj.p + k * B.cap * 3, (size_t)np * 12);
+        if (acts && np > 1) std::memcpy(acts, B.h_acts.p + k * B.cap, (size_t)(np - 1));
     }
 }
 
@@ -2758,6 +2837,26 @@ fmdp_status fmdp_schedule_departures(fmdp_ctx* c, const fmdp_request* reqs, int3
                 check_request(c, v);
             }
         run_departures(c, reqs, n, delays, n_delays, res, chosen, verdicts);
+    });
+}
+
+fmdp_status fmdp_schedule_departures_batch(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, const int64_t* delays,
+                                           int32_t n_delays, fmdp_result* res, int32_t* chosen, int32_t* verdicts) {
+    if (!c) return FMDP_ERR_ARG;
+    return guard(c, [&] {
+        require(window_of(c) == 1, FMDP_ERR_ARG, "this entry point plans with lookahead_W = 1");
+        require(n >= 0 && (n == 0 || (reqs && res)), FMDP_ERR_ARG, "null requests or results");
+        require(n_delays >= 1 && n_delays <= kBatchMax && delays, FMDP_ERR_ARG,
+                "between 1 and 1024 departure delays are required");
+        require((int64_t)n * n_delays <= (1 << 24), FMDP_ERR_ARG, "at most 2^24 variants per call");
+        for (int32_t i = 0; i < n; ++i)
+            for (int32_t d = 0; d < n_delays; ++d) {
+                require(std::llabs(delays[d]) < (1ll << 40), FMDP_ERR_ARG, "departure delay out of range");
+                fmdp_request v = reqs[i];
+                v.depart_step += delays[d];
+                check_request(c, v);
+            }
+        run_departures_batch(c, reqs, n, delays, n_delays, res, chosen, verdicts);
     });
 }
 

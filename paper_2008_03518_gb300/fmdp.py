@@ -142,6 +142,7 @@ EXPORTS = ("fmdp_options_default", "fmdp_create", "fmdp_destroy", "fmdp_last_err
            "fmdp_learned_set_params", "fmdp_learned_get_params", "fmdp_learned_train", "fmdp_learned_loss_grad",
            "fmdp_learned_evaluate", "fmdp_schedule_learned",
            "fmdp_autotune", "fmdp_tune_cache_get", "fmdp_tune_cache_put", "fmdp_schedule_departures",
+           "fmdp_schedule_departures_batch",
            "fmdp_schedule_cosim", "fmdp_selftest_wait_timeout",
            "fmdp_get_plan", "fmdp_expire", "fmdp_snapshot", "fmdp_restore", "fmdp_clear", "fmdp_rollout_trace",
            "fmdp_sep_check", "fmdp_sep_check_noalloc", "fmdp_set_profiling", "fmdp_get_stats")
@@ -198,6 +199,7 @@ def load(build_if_missing: bool = True):
     L.fmdp_selftest_wait_timeout.argtypes = [vp, P(c.c_int32)]
     L.fmdp_schedule_departures.argtypes = [vp, P(Request), c.c_int32, P(c.c_int64), c.c_int32, P(Result),
                                            P(c.c_int32), P(c.c_int32)]
+    L.fmdp_schedule_departures_batch.argtypes = L.fmdp_schedule_departures.argtypes
     L.fmdp_tune_cache_get.argtypes = [vp, P(TuneEntry), c.c_int32, P(c.c_int32)]
     L.fmdp_tune_cache_put.argtypes = [vp, P(TuneEntry), c.c_int32]
     L.fmdp_serve_options_default.argtypes = [P(ServeOptions)]
@@ -601,15 +603,17 @@ class Scheduler:
         admitted in array order."""
         return self._many(self._L.fmdp_schedule_cosim, reqs, points)
 
-    def schedule_departures(self, reqs, delays, points=True):
+    def schedule_departures(self, reqs, delays, points=True, batched=False):
         """FCFS where each request takes the first admissible of its variants departing
-        delays[d] steps later (planned together). Returns (results, chosen, verdicts)."""
+        delays[d] steps later (planned together; with batched, the variants of many requests
+        through speculative batches, same results). Returns (results, chosen, verdicts)."""
         n = len(reqs)
         dl = np.ascontiguousarray(delays, dtype=np.int64)
         D = dl.size
         chosen = np.zeros(max(n, 1), dtype=np.int32)
         verd = np.zeros((max(n, 1), max(D, 1)), dtype=np.int32)
-        out = self._many(lambda h, rq, nn, res: self._L.fmdp_schedule_departures(
+        fn = self._L.fmdp_schedule_departures_batch if batched else self._L.fmdp_schedule_departures
+        out = self._many(lambda h, rq, nn, res: fn(
             h, rq, nn, _ptr(dl, ctypes.c_int64), D, res, _ptr(chosen, ctypes.c_int32), _ptr(verd, ctypes.c_int32)),
             reqs, points)
         return out, chosen[:n], verd[:n, :D]
@@ -626,7 +630,7 @@ class Scheduler:
         """Times one wave of the sample's rollouts under each launch shape and caches the
         fastest for the current key; batched calls then use it."""
         n = len(sample)
-        rq = (Request * max(n, 1))(*[make_request(sample[i]) for i in range(n)])
+        rq = _requests(sample) if n else (Request * 1)()
         rep = TuneReport()
         self._check(self._L.fmdp_autotune(self._h, rq, n, 1 if force else 0, ctypes.byref(rep)))
         out = {k: getattr(rep, k) for k, _ in TuneReport._fields_ if k != "chosen"}

@@ -4,7 +4,10 @@ request departing later are planned together and the first admissible one is adm
 - against the oracle on the hover scenario, whose outcome is pinned in closed form;
 - against trying the variants one at a time with fmdp_schedule (the definition: rejected
   variants change nothing), bit for bit, on C1 traffic;
-- window and argument errors leave the table unchanged.
+- window and argument errors leave the table unchanged;
+- the batched call (fmdp_schedule_departures_batch: the variants of many requests through
+  speculative batches) equals the one-request-at-a-time call bit for bit, verdicts of every
+  variant and the table included, with re-plans exercised.
 """
 import numpy as np
 import pytest
@@ -115,4 +118,46 @@ def test_window_and_argument_errors_leave_the_table_unchanged():
         assert e.value.status == -6
         with pytest.raises(FmdpError):
             s.schedule_departures([request()], [])
+        assert len(s.query_plans(-(1 << 40), 1 << 40)) == 1
+
+
+@pytest.mark.parametrize("full_scan,batch_size", [(False, 0), (False, 10), (True, 0)])
+def test_batched_equals_one_request_at_a_time(full_scan, batch_size):
+    """batch_size 0: every request's variants in one batch (24 requests x 5 variants);
+    10: two requests per batch."""
+    sc = S.crowded_batch(seed=131, n_requests=24)
+    delays = [0, 25, 50, 100, 200]
+    with Scheduler.from_scenario(sc, full_scan=full_scan) as s:
+        res, chosen, verd = s.schedule_departures(sc.requests, delays)
+        t_seq = table_of(s)
+    with Scheduler.from_scenario(sc, full_scan=full_scan, batch_size=batch_size) as s:
+        bres, bchosen, bverd = s.schedule_departures(sc.requests, delays, batched=True)
+        st = s.stats()
+        t_bat = table_of(s)
+    assert list(bchosen) == list(chosen) and any(c > 0 for c in chosen)
+    np.testing.assert_array_equal(bverd, verd)
+    same_results(res, bres)
+    same_tables(t_seq, t_bat)
+    assert st["batch_rollouts"] == len(sc.requests) * len(delays) + st["batch_replans"]
+    if batch_size == 0:
+        assert st["batch_replans"] > 0 and st["batch_waves"] > 1
+
+
+def test_batched_hover_scenario_matches_the_oracle():
+    o, s = hover_pair()
+    delays = [0, 20, 60, 400, 500]
+    with s:
+        res, chosen, verd = s.schedule_departures([request(), request(depart=3, rid=8)], delays, batched=True)
+    d, tried = o.schedule_departures(request(), delays)
+    assert chosen[0] == d == 3
+    assert list(verd[0][:4]) == [t["verdict"] for t in tried]
+    np.testing.assert_array_equal(res[0]["xyz"], tried[3]["xyz"])
+
+
+def test_batched_window_errors_leave_the_table_unchanged():
+    o, s = hover_pair()
+    with s:
+        with pytest.raises(FmdpError) as e:
+            s.schedule_departures([request(), request()], [0, 5000], batched=True)
+        assert e.value.status == -6
         assert len(s.query_plans(-(1 << 40), 1 << 40)) == 1
