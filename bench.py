@@ -372,25 +372,34 @@ def main():
                           "admitted": int(sum(r["verdict"] == 0 for r in rcs)),
                           "mode": "one cooperative launch, one CTA per request, grid barrier per step"}
     if "lookahead" in want:
-        # the paper's fidelity: W = 10 sub-steps of 0.1 s, FCFS one request at a time
-        sce = S.e1_fine()
+        # the paper's fidelity: W = 10 sub-steps of 0.1 s; 48 requests through speculative
+        # waves of lookahead rollouts, and the same requests one at a time
+        sce = S.e1_fine(n_requests=48)
         se = Scheduler.from_scenario(sce, lookahead_W=sce.meta["lookahead_W"])
         se.set_stream(stream.cuda_stream)
         se.snapshot()
         se.set_profiling(1)
-        se.schedule_many(sce.requests, points=False)
+        ref = se.schedule_many(sce.requests, points=False)
         steps_e = se.stats()["rollout_steps"]
         se.set_profiling(0)
 
-        def la_step():
+        def la_step(batched):
             se.restore()
+            if batched:
+                return se.schedule_batch(sce.requests, points=False)
             return se.schedule_many(sce.requests, points=False)
 
-        mla, _ = timed(stream, la_step, 1, barrier)
+        la_step(True)
+        mla, got = timed(stream, lambda: la_step(True), 1, barrier)
         mla = max_over_ranks(mla)
+        mseq, _ = timed(stream, lambda: la_step(False), 1, barrier)
+        mseq = max_over_ranks(mseq)
+        assert [r["verdict"] for r in got] == [r["verdict"] for r in ref], "batched lookahead differs"
         modes["lookahead_w10_dt01"] = {"known_plans": len(sce.plans), "value": world * len(sce.requests) / (mla / 1e3),
                                        "unit": UNIT, "ms_per_step": mla, "requests_per_step": len(sce.requests),
-                                       "rollout_steps_per_step": steps_e, "us_per_rollout_step": 1e3 * mla / max(steps_e, 1),
+                                       "one_request_at_a_time": world * len(sce.requests) / (mseq / 1e3),
+                                       "rollout_steps_one_at_a_time": steps_e,
+                                       "us_per_rollout_step_one_at_a_time": 1e3 * mseq / max(steps_e, 1),
                                        "workload": sce.name}
         se.close()
     if "learned" in want:

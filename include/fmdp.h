@@ -89,10 +89,12 @@ typedef struct {
     int32_t lookahead_W;      /* lookahead window W (Sec. IV "Forward project", Alg. 9): each
                                  action is held for W steps of dt and valued by the largest
                                  value along them; the state advances one step. 0 or 1: the
-                                 one-step rule; at most 16. W > 1 plans one request at a time
-                                 (fmdp_schedule_batch and staged batches give the same results
-                                 that way); fmdp_serve, the learned proposal, departure
-                                 candidates and the autotuner require W = 1. */
+                                 one-step rule; at most 16. With W > 1, fmdp_schedule_batch and
+                                 staged batches run speculative waves of lookahead rollouts
+                                 (one CTA per request), the influence test covering the W
+                                 steps ahead; results equal planning one request at a time.
+                                 fmdp_serve, the learned proposal, departure candidates and the
+                                 autotuner require W = 1. */
     int32_t cluster_size;     /* CTAs cooperating on one rollout (0 = automatic) */
     int32_t threads_per_cta;  /* 0 = automatic; else a multiple of 32 in [128, 384] */
     int32_t batch_size;       /* fmdp_schedule_batch: requests per speculative batch

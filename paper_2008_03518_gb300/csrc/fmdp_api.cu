@@ -1008,7 +1008,25 @@ void enqueue_wave(fmdp_ctx* c, const Geometry& g, int n_clusters, BatchBuffers& 
         ra.n_dev = B.ctr.p + 1;
         ra.skip = c->learned_mode ? c->p_acc.p : nullptr;
         KernelTimer t(c, timed ? 0 : -1);
-        LAUNCH(c, launch_rollout(ra, g.threads, g.smem, s, n_clusters));
+        if (window_of(c) > 1) {  // lookahead rollouts (Sec. IV): one CTA per work item
+            LookArgs la{};
+            la.m = c->model;
+            la.tab = tv;
+            la.S_scan = g.S_scan;
+            la.W = window_of(c);
+            la.cap = cap;
+            la.n_req = n_cap;
+            la.reqs = B.rq;
+            la.traj = B.traj.p;
+            la.acts = B.acts.p;
+            la.out = B.rout.p;
+            la.err = c->err;
+            la.idx = todo;
+            la.n_dev = B.ctr.p + 1;
+            LAUNCH(c, launch_lookahead(la, s));
+        } else {
+            LAUNCH(c, launch_rollout(ra, g.threads, g.smem, s, n_clusters));
+        }
         t.stop();
     }
     {
@@ -1045,6 +1063,7 @@ void enqueue_wave(fmdp_ctx* c, const Geometry& g, int n_clusters, BatchBuffers& 
         ia.n_dev = B.ctr.p + 2;
         ia.reach_base = c->model.reach_base;
         ia.tau_absmax = c->model.tau_absmax;
+        ia.W = window_of(c);
         ia.n_wells = c->model.n_wells;
         for (int k = 0; k < c->model.n_wells; ++k) {
             ia.w_tau[k] = c->model.w_tau[k];
@@ -2567,7 +2586,6 @@ fmdp_status fmdp_schedule_staged(fmdp_ctx* c, int32_t batched, int32_t* n_admitt
         require((size_t)n <= c->book.free_slots.size(), FMDP_ERR_FULL, "not enough free slots for the staged run");
         c->staged_done = false;
         int32_t adm;
-        if (batched && window_of(c) > 1) batched = 0;  // lookahead rollouts run one request at a time
         if (batched) {
             c->staged_res.assign(n, fmdp_result{});
             adm = run_batch(c, c->staged.data(), n, c->staged_res.data(), c->stg.reqs.p, true);
@@ -2631,10 +2649,7 @@ fmdp_status fmdp_schedule_batch(fmdp_ctx* c, const fmdp_request* reqs, int32_t n
     return guard(c, [&] {
         require(n >= 0 && (n == 0 || (reqs && res)), FMDP_ERR_ARG, "null requests or results");
         for (int32_t i = 0; i < n; ++i) check_request(c, reqs[i]);
-        if (window_of(c) > 1)  // lookahead rollouts: FCFS one request at a time (same results)
-            run_fcfs(c, reqs, n, res, false);
-        else
-            run_batch(c, reqs, n, res, nullptr, false);
+        run_batch(c, reqs, n, res, nullptr, false);
     });
 }
 

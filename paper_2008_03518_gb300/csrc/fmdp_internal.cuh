@@ -176,6 +176,7 @@ struct InfluenceArgs {
     int32_t n_wells;            // > 0: test each well centre against its own radius
     float w_tau[kMaxWells];     // well offsets along the plan's velocity (s)
     float w_R[kMaxWells];       // well radii (m)
+    int32_t W;                  // lookahead sub-steps of each rollout step (1: the one-step rule)
     float feat_r;               // > 0: proposals read plan samples this close (m, + 1 m)
     const float* traj_p;        // proposals [n_all][cap][3], or null
     const RolloutOut* rout_p;   // proposals' n_points
@@ -311,6 +312,9 @@ struct LookArgs {
     double* mem;   // [2][n_req][8]: x, y, z, vx, vy, vz, flying, alive (by step parity)
     int32_t* bar;  // [2]: arrivals, generation of the grid barrier (zero before launch)
     int32_t absent;  // self-test only: arrivals the barrier waits for that never come
+    // speculative waves (not with cosim): CTA w plans work item idx[w] while w < *n_dev
+    const int32_t* idx;
+    const int32_t* n_dev;
 };
 size_t lookahead_smem_bytes(int A, int W);
 int lookahead_max_resident(int A, int W);  // CTAs of one cooperative launch that fit

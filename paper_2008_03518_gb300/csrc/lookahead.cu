@@ -317,8 +317,9 @@ __global__ void __launch_bounds__(kLookThreads) lookahead_kernel(const __grid_co
     unsigned long long* Ksa = reinterpret_cast<unsigned long long*>(lsm + L.Ls);
     LookState* st = reinterpret_cast<LookState*>(lsm + L.misc);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int r = blockIdx.x;
-    if (r >= a.n_req) return;
+    const int wi = blockIdx.x;
+    if (wi >= a.n_req || (a.n_dev && wi >= *a.n_dev)) return;
+    const int r = a.idx ? a.idx[wi] : wi;
     const fmdp_request req = a.reqs[r];
     float* traj = a.traj + (size_t)r * a.cap * 3;
     uint8_t* acts = a.acts + (size_t)r * a.cap;

@@ -452,7 +452,7 @@ __global__ void __launch_bounds__(128) influence_kernel(const __grid_constant__ 
     __syncthreads();
     const int nk = j < k ? a.rout[k].n_points : 0, nj = j < k ? a.rout[j].n_points : 0;
     const int64_t tk = a.reqs[k].depart_step, tj = a.reqs[j].depart_step;
-    if (nk > 0 && nj > 0 && tk < tj + nj && tj < tk + nk) {  // lifetimes overlap
+    if (nk > 0 && nj > 0 && tk < tj + nj && tj < tk + nk + (a.W - 1)) {  // lifetimes overlap (k sees W ahead)
         const float rho = (float)(a.reqs[k].speed_mps * a.dt) + a.dzmax + 1.0f;
         const float* pk = a.traj + (size_t)k * a.cap * 3;
         const float* pj = a.traj + (size_t)j * a.cap * 3;
@@ -465,31 +465,35 @@ __global__ void __launch_bounds__(128) influence_kernel(const __grid_constant__ 
                 const float dx = sx - pj[3 * t0], dy = sy - pj[3 * t0 + 1], dz = sz - pj[3 * t0 + 2];
                 if (dx * dx + dy * dy < H * H && fabsf(dz) < V) hit = 1;
             }
-            // wells of j one step later against k's state (k's action choice at this step)
-            const int64_t t1 = t0 + 1;
-            if (t1 < 0 || t1 >= nj) continue;
-            const float* q1 = pj + 3 * t1;
-            float vx = 0.f, vy = 0.f, vz = 0.f;
-            if (t1 + 1 < nj) {
-                vx = (q1[3] - q1[0]) / a.dt;
-                vy = (q1[4] - q1[1]) / a.dt;
-                vz = (q1[5] - q1[2]) / a.dt;
-            }
-            if (a.n_wells > 0) {
-                for (int w = 0; w < a.n_wells; ++w) {
-                    const float r = a.w_R[w] + 1.f + rho;
-                    const float dx = sx - (q1[0] + a.w_tau[w] * vx), dy = sy - (q1[1] + a.w_tau[w] * vy),
-                                dz = sz - (q1[2] + a.w_tau[w] * vz);
-                    if (dx * dx + dy * dy + dz * dz < r * r) hit = 1;
+            // wells of j one to W steps later against k's state (k's action choice at this
+            // step: sub-step jj of an action lies within jj successor offsets of the state)
+            for (int jj = 1; jj <= a.W; ++jj) {
+                const int64_t t1 = t0 + jj;
+                if (t1 < 0 || t1 >= nj) continue;
+                const float* q1 = pj + 3 * t1;
+                float vx = 0.f, vy = 0.f, vz = 0.f;
+                if (t1 + 1 < nj) {
+                    vx = (q1[3] - q1[0]) / a.dt;
+                    vy = (q1[4] - q1[1]) / a.dt;
+                    vz = (q1[5] - q1[2]) / a.dt;
                 }
-            } else {
-                const float reach = a.reach_base + a.tau_absmax * sqrtf(vx * vx + vy * vy + vz * vz) + rho;
-                const float dx = sx - q1[0], dy = sy - q1[1], dz = sz - q1[2];
-                if (dx * dx + dy * dy + dz * dz < reach * reach) hit = 1;
-            }
-            if (a.feat_r > 0.f) {
-                const float dx = sx - q1[0], dy = sy - q1[1], dz = sz - q1[2];
-                if (dx * dx + dy * dy + dz * dz < a.feat_r * a.feat_r) hit = 1;
+                const float rj = rho * (float)jj;
+                if (a.n_wells > 0) {
+                    for (int w = 0; w < a.n_wells; ++w) {
+                        const float r = a.w_R[w] + 1.f + rj;
+                        const float dx = sx - (q1[0] + a.w_tau[w] * vx), dy = sy - (q1[1] + a.w_tau[w] * vy),
+                                    dz = sz - (q1[2] + a.w_tau[w] * vz);
+                        if (dx * dx + dy * dy + dz * dz < r * r) hit = 1;
+                    }
+                } else {
+                    const float reach = a.reach_base + a.tau_absmax * sqrtf(vx * vx + vy * vy + vz * vz) + rj;
+                    const float dx = sx - q1[0], dy = sy - q1[1], dz = sz - q1[2];
+                    if (dx * dx + dy * dy + dz * dz < reach * reach) hit = 1;
+                }
+                if (a.feat_r > 0.f && jj == 1) {
+                    const float dx = sx - q1[0], dy = sy - q1[1], dz = sz - q1[2];
+                    if (dx * dx + dy * dy + dz * dz < a.feat_r * a.feat_r) hit = 1;
+                }
             }
         }
     }

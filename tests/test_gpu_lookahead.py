@@ -6,7 +6,8 @@ the GPU), bit-identical trajectories and verdicts under FCFS.
 - the paper's own fidelity: W = 10 sub-steps of dt = 0.1 s (the e1_fine scenario);
 - W = 2 and 4 at dt = 1 s on C1 traffic, MAX and SUM;
 - terrain clearance and static wells along the window;
-- batched calls with W > 1 give the sequential results; entry points that need W = 1
+- batched calls with W > 1 (speculative waves of lookahead rollouts, re-plans included)
+  give the sequential results; entry points that need W = 1
   refuse W > 1.
 """
 import numpy as np
@@ -23,7 +24,7 @@ from paper_2008_03518_gb300 import scenarios as S  # noqa: E402
 from paper_2008_03518_gb300.fmdp import FmdpError, Scheduler  # noqa: E402
 from tests.parity_util import fcfs_parity  # noqa: E402
 
-from test_gpu_batch import same_results  # noqa: E402
+from test_gpu_batch import same_results, same_tables, table_of  # noqa: E402
 
 
 def _pair(sc, W, **kw):
@@ -60,6 +61,34 @@ def test_terrain_and_static_wells_along_the_window():
     with s:
         verdicts, followed, steps = fcfs_parity(s, o, sc.requests[:4], trace_q=True)
     assert steps > 500
+
+
+@pytest.mark.parametrize("W", [3, 10])
+def test_batched_window_rollouts_replan_and_equal_sequential(W):
+    """Speculative waves of lookahead rollouts: crossing paths force re-plans, and the
+    results and the table equal planning one request at a time."""
+    sc = S.crowded_batch(seed=141, n_requests=32)
+    with Scheduler.from_scenario(sc, lookahead_W=W) as s:
+        a = s.schedule_many(sc.requests)
+        ta = table_of(s)
+    with Scheduler.from_scenario(sc, lookahead_W=W) as s:
+        b = s.schedule_batch(sc.requests)
+        st = s.stats()
+        tb = table_of(s)
+    same_results(a, b)
+    same_tables(ta, tb)
+    assert st["batch_replans"] > 0 and st["batch_waves"] > 1
+
+
+def test_batched_paper_fidelity_w10_dt01_equals_sequential():
+    sc = S.e1_fine()
+    with Scheduler.from_scenario(sc, lookahead_W=10) as s:
+        a = s.schedule_many(sc.requests)
+    with Scheduler.from_scenario(sc, lookahead_W=10) as s:
+        s.stage(sc.requests)
+        s.schedule_staged(batched=True)
+        b = s.fetch_staged()
+    same_results(a, b)
 
 
 def test_batched_calls_with_a_window_equal_sequential():
