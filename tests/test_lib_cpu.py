@@ -118,3 +118,19 @@ def test_vectorised_request_and_result_marshalling():
     assert out[3]["min_sep_h"] == 1.5 and out[2]["xyz"].shape == (3, 3) and (out[2]["xyz"] == 7.0).all()
     assert out[0]["actions"].shape == (0,) and out[3]["actions"].shape == (3,)
     assert set(out[0]) == {f for f, _ in fmdp.Result._fields_}
+
+
+def test_packed_plans_reject_mismatched_arrays_before_any_call():
+    """add_plans_packed checks its arrays on the host (one t0 and one count per plan, three
+    values per sample) before it reaches the library."""
+    import numpy as np
+
+    s = object.__new__(fmdp.Scheduler)  # no device context: the checks come first
+    s._L, s._h = None, None
+    with pytest.raises(ValueError):
+        fmdp.Scheduler.add_plans_packed(s, [0, 5], [3], np.zeros((3, 3), np.float32))
+    with pytest.raises(ValueError):
+        fmdp.Scheduler.add_plans_packed(s, [0], [3], np.zeros((2, 3), np.float32))
+    with pytest.raises(ValueError):
+        fmdp.Scheduler.add_plans_packed(s, [[0]], [[3]], np.zeros((3, 3), np.float32))
+    assert fmdp.Scheduler.add_plans_packed(s, [], [], np.zeros((0, 3), np.float32)).size == 0
