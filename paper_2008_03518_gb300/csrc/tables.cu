@@ -438,9 +438,10 @@ cudaError_t launch_batch_minsep(const MinSepArgs& a, cudaStream_t s) {
 // verdict could change only where the two trajectories come within the separation minima
 // (+1 m) at the same step. In learned FCFS a proposal at state s(t) reads the plan samples
 // of step t+1 within the feature radius, so j may also change k's proposal where
-// |s(t) - p_j(t+1)| < radius + 1 m, along the stored trajectory and, when the judge
-// rejected k's proposal, along the proposal's own path (j can only add conflicts to an
-// unchanged proposal, so a rejected one stays rejected unless its features change).
+// |s(t) - p_j(t+1)| < radius + 1 m along the proposal's path: the stored trajectory when the
+// judge accepted it (no FastMDP rollout ran, so its wells do not matter), else the
+// proposal's own path (j can only add conflicts to an unchanged proposal, so a rejected one
+// stays rejected unless its features change; the stored FastMDP plan keeps the wells test).
 // A false positive costs one more speculative round, never a result.
 __global__ void __launch_bounds__(128) influence_kernel(const __grid_constant__ InfluenceArgs a) {
     const int n = *a.n_dev;
@@ -452,6 +453,7 @@ __global__ void __launch_bounds__(128) influence_kernel(const __grid_constant__ 
     __syncthreads();
     const int nk = j < k ? a.rout[k].n_points : 0, nj = j < k ? a.rout[j].n_points : 0;
     const int64_t tk = a.reqs[k].depart_step, tj = a.reqs[j].depart_step;
+    const bool acc = a.accepted && a.accepted[k] != 0;  // stored trajectory = the accepted proposal
     if (nk > 0 && nj > 0 && tk < tj + nj && tj < tk + nk + (a.W - 1)) {  // lifetimes overlap (k sees W ahead)
         const float rho = (float)(a.reqs[k].speed_mps * a.dt) + a.dzmax + 1.0f;
         const float* pk = a.traj + (size_t)k * a.cap * 3;
@@ -478,7 +480,9 @@ __global__ void __launch_bounds__(128) influence_kernel(const __grid_constant__ 
                     vz = (q1[5] - q1[2]) / a.dt;
                 }
                 const float rj = rho * (float)jj;
-                if (a.n_wells > 0) {
+                if (acc) {
+                    // the accepted proposal: its features (below), not FastMDP's wells
+                } else if (a.n_wells > 0) {
                     for (int w = 0; w < a.n_wells; ++w) {
                         const float r = a.w_R[w] + 1.f + rj;
                         const float dx = sx - (q1[0] + a.w_tau[w] * vx), dy = sy - (q1[1] + a.w_tau[w] * vy),
@@ -490,7 +494,7 @@ __global__ void __launch_bounds__(128) influence_kernel(const __grid_constant__ 
                     const float dx = sx - q1[0], dy = sy - q1[1], dz = sz - q1[2];
                     if (dx * dx + dy * dy + dz * dz < reach * reach) hit = 1;
                 }
-                if (a.feat_r > 0.f && jj == 1) {
+                if (acc && a.feat_r > 0.f && jj == 1) {
                     const float dx = sx - q1[0], dy = sy - q1[1], dz = sz - q1[2];
                     if (dx * dx + dy * dy + dz * dz < a.feat_r * a.feat_r) hit = 1;
                 }
