@@ -25,6 +25,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -52,7 +53,8 @@ class ClockSampler:
 
     def __init__(self, index=0):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.path = os.path.join(os.environ.get("FMDP_CLOCKS_DIR", tempfile.gettempdir()),
+                                 f"fmdp_clocks_{os.getpid()}.csv")
         self.index = index
 
     def start(self):
@@ -107,6 +109,24 @@ def traffic_from_profile(kernel_src):
     except OSError:
         pass
     return None
+
+
+def q_eval_alu(kt, n_actions, n_wells, sm_max_mhz, n_sm=152, fp32_lanes=128):
+    """q_eval (the well scan of the rollout) against the FP32 issue peak. Every plan sample a
+    rollout step reads is tested against each well for each action: the well centre offset
+    and the squared distance are 6 FMA (12 FP32 flops) per test. Peak: SMs x FP32 lanes per
+    SM x 2 flops per FMA x the maximum SM clock."""
+    steps, ms = kt.get("rollout_steps", 0), kt.get("rollout_ms", 0.0)
+    samples = kt.get("items_scanned", 0) or kt.get("slots_scanned", 0)
+    if steps <= 0 or ms <= 0.0 or samples <= 0:
+        return None
+    tests = float(samples) * n_actions * n_wells
+    achieved = 12.0 * tests / (ms / 1e3) / 1e12
+    peak = n_sm * fp32_lanes * 2.0 * sm_max_mhz * 1e6 / 1e12
+    return {"kernel": "rollout_kernel (q_eval: the well scan)", "bound": "alu", "achieved": achieved,
+            "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "flops_per_well_test": 12,
+            "well_tests_per_rollout_step": tests / steps,
+            "peak_from": f"{n_sm} SMs x {fp32_lanes} FP32 lanes x 2 flops x {sm_max_mhz:.0f} MHz"}
 
 
 def cpu_baseline(sc, seconds=12.0):
@@ -317,6 +337,10 @@ def main():
                 / max(kt["rollout_steps"], 1),
                 "share_of_kernel_time": kt["rollout_ms"] / max(sum(kernel_ms.values()), 1e-9),
                 "kernel_ms_per_step": kernel_ms}
+    try:  # a secondary figure: never let it cost the bench line
+        qalu = q_eval_alu(kt, len(sc.actions), 5, float(peaks.get("sm_max_mhz", 2070.0)))
+    except Exception as e:  # noqa: BLE001
+        qalu = {"error": str(e)}
 
     # ---- other modes of the metric: plain sequential FCFS, and 20k known plans batched
     modes = None
@@ -500,7 +524,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(sc, n_req, args.mode),
             "admitted_per_step": admitted, "batch": batch_stats, "modes": modes, "e2e": e2e,
-            "gpu_launches": gpu_launches, "roofline": roofline, "clocks": clk,
+            "gpu_launches": gpu_launches, "roofline": roofline, "q_eval_alu": qalu, "clocks": clk,
             "p99_latency_ms_by_rate": p99, "autotune": tune}
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(sc, args.cpu_seconds)

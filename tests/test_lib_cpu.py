@@ -134,3 +134,22 @@ def test_packed_plans_reject_mismatched_arrays_before_any_call():
     with pytest.raises(ValueError):
         fmdp.Scheduler.add_plans_packed(s, [[0]], [[3]], np.zeros((3, 3), np.float32))
     assert fmdp.Scheduler.add_plans_packed(s, [], [], np.zeros((0, 3), np.float32)).size == 0
+
+
+def test_q_eval_alu_figure_of_the_bench():
+    """The bench's q_eval figure: 12 FP32 flops per (plan sample, action, well) test over
+    the rollout kernel's time, against SMs x FP32 lanes x 2 x the maximum SM clock."""
+    import sys as _sys
+
+    _sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+
+    kt = dict(rollout_steps=1000, rollout_ms=2.0, items_scanned=40_000, slots_scanned=0)
+    q = bench.q_eval_alu(kt, 25, 5, 2070.0)
+    assert q["bound"] == "alu" and q["unit"] == "TFLOP/s"
+    assert q["well_tests_per_rollout_step"] == 40 * 25 * 5
+    assert q["achieved"] == pytest.approx(12 * 40_000 * 125 / 2e-3 / 1e12)
+    assert q["peak"] == pytest.approx(152 * 128 * 2 * 2.07e9 / 1e12)
+    assert q["frac"] == pytest.approx(q["achieved"] / q["peak"])
+    assert bench.q_eval_alu(dict(kt, items_scanned=0, slots_scanned=5000), 25, 5, 2070.0)["achieved"] > 0
+    assert bench.q_eval_alu(dict(kt, rollout_steps=0), 25, 5, 2070.0) is None
