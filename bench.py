@@ -338,7 +338,11 @@ def main():
                 "share_of_kernel_time": kt["rollout_ms"] / max(sum(kernel_ms.values()), 1e-9),
                 "kernel_ms_per_step": kernel_ms}
     try:  # a secondary figure: never let it cost the bench line
-        qalu = q_eval_alu(kt, len(sc.actions), 5, float(peaks.get("sm_max_mhz", 2070.0)))
+        n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        qalu = q_eval_alu(kt, len(sc.actions), 5, float(peaks.get("sm_max_mhz", 2070.0)), n_sm=n_sm)
+        if qalu and clk and clk.get("sm_mhz"):  # the same work against the clock the run saw
+            qalu["frac_at_median_clock"] = qalu["frac"] * float(peaks.get("sm_max_mhz", 2070.0)) / clk["sm_mhz"]
+            qalu["median_sm_mhz"] = clk["sm_mhz"]
     except Exception as e:  # noqa: BLE001
         qalu = {"error": str(e)}
 

@@ -427,10 +427,13 @@ fmdp_status fmdp_sep_check(fmdp_ctx* ctx, int64_t t0_step, const float* xyz, int
  *     contents; each call clears the accumulators it needs. Calls whose device work
  *     overlaps (several host threads, or several contexts on one device) race on the
  *     array and must be serialised by the caller.
- *   - The first call on a device is a set-up call: it looks up the array's device address,
- *     and with lazy module loading that is also when the driver places the array in device
- *     memory. Make that first call during start-up, before any stream capture; later calls
- *     take no device memory. */
+ *   - The first call on a context is its set-up call: it looks up the array's address on
+ *     the context's device (kept in the context), and with lazy module loading that is also
+ *     when the driver places the array in device memory. Make that first call during
+ *     start-up, before any stream capture; later calls take no device memory.
+ *   - The call runs on the context's device whichever device is current, and restores the
+ *     caller's current device on return. It is counted in fmdp_stats as a separation-check
+ *     launch, like fmdp_sep_check. */
 #define FMDP_NOALLOC_MAX_POINTS 16384
 fmdp_status fmdp_sep_check_noalloc(fmdp_ctx* ctx, int64_t t0_step, const float* xyz, int32_t n,
                                    fmdp_sep_report* out);

@@ -188,15 +188,6 @@ struct InfluenceArgs {
     int32_t n_cap;              // row stride of out
 };
 
-// What a separation check needs from a context (implemented in fmdp_api.cu).
-struct SepView {
-    Model m;
-    TableView tab;
-    int32_t S_scan;
-    cudaStream_t stream;
-};
-void ctx_sep_view(fmdp_ctx* ctx, SepView* v);
-void ctx_set_error(fmdp_ctx* ctx, const char* msg);
 
 // kernel launchers (rollout.cu / tables.cu)
 // n_clusters > 0: persistent launch of that many clusters (work-queue mode), else one

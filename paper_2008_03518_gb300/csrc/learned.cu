@@ -63,42 +63,54 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
 
 // ------------------------------------------------------------------ training-set collection
 
-// One block per request: headings from the recorded actions, then one warp per step.
+// One block per request: headings from the recorded actions, then one warp per step. The
+// heading recurrence runs in chunks of kHeadChunk steps (one shared array per chunk), so a
+// rollout of any length writes one row per step: exactly the n_points - 1 rows the host
+// counted for it.
+constexpr int kHeadChunk = 2048;
 __global__ void __launch_bounds__(256) collect_kernel(const __grid_constant__ CollectArgs a) {
     __shared__ float feat[8][kFeat];
     __shared__ unsigned long long skey[8][kSectors];
-    __shared__ int8_t head[2048];
+    __shared__ int8_t head[kHeadChunk];
+    __shared__ int h_carry;
     const int r = blockIdx.x;
     if (r >= a.n) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const fmdp_request req = a.reqs[r];
     const int np = a.rout[r].n_points;
-    const int steps = min(np - 1, 2047);
+    const int steps = max(np - 1, 0);
     const uint8_t* act = a.acts + (size_t)r * a.cap;
-    if (threadIdx.x == 0) {
-        int h = 0;
-        for (int k = 0; k < steps; ++k) {
-            head[k] = (int8_t)h;
-            h += a.m.dh[act[k]];
-            h += h < 0 ? 24 : 0;
-            h -= h >= 24 ? 24 : 0;
-        }
-    }
-    __syncthreads();
     const float dx = (float)(req.gx - req.ox), dy = (float)(req.gy - req.oy);
     const float L = sqrtf(dx * dx + dy * dy);
     const float c0 = L > 0.f ? dx / L : 1.f, s0 = L > 0.f ? dy / L : 0.f;
     const float inv_dt = (float)(1.0 / a.m.dt);
-    for (int k = warp; k < steps; k += 8) {
-        const float* p = a.traj + ((size_t)r * a.cap + k) * 3;
-        float hc, hs;
-        heading_cs(c0, s0, head[k], hc, hs);
-        warp_features(a.m, a.iv, a.tab, req.depart_step + k + 1, p[0], p[1], p[2], hc, hs, (float)req.speed_mps,
-                      (float)req.gx, (float)req.gy, (float)req.gz, inv_dt, feat[warp], skey[warp]);
-        const size_t row = (size_t)a.row0[r] + k;
-        for (int i = lane; i < kFeat; i += 32) a.X[row * kFeat + i] = __float2bfloat16_rn(feat[warp][i]);
-        if (lane == 0) a.y[row] = act[k];
-        __syncwarp();
+    if (threadIdx.x == 0) h_carry = 0;
+    for (int k0 = 0; k0 < steps; k0 += kHeadChunk) {
+        const int k1 = min(steps, k0 + kHeadChunk);
+        __syncthreads();  // the previous chunk's headings are no longer read
+        if (threadIdx.x == 0) {
+            int h = h_carry;
+            for (int k = k0; k < k1; ++k) {
+                head[k - k0] = (int8_t)h;
+                h += a.m.dh[act[k]];
+                h += h < 0 ? 24 : 0;
+                h -= h >= 24 ? 24 : 0;
+            }
+            h_carry = h;
+        }
+        __syncthreads();
+        for (int k = k0 + warp; k < k1; k += 8) {
+            const float* p = a.traj + ((size_t)r * a.cap + k) * 3;
+            float hc, hs;
+            heading_cs(c0, s0, head[k - k0], hc, hs);
+            warp_features(a.m, a.iv, a.tab, req.depart_step + k + 1, p[0], p[1], p[2], hc, hs,
+                          (float)req.speed_mps, (float)req.gx, (float)req.gy, (float)req.gz, inv_dt, feat[warp],
+                          skey[warp]);
+            const size_t row = (size_t)a.row0[r] + k;
+            for (int i = lane; i < kFeat; i += 32) a.X[row * kFeat + i] = __float2bfloat16_rn(feat[warp][i]);
+            if (lane == 0) a.y[row] = act[k];
+            __syncwarp();
+        }
     }
 }
 

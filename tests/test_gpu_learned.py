@@ -77,6 +77,40 @@ def test_collected_features_match_the_oracle():
     assert bad <= max(2, rows // 100), (bad, rows, worst)
 
 
+def test_collect_writes_every_row_of_a_rollout_longer_than_2047_steps():
+    """A rollout at dt = 0.1 s that runs well past 2047 steps: the collector writes exactly
+    the n_points - 1 rows the host counts for it, each row the oracle's features of that
+    state and its label the action FastMDP took there."""
+    sc = S.e1_fine(lookahead_W=1)
+    req = np.zeros(1, dtype=S.REQUEST_DTYPE)
+    req[0] = (1, 150.0, 150.0, 250.0, 3850.0, 3850.0, 250.0, 20.0, 0, 4000)
+    with Scheduler.from_scenario(sc) as s:
+        rows = s.learned_collect(req)
+        X, y = s.learned_rows(rows + 16)
+        t = s.rollout_trace(req[0])
+    n = t["n_points"] - 1
+    assert n > 2047 + 300 and rows == n and len(X) == n, (n, rows, len(X))
+    np.testing.assert_array_equal(y, t["actions"][:n])
+    r = req[0]
+    c0, s0 = r["gx"] - r["ox"], r["gy"] - r["oy"]
+    L = np.hypot(c0, s0)
+    c0, s0 = c0 / L, s0 / L
+    bad = []
+    with_intruders = 0
+    for k in range(n):
+        a = np.pi / 12.0 * t["headings"][k]
+        hc, hs = c0 * np.cos(a) - s0 * np.sin(a), s0 * np.cos(a) + c0 * np.sin(a)
+        p1, p2 = plan_samples(sc, int(r["depart"]) + k + 1)
+        want = OL.features(t["xyz"][k].astype(np.float64), hc, hs, float(r["speed"]),
+                           (r["gx"], r["gy"], r["gz"]), sc.box, p1, p2, dt=sc.dt)
+        with_intruders += bool(np.any(want[OL.N_OWN:] != 0.0))
+        if np.any(np.abs(X[k] - want) > 8e-3 * np.abs(want) + 2e-3):
+            bad.append(k)
+    # a sample on a sector boundary may fall on either side: a few rows, never a run of them
+    assert len(bad) <= max(2, n // 100), (len(bad), n, bad[:10])
+    assert with_intruders > 20  # the rows past the old limit are not all own-state only
+
+
 def test_gradient_matches_the_oracle():
     """GPU loss and gradient against the oracle's bf16 network (the same rounding points:
     bf16 weights, hidden activations and matrix-product operands, fp32 accumulation), and
@@ -99,11 +133,20 @@ def test_gradient_matches_the_oracle():
     for (o_w, n_w), (o_b, n_b) in zip(_weight_blocks(), _bias_blocks()):
         for o, n in ((o_w, n_w), (o_b, n_b)):
             sl = slice(o, o + n)
-            rel_r = np.linalg.norm(g[sl] - r_g[sl]) / max(np.linalg.norm(r_g[sl]), 1e-12)
-            assert rel_r < 1e-2, (o, rel_r)
-            rel_e = np.linalg.norm(g[sl] - e_g[sl]) / max(np.linalg.norm(e_g[sl]), 1e-12)
-            bound = np.linalg.norm(r_g[sl] - e_g[sl]) / max(np.linalg.norm(e_g[sl]), 1e-12)
-            assert rel_e < 1.5 * bound + 1e-2, (o, rel_e, bound)
+            # Element by element against the bf16 oracle. Both sides round at the same
+            # points; they differ only where the GPU's fp32 accumulation (another order than
+            # the oracle's FP64 sums) lands an activation or an output gradient on the other
+            # side of a bf16 rounding boundary, which moves that value by one bf16 ulp
+            # (2^-8 relative) and the gradient elements it feeds by at most that share.
+            # rtol 2e-2 covers such an ulp on an element it dominates; the absolute floor
+            # (2e-3 of the block's largest element) covers elements near zero. A wrong sign,
+            # a transposed block or a swapped index moves elements by 100 % or more.
+            scale = float(np.abs(r_g[sl]).max())
+            np.testing.assert_allclose(g[sl], r_g[sl], rtol=2e-2, atol=2e-3 * scale,
+                                       err_msg=f"gradient block at offset {o}")
+            # and the signs of the clearly non-zero elements agree with the exact gradient
+            big = np.abs(e_g[sl]) > 0.05 * float(np.abs(e_g[sl]).max())
+            assert np.array_equal(np.sign(g[sl][big]), np.sign(e_g[sl][big])), o
     assert g.shape == (MLP_PARAMS,)
 
 

@@ -18,6 +18,7 @@ from oracle import ADMITTED  # noqa: E402
 from paper_2008_03518_gb300 import scenarios as S  # noqa: E402
 from paper_2008_03518_gb300.fmdp import Scheduler  # noqa: E402
 
+from parity_util import fcfs_parity, oracle_for  # noqa: E402
 from test_gpu_batch import same_results, same_tables, table_of  # noqa: E402
 
 
@@ -44,6 +45,21 @@ def test_served_results_equal_one_at_a_time():
     assert rep["throughput_rps"] > 0
 
 
+def test_served_results_match_the_oracle():
+    """Every served request re-derived by the FP64 oracle, in arrival order, from the table
+    the GPU had when it planned it (the known plans plus every request admitted before it):
+    trajectories bit for bit, action sequences equal except at the oracle's own near-ties,
+    verdicts and first-conflict steps identical, minimum separations within 1e-5."""
+    sc = S.crowded_batch(seed=112, n_requests=48)
+    arr = poisson(len(sc.requests), 2000.0, 3)
+    with Scheduler.from_scenario(sc, batch_size=32) as s:
+        served, lat, rep = s.serve(sc.requests, arr)
+    verdicts, _, _ = fcfs_parity(None, oracle_for(sc), sc.requests, gpu_results=served)
+    assert sum(v == ADMITTED for v in verdicts) == rep["admitted"] > 0
+    assert rep["admitted"] < len(sc.requests)  # the mix also rejects
+    assert rep["max_in_flight_seen"] > 1
+
+
 def _staggered(sc, gap):
     """Requests departing one after another, `gap` steps apart, from step 200 on."""
     r = sc.requests.copy()
@@ -66,6 +82,19 @@ def test_serving_expires_finished_plans_without_changing_results():
     assert rep["expiries"] > 0 and rep["plans_expired"] > 0
     assert remaining == len(sc.plans) + rep["admitted"] - rep["plans_expired"]
     assert rep["final_t_base"] <= int(reqs["depart"].max())
+
+
+def test_served_with_expiry_matches_the_oracle():
+    """Expiry removes only plans that ended before every departure still to plan, so the
+    oracle, which keeps every plan, derives the same results for every served request."""
+    sc = S.c1_plain_small()
+    reqs = _staggered(sc, 12)[:40]
+    arr = np.linspace(0.0, 0.4, len(reqs))
+    with Scheduler.from_scenario(sc) as s:
+        served, lat, rep = s.serve(reqs, arr, time_scale=2000.0, expire_quantum=30)
+    assert rep["plans_expired"] > 0
+    verdicts, _, _ = fcfs_parity(None, oracle_for(sc), reqs, gpu_results=served)
+    assert sum(v == ADMITTED for v in verdicts) == rep["admitted"]
 
 
 def test_memory_based_admission_defers_and_keeps_results():

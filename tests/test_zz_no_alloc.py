@@ -77,3 +77,29 @@ def test_noalloc_sep_check_matches_the_allocating_one_on_two_calls():
         # and the largest allowed size still works
         full = _trajectory_near_plans(sc, rng, 0, NOALLOC_MAX_POINTS)
         _same(s.sep_check_noalloc(0, full), s.sep_check(0, full))
+
+
+def test_noalloc_runs_on_the_context_device_and_is_counted():
+    """The call runs on the context's device whichever device the caller has current, leaves
+    the caller's device current, and counts as a separation-check launch in the stats."""
+    sc = S.c1_plain_small()
+    rng = np.random.default_rng(7)
+    t0 = 120
+    traj = _trajectory_near_plans(sc, rng, t0, 500)
+    with Scheduler.from_scenario(sc) as s:
+        want = s.sep_check(t0, traj)
+        s.set_profiling(1)
+        before = torch.cuda.current_device()
+        got = s.sep_check_noalloc(t0, traj)
+        assert torch.cuda.current_device() == before
+        _same(got, want)
+        st = s.stats()
+        assert st["sepcheck_launches"] == 1 and st["sep_pairs"] > 0
+        if torch.cuda.device_count() > 1:  # a caller that made another device current
+            other = (before + 1) % torch.cuda.device_count()
+            torch.cuda.set_device(other)
+            try:
+                _same(s.sep_check_noalloc(t0, traj), want)
+                assert torch.cuda.current_device() == other
+            finally:
+                torch.cuda.set_device(before)
