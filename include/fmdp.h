@@ -107,7 +107,10 @@ typedef struct {
     double index_cell_m;      /* index: cell edge in metres (0 = automatic) */
     int32_t index_stage_items; /* index: plan samples a rollout step stages in shared memory
                                   (0 = 1536; more are read from global memory) */
-    int32_t reserved;
+    int32_t batch_mode;       /* fmdp_schedule_batch, staged batches and fmdp_serve:
+                                 0 = pipelined where it applies (spatial index, W = 1, FastMDP
+                                 rollouts): continuous batching without waves, see
+                                 fmdp_schedule_batch; 1 = speculative waves. Same results. */
 } fmdp_options;
 
 /* Fills *o with the defaults (max combine, Table 3 wells, goal 200, W = 1, automatic). */
@@ -168,7 +171,17 @@ fmdp_status fmdp_schedule(fmdp_ctx* ctx, const fmdp_request* req, fmdp_result* r
 fmdp_status fmdp_schedule_many(fmdp_ctx* ctx, const fmdp_request* reqs, int32_t n,
                                fmdp_result* res);
 /* Batched speculative FCFS (no counterpart in the paper, which plans requests one at a
- * time, Sec. V): the requests are taken in batches of options.batch_size. Each batch is
+ * time, Sec. V). Pipelined mode (options.batch_mode = 0, with the spatial index and W = 1):
+ * one persistent rollout launch takes requests from a ring in host-mapped memory that the
+ * host keeps filling, up to options.batch_size requests past the first unresolved one;
+ * each finished plan is reported to host-mapped memory, and the host walks the requests
+ * in array order: a request is final when no admission made after its plan started can
+ * reach one of its successor states with a well or come within the separation minima of
+ * it; an admitted request is stored at once (beside the running rollouts, its index
+ * entries published only when complete), and a plan that an admission influences is
+ * planned again as soon as that admission is visible. Long index extra lists are rebuilt
+ * while no rollout runs. Wave mode (batch_mode = 1, or lookahead, full scan, learned
+ * proposals): the requests are taken in batches of options.batch_size. Each batch is
  * planned concurrently against the table as it stands (one persistent rollout launch
  * whose clusters pull requests from a device queue, replayed as a CUDA graph), then
  * re-checked in array order: a request is final when no request admitted before it in
@@ -212,6 +225,10 @@ typedef struct {
     int32_t admitted, rejected;
     int32_t max_in_flight_seen;    /* largest unresolved set */
     int32_t deferred_for_memory;   /* requests that waited for free plan slots */
+    int32_t pipelined;             /* 1: continuous batching without waves (batch_mode 0) */
+    int32_t persistent_ctas;       /* pipelined: CTAs of the persistent rollout launch */
+    int64_t drains;                /* pipelined: index rebuilds that waited for the rollouts */
+    double rollout_occupancy;      /* pipelined: summed rollout time / (CTAs x wall time) */
 } fmdp_serve_report;
 
 void fmdp_serve_options_default(fmdp_serve_options* o);
@@ -457,6 +474,11 @@ typedef struct {
     double influence_ms;         /* their summed CUDA-event durations */
     int64_t kernel_launches;     /* every kernel launch of the library, graph nodes included */
     int64_t items_scanned;       /* indexed rollouts: plan samples read by their steps (on >= 1) */
+    int64_t pipe_drains;         /* pipelined batches: index rebuilds that waited for the rollouts */
+    double pipe_cta_s;           /* pipelined: summed wall time from dispatch to report of every plan */
+    double pipe_slot_s;          /* pipelined: persistent CTAs x wall time of the calls */
+    int32_t pipe_ctas;           /* pipelined: CTAs of the last persistent launch */
+    int32_t pipe_resident;       /* pipelined: CTAs of that shape the device keeps resident */
 } fmdp_stats;
 /* on = 1: per-kernel CUDA-event timing on the context's stream; on = 2: additionally
  * per-phase cycle counters inside the rollout kernel (diagnostic, slows it slightly);

@@ -66,6 +66,7 @@ fmdp_status fmdp_create(const fmdp_airspace* air, double gamma, const fmdp_actio
         require(o.batch_size >= 0 && o.batch_size <= kBatchMax, FMDP_ERR_ARG, "batch size 0..1024");
         require(o.index_stage_items >= 0 && o.index_stage_items <= 3000, FMDP_ERR_ARG,
                 "index stage items 0..3000");
+        require(o.batch_mode == 0 || o.batch_mode == 1, FMDP_ERR_ARG, "batch_mode must be 0 (pipelined) or 1 (waves)");
         require(o.index_vmax_mps >= 0.0 && o.index_cell_m >= 0.0, FMDP_ERR_ARG, "index bounds must be >= 0");
         std::vector<fmdp_well> wells;
         if (o.wells && o.n_wells > 0) {
@@ -151,6 +152,7 @@ fmdp_status fmdp_create(const fmdp_airspace* air, double gamma, const fmdp_actio
             // 16 words of padding: rollouts stage aligned 16-byte blocks around the words they need
             CK(cudaMalloc(&c->ix_cstart, ((size_t)c->T_win * (c->ix_ncell + 1) + 16) * sizeof(int32_t)));
             CK(cudaMalloc(&c->ix_nextra, ((size_t)c->T_win + 16) * sizeof(int32_t)));
+            CK(cudaMalloc(&c->ix_nres, ((size_t)c->T_win + 16) * sizeof(int32_t)));
             CK(cudaMalloc(&c->ix_dirty, (size_t)c->T_win * sizeof(int32_t)));
             CK(cudaMalloc(&c->ix_items, plane * 2 * sizeof(float4)));
             CK(cudaMalloc(&c->items_ctr, sizeof(unsigned long long)));

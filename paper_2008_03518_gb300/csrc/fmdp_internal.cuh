@@ -69,7 +69,8 @@ struct TableView {
 
 // Spatial index of the plan table (one per ring row, rebuilt or appended as rows change).
 // Row r holds one item per slot with a sample at the row's step T: the sample p(T) and the
-// same slot's sample p(T+1) (NaN when there is none), 32 bytes. Items are grouped by the
+// same slot's sample p(T+1) (NaN when there is none), 32 bytes; the first float4's w holds
+// the slot number (its int32 bits). Items are grouped by the
 // 2-D cell of p(T) (ncx x ncy cells of `cell` metres over the airspace box, positions
 // outside the box clamped to the edge cells), in cell order; after the last cell comes the
 // extra list, scanned for every query: items moving faster than vmax (their wells reach
@@ -100,6 +101,42 @@ struct SepOut {
     int32_t pad;
 };
 
+// Pipelined speculative FCFS (continuous batching). One persistent rollout launch takes
+// work items from a ring in host-mapped memory that the host appends to while the launch
+// runs; each finished plan is checked for conflicts against the plans it could see, and
+// its trajectory and report are written to host-mapped memory, then its completion token.
+struct PipeItem {
+    int32_t r;      // request number of the call
+    int32_t token;  // written to done[r] when this plan has finished
+};
+struct PipeRecord {
+    RolloutOut ro;
+    int32_t first_conflict;  // the tail check's first conflicting sample, -1 when none
+    int32_t first_terrain;   // first sample below the terrain, -1 when none
+    int32_t tail_pub;        // admissions published before the tail check read the index
+    int32_t pad;
+};
+struct PipeArgs {
+    int32_t on;
+    int32_t qmask;            // ring entries - 1 (a power of two)
+    const PipeItem* items;    // host-mapped ring
+    const int32_t* tail;      // host-mapped: items written so far
+    const int32_t* stop;      // host-mapped: 1 = leave once the ring is empty
+    int32_t* head;            // device: items taken so far
+    int32_t* done;            // host-mapped [n]: token of the last finished plan of request r
+    PipeRecord* rec;          // host-mapped [n]
+    float* h_traj;            // host-mapped [n][cap][3]
+    SepOut* sep;              // device [n]: the tail check's report (read by the admission)
+    long long idle_cycles;    // a CTA that finds no work for this many SM cycles leaves
+    // Admissions of the call published so far (device; the table stream raises it after each
+    // admission's index entries are visible). A rollout step records the count it read
+    // before the index rows it valued (obs[r][k] for step k; copied to h_obs), so the host
+    // tests an admission only against the steps that could not see it.
+    const int32_t* pub_seq;
+    int32_t* obs;             // device [n][cap]
+    int32_t* h_obs;           // host-mapped [n][cap]
+};
+
 struct RolloutArgs {
     Model m;
     TableView tab;
@@ -128,6 +165,7 @@ struct RolloutArgs {
     IndexView iv;
     unsigned long long* items_ctr;  // indexed mode: items read by the steps (statistics) or nullptr
     const int32_t* skip;            // batch mode: request r is not planned when skip[r] (nullptr: none)
+    PipeArgs pipe;                  // pipelined mode (pipe.on): work from the host-fed ring
 };
 
 struct SepArgs {
@@ -160,6 +198,8 @@ struct AdmitArgs {
     const int32_t* idx;    // request index of work item y (nullptr: identity)
     const int32_t* n_dev;  // number of work items on the device (nullptr: all launched)
     const int32_t* err;    // device error word: nothing is stored once a wait has expired
+    int32_t* slot_ord;     // if set: slot_ord[slot] = ord for an admitted trajectory
+    int32_t ord;           // FCFS ordinal of the admitted request (see SepRowsArgs)
 };
 
 // Speculative batching: could request j's trajectory (as a stored plan) change request k's
@@ -205,7 +245,8 @@ cudaError_t launch_fill_nan(float* p, size_t n, cudaStream_t s);
 struct IndexArgs {
     TableView tab;
     int32_t* cstart;
-    int32_t* nextra;
+    int32_t* nextra;       // [T_win]: published extra-list length (readers scan this many)
+    int32_t* nres;         // [T_win]: extra-list positions handed out to appends
     int32_t* dirty;        // [T_win]: row must be rebuilt before its next use
     float4* items;
     int32_t ncx, ncy, ncell;
@@ -219,9 +260,13 @@ size_t index_build_smem(int ncell);
 cudaError_t prepare_index_kernels(size_t smem);
 // Appends the stored trajectories of the listed requests to the extra lists of their rows:
 // requests idx[0 .. *n_dev) (or 0 .. n-1), admitted ones only (SepOut verdict), samples
-// traj[r][0 .. rout[r].n_points) from step reqs[r].depart_step.
+// traj[r][0 .. rout[r].n_points) from step reqs[r].depart_step. An append takes positions
+// past the published length (nres) and writes its items there; launch_index_publish then
+// makes them visible, so a rollout that reads the index meanwhile never sees a partly
+// written item (each item is either absent or complete).
 struct IndexAppendArgs {
     IndexArgs ix;
+    const int32_t* slots;  // slot of request r (force mode: of plan r), stored in each item
     const float* traj;
     int32_t cap;
     const RolloutOut* rout;
@@ -236,6 +281,10 @@ struct IndexAppendArgs {
     const int64_t* offs;
 };
 cudaError_t launch_index_append(const IndexAppendArgs& a, int n_items, int max_points, cudaStream_t s);
+// Publishes the appended items of every row (nextra = nres); launched after the appends.
+cudaError_t launch_index_publish(const IndexArgs& a, cudaStream_t s);
+// *p = v with release semantics (a counter that readers acquire), one thread
+cudaError_t launch_store_release(int32_t* p, int32_t v, cudaStream_t s);
 // Separation check of a batch's work items, row by row: block b takes step t_base + b, the
 // samples of every work item at that step, and the row's plan samples (from the spatial
 // index when there is one, else the table planes). Same results as sepcheck_kernel.
@@ -256,6 +305,11 @@ struct SepRowsArgs {
     const int32_t* nextra;
     int32_t ncell;
     const int32_t* skip;    // request r is not checked when skip[r] (nullptr: none)
+    // ordinal filter (pipelined FCFS, where the table may already hold plans admitted after
+    // a request): request r is checked only against items whose slot's ordinal is below
+    // req_ord[r]; plans that were in the table before the call carry smaller ordinals
+    const int32_t* slot_ord;  // [S_pad] or nullptr (no filter)
+    const int32_t* req_ord;   // [n]
 };
 cudaError_t launch_sepcheck_rows(const SepRowsArgs& a, cudaStream_t s);
 size_t sepcheck_rows_smem(int n_max);

@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstring>
 #include <array>
+#include <atomic>
 #include <map>
 #include <new>
 #include <set>
@@ -100,6 +101,10 @@ struct Book {  // host bookkeeping of the table (copied by snapshot / restore)
 
 inline int32_t round_up(int32_t x, int32_t m) { return (x + m - 1) / m * m; }
 
+constexpr int32_t kExtraLimit = 48;  // appended items per index row before the row is rebuilt
+
+struct PipeState;  // pipelined FCFS (host_pipeline.cu)
+
 // Device buffers of one FCFS sequence run.
 struct SeqBuffers {
     DevArray<fmdp_request> reqs;
@@ -185,6 +190,7 @@ struct fmdp_ctx {
     bool index_on = false;
     int32_t* ix_cstart = nullptr;
     int32_t* ix_nextra = nullptr;
+    int32_t* ix_nres = nullptr;
     int32_t* ix_dirty = nullptr;
     float4* ix_items = nullptr;
     int32_t ix_ncx = 0, ix_ncy = 0, ix_ncell = 0;
@@ -276,6 +282,10 @@ struct fmdp_ctx {
     int last_cs = 1, last_threads = 256, last_chunk = 0;
     std::string err_msg;
 
+    // pipelined FCFS: streams, host-mapped ring and reports, ordinals (host_pipeline.cu)
+    PipeState* pipe = nullptr;
+    int32_t extra_limit = kExtraLimit;  // appended items per index row before it is marked dirty
+
     // allocation-free separation check: device address of the library's static scratch
     // array on this context's device (looked up by the context's first such call)
     void* noalloc_scratch = nullptr;
@@ -341,7 +351,6 @@ void grow_keep(fmdp_ctx* c, DevArray<T>& a, size_t want, size_t keep) {
 }
 // ------------------------------------------------------------------ shared constants
 
-constexpr int32_t kExtraLimit = 48;    // appended items per index row before the row is rebuilt
 constexpr int32_t kBatchDefault = 256;
 constexpr int32_t kBatchMax = 1024;
 
@@ -359,8 +368,9 @@ void index_rebuild(fmdp_ctx* c, int64_t a, int64_t b, bool dirty_only);
 void index_rebuild_all(fmdp_ctx* c);
 void index_reset(fmdp_ctx* c);
 void index_append_admitted(fmdp_ctx* c, const float* traj, int32_t cap, const RolloutOut* rout,
-                           const fmdp_request* reqs, const SepOut* sep, const int32_t* idx, const int32_t* n_dev,
-                           int32_t n_items, int64_t t_lo, int64_t t_hi);
+                           const fmdp_request* reqs, const SepOut* sep, const int32_t* slots, const int32_t* idx,
+                           const int32_t* n_dev, int32_t n_items, int64_t t_lo, int64_t t_hi,
+                           bool rebuild_dirty = true);
 bool fit_geometry(fmdp_ctx* c, Geometry& g, int cs);
 int32_t bit_length(int64_t v);
 int32_t batch_size_of(const fmdp_ctx* c);
@@ -421,6 +431,20 @@ void mlp_train(fmdp_ctx* c, int32_t epochs, int32_t batch, float lr, uint64_t se
 void learned_collect(fmdp_ctx* c, const fmdp_request* reqs, int32_t n);
 void learned_evaluate(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, double slack, fmdp_learned_report* rep,
                       int32_t* accepted, int32_t* steps_p, int32_t* steps_f);
+
+// ------------------------------------------------------------------ pipelined FCFS (host_pipeline.cu)
+
+// The arrival trace and options of a serving call.
+struct PipeServe {
+    const double* arrival_s;
+    fmdp_serve_options o;
+    double* latency_ms;
+    fmdp_serve_report* rep;
+};
+bool pipeline_eligible(const fmdp_ctx* c);
+int32_t run_pipeline(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_result* res,
+                     const fmdp_request* dev_reqs, bool keep_points, const PipeServe* serve);
+void pipe_release(fmdp_ctx* c);
 
 // ------------------------------------------------------------------ serving (host_serve.cu)
 

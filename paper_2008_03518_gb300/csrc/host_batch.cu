@@ -16,7 +16,7 @@ namespace fmdp {
 // its plan stays exact against the grown table. Each wave finalises at least one request.
 
 // kernels of one wave: admit, reset, rollout, sep_check, influence (+ index append, rebuild)
-int wave_kernels(const fmdp_ctx* c) { return (c->index_on ? 7 : 5) + (c->learned_mode ? 4 : 0); }
+int wave_kernels(const fmdp_ctx* c) { return (c->index_on ? 8 : 5) + (c->learned_mode ? 4 : 0); }
 
 // Batch geometry: the narrowest cluster whose partition fits one CTA's shared memory, so
 // that as many rollouts as possible run side by side.
@@ -80,7 +80,7 @@ void enqueue_wave(fmdp_ctx* c, const Geometry& g, int n_clusters, BatchBuffers& 
         KernelTimer t(c, timed ? 2 : -1);
         LAUNCH(c, launch_admit(aa, n_cap, cap, s));
         t.stop();
-        index_append_admitted(c, B.traj.p, cap, B.rout.p, B.rq, B.sepo.p, store, B.ctr.p + 3, n_cap,
+        index_append_admitted(c, B.traj.p, cap, B.rout.p, B.rq, B.sepo.p, slots, store, B.ctr.p + 3, n_cap,
                               c->book.t_base, c->book.t_base + c->T_win);
     }
     LAUNCH(c, launch_sep_reset_idx(B.sepo.p, todo, B.ctr.p + 1, n_cap, s));
@@ -378,6 +378,7 @@ void copy_points_back(fmdp_ctx* c, int32_t n, fmdp_result* res) {
 int32_t run_batch(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_result* res,
                   const fmdp_request* dev_reqs, bool keep_points) {
     if (n <= 0) return 0;
+    if (pipeline_eligible(c)) return run_pipeline(c, reqs, n, res, dev_reqs, keep_points, nullptr);
     const int32_t bs = c->opt.batch_size > 0 ? c->opt.batch_size : kBatchDefault;
     batch_prepare(c, reqs, n, std::min(n, bs), dev_reqs);
     if (c->learned_mode) {
@@ -518,7 +519,7 @@ void run_departures(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, const int6
                 aa.force = 0;
                 LAUNCH(c, launch_admit(aa, 1, B.cap, c->stream));
                 const int64_t d0 = cand[pick].depart_step;
-                index_append_admitted(c, aa.traj, B.cap, aa.rout, aa.reqs, aa.sep, nullptr, nullptr, 1, d0,
+                index_append_admitted(c, aa.traj, B.cap, aa.rout, aa.reqs, aa.sep, aa.slots, nullptr, nullptr, 1, d0,
                                       d0 + cand[pick].horizon + 1);
                 CK(cudaStreamSynchronize(c->stream));
             } catch (...) {

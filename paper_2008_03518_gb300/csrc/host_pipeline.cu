@@ -1,0 +1,750 @@
+// Pipelined speculative FCFS: continuous batching without waves.
+//
+// First-come-first-served planning (Sec. I, Sec. V) admits request k against every plan
+// admitted before it. Speculative batching plans many requests at once and keeps a plan
+// only when no earlier admission could have changed it (the influence test). Here the
+// planning never stops at a wave boundary:
+//   - one persistent rollout launch (one CTA per work item) takes work items from a ring
+//     in host-mapped memory that the host appends to while the launch runs;
+//   - each finished plan is checked for conflicts against the plans the index holds at
+//     that moment and reported, with its trajectory, to host-mapped memory;
+//   - the host walks the requests in arrival order as their plans land: a request is final
+//     once every admission made after its plan was dispatched has been tested and none
+//     influences it; an admitted request is stored at once (scatter into the plan table,
+//     index append, publish) on a high-priority table stream, beside the running rollouts;
+//   - a plan that an admission influences is planned again as soon as that admission is
+//     visible, without waiting for any other rollout.
+// Exactness. A rollout reads the index while admissions are appended to it. An appended
+// item becomes visible only when it is complete (published after its append kernel), so a
+// rollout sees, at every step, each admitted plan's sample either whole or not at all. A
+// plan that does not influence request k adds an exact zero to every value k's rollout
+// computes whether it is visible or not, so k's plan equals its plan against any table
+// between the one at its dispatch and the final one, unless an admission made after the
+// dispatch influences it - and each of those is tested. The index only ever holds plans of
+// requests before the one being planned (the walk admits in arrival order and stops at the
+// first unresolved request), so a conflict found against it is real; an unseen admission
+// that could add a conflict influences the plan (separation minima + 1 m). Row rebuilds,
+// which move items, happen only while no rollout runs. The exact separation report of each
+// request (minimum separations to every earlier plan) comes from the row-major check with
+// an ordinal filter: it skips plans admitted after the request.
+#include "host.cuh"
+
+namespace fmdp {
+
+namespace {
+
+// Pinned host memory mapped into the device address space.
+template <class T>
+struct MappedArray {
+    T* p = nullptr;  // host pointer
+    T* d = nullptr;  // device pointer of the same memory
+    size_t n = 0;
+    void ensure(size_t want) {
+        if (want <= n) return;
+        release();
+        const size_t m = std::max<size_t>(want, 16);
+        CK(cudaHostAlloc((void**)&p, m * sizeof(T), cudaHostAllocMapped | cudaHostAllocPortable));
+        n = m;
+        CK(cudaHostGetDevicePointer((void**)&d, p, 0));
+    }
+    void release() {
+        if (p) cudaFreeHost(p);
+        p = d = nullptr;
+        n = 0;
+    }
+};
+
+constexpr int kQueueCap = 4096;          // ring entries (a power of two)
+constexpr int kBoxChunk = 32;            // steps per bounding box of a trajectory
+constexpr int32_t kPipeExtraLimit = 96;  // appended items per row before the rows are rebuilt
+constexpr int32_t kOrdLimit = 1 << 30;   // ordinals are rebased before they reach this
+
+}  // namespace
+
+struct PipeState {
+    cudaStream_t pstream = nullptr;  // the persistent rollout launch
+    cudaStream_t tstream = nullptr;  // table operations (admission, index, expiry), high priority
+    cudaEvent_t kern_ev = nullptr;   // recorded after each persistent launch
+    cudaEvent_t sync_ev = nullptr;
+    MappedArray<PipeItem> ring;
+    MappedArray<int32_t> ctl;  // [0] tail, [1] stop
+    MappedArray<int32_t> done;
+    MappedArray<PipeRecord> rec;
+    MappedArray<float> h_traj;
+    MappedArray<int32_t> h_slot;  // slot of an admitted request (read by its admission)
+    MappedArray<int32_t> h_obs;   // per plan step: admissions published when its rows were read
+    DevArray<int32_t> head, pub_seq, obs;
+    DevArray<SepOut> sep;
+    DevArray<int32_t> slot_ord, req_ord, list, nlist;
+    PinnedArray<int32_t> h_list;
+    std::vector<cudaEvent_t> ev_free;
+    int32_t ord_base = 0;
+    bool ord_init = false;
+    ~PipeState() {
+        if (pstream) cudaStreamSynchronize(pstream);
+        if (tstream) cudaStreamSynchronize(tstream);
+        ring.release(); ctl.release(); done.release(); rec.release(); h_traj.release(); h_slot.release();
+        h_obs.release(); pub_seq.release(); obs.release();
+        head.release(); sep.release(); slot_ord.release(); req_ord.release(); list.release(); nlist.release();
+        h_list.release();
+        for (cudaEvent_t e : ev_free) cudaEventDestroy(e);
+        if (kern_ev) cudaEventDestroy(kern_ev);
+        if (sync_ev) cudaEventDestroy(sync_ev);
+        if (pstream) cudaStreamDestroy(pstream);
+        if (tstream) cudaStreamDestroy(tstream);
+    }
+};
+
+void pipe_release(fmdp_ctx* c) {
+    delete c->pipe;
+    c->pipe = nullptr;
+}
+
+bool pipeline_eligible(const fmdp_ctx* c) {
+    return c->index_on && window_of(c) == 1 && !c->learned_mode && c->opt.batch_mode == 0 && c->model.A <= 32;
+}
+
+namespace {
+
+// ---------------------------------------------------------------- influence (host side)
+
+// Bounding boxes of a trajectory over chunks of kBoxChunk steps, its largest speed, and for
+// each chunk the fewest admissions any of its steps could see (obs: per step, or null).
+struct TrajBoxes {
+    std::vector<float> b;    // [chunks][6]: min x y z, max x y z
+    std::vector<int32_t> o;  // [chunks]: smallest obs of the chunk's decision steps
+    double vmax = 0.0;
+    void build(const float* p, int n, double dt, const int32_t* obs = nullptr) {
+        const int nc = (n + kBoxChunk - 1) / kBoxChunk;
+        b.assign((size_t)nc * 6, 0.f);
+        o.assign(nc, INT32_MAX);
+        if (obs)
+            for (int i = 0; i + 1 < n; ++i) o[i / kBoxChunk] = std::min(o[i / kBoxChunk], obs[i]);
+        double v2 = 0.0;
+        for (int c = 0; c < nc; ++c) {
+            float* o = b.data() + 6 * c;
+            o[0] = o[1] = o[2] = INFINITY;
+            o[3] = o[4] = o[5] = -INFINITY;
+            for (int i = c * kBoxChunk; i < std::min(n, (c + 1) * kBoxChunk); ++i)
+                for (int a = 0; a < 3; ++a) {
+                    o[a] = std::min(o[a], p[3 * i + a]);
+                    o[3 + a] = std::max(o[3 + a], p[3 * i + a]);
+                }
+        }
+        for (int i = 0; i + 1 < n; ++i) {
+            const double dx = p[3 * i + 3] - p[3 * i], dy = p[3 * i + 4] - p[3 * i + 1], dz = p[3 * i + 5] - p[3 * i + 2];
+            v2 = std::max(v2, dx * dx + dy * dy + dz * dz);
+        }
+        vmax = std::sqrt(v2) / dt;
+    }
+};
+
+struct InflRule {
+    double dt, H, V, dzmax;
+    int n_wells;
+    double tau[kMaxWells], R[kMaxWells];
+};
+
+// Could plan j (admitted as the call's admission number aj, before k) change request k's
+// plan or verdict? The rule of the batched path's influence kernel (one-step window), taken
+// only where k's rollout could not see j: k's state at a step whose index rows were read
+// before j was published (obs_k[i] <= aj) within reach of one of j's wells one step later
+// (well w at p_j + tau_w v_j, radius R_w, reach R_w + the successor offset + 1 m); or, when
+// k's conflict check read the index before j was published (aj >= tail_pub), the two within
+// the separation minima + 1 m at one step. At a step that saw j, k's decision already
+// counted j's wells exactly. Chunk bounding boxes skip the steps where the two are far apart.
+bool influences(const InflRule& P, const float* pj, int nj, int64_t tj, const TrajBoxes& bj, int32_t aj,
+                const float* pk, int nk, int64_t tk, double speed_k, const TrajBoxes& bk, const int32_t* obs_k,
+                int32_t tail_pub) {
+    if (nk <= 0 || nj <= 0 || !(tk < tj + nj && tj < tk + nk)) return false;
+    const bool sep_unseen = aj >= tail_pub;
+    const double rho = speed_k * P.dt + P.dzmax + 1.0;
+    double e = std::max(P.H, P.V);
+    for (int w = 0; w < P.n_wells; ++w) e = std::max(e, P.R[w] + 1.0 + rho + std::fabs(P.tau[w]) * bj.vmax);
+    e += 1.0;
+    const int nck = (nk + kBoxChunk - 1) / kBoxChunk;
+    for (int c = 0; c < nck; ++c) {
+        const int i0 = c * kBoxChunk, i1 = std::min(nk, i0 + kBoxChunk);
+        if (!sep_unseen && bk.o[c] > aj) continue;  // every step of the chunk saw j
+        // j's samples a step of this chunk can meet: the same step, the next, and the one
+        // after it (the next sample's velocity)
+        const int64_t jlo = std::max<int64_t>(0, tk + i0 - tj), jhi = std::min<int64_t>(nj - 1, tk + i1 - 1 - tj + 2);
+        if (jlo > jhi) continue;
+        float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+        for (int64_t q = jlo / kBoxChunk; q <= jhi / kBoxChunk; ++q) {
+            const float* o = bj.b.data() + 6 * q;
+            for (int a = 0; a < 3; ++a) {
+                lo[a] = std::min(lo[a], o[a]);
+                hi[a] = std::max(hi[a], o[3 + a]);
+            }
+        }
+        const float* ok = bk.b.data() + 6 * c;
+        bool apart = false;
+        for (int a = 0; a < 3; ++a) apart = apart || ok[a] > hi[a] + e || ok[3 + a] < lo[a] - e;
+        if (apart) continue;
+        for (int i = i0; i < i1; ++i) {
+            const double sx = pk[3 * i], sy = pk[3 * i + 1], sz = pk[3 * i + 2];
+            const int64_t t0 = tk + i - tj;
+            if (sep_unseen && t0 >= 0 && t0 < nj) {
+                const double dx = sx - pj[3 * t0], dy = sy - pj[3 * t0 + 1], dz = sz - pj[3 * t0 + 2];
+                if (dx * dx + dy * dy < P.H * P.H && std::fabs(dz) < P.V) return true;
+            }
+            const int64_t t1 = t0 + 1;
+            if (i + 1 >= nk || obs_k[i] > aj || t1 < 0 || t1 >= nj) continue;  // no decision, or it saw j
+            const float* q1 = pj + 3 * t1;
+            double vx = 0.0, vy = 0.0, vz = 0.0;
+            if (t1 + 1 < nj) {
+                vx = ((double)q1[3] - q1[0]) / P.dt;
+                vy = ((double)q1[4] - q1[1]) / P.dt;
+                vz = ((double)q1[5] - q1[2]) / P.dt;
+            }
+            for (int w = 0; w < P.n_wells; ++w) {
+                const double r = P.R[w] + 1.0 + rho;
+                const double dx = sx - (q1[0] + P.tau[w] * vx), dy = sy - (q1[1] + P.tau[w] * vy),
+                             dz = sz - (q1[2] + P.tau[w] * vz);
+                if (dx * dx + dy * dy + dz * dz < r * r) return true;
+            }
+        }
+    }
+    return false;
+}
+
+enum Phase : uint8_t { kAbsent = 0, kWait = 1, kFlight = 2, kDone = 3, kFinal = 4 };
+
+}  // namespace
+
+// One pipelined call (see the top of this file). serve == nullptr: every request is there
+// from the start (fmdp_schedule_batch); else the arrival trace and options of fmdp_serve.
+int32_t run_pipeline(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_result* res,
+                     const fmdp_request* dev_reqs, bool keep_points, const PipeServe* serve) {
+    using clk = std::chrono::steady_clock;
+    if (n <= 0) return 0;
+    require(pipeline_eligible(c), FMDP_ERR_ARG, "internal: pipelined FCFS needs the index and W = 1");
+    const int32_t bs = c->opt.batch_size > 0 ? c->opt.batch_size : kBatchDefault;
+    int32_t window = std::max(1, std::min(bs, kBatchMax));
+    if (serve && serve->o.max_in_flight > 0) window = std::min(serve->o.max_in_flight, kBatchMax);
+    batch_prepare(c, reqs, n, window, dev_reqs);
+    BatchBuffers& B = c->bat;
+    const int32_t cap = B.cap;
+    if (!c->pipe) c->pipe = new PipeState();
+    PipeState& P = *c->pipe;
+    if (!P.tstream) {
+        int lo = 0, hi = 0;
+        CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+        CK(cudaStreamCreateWithPriority(&P.tstream, cudaStreamNonBlocking, hi));
+        CK(cudaStreamCreateWithPriority(&P.pstream, cudaStreamNonBlocking, lo));
+        CK(cudaEventCreateWithFlags(&P.kern_ev, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&P.sync_ev, cudaEventDisableTiming));
+    }
+    const size_t R = B.rq_cap;
+    P.ring.ensure(kQueueCap);
+    P.ctl.ensure(2);
+    P.done.ensure(R);
+    P.rec.ensure(R);
+    P.h_traj.ensure(R * (size_t)cap * 3);
+    P.h_slot.ensure(R);
+    P.h_obs.ensure(R * (size_t)cap);
+    P.obs.ensure(R * (size_t)cap);
+    P.pub_seq.ensure(1);
+    P.head.ensure(1);
+    P.sep.ensure(R);
+    P.req_ord.ensure(R);
+    P.list.ensure(kBatchMax);
+    P.nlist.ensure(1);
+    P.h_list.ensure(kBatchMax + 1);
+    if (!P.ord_init || P.ord_base + n >= kOrdLimit) {  // every stored plan counts as earlier
+        P.slot_ord.ensure(c->S_pad);
+        CK(cudaMemsetAsync(P.slot_ord.p, 0x80, (size_t)c->S_pad * sizeof(int32_t), c->stream));  // INT_MIN-ish
+        P.ord_base = 0;
+        P.ord_init = true;
+    }
+    const int32_t ord0 = P.ord_base;
+    P.ord_base += n;
+
+    // streams: the call's table operations go to the table stream (c->stream is swapped for
+    // the call), after the work already on the caller's stream
+    cudaStream_t user = c->stream;
+    CK(cudaEventRecord(P.sync_ev, user));
+    CK(cudaStreamWaitEvent(P.tstream, P.sync_ev, 0));
+    CK(cudaStreamWaitEvent(P.pstream, P.sync_ev, 0));
+    c->stream = P.tstream;
+    const int32_t saved_limit = c->extra_limit;
+    c->extra_limit = INT32_MAX;  // rows are rebuilt only by the pipeline's own drains
+
+    // per-request state
+    std::vector<uint8_t> phase(n, serve ? kAbsent : kWait);  // a batch's requests are all there
+    std::vector<int32_t> seen(n, 0), chk(n, 0), gate(n, 0), tok(n, 0), slot_of(n, -1), verdict(n, -1),
+        replans(n, 0), tail_pub(n, 0);
+    std::vector<uint64_t> ids(n, 0);
+    std::vector<RolloutOut> fin_ro(n);
+    std::vector<TrajBoxes> boxes(n);
+    std::vector<double> t_disp(n, 0.0), done_at(n, -1.0);
+    std::vector<int32_t> A;  // admitted requests in admission (= arrival) order
+    std::vector<int32_t> inflight;
+    struct Pub {
+        int32_t a;
+        cudaEvent_t ev;
+    };
+    std::vector<Pub> pend;  // admissions enqueued, not yet known complete
+    size_t pend_head = 0;
+    int32_t pub = 0;        // admissions whose table writes have completed
+    std::vector<int32_t> xcnt(c->T_win, 0);
+    int32_t xmax = 0;
+    bool draining = false;
+    cudaEvent_t rebuild_ev = nullptr;
+    std::vector<int32_t> unreported;
+    for (int32_t k = 0; k < n; ++k) P.done.p[k] = 0;
+    // ordinals of the call's requests, for the exact separation report
+    {
+        std::vector<int32_t> ho(n);
+        for (int32_t k = 0; k < n; ++k) ho[k] = ord0 + k;
+        CK(cudaMemcpyAsync(P.req_ord.p, ho.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, P.tstream));
+        CK(cudaStreamSynchronize(P.tstream));
+    }
+
+    InflRule rule{};
+    rule.dt = c->model.dt;
+    rule.H = c->sep.horiz_m + 1.0;
+    rule.V = c->sep.vert_m + 1.0;
+    rule.dzmax = climb_step(c);
+    rule.n_wells = c->model.n_wells;
+    for (int w = 0; w < rule.n_wells; ++w) {
+        rule.tau[w] = c->model.w_tau64[w];
+        rule.R[w] = c->model.w_R64[w];
+    }
+
+    // launch shape: the tuned indexed rollout shape; persistent CTAs leave room on a few SMs
+    // for the table stream's kernels
+    Geometry g = geometry_batch(c, c->S_pad, window);
+    const int resident = rollout_max_active_clusters(1, g.threads, g.smem);
+    require(resident >= 1, FMDP_ERR_ARG, "the rollout shape does not fit an SM");
+    const int per_sm = std::max(1, resident / std::max(1, c->n_sm));
+    const int reserve = per_sm * std::max(4, c->n_sm / 16);
+    const int n_ctas = std::max(1, std::min(resident - reserve, window));
+
+    RolloutArgs ra{};
+    ra.m = c->model;
+    ra.S_scan = g.S_scan;
+    ra.chunk = g.chunk;
+    ra.cs = 1;
+    ra.ring = g.ring;
+    ra.cap = cap;
+    ra.reqs = B.rq;
+    ra.n_req = n;
+    ra.traj = B.traj.p;
+    ra.acts = B.acts.p;
+    ra.out = B.rout.p;
+    ra.err = c->err;
+    ra.pipe.on = 1;
+    ra.pipe.qmask = kQueueCap - 1;
+    ra.pipe.items = P.ring.d;
+    ra.pipe.tail = P.ctl.d;
+    ra.pipe.stop = P.ctl.d + 1;
+    ra.pipe.head = P.head.p;
+    ra.pipe.done = P.done.d;
+    ra.pipe.rec = P.rec.d;
+    ra.pipe.h_traj = P.h_traj.d;
+    ra.pipe.sep = P.sep.p;
+    ra.pipe.idle_cycles = 1ll << 31;  // about a second without work
+    ra.pipe.pub_seq = P.pub_seq.p;
+    ra.pipe.obs = P.obs.p;
+    ra.pipe.h_obs = P.h_obs.d;
+    CK(cudaMemsetAsync(P.pub_seq.p, 0, sizeof(int32_t), P.tstream));
+    int32_t tail = 0;
+    P.ctl.p[0] = 0;
+    P.ctl.p[1] = 0;
+    CK(cudaMemsetAsync(P.head.p, 0, sizeof(int32_t), P.pstream));
+    bool launched = false;
+    auto launch = [&]() {
+        ra.tab = table_view(c);
+        set_index_args(c, ra, g);
+        std::atomic_thread_fence(std::memory_order_seq_cst);
+        LAUNCH(c, launch_rollout(ra, g.threads, g.smem, P.pstream, n_ctas));
+        CK(cudaEventRecord(P.kern_ev, P.pstream));
+        launched = true;
+    };
+    auto kernel_running = [&]() {
+        if (!launched) return false;
+        const cudaError_t e = cudaEventQuery(P.kern_ev);
+        if (e == cudaErrorNotReady) return true;
+        CK(e);
+        return false;
+    };
+    auto stop_kernel = [&]() {  // every CTA leaves once the ring is empty
+        if (!launched) return;
+        std::atomic_thread_fence(std::memory_order_seq_cst);
+        *reinterpret_cast<volatile int32_t*>(P.ctl.p + 1) = 1;
+        CK(cudaEventSynchronize(P.kern_ev));
+        launched = false;
+        *reinterpret_cast<volatile int32_t*>(P.ctl.p + 1) = 0;
+    };
+
+    const auto t0 = clk::now();
+    auto elapsed = [&]() { return std::chrono::duration<double>(clk::now() - t0).count(); };
+    double cta_time = 0.0, last_progress = 0.0;
+    int64_t n_dispatch = 0, n_replans = 0, n_drains = 0, steps_sum = 0;
+    int32_t head = 0, joined = serve ? 0 : n, finalized = 0, admitted = 0, max_seen = 0;
+    int64_t expiries = 0, expired = 0;
+    int32_t deferred = 0;
+    std::vector<uint8_t> deferred_flag(serve ? n : 0, 0);
+    std::vector<int64_t> dep_suffix;
+    int64_t sim0 = 0, quantum = 60;
+    double scale = 1.0;
+    int32_t max_active = c->S_max;
+    if (serve) {
+        dep_suffix.assign(n + 1, INT64_MAX);
+        for (int32_t i = n - 1; i >= 0; --i) dep_suffix[i] = std::min(dep_suffix[i + 1], reqs[i].depart_step);
+        sim0 = serve->o.sim_start_set ? serve->o.sim_start_step : c->book.t_base;
+        quantum = serve->o.expire_quantum > 0 ? serve->o.expire_quantum : 60;
+        scale = serve->o.time_scale > 0.0 ? serve->o.time_scale : 1.0;
+        max_active = serve->o.max_active_plans > 0 ? std::min(serve->o.max_active_plans, c->S_max) : c->S_max;
+    }
+
+    // the exact separation report (row-major check with the ordinal filter) of the listed
+    // requests, on the table stream, into B.sepo
+    auto report = [&](std::vector<int32_t>& L) {
+        for (size_t o = 0; o < L.size(); o += kBatchMax) {
+            const int32_t m = (int32_t)std::min<size_t>(kBatchMax, L.size() - o);
+            std::copy(L.begin() + o, L.begin() + o + m, P.h_list.p);
+            P.h_list.p[kBatchMax] = m;
+            CK(cudaMemcpyAsync(P.list.p, P.h_list.p, m * sizeof(int32_t), cudaMemcpyHostToDevice, P.tstream));
+            CK(cudaMemcpyAsync(P.nlist.p, P.h_list.p + kBatchMax, sizeof(int32_t), cudaMemcpyHostToDevice,
+                               P.tstream));
+            LAUNCH(c, launch_sep_reset_idx(B.sepo.p, P.list.p, P.nlist.p, m, P.tstream));
+            SepRowsArgs sp{};
+            sp.m = c->model;
+            sp.tab = table_view(c);
+            sp.S_scan = c->S_pad;
+            sp.traj = B.traj.p;
+            sp.cap = cap;
+            sp.rout = B.rout.p;
+            sp.reqs = B.rq;
+            sp.idx = P.list.p;
+            sp.n_dev = P.nlist.p;
+            sp.n_max = m;
+            sp.out = B.sepo.p;
+            sp.items = c->ix_items;
+            sp.cstart = c->ix_cstart;
+            sp.nextra = c->ix_nextra;
+            sp.ncell = c->ix_ncell;
+            sp.slot_ord = P.slot_ord.p;
+            sp.req_ord = P.req_ord.p;
+            {
+                KernelTimer t(c, 1);
+                LAUNCH(c, launch_sepcheck_rows(sp, P.tstream));
+                t.stop();
+            }
+            CK(cudaStreamSynchronize(P.tstream));  // the staging list is reused by the next chunk
+            for (int32_t i = 0; i < m; ++i) c->stats.sep_pairs += (int64_t)fin_ro[L[o + i]].n_points * c->S_pad;
+        }
+        L.clear();
+    };
+    // stores an admitted request: scatter, index append and publish on the table stream
+    auto admit = [&](int32_t k) {
+        const int32_t slot = take_slot(c);
+        const uint64_t id = c->book.next_id++;
+        c->book.plans[id] = PlanMeta{slot, reqs[k].depart_step, fin_ro[k].n_points};
+        c->book.S_hw = std::max(c->book.S_hw, slot + 1);
+        slot_of[k] = slot;
+        ids[k] = id;
+        P.h_slot.p[k] = slot;
+        std::atomic_thread_fence(std::memory_order_seq_cst);
+        AdmitArgs aa{};
+        aa.err = c->err;
+        aa.tab = table_view(c);
+        aa.cap = cap;
+        aa.traj = B.traj.p + (size_t)k * cap * 3;
+        aa.rout = B.rout.p + k;
+        aa.reqs = B.rq + k;
+        aa.slots = P.h_slot.d + k;
+        aa.sep = P.sep.p + k;
+        aa.force = 0;
+        aa.slot_ord = P.slot_ord.p;
+        aa.ord = ord0 + k;
+        {
+            KernelTimer t(c, 2);
+            LAUNCH(c, launch_admit(aa, 1, fin_ro[k].n_points, P.tstream));
+            t.stop();
+        }
+        index_append_admitted(c, aa.traj, cap, aa.rout, aa.reqs, aa.sep, aa.slots, nullptr, nullptr, 1,
+                              c->book.t_base, c->book.t_base + c->T_win, false);
+        LAUNCH(c, launch_store_release(P.pub_seq.p, (int32_t)A.size() + 1, P.tstream));  // this one is visible
+        cudaEvent_t ev;
+        if (P.ev_free.empty()) {
+            CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        } else {
+            ev = P.ev_free.back();
+            P.ev_free.pop_back();
+        }
+        CK(cudaEventRecord(ev, P.tstream));
+        pend.push_back({(int32_t)A.size(), ev});
+        A.push_back(k);
+        ++admitted;
+        // the rows the plan was appended to (host count of each row's extra list)
+        const int64_t d = reqs[k].depart_step;
+        for (int32_t i = 0; i < fin_ro[k].n_points; ++i) {
+            const int64_t T = d + i;
+            if (T < c->book.t_base || T >= c->book.t_base + c->T_win) continue;
+            int64_t row = T % c->T_win;
+            if (row < 0) row += c->T_win;
+            xmax = std::max(xmax, ++xcnt[row]);
+        }
+    };
+    // brings request k's completed plan up to date with the admissions made since its
+    // dispatch; false (and k waits for a new plan) when one of them influences it
+    auto check_plan = [&](int32_t k) {
+        const int32_t nk = fin_ro[k].n_points;
+        const float* pk = P.h_traj.p + (size_t)k * cap * 3;
+        while (chk[k] < (int32_t)A.size()) {
+            const int32_t j = A[chk[k]];
+            const float* pj = P.h_traj.p + (size_t)j * cap * 3;
+            if (influences(rule, pj, fin_ro[j].n_points, reqs[j].depart_step, boxes[j], chk[k], pk, nk,
+                           reqs[k].depart_step, reqs[k].speed_mps, boxes[k], P.h_obs.p + (size_t)k * cap,
+                           tail_pub[k])) {
+                phase[k] = kWait;
+                gate[k] = (int32_t)A.size();  // every admission so far visible to the next plan
+                ++replans[k];
+                ++n_replans;
+                return false;
+            }
+            ++chk[k];
+        }
+        return true;
+    };
+    auto dispatch = [&](int32_t k) {
+        tok[k] += 1;
+        seen[k] = pub;
+        chk[k] = pub;
+        PipeItem& it = P.ring.p[tail & (kQueueCap - 1)];
+        it.r = k;
+        it.token = tok[k];
+        std::atomic_thread_fence(std::memory_order_release);
+        *reinterpret_cast<volatile int32_t*>(P.ctl.p) = ++tail;
+        inflight.push_back(k);
+        phase[k] = kFlight;
+        t_disp[k] = elapsed();
+        ++n_dispatch;
+    };
+
+    try {
+        launch();
+        while (finalized < n) {
+            const double now = elapsed();
+            bool progress = false;
+            // admissions whose table writes are complete
+            while (pend_head < pend.size()) {
+                const cudaError_t e = cudaEventQuery(pend[pend_head].ev);
+                if (e == cudaErrorNotReady) break;
+                CK(e);
+                pub = pend[pend_head].a + 1;
+                P.ev_free.push_back(pend[pend_head].ev);
+                ++pend_head;
+                progress = true;
+            }
+            // finished plans
+            for (size_t q = 0; q < inflight.size();) {
+                const int32_t k = inflight[q];
+                if (*reinterpret_cast<volatile int32_t*>(P.done.p + k) != tok[k]) {
+                    ++q;
+                    continue;
+                }
+                std::atomic_thread_fence(std::memory_order_acquire);
+                inflight[q] = inflight.back();
+                inflight.pop_back();
+                const PipeRecord rc = P.rec.p[k];
+                fin_ro[k] = rc.ro;
+                steps_sum += rc.ro.steps;
+                c->stats.slots_scanned += (int64_t)rc.ro.steps * g.S_scan;
+                cta_time += now - t_disp[k];
+                verdict[k] = rc.ro.status != kStatusCaptured ? rc.ro.status
+                             : rc.first_conflict >= 0       ? FMDP_REJ_CONFLICT
+                             : rc.first_terrain >= 0        ? FMDP_REJ_TERRAIN
+                                                            : FMDP_ADMITTED;
+                boxes[k].build(P.h_traj.p + (size_t)k * cap * 3, rc.ro.n_points, c->model.dt,
+                               P.h_obs.p + (size_t)k * cap);
+                tail_pub[k] = rc.tail_pub;
+                phase[k] = kDone;
+                progress = true;
+            }
+            // walk in arrival order; plans behind the head are checked against each admission
+            // (every plan in flight or done lies within the window past the head)
+            for (int32_t k = head; k < std::min(joined, head + window); ++k)
+                if (phase[k] == kDone && chk[k] < (int32_t)A.size()) check_plan(k);
+            while (head < joined && phase[head] == kDone && (chk[head] == (int32_t)A.size() || check_plan(head))) {
+                const int32_t k = head;
+                if (verdict[k] == FMDP_ADMITTED) admit(k);
+                phase[k] = kFinal;
+                done_at[k] = elapsed();
+                unreported.push_back(k);
+                ++head;
+                ++finalized;
+                progress = true;
+                for (int32_t q = head; q < std::min(joined, head + window); ++q)
+                    if (phase[q] == kDone && chk[q] < (int32_t)A.size()) check_plan(q);
+            }
+            if (progress) last_progress = now;
+            if (finalized >= n) break;
+
+            // serving: expiry (a drain: the persistent launch holds the window's first step)
+            bool want_expiry = false;
+            int64_t limit = INT64_MIN;
+            if (serve) {
+                limit = sim0 + (int64_t)std::floor(now * scale / c->air.dt);
+                limit = std::min(limit, dep_suffix[joined]);
+                for (int32_t k = head; k < joined; ++k) limit = std::min(limit, reqs[k].depart_step);
+                want_expiry = limit >= c->book.t_base + quantum;
+            }
+            if (!draining && (xmax > kPipeExtraLimit || want_expiry)) draining = true;
+            if (draining && inflight.empty()) {
+                stop_kernel();  // the idle CTAs give their SMs to the rebuild
+                if (want_expiry) {
+                    report(unreported);  // before the rows of finished requests can be cleared
+                    expire_to(c, limit, &expired);
+                    ++expiries;
+                    std::fill(xcnt.begin(), xcnt.end(), 0);
+                    xmax = 0;
+                }
+                if (xmax > kPipeExtraLimit) {  // rows whose extra lists grew long: rebuilt now
+                    index_rebuild_all(c);
+                    std::fill(xcnt.begin(), xcnt.end(), 0);
+                    xmax = 0;
+                    ++n_drains;
+                }
+                if (!rebuild_ev) CK(cudaEventCreateWithFlags(&rebuild_ev, cudaEventDisableTiming));
+                CK(cudaEventRecord(rebuild_ev, P.tstream));
+                draining = false;
+            }
+            // serving: arrivals join while the set has room and the table has slots for all
+            if (serve) {
+                while (joined < n && serve->arrival_s[joined] <= now && joined - head < window) {
+                    const int64_t active = (int64_t)c->book.plans.size();
+                    const int64_t room = std::min<int64_t>((int64_t)c->book.free_slots.size(), max_active - active);
+                    if ((int64_t)(joined - head) + 1 > room) {
+                        if (!deferred_flag[joined]) {
+                            deferred_flag[joined] = 1;
+                            ++deferred;
+                        }
+                        break;
+                    }
+                    phase[joined] = kWait;
+                    ++joined;
+                }
+                max_seen = std::max(max_seen, joined - head);
+            }
+            // dispatch the waiting requests nearest the head, their admissions visible
+            const bool rebuilt = !rebuild_ev || cudaEventQuery(rebuild_ev) == cudaSuccess;
+            if (!draining && rebuilt) {
+                const int32_t end = std::min(joined, head + window);
+                for (int32_t k = head; k < end && (int32_t)inflight.size() < n_ctas; ++k)
+                    if (phase[k] == kWait && gate[k] <= pub) dispatch(k);
+            }
+            if (!inflight.empty() && !kernel_running()) {
+                require(read_error_word(c) == 0, FMDP_ERR_TIMEOUT, "a bounded device wait expired during a rollout");
+                launch();  // the launch left while idle; the ring keeps its position
+            }
+            if (serve && inflight.empty() && head == joined && joined < n) {
+                const double wait = serve->arrival_s[joined] - elapsed();
+                if (wait > 0) std::this_thread::sleep_for(std::chrono::duration<double>(std::min(wait, 0.002)));
+                if (joined - head == 0 && deferred_flag[joined] && c->book.plans.size() > 0) {
+                    int64_t first_end = INT64_MAX;  // nothing in flight and no room: only expiry frees slots
+                    for (auto& kv : c->book.plans) first_end = std::min(first_end, kv.second.t0 + kv.second.n);
+                    require(first_end <= dep_suffix[joined], FMDP_ERR_FULL, "plan table full and no plan can expire");
+                }
+                last_progress = elapsed();
+            }
+            require(elapsed() - last_progress < 30.0, FMDP_ERR_TIMEOUT, "pipelined FCFS made no progress for 30 s");
+        }
+        stop_kernel();
+        report(unreported);
+        CK(cudaStreamSynchronize(P.tstream));
+        require(read_error_word(c) == 0, FMDP_ERR_TIMEOUT, "a bounded device wait expired during a rollout");
+    } catch (...) {
+        // leave nothing running: stop the launch (it drains the ring), wait for the streams
+        if (launched) {
+            *reinterpret_cast<volatile int32_t*>(P.ctl.p + 1) = 1;
+            cudaEventSynchronize(P.kern_ev);
+            *reinterpret_cast<volatile int32_t*>(P.ctl.p + 1) = 0;
+        }
+        cudaStreamSynchronize(P.tstream);
+        if (rebuild_ev) cudaEventDestroy(rebuild_ev);
+        c->extra_limit = saved_limit;
+        c->stream = user;
+        throw;
+    }
+    if (rebuild_ev) cudaEventDestroy(rebuild_ev);
+    for (size_t q = pend_head; q < pend.size(); ++q) P.ev_free.push_back(pend[q].ev);
+    c->extra_limit = saved_limit;
+    c->stream = user;
+    CK(cudaEventRecord(P.sync_ev, P.tstream));
+    CK(cudaStreamWaitEvent(user, P.sync_ev, 0));
+    if (c->profiling) collect_timers(c);
+
+    // results: verdict from the tail check, separation report from the exact pass
+    CK(cudaMemcpyAsync(B.h_sep.p, B.sepo.p, n * sizeof(SepOut), cudaMemcpyDeviceToHost, user));
+    CK(cudaStreamSynchronize(user));
+    for (int32_t k = 0; k < n; ++k) {
+        SepOut so = B.h_sep.p[k];
+        const int32_t fc = so.first_conflict == INT_MAX ? -1 : so.first_conflict;
+        const int32_t ft = so.first_terrain == INT_MAX ? -1 : so.first_terrain;
+        require(fc == P.rec.p[k].first_conflict && ft == P.rec.p[k].first_terrain, FMDP_ERR_CUDA,
+                "internal: the exact separation report disagrees with the rollout's conflict check");
+        so.verdict = verdict[k];
+        fill_result(fin_ro[k], so, res + k);
+        res[k].plan_id = ids[k];
+        res[k].replanned = replans[k];
+    }
+    c->stats.batch_rollouts += n_dispatch;
+    c->stats.batch_replans += n_replans;
+    c->stats.rollout_steps += steps_sum;
+    c->stats.pipe_drains += n_drains;
+    const double wall = elapsed();
+    c->stats.pipe_cta_s += cta_time;
+    c->stats.pipe_slot_s += wall * n_ctas;
+    c->stats.pipe_ctas = n_ctas;
+    c->stats.pipe_resident = resident;
+    if (!keep_points) copy_points_back(c, n, res);
+    if (serve) {
+        std::vector<double> lat(n);
+        double mx = 0.0, sum = 0.0, last = 0.0;
+        for (int32_t i = 0; i < n; ++i) {
+            lat[i] = 1e3 * std::max(0.0, done_at[i] - serve->arrival_s[i]);
+            if (serve->latency_ms) serve->latency_ms[i] = lat[i];
+            mx = std::max(mx, lat[i]);
+            sum += lat[i];
+            last = std::max(last, done_at[i]);
+        }
+        if (serve->rep) {
+            std::vector<double> sorted = lat;
+            std::sort(sorted.begin(), sorted.end());
+            auto pct = [&](double q) {
+                const size_t i = (size_t)std::min<double>((double)sorted.size() - 1, std::ceil(q * sorted.size()) - 1);
+                return sorted[i];
+            };
+            fmdp_serve_report& r = *serve->rep;
+            r = fmdp_serve_report{};
+            r.wall_s = last;
+            r.throughput_rps = last > 0.0 ? n / last : 0.0;
+            r.latency_p50_ms = pct(0.50);
+            r.latency_p99_ms = pct(0.99);
+            r.latency_mean_ms = sum / n;
+            r.latency_max_ms = mx;
+            r.waves = 0;
+            r.rollouts = n_dispatch;
+            r.replans = n_replans;
+            r.expiries = expiries;
+            r.plans_expired = expired;
+            r.final_t_base = c->book.t_base;
+            r.admitted = admitted;
+            r.rejected = n - admitted;
+            r.max_in_flight_seen = max_seen;
+            r.deferred_for_memory = deferred;
+            r.pipelined = 1;
+            r.drains = n_drains;
+            r.rollout_occupancy = wall > 0.0 ? cta_time / (wall * n_ctas) : 0.0;
+            r.persistent_ctas = n_ctas;
+        }
+    }
+    return admitted;
+}
+
+}  // namespace fmdp

@@ -10,6 +10,11 @@ namespace fmdp {
 // Continuous batching over an arrival trace (see fmdp_serve in the header).
 void run_serve(fmdp_ctx* c, const fmdp_request* reqs, const double* arrival_s, int32_t n,
                const fmdp_serve_options& o, fmdp_result* res, double* latency_ms, fmdp_serve_report* rep) {
+    if (pipeline_eligible(c)) {  // continuous batching without waves (host_pipeline.cu)
+        const PipeServe ps{arrival_s, o, latency_ms, rep};
+        run_pipeline(c, reqs, n, res, nullptr, false, &ps);
+        return;
+    }
     using clk = std::chrono::steady_clock;
     const int32_t bs = c->opt.batch_size > 0 ? c->opt.batch_size : kBatchDefault;
     const int32_t in_flight = std::max(1, std::min(o.max_in_flight > 0 ? o.max_in_flight : bs, kBatchMax));

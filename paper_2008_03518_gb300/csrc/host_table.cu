@@ -106,6 +106,7 @@ IndexArgs index_args(fmdp_ctx* c) {
     a.tab = table_view(c);
     a.cstart = c->ix_cstart;
     a.nextra = c->ix_nextra;
+    a.nres = c->ix_nres;
     a.dirty = c->ix_dirty;
     a.items = c->ix_items;
     a.ncx = c->ix_ncx;
@@ -116,7 +117,7 @@ IndexArgs index_args(fmdp_ctx* c) {
     a.inv_cell = c->ix_inv;
     a.vmax = c->ix_vmax;
     a.inv_dt = (float)(1.0 / c->air.dt);
-    a.extra_limit = kExtraLimit;
+    a.extra_limit = c->extra_limit;
     return a;
 }
 
@@ -154,16 +155,19 @@ void index_reset(fmdp_ctx* c) {
     if (!c->index_on) return;
     CK(cudaMemsetAsync(c->ix_cstart, 0, ((size_t)c->T_win * (c->ix_ncell + 1) + 16) * sizeof(int32_t), c->stream));
     CK(cudaMemsetAsync(c->ix_nextra, 0, ((size_t)c->T_win + 16) * sizeof(int32_t), c->stream));
+    CK(cudaMemsetAsync(c->ix_nres, 0, ((size_t)c->T_win + 16) * sizeof(int32_t), c->stream));
     CK(cudaMemsetAsync(c->ix_dirty, 0, (size_t)c->T_win * sizeof(int32_t), c->stream));
 }
 // Appends admitted trajectories (request work items; see IndexAppendArgs) to the extra
-// lists of their rows, then rebuilds the rows that grew past the limit among [a, b).
+// lists of their rows and publishes them; then (rebuild_dirty) rebuilds the rows that grew
+// past the limit among [a, b).
 void index_append_admitted(fmdp_ctx* c, const float* traj, int32_t cap, const RolloutOut* rout,
-                           const fmdp_request* reqs, const SepOut* sep, const int32_t* idx, const int32_t* n_dev,
-                           int32_t n_items, int64_t a, int64_t b) {
+                           const fmdp_request* reqs, const SepOut* sep, const int32_t* slots, const int32_t* idx,
+                           const int32_t* n_dev, int32_t n_items, int64_t a, int64_t b, bool rebuild_dirty) {
     if (!c->index_on) return;
     IndexAppendArgs ia{};
     ia.ix = index_args(c);
+    ia.slots = slots;
     ia.traj = traj;
     ia.cap = cap;
     ia.rout = rout;
@@ -172,7 +176,8 @@ void index_append_admitted(fmdp_ctx* c, const float* traj, int32_t cap, const Ro
     ia.idx = idx;
     ia.n_dev = n_dev;
     LAUNCH(c, launch_index_append(ia, n_items, cap, c->stream));
-    index_rebuild(c, a, b, true);
+    LAUNCH(c, launch_index_publish(ia.ix, c->stream));
+    if (rebuild_dirty) index_rebuild(c, a, b, true);
 }
 
 // ------------------------------------------------------------------ launch geometry
@@ -389,7 +394,7 @@ void enqueue_sequence(fmdp_ctx* c, SeqBuffers& B, const fmdp_request* host_reqs,
         }
         // an admitted trajectory joins the index before the next request plans
         const int64_t d0 = host_reqs[i].depart_step;
-        index_append_admitted(c, ra.traj, cap, ra.out, ra.reqs, sa.out, nullptr, nullptr, 1, d0,
+        index_append_admitted(c, ra.traj, cap, ra.out, ra.reqs, sa.out, aa.slots, nullptr, nullptr, 1, d0,
                               d0 + host_reqs[i].horizon + 1);
     }
 }
@@ -474,12 +479,14 @@ void store_plans(fmdp_ctx* c, int32_t n_plans, const int64_t* t0s, const int32_t
             if (n_plans <= 8) {  // a few plans: append them to their rows' extra lists
                 IndexAppendArgs ia{};
                 ia.ix = index_args(c);
+                ia.slots = c->slots.p;
                 ia.traj = c->traj.p;
                 ia.force = 1;
                 ia.t0s = c->t0s.p;
                 ia.counts = c->counts.p;
                 ia.offs = c->offs.p;
                 LAUNCH(c, launch_index_append(ia, n_plans, maxc, c->stream));
+                LAUNCH(c, launch_index_publish(ia.ix, c->stream));
                 index_rebuild(c, tlo, thi, true);
             } else {
                 index_rebuild(c, tlo, thi, false);
@@ -546,12 +553,13 @@ void expire_to(fmdp_ctx* c, int64_t t_now, int64_t* n_expired) {
 void destroy_ctx(fmdp_ctx* c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
+    pipe_release(c);
     for (float* p : {c->X, c->Y, c->Z, c->sX, c->sY, c->sZ})
         if (p) cudaFree(p);
     if (c->hm) cudaFree(c->hm);
     if (c->statics) cudaFree(c->statics);
     if (c->err) cudaFree(c->err);
-    for (void* p : {(void*)c->ix_cstart, (void*)c->ix_nextra, (void*)c->ix_dirty, (void*)c->ix_items,
+    for (void* p : {(void*)c->ix_cstart, (void*)c->ix_nextra, (void*)c->ix_nres, (void*)c->ix_dirty, (void*)c->ix_items,
                     (void*)c->items_ctr})
         if (p) cudaFree(p);
     c->seq.release(); c->stg.release(); c->bat.release();

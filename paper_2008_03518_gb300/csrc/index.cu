@@ -119,6 +119,7 @@ __global__ void __launch_bounds__(kBuildThreads) index_build_kernel(const __grid
     for (int i = tid; i < nc1; i += NT) cs_row[i] = cnt[i];
     if (tid == 0) {
         a.nextra[row] = n_extra;
+        a.nres[row] = n_extra;
         a.dirty[row] = 0;
     }
     __syncthreads();
@@ -130,7 +131,7 @@ __global__ void __launch_bounds__(kBuildThreads) index_build_kernel(const __grid
         const float x2 = has_next ? a.tab.X[o2 + s] : nanv;
         const float y2 = has_next ? a.tab.Y[o2 + s] : nanv, z2 = has_next ? a.tab.Z[o2 + s] : nanv;
         const int pos = atomicAdd(&cnt[item_class(a, x1, y1, z1, x2, y2, z2)], 1);
-        it[2 * pos] = make_float4(x1, y1, z1, 0.f);
+        it[2 * pos] = make_float4(x1, y1, z1, __int_as_float(s));
         it[2 * pos + 1] = make_float4(x2, y2, z2, 0.f);
     }
 }
@@ -140,11 +141,12 @@ __global__ void __launch_bounds__(kBuildThreads) index_build_kernel(const __grid
 // last built, so a row never holds more than S_pad items.
 __global__ void index_append_kernel(const __grid_constant__ IndexAppendArgs a) {
     const IndexArgs& ix = a.ix;
-    int n;
+    int n, slot;
     int64_t t0;
     const float* base;
     if (a.force) {
         const int r = blockIdx.y;
+        slot = a.slots[r];
         n = a.counts[r];
         t0 = a.t0s[r];
         base = a.traj + (size_t)a.offs[r] * 3;
@@ -152,6 +154,7 @@ __global__ void index_append_kernel(const __grid_constant__ IndexAppendArgs a) {
         if (a.n_dev && (int)blockIdx.y >= *a.n_dev) return;
         const int r = a.idx ? a.idx[blockIdx.y] : (int)blockIdx.y;
         if (a.sep[r].verdict != FMDP_ADMITTED) return;
+        slot = a.slots[r];
         n = a.rout[r].n_points;
         t0 = a.reqs[r].depart_step;
         base = a.traj + (size_t)r * a.cap * 3;
@@ -165,18 +168,41 @@ __global__ void index_append_kernel(const __grid_constant__ IndexAppendArgs a) {
         const int64_t row = ring_of(T, W);
         const float* p = base + 3 * (size_t)k;
         const bool has_next = k + 1 < n && T + 1 < ix.tab.t_base + W;
-        const int pos = atomicAdd(&ix.nextra[row], 1);
+        const int pos = atomicAdd(&ix.nres[row], 1);
         const int at = ix.cstart[row * (int64_t)(ix.ncell + 1) + ix.ncell] + pos;
         if (at < S) {
             float4* it = ix.items + (size_t)row * S * 2;
-            it[2 * at] = make_float4(p[0], p[1], p[2], 0.f);
+            it[2 * at] = make_float4(p[0], p[1], p[2], __int_as_float(slot));
             it[2 * at + 1] = has_next ? make_float4(p[3], p[4], p[5], 0.f) : make_float4(nanv, nanv, nanv, 0.f);
         } else {
-            atomicSub(&ix.nextra[row], 1);  // cannot happen (see above); rebuild the row instead
+            atomicSub(&ix.nres[row], 1);  // cannot happen (see above); rebuild the row instead
             ix.dirty[row] = 1;
         }
         if (pos + 1 > ix.extra_limit) ix.dirty[row] = 1;
     }
+}
+
+// nextra = nres for every row: the items appended by earlier launches on this stream
+// become visible to readers (stream order: those launches have completed).
+__global__ void index_publish_kernel(int32_t* nextra, const int32_t* nres, int32_t n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) nextra[i] = nres[i];
+}
+
+cudaError_t launch_index_publish(const IndexArgs& a, cudaStream_t s) {
+    const int n = a.tab.T_win;
+    if (n <= 0) return cudaSuccess;
+    index_publish_kernel<<<(n + 255) / 256, 256, 0, s>>>(a.nextra, a.nres, n);
+    return cudaGetLastError();
+}
+
+__global__ void store_release_kernel(int32_t* p, int32_t v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+cudaError_t launch_store_release(int32_t* p, int32_t v, cudaStream_t s) {
+    store_release_kernel<<<1, 1, 0, s>>>(p, v);
+    return cudaGetLastError();
 }
 
 size_t index_build_smem(int ncell) { return (size_t)(ncell + 1 + 32) * sizeof(int); }

@@ -29,6 +29,7 @@
 #include <climits>
 
 #include "fmdp_internal.cuh"
+#include "sep_pair.cuh"
 
 namespace fmdp {
 
@@ -115,6 +116,11 @@ __device__ __forceinline__ int ld_cluster_s32(uint32_t addr) {
     asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
     return v;
 }
+__device__ __forceinline__ int ld_acquire_gpu(const int32_t* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
 __device__ __forceinline__ void mbar_inval(uint64_t* bar) {
     asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
@@ -173,7 +179,8 @@ struct StepState {
 // shared memory; the rest are read from the index in global memory through the ranges.
 constexpr int kMaxRanges = 8;
 struct IdxMeta {
-    int total, n_s, nr, pad;
+    int total, n_s, nr;
+    int pub;  // pipelined mode: admissions published when the extra list's length was read
     long long row_off;  // first float4 of the row's items
     int beg[kMaxRanges], cnt[kMaxRanges];
 };
@@ -226,8 +233,10 @@ __host__ __device__ inline Layout make_layout(int chunk, int depth, int icap) {
     al(16);
     L.aux = o;   // valid, Delta, deck, goal term; key, class, log2|Q|, log2 scale by step parity
     o += 12 * kMaxActions * sizeof(int);
-    L.misc = o;  // work-queue slot of the persistent batch mode
-    o += 16;
+    L.misc = o;  // work-queue slot of the persistent batch mode; pipelined mode: [0..2] the
+                 // item taken, [4..6] the tail check's first conflict and terrain sample and
+                 // the admissions published before it read the index
+    o += 32;
     L.total = (o + 127) & ~size_t(127);
     return L;
 }
@@ -647,7 +656,7 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
     };
     // lanes 0 .. kMaxRanges-1 each carry one item range (cnt 0: none): record them in
     // buffer b's metadata and copy the first icap items into shared memory
-    auto issue_items = [&](int b, int my_beg, int my_cnt, long long row_off) {
+    auto issue_items = [&](int b, int my_beg, int my_cnt, long long row_off, int pub) {
         IdxMeta& M = imeta_all[b];
         int total;
         const int off = excl_scan(lane < kMaxRanges ? my_cnt : 0, total);
@@ -661,6 +670,7 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
             M.n_s = n_s;
             M.nr = kMaxRanges;
             M.row_off = row_off;
+            M.pub = pub;
             if (a.items_ctr && total > 0) atomicAdd(a.items_ctr, (unsigned long long)total);
             if (n_s > 0) mbar_arrive_expect_tx(&bars[b], (uint32_t)n_s * 32u);
             else mbar_arrive(&bars[b]);
@@ -689,25 +699,32 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
     auto issue_direct = [&](int b, int64_t T, int64_t row, float sx, float sy, float R) {
         int my_beg = 0, my_cnt = 0;
         long long row_off = 0;
+        int pub = INT_MAX;  // pipelined mode: published admissions this query can see (all: none in the row)
         if (T >= t_lo && T < t_hi) {
             const int32_t* cs_row = iv.cstart + row * cst_row_len;
             const Box q = box_of(sx, sy, R);
             int e0 = 0, e1 = 0;
+            // L2 loads (.cg): the index may change between launches of a persistent kernel
+            // (rows rebuilt, extra lists published), so nothing of it is kept in L1
             if (!q.whole && lane < q.nrows) {
-                e0 = cs_row[(q.cy0 + lane) * iv.ncx + q.cx0];
-                e1 = cs_row[(q.cy0 + lane) * iv.ncx + q.cx1 + 1];
+                e0 = __ldcg(cs_row + (q.cy0 + lane) * iv.ncx + q.cx0);
+                e1 = __ldcg(cs_row + (q.cy0 + lane) * iv.ncx + q.cx1 + 1);
             } else if (q.whole && lane == 0) {
-                e0 = cs_row[q.cy0 * iv.ncx];
-                e1 = cs_row[(q.cy1 + 1) * iv.ncx];
+                e0 = __ldcg(cs_row + q.cy0 * iv.ncx);
+                e1 = __ldcg(cs_row + (q.cy1 + 1) * iv.ncx);
             } else if (lane == kMaxRanges - 1) {
-                e0 = cs_row[iv.ncell];
-                e1 = e0 + iv.nextra[row];
+                // the count of published admissions first (acquire), then the extra list's
+                // length: every admission counted is in the list this query copies
+                if (a.pipe.pub_seq) pub = ld_acquire_gpu(a.pipe.pub_seq);
+                e0 = __ldcg(cs_row + iv.ncell);
+                e1 = e0 + __ldcg(iv.nextra + row);
             }
             my_beg = e0;
             my_cnt = max(0, e1 - e0);
             row_off = (long long)row * a.tab.S_pad * 2;
         }
-        issue_items(b, my_beg, my_cnt, row_off);
+        pub = __shfl_sync(kFull, pub, kMaxRanges - 1);
+        issue_items(b, my_beg, my_cnt, row_off, pub);
     };
     // L2 prefetch of the cell starts a query of step T would read (issued one step early, so
     // that the next step's issue finds them in L2 instead of waiting on DRAM)
@@ -983,8 +1000,8 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
                         int q = 0, off = i;
                         while (q < M.nr - 1 && off >= M.cnt[q]) { off -= M.cnt[q]; ++q; }
                         const float4* g = a.iv.items + M.row_off + 2ll * (M.beg[q] + off);
-                        P1 = g[0];
-                        P2 = g[1];
+                        P1 = __ldcg(g);
+                        P2 = __ldcg(g + 1);
                     }
                     p1x = P1.x; p1y = P1.y; p1z = P1.z;
                     p2x = P2.x; p2y = P2.y; p2z = P2.z;
@@ -1225,6 +1242,7 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
                     traj[3 * np + 1] = tfy;
                     traj[3 * np + 2] = tfz;
                     acts[k] = (uint8_t)best;
+                    if (a.pipe.obs) a.pipe.obs[(size_t)r * a.cap + k] = imeta[k % kIBufs].pub;
                     if (a.trace && r == 0) {
                         a.st_trace[3 * np] = X;
                         a.st_trace[3 * np + 1] = Y;
@@ -1292,10 +1310,177 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
         for (int i = 0; i < 6; ++i)
             if (ph[i]) atomicAdd(&a.phase[i], ph[i]);
     if (cs > 1) cluster_barrier(); else __syncthreads();  // peers may still address this CTA's shared memory
-    if (a.queue && tid == 0) {  // the next request of this CTA initialises them again
+    if ((a.queue || a.pipe.on) && tid == 0) {  // the next request of this CTA initialises them again
         for (int e = 0; e < kRingDepth; ++e) mbar_inval(&bars[e]);
         mbar_inval(&xbar[0]);
         mbar_inval(&xbar[1]);
+    }
+}
+
+// ---------------------------------------------------------------- pipelined FCFS
+
+__device__ __forceinline__ int ld_acquire_sys(const int32_t* p) {
+    int v;
+    asm volatile("ld.acquire.sys.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ int ld_volatile_sys(const int32_t* p) {
+    int v;
+    asm volatile("ld.volatile.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_sys(int32_t* p, int v) {
+    asm volatile("st.release.sys.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Takes the next work item of the host-fed ring (thread 0). Returns its ring position, or
+// -1 when the CTA should leave: the host asked it to stop and the ring is empty, no work
+// came for idle_cycles, or a bounded wait of another CTA expired.
+__device__ int pipe_take(const RolloutArgs& a, int* r_out, int* tok_out) {
+    const PipeArgs& p = a.pipe;
+    long long t0 = clock64();
+    unsigned ns = 32;
+    for (;;) {
+        if (*reinterpret_cast<volatile const int32_t*>(a.err) != 0) return -1;
+        const int h = *reinterpret_cast<volatile int32_t*>(p.head);
+        const int t = ld_acquire_sys(p.tail);
+        if (h < t) {
+            if (atomicCAS(p.head, h, h + 1) == h) {
+                const PipeItem* it = p.items + (h & p.qmask);
+                *r_out = ld_volatile_sys(&it->r);
+                *tok_out = ld_volatile_sys(&it->token);
+                return h;
+            }
+            continue;
+        }
+        if (ld_volatile_sys(p.stop)) return -1;
+        if (clock64() - t0 > p.idle_cycles) return -1;
+        __nanosleep(ns);
+        ns = ns < 4096 ? 2 * ns : 4096;
+    }
+}
+
+// After a pipelined plan: its conflicts and terrain collisions against the plans the index
+// holds now (each sample against the items of its step within the horizontal minimum, by
+// cell, and the row's extra list), its trajectory and report to host-mapped memory, then
+// its completion token. The index only ever holds plans admitted before this request (the
+// host admits in arrival order and never past an unresolved request), so a conflict found
+// here is one the sequential order has too; a later admission that could conflict with it
+// is caught by the host's influence test, which replans it.
+__device__ void pipe_finish(const RolloutArgs& a, int r, int token, int* red) {
+    int& s_first = red[0];
+    int& s_terr = red[1];
+    const int tid = threadIdx.x, NT = blockDim.x;
+    if (tid == 0) {
+        s_first = INT_MAX;
+        s_terr = INT_MAX;
+        red[2] = INT_MAX;
+    }
+    // admissions published before this thread's index reads (all of them are seen)
+    const int my_pub = a.pipe.pub_seq ? ld_acquire_gpu(a.pipe.pub_seq) : INT_MAX;
+    __syncthreads();
+    atomicMin(&red[2], my_pub);
+    const RolloutOut ro = a.out[r];
+    const fmdp_request& rq = a.reqs[r];
+    const int n = ro.n_points;
+    const float* traj = a.traj + (size_t)r * a.cap * 3;
+    const Model& m = a.m;
+    const IndexView& iv = a.iv;
+    const SepConsts sk = sep_consts(m.sep_h, m.sep_v);
+    const float reach = (float)m.sep_h + kSepBand + 1.0f;
+    const int64_t cst_row_len = (int64_t)iv.ncell + 1;
+    int first = INT_MAX, terr = INT_MAX;
+    auto cell_of = [&](float v, float o, int nc) {
+        const float f = floorf((v - o) * iv.inv_cell);
+        return f < 0.f ? 0 : (f > (float)(nc - 1) ? nc - 1 : (int)f);
+    };
+    for (int i = tid; i < n; i += NT) {
+        const float px = traj[3 * i], py = traj[3 * i + 1], pz = traj[3 * i + 2];
+        if (m.hm && below_terrain(m, px, py, pz)) terr = min(terr, i);
+        if (i >= first) continue;  // a later sample cannot lower this thread's first conflict
+        const int64_t T = rq.depart_step + i;
+        if (T < a.tab.t_base || T >= a.tab.t_base + a.tab.T_win) continue;
+        int64_t row = T % a.tab.T_win;
+        if (row < 0) row += a.tab.T_win;
+        const int32_t* cs_row = iv.cstart + row * cst_row_len;
+        const float4* items = iv.items + (size_t)row * a.tab.S_pad * 2;
+        const int cx0 = cell_of(px - reach, iv.x0, iv.ncx), cx1 = cell_of(px + reach, iv.x0, iv.ncx);
+        const int cy0 = cell_of(py - reach, iv.y0, iv.ncy), cy1 = cell_of(py + reach, iv.y0, iv.ncy);
+        bool hit = false;
+        for (int cy = cy0; cy <= cy1 + 1 && !hit; ++cy) {
+            int b, e;
+            if (cy <= cy1) {
+                b = __ldcg(cs_row + cy * iv.ncx + cx0);
+                e = __ldcg(cs_row + cy * iv.ncx + cx1 + 1);
+            } else {  // the extra list
+                b = __ldcg(cs_row + iv.ncell);
+                e = b + __ldcg(iv.nextra + row);
+            }
+            for (int j = b; j < e; ++j) {
+                const float4 Q = __ldcg(items + 2 * (size_t)j);
+                float h2, dz;
+                bool hin, vin;
+                sep_pair(sk, px, py, pz, Q.x, Q.y, Q.z, h2, dz, hin, vin);
+                if (hin && vin) {
+                    hit = true;
+                    break;
+                }
+            }
+        }
+        if (hit) first = i;
+    }
+    if (first != INT_MAX) atomicMin(&s_first, first);
+    if (terr != INT_MAX) atomicMin(&s_terr, terr);
+    // trajectory to the host, 12-byte samples as 4-byte words
+    float* dst = a.pipe.h_traj + (size_t)r * a.cap * 3;
+    for (int i = tid; i < 3 * n; i += NT) dst[i] = traj[i];
+    const int32_t* obs = a.pipe.obs + (size_t)r * a.cap;
+    int32_t* hobs = a.pipe.h_obs + (size_t)r * a.cap;
+    for (int i = tid; i < n - 1; i += NT) hobs[i] = obs[i];
+    __threadfence_system();
+    __syncthreads();
+    if (tid == 0) {
+        SepOut so;
+        so.first_conflict = s_first;
+        so.first_terrain = s_terr;
+        so.conflicts = 0ull;
+        so.min_h_bits = 0x7f800000u;
+        so.min_v_bits = 0x7f800000u;
+        so.verdict = -1;
+        so.pad = 0;
+        a.pipe.sep[r] = so;
+        PipeRecord* rec = a.pipe.rec + r;
+        rec->ro = ro;
+        rec->first_conflict = s_first == INT_MAX ? -1 : s_first;
+        rec->first_terrain = s_terr == INT_MAX ? -1 : s_terr;
+        rec->tail_pub = red[2];
+        __threadfence_system();
+        st_release_sys(a.pipe.done + r, token);
+    }
+    __syncthreads();
+}
+
+// Persistent pipelined launch (indexed mode, one CTA per work item): plans the items the
+// host appends to the ring until it is told to stop, stays idle too long, or a wait expires.
+__device__ void pipe_loop(const RolloutArgs& a, unsigned char* smem) {
+    const Layout L = make_layout(a.chunk, a.ring, a.icap);
+    int* slot = reinterpret_cast<int*>(smem + L.misc);  // [0] ring position, [1] request, [2] token
+    for (;;) {
+        if (threadIdx.x == 0) {
+            int r = 0, tok = 0;
+            const int w = pipe_take(a, &r, &tok);
+            slot[0] = w;
+            slot[1] = r;
+            slot[2] = tok;
+        }
+        __syncthreads();
+        const int w = reinterpret_cast<volatile int*>(slot)[0];
+        const int r = reinterpret_cast<volatile int*>(slot)[1];
+        const int tok = reinterpret_cast<volatile int*>(slot)[2];
+        __syncthreads();
+        if (w < 0) break;
+        plan_request(a, r, smem);
+        pipe_finish(a, r, tok, slot + 4);
     }
 }
 
@@ -1305,6 +1490,10 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
 // takes the item and its peers read it from the lead's shared memory.
 __global__ void __launch_bounds__(384, 1) rollout_kernel(const __grid_constant__ RolloutArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
+    if (a.pipe.on) {
+        pipe_loop(a, smem);
+        return;
+    }
     if (a.queue == nullptr) {
         const int r = blockIdx.x / a.cs;
         if (r < a.n_req) plan_request(a, r, smem);  // uniform over the cluster

@@ -153,7 +153,7 @@ struct Speculator {
             KernelTimer t(c, 2);
             LAUNCH(c, launch_admit(aa, n_cap, B.cap, c->stream));
             t.stop();
-            index_append_admitted(c, B.traj.p, B.cap, B.rout.p, B.rq, B.sepo.p, aa.idx, aa.n_dev, n_cap,
+            index_append_admitted(c, B.traj.p, B.cap, B.rout.p, B.rq, B.sepo.p, aa.slots, aa.idx, aa.n_dev, n_cap,
                                   c->book.t_base, c->book.t_base + c->T_win);
         }
         // the admission list may be longer than the index block's first array: own buffer

@@ -9,6 +9,7 @@
 #include <climits>
 
 #include "fmdp_internal.cuh"
+#include "sep_pair.cuh"
 
 namespace fmdp {
 
@@ -21,49 +22,6 @@ constexpr int kSepSlotsPerCta = kSepThreads * kSepSlotsPerThread;
 __device__ __forceinline__ int64_t ring_row(int64_t T, int32_t T_win) {
     int64_t r = T % T_win;
     return r < 0 ? r + T_win : r;
-}
-
-// Separation minima of one sample pair with explicit rounding (no contraction), so that
-// every kernel that measures the same pair gets the same bits. Thresholds in the band
-// around H^2 and V are decided again in FP64 from the same fp32 inputs.
-struct SepConsts {
-    float H2, Vm, hband;
-    double H2d, Vd;
-};
-__device__ __forceinline__ SepConsts sep_consts(double sep_h, double sep_v) {
-    SepConsts k;
-    const float H = (float)sep_h;
-    k.H2 = __fmul_rn(H, H);
-    k.Vm = (float)sep_v;
-    k.hband = 2.0f * H * kSepBand + kSepBand * kSepBand;
-    k.H2d = __dmul_rn(sep_h, sep_h);
-    k.Vd = sep_v;
-    return k;
-}
-// FP64 decisions inside the bands, kept out of line: inlined, the compiler may evaluate
-// them for every pair (predicated), and FP64 runs at a small fraction of the FP32 rate here
-__device__ __noinline__ bool hin_exact(float px, float py, float qx, float qy, double H2d) {
-    const double ex = __dsub_rn((double)px, (double)qx);
-    const double ey = __dsub_rn((double)py, (double)qy);
-    return __dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)) < H2d;
-}
-__device__ __noinline__ bool vin_exact(float pz, float qz, double Vd) {
-    return fabs(__dsub_rn((double)pz, (double)qz)) < Vd;
-}
-__device__ __noinline__ bool below_terrain_exact(const Model& m, float x, float y, float z) {
-    return (double)z < terrain64(m, (double)x, (double)y);
-}
-
-// h2: squared horizontal distance, dz: |vertical distance|; hin / vin: inside the minima
-__device__ __forceinline__ void sep_pair(const SepConsts& k, float px, float py, float pz, float qx, float qy,
-                                         float qz, float& h2, float& dz, bool& hin, bool& vin) {
-    const float dx = __fsub_rn(px, qx), dy = __fsub_rn(py, qy);
-    dz = fabsf(__fsub_rn(pz, qz));
-    h2 = __fmaf_rn(dx, dx, __fmul_rn(dy, dy));
-    hin = h2 < k.H2;  // NaN (empty slot): false
-    vin = dz < k.Vm;
-    if (fabsf(h2 - k.H2) < k.hband) hin = hin_exact(px, py, qx, qy, k.H2d);
-    if (fabsf(dz - k.Vm) < kSepBand) vin = vin_exact(pz, qz, k.Vd);
 }
 
 }  // namespace
@@ -185,6 +143,7 @@ __global__ void admit_kernel(const __grid_constant__ AdmitArgs a) {
         t0 = a.reqs[r].depart_step;
         off = (size_t)r * a.cap;
     }
+    if (a.slot_ord && blockIdx.x == 0 && threadIdx.x == 0) a.slot_ord[slot] = a.ord;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         const size_t row = (size_t)ring_row(t0 + k, a.tab.T_win) * a.tab.S_pad + slot;
         const float* p = a.traj + (off + k) * 3;
@@ -269,7 +228,8 @@ constexpr int kRowThreads = 256;
 constexpr int kRowTile = 2048;
 
 size_t sepcheck_rows_smem(int n_max) {
-    return (size_t)kRowTile * sizeof(float4) + (size_t)n_max * (sizeof(float4) + 2 * sizeof(int)) + 16;
+    return (size_t)kRowTile * (sizeof(float4) + sizeof(int)) + (size_t)n_max * (sizeof(float4) + 3 * sizeof(int)) +
+           16;
 }
 
 __global__ void __launch_bounds__(kRowThreads) sepcheck_rows_kernel(const __grid_constant__ SepRowsArgs a) {
@@ -278,7 +238,9 @@ __global__ void __launch_bounds__(kRowThreads) sepcheck_rows_kernel(const __grid
     float4* pts = tile + kRowTile;
     int* pr = reinterpret_cast<int*>(pts + a.n_max);
     int* pk = pr + a.n_max;
-    int* npts_s = pk + a.n_max;
+    int* po = pk + a.n_max;       // ordinal of the sample's request (ordinal filter)
+    int* tord = po + a.n_max;     // [kRowTile] ordinal of the tile's items' slots
+    int* npts_s = tord + kRowTile;
     const int tid = threadIdx.x, NT = blockDim.x;
     const int32_t W = a.tab.T_win;
     const int64_t T = a.tab.t_base + blockIdx.x;
@@ -299,6 +261,7 @@ __global__ void __launch_bounds__(kRowThreads) sepcheck_rows_kernel(const __grid
             pts[q] = make_float4(p[0], p[1], p[2], 0.f);
             pr[q] = r;
             pk[q] = k;
+            po[q] = a.slot_ord ? a.req_ord[r] : 0;
         }
     }
     __syncthreads();
@@ -335,6 +298,8 @@ __global__ void __launch_bounds__(kRowThreads) sepcheck_rows_kernel(const __grid
         const int q = pg + tid % P, g = tid / P;
         const bool act = g < G;
         const float4 P4 = act ? pts[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const int my_ord = act ? po[q] : 0;
+        const bool filt = a.slot_ord != nullptr && it != nullptr;
         unsigned cnt = 0;
         float minh2 = INFINITY, minv = INFINITY;
         for (int s0 = 0; s0 < nslots; s0 += kRowTile) {
@@ -342,7 +307,12 @@ __global__ void __launch_bounds__(kRowThreads) sepcheck_rows_kernel(const __grid
             __syncthreads();
             for (int j = tid; j < tn; j += NT) {
                 if (it) {
-                    tile[j] = it[2 * (size_t)(s0 + j)];
+                    const float4 Q = it[2 * (size_t)(s0 + j)];
+                    tile[j] = Q;
+                    if (filt) {  // an item outside the slot range would count as earlier (unfiltered)
+                        const int sl = __float_as_int(Q.w);
+                        tord[j] = (unsigned)sl < (unsigned)a.tab.S_pad ? a.slot_ord[sl] : INT_MIN;
+                    }
                 } else {
                     const size_t o = poff + s0 + j;
                     tile[j] = make_float4(a.tab.X[o], a.tab.Y[o], a.tab.Z[o], 0.f);
@@ -353,6 +323,7 @@ __global__ void __launch_bounds__(kRowThreads) sepcheck_rows_kernel(const __grid
 #pragma unroll 4
                 for (int j = g; j < tn; j += G) {
                     const float4 Q = tile[j];
+                    if (filt && tord[j] >= my_ord) continue;  // admitted after this request
                     float h2, dz;
                     bool hin, vin;
                     sep_pair(sk, P4.x, P4.y, P4.z, Q.x, Q.y, Q.z, h2, dz, hin, vin);

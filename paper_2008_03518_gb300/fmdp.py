@@ -55,7 +55,7 @@ class Options(ctypes.Structure):
                 ("goal_reward", ctypes.c_double), ("lookahead_W", ctypes.c_int32),
                 ("cluster_size", ctypes.c_int32), ("threads_per_cta", ctypes.c_int32), ("batch_size", ctypes.c_int32),
                 ("full_scan", ctypes.c_int32), ("index_vmax_mps", ctypes.c_double), ("index_cell_m", ctypes.c_double),
-                ("index_stage_items", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("index_stage_items", ctypes.c_int32), ("batch_mode", ctypes.c_int32)]
 
 
 class Request(ctypes.Structure):
@@ -117,7 +117,8 @@ class ServeReport(ctypes.Structure):
                 ("waves", ctypes.c_int64), ("rollouts", ctypes.c_int64), ("replans", ctypes.c_int64),
                 ("expiries", ctypes.c_int64), ("plans_expired", ctypes.c_int64), ("final_t_base", ctypes.c_int64),
                 ("admitted", ctypes.c_int32), ("rejected", ctypes.c_int32), ("max_in_flight_seen", ctypes.c_int32),
-                ("deferred_for_memory", ctypes.c_int32)]
+                ("deferred_for_memory", ctypes.c_int32), ("pipelined", ctypes.c_int32),
+                ("persistent_ctas", ctypes.c_int32), ("drains", ctypes.c_int64), ("rollout_occupancy", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -130,7 +131,9 @@ class Stats(ctypes.Structure):
                 ("reserved", ctypes.c_int32), ("phase_cycles", ctypes.c_int64 * 6),
                 ("batch_waves", ctypes.c_int64), ("batch_rollouts", ctypes.c_int64), ("batch_replans", ctypes.c_int64),
                 ("influence_launches", ctypes.c_int64), ("influence_ms", ctypes.c_double),
-                ("kernel_launches", ctypes.c_int64), ("items_scanned", ctypes.c_int64)]
+                ("kernel_launches", ctypes.c_int64), ("items_scanned", ctypes.c_int64),
+                ("pipe_drains", ctypes.c_int64), ("pipe_cta_s", ctypes.c_double), ("pipe_slot_s", ctypes.c_double),
+                ("pipe_ctas", ctypes.c_int32), ("pipe_resident", ctypes.c_int32)]
 
 
 # every exported symbol of include/fmdp.h
@@ -325,7 +328,7 @@ class Scheduler:
     def __init__(self, box, dt, gamma, actions, sep, n_slices_window=4096, max_slots=4096, heightmap=None,
                  clearance=0.0, deck_value=1000.0, static_wells=None, combine=0, wells=None, goal_reward=200.0,
                  cluster_size=0, threads_per_cta=0, batch_size=0, full_scan=False, index_vmax_mps=0.0,
-                 index_cell_m=0.0, index_stage_items=0, lookahead_W=1):
+                 index_cell_m=0.0, index_stage_items=0, lookahead_W=1, batch_mode=0):
         self._L = load()
         air = Airspace()
         air.x0, air.y0, air.z0, air.x1, air.y1, air.z1 = map(float, box)
@@ -358,6 +361,7 @@ class Scheduler:
         opt.index_vmax_mps = float(index_vmax_mps)
         opt.index_cell_m = float(index_cell_m)
         opt.index_stage_items = int(index_stage_items)
+        opt.batch_mode = int(batch_mode)
         opt.lookahead_W = int(lookahead_W)
         if wells is not None:
             warr = (Well * len(wells))(*[Well(*map(float, w)) for w in wells])

@@ -1,7 +1,9 @@
 """Batched speculative FCFS (fmdp_schedule_batch) against sequential FCFS.
 
 The batch path plans many requests at once against the table as it stands and replans
-only those an earlier admission of the same batch may have changed. Its results must be
+only those an earlier admission of the same batch may have changed. It runs in two modes:
+pipelined (batch_mode 0, the default: one persistent rollout launch fed by the host, no
+waves) and speculative waves (batch_mode 1); both are checked. Its results must be
 identical, bit for bit, to planning the requests one after the other (fmdp_schedule_many,
 itself checked against the FP64 oracle in test_gpu_parity.py), and the table it leaves
 must hold the same plans. The crowded scenario makes the requests' paths cross so that
@@ -65,10 +67,11 @@ def run_both(sc, reqs=None, **kw):
     return many, bat, t1, t2, st
 
 
+@pytest.mark.parametrize("batch_mode", [0, 1])
 @pytest.mark.parametrize("batch_size", [0, 16])
-def test_batch_equals_sequential_c1(batch_size):
+def test_batch_equals_sequential_c1(batch_size, batch_mode):
     sc = S.c1_plain_small()
-    many, bat, t1, t2, st = run_both(sc, batch_size=batch_size)
+    many, bat, t1, t2, st = run_both(sc, batch_size=batch_size, batch_mode=batch_mode)
     same_results(many, bat)
     same_tables(t1, t2)
     assert sum(r["verdict"] == ADMITTED for r in bat) > 0
@@ -78,7 +81,7 @@ def test_batch_equals_sequential_c1(batch_size):
 @pytest.mark.parametrize("cs", [0, 2, 4])
 def test_crowded_batch_replans_and_matches(cs):
     sc = S.crowded_batch()
-    many, bat, t1, t2, st = run_both(sc, cluster_size=cs)
+    many, bat, t1, t2, st = run_both(sc, cluster_size=cs, batch_mode=1)
     same_results(many, bat)
     same_tables(t1, t2)
     # the paths cross: some requests were planned again, and the walk took several waves
@@ -87,9 +90,24 @@ def test_crowded_batch_replans_and_matches(cs):
     assert st["batch_rollouts"] == len(sc.requests) + st["batch_replans"]
 
 
-def test_crowded_batch_against_the_oracle():
+@pytest.mark.parametrize("batch_size", [0, 4])
+def test_pipelined_crowded_batch_replans_and_matches(batch_size):
+    """Pipelined mode (no waves): the crossing paths force re-plans, every re-plan is
+    counted once, and the results and the table equal sequential FCFS."""
+    sc = S.crowded_batch()
+    many, bat, t1, t2, st = run_both(sc, batch_size=batch_size)
+    same_results(many, bat)
+    same_tables(t1, t2)
+    assert st["batch_replans"] > 0 and st["batch_waves"] == 0
+    assert sum(r["replanned"] for r in bat) == st["batch_replans"]
+    assert st["batch_rollouts"] == len(sc.requests) + st["batch_replans"]
+    assert 0 < st["pipe_ctas"] <= st["pipe_resident"]
+
+
+@pytest.mark.parametrize("batch_mode", [0, 1])
+def test_crowded_batch_against_the_oracle(batch_mode):
     sc = S.crowded_batch(n_requests=24)
-    with Scheduler.from_scenario(sc) as s:
+    with Scheduler.from_scenario(sc, batch_mode=batch_mode) as s:
         bat = s.schedule_batch(sc.requests)
         st = s.stats()
     assert st["batch_replans"] > 0
@@ -101,7 +119,7 @@ def test_crowded_batch_against_the_oracle():
 
 def test_graph_replay_equals_eager_launches():
     sc = S.crowded_batch(seed=105, n_requests=40)
-    with Scheduler.from_scenario(sc) as s:
+    with Scheduler.from_scenario(sc, batch_mode=1) as s:
         s.snapshot()
         g1 = s.schedule_batch(sc.requests)  # captured graph
         s.restore()
@@ -115,7 +133,8 @@ def test_graph_replay_equals_eager_launches():
     assert st["rollout_launches"] >= 1 and st["influence_launches"] >= 1
 
 
-def test_consecutive_batches_with_expiry_and_edge_cases():
+@pytest.mark.parametrize("batch_mode", [0, 1])
+def test_consecutive_batches_with_expiry_and_edge_cases(batch_mode):
     sc = S.crowded_batch(seed=106, n_requests=30)
     reqs = sc.requests.copy()
     reqs[3]["horizon"] = 0                      # no step: rejected on the horizon at once
@@ -127,7 +146,7 @@ def test_consecutive_batches_with_expiry_and_edge_cases():
     second["depart"] += 200
     out = []
     for fn in ("schedule_many", "schedule_batch"):
-        with Scheduler.from_scenario(sc, batch_size=8) as s:
+        with Scheduler.from_scenario(sc, batch_size=8, batch_mode=batch_mode) as s:
             a = getattr(s, fn)(first)
             assert getattr(s, fn)(first[:0]) == []
             s.expire(150)
@@ -138,14 +157,15 @@ def test_consecutive_batches_with_expiry_and_edge_cases():
     assert out[1][0][3]["n_points"] == 1 and out[1][0][9]["n_points"] == 1
 
 
-def test_c3_full_size_batch_of_256():
+@pytest.mark.parametrize("batch_mode", [0, 1])
+def test_c3_full_size_batch_of_256(batch_mode):
     """20k known plans, one batch of 256 requests with horizons U[60,1800]: identical to
     sequential FCFS; the requests ahead of the first admission go to the oracle too."""
     sc = S.c3_batched(n_requests=256)
     reqs = sc.requests.copy()
     order = np.argsort(reqs["horizon"], kind="stable")  # short horizons first: cheap oracle prefix
     reqs = reqs[np.concatenate([order[:6], np.sort(order[6:])])]
-    with Scheduler.from_scenario(sc) as s:
+    with Scheduler.from_scenario(sc, batch_mode=batch_mode) as s:
         s.snapshot()
         many = s.schedule_many(reqs)
         t1 = table_of(s)
@@ -160,12 +180,13 @@ def test_c3_full_size_batch_of_256():
     fcfs_parity(None, o, reqs[:6], gpu_results=bat[:6])
 
 
+@pytest.mark.parametrize("batch_mode", [0, 1])
 @pytest.mark.parametrize("batch_size", [0, 16])
-def test_staged_batch_equals_sequential(batch_size):
+def test_staged_batch_equals_sequential(batch_size, batch_mode):
     """The device-resident batched run (requests staged once, trajectories left on the
     device and fetched afterwards) gives the sequential results."""
     sc = S.c1_plain_small()
-    with Scheduler.from_scenario(sc, batch_size=batch_size) as s:
+    with Scheduler.from_scenario(sc, batch_size=batch_size, batch_mode=batch_mode) as s:
         s.snapshot()
         many = s.schedule_many(sc.requests)
         s.restore()
@@ -176,7 +197,10 @@ def test_staged_batch_equals_sequential(batch_size):
         got = s.fetch_staged()
     same_results(many, got)
     assert n_adm == sum(r["verdict"] == ADMITTED for r in many)
-    assert st["batch_waves"] >= 1 and st["kernel_launches"] >= 5 * st["batch_waves"]
+    if batch_mode == 1:
+        assert st["batch_waves"] >= 1 and st["kernel_launches"] >= 5 * st["batch_waves"]
+    else:
+        assert st["batch_waves"] == 0 and st["batch_rollouts"] >= len(sc.requests)
 
 
 def _side_by_side(offset_m, speed=30.0):
@@ -189,15 +213,45 @@ def _side_by_side(offset_m, speed=30.0):
                       n_slices_window=2048, max_slots=64)
 
 
+@pytest.mark.parametrize("batch_mode", [0, 1])
 @pytest.mark.parametrize("offset,waves", [(700.0, 1), (300.0, 2)])
-def test_influence_follows_each_well(offset, waves):
+def test_influence_follows_each_well(offset, waves, batch_mode):
     """The first request's wells lie along its track (Table 3: centres p + tau v, radii
     250-450 m). At 700 m abeam the second request is out of reach of every well, though
     inside one ball of radius max R + max|tau| |v| around the first request, so both are
     final after one wave; at 300 m the tau = 0 well reaches it and it is planned again."""
     sc = _side_by_side(offset)
-    many, bat, t1, t2, st = run_both(sc)
+    many, bat, t1, t2, st = run_both(sc, batch_mode=batch_mode)
     same_results(many, bat)
     same_tables(t1, t2)
     assert [r["verdict"] for r in bat] == [ADMITTED, ADMITTED]
-    assert st["batch_waves"] == waves and st["batch_replans"] == waves - 1
+    assert st["batch_replans"] == waves - 1
+    if batch_mode == 1:
+        assert st["batch_waves"] == waves
+
+
+def test_c2_full_size_pipelined_equals_waves_and_sequential():
+    """The 3000-plan, 1000-request workload in the launch configuration the benchmark
+    times (staged requests, batched): pipelined and wave results equal sequential FCFS,
+    and the pipelined run's admissions grow index rows past the rebuild mark, so the
+    rebuild-while-no-rollout-runs path runs."""
+    sc = S.c2_plain_scale()
+    out = {}
+    for mode in (0, 1):
+        with Scheduler.from_scenario(sc, batch_mode=mode) as s:
+            s.snapshot()
+            if mode == 0:
+                out["many"] = s.schedule_many(sc.requests)
+                out["t_many"] = table_of(s)
+                s.restore()
+            s.stage(sc.requests)
+            s.set_profiling(0)
+            s.schedule_staged(batched=True)
+            out[mode] = s.fetch_staged()
+            out[("t", mode)] = table_of(s)
+            out[("st", mode)] = s.stats()
+    same_results(out["many"], out[0])
+    same_results(out["many"], out[1])
+    same_tables(out["t_many"], out[("t", 0)])
+    same_tables(out["t_many"], out[("t", 1)])
+    assert out[("st", 0)]["pipe_drains"] >= 1 and out[("st", 0)]["batch_waves"] == 0

@@ -41,8 +41,22 @@ def test_served_results_equal_one_at_a_time():
     assert rep["admitted"] == sum(r["verdict"] == ADMITTED for r in alone)
     assert rep["admitted"] + rep["rejected"] == len(sc.requests)
     assert (lat > 0).all() and rep["latency_p99_ms"] >= rep["latency_p50_ms"] > 0
-    assert rep["max_in_flight_seen"] > 1 and rep["waves"] >= 1  # requests shared waves
+    assert rep["max_in_flight_seen"] > 1  # requests were planned side by side
+    assert rep["pipelined"] == 1 and rep["waves"] == 0 and rep["rollouts"] >= len(sc.requests)
+    assert 0.0 < rep["rollout_occupancy"] <= 1.0
     assert rep["throughput_rps"] > 0
+
+
+def test_wave_serving_equals_one_at_a_time():
+    """The same trace served by speculative waves (batch_mode 1)."""
+    sc = S.crowded_batch(seed=111, n_requests=60)
+    arr = poisson(len(sc.requests), 2000.0, 1)
+    with Scheduler.from_scenario(sc) as s:
+        alone = s.schedule_many(sc.requests)
+    with Scheduler.from_scenario(sc, batch_size=32, batch_mode=1) as s:
+        mixed, lat, rep = s.serve(sc.requests, arr)
+    same_results(alone, mixed)
+    assert rep["pipelined"] == 0 and rep["waves"] >= 1
 
 
 def test_served_results_match_the_oracle():
