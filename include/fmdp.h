@@ -479,6 +479,10 @@ typedef struct {
     double pipe_slot_s;          /* pipelined: persistent CTAs x wall time of the calls */
     int32_t pipe_ctas;           /* pipelined: CTAs of the last persistent launch */
     int32_t pipe_resident;       /* pipelined: CTAs of that shape the device keeps resident */
+    int64_t pipe_resumes;        /* pipelined re-plans that kept the steps before the first one an
+                                    admission could change */
+    int64_t pipe_rechecks;       /* pipelined re-plans that kept the whole plan and redid only its
+                                    conflict check */
 } fmdp_stats;
 /* on = 1: per-kernel CUDA-event timing on the context's stream; on = 2: additionally
  * per-phase cycle counters inside the rollout kernel (diagnostic, slows it slightly);

@@ -108,6 +108,9 @@ struct SepOut {
 struct PipeItem {
     int32_t r;      // request number of the call
     int32_t token;  // written to done[r] when this plan has finished
+    int32_t start;  // 0: plan from the origin; k > 0: keep the plan's first k steps and plan on
+                    // from its state at step k; -1: keep the plan, redo only its conflict check
+    int32_t pad;
 };
 struct PipeRecord {
     RolloutOut ro;
@@ -135,6 +138,13 @@ struct PipeArgs {
     const int32_t* pub_seq;
     int32_t* obs;             // device [n][cap]
     int32_t* h_obs;           // host-mapped [n][cap]
+    // What a plan resumed at step k needs of step k (FastMDP's choice at a step depends on
+    // the state then, not on how it was reached): per trajectory point, the exact state, its
+    // double-float copy and the heading index; per decision step, its near-tie flag.
+    double* st_s;             // device [n][cap][3]
+    float* st_df;             // device [n][cap][6]: hi, lo of x, y, z
+    uint8_t* st_h;            // device [n][cap]
+    uint8_t* ties;            // device [n][cap]
 };
 
 struct RolloutArgs {

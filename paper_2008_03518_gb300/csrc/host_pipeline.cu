@@ -74,6 +74,9 @@ struct PipeState {
     MappedArray<int32_t> h_slot;  // slot of an admitted request (read by its admission)
     MappedArray<int32_t> h_obs;   // per plan step: admissions published when its rows were read
     DevArray<int32_t> head, pub_seq, obs;
+    DevArray<double> st_s;        // per trajectory point: what a resumed plan starts from
+    DevArray<float> st_df;
+    DevArray<uint8_t> st_h, ties;
     DevArray<SepOut> sep;
     DevArray<int32_t> slot_ord, req_ord, list, nlist;
     PinnedArray<int32_t> h_list;
@@ -84,7 +87,8 @@ struct PipeState {
         if (pstream) cudaStreamSynchronize(pstream);
         if (tstream) cudaStreamSynchronize(tstream);
         ring.release(); ctl.release(); done.release(); rec.release(); h_traj.release(); h_slot.release();
-        h_obs.release(); pub_seq.release(); obs.release();
+        h_obs.release(); pub_seq.release(); obs.release(); st_s.release(); st_df.release(); st_h.release();
+        ties.release();
         head.release(); sep.release(); slot_ord.release(); req_ord.release(); list.release(); nlist.release();
         h_list.release();
         for (cudaEvent_t e : ev_free) cudaEventDestroy(e);
@@ -153,10 +157,14 @@ struct InflRule {
 // k's conflict check read the index before j was published (aj >= tail_pub), the two within
 // the separation minima + 1 m at one step. At a step that saw j, k's decision already
 // counted j's wells exactly. Chunk bounding boxes skip the steps where the two are far apart.
-bool influences(const InflRule& P, const float* pj, int nj, int64_t tj, const TrajBoxes& bj, int32_t aj,
-                const float* pk, int nk, int64_t tk, double speed_k, const TrajBoxes& bk, const int32_t* obs_k,
-                int32_t tail_pub) {
-    if (nk <= 0 || nj <= 0 || !(tk < tj + nj && tj < tk + nk)) return false;
+// Returns the first decision step that j could change (-1: none); *sep: j could change the
+// verdict. The steps before the first one keep their decisions, so the plan may go on from
+// its state there.
+int first_influenced(const InflRule& P, const float* pj, int nj, int64_t tj, const TrajBoxes& bj, int32_t aj,
+                     const float* pk, int nk, int64_t tk, double speed_k, const TrajBoxes& bk, const int32_t* obs_k,
+                     int32_t tail_pub, bool* sep) {
+    *sep = false;
+    if (nk <= 0 || nj <= 0 || !(tk < tj + nj && tj < tk + nk)) return -1;
     const bool sep_unseen = aj >= tail_pub;
     const double rho = speed_k * P.dt + P.dzmax + 1.0;
     double e = std::max(P.H, P.V);
@@ -165,7 +173,7 @@ bool influences(const InflRule& P, const float* pj, int nj, int64_t tj, const Tr
     const int nck = (nk + kBoxChunk - 1) / kBoxChunk;
     for (int c = 0; c < nck; ++c) {
         const int i0 = c * kBoxChunk, i1 = std::min(nk, i0 + kBoxChunk);
-        if (!sep_unseen && bk.o[c] > aj) continue;  // every step of the chunk saw j
+        if ((!sep_unseen || *sep) && bk.o[c] > aj) continue;  // every step of the chunk saw j
         // j's samples a step of this chunk can meet: the same step, the next, and the one
         // after it (the next sample's velocity)
         const int64_t jlo = std::max<int64_t>(0, tk + i0 - tj), jhi = std::min<int64_t>(nj - 1, tk + i1 - 1 - tj + 2);
@@ -185,9 +193,9 @@ bool influences(const InflRule& P, const float* pj, int nj, int64_t tj, const Tr
         for (int i = i0; i < i1; ++i) {
             const double sx = pk[3 * i], sy = pk[3 * i + 1], sz = pk[3 * i + 2];
             const int64_t t0 = tk + i - tj;
-            if (sep_unseen && t0 >= 0 && t0 < nj) {
+            if (sep_unseen && !*sep && t0 >= 0 && t0 < nj) {
                 const double dx = sx - pj[3 * t0], dy = sy - pj[3 * t0 + 1], dz = sz - pj[3 * t0 + 2];
-                if (dx * dx + dy * dy < P.H * P.H && std::fabs(dz) < P.V) return true;
+                if (dx * dx + dy * dy < P.H * P.H && std::fabs(dz) < P.V) *sep = true;
             }
             const int64_t t1 = t0 + 1;
             if (i + 1 >= nk || obs_k[i] > aj || t1 < 0 || t1 >= nj) continue;  // no decision, or it saw j
@@ -202,11 +210,11 @@ bool influences(const InflRule& P, const float* pj, int nj, int64_t tj, const Tr
                 const double r = P.R[w] + 1.0 + rho;
                 const double dx = sx - (q1[0] + P.tau[w] * vx), dy = sy - (q1[1] + P.tau[w] * vy),
                              dz = sz - (q1[2] + P.tau[w] * vz);
-                if (dx * dx + dy * dy + dz * dz < r * r) return true;
+                if (dx * dx + dy * dy + dz * dz < r * r) return i;
             }
         }
     }
-    return false;
+    return -1;
 }
 
 enum Phase : uint8_t { kAbsent = 0, kWait = 1, kFlight = 2, kDone = 3, kFinal = 4 };
@@ -246,6 +254,10 @@ int32_t run_pipeline(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_resu
     P.h_obs.ensure(R * (size_t)cap);
     P.obs.ensure(R * (size_t)cap);
     P.pub_seq.ensure(1);
+    P.st_s.ensure(R * (size_t)cap * 3);
+    P.st_df.ensure(R * (size_t)cap * 6);
+    P.st_h.ensure(R * (size_t)cap);
+    P.ties.ensure(R * (size_t)cap);
     P.head.ensure(1);
     P.sep.ensure(R);
     P.req_ord.ensure(R);
@@ -274,7 +286,7 @@ int32_t run_pipeline(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_resu
     // per-request state
     std::vector<uint8_t> phase(n, serve ? kAbsent : kWait);  // a batch's requests are all there
     std::vector<int32_t> seen(n, 0), chk(n, 0), gate(n, 0), tok(n, 0), slot_of(n, -1), verdict(n, -1),
-        replans(n, 0), tail_pub(n, 0);
+        replans(n, 0), tail_pub(n, 0), start(n, 0);
     std::vector<uint64_t> ids(n, 0);
     std::vector<RolloutOut> fin_ro(n);
     std::vector<TrajBoxes> boxes(n);
@@ -349,6 +361,10 @@ int32_t run_pipeline(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_resu
     ra.pipe.pub_seq = P.pub_seq.p;
     ra.pipe.obs = P.obs.p;
     ra.pipe.h_obs = P.h_obs.d;
+    ra.pipe.st_s = P.st_s.p;
+    ra.pipe.st_df = P.st_df.p;
+    ra.pipe.st_h = P.st_h.p;
+    ra.pipe.ties = P.ties.p;
     CK(cudaMemsetAsync(P.pub_seq.p, 0, sizeof(int32_t), P.tstream));
     int32_t tail = 0;
     P.ctl.p[0] = 0;
@@ -382,7 +398,7 @@ int32_t run_pipeline(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_resu
     const auto t0 = clk::now();
     auto elapsed = [&]() { return std::chrono::duration<double>(clk::now() - t0).count(); };
     double cta_time = 0.0, last_progress = 0.0;
-    int64_t n_dispatch = 0, n_replans = 0, n_drains = 0, steps_sum = 0;
+    int64_t n_dispatch = 0, n_replans = 0, n_drains = 0, steps_sum = 0, n_resumes = 0, n_rechecks = 0;
     int32_t head = 0, joined = serve ? 0 : n, finalized = 0, admitted = 0, max_seen = 0;
     int64_t expiries = 0, expired = 0;
     int32_t deferred = 0;
@@ -491,33 +507,46 @@ int32_t run_pipeline(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_resu
         }
     };
     // brings request k's completed plan up to date with the admissions made since its
-    // dispatch; false (and k waits for a new plan) when one of them influences it
+    // dispatch; false (and k waits for a new plan) when one of them influences it. The new
+    // plan keeps the steps before the first one any of them could change, and only the
+    // conflict check runs again when none changes a step but one may change the verdict.
     auto check_plan = [&](int32_t k) {
         const int32_t nk = fin_ro[k].n_points;
         const float* pk = P.h_traj.p + (size_t)k * cap * 3;
-        while (chk[k] < (int32_t)A.size()) {
+        int first = INT32_MAX;
+        bool sep_any = false;
+        for (; chk[k] < (int32_t)A.size(); ++chk[k]) {
             const int32_t j = A[chk[k]];
             const float* pj = P.h_traj.p + (size_t)j * cap * 3;
-            if (influences(rule, pj, fin_ro[j].n_points, reqs[j].depart_step, boxes[j], chk[k], pk, nk,
-                           reqs[k].depart_step, reqs[k].speed_mps, boxes[k], P.h_obs.p + (size_t)k * cap,
-                           tail_pub[k])) {
-                phase[k] = kWait;
-                gate[k] = (int32_t)A.size();  // every admission so far visible to the next plan
-                ++replans[k];
-                ++n_replans;
-                return false;
-            }
-            ++chk[k];
+            bool sep = false;
+            const int f = first_influenced(rule, pj, fin_ro[j].n_points, reqs[j].depart_step, boxes[j], chk[k], pk,
+                                           nk, reqs[k].depart_step, reqs[k].speed_mps, boxes[k],
+                                           P.h_obs.p + (size_t)k * cap, tail_pub[k], &sep);
+            if (f >= 0) first = std::min(first, f);
+            sep_any = sep_any || sep;
         }
-        return true;
+        if (first == INT32_MAX && !sep_any) return true;
+        phase[k] = kWait;
+        gate[k] = (int32_t)A.size();  // every admission so far visible to the next plan
+        start[k] = first == INT32_MAX ? -1 : first;
+        ++replans[k];
+        ++n_replans;
+        if (start[k] > 0) ++n_resumes;
+        if (start[k] < 0) ++n_rechecks;
+        return false;
     };
     auto dispatch = [&](int32_t k) {
         tok[k] += 1;
         seen[k] = pub;
-        chk[k] = pub;
+        // a plan from the origin sees every published admission; a resumed plan's kept steps
+        // were checked up to chk[k] and keep their observations
+        if (start[k] == 0) chk[k] = pub;
         PipeItem& it = P.ring.p[tail & (kQueueCap - 1)];
         it.r = k;
         it.token = tok[k];
+        it.start = start[k];
+        it.pad = 0;
+        start[k] = 0;
         std::atomic_thread_fence(std::memory_order_release);
         *reinterpret_cast<volatile int32_t*>(P.ctl.p) = ++tail;
         inflight.push_back(k);
@@ -697,6 +726,8 @@ int32_t run_pipeline(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_resu
     c->stats.batch_replans += n_replans;
     c->stats.rollout_steps += steps_sum;
     c->stats.pipe_drains += n_drains;
+    c->stats.pipe_resumes += n_resumes;
+    c->stats.pipe_rechecks += n_rechecks;
     const double wall = elapsed();
     c->stats.pipe_cta_s += cta_time;
     c->stats.pipe_slot_s += wall * n_ctas;

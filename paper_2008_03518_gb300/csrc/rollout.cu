@@ -432,7 +432,9 @@ __device__ __forceinline__ void fold_well(const Model& m, int w, float qx, float
 
 // Plans request r with this CTA (and its cluster peers). Every thread of the cluster calls
 // it; all shared memory it uses is re-initialised, so a CTA can plan requests back to back.
-__device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, unsigned char* smem) {
+// k0 > 0 (pipelined mode): the plan keeps its first k0 steps and resumes from its state at
+// step k0, as stored by the run that planned them.
+__device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, unsigned char* smem, const int k0 = 0) {
     const Model& m = a.m;
     const int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31, warp = tid >> 5, NW = NT >> 5;
     const int cs = a.cs;
@@ -556,6 +558,26 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
         st->n_points = 1;
         st->near_ties = 0;
         st->steps = 0;
+        if (k0 > 0) {
+            // resume at step k0: the state as the step that reached it published it, and the
+            // goal vector formed from its double-float copy exactly as a step forms it
+            const size_t o = (size_t)r * a.cap + k0;
+            for (int q = 0; q < 3; ++q) {
+                st->s[q] = a.pipe.st_s[3 * o + q];
+                st->s_hi[q] = a.pipe.st_df[6 * o + 2 * q];
+                st->s_lo[q] = a.pipe.st_df[6 * o + 2 * q + 1];
+                float gh = (float)g0[q];
+                float gl = (float)__dsub_rn(g0[q], (double)gh);
+                df_add(gh, gl, -st->s_hi[q], -st->s_lo[q]);
+                st->G_hi[q] = gh;
+                st->G_lo[q] = gl;
+            }
+            st->h = a.pipe.st_h[o];
+            st->done = 0;  // the run that planned these steps went on from step k0
+            st->status = FMDP_REJ_HORIZON;
+            st->n_points = k0 + 1;
+            st->steps = k0;
+        }
         st->abort_flag[0] = st->abort_flag[1] = 0;
         st->last_best[0] = st->last_best[1] = 99;
         for (int e = 0; e < kRingDepth; ++e) st->ent_valid[e] = 0;
@@ -568,6 +590,11 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
         }
     }
     if (cs > 1) cluster_barrier(); else __syncthreads();  // mbarriers initialised cluster-wide
+    if (k0 > 0) {  // near ties of the kept steps
+        int nt = 0;
+        for (int i = tid; i < k0; i += NT) nt += a.pipe.ties[(size_t)r * a.cap + i];
+        if (nt) atomicAdd(&st->near_ties, nt);
+    }
 
     // ---- producer state (thread 32: warp 1, lane 0)
     const bool producer = (tid == 32);
@@ -775,17 +802,19 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
     const float inv_dt = (float)(1.0 / m.dt);
     const float Rq = reach0 + m.tau_absmax * a.iv.vmax * 1.0001f + stepf + 2.0f;  // indexed query radius
     if (indexed && warp == 2 && !st->done) {
-        // steps 0 and 1 from the origin
-        const float ox = (float)req.ox, oy = (float)req.oy;
-        issue_direct(0, req.depart_step + 1, row_of(req.depart_step + 1), ox, oy, Rq);
-        issue_direct(1, req.depart_step + 2, row_of(req.depart_step + 2), ox, oy, Rq);
-        const int to = wait_bar(&bars[0], ifill[0], ipend[0]);
-        if (lane == 0) st->abort_flag[0] = to;
+        // steps k0 and k0 + 1 from the state at step k0 (the origin when k0 = 0)
+        const float ox = k0 > 0 ? st->s_hi[0] + st->s_lo[0] : (float)req.ox;
+        const float oy = k0 > 0 ? st->s_hi[1] + st->s_lo[1] : (float)req.oy;
+        const int b0 = k0 % kIBufs, b1 = (k0 + 1) % kIBufs;
+        issue_direct(b0, req.depart_step + k0 + 1, row_of(req.depart_step + k0 + 1), ox, oy, Rq);
+        issue_direct(b1, req.depart_step + k0 + 2, row_of(req.depart_step + k0 + 2), ox, oy, Rq);
+        const int to = wait_bar(&bars[b0], ifill[b0], ipend[b0]);
+        if (lane == 0) st->abort_flag[k0 & 1] = to;
         stalled = to != 0;
     }
     // ring row of the query the producer issues at step k (for step k + 2): advanced by one
     // row per step, so the loop needs no 64-bit modulo
-    int64_t prow = indexed ? row_of(req.depart_step + 3) : 0;
+    int64_t prow = indexed ? row_of(req.depart_step + k0 + 3) : 0;
     float ghi[3], glo[3];  // goal as double-float
     {
         const double g0[3] = {req.gx, req.gy, req.gz};
@@ -823,7 +852,7 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
     long long tp = 0;
 
     // ---------------------------------------------------------------- step loop
-    int k = 0;
+    int k = k0;
     for (;; ++k) {
         if (timing && tid == 0) tp = clock64();
         __syncthreads();  // S1: state and ring entries published
@@ -1242,7 +1271,15 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
                     traj[3 * np + 1] = tfy;
                     traj[3 * np + 2] = tfz;
                     acts[k] = (uint8_t)best;
-                    if (a.pipe.obs) a.pipe.obs[(size_t)r * a.cap + k] = imeta[k % kIBufs].pub;
+                    if (a.pipe.obs) {  // what a resumed plan and the host's influence test need
+                        const size_t o = (size_t)r * a.cap;
+                        a.pipe.obs[o + k] = imeta[k % kIBufs].pub;
+                        double* ps = a.pipe.st_s + 3 * (o + np);
+                        ps[0] = X; ps[1] = Y; ps[2] = Z;
+                        float* pd = a.pipe.st_df + 6 * (o + np);
+                        pd[0] = nhx; pd[1] = nlx; pd[2] = nhy; pd[3] = nly; pd[4] = nhz; pd[5] = nlz;
+                        a.pipe.st_h[o + np] = (uint8_t)hn;
+                    }
                     if (a.trace && r == 0) {
                         a.st_trace[3 * np] = X;
                         a.st_trace[3 * np + 1] = Y;
@@ -1263,8 +1300,9 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
             if (timing && tid == 0) ph[3] += clock64() - tp;
         } else {
             // evaluator warp: near-tie flag of the previous step, off the step's critical path
-            if (warp == 1 && k > 0)
-                deferred_tie(st, qkey_s, cls_s, la_s, lt_s, par ^ 1, lane, trace0 ? a.tie_trace + (k - 1) : nullptr);
+            if (warp == 1 && k > k0)
+                deferred_tie(st, qkey_s, cls_s, la_s, lt_s, par ^ 1, lane,
+                             trace0 ? a.tie_trace + (k - 1) : (a.pipe.ties ? a.pipe.ties + (size_t)r * a.cap + (k - 1) : nullptr));
         }
         if (producer && !indexed) {
             // ---- producer: slices needed two or more steps ahead
@@ -1284,8 +1322,9 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
     }
 
     // ---- epilogue: near-tie flag of the last step, drain the ring, outputs
-    if (warp == 1 && k > 0)
-        deferred_tie(st, qkey_s, cls_s, la_s, lt_s, (k - 1) & 1, lane, trace0 ? a.tie_trace + (k - 1) : nullptr);
+    if (warp == 1 && k > k0)
+        deferred_tie(st, qkey_s, cls_s, la_s, lt_s, (k - 1) & 1, lane,
+                     trace0 ? a.tie_trace + (k - 1) : (a.pipe.ties ? a.pipe.ties + (size_t)r * a.cap + (k - 1) : nullptr));
     __syncthreads();
     if (indexed && warp == 2) drain();
     if (producer) {
@@ -1336,7 +1375,7 @@ __device__ __forceinline__ void st_release_sys(int32_t* p, int v) {
 // Takes the next work item of the host-fed ring (thread 0). Returns its ring position, or
 // -1 when the CTA should leave: the host asked it to stop and the ring is empty, no work
 // came for idle_cycles, or a bounded wait of another CTA expired.
-__device__ int pipe_take(const RolloutArgs& a, int* r_out, int* tok_out) {
+__device__ int pipe_take(const RolloutArgs& a, int* r_out, int* tok_out, int* start_out) {
     const PipeArgs& p = a.pipe;
     long long t0 = clock64();
     unsigned ns = 32;
@@ -1349,6 +1388,7 @@ __device__ int pipe_take(const RolloutArgs& a, int* r_out, int* tok_out) {
                 const PipeItem* it = p.items + (h & p.qmask);
                 *r_out = ld_volatile_sys(&it->r);
                 *tok_out = ld_volatile_sys(&it->token);
+                *start_out = ld_volatile_sys(&it->start);
                 return h;
             }
             continue;
@@ -1464,22 +1504,24 @@ __device__ void pipe_finish(const RolloutArgs& a, int r, int token, int* red) {
 // host appends to the ring until it is told to stop, stays idle too long, or a wait expires.
 __device__ void pipe_loop(const RolloutArgs& a, unsigned char* smem) {
     const Layout L = make_layout(a.chunk, a.ring, a.icap);
-    int* slot = reinterpret_cast<int*>(smem + L.misc);  // [0] ring position, [1] request, [2] token
+    int* slot = reinterpret_cast<int*>(smem + L.misc);  // [0] ring position, [1] request, [2] token, [3] start
     for (;;) {
         if (threadIdx.x == 0) {
-            int r = 0, tok = 0;
-            const int w = pipe_take(a, &r, &tok);
+            int r = 0, tok = 0, k0 = 0;
+            const int w = pipe_take(a, &r, &tok, &k0);
             slot[0] = w;
             slot[1] = r;
             slot[2] = tok;
+            slot[3] = k0;
         }
         __syncthreads();
         const int w = reinterpret_cast<volatile int*>(slot)[0];
         const int r = reinterpret_cast<volatile int*>(slot)[1];
         const int tok = reinterpret_cast<volatile int*>(slot)[2];
+        const int k0 = reinterpret_cast<volatile int*>(slot)[3];
         __syncthreads();
         if (w < 0) break;
-        plan_request(a, r, smem);
+        if (k0 >= 0) plan_request(a, r, smem, k0);  // k0 < 0: the plan stands, only its check again
         pipe_finish(a, r, tok, slot + 4);
     }
 }

@@ -133,7 +133,8 @@ class Stats(ctypes.Structure):
                 ("influence_launches", ctypes.c_int64), ("influence_ms", ctypes.c_double),
                 ("kernel_launches", ctypes.c_int64), ("items_scanned", ctypes.c_int64),
                 ("pipe_drains", ctypes.c_int64), ("pipe_cta_s", ctypes.c_double), ("pipe_slot_s", ctypes.c_double),
-                ("pipe_ctas", ctypes.c_int32), ("pipe_resident", ctypes.c_int32)]
+                ("pipe_ctas", ctypes.c_int32), ("pipe_resident", ctypes.c_int32),
+                ("pipe_resumes", ctypes.c_int64), ("pipe_rechecks", ctypes.c_int64)]
 
 
 # every exported symbol of include/fmdp.h
