@@ -483,7 +483,30 @@ typedef struct {
                                     admission could change */
     int64_t pipe_rechecks;       /* pipelined re-plans that kept the whole plan and redid only its
                                     conflict check */
+    int64_t qe_items;            /* indexed rollouts (on >= 1): plan samples culled by the well scan */
+    int64_t qe_near;             /* ... of them inside the cull radius (their wells are masked) */
+    int64_t qe_wells;            /* (sample, reachable well) pairs valued, each for every action */
 } fmdp_stats;
+/* Switches the batch mode (fmdp_options.batch_mode) of later calls: 0 pipelined, 1 waves. */
+fmdp_status fmdp_set_batch_mode(fmdp_ctx* ctx, int32_t mode);
+/* Completion time of each request of the last fmdp_schedule_many / _batch / _staged /
+ * fmdp_schedule_learned call, in ms from the call's start (sequential calls: CUDA events
+ * after each request's admission step; batched calls: when the host finalised it). Copies
+ * min(cap, n) values; *n_out = n, the call's request count. Measurement support, no
+ * counterpart in the paper. */
+fmdp_status fmdp_last_call_times(fmdp_ctx* ctx, double* ms, int32_t cap, int32_t* n_out);
+/* Measured throughput of the units the well scan uses, on the context's device: FP32 FMA
+ * (2 flops each), MUFU reciprocal square root and exp2, over all SMs, with the mean SM clock
+ * during the FMA probe. Takes a few milliseconds. Measurement support, no counterpart in
+ * the paper. */
+typedef struct {
+    double fp32_tflops;
+    double mufu_rsqrt_tops;
+    double mufu_ex2_tops;
+    double sm_mhz;
+} fmdp_peaks;
+fmdp_status fmdp_probe_peaks(fmdp_ctx* ctx, fmdp_peaks* out);
+
 /* on = 1: per-kernel CUDA-event timing on the context's stream; on = 2: additionally
  * per-phase cycle counters inside the rollout kernel (diagnostic, slows it slightly);
  * 0: off (default). Resets the statistics. */

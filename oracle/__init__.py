@@ -75,6 +75,8 @@ def lib():
         L.orc_add_plan.argtypes = [ctypes.c_void_p, ctypes.c_int64, fp, ctypes.c_int32]
         L.orc_n_plans.restype = ctypes.c_int32
         L.orc_n_plans.argtypes = [ctypes.c_void_p]
+        L.orc_set_threads.argtypes = [ctypes.c_int32]
+        L.orc_set_threads.restype = ctypes.c_int32
         L.orc_heading_table.argtypes = [ctypes.c_double] * 4 + [dp, dp]
         L.orc_terrain.restype = ctypes.c_double
         L.orc_terrain.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double]
@@ -93,6 +95,12 @@ def lib():
         L.orc_schedule.argtypes = [ctypes.c_void_p, P(OrcRequest), ctypes.c_int32, fp, ip, P(OrcResult)]
         _lib = L
     return _lib
+
+
+def set_threads(n):
+    """Threads that value a rollout step's actions (OpenMP build); returns the number in
+    effect. The results do not depend on it."""
+    return int(lib().orc_set_threads(int(n)))
 
 
 def _ptr(a, ctype):

@@ -254,6 +254,18 @@ static void state_terms(const orc_t* o, double x, double y, double z, int64_t tn
     }
 }
 
+/* threads over which a step's actions are valued (1: the plain sequential loop) */
+static int g_threads = 1;
+
+int32_t orc_set_threads(int32_t n) {
+#ifdef _OPENMP
+    g_threads = n > 1 ? n : 1;
+#else
+    g_threads = 1;
+#endif
+    return g_threads;
+}
+
 static int in_box(const orc_params* p, double x, double y, double z) {
     return x >= p->x0 && x <= p->x1 && y >= p->y0 && y <= p->y1 && z >= p->z0 && z <= p->z1;
 }
@@ -265,6 +277,11 @@ static int64_t q_values_x(const orc_t* o, const double* s, int32_t h, int64_t t,
     double step = speed * p->dt;
     int W = p->lookahead_W > 1 ? p->lookahead_W : 1;
     int64_t tests = 0;
+    /* the actions' values are independent of one another: with OpenMP (orc_set_threads) the
+     * actions are shared out over threads; every value is computed exactly as written */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) reduction(+ : tests) if (g_threads > 1) num_threads(g_threads)
+#endif
     for (int a = 0; a < p->n_actions; ++a) {
         /* forward projection (Alg. 3): turn, then move */
         int hn = ((h + o->dh[a]) % 24 + 24) % 24;

@@ -78,6 +78,9 @@ orc_t* orc_create(const orc_params* p);
 void orc_destroy(orc_t* o);
 int64_t orc_add_plan(orc_t* o, int64_t t0, const float* xyz, int32_t n);
 int32_t orc_n_plans(const orc_t* o);
+/* Threads that value a step's actions (OpenMP build; the results do not depend on it).
+ * Returns the number in effect (1 without OpenMP). Process-wide. */
+int32_t orc_set_threads(int32_t n);
 
 /* Unit heading vectors for the 24 headings psi0 + k*15 deg, psi0 = bearing origin->goal. */
 void orc_heading_table(double ox, double oy, double gx, double gy, double* C, double* S);

@@ -13,7 +13,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(OUT, "libfmdp.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["capi.cu", "host_table.cu", "host_fcfs.cu", "host_batch.cu", "host_learned.cu", "host_serve.cu", "host_pipeline.cu", "rollout.cu", "tables.cu", "index.cu", "learned.cu", "noalloc.cu", "lookahead.cu"]
+SOURCES = ["capi.cu", "host_table.cu", "host_fcfs.cu", "host_batch.cu", "host_learned.cu", "host_serve.cu", "host_pipeline.cu", "rollout.cu", "tables.cu", "index.cu", "learned.cu", "noalloc.cu", "lookahead.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "--expt-relaxed-constexpr"]
 

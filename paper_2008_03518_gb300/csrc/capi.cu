@@ -155,8 +155,8 @@ fmdp_status fmdp_create(const fmdp_airspace* air, double gamma, const fmdp_actio
             CK(cudaMalloc(&c->ix_nres, ((size_t)c->T_win + 16) * sizeof(int32_t)));
             CK(cudaMalloc(&c->ix_dirty, (size_t)c->T_win * sizeof(int32_t)));
             CK(cudaMalloc(&c->ix_items, plane * 2 * sizeof(float4)));
-            CK(cudaMalloc(&c->items_ctr, sizeof(unsigned long long)));
-            CK(cudaMemsetAsync(c->items_ctr, 0, sizeof(unsigned long long), c->stream));
+            CK(cudaMalloc(&c->items_ctr, 4 * sizeof(unsigned long long)));  // items; q_eval counters
+            CK(cudaMemsetAsync(c->items_ctr, 0, 4 * sizeof(unsigned long long), c->stream));
             c->ix_smem = index_build_smem(c->ix_ncell);
             CK(prepare_index_kernels(c->ix_smem));
             index_reset(c);
@@ -822,7 +822,7 @@ fmdp_status fmdp_set_profiling(fmdp_ctx* c, int32_t on) {
         c->stats = fmdp_stats{};
         c->pending.clear();
         c->ev_next = 0;
-        if (c->items_ctr) CK(cudaMemsetAsync(c->items_ctr, 0, sizeof(unsigned long long), c->stream));
+        if (c->items_ctr) CK(cudaMemsetAsync(c->items_ctr, 0, 4 * sizeof(unsigned long long), c->stream));
         if (c->phase_timing) {
             c->phase.ensure(6);
             CK(cudaMemsetAsync(c->phase.p, 0, 6 * sizeof(unsigned long long), c->stream));
@@ -842,14 +842,44 @@ fmdp_status fmdp_get_stats(fmdp_ctx* c, fmdp_stats* out) {
             for (int i = 0; i < 6; ++i) out->phase_cycles[i] = (int64_t)ph[i];
         }
         if (c->items_ctr) {
-            unsigned long long n = 0;
-            CK(cudaMemcpyAsync(&n, c->items_ctr, sizeof(n), cudaMemcpyDeviceToHost, c->stream));
+            unsigned long long n[4] = {0, 0, 0, 0};
+            CK(cudaMemcpyAsync(n, c->items_ctr, sizeof(n), cudaMemcpyDeviceToHost, c->stream));
             CK(cudaStreamSynchronize(c->stream));
-            out->items_scanned = (int64_t)n;
+            out->items_scanned = (int64_t)n[0];
+            out->qe_items = (int64_t)n[1];
+            out->qe_near = (int64_t)n[2];
+            out->qe_wells = (int64_t)n[3];
         }
         out->cluster_size = c->last_cs;
         out->threads_per_cta = c->last_threads;
         out->slots_per_cta = c->last_chunk;
+    });
+}
+
+fmdp_status fmdp_set_batch_mode(fmdp_ctx* c, int32_t mode) {
+    if (!c) return FMDP_ERR_ARG;
+    return guard(c, [&] {
+        require(mode == 0 || mode == 1, FMDP_ERR_ARG, "batch_mode must be 0 (pipelined) or 1 (waves)");
+        c->opt.batch_mode = mode;
+    });
+}
+
+fmdp_status fmdp_last_call_times(fmdp_ctx* c, double* ms, int32_t cap, int32_t* n_out) {
+    if (!c) return FMDP_ERR_ARG;
+    return guard(c, [&] {
+        require(n_out && cap >= 0 && (cap == 0 || ms), FMDP_ERR_ARG, "null output");
+        const int32_t n = (int32_t)std::min<size_t>(c->call_ms.size(), (size_t)cap);
+        std::copy(c->call_ms.begin(), c->call_ms.begin() + n, ms);
+        *n_out = (int32_t)c->call_ms.size();
+    });
+}
+
+fmdp_status fmdp_probe_peaks(fmdp_ctx* c, fmdp_peaks* out) {
+    if (!c) return FMDP_ERR_ARG;
+    return guard(c, [&] {
+        require(out != nullptr, FMDP_ERR_ARG, "null output");
+        CK(cudaStreamSynchronize(c->stream));
+        CK(probe_peaks(c->n_sm, c->stream, out));
     });
 }
 

@@ -174,6 +174,8 @@ struct RolloutArgs {
     int32_t icap;     // indexed mode: items per staging buffer in shared memory
     IndexView iv;
     unsigned long long* items_ctr;  // indexed mode: items read by the steps (statistics) or nullptr
+    unsigned long long* qe_ctr;     // indexed mode (statistics) or nullptr: [0] items culled, [1] items
+                                    // inside the cull radius, [2] (item, reachable well) pairs valued
     const int32_t* skip;            // batch mode: request r is not planned when skip[r] (nullptr: none)
     PipeArgs pipe;                  // pipelined mode (pipe.on): work from the host-fed ring
 };
@@ -238,6 +240,10 @@ struct InfluenceArgs {
     int32_t n_cap;              // row stride of out
 };
 
+
+// Throughput probes (probe.cu): FP32 FMA, and the MUFU reciprocal square root and exp2 the
+// rollout's value terms use, over every SM; the SM clock from clock64 against event time.
+cudaError_t probe_peaks(int n_sm, cudaStream_t s, fmdp_peaks* out);
 
 // kernel launchers (rollout.cu / tables.cu)
 // n_clusters > 0: persistent launch of that many clusters (work-queue mode), else one

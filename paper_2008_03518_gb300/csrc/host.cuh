@@ -282,6 +282,12 @@ struct fmdp_ctx {
     int last_cs = 1, last_threads = 256, last_chunk = 0;
     std::string err_msg;
 
+    // per-request completion times of the last scheduling call (ms from its start); the
+    // sequential path records an event after each request (req_ev, from req_ev_base)
+    std::vector<double> call_ms;
+    std::vector<cudaEvent_t> req_ev;
+    int32_t req_ev_base = -1;  // -1: no recording
+
     // pipelined FCFS: streams, host-mapped ring and reports, ordinals (host_pipeline.cu)
     PipeState* pipe = nullptr;
     int32_t extra_limit = kExtraLimit;  // appended items per index row before it is marked dirty

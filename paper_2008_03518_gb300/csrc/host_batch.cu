@@ -394,13 +394,21 @@ int32_t run_batch(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_result*
     }
     Speculator sp(c, reqs, n);
     std::vector<int32_t> resolved;
+    c->call_ms.assign(n, 0.0);
+    const auto t_start = std::chrono::steady_clock::now();
     for (int32_t b0 = 0; b0 < n; b0 += bs) {
         const int32_t m = std::min(bs, n - b0);
         sp.set_geometry(batch_geometry(c, m, m));
         for (int32_t i = 0; i < m; ++i) sp.add(b0 + i);
         sp.adm_all.clear();
         try {
-            while (!sp.U.empty()) sp.wave(resolved);
+            while (!sp.U.empty()) {
+                const size_t before = resolved.size();
+                sp.wave(resolved);
+                const double t =
+                    std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+                for (size_t q = before; q < resolved.size(); ++q) c->call_ms[resolved[q]] = t;
+            }
             sp.finish(b0, m);
         } catch (...) {
             sp.rollback();

@@ -11,6 +11,14 @@ int32_t run_fcfs(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_result* 
     const bool keep_on_device = staged;
     int32_t admitted = 0;
     int32_t done = 0;
+    // completion time of each request: an event after its admission step ([0] the start)
+    while ((int32_t)c->req_ev.size() < n + 1) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        c->req_ev.push_back(e);
+    }
+    CK(cudaEventRecord(c->req_ev[n], c->stream));
+    c->call_ms.assign(n, 0.0);
     while (done < n) {
         const int32_t m = std::min<int32_t>(n - done, (int32_t)c->book.free_slots.size());
         require(m > 0, FMDP_ERR_FULL, "no free plan slot");
@@ -64,7 +72,9 @@ int32_t run_fcfs(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_result* 
                 LAUNCH(c, launch_lookahead(la, c->stream));
                 t.stop();
             }
+            c->req_ev_base = cosim ? -1 : done;
             enqueue_sequence(c, B, reqs + done, m, cap, g, !cosim);
+            c->req_ev_base = -1;
             c->h_rout.ensure(m);
             c->h_sep.ensure(m);
             CK(cudaMemcpyAsync(c->h_rout.p, B.rout.p, m * sizeof(RolloutOut), cudaMemcpyDeviceToHost, c->stream));
@@ -77,6 +87,12 @@ int32_t run_fcfs(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_result* 
                 CK(cudaMemcpyAsync(c->h_acts.p, B.acts.p, (size_t)m * cap, cudaMemcpyDeviceToHost, c->stream));
             }
             CK(cudaStreamSynchronize(c->stream));
+            if (!cosim)
+                for (int32_t i = 0; i < m; ++i) {
+                    float ms = 0.f;
+                    CK(cudaEventElapsedTime(&ms, c->req_ev[n], c->req_ev[done + i]));
+                    c->call_ms[done + i] = ms;
+                }
             if (c->profiling) collect_timers(c);
             const int32_t ew = read_error_word(c);
             require(ew == 0, FMDP_ERR_TIMEOUT, "a bounded device wait expired during a rollout");

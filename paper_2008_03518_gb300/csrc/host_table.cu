@@ -142,6 +142,7 @@ void set_index_args(fmdp_ctx* c, RolloutArgs& ra, const Geometry& g) {
     ra.icap = g.icap;
     ra.iv = index_view(c);
     ra.items_ctr = (c->index_on && c->profiling && !c->capturing) ? c->items_ctr : nullptr;
+    ra.qe_ctr = ra.items_ctr ? c->items_ctr + 1 : nullptr;
 }
 
 // rebuilds the index rows of steps [a, b) (at most one window length)
@@ -396,6 +397,7 @@ void enqueue_sequence(fmdp_ctx* c, SeqBuffers& B, const fmdp_request* host_reqs,
         const int64_t d0 = host_reqs[i].depart_step;
         index_append_admitted(c, ra.traj, cap, ra.out, ra.reqs, sa.out, aa.slots, nullptr, nullptr, 1, d0,
                               d0 + host_reqs[i].horizon + 1);
+        if (c->req_ev_base >= 0) CK(cudaEventRecord(c->req_ev[c->req_ev_base + i], c->stream));
     }
 }
 
@@ -576,6 +578,7 @@ void destroy_ctx(fmdp_ctx* c) {
     c->phase.release();
     c->h_traj.release(); c->h_acts.release(); c->h_rout.release(); c->h_sep.release();
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    for (cudaEvent_t e : c->req_ev) cudaEventDestroy(e);
     if (c->own) cudaStreamDestroy(c->own);
     delete c;
 }

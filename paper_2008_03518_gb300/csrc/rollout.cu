@@ -849,6 +849,9 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
 
     const bool timing = a.phase != nullptr && lead;
     unsigned long long ph[6] = {0, 0, 0, 0, 0, 0};
+    // indexed scanners' work (statistics): items culled, items inside the cull radius,
+    // (item, reachable well) pairs evaluated for every action
+    unsigned qe_items = 0u, qe_dnear = 0u, qe_wells = 0u;
     long long tp = 0;
 
     // ---------------------------------------------------------------- step loop
@@ -1065,9 +1068,12 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
                             const float reach =
                                 fmaf(tau_absmax, approx_sqrt(vx[u] * vx[u] + vy[u] * vy[u] + vz[u] * vz[u]), reach0);
                             near[u] = (qx[u] * qx[u] + qy[u] * qy[u] + qz[u] * qz[u]) < reach * reach;
+                            ++qe_items;
                         }
+                        qe_dnear += near[u] ? 1u : 0u;
                         wm[u] = near[u] ? well_mask(qx[u], qy[u], qz[u], vx[u], vy[u], vz[u]) : 0u;
                         near[u] = wm[u] != 0u;
+                        qe_wells += __popc(wm[u]);
                     }
 #pragma unroll
                     for (int u = 0; u < U; ++u) {
@@ -1348,6 +1354,18 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
     if (timing && (tid == 0 || tid == NT - 32 || producer))
         for (int i = 0; i < 6; ++i)
             if (ph[i]) atomicAdd(&a.phase[i], ph[i]);
+    if (a.qe_ctr && warp >= 3) {
+        for (int off = 16; off; off >>= 1) {
+            qe_items += __shfl_xor_sync(kFull, qe_items, off);
+            qe_dnear += __shfl_xor_sync(kFull, qe_dnear, off);
+            qe_wells += __shfl_xor_sync(kFull, qe_wells, off);
+        }
+        if (lane == 0 && qe_items) {
+            atomicAdd(&a.qe_ctr[0], (unsigned long long)qe_items);
+            atomicAdd(&a.qe_ctr[1], (unsigned long long)qe_dnear);
+            atomicAdd(&a.qe_ctr[2], (unsigned long long)qe_wells);
+        }
+    }
     if (cs > 1) cluster_barrier(); else __syncthreads();  // peers may still address this CTA's shared memory
     if ((a.queue || a.pipe.on) && tid == 0) {  // the next request of this CTA initialises them again
         for (int e = 0; e < kRingDepth; ++e) mbar_inval(&bars[e]);

@@ -134,7 +134,13 @@ class Stats(ctypes.Structure):
                 ("kernel_launches", ctypes.c_int64), ("items_scanned", ctypes.c_int64),
                 ("pipe_drains", ctypes.c_int64), ("pipe_cta_s", ctypes.c_double), ("pipe_slot_s", ctypes.c_double),
                 ("pipe_ctas", ctypes.c_int32), ("pipe_resident", ctypes.c_int32),
-                ("pipe_resumes", ctypes.c_int64), ("pipe_rechecks", ctypes.c_int64)]
+                ("pipe_resumes", ctypes.c_int64), ("pipe_rechecks", ctypes.c_int64),
+                ("qe_items", ctypes.c_int64), ("qe_near", ctypes.c_int64), ("qe_wells", ctypes.c_int64)]
+
+
+class Peaks(ctypes.Structure):
+    _fields_ = [("fp32_tflops", ctypes.c_double), ("mufu_rsqrt_tops", ctypes.c_double),
+                ("mufu_ex2_tops", ctypes.c_double), ("sm_mhz", ctypes.c_double)]
 
 
 # every exported symbol of include/fmdp.h
@@ -149,7 +155,8 @@ EXPORTS = ("fmdp_options_default", "fmdp_create", "fmdp_destroy", "fmdp_last_err
            "fmdp_schedule_departures_batch",
            "fmdp_schedule_cosim", "fmdp_selftest_wait_timeout",
            "fmdp_get_plan", "fmdp_expire", "fmdp_snapshot", "fmdp_restore", "fmdp_clear", "fmdp_rollout_trace",
-           "fmdp_sep_check", "fmdp_sep_check_noalloc", "fmdp_set_profiling", "fmdp_get_stats")
+           "fmdp_sep_check", "fmdp_sep_check_noalloc", "fmdp_set_profiling", "fmdp_get_stats",
+           "fmdp_set_batch_mode", "fmdp_last_call_times", "fmdp_probe_peaks")
 
 NOALLOC_MAX_POINTS = 16384  # FMDP_NOALLOC_MAX_POINTS
 
@@ -221,6 +228,9 @@ def load(build_if_missing: bool = True):
     L.fmdp_sep_check_noalloc.argtypes = [vp, c.c_int64, _fp, c.c_int32, P(SepReport)]
     L.fmdp_set_profiling.argtypes = [vp, c.c_int32]
     L.fmdp_get_stats.argtypes = [vp, P(Stats)]
+    L.fmdp_set_batch_mode.argtypes = [vp, c.c_int32]
+    L.fmdp_last_call_times.argtypes = [vp, _dp, c.c_int32, P(c.c_int32)]
+    L.fmdp_probe_peaks.argtypes = [vp, P(Peaks)]
     for name in EXPORTS:
         f = getattr(L, name)
         if f.restype is ctypes.c_int:  # default restype: all statuses are int32
@@ -715,6 +725,25 @@ class Scheduler:
     # ------------------------------------------------------------ profiling
     def set_profiling(self, on=True):
         self._check(self._L.fmdp_set_profiling(self._h, int(on)))
+
+    def set_batch_mode(self, mode):
+        """0: pipelined batches (default), 1: speculative waves; same results."""
+        self._check(self._L.fmdp_set_batch_mode(self._h, int(mode)))
+
+    def last_call_times(self):
+        """Completion time of each request of the last scheduling call, ms from its start."""
+        n = ctypes.c_int32()
+        self._check(self._L.fmdp_last_call_times(self._h, None, 0, ctypes.byref(n)))
+        out = np.zeros(n.value)
+        if n.value:
+            self._check(self._L.fmdp_last_call_times(self._h, _ptr(out, ctypes.c_double), n.value, ctypes.byref(n)))
+        return out
+
+    def probe_peaks(self):
+        """Measured FP32 FMA (TFLOP/s), MUFU rsqrt and exp2 (Top/s) rates and the SM clock."""
+        pk = Peaks()
+        self._check(self._L.fmdp_probe_peaks(self._h, ctypes.byref(pk)))
+        return {k: getattr(pk, k) for k, _ in Peaks._fields_}
 
     def stats(self):
         s = Stats()

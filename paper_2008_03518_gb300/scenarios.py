@@ -302,18 +302,29 @@ def crowded_batch(seed: int = 104, n_plans: int = 200, n_requests: int = 48, spr
                     max_slots=n_plans + n_requests + 64)
 
 
-def c4_serving(seed: int = 104, n_plans: int = 40000) -> Scenario:
-    """Serving airspace: 60 km x 60 km x 1 km, C2-style terrain stretched over it, `n_plans`
-    multi-leg known plans departing U[0, 1800] s, a window of 4096 steps and room for
-    100k plans (the sliding-window table). Requests come from `serving_requests`."""
-    hm = fractal_heightmap(seed)
+def c4_serving(seed: int = 104, n_plans: int = 100000) -> Scenario:
+    """Serving workload: C2's airspace and terrain (30 km x 30 km x 1 km) with `n_plans` known
+    plans in a sliding window of 4096 steps, room for 100k active plans plus the requests.
+    Known plans are 1-2 legs of 2-6 km departing U[0, 3000] s, about 200 s of flight each, so
+    some 6-7k of them are in the air at a time (the 20k-plan workload's density). Serving
+    starts its simulated clock at step meta["sim_start"] (plans that ended before it can be
+    expired at once); `serving_requests` makes the arrivals, `sweep_requests` a batch."""
+    hm = fractal_heightmap(102)
     rng = np.random.default_rng(seed + 1000)
-    box = (0.0, 0.0, 0.0, 60000.0, 60000.0, 1000.0)
-    plans = multileg_plans(rng, box, n_plans, hm, tlo=0, thi=1800)
-    return Scenario(f"c4_serving_60km_{n_plans}plans_A25", box, 1.0, 0.99,
+    box = (0.0, 0.0, 0.0, 30000.0, 30000.0, 1000.0)
+    plans = multileg_plans(rng, box, n_plans, hm, legs=(1, 2), leg_len=(2000.0, 6000.0), tlo=0, thi=3000)
+    return Scenario(f"c4_serving_30km_{n_plans}plans_A25", box, 1.0, 0.99,
                     action_grid((-4.0, -2.0, 0.0, 2.0, 4.0)), (150.0, 30.0), plans,
                     np.zeros(0, dtype=REQUEST_DTYPE), heightmap=hm, clearance=60.0, n_slices_window=4096,
-                    max_slots=100000)
+                    max_slots=n_plans + 16384, meta={"max_active_plans": 100000, "sim_start": 600})
+
+
+def sweep_requests(sc: Scenario, n: int, seed: int, tlo: int = 600, thi: int = 2000) -> np.ndarray:
+    """A batch of FCFS requests shaped like the 20k-plan workload's (horizons U[60, 1800],
+    destination 0.8 v H from the origin), departing U[tlo, thi]."""
+    rng = np.random.default_rng(seed)
+    return make_requests(rng, sc.box, n, hm=sc.heightmap, zspan=(60.0, 500.0), tlo=tlo, thi=thi,
+                         horizon_range=(60, 1800), reach_frac=0.8)
 
 
 def poisson_arrivals(seed: int, rate_per_s: float, duration_s: float) -> np.ndarray:
@@ -325,14 +336,16 @@ def poisson_arrivals(seed: int, rate_per_s: float, duration_s: float) -> np.ndar
 
 
 def serving_requests(sc: Scenario, arrival_s: np.ndarray, seed: int, time_scale: float,
-                     lead_s=(120.0, 600.0), horizon_range=(60, 1200), reach_frac=0.5) -> np.ndarray:
+                     lead_s=(120.0, 600.0), horizon_range=(60, 1200), reach_frac=0.5,
+                     sim_start: int = 0) -> np.ndarray:
     """One request per arrival: it departs `lead` simulated seconds after its arrival on the
-    simulated clock (arrival x time_scale), towards a destination reach_frac v H away."""
+    simulated clock (sim_start + arrival x time_scale), towards a destination reach_frac v H
+    away."""
     rng = np.random.default_rng(seed)
     req = make_requests(rng, sc.box, len(arrival_s), hm=sc.heightmap, zspan=(60.0, 500.0), tlo=0, thi=0,
                         horizon_range=horizon_range, reach_frac=reach_frac)
     lead = rng.uniform(*lead_s, size=len(arrival_s))
-    req["depart"] = np.floor((arrival_s * time_scale + lead) / sc.dt).astype(np.int64)
+    req["depart"] = sim_start + np.floor((arrival_s * time_scale + lead) / sc.dt).astype(np.int64)
     return req
 
 

@@ -136,20 +136,25 @@ def test_packed_plans_reject_mismatched_arrays_before_any_call():
     assert fmdp.Scheduler.add_plans_packed(s, [], [], np.zeros((0, 3), np.float32)).size == 0
 
 
-def test_q_eval_alu_figure_of_the_bench():
-    """The bench's q_eval figure: 12 FP32 flops per (plan sample, action, well) test over
-    the rollout kernel's time, against SMs x FP32 lanes x 2 x the maximum SM clock."""
+def test_q_eval_figure_of_the_bench():
+    """The bench's q_eval figure: the well scan's operations as the kernel performs them
+    (20 FP32 + 1 MUFU per sample culled, 7 FP32 per well of a sample inside the cull radius,
+    10 FP32 + 1 MUFU per (sample, reachable well) pair and action) over the rollout kernel's
+    time, against the rates the device probe measured."""
     import sys as _sys
 
     _sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     import bench
 
-    kt = dict(rollout_steps=1000, rollout_ms=2.0, items_scanned=40_000, slots_scanned=0)
-    q = bench.q_eval_alu(kt, 25, 5, 2070.0)
-    assert q["bound"] == "alu" and q["unit"] == "TFLOP/s"
-    assert q["well_tests_per_rollout_step"] == 40 * 25 * 5
-    assert q["achieved"] == pytest.approx(12 * 40_000 * 125 / 2e-3 / 1e12)
-    assert q["peak"] == pytest.approx(152 * 128 * 2 * 2.07e9 / 1e12)
-    assert q["frac"] == pytest.approx(q["achieved"] / q["peak"])
-    assert bench.q_eval_alu(dict(kt, items_scanned=0, slots_scanned=5000), 25, 5, 2070.0)["achieved"] > 0
-    assert bench.q_eval_alu(dict(kt, rollout_steps=0), 25, 5, 2070.0) is None
+    kt = dict(rollout_steps=1000, qe_items=40_000, qe_near=3_000, qe_wells=1_000)
+    peaks = dict(fp32_tflops=80.0, mufu_rsqrt_tops=5.0, sm_mhz=2000.0)
+    q = bench.q_eval_counted(kt, 25, 5, peaks, 1900.0, 2.0)
+    assert q["bound"] == "alu"
+    fp32 = 20 * 40_000 + 7 * 5 * 3_000 + 10 * 25 * 1_000
+    mufu = 40_000 + 25 * 1_000
+    assert q["counted"]["fp32_ops"] == fp32 and q["counted"]["mufu_ops"] == mufu
+    assert q["fp32"]["achieved"] == pytest.approx(fp32 / 2e-3 / 1e12)
+    assert q["fp32"]["frac"] == pytest.approx(q["fp32"]["achieved"] / 80.0)
+    assert q["mufu"]["frac"] == pytest.approx(mufu / 2e-3 / 1e12 / 5.0)
+    assert bench.q_eval_counted(dict(kt, qe_items=0), 25, 5, peaks, None, 2.0) is None
+    assert bench.q_eval_counted(kt, 25, 5, None, None, 2.0) is None

@@ -449,3 +449,23 @@ def test_exact_ties_go_to_the_lowest_action_index():
     assert list(best) == [ACT15.index(a) for a in ((-30.0, -2.0), (-30.0, 2.0), (30.0, -2.0), (30.0, 2.0))]
     d = o.rollout(req(1000.0, 5000.0, 200.0, 9000.0, 5000.0, 200.0, speed=30.0, horizon=1))
     assert d["actions"][0] == 0
+
+
+def test_threaded_oracle_gives_the_same_results():
+    """The multi-core oracle (a step's actions valued on several threads) computes every
+    value as the single-threaded one does: identical trajectories, values and verdicts."""
+    import oracle as O
+    from paper_2008_03518_gb300 import scenarios as S
+
+    sc = S.c1_plain_small()
+    out = []
+    try:
+        for n in (1, 4):
+            O.set_threads(n)
+            o = O.Oracle.from_scenario(sc)
+            out.append([o.schedule(r) for r in sc.requests[:6]])
+    finally:
+        O.set_threads(1)
+    for a, b in zip(*out):
+        assert a["verdict"] == b["verdict"]
+        np.testing.assert_array_equal(a["xyz"], b["xyz"])
