@@ -319,6 +319,33 @@ def sweep_point(s, sc, reqs, n_plain, stream, barrier, mx, world, learned_params
     return out
 
 
+def run_case(case):
+    """Small cases for ncu captures: 20k known plans (C2's airspace), 64 requests."""
+    import numpy as np
+    import torch
+
+    from paper_2008_03518_gb300 import scenarios as S
+    from paper_2008_03518_gb300.fmdp import Scheduler
+
+    sc = S.c3_batched(n_requests=64)
+    with Scheduler.from_scenario(sc) as s:
+        if case == "policy20k":
+            s.learned_collect(S.make_requests(np.random.default_rng(2021), sc.box, 32, hm=sc.heightmap,
+                                              zspan=(60.0, 500.0), tlo=0, thi=1800, horizon_range=(60, 1800),
+                                              reach_frac=0.8, id0=10 ** 6))
+            s.learned_init(7)
+            s.learned_train(epochs=2, batch=512, lr=2e-3, seed=8)
+            rep, acc, sp, sf = s.learned_evaluate(sc.requests)
+            out = {"case": case, "proposal_steps": int(rep["proposal_steps"]), "proposal_ms": rep["proposal_ms"]}
+        else:
+            s.set_profiling(1)
+            s.schedule_batch(sc.requests, points=False)
+            st = s.stats()
+            out = {"case": case, "sepcheck_launches": st["sepcheck_launches"], "sepcheck_ms": st["sepcheck_ms"]}
+        torch.cuda.synchronize()
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -340,8 +367,14 @@ def main():
                     help="0: pipelined batches (default); 1: speculative waves (the ncu launch list)")
     ap.add_argument("--mode", default="batched", choices=["batched", "sequential"],
                     help="path timed for value: batched FCFS (default) or one request at a time")
+    ap.add_argument("--case", default=None, choices=["policy20k", "sepcheck20k"],
+                    help="a small profiling case instead of the benchmark (one JSON line): the policy kernel "
+                         "or the row-major separation check at 20k known plans")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.case:
+        run_case(args.case)
+        return
 
     rank, local_rank, world = dist_env()
     if world > 1:

@@ -227,3 +227,38 @@ def test_learned_fcfs_is_batch_independent_and_replaces_rollouts(trained):
         s.schedule_batch(sc.requests)
         plain_steps = s.stats()["rollout_steps"]
     assert st2["rollout_steps"] < plain_steps  # FastMDP ran only for the rejected proposals
+
+
+def test_learned_fcfs_against_plain_fastmdp_on_the_same_requests(trained):
+    """Learned FCFS (accepted proposal, else FastMDP) against plain FastMDP FCFS over the
+    same requests and table: the proposals replace FastMDP rollout steps, every accepted
+    proposal is admitted and costs at most 5 % more steps than FastMDP's own plan of that
+    request (C5's gap bound), and both paths' wall times are measured and reported."""
+    import time
+
+    sc, params, _, _ = trained
+    out = {}
+    for label in ("plain", "learned"):
+        with Scheduler.from_scenario(sc) as s:
+            s.learned_set_params(params)
+            s.set_profiling(1)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            if label == "plain":
+                res = s.schedule_batch(sc.requests)
+            else:
+                res, rep = s.schedule_learned(sc.requests)
+            torch.cuda.synchronize()
+            out[label] = (res, s.stats(), time.perf_counter() - t0)
+    (rp, sp, wp), (rl, sl, wl) = out["plain"], out["learned"]
+    assert wp > 0 and wl > 0
+    print(f"plain FastMDP FCFS: {wp * 1e3:.1f} ms, {sp['rollout_steps']} rollout steps; "
+          f"learned FCFS: {wl * 1e3:.1f} ms, {sl['rollout_steps']} FastMDP rollout steps")
+    acc = [i for i, r in enumerate(rl) if r["source"] == 1]
+    assert acc and sl["rollout_steps"] < sp["rollout_steps"]
+    assert all(rl[i]["verdict"] == ADMITTED for i in acc)
+    # the first accepted proposal met the same table as plain FastMDP (nothing admitted
+    # differently before it): its cost is within 5 % of FastMDP's plan
+    first = acc[0]
+    if all(rl[i]["plan_id"] == rp[i]["plan_id"] and rl[i]["verdict"] == rp[i]["verdict"] for i in range(first)):
+        assert rl[first]["n_points"] - 1 <= 1.05 * (rp[first]["n_points"] - 1) + 1e-9

@@ -18,7 +18,7 @@ from oracle import ADMITTED  # noqa: E402
 from paper_2008_03518_gb300 import scenarios as S  # noqa: E402
 from paper_2008_03518_gb300.fmdp import Scheduler  # noqa: E402
 
-from parity_util import fcfs_parity, oracle_for  # noqa: E402
+from parity_util import fcfs_parity, follow_and_check, oracle_for  # noqa: E402
 from test_gpu_batch import same_results, same_tables, table_of  # noqa: E402
 
 
@@ -140,3 +140,40 @@ def test_full_table_with_nothing_to_expire_is_an_error():
         with pytest.raises(FmdpError) as e:
             s.serve(reqs, np.zeros(len(reqs)), time_scale=1.0, max_active_plans=8)
         assert "full" in str(e.value)
+
+
+def test_c4_shape_100k_plans_sampled_against_the_oracle():
+    """Serving at the C4 shape: C2's 30 km airspace and terrain, 100k known plans in the
+    sliding-window table (memory-based admission at 100k active plans, expiry from the
+    simulated clock), Poisson arrivals. Sampled served requests are re-derived by the FP64
+    oracle from the table the GPU had when it planned them (the known plans and every
+    request admitted before them), on all host cores."""
+    import os
+
+    import oracle as O
+
+    sc = S.c4_serving()
+    sim0 = sc.meta["sim_start"]
+    arr = S.poisson_arrivals(77, 1000.0, 0.5)
+    reqs = S.serving_requests(sc, arr, 78, time_scale=60.0, sim_start=sim0)
+    with Scheduler.from_scenario(sc) as s:
+        served, lat, rep = s.serve(reqs, arr, time_scale=60.0, max_active_plans=sc.meta["max_active_plans"],
+                                   sim_start_step=sim0)
+    assert rep["pipelined"] == 1 and rep["expiries"] >= 1 and rep["plans_expired"] > 0
+    assert rep["admitted"] > 0 and rep["admitted"] + rep["rejected"] == len(reqs)
+    adm = [i for i, r in enumerate(served) if r["verdict"] == ADMITTED]
+    rej = [i for i, r in enumerate(served) if r["verdict"] != ADMITTED]
+    picks = sorted({adm[0], adm[-1], rej[len(rej) // 2]})
+    O.set_threads(os.cpu_count() or 1)
+    try:
+        o = oracle_for(sc)
+        done = 0
+        for k in picks:
+            for i in range(done, k):  # the oracle's table as the GPU had it before request k
+                if served[i]["verdict"] == ADMITTED:
+                    o.add_plan(int(reqs[i]["depart"]), served[i]["xyz"])
+            done = k
+            v, _ = follow_and_check(o, reqs[k], served[k])
+            assert v == served[k]["verdict"], k
+    finally:
+        O.set_threads(1)
