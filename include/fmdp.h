@@ -486,6 +486,13 @@ typedef struct {
     int64_t qe_items;            /* indexed rollouts (on >= 1): plan samples culled by the well scan */
     int64_t qe_near;             /* ... of them inside the cull radius (their wells are masked) */
     int64_t qe_wells;            /* (sample, reachable well) pairs valued, each for every action */
+    int64_t pipe_head_n[5];      /* pipelined: requests by how they waited at the head of the line:
+                                    [0] plan ready and valid, [1] plan in flight, then valid, [2] in
+                                    flight, then planned again, [3] ready but planned again, [4] not
+                                    yet dispatched */
+    double pipe_head_s[5];       /* ... and the wall seconds they waited there, per kind */
+    int64_t pipe_publishes;      /* pipelined: tentative plans published for later requests */
+    int64_t pipe_withdrawals;    /* pipelined: tentative plans withdrawn (superseded or rejected) */
 } fmdp_stats;
 /* Switches the batch mode (fmdp_options.batch_mode) of later calls: 0 pipelined, 1 waves. */
 fmdp_status fmdp_set_batch_mode(fmdp_ctx* ctx, int32_t mode);

@@ -70,15 +70,24 @@ struct TableView {
 // Spatial index of the plan table (one per ring row, rebuilt or appended as rows change).
 // Row r holds one item per slot with a sample at the row's step T: the sample p(T) and the
 // same slot's sample p(T+1) (NaN when there is none), 32 bytes; the first float4's w holds
-// the slot number (its int32 bits). Items are grouped by the
-// 2-D cell of p(T) (ncx x ncy cells of `cell` metres over the airspace box, positions
+// a tag (its int32 bits): the slot number (>= 0) of a stored plan; during a pipelined call
+// also -(o + 2) for a sample of the tentative plan of the request with FCFS ordinal o
+// (seen only by the rollouts of later requests), or -1 for a withdrawn tentative sample.
+// Items are grouped by the 2-D cell of p(T) (ncx x ncy cells of `cell` metres over the airspace box, positions
 // outside the box clamped to the edge cells), in cell order; after the last cell comes the
 // extra list, scanned for every query: items moving faster than vmax (their wells reach
 // further than the cell query covers) and items appended since the row was last rebuilt.
+constexpr int32_t kTagDead = -1;
+__host__ __device__ __forceinline__ int32_t tentative_tag(int32_t ord) { return -(ord + 2); }
+// Is an item with this tag part of the table that the request with ordinal my_ord plans
+// against? (stored plans always; tentative plans of earlier requests; never withdrawn ones)
+__host__ __device__ __forceinline__ bool tag_visible(int32_t tag, int32_t my_ord) {
+    return tag >= 0 || (tag <= -2 && -tag - 2 < my_ord);
+}
 struct IndexView {
     const int32_t* cstart;  // [T_win][ncell + 1]: first item of each cell; [ncell] = extra list start
     const int32_t* nextra;  // [T_win]: items in the extra list
-    const float4* items;    // [T_win][S_pad][2]: {x, y, z, 0} at T and at T + 1
+    const float4* items;    // [T_win][S_pad][2]: {x, y, z, tag} at T and {x, y, z, 0} at T + 1
     int32_t ncx, ncy, ncell;
     float x0, y0, inv_cell;  // cell of x: floor((x - x0) * inv_cell), clamped
     float vmax;              // speed bound of the items outside the extra list (m/s)
@@ -145,6 +154,7 @@ struct PipeArgs {
     float* st_df;             // device [n][cap][6]: hi, lo of x, y, z
     uint8_t* st_h;            // device [n][cap]
     uint8_t* ties;            // device [n][cap]
+    int32_t ord0;             // FCFS ordinal of the call's request 0 (request r: ord0 + r)
 };
 
 struct RolloutArgs {
@@ -283,6 +293,9 @@ cudaError_t prepare_index_kernels(size_t smem);
 struct IndexAppendArgs {
     IndexArgs ix;
     const int32_t* slots;  // slot of request r (force mode: of plan r), stored in each item
+    int32_t tentative;     // 1: tag the items tentative_tag(tent_ord) instead of the slot, take
+    int32_t tent_ord;      // the trajectory whatever its verdict, and record each sample's
+    int32_t* tpos;         // position in tpos[r][k] (-1: not stored); 0: stored plans
     const float* traj;
     int32_t cap;
     const RolloutOut* rout;
@@ -299,6 +312,9 @@ struct IndexAppendArgs {
 cudaError_t launch_index_append(const IndexAppendArgs& a, int n_items, int max_points, cudaStream_t s);
 // Publishes the appended items of every row (nextra = nres); launched after the appends.
 cudaError_t launch_index_publish(const IndexArgs& a, cudaStream_t s);
+// Withdraws the tentative items of one trajectory (n samples from step t0, positions
+// tpos[0 .. n) as its append recorded them): their tag becomes kTagDead.
+cudaError_t launch_index_withdraw(const IndexArgs& a, const int32_t* tpos, int64_t t0, int32_t n, cudaStream_t s);
 // *p = v with release semantics (a counter that readers acquire), one thread
 cudaError_t launch_store_release(int32_t* p, int32_t v, cudaStream_t s);
 // Separation check of a batch's work items, row by row: block b takes step t_base + b, the

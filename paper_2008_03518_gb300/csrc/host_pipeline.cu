@@ -2,31 +2,36 @@
 //
 // First-come-first-served planning (Sec. I, Sec. V) admits request k against every plan
 // admitted before it. Speculative batching plans many requests at once and keeps a plan
-// only when no earlier admission could have changed it (the influence test). Here the
+// only when nothing it did not see could have changed it (the influence test). Here the
 // planning never stops at a wave boundary:
 //   - one persistent rollout launch (one CTA per work item) takes work items from a ring
 //     in host-mapped memory that the host appends to while the launch runs;
-//   - each finished plan is checked for conflicts against the plans the index holds at
-//     that moment and reported, with its trajectory, to host-mapped memory;
-//   - the host walks the requests in arrival order as their plans land: a request is final
-//     once every admission made after its plan was dispatched has been tested and none
-//     influences it; an admitted request is stored at once (scatter into the plan table,
-//     index append, publish) on a high-priority table stream, beside the running rollouts;
-//   - a plan that an admission influences is planned again as soon as that admission is
-//     visible, without waiting for any other rollout.
-// Exactness. A rollout reads the index while admissions are appended to it. An appended
-// item becomes visible only when it is complete (published after its append kernel), so a
-// rollout sees, at every step, each admitted plan's sample either whole or not at all. A
-// plan that does not influence request k adds an exact zero to every value k's rollout
-// computes whether it is visible or not, so k's plan equals its plan against any table
-// between the one at its dispatch and the final one, unless an admission made after the
-// dispatch influences it - and each of those is tested. The index only ever holds plans of
-// requests before the one being planned (the walk admits in arrival order and stops at the
-// first unresolved request), so a conflict found against it is real; an unseen admission
-// that could add a conflict influences the plan (separation minima + 1 m). Row rebuilds,
-// which move items, happen only while no rollout runs. The exact separation report of each
-// request (minimum separations to every earlier plan) comes from the row-major check with
-// an ordinal filter: it skips plans admitted after the request.
+//   - each finished plan is checked for conflicts against the plans its request's table
+//     holds at that moment and reported, with its trajectory, to host-mapped memory;
+//   - the requests just behind the head of the line publish their current plans as
+//     tentative plans in the index: a tentative plan of request j is part of the table of
+//     every later request (the guess that j will be admitted as planned), so a later
+//     request plans against it at once instead of after j's admission. A superseded or
+//     rejected tentative plan is withdrawn;
+//   - the host walks the requests in arrival order: a request is final once every change of
+//     an earlier request's contribution (a tentative plan published or withdrawn) has been
+//     tested against its plan and none influences it; an admitted request is stored on a
+//     high-priority table stream, beside the running rollouts, and its tentative plan stays;
+//   - a plan that a change influences is planned again as soon as the change is visible,
+//     from the first step it can alter (the steps before it keep their decisions).
+// Exactness. FastMDP's choice at a step depends only on the state and the table at the next
+// step, and a plan whose wells cannot reach the successors adds an exact zero. Every table
+// change (an index append then its publication, or a withdrawal) is a numbered operation
+// that raises a device counter when it completes; each rollout step records the counter it
+// read before the index rows it valued, so the host knows, step by step, which versions of
+// an earlier request's plan the step could have seen. A step is exact if the earlier
+// requests' final contributions were visible to it and nothing else of theirs was, or if
+// the difference has no influence at that step; the walk tests exactly the differences. An
+// appended item becomes visible only when complete, and a withdrawal only flips its tag, so
+// each item is read either whole or not at all. Row rebuilds, which move items, happen
+// only while no rollout runs; the tentative plans are published again after them. The exact
+// separation report of each request (minimum separations to every earlier plan) comes from
+// the row-major check with an ordinal filter: it skips plans of later requests.
 #include "host.cuh"
 
 namespace fmdp {
@@ -54,10 +59,11 @@ struct MappedArray {
     }
 };
 
-constexpr int kQueueCap = 4096;          // ring entries (a power of two)
-constexpr int kBoxChunk = 32;            // steps per bounding box of a trajectory
-constexpr int32_t kPipeExtraLimit = 96;  // appended items per row before the rows are rebuilt
-constexpr int32_t kOrdLimit = 1 << 30;   // ordinals are rebased before they reach this
+constexpr int kQueueCap = 4096;           // ring entries (a power of two)
+constexpr int kBoxChunk = 32;             // steps per bounding box of a trajectory
+constexpr int32_t kPipeExtraLimit = 192;  // appended items per row before the rows are rebuilt
+constexpr int32_t kPublishAhead = 32;     // requests past the head whose plans are published
+constexpr int32_t kOrdLimit = 1 << 30;    // ordinals are rebased before they reach this
 
 }  // namespace
 
@@ -72,9 +78,9 @@ struct PipeState {
     MappedArray<PipeRecord> rec;
     MappedArray<float> h_traj;
     MappedArray<int32_t> h_slot;  // slot of an admitted request (read by its admission)
-    MappedArray<int32_t> h_obs;   // per plan step: admissions published when its rows were read
-    DevArray<int32_t> head, pub_seq, obs;
-    DevArray<double> st_s;        // per trajectory point: what a resumed plan starts from
+    MappedArray<int32_t> h_obs;   // per plan step: table operations done when its rows were read
+    DevArray<int32_t> head, pub_seq, obs, tpos;
+    DevArray<double> st_s;  // per trajectory point: what a resumed plan starts from
     DevArray<float> st_df;
     DevArray<uint8_t> st_h, ties;
     DevArray<SepOut> sep;
@@ -87,8 +93,8 @@ struct PipeState {
         if (pstream) cudaStreamSynchronize(pstream);
         if (tstream) cudaStreamSynchronize(tstream);
         ring.release(); ctl.release(); done.release(); rec.release(); h_traj.release(); h_slot.release();
-        h_obs.release(); pub_seq.release(); obs.release(); st_s.release(); st_df.release(); st_h.release();
-        ties.release();
+        h_obs.release(); pub_seq.release(); obs.release(); tpos.release(); st_s.release(); st_df.release();
+        st_h.release(); ties.release();
         head.release(); sep.release(); slot_ord.release(); req_ord.release(); list.release(); nlist.release();
         h_list.release();
         for (cudaEvent_t e : ev_free) cudaEventDestroy(e);
@@ -113,17 +119,22 @@ namespace {
 // ---------------------------------------------------------------- influence (host side)
 
 // Bounding boxes of a trajectory over chunks of kBoxChunk steps, its largest speed, and for
-// each chunk the fewest admissions any of its steps could see (obs: per step, or null).
+// each chunk the range of table-operation counts its decision steps read (obs: per step, or
+// null).
 struct TrajBoxes {
-    std::vector<float> b;    // [chunks][6]: min x y z, max x y z
-    std::vector<int32_t> o;  // [chunks]: smallest obs of the chunk's decision steps
+    std::vector<float> b;                // [chunks][6]: min x y z, max x y z
+    std::vector<int32_t> omin, omax;     // [chunks]
     double vmax = 0.0;
     void build(const float* p, int n, double dt, const int32_t* obs = nullptr) {
         const int nc = (n + kBoxChunk - 1) / kBoxChunk;
         b.assign((size_t)nc * 6, 0.f);
-        o.assign(nc, INT32_MAX);
+        omin.assign(nc, INT32_MAX);
+        omax.assign(nc, INT32_MIN);
         if (obs)
-            for (int i = 0; i + 1 < n; ++i) o[i / kBoxChunk] = std::min(o[i / kBoxChunk], obs[i]);
+            for (int i = 0; i + 1 < n; ++i) {
+                omin[i / kBoxChunk] = std::min(omin[i / kBoxChunk], obs[i]);
+                omax[i / kBoxChunk] = std::max(omax[i / kBoxChunk], obs[i]);
+            }
         double v2 = 0.0;
         for (int c = 0; c < nc; ++c) {
             float* o = b.data() + 6 * c;
@@ -149,23 +160,22 @@ struct InflRule {
     double tau[kMaxWells], R[kMaxWells];
 };
 
-// Could plan j (admitted as the call's admission number aj, before k) change request k's
-// plan or verdict? The rule of the batched path's influence kernel (one-step window), taken
-// only where k's rollout could not see j: k's state at a step whose index rows were read
-// before j was published (obs_k[i] <= aj) within reach of one of j's wells one step later
-// (well w at p_j + tau_w v_j, radius R_w, reach R_w + the successor offset + 1 m); or, when
-// k's conflict check read the index before j was published (aj >= tail_pub), the two within
-// the separation minima + 1 m at one step. At a step that saw j, k's decision already
-// counted j's wells exactly. Chunk bounding boxes skip the steps where the two are far apart.
-// Returns the first decision step that j could change (-1: none); *sep: j could change the
-// verdict. The steps before the first one keep their decisions, so the plan may go on from
-// its state there.
-int first_influenced(const InflRule& P, const float* pj, int nj, int64_t tj, const TrajBoxes& bj, int32_t aj,
-                     const float* pk, int nk, int64_t tk, double speed_k, const TrajBoxes& bk, const int32_t* obs_k,
-                     int32_t tail_pub, bool* sep) {
+// Could trajectory j (of a request before k) change request k's plan or verdict at the steps
+// where its presence in k's table differs from what k's rollout read? The rule of the
+// batched path's influence kernel (one-step window), taken only at those steps: k's state at
+// a step whose index rows were read with a table-operation count in [q_lo, q_hi) within
+// reach of one of j's wells one step later (well w at p_j + tau_w v_j, radius R_w, reach R_w
+// + the successor offset + 1 m); or, when k's conflict check read the index with a count in
+// [q_lo, q_hi), the two within the separation minima + 1 m at one step. Chunk bounding boxes
+// skip the steps where the two are far apart. Returns the first decision step j could
+// change (-1: none); *sep: j could change the verdict. The steps before the first one keep
+// their decisions, so the plan may go on from its state there.
+int first_influenced(const InflRule& P, const float* pj, int nj, int64_t tj, const TrajBoxes& bj, int32_t q_lo,
+                     int32_t q_hi, const float* pk, int nk, int64_t tk, double speed_k, const TrajBoxes& bk,
+                     const int32_t* obs_k, int32_t tail_obs, bool* sep) {
     *sep = false;
     if (nk <= 0 || nj <= 0 || !(tk < tj + nj && tj < tk + nk)) return -1;
-    const bool sep_unseen = aj >= tail_pub;
+    const bool sep_unseen = q_lo <= tail_obs && tail_obs < q_hi;
     const double rho = speed_k * P.dt + P.dzmax + 1.0;
     double e = std::max(P.H, P.V);
     for (int w = 0; w < P.n_wells; ++w) e = std::max(e, P.R[w] + 1.0 + rho + std::fabs(P.tau[w]) * bj.vmax);
@@ -173,7 +183,8 @@ int first_influenced(const InflRule& P, const float* pj, int nj, int64_t tj, con
     const int nck = (nk + kBoxChunk - 1) / kBoxChunk;
     for (int c = 0; c < nck; ++c) {
         const int i0 = c * kBoxChunk, i1 = std::min(nk, i0 + kBoxChunk);
-        if ((!sep_unseen || *sep) && bk.o[c] > aj) continue;  // every step of the chunk saw j
+        const bool wells_here = bk.omax[c] >= q_lo && bk.omin[c] < q_hi;
+        if (!wells_here && (!sep_unseen || *sep)) continue;
         // j's samples a step of this chunk can meet: the same step, the next, and the one
         // after it (the next sample's velocity)
         const int64_t jlo = std::max<int64_t>(0, tk + i0 - tj), jhi = std::min<int64_t>(nj - 1, tk + i1 - 1 - tj + 2);
@@ -198,7 +209,8 @@ int first_influenced(const InflRule& P, const float* pj, int nj, int64_t tj, con
                 if (dx * dx + dy * dy < P.H * P.H && std::fabs(dz) < P.V) *sep = true;
             }
             const int64_t t1 = t0 + 1;
-            if (i + 1 >= nk || obs_k[i] > aj || t1 < 0 || t1 >= nj) continue;  // no decision, or it saw j
+            // no decision at the last point; a step outside [q_lo, q_hi) read j as it stands
+            if (i + 1 >= nk || obs_k[i] < q_lo || obs_k[i] >= q_hi || t1 < 0 || t1 >= nj) continue;
             const float* q1 = pj + 3 * t1;
             double vx = 0.0, vy = 0.0, vz = 0.0;
             if (t1 + 1 < nj) {
@@ -218,6 +230,23 @@ int first_influenced(const InflRule& P, const float* pj, int nj, int64_t tj, con
 }
 
 enum Phase : uint8_t { kAbsent = 0, kWait = 1, kFlight = 2, kDone = 3, kFinal = 4 };
+
+// A published tentative plan of one request: visible to reads made with a table-operation
+// count in [q_pub, q_kill).
+struct Version {
+    int32_t j;
+    int32_t n;
+    int32_t q_pub, q_kill;
+    std::vector<float> xyz;
+    TrajBoxes boxes;
+};
+
+// A change of request j's contribution to the tables of later requests.
+struct Change {
+    int32_t j;
+    int32_t v_old, v_new;  // versions withdrawn and published (-1: none)
+    int32_t q_last;        // the last table operation of the change
+};
 
 }  // namespace
 
@@ -253,6 +282,7 @@ int32_t run_pipeline(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_resu
     P.h_slot.ensure(R);
     P.h_obs.ensure(R * (size_t)cap);
     P.obs.ensure(R * (size_t)cap);
+    P.tpos.ensure(R * (size_t)cap);
     P.pub_seq.ensure(1);
     P.st_s.ensure(R * (size_t)cap * 3);
     P.st_df.ensure(R * (size_t)cap * 6);
@@ -285,25 +315,29 @@ int32_t run_pipeline(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_resu
 
     // per-request state
     std::vector<uint8_t> phase(n, serve ? kAbsent : kWait);  // a batch's requests are all there
-    std::vector<int32_t> seen(n, 0), chk(n, 0), gate(n, 0), tok(n, 0), slot_of(n, -1), verdict(n, -1),
-        replans(n, 0), tail_pub(n, 0), start(n, 0);
+    std::vector<int32_t> chk(n, 0), gate(n, 0), tok(n, 0), slot_of(n, -1), verdict(n, -1), replans(n, 0),
+        tail_obs(n, 0), start(n, 0), cur(n, -1), contrib_tok(n, 0);
     std::vector<uint64_t> ids(n, 0);
     std::vector<RolloutOut> fin_ro(n);
     std::vector<TrajBoxes> boxes(n);
     std::vector<double> t_disp(n, 0.0), done_at(n, -1.0);
-    std::vector<int32_t> A;  // admitted requests in admission (= arrival) order
-    std::vector<int32_t> inflight;
-    struct Pub {
-        int32_t a;
+    std::vector<Version> V;
+    std::vector<Change> E;      // contribution changes, in table-operation order
+    size_t e_done = 0;          // E[0 .. e_done) have completed all their operations
+    int32_t ops = 0;            // table operations enqueued (numbered 1 .. ops)
+    int32_t ops_done = 0;       // ... and known complete
+    struct OpEv {
+        int32_t q;
         cudaEvent_t ev;
     };
-    std::vector<Pub> pend;  // admissions enqueued, not yet known complete
-    size_t pend_head = 0;
-    int32_t pub = 0;        // admissions whose table writes have completed
+    std::vector<OpEv> op_ev;    // completion events of enqueued operations, in order
+    size_t op_head = 0;
+    std::vector<int32_t> inflight;
     std::vector<int32_t> xcnt(c->T_win, 0);
     int32_t xmax = 0;
     bool draining = false;
-    cudaEvent_t rebuild_ev = nullptr;
+    int32_t dispatch_gate = 0;  // after a drain: operations that must be complete first
+    bool tentative_used = false;
     std::vector<int32_t> unreported;
     for (int32_t k = 0; k < n; ++k) P.done.p[k] = 0;
     // ordinals of the call's requests, for the exact separation report
@@ -365,6 +399,7 @@ int32_t run_pipeline(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_resu
     ra.pipe.st_df = P.st_df.p;
     ra.pipe.st_h = P.st_h.p;
     ra.pipe.ties = P.ties.p;
+    ra.pipe.ord0 = ord0;
     CK(cudaMemsetAsync(P.pub_seq.p, 0, sizeof(int32_t), P.tstream));
     int32_t tail = 0;
     P.ctl.p[0] = 0;
@@ -409,7 +444,12 @@ int32_t run_pipeline(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_resu
     auto elapsed = [&]() { return std::chrono::duration<double>(clk::now() - t0).count(); };
     double cta_time = 0.0, last_progress = 0.0;
     int64_t n_dispatch = 0, n_replans = 0, n_drains = 0, steps_sum = 0, n_resumes = 0, n_rechecks = 0;
+    int64_t n_publish = 0, n_withdraw = 0;
     int32_t head = 0, joined = serve ? 0 : n, finalized = 0, admitted = 0, max_seen = 0;
+    // how each head of line waited (statistics): its phase and re-plans when it became head
+    int32_t head_mark = -1, head_replans = 0;
+    uint8_t head_phase = kAbsent;
+    double head_since = 0.0;
     int64_t expiries = 0, expired = 0;
     int32_t deferred = 0;
     std::vector<uint8_t> deferred_flag(serve ? n : 0, 0);
@@ -465,7 +505,80 @@ int32_t run_pipeline(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_resu
         }
         L.clear();
     };
-    // stores an admitted request: scatter, index append and publish on the table stream
+    // a table operation was just enqueued: number it, raise the device counter after it, and
+    // keep an event to learn when it is complete
+    auto close_op = [&]() {
+        ++ops;
+        LAUNCH(c, launch_store_release(P.pub_seq.p, ops, P.tstream));
+        cudaEvent_t ev;
+        if (P.ev_free.empty()) {
+            CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        } else {
+            ev = P.ev_free.back();
+            P.ev_free.pop_back();
+        }
+        CK(cudaEventRecord(ev, P.tstream));
+        op_ev.push_back({ops, ev});
+        return ops;
+    };
+    auto count_rows = [&](int32_t k, int32_t np) {  // the rows a trajectory was appended to
+        const int64_t d = reqs[k].depart_step;
+        for (int32_t i = 0; i < np; ++i) {
+            const int64_t T = d + i;
+            if (T < c->book.t_base || T >= c->book.t_base + c->T_win) continue;
+            int64_t row = T % c->T_win;
+            if (row < 0) row += c->T_win;
+            xmax = std::max(xmax, ++xcnt[row]);
+        }
+    };
+    // appends request k's latest plan (as planned on the device) to the index as its
+    // tentative plan and publishes it
+    auto append_tentative = [&](int32_t k, int32_t np) {
+        IndexAppendArgs ia{};
+        ia.ix = index_args(c);
+        ia.tentative = 1;
+        ia.tent_ord = ord0 + k;
+        ia.tpos = P.tpos.p + (size_t)k * cap;
+        ia.traj = B.traj.p + (size_t)k * cap * 3;
+        ia.cap = cap;
+        ia.rout = B.rout.p + k;
+        ia.reqs = B.rq + k;
+        ia.sep = P.sep.p + k;
+        LAUNCH(c, launch_index_append(ia, 1, np, P.tstream));
+        LAUNCH(c, launch_index_publish(ia.ix, P.tstream));
+        count_rows(k, np);
+        tentative_used = true;
+    };
+    // request k's contribution becomes its latest plan (published when admissible) or nothing
+    auto set_contribution = [&](int32_t k) {
+        const int32_t v_old = cur[k];
+        int32_t v_new = -1;
+        if (v_old >= 0) {
+            const Version& x = V[v_old];
+            LAUNCH(c, launch_index_withdraw(index_args(c), P.tpos.p + (size_t)k * cap, reqs[k].depart_step, x.n,
+                                            P.tstream));
+            V[v_old].q_kill = close_op();
+            ++n_withdraw;
+        }
+        if (verdict[k] == FMDP_ADMITTED) {
+            Version x;
+            x.j = k;
+            x.n = fin_ro[k].n_points;
+            x.xyz.assign(P.h_traj.p + (size_t)k * cap * 3, P.h_traj.p + (size_t)k * cap * 3 + 3 * (size_t)x.n);
+            x.boxes = boxes[k];
+            append_tentative(k, x.n);
+            x.q_pub = close_op();
+            x.q_kill = INT32_MAX;
+            v_new = (int32_t)V.size();
+            V.push_back(std::move(x));
+            ++n_publish;
+        }
+        cur[k] = v_new;
+        contrib_tok[k] = tok[k];
+        if (v_old >= 0 || v_new >= 0) E.push_back({k, v_old, v_new, ops});
+    };
+    // stores an admitted request: scatter into the plan table on the table stream (its index
+    // items are its tentative plan's, already published)
     auto admit = [&](int32_t k) {
         const int32_t slot = take_slot(c);
         const uint64_t id = c->book.next_id++;
@@ -487,57 +600,44 @@ int32_t run_pipeline(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_resu
         aa.force = 0;
         aa.slot_ord = P.slot_ord.p;
         aa.ord = ord0 + k;
-        {
-            KernelTimer t(c, 2);
-            LAUNCH(c, launch_admit(aa, 1, fin_ro[k].n_points, P.tstream));
-            t.stop();
-        }
-        index_append_admitted(c, aa.traj, cap, aa.rout, aa.reqs, aa.sep, aa.slots, nullptr, nullptr, 1,
-                              c->book.t_base, c->book.t_base + c->T_win, false);
-        LAUNCH(c, launch_store_release(P.pub_seq.p, (int32_t)A.size() + 1, P.tstream));  // this one is visible
-        cudaEvent_t ev;
-        if (P.ev_free.empty()) {
-            CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-        } else {
-            ev = P.ev_free.back();
-            P.ev_free.pop_back();
-        }
-        CK(cudaEventRecord(ev, P.tstream));
-        pend.push_back({(int32_t)A.size(), ev});
-        A.push_back(k);
+        KernelTimer t(c, 2);
+        LAUNCH(c, launch_admit(aa, 1, fin_ro[k].n_points, P.tstream));
+        t.stop();
         ++admitted;
-        // the rows the plan was appended to (host count of each row's extra list)
-        const int64_t d = reqs[k].depart_step;
-        for (int32_t i = 0; i < fin_ro[k].n_points; ++i) {
-            const int64_t T = d + i;
-            if (T < c->book.t_base || T >= c->book.t_base + c->T_win) continue;
-            int64_t row = T % c->T_win;
-            if (row < 0) row += c->T_win;
-            xmax = std::max(xmax, ++xcnt[row]);
-        }
     };
-    // brings request k's completed plan up to date with the admissions made since its
-    // dispatch; false (and k waits for a new plan) when one of them influences it. The new
+    // brings request k's completed plan up to date with the contribution changes of earlier
+    // requests; false (and k waits for a new plan) when one of them influences it. The new
     // plan keeps the steps before the first one any of them could change, and only the
     // conflict check runs again when none changes a step but one may change the verdict.
     auto check_plan = [&](int32_t k) {
         const int32_t nk = fin_ro[k].n_points;
         const float* pk = P.h_traj.p + (size_t)k * cap * 3;
+        const int32_t* ok = P.h_obs.p + (size_t)k * cap;
         int first = INT32_MAX;
         bool sep_any = false;
-        for (; chk[k] < (int32_t)A.size(); ++chk[k]) {
-            const int32_t j = A[chk[k]];
-            const float* pj = P.h_traj.p + (size_t)j * cap * 3;
+        for (; chk[k] < (int32_t)E.size(); ++chk[k]) {
+            const Change& ch = E[chk[k]];
+            if (ch.j >= k) continue;  // later requests are not part of k's table
+            const int64_t tj = reqs[ch.j].depart_step;
             bool sep = false;
-            const int f = first_influenced(rule, pj, fin_ro[j].n_points, reqs[j].depart_step, boxes[j], chk[k], pk,
-                                           nk, reqs[k].depart_step, reqs[k].speed_mps, boxes[k],
-                                           P.h_obs.p + (size_t)k * cap, tail_pub[k], &sep);
-            if (f >= 0) first = std::min(first, f);
-            sep_any = sep_any || sep;
+            if (ch.v_old >= 0) {  // withdrawn: where k could have seen it
+                const Version& x = V[ch.v_old];
+                const int f = first_influenced(rule, x.xyz.data(), x.n, tj, x.boxes, x.q_pub, x.q_kill, pk, nk,
+                                               reqs[k].depart_step, reqs[k].speed_mps, boxes[k], ok, tail_obs[k], &sep);
+                if (f >= 0) first = std::min(first, f);
+                sep_any = sep_any || sep;
+            }
+            if (ch.v_new >= 0) {  // published: where k could not see it yet
+                const Version& x = V[ch.v_new];
+                const int f = first_influenced(rule, x.xyz.data(), x.n, tj, x.boxes, INT32_MIN, x.q_pub, pk, nk,
+                                               reqs[k].depart_step, reqs[k].speed_mps, boxes[k], ok, tail_obs[k], &sep);
+                if (f >= 0) first = std::min(first, f);
+                sep_any = sep_any || sep;
+            }
         }
         if (first == INT32_MAX && !sep_any) return true;
         phase[k] = kWait;
-        gate[k] = (int32_t)A.size();  // every admission so far visible to the next plan
+        gate[k] = ops;  // every operation so far visible to the next plan
         start[k] = first == INT32_MAX ? -1 : first;
         ++replans[k];
         ++n_replans;
@@ -547,10 +647,9 @@ int32_t run_pipeline(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_resu
     };
     auto dispatch = [&](int32_t k) {
         tok[k] += 1;
-        seen[k] = pub;
-        // a plan from the origin sees every published admission; a resumed plan's kept steps
+        // a plan from the origin reads every completed change; a resumed plan's kept steps
         // were checked up to chk[k] and keep their observations
-        if (start[k] == 0) chk[k] = pub;
+        if (start[k] == 0) chk[k] = (int32_t)e_done;
         PipeItem& it = P.ring.p[tail & (kQueueCap - 1)];
         it.r = k;
         it.token = tok[k];
@@ -570,16 +669,17 @@ int32_t run_pipeline(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_resu
         while (finalized < n) {
             const double now = elapsed();
             bool progress = false;
-            // admissions whose table writes are complete
-            while (pend_head < pend.size()) {
-                const cudaError_t e = cudaEventQuery(pend[pend_head].ev);
+            // table operations that are complete, and the changes they close
+            while (op_head < op_ev.size()) {
+                const cudaError_t e = cudaEventQuery(op_ev[op_head].ev);
                 if (e == cudaErrorNotReady) break;
                 CK(e);
-                pub = pend[pend_head].a + 1;
-                P.ev_free.push_back(pend[pend_head].ev);
-                ++pend_head;
+                ops_done = op_ev[op_head].q;
+                P.ev_free.push_back(op_ev[op_head].ev);
+                ++op_head;
                 progress = true;
             }
+            while (e_done < E.size() && E[e_done].q_last <= ops_done) ++e_done;
             // finished plans
             for (size_t q = 0; q < inflight.size();) {
                 const int32_t k = inflight[q];
@@ -601,25 +701,47 @@ int32_t run_pipeline(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_resu
                                                             : FMDP_ADMITTED;
                 boxes[k].build(P.h_traj.p + (size_t)k * cap * 3, rc.ro.n_points, c->model.dt,
                                P.h_obs.p + (size_t)k * cap);
-                tail_pub[k] = rc.tail_pub;
+                tail_obs[k] = rc.tail_pub;
                 phase[k] = kDone;
                 progress = true;
             }
-            // walk in arrival order; plans behind the head are checked against each admission
-            // (every plan in flight or done lies within the window past the head)
-            for (int32_t k = head; k < std::min(joined, head + window); ++k)
-                if (phase[k] == kDone && chk[k] < (int32_t)A.size()) check_plan(k);
-            while (head < joined && phase[head] == kDone && (chk[head] == (int32_t)A.size() || check_plan(head))) {
+            // plans near the head: up to date with every change, published when they are new
+            const int32_t lim = std::min(joined, head + window);
+            for (int32_t k = head; k < lim; ++k)
+                if (phase[k] == kDone && check_plan(k) && k < head + kPublishAhead && contrib_tok[k] != tok[k])
+                    set_contribution(k);
+            if (head < joined && head_mark != head) {  // a new head of line: how it waits
+                head_mark = head;
+                head_since = now;
+                head_phase = phase[head];
+                head_replans = replans[head];
+            }
+            // the walk: a head whose plan is up to date is final
+            while (head < joined && phase[head] == kDone && check_plan(head)) {
                 const int32_t k = head;
+                if (contrib_tok[k] != tok[k]) set_contribution(k);
                 if (verdict[k] == FMDP_ADMITTED) admit(k);
                 phase[k] = kFinal;
                 done_at[k] = elapsed();
                 unreported.push_back(k);
+                if (head_mark == k) {
+                    const bool again = replans[k] > head_replans;
+                    const int cls = head_phase == kWait ? 4 : head_phase == kFlight ? (again ? 2 : 1) : (again ? 3 : 0);
+                    ++c->stats.pipe_head_n[cls];
+                    c->stats.pipe_head_s[cls] += done_at[k] - head_since;
+                }
                 ++head;
                 ++finalized;
                 progress = true;
-                for (int32_t q = head; q < std::min(joined, head + window); ++q)
-                    if (phase[q] == kDone && chk[q] < (int32_t)A.size()) check_plan(q);
+                if (head < joined) {
+                    head_mark = head;
+                    head_since = done_at[k];
+                    head_phase = phase[head];
+                    head_replans = replans[head];
+                }
+                // the request that joins the published range
+                const int32_t q = head + kPublishAhead - 1;
+                if (q < joined && phase[q] == kDone && check_plan(q) && contrib_tok[q] != tok[q]) set_contribution(q);
             }
             if (progress) last_progress = now;
             if (finalized >= n) break;
@@ -640,17 +762,32 @@ int32_t run_pipeline(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_resu
                     report(unreported);  // before the rows of finished requests can be cleared
                     expire_to(c, limit, &expired);
                     ++expiries;
-                    std::fill(xcnt.begin(), xcnt.end(), 0);
-                    xmax = 0;
                 }
                 if (xmax > kPipeExtraLimit) {  // rows whose extra lists grew long: rebuilt now
                     index_rebuild_all(c);
                     std::fill(xcnt.begin(), xcnt.end(), 0);
                     xmax = 0;
                     ++n_drains;
+                    // the rebuild keeps only stored plans. A tentative plan that is still its
+                    // request's latest plan goes back in (the same version: visible to every
+                    // read after the drain as before it); one whose request has planned again
+                    // since (the device holds the newer plan) is withdrawn
+                    const int32_t q_rebuild = close_op();
+                    for (int32_t k = head; k < joined; ++k) {
+                        if (cur[k] < 0) continue;
+                        if (contrib_tok[k] == tok[k]) {  // (nothing is in flight: the device holds it)
+                            append_tentative(k, V[cur[k]].n);
+                            close_op();
+                        } else {
+                            V[cur[k]].q_kill = q_rebuild;
+                            E.push_back({k, cur[k], -1, q_rebuild});
+                            cur[k] = -1;
+                            contrib_tok[k] = -1;
+                            ++n_withdraw;
+                        }
+                    }
                 }
-                if (!rebuild_ev) CK(cudaEventCreateWithFlags(&rebuild_ev, cudaEventDisableTiming));
-                CK(cudaEventRecord(rebuild_ev, P.tstream));
+                dispatch_gate = ops;
                 draining = false;
             }
             // serving: arrivals join while the set has room and the table has slots for all
@@ -670,48 +807,59 @@ int32_t run_pipeline(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_resu
                 }
                 max_seen = std::max(max_seen, joined - head);
             }
-            // dispatch the waiting requests nearest the head, their admissions visible
-            const bool rebuilt = !rebuild_ev || cudaEventQuery(rebuild_ev) == cudaSuccess;
-            if (!draining && rebuilt) {
+            // dispatch the waiting requests nearest the head, the changes they wait for visible
+            if (!draining && ops_done >= dispatch_gate) {
                 const int32_t end = std::min(joined, head + window);
                 for (int32_t k = head; k < end && (int32_t)inflight.size() < n_ctas; ++k)
-                    if (phase[k] == kWait && gate[k] <= pub) dispatch(k);
+                    if (phase[k] == kWait && gate[k] <= ops_done) dispatch(k);
             }
             if (!inflight.empty() && !kernel_running()) {
                 require(read_error_word(c) == 0, FMDP_ERR_TIMEOUT, "a bounded device wait expired during a rollout");
                 launch();  // the launch left while idle; the ring keeps its position
             }
             if (serve && inflight.empty() && head == joined && joined < n) {
-                const double wait = serve->arrival_s[joined] - elapsed();
-                if (wait > 0) std::this_thread::sleep_for(std::chrono::duration<double>(std::min(wait, 0.002)));
-                if (joined - head == 0 && deferred_flag[joined] && c->book.plans.size() > 0) {
-                    int64_t first_end = INT64_MAX;  // nothing in flight and no room: only expiry frees slots
+                if (deferred_flag[joined]) {  // nothing unresolved and no room: only expiry frees slots
+                    int64_t first_end = INT64_MAX;
                     for (auto& kv : c->book.plans) first_end = std::min(first_end, kv.second.t0 + kv.second.n);
                     require(first_end <= dep_suffix[joined], FMDP_ERR_FULL, "plan table full and no plan can expire");
+                    std::this_thread::sleep_for(std::chrono::microseconds(200));
+                } else {
+                    const double wait = serve->arrival_s[joined] - elapsed();
+                    if (wait > 0) std::this_thread::sleep_for(std::chrono::duration<double>(std::min(wait, 0.002)));
                 }
                 last_progress = elapsed();
             }
             require(elapsed() - last_progress < 30.0, FMDP_ERR_TIMEOUT, "pipelined FCFS made no progress for 30 s");
         }
         stop_kernel();
+        // the index again holds only stored plans (tentative and withdrawn items go), then
+        // the exact separation reports
+        if (tentative_used) index_rebuild_all(c);
         report(unreported);
         CK(cudaStreamSynchronize(P.tstream));
         require(read_error_word(c) == 0, FMDP_ERR_TIMEOUT, "a bounded device wait expired during a rollout");
     } catch (...) {
-        // leave nothing running: stop the launch (it drains the ring), wait for the streams
+        // leave nothing running: stop the launch (it drains the ring), wait for the streams,
+        // and rebuild the index from the stored plans
         if (launched) {
             *reinterpret_cast<volatile int32_t*>(P.ctl.p + 1) = 1;
             cudaEventSynchronize(P.kern_ev);
             *reinterpret_cast<volatile int32_t*>(P.ctl.p + 1) = 0;
         }
         cudaStreamSynchronize(P.tstream);
-        if (rebuild_ev) cudaEventDestroy(rebuild_ev);
+        if (tentative_used) {
+            try {
+                index_rebuild_all(c);
+                cudaStreamSynchronize(P.tstream);
+            } catch (...) {
+            }
+        }
+        for (size_t q = op_head; q < op_ev.size(); ++q) P.ev_free.push_back(op_ev[q].ev);
         c->extra_limit = saved_limit;
         c->stream = user;
         throw;
     }
-    if (rebuild_ev) cudaEventDestroy(rebuild_ev);
-    for (size_t q = pend_head; q < pend.size(); ++q) P.ev_free.push_back(pend[q].ev);
+    for (size_t q = op_head; q < op_ev.size(); ++q) P.ev_free.push_back(op_ev[q].ev);
     c->extra_limit = saved_limit;
     c->stream = user;
     CK(cudaEventRecord(P.sync_ev, P.tstream));
@@ -740,6 +888,8 @@ int32_t run_pipeline(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_resu
     c->stats.pipe_drains += n_drains;
     c->stats.pipe_resumes += n_resumes;
     c->stats.pipe_rechecks += n_rechecks;
+    c->stats.pipe_publishes += n_publish;
+    c->stats.pipe_withdrawals += n_withdraw;
     const double wall = elapsed();
     c->stats.pipe_cta_s += cta_time;
     c->stats.pipe_slot_s += wall * n_ctas;

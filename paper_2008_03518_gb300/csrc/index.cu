@@ -153,8 +153,8 @@ __global__ void index_append_kernel(const __grid_constant__ IndexAppendArgs a) {
     } else {
         if (a.n_dev && (int)blockIdx.y >= *a.n_dev) return;
         const int r = a.idx ? a.idx[blockIdx.y] : (int)blockIdx.y;
-        if (a.sep[r].verdict != FMDP_ADMITTED) return;
-        slot = a.slots[r];
+        if (!a.tentative && a.sep[r].verdict != FMDP_ADMITTED) return;
+        slot = a.tentative ? 0 : a.slots[r];
         n = a.rout[r].n_points;
         t0 = a.reqs[r].depart_step;
         base = a.traj + (size_t)r * a.cap * 3;
@@ -162,8 +162,12 @@ __global__ void index_append_kernel(const __grid_constant__ IndexAppendArgs a) {
     const int32_t W = ix.tab.T_win;
     const int S = ix.tab.S_pad;
     const float nanv = __int_as_float(0x7fc00000);
+    const bool tent = a.tentative != 0;
+    const int32_t tag = tent ? tentative_tag(a.tent_ord) : slot;
+    int32_t* tpos = tent ? a.tpos + (size_t)(a.idx ? a.idx[blockIdx.y] : (int)blockIdx.y) * a.cap : nullptr;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         const int64_t T = t0 + k;
+        if (tpos) tpos[k] = -1;
         if (T < ix.tab.t_base || T >= ix.tab.t_base + W) continue;
         const int64_t row = ring_of(T, W);
         const float* p = base + 3 * (size_t)k;
@@ -172,8 +176,9 @@ __global__ void index_append_kernel(const __grid_constant__ IndexAppendArgs a) {
         const int at = ix.cstart[row * (int64_t)(ix.ncell + 1) + ix.ncell] + pos;
         if (at < S) {
             float4* it = ix.items + (size_t)row * S * 2;
-            it[2 * at] = make_float4(p[0], p[1], p[2], __int_as_float(slot));
+            it[2 * at] = make_float4(p[0], p[1], p[2], __int_as_float(tag));
             it[2 * at + 1] = has_next ? make_float4(p[3], p[4], p[5], 0.f) : make_float4(nanv, nanv, nanv, 0.f);
+            if (tpos) tpos[k] = at;
         } else {
             atomicSub(&ix.nres[row], 1);  // cannot happen (see above); rebuild the row instead
             ix.dirty[row] = 1;
@@ -193,6 +198,25 @@ cudaError_t launch_index_publish(const IndexArgs& a, cudaStream_t s) {
     const int n = a.tab.T_win;
     if (n <= 0) return cudaSuccess;
     index_publish_kernel<<<(n + 255) / 256, 256, 0, s>>>(a.nextra, a.nres, n);
+    return cudaGetLastError();
+}
+
+__global__ void index_withdraw_kernel(const __grid_constant__ IndexArgs ix, const int32_t* tpos, int64_t t0,
+                                      int32_t n) {
+    const int32_t W = ix.tab.T_win;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const int64_t T = t0 + k;
+        const int32_t at = tpos[k];
+        if (at < 0 || T < ix.tab.t_base || T >= ix.tab.t_base + W) continue;
+        const int64_t row = ring_of(T, W);
+        float* w = reinterpret_cast<float*>(ix.items + ((size_t)row * ix.tab.S_pad + at) * 2) + 3;
+        *w = __int_as_float(kTagDead);
+    }
+}
+
+cudaError_t launch_index_withdraw(const IndexArgs& a, const int32_t* tpos, int64_t t0, int32_t n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    index_withdraw_kernel<<<(n + 255) / 256, 256, 0, s>>>(a, tpos, t0, n);
     return cudaGetLastError();
 }
 

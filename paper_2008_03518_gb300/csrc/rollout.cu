@@ -488,6 +488,8 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
     const int64_t t_lo = a.tab.t_base, t_hi = a.tab.t_base + a.tab.T_win;
     const int64_t last_j = (int64_t)req.horizon + 1;
     const int KEY_NONE = float_key(-INFINITY);
+    // FCFS ordinal of this request: tentative plans of later requests are not part of its table
+    const int32_t my_ord = a.pipe.on ? a.pipe.ord0 + r : INT_MAX;
 
     // ---------------------------------------------------------------- prologue
     if (tid < kHeadings) {
@@ -1023,6 +1025,7 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
                 const IdxMeta& M = imeta[b];
                 const int total = M.total, n_s = M.n_s;
                 const float4* sb4 = ibuf + (size_t)b * icap * 2;
+                int itag = 0;  // tag of the item item_at read last
                 auto item_at = [&](int i, float& p1x, float& p1y, float& p1z, float& p2x, float& p2y, float& p2z) {
                     float4 P1, P2;
                     if (i < n_s) {
@@ -1037,6 +1040,7 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
                     }
                     p1x = P1.x; p1y = P1.y; p1z = P1.z;
                     p2x = P2.x; p2y = P2.y; p2z = P2.z;
+                    itag = __float_as_int(P1.w);
                 };
                 // items interleaved over the scanner warps (item i to warp i mod nscan): the
                 // items within reach, each costing a well evaluation per action, sit next to
@@ -1057,6 +1061,9 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
                         if (j < wn) {
                             float p1x, p1y, p1z, p2x, p2y, p2z;
                             item_at(i, p1x, p1y, p1z, p2x, p2y, p2z);
+                            // not in this request's table (a later request's tentative plan,
+                            // or a withdrawn one): culled like a plan far away
+                            if (!tag_visible(itag, my_ord)) p1x = p2x = __int_as_float(0x7fc00000);
                             qx[u] = (p1x - shx) - slx;
                             qy[u] = (p1y - shy) - sly;
                             qz[u] = (p1z - shz) - slz;
@@ -1446,6 +1453,7 @@ __device__ void pipe_finish(const RolloutArgs& a, int r, int token, int* red) {
     const IndexView& iv = a.iv;
     const SepConsts sk = sep_consts(m.sep_h, m.sep_v);
     const float reach = (float)m.sep_h + kSepBand + 1.0f;
+    const int32_t my_ord = a.pipe.ord0 + r;
     const int64_t cst_row_len = (int64_t)iv.ncell + 1;
     int first = INT_MAX, terr = INT_MAX;
     auto cell_of = [&](float v, float o, int nc) {
@@ -1476,6 +1484,7 @@ __device__ void pipe_finish(const RolloutArgs& a, int r, int token, int* red) {
             }
             for (int j = b; j < e; ++j) {
                 const float4 Q = __ldcg(items + 2 * (size_t)j);
+                if (!tag_visible(__float_as_int(Q.w), my_ord)) continue;
                 float h2, dz;
                 bool hin, vin;
                 sep_pair(sk, px, py, pz, Q.x, Q.y, Q.z, h2, dz, hin, vin);

@@ -309,9 +309,11 @@ __global__ void __launch_bounds__(kRowThreads) sepcheck_rows_kernel(const __grid
                 if (it) {
                     const float4 Q = it[2 * (size_t)(s0 + j)];
                     tile[j] = Q;
-                    if (filt) {  // an item outside the slot range would count as earlier (unfiltered)
-                        const int sl = __float_as_int(Q.w);
-                        tord[j] = (unsigned)sl < (unsigned)a.tab.S_pad ? a.slot_ord[sl] : INT_MIN;
+                    if (filt) {  // the ordinal of the item's plan: a stored plan's slot ordinal, a
+                                 // tentative plan's own; a withdrawn item is never counted
+                        const int tag = __float_as_int(Q.w);
+                        tord[j] = tag >= 0 ? ((unsigned)tag < (unsigned)a.tab.S_pad ? a.slot_ord[tag] : INT_MIN)
+                                           : (tag == kTagDead ? INT_MAX : -tag - 2);
                     }
                 } else {
                     const size_t o = poff + s0 + j;

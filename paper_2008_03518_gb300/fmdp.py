@@ -135,7 +135,9 @@ class Stats(ctypes.Structure):
                 ("pipe_drains", ctypes.c_int64), ("pipe_cta_s", ctypes.c_double), ("pipe_slot_s", ctypes.c_double),
                 ("pipe_ctas", ctypes.c_int32), ("pipe_resident", ctypes.c_int32),
                 ("pipe_resumes", ctypes.c_int64), ("pipe_rechecks", ctypes.c_int64),
-                ("qe_items", ctypes.c_int64), ("qe_near", ctypes.c_int64), ("qe_wells", ctypes.c_int64)]
+                ("qe_items", ctypes.c_int64), ("qe_near", ctypes.c_int64), ("qe_wells", ctypes.c_int64),
+                ("pipe_head_n", ctypes.c_int64 * 5), ("pipe_head_s", ctypes.c_double * 5),
+                ("pipe_publishes", ctypes.c_int64), ("pipe_withdrawals", ctypes.c_int64)]
 
 
 class Peaks(ctypes.Structure):
@@ -748,6 +750,8 @@ class Scheduler:
     def stats(self):
         s = Stats()
         self._check(self._L.fmdp_get_stats(self._h, ctypes.byref(s)))
-        d = {k: getattr(s, k) for k, _ in Stats._fields_ if k != "phase_cycles"}
+        d = {k: getattr(s, k) for k, _ in Stats._fields_ if k not in ("phase_cycles", "pipe_head_n", "pipe_head_s")}
+        d["pipe_head_n"] = list(s.pipe_head_n)
+        d["pipe_head_s"] = list(s.pipe_head_s)
         d["phase_cycles"] = list(s.phase_cycles)
         return d
