@@ -100,6 +100,8 @@ fmdp_status fmdp_create(const fmdp_airspace* air, double gamma, const fmdp_actio
         CK(cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking));
         c->stream = c->own;
         CK(prepare_rollout_kernel((size_t)c->max_smem));
+        CK(preload_index_kernels());
+        CK(preload_table_kernels());
         CK(prepare_sepcheck_rows(sepcheck_rows_smem(kBatchMax)));
         CK(prepare_policy_kernel());
         CK(prepare_lookahead_kernel());

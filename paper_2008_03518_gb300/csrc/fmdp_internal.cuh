@@ -261,6 +261,10 @@ cudaError_t probe_peaks(int n_sm, cudaStream_t s, fmdp_peaks* out);
 cudaError_t launch_rollout(const RolloutArgs& a, int threads, size_t smem, cudaStream_t s, int n_clusters = 0);
 size_t rollout_smem_bytes(int chunk, int depth, int icap);
 cudaError_t prepare_rollout_kernel(size_t smem);
+// Load the kernels of index.cu / tables.cu at context creation instead of at their first launch
+// (a lazy load waits for the kernels running at the time, such as a persistent rollout launch).
+cudaError_t preload_index_kernels();
+cudaError_t preload_table_kernels();
 int rollout_max_active_clusters(int cs, int threads, size_t smem);
 cudaError_t launch_sepcheck(const SepArgs& a, int n_req, int max_points, cudaStream_t s);
 cudaError_t launch_sep_reset(SepOut* out, int n, cudaStream_t s);
@@ -296,6 +300,8 @@ struct IndexAppendArgs {
     int32_t tentative;     // 1: tag the items tentative_tag(tent_ord) instead of the slot, take
     int32_t tent_ord;      // the trajectory whatever its verdict, and record each sample's
     int32_t* tpos;         // position in tpos[r][k] (-1: not stored); 0: stored plans
+    int32_t first;         // tentative: samples before this one keep the items (and tpos
+                           // entries) an earlier append made for them; only [first, n) are added
     const float* traj;
     int32_t cap;
     const RolloutOut* rout;

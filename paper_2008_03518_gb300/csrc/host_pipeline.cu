@@ -62,7 +62,7 @@ struct MappedArray {
 constexpr int kQueueCap = 4096;           // ring entries (a power of two)
 constexpr int kBoxChunk = 32;             // steps per bounding box of a trajectory
 constexpr int32_t kPipeExtraLimit = 192;  // appended items per row before the rows are rebuilt
-constexpr int32_t kPublishAhead = 32;     // requests past the head whose plans are published
+constexpr int32_t kPublishAhead = 128;    // requests past the head whose plans are published
 constexpr int32_t kOrdLimit = 1 << 30;    // ordinals are rebased before they reach this
 
 }  // namespace
@@ -170,11 +170,13 @@ struct InflRule {
 // skip the steps where the two are far apart. Returns the first decision step j could
 // change (-1: none); *sep: j could change the verdict. The steps before the first one keep
 // their decisions, so the plan may go on from its state there.
+// jfloor: j's items below this index (item i: sample i and the next one) did not change
+// (only the items at or past it can make a difference).
 int first_influenced(const InflRule& P, const float* pj, int nj, int64_t tj, const TrajBoxes& bj, int32_t q_lo,
                      int32_t q_hi, const float* pk, int nk, int64_t tk, double speed_k, const TrajBoxes& bk,
-                     const int32_t* obs_k, int32_t tail_obs, bool* sep) {
+                     const int32_t* obs_k, int32_t tail_obs, bool* sep, int32_t jfloor = 0) {
     *sep = false;
-    if (nk <= 0 || nj <= 0 || !(tk < tj + nj && tj < tk + nk)) return -1;
+    if (nk <= 0 || nj <= 0 || !(tk < tj + nj && tj < tk + nk) || jfloor >= nj || q_lo >= q_hi) return -1;
     const bool sep_unseen = q_lo <= tail_obs && tail_obs < q_hi;
     const double rho = speed_k * P.dt + P.dzmax + 1.0;
     double e = std::max(P.H, P.V);
@@ -188,7 +190,7 @@ int first_influenced(const InflRule& P, const float* pj, int nj, int64_t tj, con
         // j's samples a step of this chunk can meet: the same step, the next, and the one
         // after it (the next sample's velocity)
         const int64_t jlo = std::max<int64_t>(0, tk + i0 - tj), jhi = std::min<int64_t>(nj - 1, tk + i1 - 1 - tj + 2);
-        if (jlo > jhi) continue;
+        if (jlo > jhi || jhi < jfloor) continue;
         float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
         for (int64_t q = jlo / kBoxChunk; q <= jhi / kBoxChunk; ++q) {
             const float* o = bj.b.data() + 6 * q;
@@ -204,13 +206,14 @@ int first_influenced(const InflRule& P, const float* pj, int nj, int64_t tj, con
         for (int i = i0; i < i1; ++i) {
             const double sx = pk[3 * i], sy = pk[3 * i + 1], sz = pk[3 * i + 2];
             const int64_t t0 = tk + i - tj;
-            if (sep_unseen && !*sep && t0 >= 0 && t0 < nj) {
+            if (sep_unseen && !*sep && t0 >= jfloor && t0 >= 0 && t0 < nj) {
                 const double dx = sx - pj[3 * t0], dy = sy - pj[3 * t0 + 1], dz = sz - pj[3 * t0 + 2];
                 if (dx * dx + dy * dy < P.H * P.H && std::fabs(dz) < P.V) *sep = true;
             }
             const int64_t t1 = t0 + 1;
             // no decision at the last point; a step outside [q_lo, q_hi) read j as it stands
-            if (i + 1 >= nk || obs_k[i] < q_lo || obs_k[i] >= q_hi || t1 < 0 || t1 >= nj) continue;
+            if (i + 1 >= nk || obs_k[i] < q_lo || obs_k[i] >= q_hi || t1 < 0 || t1 >= nj || t1 < jfloor)
+                continue;
             const float* q1 = pj + 3 * t1;
             double vx = 0.0, vy = 0.0, vz = 0.0;
             if (t1 + 1 < nj) {
@@ -231,12 +234,19 @@ int first_influenced(const InflRule& P, const float* pj, int nj, int64_t tj, con
 
 enum Phase : uint8_t { kAbsent = 0, kWait = 1, kFlight = 2, kDone = 3, kFinal = 4 };
 
-// A published tentative plan of one request: visible to reads made with a table-operation
-// count in [q_pub, q_kill).
+// A published tentative plan of one request. A read that acquired the table-operation count q
+// sees the work of every operation up to q and may see any part of a later one: an item
+// appended by operation a and withdrawn by operation w is seen by the reads with
+// a <= q < w and may be seen by any read with q < w. q_pub: the operation that appended this
+// version's items past the ones it kept from the version before it; q_kill: the one that
+// withdrew its items past the ones the next version kept; q_from: the one that appended the
+// oldest item it holds (the first version of the chain whose versions kept items from one
+// another).
 struct Version {
     int32_t j;
     int32_t n;
     int32_t q_pub, q_kill;
+    int32_t q_from;
     std::vector<float> xyz;
     TrajBoxes boxes;
 };
@@ -246,6 +256,7 @@ struct Change {
     int32_t j;
     int32_t v_old, v_new;  // versions withdrawn and published (-1: none)
     int32_t q_last;        // the last table operation of the change
+    int32_t keep;          // items [0, keep) of both versions are the same ones, left in place
 };
 
 }  // namespace
@@ -533,10 +544,11 @@ int32_t run_pipeline(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_resu
     };
     // appends request k's latest plan (as planned on the device) to the index as its
     // tentative plan and publishes it
-    auto append_tentative = [&](int32_t k, int32_t np) {
+    auto append_tentative = [&](int32_t k, int32_t np, int32_t first) {
         IndexAppendArgs ia{};
         ia.ix = index_args(c);
         ia.tentative = 1;
+        ia.first = first;
         ia.tent_ord = ord0 + k;
         ia.tpos = P.tpos.p + (size_t)k * cap;
         ia.traj = B.traj.p + (size_t)k * cap * 3;
@@ -549,33 +561,50 @@ int32_t run_pipeline(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_resu
         count_rows(k, np);
         tentative_used = true;
     };
-    // request k's contribution becomes its latest plan (published when admissible) or nothing
+    // request k's contribution becomes its latest plan (published when admissible) or nothing.
+    // A plan resumed from a later step keeps its first samples: the items of those (sample i
+    // and sample i + 1 each) stay in the index as they are, so that no read ever misses them,
+    // and only the items past them are withdrawn and appended.
     auto set_contribution = [&](int32_t k) {
         const int32_t v_old = cur[k];
+        const bool admissible = verdict[k] == FMDP_ADMITTED;
+        const int32_t n_new = admissible ? fin_ro[k].n_points : 0;
+        const float* xyz = P.h_traj.p + (size_t)k * cap * 3;
+        int32_t keep = 0;  // items kept
+        if (v_old >= 0 && admissible) {
+            const Version& a = V[v_old];
+            const int32_t m = std::min(a.n, n_new);
+            int32_t same = 0;  // samples equal in both
+            while (same < m && a.xyz[3 * same] == xyz[3 * same] && a.xyz[3 * same + 1] == xyz[3 * same + 1] &&
+                   a.xyz[3 * same + 2] == xyz[3 * same + 2])
+                ++same;
+            keep = std::max(same - 1, 0);
+        }
         int32_t v_new = -1;
         if (v_old >= 0) {
             const Version& x = V[v_old];
-            LAUNCH(c, launch_index_withdraw(index_args(c), P.tpos.p + (size_t)k * cap, reqs[k].depart_step, x.n,
-                                            P.tstream));
+            LAUNCH(c, launch_index_withdraw(index_args(c), P.tpos.p + (size_t)k * cap + keep,
+                                            reqs[k].depart_step + keep, x.n - keep, P.tstream));
             V[v_old].q_kill = close_op();
             ++n_withdraw;
         }
-        if (verdict[k] == FMDP_ADMITTED) {
+        if (admissible) {
             Version x;
             x.j = k;
-            x.n = fin_ro[k].n_points;
-            x.xyz.assign(P.h_traj.p + (size_t)k * cap * 3, P.h_traj.p + (size_t)k * cap * 3 + 3 * (size_t)x.n);
+            x.n = n_new;
+            x.xyz.assign(xyz, xyz + 3 * (size_t)n_new);
             x.boxes = boxes[k];
-            append_tentative(k, x.n);
+            append_tentative(k, n_new, keep);
             x.q_pub = close_op();
             x.q_kill = INT32_MAX;
+            x.q_from = keep > 0 ? V[v_old].q_from : x.q_pub;
             v_new = (int32_t)V.size();
             V.push_back(std::move(x));
             ++n_publish;
         }
         cur[k] = v_new;
         contrib_tok[k] = tok[k];
-        if (v_old >= 0 || v_new >= 0) E.push_back({k, v_old, v_new, ops});
+        if (v_old >= 0 || v_new >= 0) E.push_back({k, v_old, v_new, ops, keep});
     };
     // stores an admitted request: scatter into the plan table on the table stream (its index
     // items are its tentative plan's, already published)
@@ -620,20 +649,18 @@ int32_t run_pipeline(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_resu
             if (ch.j >= k) continue;  // later requests are not part of k's table
             const int64_t tj = reqs[ch.j].depart_step;
             bool sep = false;
-            if (ch.v_old >= 0) {  // withdrawn: where k could have seen it
-                const Version& x = V[ch.v_old];
-                const int f = first_influenced(rule, x.xyz.data(), x.n, tj, x.boxes, x.q_pub, x.q_kill, pk, nk,
-                                               reqs[k].depart_step, reqs[k].speed_mps, boxes[k], ok, tail_obs[k], &sep);
+            auto test = [&](const Version& x, int32_t q_lo, int32_t q_hi, int32_t floor_) {
+                const int f = first_influenced(rule, x.xyz.data(), x.n, tj, x.boxes, q_lo, q_hi, pk, nk,
+                                               reqs[k].depart_step, reqs[k].speed_mps, boxes[k], ok, tail_obs[k], &sep,
+                                               floor_);
                 if (f >= 0) first = std::min(first, f);
                 sep_any = sep_any || sep;
-            }
-            if (ch.v_new >= 0) {  // published: where k could not see it yet
-                const Version& x = V[ch.v_new];
-                const int f = first_influenced(rule, x.xyz.data(), x.n, tj, x.boxes, INT32_MIN, x.q_pub, pk, nk,
-                                               reqs[k].depart_step, reqs[k].speed_mps, boxes[k], ok, tail_obs[k], &sep);
-                if (f >= 0) first = std::min(first, f);
-                sep_any = sep_any || sep;
-            }
+            };
+            // only the items past the kept ones changed: the withdrawn ones where a read could
+            // still see them (from the first append of the chain of versions they belong to),
+            // the appended ones where a read could still miss them
+            if (ch.v_old >= 0) test(V[ch.v_old], V[ch.v_old].q_from, V[ch.v_old].q_kill, ch.keep);
+            if (ch.v_new >= 0) test(V[ch.v_new], INT32_MIN, V[ch.v_new].q_pub, ch.keep);
         }
         if (first == INT32_MAX && !sep_any) return true;
         phase[k] = kWait;
@@ -776,11 +803,11 @@ int32_t run_pipeline(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_resu
                     for (int32_t k = head; k < joined; ++k) {
                         if (cur[k] < 0) continue;
                         if (contrib_tok[k] == tok[k]) {  // (nothing is in flight: the device holds it)
-                            append_tentative(k, V[cur[k]].n);
+                            append_tentative(k, V[cur[k]].n, 0);
                             close_op();
                         } else {
                             V[cur[k]].q_kill = q_rebuild;
-                            E.push_back({k, cur[k], -1, q_rebuild});
+                            E.push_back({k, cur[k], -1, q_rebuild, 0});
                             cur[k] = -1;
                             contrib_tok[k] = -1;
                             ++n_withdraw;

@@ -165,7 +165,8 @@ __global__ void index_append_kernel(const __grid_constant__ IndexAppendArgs a) {
     const bool tent = a.tentative != 0;
     const int32_t tag = tent ? tentative_tag(a.tent_ord) : slot;
     int32_t* tpos = tent ? a.tpos + (size_t)(a.idx ? a.idx[blockIdx.y] : (int)blockIdx.y) * a.cap : nullptr;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const int k0 = tent ? a.first : 0;
+    for (int k = k0 + blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         const int64_t T = t0 + k;
         if (tpos) tpos[k] = -1;
         if (T < ix.tab.t_base || T >= ix.tab.t_base + W) continue;
@@ -227,6 +228,19 @@ __global__ void store_release_kernel(int32_t* p, int32_t v) {
 cudaError_t launch_store_release(int32_t* p, int32_t v, cudaStream_t s) {
     store_release_kernel<<<1, 1, 0, s>>>(p, v);
     return cudaGetLastError();
+}
+
+// Loads the index kernels now. Under lazy module loading a kernel's code is loaded at its first
+// launch, and that load waits for the kernels running at the time; the pipelined mode launches
+// these kernels beside a persistent rollout launch that runs until the host stops it.
+cudaError_t preload_index_kernels() {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, index_build_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, index_append_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, index_publish_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, index_withdraw_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, store_release_kernel);
+    return e;
 }
 
 size_t index_build_smem(int ncell) { return (size_t)(ncell + 1 + 32) * sizeof(int); }

@@ -516,6 +516,20 @@ cudaError_t launch_sep_reset_idx(SepOut* out, const int32_t* idx, const int32_t*
     return cudaGetLastError();
 }
 
+// Loads the table kernels now, for the reason given at preload_index_kernels.
+cudaError_t preload_table_kernels() {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, sepcheck_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, sep_reset_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, admit_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, fill_nan_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, sepcheck_rows_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, batch_minsep_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, influence_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, sep_reset_idx_kernel);
+    return e;
+}
+
 cudaError_t launch_fill_nan(float* p, size_t n, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     const size_t want = (n + 255) / 256;

@@ -104,6 +104,27 @@ def test_pipelined_crowded_batch_replans_and_matches(batch_size):
     assert 0 < st["pipe_ctas"] <= st["pipe_resident"]
 
 
+@pytest.mark.parametrize("batch_size,spread", [(0, 1500.0), (16, 1500.0), (0, 700.0), (32, 700.0)])
+def test_pipelined_crowded_seeds(batch_size, spread):
+    """Many interleavings of the pipelined mode: crowded airspaces over sixteen seeds, where
+    tentative plans are published, replaced by resumed plans that keep their first samples,
+    withdrawn and published again while later requests read them. Every seed must give the
+    sequential results and table."""
+    resumes = publishes = withdrawals = 0
+    for seed in range(300, 316):
+        sc = S.crowded_batch(seed=seed, n_requests=64, spread_m=spread)
+        many, bat, t1, t2, st = run_both(sc, batch_size=batch_size)
+        try:
+            same_results(many, bat)
+            same_tables(t1, t2)
+        except AssertionError as e:
+            raise AssertionError(f"seed {seed}: {e}") from None
+        resumes += st["pipe_resumes"]
+        publishes += st["pipe_publishes"]
+        withdrawals += st["pipe_withdrawals"]
+    assert resumes > 0 and publishes > 0 and withdrawals > 0
+
+
 @pytest.mark.parametrize("batch_mode", [0, 1])
 def test_crowded_batch_against_the_oracle(batch_mode):
     sc = S.crowded_batch(n_requests=24)
