@@ -301,6 +301,11 @@ def sweep_point(s, sc, reqs, n_plain, stream, barrier, mx, world, learned_params
         s.learned_set_params(learned_params)
         s.restore()
         rep, acc, sp_, sf_ = s.learned_evaluate(reqs)
+        # C5's own rule: a valid proposal (captured, no conflict, no terrain: the judge with an
+        # unbounded step allowance) whose cost is within 5 % of FastMDP's plan of the request
+        s.restore()
+        _, valid, sp_u, sf_u = s.learned_evaluate(reqs, slack=1e9)
+        c5 = int(((valid != 0) & (sp_u <= 1.05 * sf_u)).sum())
 
         def learned():
             s.restore()
@@ -314,7 +319,10 @@ def sweep_point(s, sc, reqs, n_plain, stream, barrier, mx, world, learned_params
             "proposals_reaching_goal": rep["proposals_captured"], "proposal_steps": rep["proposal_steps"],
             "proposal_rollout_ms": rep["proposal_ms"], "fastmdp_rollout_ms": rep["fastmdp_ms"],
             "fastmdp_steps": rep["fastmdp_steps"],
-            "judge": "reaches the goal, no conflict or terrain, steps <= 1.05 x fewest possible (gap <= 5 %)"})
+            "judge": "reaches the goal, no conflict or terrain, steps <= 1.05 x fewest possible (gap <= 5 %)",
+            "valid_proposals": int((valid != 0).sum()),
+            "accepted_by_gap_to_fastmdp": c5, "acceptance_rate_by_gap_to_fastmdp": c5 / max(len(reqs), 1),
+            "gap_rule": "valid proposal with steps <= 1.05 x FastMDP's steps for the same request"})
     s.restore()
     return out
 

@@ -448,6 +448,8 @@ struct PipeServe {
     fmdp_serve_report* rep;
 };
 bool pipeline_eligible(const fmdp_ctx* c);
+struct PipeServe;
+bool pipeline_fits(fmdp_ctx* c, int32_t n, const PipeServe* serve);
 int32_t run_pipeline(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_result* res,
                      const fmdp_request* dev_reqs, bool keep_points, const PipeServe* serve);
 void pipe_release(fmdp_ctx* c);

@@ -378,7 +378,8 @@ void copy_points_back(fmdp_ctx* c, int32_t n, fmdp_result* res) {
 int32_t run_batch(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_result* res,
                   const fmdp_request* dev_reqs, bool keep_points) {
     if (n <= 0) return 0;
-    if (pipeline_eligible(c)) return run_pipeline(c, reqs, n, res, dev_reqs, keep_points, nullptr);
+    if (pipeline_eligible(c) && pipeline_fits(c, n, nullptr))
+        return run_pipeline(c, reqs, n, res, dev_reqs, keep_points, nullptr);
     const int32_t bs = c->opt.batch_size > 0 ? c->opt.batch_size : kBatchDefault;
     batch_prepare(c, reqs, n, std::min(n, bs), dev_reqs);
     if (c->learned_mode) {

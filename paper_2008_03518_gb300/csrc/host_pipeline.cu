@@ -23,13 +23,16 @@
 // step, and a plan whose wells cannot reach the successors adds an exact zero. Every table
 // change (an index append then its publication, or a withdrawal) is a numbered operation
 // that raises a device counter when it completes; each rollout step records the counter it
-// read before the index rows it valued, so the host knows, step by step, which versions of
-// an earlier request's plan the step could have seen. A step is exact if the earlier
+// read before the index rows it valued, so the host knows, step by step, which items of an
+// earlier request's plans the step saw for certain (those of every operation up to the
+// counter) and which it may have seen (any later operation). A step is exact if the earlier
 // requests' final contributions were visible to it and nothing else of theirs was, or if
 // the difference has no influence at that step; the walk tests exactly the differences. An
 // appended item becomes visible only when complete, and a withdrawal only flips its tag, so
-// each item is read either whole or not at all. Row rebuilds, which move items, happen
-// only while no rollout runs; the tentative plans are published again after them. The exact
+// each item is read either whole or not at all. A plan resumed from a later step keeps the
+// items of its unchanged first samples in place (only the items past them are withdrawn and
+// appended), so no read misses those. Row rebuilds, which move items, happen only while no
+// rollout runs; the tentative plans are published again after them. The exact
 // separation report of each request (minimum separations to every earlier plan) comes from
 // the row-major check with an ordinal filter: it skips plans of later requests.
 #include "host.cuh"
@@ -61,6 +64,7 @@ struct MappedArray {
 
 constexpr int kQueueCap = 4096;           // ring entries (a power of two)
 constexpr int kBoxChunk = 32;             // steps per bounding box of a trajectory
+constexpr int kBoxSuper = 8;              // chunks per coarse box
 constexpr int32_t kPipeExtraLimit = 192;  // appended items per row before the rows are rebuilt
 constexpr int32_t kPublishAhead = 128;    // requests past the head whose plans are published
 constexpr int32_t kOrdLimit = 1 << 30;    // ordinals are rebased before they reach this
@@ -116,14 +120,54 @@ bool pipeline_eligible(const fmdp_ctx* c) {
 
 namespace {
 
+int32_t pipeline_window(const fmdp_ctx* c, const PipeServe* serve) {
+    const int32_t bs = c->opt.batch_size > 0 ? c->opt.batch_size : kBatchDefault;
+    int32_t window = std::max(1, std::min(bs, kBatchMax));
+    if (serve && serve->o.max_in_flight > 0) window = std::min(serve->o.max_in_flight, kBatchMax);
+    return window;
+}
+
+// Items each index row holds now (built items + appended ones), from the device.
+std::vector<int32_t> row_fill(fmdp_ctx* c) {
+    const int32_t W = c->T_win;
+    std::vector<int32_t> built(W), extra(W);
+    CK(cudaMemcpy2DAsync(built.data(), sizeof(int32_t), c->ix_cstart + c->ix_ncell,
+                         (size_t)(c->ix_ncell + 1) * sizeof(int32_t), sizeof(int32_t), W, cudaMemcpyDeviceToHost,
+                         c->stream));
+    CK(cudaMemcpyAsync(extra.data(), c->ix_nres, (size_t)W * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (int32_t r = 0; r < W; ++r) built[r] += extra[r];
+    return built;
+}
+
+// Appends a row can still receive after the pipeline decided to rebuild the rows: dispatch
+// stops at that moment, so each request of the window appends at most its latest plan.
+int32_t append_margin(int32_t window, int32_t n) { return std::min(window, n) + 2; }
+
+}  // namespace
+
+// Room for the pipelined mode's appends in every index row (an item that finds its row full
+// would be lost, so the mode runs only where the rows have room for the appends a rebuild
+// margin allows, and a few more); otherwise the caller batches in waves.
+bool pipeline_fits(fmdp_ctx* c, int32_t n, const PipeServe* serve) {
+    const std::vector<int32_t> fill = row_fill(c);
+    const int32_t mx = fill.empty() ? 0 : *std::max_element(fill.begin(), fill.end());
+    return (int64_t)mx + append_margin(pipeline_window(c, serve), n) + 32 <= c->S_pad;
+}
+
+namespace {
+
 // ---------------------------------------------------------------- influence (host side)
 
-// Bounding boxes of a trajectory over chunks of kBoxChunk steps, its largest speed, and for
-// each chunk the range of table-operation counts its decision steps read (obs: per step, or
-// null).
+// Bounding boxes of a trajectory over chunks of kBoxChunk steps and over groups of kBoxSuper
+// chunks, its largest speed, and for each chunk and group the range of table-operation
+// counts its decision steps read (obs: per step, or null).
 struct TrajBoxes {
     std::vector<float> b;                // [chunks][6]: min x y z, max x y z
     std::vector<int32_t> omin, omax;     // [chunks]
+    std::vector<float> sb;               // [groups][6]
+    std::vector<int32_t> somin, somax;   // [groups]
+    int32_t amin = INT32_MAX, amax = INT32_MIN;  // over every step
     double vmax = 0.0;
     void build(const float* p, int n, double dt, const int32_t* obs = nullptr) {
         const int nc = (n + kBoxChunk - 1) / kBoxChunk;
@@ -151,6 +195,46 @@ struct TrajBoxes {
             v2 = std::max(v2, dx * dx + dy * dy + dz * dz);
         }
         vmax = std::sqrt(v2) / dt;
+        const int ng = (nc + kBoxSuper - 1) / kBoxSuper;
+        sb.assign((size_t)ng * 6, 0.f);
+        somin.assign(ng, INT32_MAX);
+        somax.assign(ng, INT32_MIN);
+        for (int g = 0; g < ng; ++g) {
+            float* o = sb.data() + 6 * g;
+            o[0] = o[1] = o[2] = INFINITY;
+            o[3] = o[4] = o[5] = -INFINITY;
+            for (int c = g * kBoxSuper; c < std::min(nc, (g + 1) * kBoxSuper); ++c) {
+                for (int a = 0; a < 3; ++a) {
+                    o[a] = std::min(o[a], b[6 * c + a]);
+                    o[3 + a] = std::max(o[3 + a], b[6 * c + 3 + a]);
+                }
+                somin[g] = std::min(somin[g], omin[c]);
+                somax[g] = std::max(somax[g], omax[c]);
+            }
+            amin = std::min(amin, somin[g]);
+            amax = std::max(amax, somax[g]);
+        }
+    }
+    // the box of steps [lo, hi] (clamped to the trajectory), from the coarsest boxes that fit
+    void span(int64_t lo, int64_t hi, float* out) const {
+        out[0] = out[1] = out[2] = INFINITY;
+        out[3] = out[4] = out[5] = -INFINITY;
+        int64_t c = lo / kBoxChunk;
+        const int64_t c1 = hi / kBoxChunk;
+        while (c <= c1) {
+            const float* o;
+            if (c % kBoxSuper == 0 && c + kBoxSuper - 1 <= c1) {
+                o = sb.data() + 6 * (c / kBoxSuper);
+                c += kBoxSuper;
+            } else {
+                o = b.data() + 6 * c;
+                c += 1;
+            }
+            for (int a = 0; a < 3; ++a) {
+                out[a] = std::min(out[a], o[a]);
+                out[3 + a] = std::max(out[3 + a], o[3 + a]);
+            }
+        }
     }
 };
 
@@ -178,31 +262,43 @@ int first_influenced(const InflRule& P, const float* pj, int nj, int64_t tj, con
     *sep = false;
     if (nk <= 0 || nj <= 0 || !(tk < tj + nj && tj < tk + nk) || jfloor >= nj || q_lo >= q_hi) return -1;
     const bool sep_unseen = q_lo <= tail_obs && tail_obs < q_hi;
+    if (!sep_unseen && (bk.amax < q_lo || bk.amin >= q_hi)) return -1;  // no step read j differently
     const double rho = speed_k * P.dt + P.dzmax + 1.0;
     double e = std::max(P.H, P.V);
     for (int w = 0; w < P.n_wells; ++w) e = std::max(e, P.R[w] + 1.0 + rho + std::fabs(P.tau[w]) * bj.vmax);
     e += 1.0;
-    const int nck = (nk + kBoxChunk - 1) / kBoxChunk;
-    for (int c = 0; c < nck; ++c) {
-        const int i0 = c * kBoxChunk, i1 = std::min(nk, i0 + kBoxChunk);
-        const bool wells_here = bk.omax[c] >= q_lo && bk.omin[c] < q_hi;
-        if (!wells_here && (!sep_unseen || *sep)) continue;
-        // j's samples a step of this chunk can meet: the same step, the next, and the one
-        // after it (the next sample's velocity)
-        const int64_t jlo = std::max<int64_t>(0, tk + i0 - tj), jhi = std::min<int64_t>(nj - 1, tk + i1 - 1 - tj + 2);
-        if (jlo > jhi || jhi < jfloor) continue;
-        float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-        for (int64_t q = jlo / kBoxChunk; q <= jhi / kBoxChunk; ++q) {
-            const float* o = bj.b.data() + 6 * q;
-            for (int a = 0; a < 3; ++a) {
-                lo[a] = std::min(lo[a], o[a]);
-                hi[a] = std::max(hi[a], o[3 + a]);
+    // k's steps i that can meet one of j's items at or past jfloor: the same step's sample
+    // (t0 = tk + i - tj), the next one and the one after it, so t0 in [jfloor - 2, nj)
+    const int64_t i_lo = std::max<int64_t>(0, tj + jfloor - 2 - tk), i_hi = std::min<int64_t>(nk, tj + nj - tk);
+    if (i_lo >= i_hi) return -1;
+    // j's boxes over the samples a range of k's steps [i0, i1) can meet: the same step, the
+    // next, and the one after it (the next sample's velocity); false when the range is apart
+    auto near = [&](const float* ok, int64_t i0, int64_t i1) {
+        const int64_t jlo = std::max<int64_t>(std::max<int64_t>(0, jfloor - 2), tk + i0 - tj);
+        const int64_t jhi = std::min<int64_t>(nj - 1, tk + i1 - 1 - tj + 2);
+        if (jlo > jhi) return false;
+        float jb[6];
+        bj.span(jlo, jhi, jb);
+        for (int a = 0; a < 3; ++a)
+            if (ok[a] > jb[3 + a] + e || ok[3 + a] < jb[a] - e) return false;
+        return true;
+    };
+    const int c_lo = (int)(i_lo / kBoxChunk), c_hi = (int)((i_hi - 1) / kBoxChunk);
+    for (int c = c_lo; c <= c_hi; ++c) {
+        if (c % kBoxSuper == 0 || c == c_lo) {  // a group of chunks: skip it whole when it can
+            const int g = c / kBoxSuper;
+            const bool wells_g = bk.somax[g] >= q_lo && bk.somin[g] < q_hi;
+            const int64_t g0 = std::max<int64_t>((int64_t)c * kBoxChunk, i_lo);
+            const int64_t g1 = std::min<int64_t>(std::min<int64_t>((int64_t)(g + 1) * kBoxSuper * kBoxChunk, nk), i_hi);
+            if ((!wells_g && (!sep_unseen || *sep)) || !near(bk.sb.data() + 6 * g, g0, g1)) {
+                c = std::min(c_hi, (g + 1) * kBoxSuper - 1);
+                continue;
             }
         }
-        const float* ok = bk.b.data() + 6 * c;
-        bool apart = false;
-        for (int a = 0; a < 3; ++a) apart = apart || ok[a] > hi[a] + e || ok[3 + a] < lo[a] - e;
-        if (apart) continue;
+        const int i0 = std::max<int>(c * kBoxChunk, (int)i_lo), i1 = std::min<int>(std::min(nk, (c + 1) * kBoxChunk), (int)i_hi);
+        const bool wells_here = bk.omax[c] >= q_lo && bk.omin[c] < q_hi;
+        if (!wells_here && (!sep_unseen || *sep)) continue;
+        if (!near(bk.b.data() + 6 * c, i0, i1)) continue;
         for (int i = i0; i < i1; ++i) {
             const double sx = pk[3 * i], sy = pk[3 * i + 1], sz = pk[3 * i + 2];
             const int64_t t0 = tk + i - tj;
@@ -268,9 +364,7 @@ int32_t run_pipeline(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_resu
     using clk = std::chrono::steady_clock;
     if (n <= 0) return 0;
     require(pipeline_eligible(c), FMDP_ERR_ARG, "internal: pipelined FCFS needs the index and W = 1");
-    const int32_t bs = c->opt.batch_size > 0 ? c->opt.batch_size : kBatchDefault;
-    int32_t window = std::max(1, std::min(bs, kBatchMax));
-    if (serve && serve->o.max_in_flight > 0) window = std::min(serve->o.max_in_flight, kBatchMax);
+    const int32_t window = pipeline_window(c, serve);
     batch_prepare(c, reqs, n, window, dev_reqs);
     BatchBuffers& B = c->bat;
     const int32_t cap = B.cap;
@@ -346,6 +440,20 @@ int32_t run_pipeline(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_resu
     std::vector<int32_t> inflight;
     std::vector<int32_t> xcnt(c->T_win, 0);
     int32_t xmax = 0;
+    // rows rebuilt before any of them could fill up: the appends since the rows were last
+    // measured (acnt) reaching room[row] start a drain
+    const int32_t margin = append_margin(window, n);
+    std::vector<int32_t> room(c->T_win, 0), acnt(c->T_win, 0);
+    bool overfull = false;
+    auto measure_rows = [&]() {
+        const std::vector<int32_t> fill = row_fill(c);
+        for (int32_t r = 0; r < c->T_win; ++r) {
+            room[r] = c->S_pad - margin - fill[r];
+            require(room[r] >= 1, FMDP_ERR_FULL, "an index row has no room left for pipelined batching");
+        }
+        std::fill(acnt.begin(), acnt.end(), 0);
+        overfull = false;
+    };
     bool draining = false;
     int32_t dispatch_gate = 0;  // after a drain: operations that must be complete first
     bool tentative_used = false;
@@ -532,14 +640,15 @@ int32_t run_pipeline(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_resu
         op_ev.push_back({ops, ev});
         return ops;
     };
-    auto count_rows = [&](int32_t k, int32_t np) {  // the rows a trajectory was appended to
+    auto count_rows = [&](int32_t k, int32_t first, int32_t np) {  // rows that items [first, np) went to
         const int64_t d = reqs[k].depart_step;
-        for (int32_t i = 0; i < np; ++i) {
+        for (int32_t i = first; i < np; ++i) {
             const int64_t T = d + i;
             if (T < c->book.t_base || T >= c->book.t_base + c->T_win) continue;
             int64_t row = T % c->T_win;
             if (row < 0) row += c->T_win;
             xmax = std::max(xmax, ++xcnt[row]);
+            if (++acnt[row] >= room[row]) overfull = true;
         }
     };
     // appends request k's latest plan (as planned on the device) to the index as its
@@ -558,7 +667,7 @@ int32_t run_pipeline(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_resu
         ia.sep = P.sep.p + k;
         LAUNCH(c, launch_index_append(ia, 1, np, P.tstream));
         LAUNCH(c, launch_index_publish(ia.ix, P.tstream));
-        count_rows(k, np);
+        count_rows(k, first, np);
         tentative_used = true;
     };
     // request k's contribution becomes its latest plan (published when admissible) or nothing.
@@ -691,6 +800,9 @@ int32_t run_pipeline(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_resu
         ++n_dispatch;
     };
 
+    measure_rows();
+    size_t e_seen = SIZE_MAX;
+    int32_t head_seen = -1;
     try {
         launch();
         while (finalized < n) {
@@ -733,10 +845,18 @@ int32_t run_pipeline(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_resu
                 progress = true;
             }
             // plans near the head: up to date with every change, published when they are new
-            const int32_t lim = std::min(joined, head + window);
-            for (int32_t k = head; k < lim; ++k)
-                if (phase[k] == kDone && check_plan(k) && k < head + kPublishAhead && contrib_tok[k] != tok[k])
-                    set_contribution(k);
+            // (only when a change was logged, a plan finished or the head moved since the last
+            // pass: otherwise nothing here can differ)
+            if (progress || E.size() != e_seen || head != head_seen) {
+                const int32_t lim = std::min(joined, head + window);
+                for (int32_t k = head; k < lim; ++k) {
+                    if (phase[k] != kDone) continue;
+                    if (chk[k] < (int32_t)E.size() && !check_plan(k)) continue;
+                    if (k < head + kPublishAhead && contrib_tok[k] != tok[k]) set_contribution(k);
+                }
+                e_seen = E.size();
+                head_seen = head;
+            }
             if (head < joined && head_mark != head) {  // a new head of line: how it waits
                 head_mark = head;
                 head_since = now;
@@ -782,18 +902,20 @@ int32_t run_pipeline(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_resu
                 for (int32_t k = head; k < joined; ++k) limit = std::min(limit, reqs[k].depart_step);
                 want_expiry = limit >= c->book.t_base + quantum;
             }
-            if (!draining && (xmax > kPipeExtraLimit || want_expiry)) draining = true;
+            if (!draining && (xmax > kPipeExtraLimit || overfull || want_expiry)) draining = true;
             if (draining && inflight.empty()) {
                 stop_kernel();  // the idle CTAs give their SMs to the rebuild
                 if (want_expiry) {
                     report(unreported);  // before the rows of finished requests can be cleared
                     expire_to(c, limit, &expired);
                     ++expiries;
+                    measure_rows();
                 }
-                if (xmax > kPipeExtraLimit) {  // rows whose extra lists grew long: rebuilt now
+                if (xmax > kPipeExtraLimit || overfull) {  // rows whose extra lists grew long: rebuilt now
                     index_rebuild_all(c);
                     std::fill(xcnt.begin(), xcnt.end(), 0);
                     xmax = 0;
+                    measure_rows();
                     ++n_drains;
                     // the rebuild keeps only stored plans. A tentative plan that is still its
                     // request's latest plan goes back in (the same version: visible to every

@@ -1428,10 +1428,13 @@ __device__ int pipe_take(const RolloutArgs& a, int* r_out, int* tok_out, int* st
 // After a pipelined plan: its conflicts and terrain collisions against the plans the index
 // holds now (each sample against the items of its step within the horizontal minimum, by
 // cell, and the row's extra list), its trajectory and report to host-mapped memory, then
-// its completion token. The index only ever holds plans admitted before this request (the
-// host admits in arrival order and never past an unresolved request), so a conflict found
-// here is one the sequential order has too; a later admission that could conflict with it
-// is caught by the host's influence test, which replans it.
+// its completion token. The index holds the plans admitted before this request (the host
+// admits in arrival order and never past an unresolved request) and the tentative plans of
+// earlier requests (the items of later requests' plans are skipped by their tag). The
+// table-operation count read before the rows goes into the report: where the request's
+// final table differs from what this check could have seen (a tentative plan replaced or
+// withdrawn since, or published after that count), the host's influence test finds it and
+// has the check (or the plan) done again.
 __device__ void pipe_finish(const RolloutArgs& a, int r, int token, int* red) {
     int& s_first = red[0];
     int& s_terr = red[1];
