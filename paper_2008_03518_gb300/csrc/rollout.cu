@@ -433,11 +433,13 @@ __device__ __forceinline__ void fold_well(const Model& m, int w, float qx, float
 // Plans request r with this CTA (and its cluster peers). Every thread of the cluster calls
 // it; all shared memory it uses is re-initialised, so a CTA can plan requests back to back.
 // k0 > 0 (pipelined mode): the plan keeps its first k0 steps and resumes from its state at
-// step k0, as stored by the run that planned them.
+// step k0, as stored by the run that planned them. IDX: indexed mode (one CTA, no cluster),
+// compiled apart from the full-scan mode so that each step's code stays small.
+template <bool IDX>
 __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, unsigned char* smem, const int k0 = 0) {
     const Model& m = a.m;
     const int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31, warp = tid >> 5, NW = NT >> 5;
-    const int cs = a.cs;
+    const int cs = IDX ? 1 : a.cs;
     const uint32_t rank = cs > 1 ? cluster_rank() : 0u;
     const fmdp_request req = a.reqs[r];
     const int A = m.A;
@@ -446,7 +448,7 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
     const int c_len = max(0, min(chunk, a.S_scan - c_begin));
     const int depth = a.ring;                    // 4 or 8 slices
     const int dshift = depth == 8 ? 3 : 2;
-    const bool indexed = a.indexed != 0;
+    constexpr bool indexed = IDX;
     const int icap = a.icap;
     const Layout L = make_layout(chunk, depth, indexed ? icap : 0);
     float4* ibuf = reinterpret_cast<float4*>(smem + L.ibuf);
@@ -1551,7 +1553,7 @@ __device__ void pipe_loop(const RolloutArgs& a, unsigned char* smem) {
         const int k0 = reinterpret_cast<volatile int*>(slot)[3];
         __syncthreads();
         if (w < 0) break;
-        if (k0 >= 0) plan_request(a, r, smem, k0);  // k0 < 0: the plan stands, only its check again
+        if (k0 >= 0) plan_request<true>(a, r, smem, k0);  // k0 < 0: the plan stands, only its check again
         pipe_finish(a, r, tok, slot + 4);
     }
 }
@@ -1560,26 +1562,31 @@ __device__ void pipe_loop(const RolloutArgs& a, unsigned char* smem) {
 // With a work queue (batch mode), each resident cluster pulls work items from a device
 // counter until none are left, which balances requests of uneven horizon: the lead CTA
 // takes the item and its peers read it from the lead's shared memory.
+// IDX: the indexed-mode instance (cluster size 1; the pipelined mode runs only there).
+template <bool IDX>
 __global__ void __launch_bounds__(384, 1) rollout_kernel(const __grid_constant__ RolloutArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
-    if (a.pipe.on) {
-        pipe_loop(a, smem);
-        return;
+    const int cs = IDX ? 1 : a.cs;
+    if constexpr (IDX) {
+        if (a.pipe.on) {
+            pipe_loop(a, smem);
+            return;
+        }
     }
     if (a.queue == nullptr) {
-        const int r = blockIdx.x / a.cs;
-        if (r < a.n_req) plan_request(a, r, smem);  // uniform over the cluster
+        const int r = blockIdx.x / cs;
+        if (r < a.n_req) plan_request<IDX>(a, r, smem);  // uniform over the cluster
         return;
     }
-    const Layout L = make_layout(a.chunk, a.ring, a.indexed ? a.icap : 0);
+    const Layout L = make_layout(a.chunk, a.ring, IDX ? a.icap : 0);
     int* next = reinterpret_cast<int*>(smem + L.misc);
     const int n = a.n_dev ? *a.n_dev : a.n_req;
-    const bool lead = a.cs == 1 || cluster_rank() == 0;
+    const bool lead = cs == 1 || cluster_rank() == 0;
     for (;;) {
         if (threadIdx.x == 0 && lead)  // after a device error, stop taking work
             *next = *reinterpret_cast<volatile int32_t*>(a.err) != 0 ? n : atomicAdd(a.queue, 1);
         int w;
-        if (a.cs > 1) {
+        if (cs > 1) {
             cluster_barrier();
             w = ld_cluster_s32(dsmem_addr(smem_u32(next), 0));
             cluster_barrier();  // every CTA has read the item before the lead takes the next
@@ -1591,16 +1598,18 @@ __global__ void __launch_bounds__(384, 1) rollout_kernel(const __grid_constant__
         if (w >= n) break;
         const int r = a.idx ? a.idx[w] : w;
         if (a.skip && a.skip[r]) continue;  // uniform over the cluster: every CTA read the same item
-        plan_request(a, r, smem);
+        plan_request<IDX>(a, r, smem);
     }
 }
 
 size_t rollout_smem_bytes(int chunk, int depth, int icap) { return make_layout(chunk, depth, icap).total; }
 
 cudaError_t prepare_rollout_kernel(size_t smem) {
-    cudaError_t e = cudaFuncSetAttribute(rollout_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(rollout_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(rollout_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(rollout_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    return cudaFuncSetAttribute(rollout_kernel<false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
 }
 
 int rollout_max_active_clusters_query(int cs, int threads, size_t smem);
@@ -1628,7 +1637,8 @@ int rollout_max_active_clusters(int cs, int threads, size_t smem) {
     return n;
 }
 
-int rollout_max_active_clusters_query(int cs, int threads, size_t smem) {
+template <bool IDX>
+int rollout_max_active_clusters_of(int cs, int threads, size_t smem) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)cs, 1, 1);
     cfg.blockDim = dim3((unsigned)threads, 1, 1);
@@ -1641,14 +1651,23 @@ int rollout_max_active_clusters_query(int cs, int threads, size_t smem) {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, rollout_kernel, &cfg) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveClusters(&n, rollout_kernel<IDX>, &cfg) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
     return n;
 }
 
+// Clusters of cs CTAs that fit at once. Cluster size 1 may run either instance: the smaller
+// of the two answers holds for both.
+int rollout_max_active_clusters_query(int cs, int threads, size_t smem) {
+    const int nf = rollout_max_active_clusters_of<false>(cs, threads, smem);
+    return cs > 1 ? nf : std::min(nf, rollout_max_active_clusters_of<true>(cs, threads, smem));
+}
+
 cudaError_t launch_rollout(const RolloutArgs& a, int threads, size_t smem, cudaStream_t s, int n_clusters) {
+    if (a.indexed && a.cs != 1) return cudaErrorInvalidValue;  // the indexed instance has no cluster
+    if (a.pipe.on && !a.indexed) return cudaErrorInvalidValue;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)((n_clusters > 0 ? n_clusters : a.n_req) * a.cs), 1, 1);
     cfg.blockDim = dim3((unsigned)threads, 1, 1);
@@ -1661,7 +1680,7 @@ cudaError_t launch_rollout(const RolloutArgs& a, int threads, size_t smem, cudaS
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, rollout_kernel, a);
+    return a.indexed ? cudaLaunchKernelEx(&cfg, rollout_kernel<true>, a) : cudaLaunchKernelEx(&cfg, rollout_kernel<false>, a);
 }
 
 }  // namespace fmdp
