@@ -1049,7 +1049,9 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
                 // one another in the index (same cells), so this spreads them over the warps
                 const int nscan = NW - 3, sw = warp - 3;
                 const int wn = total > sw ? (total - sw + nscan - 1) / nscan : 0;  // items of this warp
-                constexpr int U = 2;
+                // one item per lane per pass: a warp rarely holds more than 32 items of a step,
+                // and a second unrolled copy of the fold only lengthens the step's code
+                constexpr int U = 1;
                 for (int base = 0; base < wn; base += 32 * U) {
                     float qx[U], qy[U], qz[U], vx[U], vy[U], vz[U];
                     bool near[U];
