@@ -434,8 +434,10 @@ __device__ __forceinline__ void fold_well(const Model& m, int w, float qx, float
 // it; all shared memory it uses is re-initialised, so a CTA can plan requests back to back.
 // k0 > 0 (pipelined mode): the plan keeps its first k0 steps and resumes from its state at
 // step k0, as stored by the run that planned them. IDX: indexed mode (one CTA, no cluster),
-// compiled apart from the full-scan mode so that each step's code stays small.
-template <bool IDX>
+// compiled apart from the full-scan mode so that each step's code stays small; TIMED: the
+// per-phase clock stamps of fmdp_set_profiling(2), compiled only into instances of their own
+// (the stamps' code alone lengthens a step by about 3 %).
+template <bool IDX, bool TIMED>
 __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, unsigned char* smem, const int k0 = 0) {
     const Model& m = a.m;
     const int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31, warp = tid >> 5, NW = NT >> 5;
@@ -851,7 +853,7 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
     }
     __syncthreads();
 
-    const bool timing = a.phase != nullptr && lead;
+    const bool timing = TIMED && a.phase != nullptr && lead;
     unsigned long long ph[6] = {0, 0, 0, 0, 0, 0};
     // indexed scanners' work (statistics): items culled, items inside the cull radius,
     // (item, reachable well) pairs evaluated for every action
@@ -1536,6 +1538,7 @@ __device__ void pipe_finish(const RolloutArgs& a, int r, int token, int* red) {
 
 // Persistent pipelined launch (indexed mode, one CTA per work item): plans the items the
 // host appends to the ring until it is told to stop, stays idle too long, or a wait expires.
+template <bool TIMED>
 __device__ void pipe_loop(const RolloutArgs& a, unsigned char* smem) {
     const Layout L = make_layout(a.chunk, a.ring, a.icap);
     int* slot = reinterpret_cast<int*>(smem + L.misc);  // [0] ring position, [1] request, [2] token, [3] start
@@ -1555,7 +1558,7 @@ __device__ void pipe_loop(const RolloutArgs& a, unsigned char* smem) {
         const int k0 = reinterpret_cast<volatile int*>(slot)[3];
         __syncthreads();
         if (w < 0) break;
-        if (k0 >= 0) plan_request<true>(a, r, smem, k0);  // k0 < 0: the plan stands, only its check again
+        if (k0 >= 0) plan_request<true, TIMED>(a, r, smem, k0);  // k0 < 0: the plan stands, only its check again
         pipe_finish(a, r, tok, slot + 4);
     }
 }
@@ -1564,20 +1567,21 @@ __device__ void pipe_loop(const RolloutArgs& a, unsigned char* smem) {
 // With a work queue (batch mode), each resident cluster pulls work items from a device
 // counter until none are left, which balances requests of uneven horizon: the lead CTA
 // takes the item and its peers read it from the lead's shared memory.
-// IDX: the indexed-mode instance (cluster size 1; the pipelined mode runs only there).
-template <bool IDX>
+// IDX: the indexed-mode instance (cluster size 1; the pipelined mode runs only there);
+// TIMED: with the phase clock stamps.
+template <bool IDX, bool TIMED>
 __global__ void __launch_bounds__(384, 1) rollout_kernel(const __grid_constant__ RolloutArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int cs = IDX ? 1 : a.cs;
     if constexpr (IDX) {
         if (a.pipe.on) {
-            pipe_loop(a, smem);
+            pipe_loop<TIMED>(a, smem);
             return;
         }
     }
     if (a.queue == nullptr) {
         const int r = blockIdx.x / cs;
-        if (r < a.n_req) plan_request<IDX>(a, r, smem);  // uniform over the cluster
+        if (r < a.n_req) plan_request<IDX, TIMED>(a, r, smem);  // uniform over the cluster
         return;
     }
     const Layout L = make_layout(a.chunk, a.ring, IDX ? a.icap : 0);
@@ -1600,18 +1604,22 @@ __global__ void __launch_bounds__(384, 1) rollout_kernel(const __grid_constant__
         if (w >= n) break;
         const int r = a.idx ? a.idx[w] : w;
         if (a.skip && a.skip[r]) continue;  // uniform over the cluster: every CTA read the same item
-        plan_request<IDX>(a, r, smem);
+        plan_request<IDX, TIMED>(a, r, smem);
     }
 }
 
 size_t rollout_smem_bytes(int chunk, int depth, int icap) { return make_layout(chunk, depth, icap).total; }
 
 cudaError_t prepare_rollout_kernel(size_t smem) {
-    cudaError_t e = cudaFuncSetAttribute(rollout_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(rollout_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const void* fs[4] = {(const void*)rollout_kernel<true, false>, (const void*)rollout_kernel<false, false>,
+                         (const void*)rollout_kernel<true, true>, (const void*)rollout_kernel<false, true>};
+    for (const void* f : fs) {
+        cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    cudaError_t e = cudaFuncSetAttribute(fs[1], cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(rollout_kernel<false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    return cudaFuncSetAttribute(fs[3], cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
 }
 
 int rollout_max_active_clusters_query(int cs, int threads, size_t smem);
@@ -1639,7 +1647,7 @@ int rollout_max_active_clusters(int cs, int threads, size_t smem) {
     return n;
 }
 
-template <bool IDX>
+template <bool IDX, bool TIMED>
 int rollout_max_active_clusters_of(int cs, int threads, size_t smem) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)cs, 1, 1);
@@ -1653,18 +1661,22 @@ int rollout_max_active_clusters_of(int cs, int threads, size_t smem) {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, rollout_kernel<IDX>, &cfg) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveClusters(&n, rollout_kernel<IDX, TIMED>, &cfg) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
     return n;
 }
 
-// Clusters of cs CTAs that fit at once. Cluster size 1 may run either instance: the smaller
-// of the two answers holds for both.
+// Clusters of cs CTAs that fit at once. Every instance that may run that shape is asked (the
+// indexed ones only for cluster size 1); the smallest answer holds for all of them.
 int rollout_max_active_clusters_query(int cs, int threads, size_t smem) {
-    const int nf = rollout_max_active_clusters_of<false>(cs, threads, smem);
-    return cs > 1 ? nf : std::min(nf, rollout_max_active_clusters_of<true>(cs, threads, smem));
+    int n = std::min(rollout_max_active_clusters_of<false, false>(cs, threads, smem),
+                     rollout_max_active_clusters_of<false, true>(cs, threads, smem));
+    if (cs == 1)
+        n = std::min(n, std::min(rollout_max_active_clusters_of<true, false>(cs, threads, smem),
+                                 rollout_max_active_clusters_of<true, true>(cs, threads, smem)));
+    return n;
 }
 
 cudaError_t launch_rollout(const RolloutArgs& a, int threads, size_t smem, cudaStream_t s, int n_clusters) {
@@ -1682,7 +1694,12 @@ cudaError_t launch_rollout(const RolloutArgs& a, int threads, size_t smem, cudaS
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return a.indexed ? cudaLaunchKernelEx(&cfg, rollout_kernel<true>, a) : cudaLaunchKernelEx(&cfg, rollout_kernel<false>, a);
+    const bool timed = a.phase != nullptr;
+    if (a.indexed)
+        return timed ? cudaLaunchKernelEx(&cfg, rollout_kernel<true, true>, a)
+                     : cudaLaunchKernelEx(&cfg, rollout_kernel<true, false>, a);
+    return timed ? cudaLaunchKernelEx(&cfg, rollout_kernel<false, true>, a)
+                 : cudaLaunchKernelEx(&cfg, rollout_kernel<false, false>, a);
 }
 
 }  // namespace fmdp
