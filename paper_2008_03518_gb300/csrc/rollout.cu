@@ -410,7 +410,7 @@ __device__ __forceinline__ unsigned long long sum_term(float l, float ref) {
 // Scores one well of a plan for this lane's action: max-fold of log2(|r| gamma^d).
 __device__ __forceinline__ void fold_well(const Model& m, int w, float qx, float qy, float qz, float vx, float vy,
                                           float vz, float dxa, float dya, float dza, float& mloc,
-                                          unsigned long long& sloc, bool& band) {
+                                          unsigned long long& sloc, bool& band, bool use_sum) {
     const float tau = m.w_tau[w];
     const float ex = dxa - fmaf(tau, vx, qx);
     const float ey = dya - fmaf(tau, vy, qy);
@@ -421,7 +421,7 @@ __device__ __forceinline__ void fold_well(const Model& m, int w, float qx, float
         if (d2 < R2 - bw) {
             const float l = fmaf(approx_sqrt(d2), m.w_lg[w], m.w_L[w]);
             mloc = fmaxf(mloc, l);
-            if (m.combine) sloc += sum_term(l, m.sum_ref);
+            if (use_sum) sloc += sum_term(l, m.sum_ref);
         } else {
             band = true;
         }
@@ -434,10 +434,12 @@ __device__ __forceinline__ void fold_well(const Model& m, int w, float qx, float
 // it; all shared memory it uses is re-initialised, so a CTA can plan requests back to back.
 // k0 > 0 (pipelined mode): the plan keeps its first k0 steps and resumes from its state at
 // step k0, as stored by the run that planned them. IDX: indexed mode (one CTA, no cluster),
-// compiled apart from the full-scan mode so that each step's code stays small; TIMED: the
-// per-phase clock stamps of fmdp_set_profiling(2), compiled only into instances of their own
-// (the stamps' code alone lengthens a step by about 3 %).
-template <bool IDX, bool TIMED>
+// compiled apart from the full-scan mode so that each step's code stays small; GEN: the
+// general instance, with the uncommon features (the per-phase clock stamps of
+// fmdp_set_profiling(2), the trace of fmdp_rollout_trace, the SUM combination); without it the
+// step's code holds only the common configuration (the stamps' code alone lengthens a step by
+// about 3 %).
+template <bool IDX, bool GEN>
 __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, unsigned char* smem, const int k0 = 0) {
     const Model& m = a.m;
     const int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31, warp = tid >> 5, NW = NT >> 5;
@@ -839,10 +841,12 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
     const float* __restrict__ hm = m.hm;
     const int hm_nx = m.hm_nx, hm_ny = m.hm_ny;
     const float hm_sx = m.hm_sx, hm_sy = m.hm_sy;
-    const int n_static = m.n_static, n_wells = m.n_wells, combine = m.combine;
+    // SUM combination (an option): the general instance only
+    const bool combine = GEN && m.combine != 0;
+    const int n_static = m.n_static, n_wells = m.n_wells;
     const float lg32 = m.lg32, sum_ref = m.sum_ref, tau_absmax = m.tau_absmax;
     const float sum_unit = exp2f(sum_ref - (float)kSumBits);  // value of one unit of the fixed-point sum
-    const bool trace0 = a.trace && lead && r == 0;
+    const bool trace0 = GEN && a.trace && lead && r == 0;
     if (tid == 0) {
         int n0;
         float phi;
@@ -853,7 +857,7 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
     }
     __syncthreads();
 
-    const bool timing = TIMED && a.phase != nullptr && lead;
+    const bool timing = GEN && a.phase != nullptr && lead;
     unsigned long long ph[6] = {0, 0, 0, 0, 0, 0};
     // indexed scanners' work (statistics): items culled, items inside the cull radius,
     // (item, reachable well) pairs evaluated for every action
@@ -1003,7 +1007,7 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
                 for (int w = 0; w < n_wells; ++w) {
                     if (!((bwm >> w) & 1u)) continue;  // this well reaches no successor
                     bool bw = false;
-                    fold_well(m, w, bqx, bqy, bqz, bvx, bvy, bvz, dxa, dya, dza, mb, sb, bw);
+                    fold_well(m, w, bqx, bqy, bqz, bvx, bvy, bvz, dxa, dya, dza, mb, sb, bw, combine);
                     if (bw) {
                         float p1x, p1y, p1z, p2x, p2y, p2z;
                         item_at(ii, p1x, p1y, p1z, p2x, p2y, p2z);
@@ -1016,7 +1020,7 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
                             const float l =
                                 fmaf(approx_sqrt(fmaf(ex, ex, fmaf(ey, ey, ez * ez))), m.w_lg[w], m.w_L[w]);
                             mb = fmaxf(mb, l);
-                            if (m.combine) sb += sum_term(l, m.sum_ref);
+                            if (combine) sb += sum_term(l, m.sum_ref);
                         }
                     }
                 }
@@ -1170,7 +1174,7 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
         }
         if (lane < A) {
             if (mloc > -INFINITY) atomicMax(&keys[lane], float_key(mloc));
-            if (sloc) atomicAdd(&sums[lane], sloc);
+            if (combine && sloc) atomicAdd(&sums[lane], sloc);
         }
         __syncwarp();
         if (timing && tid == 0) tp = clock64();
@@ -1186,11 +1190,14 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
         if (warp == 0) {
             // ---- exchange across the cluster (DSMEM push, one hop) or read locally
             int key = lane < A ? keys[lane] : KEY_NONE;
-            unsigned long long ssum = lane < A ? sums[lane] : 0ull;
+            unsigned long long ssum = (combine && lane < A) ? sums[lane] : 0ull;
             int ab = st->abort_flag[par];
-            if (lane < A) { keys[lane] = KEY_NONE; sums[lane] = 0ull; }
+            if (lane < A) {
+                keys[lane] = KEY_NONE;
+                if (combine) sums[lane] = 0ull;
+            }
             if (cs > 1) {
-                const uint32_t bytes = (uint32_t)cs * ((uint32_t)A * (m.combine ? 12u : 4u) + 4u);
+                const uint32_t bytes = (uint32_t)cs * ((uint32_t)A * (combine ? 12u : 4u) + 4u);
                 if (lane == 0) mbar_arrive_expect_tx(&xbar[par], bytes);
                 const uint32_t kslot = smem_u32(&xkeys[(par * kMaxCluster + (int)rank) * kMaxActions + lane]);
                 const uint32_t sslot = smem_u32(&xsums[(par * kMaxCluster + (int)rank) * kMaxActions + lane]);
@@ -1200,7 +1207,7 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
                     const uint32_t rb = dsmem_addr(bslot, (uint32_t)q);
                     if (lane < A) {
                         st_async_s32(dsmem_addr(kslot, (uint32_t)q), key, rb);
-                        if (m.combine) st_async_u64(dsmem_addr(sslot, (uint32_t)q), ssum, rb);
+                        if (combine) st_async_u64(dsmem_addr(sslot, (uint32_t)q), ssum, rb);
                     }
                     if (lane == 31) st_async_s32(dsmem_addr(aslot, (uint32_t)q), ab, rb);
                 }
@@ -1299,7 +1306,7 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
                         pd[0] = nhx; pd[1] = nlx; pd[2] = nhy; pd[3] = nly; pd[4] = nhz; pd[5] = nlz;
                         a.pipe.st_h[o + np] = (uint8_t)hn;
                     }
-                    if (a.trace && r == 0) {
+                    if (GEN && a.trace && r == 0) {
                         a.st_trace[3 * np] = X;
                         a.st_trace[3 * np + 1] = Y;
                         a.st_trace[3 * np + 2] = Z;
@@ -1538,7 +1545,7 @@ __device__ void pipe_finish(const RolloutArgs& a, int r, int token, int* red) {
 
 // Persistent pipelined launch (indexed mode, one CTA per work item): plans the items the
 // host appends to the ring until it is told to stop, stays idle too long, or a wait expires.
-template <bool TIMED>
+template <bool GEN>
 __device__ void pipe_loop(const RolloutArgs& a, unsigned char* smem) {
     const Layout L = make_layout(a.chunk, a.ring, a.icap);
     int* slot = reinterpret_cast<int*>(smem + L.misc);  // [0] ring position, [1] request, [2] token, [3] start
@@ -1558,7 +1565,7 @@ __device__ void pipe_loop(const RolloutArgs& a, unsigned char* smem) {
         const int k0 = reinterpret_cast<volatile int*>(slot)[3];
         __syncthreads();
         if (w < 0) break;
-        if (k0 >= 0) plan_request<true, TIMED>(a, r, smem, k0);  // k0 < 0: the plan stands, only its check again
+        if (k0 >= 0) plan_request<true, GEN>(a, r, smem, k0);  // k0 < 0: the plan stands, only its check again
         pipe_finish(a, r, tok, slot + 4);
     }
 }
@@ -1568,20 +1575,20 @@ __device__ void pipe_loop(const RolloutArgs& a, unsigned char* smem) {
 // counter until none are left, which balances requests of uneven horizon: the lead CTA
 // takes the item and its peers read it from the lead's shared memory.
 // IDX: the indexed-mode instance (cluster size 1; the pipelined mode runs only there);
-// TIMED: with the phase clock stamps.
-template <bool IDX, bool TIMED>
+// GEN: with the phase clock stamps.
+template <bool IDX, bool GEN>
 __global__ void __launch_bounds__(384, 1) rollout_kernel(const __grid_constant__ RolloutArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int cs = IDX ? 1 : a.cs;
     if constexpr (IDX) {
         if (a.pipe.on) {
-            pipe_loop<TIMED>(a, smem);
+            pipe_loop<GEN>(a, smem);
             return;
         }
     }
     if (a.queue == nullptr) {
         const int r = blockIdx.x / cs;
-        if (r < a.n_req) plan_request<IDX, TIMED>(a, r, smem);  // uniform over the cluster
+        if (r < a.n_req) plan_request<IDX, GEN>(a, r, smem);  // uniform over the cluster
         return;
     }
     const Layout L = make_layout(a.chunk, a.ring, IDX ? a.icap : 0);
@@ -1604,7 +1611,7 @@ __global__ void __launch_bounds__(384, 1) rollout_kernel(const __grid_constant__
         if (w >= n) break;
         const int r = a.idx ? a.idx[w] : w;
         if (a.skip && a.skip[r]) continue;  // uniform over the cluster: every CTA read the same item
-        plan_request<IDX, TIMED>(a, r, smem);
+        plan_request<IDX, GEN>(a, r, smem);
     }
 }
 
@@ -1647,7 +1654,7 @@ int rollout_max_active_clusters(int cs, int threads, size_t smem) {
     return n;
 }
 
-template <bool IDX, bool TIMED>
+template <bool IDX, bool GEN>
 int rollout_max_active_clusters_of(int cs, int threads, size_t smem) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)cs, 1, 1);
@@ -1661,7 +1668,7 @@ int rollout_max_active_clusters_of(int cs, int threads, size_t smem) {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, rollout_kernel<IDX, TIMED>, &cfg) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveClusters(&n, rollout_kernel<IDX, GEN>, &cfg) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
@@ -1694,7 +1701,7 @@ cudaError_t launch_rollout(const RolloutArgs& a, int threads, size_t smem, cudaS
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    const bool timed = a.phase != nullptr;
+    const bool timed = a.phase != nullptr || a.trace != 0 || a.m.combine != 0;  // the general instance
     if (a.indexed)
         return timed ? cudaLaunchKernelEx(&cfg, rollout_kernel<true, true>, a)
                      : cudaLaunchKernelEx(&cfg, rollout_kernel<true, false>, a);
