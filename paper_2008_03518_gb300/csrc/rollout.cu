@@ -436,7 +436,7 @@ __device__ __forceinline__ void fold_well(const Model& m, int w, float qx, float
 // step k0, as stored by the run that planned them. IDX: indexed mode (one CTA, no cluster),
 // compiled apart from the full-scan mode so that each step's code stays small; GEN: the
 // general instance, with the uncommon features (the per-phase clock stamps of
-// fmdp_set_profiling(2), the trace of fmdp_rollout_trace, the SUM combination); without it the
+// fmdp_set_profiling(2), the trace of fmdp_rollout_trace, the SUM combination, static wells); without it the
 // step's code holds only the common configuration (the stamps' code alone lengthens a step by
 // about 3 %).
 template <bool IDX, bool GEN>
@@ -968,7 +968,7 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
                 Vd_s[lane] = Vd;
                 gh_s[lane] = has_goal ? exp2f(st->phi + Dl * lg32) : 0.f;  // g / 2^n0
                 // static negative peaks (restricted volumes / terrain wells), CTA 0 only
-                if (lead && n_static > 0)
+                if (GEN && lead && n_static > 0)
                     fold_statics(m, st, sch, scl, shx, shy, shz, slx, sly, slz, dxa, dya, dza, Dx[hn], Dy[hn], my_Dz,
                                  mloc, sloc);
             }
@@ -1701,7 +1701,8 @@ cudaError_t launch_rollout(const RolloutArgs& a, int threads, size_t smem, cudaS
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    const bool timed = a.phase != nullptr || a.trace != 0 || a.m.combine != 0;  // the general instance
+    // the general instance: phase stamps, trace, SUM combination or static wells
+    const bool timed = a.phase != nullptr || a.trace != 0 || a.m.combine != 0 || a.m.n_static > 0;
     if (a.indexed)
         return timed ? cudaLaunchKernelEx(&cfg, rollout_kernel<true, true>, a)
                      : cudaLaunchKernelEx(&cfg, rollout_kernel<true, false>, a);
