@@ -156,6 +156,9 @@ __device__ __forceinline__ float approx_sqrt(float x) { return x > 0.f ? x * rsq
 
 struct StepState {
     float wlim2[kMaxWells];  // per well: (R + largest successor offset + 1 m)^2, the reach test
+    // the well constants the scanners read every step, copied from the kernel parameters
+    // (parameter-space reads with a run-time index wait on the constant cache)
+    float w_tau[kMaxWells], w_R2[kMaxWells], w_band[kMaxWells], w_lg[kMaxWells], w_L[kMaxWells];
     double s[3];       // exact state (FP64)
     double cap2;       // (speed * dt)^2
     double step;       // speed * dt
@@ -408,20 +411,20 @@ __device__ __forceinline__ unsigned long long sum_term(float l, float ref) {
 }
 
 // Scores one well of a plan for this lane's action: max-fold of log2(|r| gamma^d).
-__device__ __forceinline__ void fold_well(const Model& m, int w, float qx, float qy, float qz, float vx, float vy,
-                                          float vz, float dxa, float dya, float dza, float& mloc,
-                                          unsigned long long& sloc, bool& band, bool use_sum) {
-    const float tau = m.w_tau[w];
+__device__ __forceinline__ void fold_well(const StepState* st, int w, float qx, float qy, float qz, float vx,
+                                          float vy, float vz, float dxa, float dya, float dza, float& mloc,
+                                          unsigned long long& sloc, bool& band, bool use_sum, float sum_ref) {
+    const float tau = st->w_tau[w];
     const float ex = dxa - fmaf(tau, vx, qx);
     const float ey = dya - fmaf(tau, vy, qy);
     const float ez = dza - fmaf(tau, vz, qz);
     const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-    const float R2 = m.w_R2[w], bw = m.w_band[w];
+    const float R2 = st->w_R2[w], bw = st->w_band[w];
     if (d2 < R2 + bw) {
         if (d2 < R2 - bw) {
-            const float l = fmaf(approx_sqrt(d2), m.w_lg[w], m.w_L[w]);
+            const float l = fmaf(approx_sqrt(d2), st->w_lg[w], st->w_L[w]);
             mloc = fmaxf(mloc, l);
-            if (use_sum) sloc += sum_term(l, m.sum_ref);
+            if (use_sum) sloc += sum_term(l, sum_ref);
         } else {
             band = true;
         }
@@ -547,6 +550,11 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
             for (int w = 0; w < m.n_wells; ++w) {
                 const float lim = sqrtf(m.w_R2[w]) + (float)step + dzm + 1.f;
                 st->wlim2[w] = lim * lim;
+                st->w_tau[w] = m.w_tau[w];
+                st->w_R2[w] = m.w_R2[w];
+                st->w_band[w] = m.w_band[w];
+                st->w_lg[w] = m.w_lg[w];
+                st->w_L[w] = m.w_L[w];
             }
         }
         const double s0[3] = {req.ox, req.oy, req.oz};
@@ -993,7 +1001,7 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
             auto well_mask = [&](float qx_, float qy_, float qz_, float vx_, float vy_, float vz_) {
                 unsigned msk = 0u;
                 for (int w = 0; w < n_wells; ++w) {
-                    const float tau = m.w_tau[w];
+                    const float tau = st->w_tau[w];
                     const float cx = fmaf(tau, vx_, qx_), cy = fmaf(tau, vy_, qy_), cz = fmaf(tau, vz_, qz_);
                     if (fmaf(cx, cx, fmaf(cy, cy, cz * cz)) < st->wlim2[w]) msk |= 1u << w;
                 }
@@ -1004,23 +1012,32 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
                 if (lane >= A) return;
                 float mb = -INFINITY;
                 unsigned long long sb = 0ull;
-                for (int w = 0; w < n_wells; ++w) {
-                    if (!((bwm >> w) & 1u)) continue;  // this well reaches no successor
+                // the wells that reach a successor (set bits of bwm); a well whose edge lies within
+                // the FP32 band of this lane's successor is decided after the loop, so that the
+                // loop stays short (its band branch, rarely taken, held the item read and an FP64
+                // call)
+                unsigned band = 0u;
+                for (unsigned msk = bwm; msk; msk &= msk - 1u) {
+                    const int w = __ffs(msk) - 1;
                     bool bw = false;
-                    fold_well(m, w, bqx, bqy, bqz, bvx, bvy, bvz, dxa, dya, dza, mb, sb, bw, combine);
-                    if (bw) {
-                        float p1x, p1y, p1z, p2x, p2y, p2z;
-                        item_at(ii, p1x, p1y, p1z, p2x, p2y, p2z);
-                        const bool has2 = p2x == p2x;
+                    fold_well(st, w, bqx, bqy, bqz, bvx, bvy, bvz, dxa, dya, dza, mb, sb, bw, combine, sum_ref);
+                    band |= bw ? 1u << w : 0u;
+                }
+                if (band) {
+                    float p1x, p1y, p1z, p2x, p2y, p2z;
+                    item_at(ii, p1x, p1y, p1z, p2x, p2y, p2z);
+                    const bool has2 = p2x == p2x;
+                    for (; band; band &= band - 1u) {
+                        const int w = __ffs(band) - 1;
                         if (well_inside_exact(m, st, Dx[hn], Dy[hn], my_Dz, p1x, p1y, p1z, has2 ? p2x : 0.f,
                                               has2 ? p2y : 0.f, has2 ? p2z : 0.f, has2, w)) {
-                            const float tau = m.w_tau[w];
+                            const float tau = st->w_tau[w];
                             const float ex = dxa - fmaf(tau, bvx, bqx), ey = dya - fmaf(tau, bvy, bqy),
                                         ez = dza - fmaf(tau, bvz, bqz);
                             const float l =
-                                fmaf(approx_sqrt(fmaf(ex, ex, fmaf(ey, ey, ez * ez))), m.w_lg[w], m.w_L[w]);
+                                fmaf(approx_sqrt(fmaf(ex, ex, fmaf(ey, ey, ez * ez))), st->w_lg[w], st->w_L[w]);
                             mb = fmaxf(mb, l);
-                            if (combine) sb += sum_term(l, m.sum_ref);
+                            if (combine) sb += sum_term(l, sum_ref);
                         }
                     }
                 }
