@@ -120,6 +120,8 @@ struct PipeItem {
     int32_t start;  // 0: plan from the origin; k > 0: keep the plan's first k steps and plan on
                     // from its state at step k; -1: keep the plan, redo only its conflict check
     int32_t pad;
+    int64_t t_base;  // first step of the table window when the item was dispatched (an expiry
+                     // moves it while earlier items are still in flight)
 };
 struct PipeRecord {
     RolloutOut ro;
@@ -348,6 +350,9 @@ struct SepRowsArgs {
     // req_ord[r]; plans that were in the table before the call carry smaller ordinals
     const int32_t* slot_ord;  // [S_pad] or nullptr (no filter)
     const int32_t* req_ord;   // [n]
+    // rows checked: the steps t_base + row0 .. + nrows - 1 (nrows 0: the whole window); the
+    // rows no listed trajectory reaches add nothing
+    int32_t row0, nrows;
 };
 cudaError_t launch_sepcheck_rows(const SepRowsArgs& a, cudaStream_t s);
 size_t sepcheck_rows_smem(int n_max);

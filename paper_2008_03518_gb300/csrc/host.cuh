@@ -14,6 +14,7 @@
 #include <map>
 #include <new>
 #include <set>
+#include <functional>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -94,9 +95,18 @@ struct PlanMeta {
 struct Book {  // host bookkeeping of the table (copied by snapshot / restore)
     std::set<int32_t> free_slots;
     std::map<uint64_t, PlanMeta> plans;
+    // (last step, id) of every plan added, a min-heap: an expiry takes the plans that ended
+    // from its top instead of walking every plan (an entry whose plan is gone or changed is
+    // passed over)
+    std::vector<std::pair<int64_t, uint64_t>> by_end;
     uint64_t next_id = 1;
     int64_t t_base = 0;
     int32_t S_hw = 0;
+    void add(uint64_t id, const PlanMeta& pm) {
+        plans[id] = pm;
+        by_end.emplace_back(pm.t0 + pm.n - 1, id);
+        std::push_heap(by_end.begin(), by_end.end(), std::greater<std::pair<int64_t, uint64_t>>());
+    }
 };
 
 inline int32_t round_up(int32_t x, int32_t m) { return (x + m - 1) / m * m; }
@@ -305,17 +315,18 @@ struct Geometry;
 struct KernelTimer {
     fmdp_ctx* c;
     int kind;
+    cudaStream_t s;  // the stream the timed kernels run on
     cudaEvent_t a = nullptr;
-    KernelTimer(fmdp_ctx* c_, int k) : c(c_), kind(k) {
+    KernelTimer(fmdp_ctx* c_, int k, cudaStream_t st = nullptr) : c(c_), kind(k), s(st ? st : c_->stream) {
         if (c->profiling && kind >= 0) {
             a = next_event(c);
-            CK(cudaEventRecord(a, c->stream));
+            CK(cudaEventRecord(a, s));
         }
     }
     void stop() {
         if (c->profiling && kind >= 0) {
             cudaEvent_t b = next_event(c);
-            CK(cudaEventRecord(b, c->stream));
+            CK(cudaEventRecord(b, s));
             c->pending.push_back({kind, a, b});
         }
     }
@@ -397,7 +408,9 @@ void fill_result(const RolloutOut& ro, const SepOut& so, fmdp_result* res);
 void store_plans(fmdp_ctx* c, int32_t n_plans, const int64_t* t0s, const int32_t* counts, const float* xyz,
                  uint64_t* ids_out);
 void clear_rows(fmdp_ctx* c, int64_t a, int64_t b);
-void expire_to(fmdp_ctx* c, int64_t t_now, int64_t* n_expired);
+// Expires the plans that ended before t_now and moves the window to start there (device
+// work on the context's stream; sync: wait for it).
+void expire_to(fmdp_ctx* c, int64_t t_now, int64_t* n_expired, bool sync = true);
 void destroy_ctx(fmdp_ctx* c);
 
 // ------------------------------------------------------------------ FCFS (host_fcfs.cu)

@@ -536,7 +536,7 @@ void run_departures(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, const int6
                 throw;
             }
             id = c->book.next_id++;
-            c->book.plans[id] = PlanMeta{slot, cand[pick].depart_step, B.h_rout.p[pick].n_points};
+            c->book.add(id, PlanMeta{slot, cand[pick].depart_step, B.h_rout.p[pick].n_points});
             c->book.S_hw = std::max(c->book.S_hw, slot + 1);
         }
         if (chosen) chosen[i] = pick;

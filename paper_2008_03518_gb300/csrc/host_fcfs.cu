@@ -110,7 +110,7 @@ int32_t run_fcfs(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_result* 
             uint64_t id = 0;
             if (so.verdict == FMDP_ADMITTED) {
                 id = c->book.next_id++;
-                c->book.plans[id] = PlanMeta{sl[i], rq.depart_step, ro.n_points};
+                c->book.add(id, PlanMeta{sl[i], rq.depart_step, ro.n_points});
                 c->book.S_hw = std::max(c->book.S_hw, sl[i] + 1);
                 ++admitted;
             } else {

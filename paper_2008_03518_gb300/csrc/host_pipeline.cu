@@ -63,6 +63,8 @@ struct MappedArray {
 };
 
 constexpr int kQueueCap = 4096;           // ring entries (a power of two)
+constexpr int kRepSlots = 8;              // staging slots of the asynchronous separation reports
+constexpr int kRepChunk = 64;             // finished requests per report while the launch runs
 constexpr int kBoxChunk = 32;             // steps per bounding box of a trajectory
 constexpr int kBoxSuper = 8;              // chunks per coarse box
 constexpr int32_t kPipeExtraLimit = 192;  // appended items per row before the rows are rebuilt
@@ -90,6 +92,9 @@ struct PipeState {
     DevArray<SepOut> sep;
     DevArray<int32_t> slot_ord, req_ord, list, nlist;
     PinnedArray<int32_t> h_list;
+    cudaEvent_t rep_ev[kRepSlots] = {};  // separation reports: a staging slot is free again after its event
+    bool rep_used[kRepSlots] = {};
+    int rep_next = 0;
     std::vector<cudaEvent_t> ev_free;
     int32_t ord_base = 0;
     bool ord_init = false;
@@ -101,6 +106,8 @@ struct PipeState {
         st_h.release(); ties.release();
         head.release(); sep.release(); slot_ord.release(); req_ord.release(); list.release(); nlist.release();
         h_list.release();
+        for (cudaEvent_t e : rep_ev)
+            if (e) cudaEventDestroy(e);
         for (cudaEvent_t e : ev_free) cudaEventDestroy(e);
         if (kern_ev) cudaEventDestroy(kern_ev);
         if (sync_ev) cudaEventDestroy(sync_ev);
@@ -396,9 +403,11 @@ int32_t run_pipeline(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_resu
     P.head.ensure(1);
     P.sep.ensure(R);
     P.req_ord.ensure(R);
-    P.list.ensure(kBatchMax);
-    P.nlist.ensure(1);
-    P.h_list.ensure(kBatchMax + 1);
+    P.list.ensure((size_t)kRepSlots * kBatchMax);
+    P.nlist.ensure(kRepSlots);
+    P.h_list.ensure((size_t)kRepSlots * (kBatchMax + 1));
+    for (cudaEvent_t& e : P.rep_ev)
+        if (!e) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     if (!P.ord_init || P.ord_base + n >= kOrdLimit) {  // every stored plan counts as earlier
         P.slot_ord.ensure(c->S_pad);
         CK(cudaMemsetAsync(P.slot_ord.p, 0x80, (size_t)c->S_pad * sizeof(int32_t), c->stream));  // INT_MIN-ish
@@ -586,16 +595,31 @@ int32_t run_pipeline(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_resu
     }
 
     // the exact separation report (row-major check with the ordinal filter) of the listed
-    // requests, on the table stream, into B.sepo
+    // requests, on the table stream, into B.sepo: the rows their trajectories reach only, and
+    // without waiting (a staging slot is reused once the report that last used it is done)
     auto report = [&](std::vector<int32_t>& L) {
         for (size_t o = 0; o < L.size(); o += kBatchMax) {
             const int32_t m = (int32_t)std::min<size_t>(kBatchMax, L.size() - o);
-            std::copy(L.begin() + o, L.begin() + o + m, P.h_list.p);
-            P.h_list.p[kBatchMax] = m;
-            CK(cudaMemcpyAsync(P.list.p, P.h_list.p, m * sizeof(int32_t), cudaMemcpyHostToDevice, P.tstream));
-            CK(cudaMemcpyAsync(P.nlist.p, P.h_list.p + kBatchMax, sizeof(int32_t), cudaMemcpyHostToDevice,
-                               P.tstream));
-            LAUNCH(c, launch_sep_reset_idx(B.sepo.p, P.list.p, P.nlist.p, m, P.tstream));
+            const int q = P.rep_next;
+            P.rep_next = (P.rep_next + 1) % kRepSlots;
+            if (P.rep_used[q]) CK(cudaEventSynchronize(P.rep_ev[q]));
+            int32_t* hl = P.h_list.p + (size_t)q * (kBatchMax + 1);
+            int32_t* dl = P.list.p + (size_t)q * kBatchMax;
+            int32_t* dn = P.nlist.p + q;
+            std::copy(L.begin() + o, L.begin() + o + m, hl);
+            hl[kBatchMax] = m;
+            int64_t t_lo = INT64_MAX, t_hi = INT64_MIN;
+            for (int32_t i = 0; i < m; ++i) {
+                const int32_t k = L[o + i];
+                t_lo = std::min<int64_t>(t_lo, reqs[k].depart_step);
+                t_hi = std::max<int64_t>(t_hi, reqs[k].depart_step + fin_ro[k].n_points);
+            }
+            const int64_t w0 = c->book.t_base, w1 = c->book.t_base + c->T_win;
+            t_lo = std::max(t_lo, w0);
+            t_hi = std::min(t_hi, w1);
+            CK(cudaMemcpyAsync(dl, hl, m * sizeof(int32_t), cudaMemcpyHostToDevice, P.tstream));
+            CK(cudaMemcpyAsync(dn, hl + kBatchMax, sizeof(int32_t), cudaMemcpyHostToDevice, P.tstream));
+            LAUNCH(c, launch_sep_reset_idx(B.sepo.p, dl, dn, m, P.tstream));
             SepRowsArgs sp{};
             sp.m = c->model;
             sp.tab = table_view(c);
@@ -604,8 +628,8 @@ int32_t run_pipeline(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_resu
             sp.cap = cap;
             sp.rout = B.rout.p;
             sp.reqs = B.rq;
-            sp.idx = P.list.p;
-            sp.n_dev = P.nlist.p;
+            sp.idx = dl;
+            sp.n_dev = dn;
             sp.n_max = m;
             sp.out = B.sepo.p;
             sp.items = c->ix_items;
@@ -614,12 +638,15 @@ int32_t run_pipeline(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_resu
             sp.ncell = c->ix_ncell;
             sp.slot_ord = P.slot_ord.p;
             sp.req_ord = P.req_ord.p;
-            {
-                KernelTimer t(c, 1);
+            if (t_hi > t_lo) {
+                sp.row0 = (int32_t)(t_lo - w0);
+                sp.nrows = (int32_t)(t_hi - t_lo);
+                KernelTimer t(c, 1, P.tstream);
                 LAUNCH(c, launch_sepcheck_rows(sp, P.tstream));
                 t.stop();
             }
-            CK(cudaStreamSynchronize(P.tstream));  // the staging list is reused by the next chunk
+            CK(cudaEventRecord(P.rep_ev[q], P.tstream));
+            P.rep_used[q] = true;
             for (int32_t i = 0; i < m; ++i) c->stats.sep_pairs += (int64_t)fin_ro[L[o + i]].n_points * c->S_pad;
         }
         L.clear();
@@ -720,7 +747,7 @@ int32_t run_pipeline(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_resu
     auto admit = [&](int32_t k) {
         const int32_t slot = take_slot(c);
         const uint64_t id = c->book.next_id++;
-        c->book.plans[id] = PlanMeta{slot, reqs[k].depart_step, fin_ro[k].n_points};
+        c->book.add(id, PlanMeta{slot, reqs[k].depart_step, fin_ro[k].n_points});
         c->book.S_hw = std::max(c->book.S_hw, slot + 1);
         slot_of[k] = slot;
         ids[k] = id;
@@ -738,7 +765,7 @@ int32_t run_pipeline(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_resu
         aa.force = 0;
         aa.slot_ord = P.slot_ord.p;
         aa.ord = ord0 + k;
-        KernelTimer t(c, 2);
+        KernelTimer t(c, 2, P.tstream);
         LAUNCH(c, launch_admit(aa, 1, fin_ro[k].n_points, P.tstream));
         t.stop();
         ++admitted;
@@ -791,6 +818,7 @@ int32_t run_pipeline(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_resu
         it.token = tok[k];
         it.start = start[k];
         it.pad = 0;
+        it.t_base = c->book.t_base;
         start[k] = 0;
         std::atomic_thread_fence(std::memory_order_release);
         *reinterpret_cast<volatile int32_t*>(P.ctl.p) = ++tail;
@@ -890,6 +918,7 @@ int32_t run_pipeline(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_resu
                 const int32_t q = head + kPublishAhead - 1;
                 if (q < joined && phase[q] == kDone && check_plan(q) && contrib_tok[q] != tok[q]) set_contribution(q);
             }
+            if (unreported.size() >= (size_t)kRepChunk) report(unreported);  // as they come, off the expiry
             if (progress) last_progress = now;
             if (finalized >= n) break;
 
@@ -902,16 +931,33 @@ int32_t run_pipeline(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_resu
                 for (int32_t k = head; k < joined; ++k) limit = std::min(limit, reqs[k].depart_step);
                 want_expiry = limit >= c->book.t_base + quantum;
             }
-            if (!draining && (xmax > kPipeExtraLimit || overfull || want_expiry)) draining = true;
+            // an expiry moves the window's first step without stopping the launch: a plan in
+            // flight keeps the window its item was dispatched with, and none of them reads the
+            // rows the expiry clears (every unresolved request departs at or after the new
+            // first step); the clearing is a table operation that later dispatches wait for
+            if (want_expiry && !draining) {
+                report(unreported);  // before the rows of finished requests can be cleared
+                {
+                    cudaStream_t own = c->stream;
+                    c->stream = P.tstream;  // in order with the other table operations
+                    try {
+                        expire_to(c, limit, &expired, false);
+                    } catch (...) {
+                        c->stream = own;
+                        throw;
+                    }
+                    c->stream = own;
+                }
+                close_op();
+                dispatch_gate = ops;
+                ++expiries;
+                // (the rows' room stays as measured: clearing rows only lowers their fill)
+            }
+            if (!draining && (xmax > kPipeExtraLimit || overfull)) draining = true;
             if (draining && inflight.empty()) {
                 stop_kernel();  // the idle CTAs give their SMs to the rebuild
-                if (want_expiry) {
-                    report(unreported);  // before the rows of finished requests can be cleared
-                    expire_to(c, limit, &expired);
-                    ++expiries;
-                    measure_rows();
-                }
                 if (xmax > kPipeExtraLimit || overfull) {  // rows whose extra lists grew long: rebuilt now
+                    CK(cudaStreamSynchronize(P.tstream));  // no report still reads the rows
                     index_rebuild_all(c);
                     std::fill(xcnt.begin(), xcnt.end(), 0);
                     xmax = 0;
@@ -983,6 +1029,7 @@ int32_t run_pipeline(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_resu
         stop_kernel();
         // the index again holds only stored plans (tentative and withdrawn items go), then
         // the exact separation reports
+        CK(cudaStreamSynchronize(P.tstream));  // no report still reads the rows
         if (tentative_used) index_rebuild_all(c);
         report(unreported);
         CK(cudaStreamSynchronize(P.tstream));

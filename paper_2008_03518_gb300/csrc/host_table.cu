@@ -501,7 +501,7 @@ void store_plans(fmdp_ctx* c, int32_t n_plans, const int64_t* t0s, const int32_t
     }
     for (int32_t i = 0; i < n_plans; ++i) {
         const uint64_t id = c->book.next_id++;
-        c->book.plans[id] = PlanMeta{sl[i], t0s[i], counts[i]};
+        c->book.add(id, PlanMeta{sl[i], t0s[i], counts[i]});
         c->book.S_hw = std::max(c->book.S_hw, sl[i] + 1);
         if (ids_out) ids_out[i] = id;
     }
@@ -533,22 +533,27 @@ void clear_rows(fmdp_ctx* c, int64_t a, int64_t b) {
     index_rebuild(c, a, b, false);  // the cleared rows hold no items
 }
 
-void expire_to(fmdp_ctx* c, int64_t t_now, int64_t* n_expired) {
+void expire_to(fmdp_ctx* c, int64_t t_now, int64_t* n_expired, bool sync) {
     if (t_now <= c->book.t_base) return;
     int64_t n = 0;
-    for (auto it = c->book.plans.begin(); it != c->book.plans.end();) {
-        if (it->second.t0 + it->second.n - 1 < t_now) {
-            c->book.free_slots.insert(it->second.slot);
-            it = c->book.plans.erase(it);
-            ++n;
-        } else {
-            ++it;
-        }
+    Book& bk = c->book;
+    const auto later = std::greater<std::pair<int64_t, uint64_t>>();
+    while (!bk.by_end.empty() && bk.by_end.front().first < t_now) {
+        std::pop_heap(bk.by_end.begin(), bk.by_end.end(), later);
+        const auto [end, id] = bk.by_end.back();
+        bk.by_end.pop_back();
+        const auto it = bk.plans.find(id);
+        if (it == bk.plans.end() || it->second.t0 + it->second.n - 1 != end) continue;  // gone or changed
+        bk.free_slots.insert(it->second.slot);
+        bk.plans.erase(it);
+        ++n;
     }
     clear_rows(c, c->book.t_base, t_now);
     c->book.t_base = t_now;
-    recompute_hw(c);
-    CK(cudaStreamSynchronize(c->stream));
+    // the slot high-water mark stays an upper bound (it only sizes scans): lowered only when
+    // the table empties, not by walking every plan
+    if (bk.plans.empty()) c->book.S_hw = 0;
+    if (sync) CK(cudaStreamSynchronize(c->stream));
     if (n_expired) *n_expired += n;
 }
 

@@ -236,10 +236,10 @@ __host__ __device__ inline Layout make_layout(int chunk, int depth, int icap) {
     al(16);
     L.aux = o;   // valid, Delta, deck, goal term; key, class, log2|Q|, log2 scale by step parity
     o += 12 * kMaxActions * sizeof(int);
-    L.misc = o;  // work-queue slot of the persistent batch mode; pipelined mode: [0..2] the
+    L.misc = o;  // work-queue slot of the persistent batch mode; pipelined mode: [0..3] the
                  // item taken, [4..6] the tail check's first conflict and terrain sample and
-                 // the admissions published before it read the index
-    o += 32;
+                 // the admissions published before it read the index, [8..9] the item's window
+    o += 48;
     L.total = (o + 127) & ~size_t(127);
     return L;
 }
@@ -436,14 +436,16 @@ __device__ __forceinline__ void fold_well(const StepState* st, int w, float qx, 
 // Plans request r with this CTA (and its cluster peers). Every thread of the cluster calls
 // it; all shared memory it uses is re-initialised, so a CTA can plan requests back to back.
 // k0 > 0 (pipelined mode): the plan keeps its first k0 steps and resumes from its state at
-// step k0, as stored by the run that planned them. IDX: indexed mode (one CTA, no cluster),
+// step k0, as stored by the run that planned them. tbase: the first step of the table window
+// the plan reads (the launch's, or in pipelined mode the one its item was dispatched with). IDX: indexed mode (one CTA, no cluster),
 // compiled apart from the full-scan mode so that each step's code stays small; GEN: the
 // general instance, with the uncommon features (the per-phase clock stamps of
 // fmdp_set_profiling(2), the trace of fmdp_rollout_trace, the SUM combination, static wells); without it the
 // step's code holds only the common configuration (the stamps' code alone lengthens a step by
 // about 3 %).
 template <bool IDX, bool GEN>
-__device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, unsigned char* smem, const int k0 = 0) {
+__device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, unsigned char* smem,
+                                             const int64_t tbase, const int k0 = 0) {
     const Model& m = a.m;
     const int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31, warp = tid >> 5, NW = NT >> 5;
     const int cs = IDX ? 1 : a.cs;
@@ -494,7 +496,7 @@ __device__ __forceinline__ void plan_request(const RolloutArgs& a, const int r, 
     const bool lead = (rank == 0);
     float* traj = a.traj + (size_t)r * a.cap * 3;
     uint8_t* acts = a.acts + (size_t)r * a.cap;
-    const int64_t t_lo = a.tab.t_base, t_hi = a.tab.t_base + a.tab.T_win;
+    const int64_t t_lo = tbase, t_hi = tbase + a.tab.T_win;  // the table window this plan reads
     const int64_t last_j = (int64_t)req.horizon + 1;
     const int KEY_NONE = float_key(-INFINITY);
     // FCFS ordinal of this request: tentative plans of later requests are not part of its table
@@ -1423,6 +1425,11 @@ __device__ __forceinline__ int ld_volatile_sys(const int32_t* p) {
     asm volatile("ld.volatile.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
+__device__ __forceinline__ long long ld_volatile_sys64(const int64_t* p) {
+    long long v;
+    asm volatile("ld.volatile.global.s64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
 __device__ __forceinline__ void st_release_sys(int32_t* p, int v) {
     asm volatile("st.release.sys.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
@@ -1430,7 +1437,7 @@ __device__ __forceinline__ void st_release_sys(int32_t* p, int v) {
 // Takes the next work item of the host-fed ring (thread 0). Returns its ring position, or
 // -1 when the CTA should leave: the host asked it to stop and the ring is empty, no work
 // came for idle_cycles, or a bounded wait of another CTA expired.
-__device__ int pipe_take(const RolloutArgs& a, int* r_out, int* tok_out, int* start_out) {
+__device__ int pipe_take(const RolloutArgs& a, int* r_out, int* tok_out, int* start_out, long long* tb_out) {
     const PipeArgs& p = a.pipe;
     long long t0 = clock64();
     unsigned ns = 32;
@@ -1443,6 +1450,7 @@ __device__ int pipe_take(const RolloutArgs& a, int* r_out, int* tok_out, int* st
                 const PipeItem* it = p.items + (h & p.qmask);
                 *r_out = ld_volatile_sys(&it->r);
                 *tok_out = ld_volatile_sys(&it->token);
+                *tb_out = ld_volatile_sys64(&it->t_base);
                 *start_out = ld_volatile_sys(&it->start);
                 return h;
             }
@@ -1465,7 +1473,7 @@ __device__ int pipe_take(const RolloutArgs& a, int* r_out, int* tok_out, int* st
 // final table differs from what this check could have seen (a tentative plan replaced or
 // withdrawn since, or published after that count), the host's influence test finds it and
 // has the check (or the plan) done again.
-__device__ void pipe_finish(const RolloutArgs& a, int r, int token, int* red) {
+__device__ void pipe_finish(const RolloutArgs& a, int r, int token, int* red, long long tbase) {
     int& s_first = red[0];
     int& s_terr = red[1];
     const int tid = threadIdx.x, NT = blockDim.x;
@@ -1498,7 +1506,7 @@ __device__ void pipe_finish(const RolloutArgs& a, int r, int token, int* red) {
         if (m.hm && below_terrain(m, px, py, pz)) terr = min(terr, i);
         if (i >= first) continue;  // a later sample cannot lower this thread's first conflict
         const int64_t T = rq.depart_step + i;
-        if (T < a.tab.t_base || T >= a.tab.t_base + a.tab.T_win) continue;
+        if (T < tbase || T >= tbase + a.tab.T_win) continue;
         int64_t row = T % a.tab.T_win;
         if (row < 0) row += a.tab.T_win;
         const int32_t* cs_row = iv.cstart + row * cst_row_len;
@@ -1566,24 +1574,28 @@ template <bool GEN>
 __device__ void pipe_loop(const RolloutArgs& a, unsigned char* smem) {
     const Layout L = make_layout(a.chunk, a.ring, a.icap);
     int* slot = reinterpret_cast<int*>(smem + L.misc);  // [0] ring position, [1] request, [2] token, [3] start
+    long long* slot_tb = reinterpret_cast<long long*>(slot + 8);  // the item's window
     for (;;) {
         if (threadIdx.x == 0) {
             int r = 0, tok = 0, k0 = 0;
-            const int w = pipe_take(a, &r, &tok, &k0);
+            long long tb = 0;
+            const int w = pipe_take(a, &r, &tok, &k0, &tb);
             slot[0] = w;
             slot[1] = r;
             slot[2] = tok;
             slot[3] = k0;
+            *slot_tb = tb;
         }
         __syncthreads();
         const int w = reinterpret_cast<volatile int*>(slot)[0];
         const int r = reinterpret_cast<volatile int*>(slot)[1];
         const int tok = reinterpret_cast<volatile int*>(slot)[2];
         const int k0 = reinterpret_cast<volatile int*>(slot)[3];
+        const long long tb = *reinterpret_cast<volatile long long*>(slot_tb);
         __syncthreads();
         if (w < 0) break;
-        if (k0 >= 0) plan_request<true, GEN>(a, r, smem, k0);  // k0 < 0: the plan stands, only its check again
-        pipe_finish(a, r, tok, slot + 4);
+        if (k0 >= 0) plan_request<true, GEN>(a, r, smem, tb, k0);  // k0 < 0: the plan stands, only its check again
+        pipe_finish(a, r, tok, slot + 4, tb);
     }
 }
 
@@ -1605,7 +1617,7 @@ __global__ void __launch_bounds__(384, 1) rollout_kernel(const __grid_constant__
     }
     if (a.queue == nullptr) {
         const int r = blockIdx.x / cs;
-        if (r < a.n_req) plan_request<IDX, GEN>(a, r, smem);  // uniform over the cluster
+        if (r < a.n_req) plan_request<IDX, GEN>(a, r, smem, a.tab.t_base);  // uniform over the cluster
         return;
     }
     const Layout L = make_layout(a.chunk, a.ring, IDX ? a.icap : 0);
@@ -1628,7 +1640,7 @@ __global__ void __launch_bounds__(384, 1) rollout_kernel(const __grid_constant__
         if (w >= n) break;
         const int r = a.idx ? a.idx[w] : w;
         if (a.skip && a.skip[r]) continue;  // uniform over the cluster: every CTA read the same item
-        plan_request<IDX, GEN>(a, r, smem);
+        plan_request<IDX, GEN>(a, r, smem, a.tab.t_base);
     }
 }
 

@@ -100,7 +100,7 @@ struct Speculator {
                     const int32_t slot = take_slot(c);
                     require(slot < g.S_scan, FMDP_ERR_ARG, "internal: batch slot beyond the scanned range");
                     const uint64_t id = c->book.next_id++;
-                    c->book.plans[id] = PlanMeta{slot, reqs[k].depart_step, fin_ro[k].n_points};
+                    c->book.add(id, PlanMeta{slot, reqs[k].depart_step, fin_ro[k].n_points});
                     c->book.S_hw = std::max(c->book.S_hw, slot + 1);
                     pending.push_back({id, slot});
                     slot_of[k] = slot;

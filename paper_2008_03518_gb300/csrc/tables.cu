@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(kRowThreads) sepcheck_rows_kernel(const __grid
     int* npts_s = tord + kRowTile;
     const int tid = threadIdx.x, NT = blockDim.x;
     const int32_t W = a.tab.T_win;
-    const int64_t T = a.tab.t_base + blockIdx.x;
+    const int64_t T = a.tab.t_base + a.row0 + blockIdx.x;
     int64_t row = T % W;
     if (row < 0) row += W;
     if (tid == 0) *npts_s = 0;
@@ -354,7 +354,9 @@ cudaError_t prepare_sepcheck_rows(size_t smem) {
 }
 
 cudaError_t launch_sepcheck_rows(const SepRowsArgs& a, cudaStream_t s) {
-    sepcheck_rows_kernel<<<(unsigned)a.tab.T_win, kRowThreads, sepcheck_rows_smem(a.n_max), s>>>(a);
+    const int32_t rows = a.nrows > 0 ? a.nrows : a.tab.T_win;
+    if (a.row0 < 0 || a.row0 + rows > a.tab.T_win) return cudaErrorInvalidValue;
+    sepcheck_rows_kernel<<<(unsigned)rows, kRowThreads, sepcheck_rows_smem(a.n_max), s>>>(a);
     return cudaGetLastError();
 }
 
