@@ -494,7 +494,15 @@ int32_t run_pipeline(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_resu
     require(resident >= 1, FMDP_ERR_ARG, "the rollout shape does not fit an SM");
     const int per_sm = std::max(1, resident / std::max(1, c->n_sm));
     const int reserve = per_sm * std::max(4, c->n_sm / 16);
-    const int n_ctas = std::max(1, std::min(resident - reserve, window));
+    // persistent CTAs: serving, at most two thirds of the SM count (its reports and expiry
+    // clearing run beside the launch and must find room, or every table operation behind them
+    // waits until the launch idles out); a batch call, at most the SM count (it reports at its
+    // end). Measured on 152 SMs: serving C4 with 100 CTAs held 32k req/s at p99 11 ms where
+    // 144 fell to 7.6k/s and 256 to 4.5k/s; batches: C2 0.101 / 0.103 / 0.110 s per call with
+    // 100 / 144 / 256 CTAs, the 20k-plan batch of 512 27.2k / 26.3k / 26.0k plans/s with
+    // 100 / 152 / 256, the 100k-plan batch of 512 23.6k / 26.0k / 27.1k
+    const int cta_cap = serve ? c->n_sm * 2 / 3 : c->n_sm;
+    const int n_ctas = std::max(1, std::min(std::min(resident - reserve, window), cta_cap));
 
     RolloutArgs ra{};
     ra.m = c->model;
@@ -918,7 +926,11 @@ int32_t run_pipeline(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_resu
                 const int32_t q = head + kPublishAhead - 1;
                 if (q < joined && phase[q] == kDone && check_plan(q) && contrib_tok[q] != tok[q]) set_contribution(q);
             }
-            if (unreported.size() >= (size_t)kRepChunk) report(unreported);  // as they come, off the expiry
+            // serving: reports as requests finish, so that an expiry (which must report the
+            // finished requests before it clears their rows) finds few waiting. A batch call
+            // reports at its end: a report kernel beside a busy persistent launch could hold
+            // up the table stream behind it until the launch idled out
+            if (serve && unreported.size() >= (size_t)kRepChunk) report(unreported);
             if (progress) last_progress = now;
             if (finalized >= n) break;
 
