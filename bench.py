@@ -375,6 +375,8 @@ def main():
                     help="0: pipelined batches (default); 1: speculative waves (the ncu launch list)")
     ap.add_argument("--mode", default="batched", choices=["batched", "sequential"],
                     help="path timed for value: batched FCFS (default) or one request at a time")
+    ap.add_argument("--metrics-jsonl", default=None,
+                    help="also append the result line to this file (one JSON line per run)")
     ap.add_argument("--case", default=None, choices=["policy20k", "sepcheck20k"],
                     help="a small profiling case instead of the benchmark (one JSON line): the policy kernel "
                          "or the row-major separation check at 20k known plans")
@@ -564,9 +566,13 @@ def main():
             # saturation; each result equals one-at-a-time FCFS
             serving = {}
             sim0 = sc4.meta["sim_start"]
-            rates = (50, 200, 1000, 2000, 4000, 8000, 16000, 32000)
+            rates = (50, 200, 1000, 2000, 4000, 8000, 16000, 32000, 64000, 128000)
+
+            def window_s(rate):  # arrival window per offered rate (about 16k to 64k requests above 8k/s)
+                return args.serve_seconds if rate <= 8000 else (1.0 if rate <= 32000 else 0.5)
+
             for rate in rates:
-                arr = S.poisson_arrivals(900 + rate, float(rate), args.serve_seconds if rate <= 8000 else 1.0)
+                arr = S.poisson_arrivals(900 + rate, float(rate), window_s(rate))
                 rq = S.serving_requests(sc4, arr, 901 + rate, time_scale=args.time_scale, sim_start=sim0)
                 s4.restore()
                 barrier()
@@ -590,7 +596,7 @@ def main():
                     break
             modes["serving"] = {"known_plans": len(sc4.plans), "max_active_plans": sc4.meta["max_active_plans"],
                                 "workload": sc4.name,
-                                "arrivals": f"Poisson, {args.serve_seconds} s per rate (1 s above 8000 /s)",
+                                "arrivals": f"Poisson, {args.serve_seconds} s per rate (1 s for 16k-32k /s, 0.5 s above)",
                                 "time_scale": args.time_scale, "sim_start_step": sim0, "rates_per_s": serving,
                                 "saturation_rate": knee,
                                 "saturation_rule": "first offered rate served below 0.9 x its rate or with p99 "
@@ -708,6 +714,9 @@ def main():
         line["cpu_baseline"] = cpu_baseline(sc, args.cpu_seconds)
     if rank == 0:
         print(json.dumps(line), flush=True)
+        if args.metrics_jsonl:
+            from paper_2008_03518_gb300.fmdp import append_jsonl
+            append_jsonl(args.metrics_jsonl, line)
     s.close()
     reps.close()
 

@@ -43,6 +43,7 @@ typedef int32_t fmdp_status;
 #define FMDP_ERR_FULL (-5)    /* no free plan slot */
 #define FMDP_ERR_RANGE (-6)   /* time steps outside the table's sliding window */
 #define FMDP_ERR_NOTFOUND (-7)
+#define FMDP_ERR_IO (-8)      /* a file could not be read or written, or is not a plan file */
 
 /* Verdicts of a planning request (Sec. V: only a collision-free trajectory is accepted). */
 #define FMDP_ADMITTED 0
@@ -402,6 +403,21 @@ fmdp_status fmdp_query_plans(fmdp_ctx* ctx, int64_t t_begin, int64_t t_end, uint
 /* Samples of a stored plan (cap points of room in xyz). */
 fmdp_status fmdp_get_plan(fmdp_ctx* ctx, uint64_t id, int64_t* t0_out, float* xyz, int32_t cap,
                           int32_t* n_out);
+
+/* The plan table to a file and back (checkpoint / resume of the accepted-plan database, which
+ * Sec. V keeps across scheduling runs: loaded at start, appended to by every admission).
+ * fmdp_save_plans writes every stored plan's samples that are still inside the window (a
+ * plan that started before the window is saved from the window's first step), in plan-id
+ * order, to the file at `path` (created or replaced): a header {"FMDPPLN1", window start,
+ * plans, samples}, one record {first step, count} per plan, then every sample (x, y, z as
+ * float32), little-endian; n_out (optional): plans written. fmdp_load_plans adds the plans of
+ * such a file as known plans, like fmdp_add_plans (new ids: ids_out, optional, receives the
+ * first cap of them in file order; n_out, optional: plans in the file). A context holding no
+ * plans first moves its window to the file's start; otherwise every plan must fall inside
+ * the window (FMDP_ERR_RANGE). FMDP_ERR_IO: the file cannot be opened, written or read, or
+ * is not a whole plan file; FMDP_ERR_FULL: not enough free slots. */
+fmdp_status fmdp_save_plans(fmdp_ctx* ctx, const char* path, int64_t* n_out);
+fmdp_status fmdp_load_plans(fmdp_ctx* ctx, const char* path, uint64_t* ids_out, int64_t cap, int64_t* n_out);
 /* Slides the window to start at t_now_step: plans whose last sample is before it are
  * removed and their slots freed; table rows of earlier steps are cleared for reuse. */
 fmdp_status fmdp_expire(fmdp_ctx* ctx, int64_t t_now_step);

@@ -316,6 +316,127 @@ fmdp_status fmdp_schedule_batch(fmdp_ctx* c, const fmdp_request* reqs, int32_t n
     });
 }
 
+// ---- plan table file: header, one record per plan, then every sample (little-endian, the
+// layout of the structs below)
+namespace {
+struct PlanFileHeader {
+    char magic[8];      // "FMDPPLN1"
+    int64_t t_base;     // the table window's first step when saved
+    int64_t n_plans;
+    int64_t n_samples;  // sum of the records' counts
+};
+struct PlanFileRecord {
+    int64_t t0;     // first step of the saved samples
+    int32_t count;  // samples
+    int32_t pad;
+};
+const char kPlanMagic[8] = {'F', 'M', 'D', 'P', 'P', 'L', 'N', '1'};
+}  // namespace
+
+fmdp_status fmdp_save_plans(fmdp_ctx* c, const char* path, int64_t* n_out) {
+    if (!c) return FMDP_ERR_ARG;
+    return guard(c, [&] {
+        require(path != nullptr, FMDP_ERR_ARG, "null path");
+        // the samples of every stored plan that are still in the window, in id order
+        std::vector<int32_t> slots, counts;
+        std::vector<int64_t> t0s, offs;
+        int64_t total = 0;
+        int32_t maxc = 0;
+        for (auto& kv : c->book.plans) {
+            const PlanMeta& p = kv.second;
+            const int64_t a = std::max<int64_t>(p.t0, c->book.t_base), b = p.t0 + p.n;
+            if (b <= a) continue;
+            slots.push_back(p.slot);
+            t0s.push_back(a);
+            counts.push_back((int32_t)(b - a));
+            offs.push_back(total);
+            total += b - a;
+            maxc = std::max(maxc, (int32_t)(b - a));
+        }
+        const int64_t n = (int64_t)t0s.size();
+        std::vector<float> xyz((size_t)total * 3);
+        if (n > 0) {
+            c->slots.ensure((size_t)n);
+            c->t0s.ensure((size_t)n);
+            c->offs.ensure((size_t)n);
+            c->counts.ensure((size_t)n);
+            c->traj.ensure((size_t)total * 3);
+            CK(cudaMemcpyAsync(c->slots.p, slots.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+            CK(cudaMemcpyAsync(c->t0s.p, t0s.data(), n * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
+            CK(cudaMemcpyAsync(c->offs.p, offs.data(), n * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
+            CK(cudaMemcpyAsync(c->counts.p, counts.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+            LAUNCH(c, launch_gather_plans(c->X, c->Y, c->Z, c->S_pad, c->T_win, c->slots.p, c->t0s.p, c->counts.p,
+                                          c->offs.p, c->traj.p, (int)n, maxc, c->stream));
+            CK(cudaMemcpyAsync(xyz.data(), c->traj.p, (size_t)total * 3 * sizeof(float), cudaMemcpyDeviceToHost,
+                               c->stream));
+            CK(cudaStreamSynchronize(c->stream));
+        }
+        FILE* f = std::fopen(path, "wb");
+        require(f != nullptr, FMDP_ERR_IO, "cannot open the plan file for writing");
+        PlanFileHeader h{};
+        std::memcpy(h.magic, kPlanMagic, 8);
+        h.t_base = c->book.t_base;
+        h.n_plans = n;
+        h.n_samples = total;
+        bool ok = std::fwrite(&h, sizeof(h), 1, f) == 1;
+        for (int64_t i = 0; ok && i < n; ++i) {
+            const PlanFileRecord r{t0s[i], counts[i], 0};
+            ok = std::fwrite(&r, sizeof(r), 1, f) == 1;
+        }
+        if (ok && total > 0) ok = std::fwrite(xyz.data(), sizeof(float), xyz.size(), f) == xyz.size();
+        ok = (std::fclose(f) == 0) && ok;
+        require(ok, FMDP_ERR_IO, "writing the plan file failed");
+        if (n_out) *n_out = n;
+    });
+}
+
+fmdp_status fmdp_load_plans(fmdp_ctx* c, const char* path, uint64_t* ids_out, int64_t cap, int64_t* n_out) {
+    if (!c) return FMDP_ERR_ARG;
+    return guard(c, [&] {
+        require(path != nullptr && cap >= 0 && (cap == 0 || ids_out), FMDP_ERR_ARG, "null path or ids");
+        FILE* f = std::fopen(path, "rb");
+        require(f != nullptr, FMDP_ERR_IO, "cannot open the plan file");
+        PlanFileHeader h{};
+        std::vector<PlanFileRecord> recs;
+        std::vector<float> xyz;
+        bool ok = std::fread(&h, sizeof(h), 1, f) == 1 && std::memcmp(h.magic, kPlanMagic, 8) == 0 &&
+                  h.n_plans >= 0 && h.n_samples >= 0 && h.n_plans <= (int64_t)c->S_max &&
+                  h.n_samples <= (int64_t)c->S_max * c->T_win;
+        if (ok) {
+            recs.resize((size_t)h.n_plans);
+            xyz.resize((size_t)h.n_samples * 3);
+            ok = (h.n_plans == 0 || std::fread(recs.data(), sizeof(PlanFileRecord), recs.size(), f) == recs.size()) &&
+                 (h.n_samples == 0 || std::fread(xyz.data(), sizeof(float), xyz.size(), f) == xyz.size());
+        }
+        std::fclose(f);
+        require(ok, FMDP_ERR_IO, "not a plan file, or a truncated one");
+        int64_t sum = 0;
+        for (const auto& r : recs) {
+            require(r.count >= 1, FMDP_ERR_IO, "a plan record without samples");
+            sum += r.count;
+        }
+        require(sum == h.n_samples, FMDP_ERR_IO, "the records do not account for the samples");
+        // an empty table takes the saved window (its rows are cleared on the way)
+        if (c->book.plans.empty() && h.t_base > c->book.t_base) expire_to(c, h.t_base, nullptr);
+        std::vector<int64_t> t0s(recs.size());
+        std::vector<int32_t> counts(recs.size());
+        for (size_t i = 0; i < recs.size(); ++i) {
+            t0s[i] = recs[i].t0;
+            counts[i] = recs[i].count;
+        }
+        std::vector<uint64_t> ids(recs.size());
+        int64_t off = 0;
+        for (size_t i0 = 0; i0 < recs.size();) {  // in chunks of the packed call's size
+            const int32_t m = (int32_t)std::min<size_t>(recs.size() - i0, 1u << 20);
+            store_plans(c, m, t0s.data() + i0, counts.data() + i0, xyz.data() + 3 * off, ids.data() + i0);
+            for (int32_t i = 0; i < m; ++i) off += counts[i0 + i];
+            i0 += m;
+        }
+        for (int64_t i = 0; i < std::min<int64_t>(cap, (int64_t)ids.size()); ++i) ids_out[i] = ids[i];
+        if (n_out) *n_out = (int64_t)recs.size();
+    });
+}
+
 fmdp_status fmdp_query_plans(fmdp_ctx* c, int64_t t_begin, int64_t t_end, uint64_t* ids, int32_t cap,
                              int32_t* n_out) {
     if (!c) return FMDP_ERR_ARG;

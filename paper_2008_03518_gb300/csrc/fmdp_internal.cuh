@@ -267,6 +267,11 @@ cudaError_t prepare_rollout_kernel(size_t smem);
 // (a lazy load waits for the kernels running at the time, such as a persistent rollout launch).
 cudaError_t preload_index_kernels();
 cudaError_t preload_table_kernels();
+// Packs the samples of n plans (slot, first step, count each; offsets into out in samples)
+// from the table planes into out [sum counts][3].
+cudaError_t launch_gather_plans(const float* X, const float* Y, const float* Z, int32_t S_pad, int32_t T_win,
+                                const int32_t* slots, const int64_t* t0s, const int32_t* counts, const int64_t* offs,
+                                float* out, int n_plans, int max_count, cudaStream_t s);
 int rollout_max_active_clusters(int cs, int threads, size_t smem);
 cudaError_t launch_sepcheck(const SepArgs& a, int n_req, int max_points, cudaStream_t s);
 cudaError_t launch_sep_reset(SepOut* out, int n, cudaStream_t s);

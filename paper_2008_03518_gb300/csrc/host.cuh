@@ -19,6 +19,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "learned.cuh"
 
 namespace fmdp {
@@ -312,6 +314,14 @@ namespace fmdp {
 cudaEvent_t next_event(fmdp_ctx* c);
 struct Geometry;
 
+// Names a coarse host phase on timeline tools (an NVTX range; nothing happens unless a tool
+// is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 struct KernelTimer {
     fmdp_ctx* c;
     int kind;

@@ -378,6 +378,7 @@ void copy_points_back(fmdp_ctx* c, int32_t n, fmdp_result* res) {
 int32_t run_batch(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_result* res,
                   const fmdp_request* dev_reqs, bool keep_points) {
     if (n <= 0) return 0;
+    const NvtxRange range("fmdp batch FCFS");
     if (pipeline_eligible(c) && pipeline_fits(c, n, nullptr))
         return run_pipeline(c, reqs, n, res, dev_reqs, keep_points, nullptr);
     const int32_t bs = c->opt.batch_size > 0 ? c->opt.batch_size : kBatchDefault;

@@ -7,6 +7,7 @@ namespace fmdp {
 
 int32_t run_fcfs(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_result* res, bool staged,
                  bool cosim, int32_t absent) {
+    const NvtxRange range("fmdp sequential FCFS");
     SeqBuffers& B = staged ? c->stg : c->seq;
     const bool keep_on_device = staged;
     int32_t admitted = 0;

@@ -108,6 +108,7 @@ void mlp_train(fmdp_ctx* c, int32_t epochs, int32_t batch, float lr, uint64_t se
 
 
 void learned_collect(fmdp_ctx* c, const fmdp_request* reqs, int32_t n) {
+    const NvtxRange range("fmdp learned collect");
     require(c->index_on, FMDP_ERR_ARG, "the learned proposal reads the spatial index (full_scan must be 0)");
     if (n <= 0) return;
     batch_prepare(c, reqs, n, 64, nullptr);

@@ -370,6 +370,7 @@ int32_t run_pipeline(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_resu
                      const fmdp_request* dev_reqs, bool keep_points, const PipeServe* serve) {
     using clk = std::chrono::steady_clock;
     if (n <= 0) return 0;
+    const NvtxRange range("fmdp pipelined FCFS");
     require(pipeline_eligible(c), FMDP_ERR_ARG, "internal: pipelined FCFS needs the index and W = 1");
     const int32_t window = pipeline_window(c, serve);
     batch_prepare(c, reqs, n, window, dev_reqs);
@@ -606,6 +607,7 @@ int32_t run_pipeline(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_resu
     // requests, on the table stream, into B.sepo: the rows their trajectories reach only, and
     // without waiting (a staging slot is reused once the report that last used it is done)
     auto report = [&](std::vector<int32_t>& L) {
+        const NvtxRange range("fmdp separation report");
         for (size_t o = 0; o < L.size(); o += kBatchMax) {
             const int32_t m = (int32_t)std::min<size_t>(kBatchMax, L.size() - o);
             const int q = P.rep_next;
@@ -969,6 +971,7 @@ int32_t run_pipeline(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_resu
             if (draining && inflight.empty()) {
                 stop_kernel();  // the idle CTAs give their SMs to the rebuild
                 if (xmax > kPipeExtraLimit || overfull) {  // rows whose extra lists grew long: rebuilt now
+                    const NvtxRange range("fmdp drain: index rows rebuilt");
                     CK(cudaStreamSynchronize(P.tstream));  // no report still reads the rows
                     index_rebuild_all(c);
                     std::fill(xcnt.begin(), xcnt.end(), 0);

@@ -10,6 +10,7 @@ namespace fmdp {
 // Continuous batching over an arrival trace (see fmdp_serve in the header).
 void run_serve(fmdp_ctx* c, const fmdp_request* reqs, const double* arrival_s, int32_t n,
                const fmdp_serve_options& o, fmdp_result* res, double* latency_ms, fmdp_serve_report* rep) {
+    const NvtxRange range("fmdp serve");
     const PipeServe ps{arrival_s, o, latency_ms, rep};
     if (pipeline_eligible(c) && pipeline_fits(c, n, &ps)) {  // continuous batching without waves
         run_pipeline(c, reqs, n, res, nullptr, false, &ps);

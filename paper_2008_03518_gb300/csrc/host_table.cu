@@ -430,6 +430,7 @@ void fill_result(const RolloutOut& ro, const SepOut& so, fmdp_result* res) {
 // c->stg.reqs on the device and trajectories stay there. Returns the number admitted.
 void store_plans(fmdp_ctx* c, int32_t n_plans, const int64_t* t0s, const int32_t* counts, const float* xyz,
                  uint64_t* ids_out) {
+    const NvtxRange range("fmdp store plans");
     require(n_plans >= 0, FMDP_ERR_ARG, "n_plans < 0");
     if (n_plans == 0) return;
     require(t0s && counts && xyz, FMDP_ERR_ARG, "null plan arrays");
@@ -534,6 +535,7 @@ void clear_rows(fmdp_ctx* c, int64_t a, int64_t b) {
 }
 
 void expire_to(fmdp_ctx* c, int64_t t_now, int64_t* n_expired, bool sync) {
+    const NvtxRange range("fmdp expiry");
     if (t_now <= c->book.t_base) return;
     int64_t n = 0;
     Book& bk = c->book;

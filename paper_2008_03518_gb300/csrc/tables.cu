@@ -518,6 +518,40 @@ cudaError_t launch_sep_reset_idx(SepOut* out, const int32_t* idx, const int32_t*
     return cudaGetLastError();
 }
 
+// Copies the samples of n plans out of the table planes into one packed [sum counts][3]
+// array (plan i's samples at offs[i]): grid x strides over samples, y over plans.
+__global__ void gather_plans_kernel(const float* X, const float* Y, const float* Z, int32_t S_pad, int32_t T_win,
+                                    const int32_t* slots, const int64_t* t0s, const int32_t* counts,
+                                    const int64_t* offs, float* out) {
+    const int p = blockIdx.y;
+    const int32_t n = counts[p], slot = slots[p];
+    const int64_t t0 = t0s[p], off = offs[p];
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        int64_t row = (t0 + k) % T_win;
+        if (row < 0) row += T_win;
+        const size_t at = (size_t)row * S_pad + slot;
+        float* o = out + 3 * (size_t)(off + k);
+        o[0] = X[at];
+        o[1] = Y[at];
+        o[2] = Z[at];
+    }
+}
+
+cudaError_t launch_gather_plans(const float* X, const float* Y, const float* Z, int32_t S_pad, int32_t T_win,
+                                const int32_t* slots, const int64_t* t0s, const int32_t* counts, const int64_t* offs,
+                                float* out, int n_plans, int max_count, cudaStream_t s) {
+    if (n_plans <= 0 || max_count <= 0) return cudaSuccess;
+    const int bx = min((max_count + 255) / 256, 16);
+    for (int p0 = 0; p0 < n_plans; p0 += 65535) {
+        const int np = min(65535, n_plans - p0);
+        gather_plans_kernel<<<dim3((unsigned)bx, (unsigned)np), 256, 0, s>>>(X, Y, Z, S_pad, T_win, slots + p0, t0s + p0,
+                                                                            counts + p0, offs + p0, out);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 // Loads the table kernels now, for the reason given at preload_index_kernels.
 cudaError_t preload_table_kernels() {
     cudaFuncAttributes fa;
@@ -529,6 +563,7 @@ cudaError_t preload_table_kernels() {
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, batch_minsep_kernel);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, influence_kernel);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, sep_reset_idx_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, gather_plans_kernel);
     return e;
 }
 

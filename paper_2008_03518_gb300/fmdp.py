@@ -15,7 +15,27 @@ from . import build as _build
 
 ADMITTED, REJ_CONFLICT, REJ_TERRAIN, REJ_HORIZON, REJ_NO_ACTION = range(5)
 STATUS_NAMES = {0: "OK", -1: "ERR_ARG", -2: "ERR_OOM", -3: "ERR_CUDA", -4: "ERR_TIMEOUT", -5: "ERR_FULL",
-                -6: "ERR_RANGE", -7: "ERR_NOTFOUND"}
+                -6: "ERR_RANGE", -7: "ERR_NOTFOUND", -8: "ERR_IO"}
+
+
+def append_jsonl(path, record):
+    """Appends one metrics record as a JSON line (numpy scalars and arrays as plain numbers
+    and lists) to the file at path."""
+    import json
+
+    def plain(v):
+        if isinstance(v, dict):
+            return {str(k): plain(x) for k, x in v.items()}
+        if isinstance(v, (list, tuple)):
+            return [plain(x) for x in v]
+        if isinstance(v, np.ndarray):
+            return v.tolist()
+        if isinstance(v, np.generic):
+            return v.item()
+        return v
+
+    with open(path, "a", encoding="utf-8") as f:
+        f.write(json.dumps(plain(record), sort_keys=True) + "\n")
 
 
 class FmdpError(RuntimeError):
@@ -156,7 +176,7 @@ EXPORTS = ("fmdp_options_default", "fmdp_create", "fmdp_destroy", "fmdp_last_err
            "fmdp_autotune", "fmdp_tune_cache_get", "fmdp_tune_cache_put", "fmdp_schedule_departures",
            "fmdp_schedule_departures_batch",
            "fmdp_schedule_cosim", "fmdp_selftest_wait_timeout",
-           "fmdp_get_plan", "fmdp_expire", "fmdp_snapshot", "fmdp_restore", "fmdp_clear", "fmdp_rollout_trace",
+           "fmdp_get_plan", "fmdp_save_plans", "fmdp_load_plans", "fmdp_expire", "fmdp_snapshot", "fmdp_restore", "fmdp_clear", "fmdp_rollout_trace",
            "fmdp_sep_check", "fmdp_sep_check_noalloc", "fmdp_set_profiling", "fmdp_get_stats",
            "fmdp_set_batch_mode", "fmdp_last_call_times", "fmdp_probe_peaks")
 
@@ -222,6 +242,8 @@ def load(build_if_missing: bool = True):
     L.fmdp_fetch_staged.argtypes = [vp, P(Result), c.c_int32]
     L.fmdp_query_plans.argtypes = [vp, c.c_int64, c.c_int64, P(c.c_uint64), c.c_int32, P(c.c_int32)]
     L.fmdp_get_plan.argtypes = [vp, c.c_uint64, P(c.c_int64), _fp, c.c_int32, P(c.c_int32)]
+    L.fmdp_save_plans.argtypes = [vp, c.c_char_p, P(c.c_int64)]
+    L.fmdp_load_plans.argtypes = [vp, c.c_char_p, P(c.c_uint64), c.c_int64, P(c.c_int64)]
     L.fmdp_expire.argtypes = [vp, c.c_int64]
     for name in ("fmdp_snapshot", "fmdp_restore", "fmdp_clear"):
         getattr(L, name).argtypes = [vp]
@@ -469,6 +491,21 @@ class Scheduler:
         self._check(self._L.fmdp_query_plans(self._h, int(t_begin), int(t_end), _ptr(ids, ctypes.c_uint64),
                                              ids.size, ctypes.byref(n)))
         return ids[: n.value]
+
+    def save_plans(self, path):
+        """Writes the plan table to a file (fmdp_save_plans); returns the plans written."""
+        n = ctypes.c_int64()
+        self._check(self._L.fmdp_save_plans(self._h, os.fsencode(path), ctypes.byref(n)))
+        return n.value
+
+    def load_plans(self, path, max_ids=1 << 22):
+        """Adds the plans of a plan file as known plans (fmdp_load_plans); returns their new
+        ids in file order (the first max_ids of them)."""
+        ids = np.zeros(max_ids, dtype=np.uint64)
+        n = ctypes.c_int64()
+        self._check(self._L.fmdp_load_plans(self._h, os.fsencode(path), _ptr(ids, ctypes.c_uint64), max_ids,
+                                            ctypes.byref(n)))
+        return ids[:min(n.value, max_ids)].copy()
 
     def get_plan(self, pid):
         t0, n = ctypes.c_int64(), ctypes.c_int32()
@@ -746,6 +783,12 @@ class Scheduler:
         pk = Peaks()
         self._check(self._L.fmdp_probe_peaks(self._h, ctypes.byref(pk)))
         return {k: getattr(pk, k) for k, _ in Peaks._fields_}
+
+    def write_metrics(self, path, **tags):
+        """Appends this context's statistics (fmdp_get_stats) and the given tags, with a
+        wall-clock time stamp, as one JSON line to the file at path."""
+        import time
+        append_jsonl(path, {"time_unix_s": time.time(), "tags": tags, "stats": self.stats()})
 
     def stats(self):
         s = Stats()

@@ -77,6 +77,21 @@ def test_null_arguments_are_rejected_without_a_device(lib):
     assert h.value is None
     assert lib.fmdp_schedule(None, None, None) == -1
     assert lib.fmdp_add_plan(None, 0, None, 0, None) == -1
+    assert lib.fmdp_save_plans(None, b"x", None) == -1
+    assert lib.fmdp_load_plans(None, b"x", None, 0, None) == -1
+
+
+def test_metrics_lines_are_plain_json(tmp_path):
+    """append_jsonl writes one JSON line per record, numpy values as plain numbers."""
+    import json
+
+    import numpy as np
+
+    p = tmp_path / "m.jsonl"
+    fmdp.append_jsonl(str(p), {"a": np.int64(3), "b": np.arange(3, dtype=np.float32), "c": {"d": np.float64(0.5)}})
+    fmdp.append_jsonl(str(p), {"a": 4})
+    lines = p.read_text().splitlines()
+    assert [json.loads(x) for x in lines] == [{"a": 3, "b": [0.0, 1.0, 2.0], "c": {"d": 0.5}}, {"a": 4}]
 
 
 def test_no_cpu_fallback_without_gpu():
