@@ -20,7 +20,6 @@ constexpr int kHeadings = 24;    // 15-degree heading table
 constexpr int kRing = 4;         // slice buffers per CTA (two in use, two in flight)
 constexpr int kMaxCluster = 16;
 constexpr float kWellBand = 4e-5f;  // |d^2 - R^2| <= kWellBand * R^2 -> FP64 re-evaluation
-constexpr float kSepBand = 0.05f;   // metres around a separation threshold -> FP64
 constexpr float kClrBand = 0.05f;   // metres around the clearance threshold -> FP64
 constexpr double kTieRel = 1e-4;    // near-tie bar on the top-2 action values
 constexpr int kStatusCaptured = 0;

@@ -1493,7 +1493,7 @@ __device__ void pipe_finish(const RolloutArgs& a, int r, int token, int* red, lo
     const Model& m = a.m;
     const IndexView& iv = a.iv;
     const SepConsts sk = sep_consts(m.sep_h, m.sep_v);
-    const float reach = (float)m.sep_h + kSepBand + 1.0f;
+    const float reach = (float)m.sep_h + 1.0f;  // past it every pair is clear horizontally
     const int32_t my_ord = a.pipe.ord0 + r;
     const int64_t cst_row_len = (int64_t)iv.ncell + 1;
     int first = INT_MAX, terr = INT_MAX;

@@ -62,14 +62,16 @@ def test_sep_check_parity_including_threshold_pairs():
         for q in range(8):
             t0 = int(rng.integers(0, 20))
             traj = (base[rng.integers(0, 40)] + rng.uniform(-400, 400, size=(50, 3))).astype(np.float32)
-            # plant pairs exactly at, just inside and just outside the minima
+            # plant pairs exactly at, just inside and just outside the minima (1e-3 m is a few
+            # fp32 ulps at these coordinates, 3e-5 m below one: the sum rounds to the nearest
+            # representable sample, so those pairs sit within an ulp or two of the minima)
             for k in range(0, 50, 5):
                 j = int(rng.integers(0, len(plans)))
                 pt0, pxyz = plans[j]
                 idx = t0 + k - pt0
                 if 0 <= idx < len(pxyz):
-                    off = rng.choice([150.0, 149.999, 150.001, 0.0])
-                    dz = rng.choice([30.0, 29.999, 30.001, 0.0])
+                    off = rng.choice([150.0, 149.999, 150.001, 149.99997, 150.00003, 0.0])
+                    dz = rng.choice([30.0, 29.999, 30.001, 29.99997, 30.00003, 0.0])
                     ang = rng.uniform(0, 2 * np.pi)
                     traj[k] = pxyz[idx] + np.array([off * np.cos(ang), off * np.sin(ang), dz], dtype=np.float32)
             g = s.sep_check(t0, traj)
