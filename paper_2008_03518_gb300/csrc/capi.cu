@@ -130,7 +130,7 @@ fmdp_status fmdp_create(const fmdp_airspace* air, double gamma, const fmdp_actio
         }
         CK(cudaMalloc(&c->err, sizeof(int32_t)));
         CK(cudaMemsetAsync(c->err, 0, sizeof(int32_t), c->stream));
-        for (int32_t s = 0; s < c->S_max; ++s) c->book.free_slots.insert(c->book.free_slots.end(), s);
+        c->book.reset(c->S_max, c->T_win);
         fill_model(c, wells, acts, a.static_wells);
         c->index_on = o.full_scan == 0;
         if (c->index_on) {
@@ -342,17 +342,16 @@ fmdp_status fmdp_save_plans(fmdp_ctx* c, const char* path, int64_t* n_out) {
         std::vector<int64_t> t0s, offs;
         int64_t total = 0;
         int32_t maxc = 0;
-        for (auto& kv : c->book.plans) {
-            const PlanMeta& p = kv.second;
+        c->book.for_each([&](uint64_t, const PlanMeta& p) {
             const int64_t a = std::max<int64_t>(p.t0, c->book.t_base), b = p.t0 + p.n;
-            if (b <= a) continue;
+            if (b <= a) return;
             slots.push_back(p.slot);
             t0s.push_back(a);
             counts.push_back((int32_t)(b - a));
             offs.push_back(total);
             total += b - a;
             maxc = std::max(maxc, (int32_t)(b - a));
-        }
+        });
         const int64_t n = (int64_t)t0s.size();
         std::vector<float> xyz((size_t)total * 3);
         if (n > 0) {
@@ -417,7 +416,7 @@ fmdp_status fmdp_load_plans(fmdp_ctx* c, const char* path, uint64_t* ids_out, in
         }
         require(sum == h.n_samples, FMDP_ERR_IO, "the records do not account for the samples");
         // an empty table takes the saved window (its rows are cleared on the way)
-        if (c->book.plans.empty() && h.t_base > c->book.t_base) expire_to(c, h.t_base, nullptr);
+        if (c->book.empty() && h.t_base > c->book.t_base) expire_to(c, h.t_base, nullptr);
         std::vector<int64_t> t0s(recs.size());
         std::vector<int32_t> counts(recs.size());
         for (size_t i = 0; i < recs.size(); ++i) {
@@ -443,13 +442,12 @@ fmdp_status fmdp_query_plans(fmdp_ctx* c, int64_t t_begin, int64_t t_end, uint64
     return guard(c, [&] {
         require(n_out && (cap == 0 || ids) && cap >= 0, FMDP_ERR_ARG, "null output");
         int32_t n = 0;
-        for (auto& kv : c->book.plans) {
-            const PlanMeta& p = kv.second;
+        c->book.for_each([&](uint64_t id, const PlanMeta& p) {
             if (p.t0 < t_end && p.t0 + p.n > t_begin) {
-                if (n < cap) ids[n] = kv.first;
+                if (n < cap) ids[n] = id;
                 ++n;
             }
-        }
+        });
         *n_out = n;
     });
 }
@@ -457,9 +455,9 @@ fmdp_status fmdp_query_plans(fmdp_ctx* c, int64_t t_begin, int64_t t_end, uint64
 fmdp_status fmdp_get_plan(fmdp_ctx* c, uint64_t id, int64_t* t0_out, float* xyz, int32_t cap, int32_t* n_out) {
     if (!c) return FMDP_ERR_ARG;
     return guard(c, [&] {
-        auto it = c->book.plans.find(id);
-        require(it != c->book.plans.end(), FMDP_ERR_NOTFOUND, "no such plan");
-        const PlanMeta& p = it->second;
+        const PlanMeta* pp = c->book.find(id);
+        require(pp != nullptr, FMDP_ERR_NOTFOUND, "no such plan");
+        const PlanMeta p = *pp;
         if (t0_out) *t0_out = p.t0;
         if (n_out) *n_out = p.n;
         if (!xyz) return;
@@ -693,7 +691,7 @@ fmdp_status fmdp_selftest_wait_timeout(fmdp_ctx* c, int32_t* observed) {
             r[i].horizon = 4;
             check_request(c, r[i]);
         }
-        const size_t plans_before = c->book.plans.size();
+        const size_t plans_before = c->book.size();
         int32_t st = FMDP_OK;
         try {
             run_fcfs(c, r, 2, nullptr, false, true, 1);
@@ -702,7 +700,7 @@ fmdp_status fmdp_selftest_wait_timeout(fmdp_ctx* c, int32_t* observed) {
         }
         if (observed) *observed = st;
         require(st == FMDP_ERR_TIMEOUT, FMDP_ERR_CUDA, "the self-test wait did not report a timeout");
-        require(c->book.plans.size() == plans_before, FMDP_ERR_CUDA, "the self-test admitted a plan");
+        require(c->book.size() == plans_before, FMDP_ERR_CUDA, "the self-test admitted a plan");
     });
 }
 
@@ -825,9 +823,8 @@ fmdp_status fmdp_clear(fmdp_ctx* c) {
         index_reset(c);
         CK(cudaStreamSynchronize(c->stream));
         const int64_t tb = c->book.t_base;
-        c->book = Book();
+        c->book.reset(c->S_max, c->T_win);
         c->book.t_base = tb;
-        for (int32_t s = 0; s < c->S_max; ++s) c->book.free_slots.insert(c->book.free_slots.end(), s);
     });
 }
 

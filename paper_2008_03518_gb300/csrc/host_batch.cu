@@ -348,8 +348,10 @@ Geometry batch_geometry(fmdp_ctx* c, int32_t n_new, int32_t wave) {
     if (c->index_on) return geometry_batch(c, c->S_pad, wave);
     require((size_t)n_new <= c->book.free_slots.size(), FMDP_ERR_FULL, "not enough free plan slots for the batch");
     int32_t bound = c->book.S_hw;
-    auto it = c->book.free_slots.begin();
-    for (int32_t i = 0; i < n_new; ++i, ++it) bound = std::max(bound, *it + 1);
+    for (int32_t i = 0, s = -1; i < n_new; ++i) {
+        s = c->book.free_slots.next(s + 1);
+        bound = std::max(bound, s + 1);
+    }
     return geometry_batch(c, round_up(bound, 512), wave);
 }
 

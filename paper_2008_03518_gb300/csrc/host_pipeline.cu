@@ -1003,7 +1003,7 @@ int32_t run_pipeline(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_resu
             // serving: arrivals join while the set has room and the table has slots for all
             if (serve) {
                 while (joined < n && serve->arrival_s[joined] <= now && joined - head < window) {
-                    const int64_t active = (int64_t)c->book.plans.size();
+                    const int64_t active = (int64_t)c->book.size();
                     const int64_t room = std::min<int64_t>((int64_t)c->book.free_slots.size(), max_active - active);
                     if ((int64_t)(joined - head) + 1 > room) {
                         if (!deferred_flag[joined]) {
@@ -1030,7 +1030,7 @@ int32_t run_pipeline(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_resu
             if (serve && inflight.empty() && head == joined && joined < n) {
                 if (deferred_flag[joined]) {  // nothing unresolved and no room: only expiry frees slots
                     int64_t first_end = INT64_MAX;
-                    for (auto& kv : c->book.plans) first_end = std::min(first_end, kv.second.t0 + kv.second.n);
+                    c->book.for_each([&](uint64_t, const PlanMeta& p) { first_end = std::min(first_end, p.t0 + p.n); });
                     require(first_end <= dep_suffix[joined], FMDP_ERR_FULL, "plan table full and no plan can expire");
                     std::this_thread::sleep_for(std::chrono::microseconds(200));
                 } else {

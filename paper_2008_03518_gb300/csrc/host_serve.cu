@@ -54,7 +54,7 @@ void run_serve(fmdp_ctx* c, const fmdp_request* reqs, const double* arrival_s, i
             // admission: arrived requests join while the set has room and slots remain for all
             bool blocked = false;
             while (next < n && arrival_s[next] <= now && (int32_t)sp.U.size() < in_flight) {
-                const int64_t active = (int64_t)c->book.plans.size();
+                const int64_t active = (int64_t)c->book.size();
                 const int64_t room = std::min<int64_t>((int64_t)c->book.free_slots.size(), max_active - active);
                 if ((int64_t)sp.U.size() + 1 > room) {
                     blocked = true;
@@ -77,7 +77,7 @@ void run_serve(fmdp_ctx* c, const fmdp_request* reqs, const double* arrival_s, i
                 // nothing in flight and no room: only the clock can free slots, by expiring a
                 // plan that ends before the next departure
                 int64_t first_end = INT64_MAX;
-                for (auto& kv : c->book.plans) first_end = std::min(first_end, kv.second.t0 + kv.second.n);
+                c->book.for_each([&](uint64_t, const PlanMeta& p) { first_end = std::min(first_end, p.t0 + p.n); });
                 require(first_end <= dep_suffix[next], FMDP_ERR_FULL, "plan table full and no plan can expire");
                 std::this_thread::sleep_for(std::chrono::microseconds(200));
                 continue;

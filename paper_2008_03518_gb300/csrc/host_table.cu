@@ -234,7 +234,7 @@ void launch_window_rollout(fmdp_ctx* c, const Geometry& g, const fmdp_request* r
     LAUNCH(c, launch_lookahead(la, c->stream));
 }
 std::array<int32_t, 4> tune_key(const fmdp_ctx* c, int32_t wave) {
-    return {c->A, c->opt.combine, bit_length((int64_t)c->book.plans.size()), bit_length(wave)};
+    return {c->A, c->opt.combine, bit_length((int64_t)c->book.size()), bit_length(wave)};
 }
 // the cached shape for a wave of `wave` rollouts: its own bucket, else the nearest tuned one
 const fmdp_tune_entry* tune_lookup(const fmdp_ctx* c, int32_t wave) {
@@ -321,15 +321,13 @@ void check_request(fmdp_ctx* c, const fmdp_request& r) {
 
 int32_t take_slot(fmdp_ctx* c) {
     require(!c->book.free_slots.empty(), FMDP_ERR_FULL, "no free plan slot");
-    const int32_t s = *c->book.free_slots.begin();
-    c->book.free_slots.erase(c->book.free_slots.begin());
+    const int32_t s = c->book.free_slots.lowest();
+    c->book.free_slots.erase(s);
     return s;
 }
 
 void recompute_hw(fmdp_ctx* c) {
-    int32_t hw = 0;
-    for (auto& kv : c->book.plans) hw = std::max(hw, kv.second.slot + 1);
-    c->book.S_hw = hw;
+    c->book.S_hw = c->book.slot_bound();
 }
 
 // Enqueue rollout -> sep_check -> admission for n requests (device array c->reqs, slots in
@@ -537,24 +535,13 @@ void clear_rows(fmdp_ctx* c, int64_t a, int64_t b) {
 void expire_to(fmdp_ctx* c, int64_t t_now, int64_t* n_expired, bool sync) {
     const NvtxRange range("fmdp expiry");
     if (t_now <= c->book.t_base) return;
-    int64_t n = 0;
     Book& bk = c->book;
-    const auto later = std::greater<std::pair<int64_t, uint64_t>>();
-    while (!bk.by_end.empty() && bk.by_end.front().first < t_now) {
-        std::pop_heap(bk.by_end.begin(), bk.by_end.end(), later);
-        const auto [end, id] = bk.by_end.back();
-        bk.by_end.pop_back();
-        const auto it = bk.plans.find(id);
-        if (it == bk.plans.end() || it->second.t0 + it->second.n - 1 != end) continue;  // gone or changed
-        bk.free_slots.insert(it->second.slot);
-        bk.plans.erase(it);
-        ++n;
-    }
+    const int64_t n = bk.expire(t_now);
     clear_rows(c, c->book.t_base, t_now);
     c->book.t_base = t_now;
     // the slot high-water mark stays an upper bound (it only sizes scans): lowered only when
     // the table empties, not by walking every plan
-    if (bk.plans.empty()) c->book.S_hw = 0;
+    if (bk.empty()) c->book.S_hw = 0;
     if (sync) CK(cudaStreamSynchronize(c->stream));
     if (n_expired) *n_expired += n;
 }

@@ -182,7 +182,7 @@ struct Speculator {
     }
     void rollback() {  // admissions whose plans never reached the table
         for (auto& pr : pending) {
-            c->book.plans.erase(pr.first);
+            c->book.erase(pr.first);
             c->book.free_slots.insert(pr.second);
         }
         pending.clear();
