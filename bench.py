@@ -571,7 +571,7 @@ def main():
             def window_s(rate):  # arrival window per offered rate (about 16k to 64k requests above 8k/s)
                 return args.serve_seconds if rate <= 8000 else (1.0 if rate <= 32000 else 0.5)
 
-            for rate in rates:
+            def serve_rate(rate):
                 arr = S.poisson_arrivals(900 + rate, float(rate), window_s(rate))
                 rq = S.serving_requests(sc4, arr, 901 + rate, time_scale=args.time_scale, sim_start=sim0)
                 s4.restore()
@@ -579,28 +579,39 @@ def main():
                 _, lat, rep = s4.serve(rq, arr, time_scale=args.time_scale, max_in_flight=256,
                                        max_active_plans=sc4.meta["max_active_plans"], sim_start_step=sim0,
                                        points=False)
-                serving[str(rate)] = {"requests": len(rq), "throughput_rps": rep["throughput_rps"],
-                                      "latency_p50_ms": rep["latency_p50_ms"],
-                                      "latency_p99_ms": rep["latency_p99_ms"], "latency_max_ms": rep["latency_max_ms"],
-                                      "admitted": rep["admitted"], "rollouts": rep["rollouts"],
-                                      "replans": rep["replans"], "max_in_flight_seen": rep["max_in_flight_seen"],
-                                      "expiries": rep["expiries"], "plans_expired": rep["plans_expired"],
-                                      "deferred_for_memory": rep["deferred_for_memory"],
-                                      "rollout_occupancy": rep["rollout_occupancy"], "drains": rep["drains"]}
+                return {"requests": len(rq), "throughput_rps": rep["throughput_rps"],
+                        "latency_p50_ms": rep["latency_p50_ms"],
+                        "latency_p99_ms": rep["latency_p99_ms"], "latency_max_ms": rep["latency_max_ms"],
+                        "admitted": rep["admitted"], "rollouts": rep["rollouts"],
+                        "replans": rep["replans"], "max_in_flight_seen": rep["max_in_flight_seen"],
+                        "expiries": rep["expiries"], "plans_expired": rep["plans_expired"],
+                        "deferred_for_memory": rep["deferred_for_memory"],
+                        "rollout_occupancy": rep["rollout_occupancy"], "drains": rep["drains"]}
+
+            for rate in rates:
+                serving[str(rate)] = serve_rate(rate)
             base = serving["50"]["latency_p99_ms"]
+
+            def saturated(r, v):
+                return v["throughput_rps"] < 0.9 * float(r) or v["latency_p99_ms"] > 10.0 * max(base, 1.0)
+
             knee = None
             for r in map(str, rates):
-                v = serving[r]
-                if v["throughput_rps"] < 0.9 * float(r) or v["latency_p99_ms"] > 10.0 * max(base, 1.0):
-                    knee = r
-                    break
+                if saturated(r, serving[r]):
+                    # a rate that trips the rule runs once more: saturation shows in both runs,
+                    # a passing stall of the host or the device in one (both are reported)
+                    serving[r]["rerun"] = serve_rate(int(r))
+                    if saturated(r, serving[r]["rerun"]):
+                        knee = r
+                        break
             modes["serving"] = {"known_plans": len(sc4.plans), "max_active_plans": sc4.meta["max_active_plans"],
                                 "workload": sc4.name,
                                 "arrivals": f"Poisson, {args.serve_seconds} s per rate (1 s for 16k-32k /s, 0.5 s above)",
                                 "time_scale": args.time_scale, "sim_start_step": sim0, "rates_per_s": serving,
                                 "saturation_rate": knee,
                                 "saturation_rule": "first offered rate served below 0.9 x its rate or with p99 "
-                                                   "above 10 x the p99 at 50 requests/s"}
+                                                   "above 10 x the p99 at 50 requests/s, in its run and in a "
+                                                   "second run of the same arrivals"}
         s4.close()
     if mlp:
         modes["mlp_bf16"] = mlp

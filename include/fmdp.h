@@ -112,6 +112,10 @@ typedef struct {
                                  0 = pipelined where it applies (spatial index, W = 1, FastMDP
                                  rollouts): continuous batching without waves, see
                                  fmdp_schedule_batch; 1 = speculative waves. Same results. */
+    int32_t pipe_rebuild_items; /* pipelined mode: items appended to one index row before the
+                                   rows are rebuilt while no rollout runs (0 = 768). Fewer
+                                   keep each step's scan of appended items short; more make
+                                   rebuilds rarer. Same results. */
 } fmdp_options;
 
 /* Fills *o with the defaults (max combine, Table 3 wells, goal 200, W = 1, automatic). */
@@ -356,10 +360,12 @@ fmdp_status fmdp_selftest_wait_timeout(fmdp_ctx* ctx, int32_t* observed);
  * {128, 192, 256, 320, 384} x staged samples in {512, 1024, 1536, 2048} (those whose
  * staging buffers fit in shared memory), for W = min(n,
  * batch size) and its halvings down to 8, and caches the fastest shape under the key
- * (n_actions, combine, plan-count bucket, wave-size bucket). Each wave of a batched call
- * (fmdp_schedule_batch, fmdp_serve, fmdp_schedule_learned, staged batches) then launches
- * with the cached shape of its key, or of the nearest tuned wave-size bucket;
- * options.threads_per_cta and options.index_stage_items, when set, take precedence. */
+ * (n_actions, combine, plan-count bucket, wave-size bucket). Each wave of a batched call in
+ * wave mode (fmdp_schedule_batch, fmdp_serve, fmdp_schedule_learned, staged batches) then
+ * launches with the cached shape of its key, or of the nearest tuned wave-size bucket. The
+ * pipelined mode's persistent launch holds at most one CTA per multiprocessor and takes
+ * the widest shape (384 threads, 1536 staged samples). options.threads_per_cta and
+ * options.index_stage_items, when set, take precedence in both modes. */
 typedef struct {
     int32_t n_actions, combine;
     int32_t plans_bucket;        /* bit length of the number of stored plans */

@@ -67,6 +67,7 @@ fmdp_status fmdp_create(const fmdp_airspace* air, double gamma, const fmdp_actio
         require(o.index_stage_items >= 0 && o.index_stage_items <= 3000, FMDP_ERR_ARG,
                 "index stage items 0..3000");
         require(o.batch_mode == 0 || o.batch_mode == 1, FMDP_ERR_ARG, "batch_mode must be 0 (pipelined) or 1 (waves)");
+        require(o.pipe_rebuild_items >= 0, FMDP_ERR_ARG, "pipe_rebuild_items must be >= 0");
         require(o.index_vmax_mps >= 0.0 && o.index_cell_m >= 0.0, FMDP_ERR_ARG, "index bounds must be >= 0");
         std::vector<fmdp_well> wells;
         if (o.wells && o.n_wells > 0) {

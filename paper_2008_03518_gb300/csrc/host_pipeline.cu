@@ -67,7 +67,7 @@ constexpr int kRepSlots = 8;              // staging slots of the asynchronous s
 constexpr int kRepChunk = 64;             // finished requests per report while the launch runs
 constexpr int kBoxChunk = 32;             // steps per bounding box of a trajectory
 constexpr int kBoxSuper = 8;              // chunks per coarse box
-constexpr int32_t kPipeExtraLimit = 192;  // appended items per row before the rows are rebuilt
+constexpr int32_t kPipeExtraLimit = 768;  // appended items per row before the rows are rebuilt (default)
 constexpr int32_t kPublishAhead = 128;    // requests past the head whose plans are published
 constexpr int32_t kOrdLimit = 1 << 30;    // ordinals are rebased before they reach this
 
@@ -453,6 +453,7 @@ int32_t run_pipeline(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_resu
     // rows rebuilt before any of them could fill up: the appends since the rows were last
     // measured (acnt) reaching room[row] start a drain
     const int32_t margin = append_margin(window, n);
+    const int32_t rebuild_mark = c->opt.pipe_rebuild_items > 0 ? c->opt.pipe_rebuild_items : kPipeExtraLimit;
     std::vector<int32_t> room(c->T_win, 0), acnt(c->T_win, 0);
     bool overfull = false;
     auto measure_rows = [&]() {
@@ -488,9 +489,12 @@ int32_t run_pipeline(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_resu
         rule.R[w] = c->model.w_R64[w];
     }
 
-    // launch shape: the tuned indexed rollout shape; persistent CTAs leave room on a few SMs
-    // for the table stream's kernels
-    Geometry g = geometry_batch(c, c->S_pad, window);
+    // launch shape: the widest indexed shape (384 threads, unless the options set one). The
+    // persistent launch holds at most one CTA per SM, where more scanner warps give the
+    // shortest step; the autotuner's shapes are chosen for waves of full rollouts side by
+    // side, two CTAs per SM when a wave holds more rollouts than there are SMs. Persistent
+    // CTAs leave room on a few SMs for the table stream's kernels
+    Geometry g = geometry_indexed(c, c->S_pad, 0);
     const int resident = rollout_max_active_clusters(1, g.threads, g.smem);
     require(resident >= 1, FMDP_ERR_ARG, "the rollout shape does not fit an SM");
     const int per_sm = std::max(1, resident / std::max(1, c->n_sm));
@@ -967,10 +971,10 @@ int32_t run_pipeline(fmdp_ctx* c, const fmdp_request* reqs, int32_t n, fmdp_resu
                 ++expiries;
                 // (the rows' room stays as measured: clearing rows only lowers their fill)
             }
-            if (!draining && (xmax > kPipeExtraLimit || overfull)) draining = true;
+            if (!draining && (xmax > rebuild_mark || overfull)) draining = true;
             if (draining && inflight.empty()) {
                 stop_kernel();  // the idle CTAs give their SMs to the rebuild
-                if (xmax > kPipeExtraLimit || overfull) {  // rows whose extra lists grew long: rebuilt now
+                if (xmax > rebuild_mark || overfull) {  // rows whose extra lists grew long: rebuilt now
                     const NvtxRange range("fmdp drain: index rows rebuilt");
                     CK(cudaStreamSynchronize(P.tstream));  // no report still reads the rows
                     index_rebuild_all(c);

@@ -75,7 +75,8 @@ class Options(ctypes.Structure):
                 ("goal_reward", ctypes.c_double), ("lookahead_W", ctypes.c_int32),
                 ("cluster_size", ctypes.c_int32), ("threads_per_cta", ctypes.c_int32), ("batch_size", ctypes.c_int32),
                 ("full_scan", ctypes.c_int32), ("index_vmax_mps", ctypes.c_double), ("index_cell_m", ctypes.c_double),
-                ("index_stage_items", ctypes.c_int32), ("batch_mode", ctypes.c_int32)]
+                ("index_stage_items", ctypes.c_int32), ("batch_mode", ctypes.c_int32),
+                ("pipe_rebuild_items", ctypes.c_int32)]
 
 
 class Request(ctypes.Structure):
@@ -363,7 +364,7 @@ class Scheduler:
     def __init__(self, box, dt, gamma, actions, sep, n_slices_window=4096, max_slots=4096, heightmap=None,
                  clearance=0.0, deck_value=1000.0, static_wells=None, combine=0, wells=None, goal_reward=200.0,
                  cluster_size=0, threads_per_cta=0, batch_size=0, full_scan=False, index_vmax_mps=0.0,
-                 index_cell_m=0.0, index_stage_items=0, lookahead_W=1, batch_mode=0):
+                 index_cell_m=0.0, index_stage_items=0, lookahead_W=1, batch_mode=0, pipe_rebuild_items=0):
         self._L = load()
         air = Airspace()
         air.x0, air.y0, air.z0, air.x1, air.y1, air.z1 = map(float, box)
@@ -397,6 +398,7 @@ class Scheduler:
         opt.index_cell_m = float(index_cell_m)
         opt.index_stage_items = int(index_stage_items)
         opt.batch_mode = int(batch_mode)
+        opt.pipe_rebuild_items = int(pipe_rebuild_items)
         opt.lookahead_W = int(lookahead_W)
         if wells is not None:
             warr = (Well * len(wells))(*[Well(*map(float, w)) for w in wells])

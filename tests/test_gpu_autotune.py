@@ -75,10 +75,19 @@ def test_autotune_picks_a_candidate_caches_it_and_batches_use_it(crowded):
         assert len(s.query_plans(-(1 << 40), 1 << 40)) == len(sc.plans)
         shapes = {e["threads_per_cta"] for e in s.tune_cache()}
         assert len(s.tune_cache()) == 2
+        s.snapshot()
+        res_p = s.schedule_batch(sc.requests)  # pipelined: one CTA per SM, the widest shape
+        st_p = s.stats()
+        t_p = table_of(s)
+        s.restore()
+        s.set_batch_mode(1)  # waves: the tuned shapes
         res = s.schedule_batch(sc.requests)
         st = s.stats()
         t = table_of(s)
+    assert st_p["threads_per_cta"] == 384
     assert st["threads_per_cta"] in shapes  # the last wave's tuned shape
+    same_results(alone, res_p)
+    same_tables(t_alone, t_p)
     same_results(alone, res)
     same_tables(t_alone, t)
 
@@ -91,7 +100,7 @@ def test_cache_round_trip_and_rejected_entries(crowded):
     assert len(entries) == 1
     e = dict(entries[0])
     e["threads_per_cta"] = 192 if e["threads_per_cta"] != 192 else 256
-    with Scheduler.from_scenario(sc, batch_size=16) as s:
+    with Scheduler.from_scenario(sc, batch_size=16, batch_mode=1) as s:  # waves take the cached shape
         s.load_tune_cache([e])
         rep = s.autotune(sc.requests[:8])
         assert rep["from_cache"] == 1 and rep["chosen"]["threads_per_cta"] == e["threads_per_cta"]

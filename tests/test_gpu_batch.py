@@ -254,12 +254,13 @@ def test_influence_follows_each_well(offset, waves, batch_mode):
 def test_c2_full_size_pipelined_equals_waves_and_sequential():
     """The 3000-plan, 1000-request workload in the launch configuration the benchmark
     times (staged requests, batched): pipelined and wave results equal sequential FCFS,
-    and the pipelined run's admissions grow index rows past the rebuild mark, so the
+    and the pipelined run's admissions grow index rows past the rebuild mark (set to 192
+    appended items here, below what this workload reaches), so the
     rebuild-while-no-rollout-runs path runs."""
     sc = S.c2_plain_scale()
     out = {}
     for mode in (0, 1):
-        with Scheduler.from_scenario(sc, batch_mode=mode) as s:
+        with Scheduler.from_scenario(sc, batch_mode=mode, pipe_rebuild_items=192) as s:
             s.snapshot()
             if mode == 0:
                 out["many"] = s.schedule_many(sc.requests)
