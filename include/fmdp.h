@@ -179,13 +179,17 @@ fmdp_status fmdp_schedule_many(fmdp_ctx* ctx, const fmdp_request* reqs, int32_t 
  * time, Sec. V). Pipelined mode (options.batch_mode = 0, with the spatial index and W = 1):
  * one persistent rollout launch takes requests from a ring in host-mapped memory that the
  * host keeps filling, up to options.batch_size requests past the first unresolved one;
- * each finished plan is reported to host-mapped memory, and the host walks the requests
- * in array order: a request is final when no admission made after its plan started can
- * reach one of its successor states with a well or come within the separation minima of
- * it; an admitted request is stored at once (beside the running rollouts, its index
- * entries published only when complete), and a plan that an admission influences is
- * planned again as soon as that admission is visible. Long index extra lists are rebuilt
- * while no rollout runs. Wave mode (batch_mode = 1, or lookahead, full scan, learned
+ * each finished plan is reported to host-mapped memory. The requests just behind the
+ * first unresolved one publish their current plans in the index as tentative plans, which
+ * only later requests see (the guess that they are admitted as planned). The host walks
+ * the requests in array order: a request is final when no change of an earlier request's
+ * contribution that its plan could not have seen (a tentative plan published or
+ * withdrawn, an admission) can reach one of its successor states with a well or come
+ * within the separation minima of it; an admitted request is stored at once (beside the
+ * running rollouts, its index entries published only when complete), and a plan that a
+ * change influences is planned again, from the first step it can alter, as soon as the
+ * change is visible. Index rows whose appended lists pass options.pipe_rebuild_items are
+ * rebuilt while no rollout runs. Wave mode (batch_mode = 1, or lookahead, full scan, learned
  * proposals): the requests are taken in batches of options.batch_size. Each batch is
  * planned concurrently against the table as it stands (one persistent rollout launch
  * whose clusters pull requests from a device queue, replayed as a CUDA graph), then
