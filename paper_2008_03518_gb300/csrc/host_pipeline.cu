@@ -163,6 +163,10 @@ bool pipeline_fits(fmdp_ctx* c, int32_t n, const PipeServe* serve) {
 
 namespace {
 
+static_assert(kInflWells == kMaxWells, "the influence rule holds every well of a plan");
+
+enum Phase : uint8_t { kAbsent = 0, kWait = 1, kFlight = 2, kDone = 3, kFinal = 4 };
+
 // A published tentative plan of one request. A read that acquired the table-operation count q
 // sees the work of every operation up to q and may see any part of a later one: an item
 // appended by operation a and withdrawn by operation w is seen by the reads with

@@ -1,19 +1,20 @@
 // The pipelined engine's influence test on the host (Sec. III: a known plan changes a
 // FastMDP step only through wells that reach the step's successors; Sec. V: a conflict is a
-// pair inside both separation minima at one step). Included by the pipelined engine only.
+// pair inside both separation minima at one step). Included by the pipelined engine only;
+// plain C++ with no CUDA types, so that it can be compiled and checked on a host.
 #pragma once
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdint>
 #include <vector>
 
-#include "fmdp_internal.cuh"
-
 namespace fmdp {
 
-constexpr int kBoxChunk = 32;  // steps per bounding box of a trajectory
-constexpr int kBoxSuper = 8;   // chunks per coarse box
+constexpr int kBoxChunk = 32;   // steps per bounding box of a trajectory
+constexpr int kBoxSuper = 8;    // chunks per coarse box
+constexpr int kInflWells = 8;   // wells per plan the rule holds (the model's maximum)
 
 // ---------------------------------------------------------------- influence (host side)
 
@@ -99,7 +100,7 @@ struct TrajBoxes {
 struct InflRule {
     double dt, H, V, dzmax;
     int n_wells;
-    double tau[kMaxWells], R[kMaxWells];
+    double tau[kInflWells], R[kInflWells];
 };
 
 // Could trajectory j (of a request before k) change request k's plan or verdict at the steps
@@ -185,7 +186,5 @@ inline int first_influenced(const InflRule& P, const float* pj, int nj, int64_t 
     }
     return -1;
 }
-
-enum Phase : uint8_t { kAbsent = 0, kWait = 1, kFlight = 2, kDone = 3, kFinal = 4 };
 
 }  // namespace fmdp
